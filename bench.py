@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark of the RSOT dual + gradient hot path on one GB300 (or N replicas).
+
+Workload (default): unit cube, 32^3 hexes x 6 tets x 4-point rule = 786,432
+quadrature points, 65,536 targets from a 4-component mixture, nu ~ U(0.5,1.5)
+normalised, eps = 1e-3, dense evaluation (5.154e10 pairs per step).  A step is
+one complete dual + gradient evaluation: target prep, pass 1 (log-sum-exp),
+combine, pass 2 (gradient), final reductions.
+
+Metric: G pairs/s (pairs = nq * n per dense evaluation), inputs resident in
+HBM (`value`), and through the C ABI with host buffers (`e2e`).  L2 is flushed
+(256 MiB write) between timed steps; per-step time is taken with CUDA events
+on the library's stream, the flush outside them.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SFU_EX2_PER_CLK_PER_SM = 16          # MUFU.EX2 results / clock / SM (CUDA throughput table)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mesh", type=int, default=32, help="hexes per side (32 -> 786,432 points)")
+    ap.add_argument("--targets", type=int, default=65536)
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (recipe's clocks line)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2507_23602_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(ROOT, "paper_2507_23602_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return None
+    e = t.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(p, psi, target_seconds=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    the first S quadrature points against all targets, one dense evaluation."""
+    import oracle
+    cores = oracle.threads_used()
+    s0 = min(p.nq, max(256, cores * 64))
+    t = time.perf_counter()
+    oracle.dual_grad(p.x[:s0], p.mass[:s0], p.y, p.nu, psi, p.eps)
+    dt0 = time.perf_counter() - t
+    s = int(min(p.nq, max(s0, s0 * target_seconds / max(dt0, 1e-3))))
+    t = time.perf_counter()
+    oracle.dual_grad(p.x[:s], p.mass[:s], p.y, p.nu, psi, p.eps)
+    dt = time.perf_counter() - t
+    pairs = s * p.n
+    return {"value": pairs / dt / 1e9, "unit": "G pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"dense FP64 evaluation of quadrature points 0..{s - 1} of {p.nq} against all "
+                      f"{p.n} targets ({pairs:.3e} pairs, {dt:.1f} s)"}
+
+
+def run_reference(args, p, psi, workload):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    cores = oracle.threads_used()
+    # calibrate one step to ~ (a few minutes / (steps + warmup))
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    s0 = min(p.nq, max(256, cores * 64))
+    t = time.perf_counter()
+    oracle.dual_grad(p.x[:s0], p.mass[:s0], p.y, p.nu, psi, p.eps)
+    dt0 = time.perf_counter() - t
+    s = int(min(p.nq, max(s0, s0 * budget / max(dt0, 1e-3))))
+    for _ in range(args.warmup):
+        oracle.dual_grad(p.x[:s], p.mass[:s], p.y, p.nu, psi, p.eps)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.dual_grad(p.x[:s], p.mass[:s], p.y, p.nu, psi, p.eps)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    val = s * p.n / (ms * 1e-3) / 1e9
+    sample = f"each step: dense FP64 oracle evaluation of points 0..{s - 1} of {p.nq} x {p.n} targets"
+    print(json.dumps({
+        "impl": "reference", "metric": "dual+grad G pairs/s (dense)", "value": val,
+        "unit": "G pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "sample_points": s},
+        "cpu_baseline": {"value": val, "unit": "G pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "G pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    import numpy as np
+    import rsot_inputs as ri
+
+    p = ri.cube_3d(mesh_n=args.mesh, n_targets=args.targets, eps=args.eps)
+    psi = 0.005 * np.random.default_rng(2024).standard_normal(p.n)
+    workload = f"cube-{p.nq}x{p.n}-dense-eps{args.eps:g}"
+    if args.impl == "reference":
+        run_reference(args, p, psi, workload)
+        return
+
+    import torch
+    import paper_2507_23602_gb300 as rs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    P = rs.Problem(p.x, p.mass, p.y, p.nu, stream=torch.cuda.current_stream())
+    psi_d = torch.tensor(psi, device=dev)
+    grad_d = torch.empty(p.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    pairs = p.nq * p.n
+
+    for _ in range(args.warmup):
+        P.eval(psi_d, p.eps, 0.0, rs.MIXED, grad_out=grad_d)
+
+    clocks = Clocks(local)
+    P.kernel_timing(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record()
+        P.eval(psi_d, p.eps, 0.0, rs.MIXED, grad_out=grad_d)
+        ends[k].record()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ktimes = P.kernel_times()
+    P.kernel_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = pairs * args.steps * world / total_s / 1e9
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    e2e = None
+    if not args.no_e2e:
+        psi_h = torch.tensor(psi, dtype=torch.float64).pin_memory()
+        grad_h = torch.empty(p.n, dtype=torch.float64).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            P.eval(psi_h, p.eps, 0.0, rs.MIXED, grad_out=grad_h)
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            P.eval(psi_h, p.eps, 0.0, rs.MIXED, grad_out=grad_h)
+            e2e_s += time.perf_counter() - t
+        if world > 1:
+            import torch.distributed as tdist
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": pairs * args.steps * world / e2e_s / 1e9, "unit": "G pairs/s",
+               "h2d_bytes_per_step": p.n * 8, "d2h_bytes_per_step": p.n * 8 + 48}
+
+    if rank != 0:
+        P.close()
+        return
+
+    # roofline of the dominant kernel (exponential-bound: 1 ex2 per pair per pass)
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    tot_ms, launches = ktimes[dom]
+    per_launch_s = tot_ms / launches / 1e3
+    ex2_per_launch = pairs if dom in ("lse_mixed", "grad_mixed") else float("nan")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SFU_EX2_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e9
+    achieved = ex2_per_launch / per_launch_s / 1e9
+    try:
+        probe = rs.probe_ex2_rate() / 1e9
+    except Exception:
+        probe = None
+    roof = {"bound": "alu", "unit": "Gex2/s", "kernel": dom, "achieved": achieved, "peak": peak,
+            "frac": achieved / peak,
+            "peak_basis": f"{SFU_EX2_PER_CLK_PER_SM} ex2/clk/SM x {sms} SMs x {sm_max:.0f} MHz "
+                          "(nominal unit count at the maximum SM clock)",
+            "probe_ex2_gps": probe,
+            "frac_of_probe": (achieved / probe) if probe else None,
+            "traffic": traffic_for(dom, workload),
+            "per_kernel_ms": {k: v[0] / v[1] for k, v in ktimes.items()}}
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (SFU_EX2_PER_CLK_PER_SM * sms * clk["sm_mhz"] * 1e6 / 1e9)
+
+    out = {
+        "metric": "dual+grad G pairs/s (dense)", "value": value, "unit": "G pairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload, "nq": p.nq, "n": p.n, "eps": p.eps,
+                   "pairs_per_step": pairs, "precision": "mixed (f32 pairs, f64 reductions)",
+                   "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(sum(v[1] for v in ktimes.values())),
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, psi)
+    print(json.dumps(out))
+    P.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * rsot.h -- C ABI of librsot, a GB300 (sm_103a) implementation of the
+ * entropy-regularised semi-discrete optimal transport (RSOT) dual evaluation
+ * and its solver.
+ *
+ * Notation (Sec. 2-3 of the paper): quadrature points x_q in R^d with masses
+ * m_q = rho_h(x_q) w_q (Remark 3.1), targets y_j with weights nu_j, dual
+ * potentials psi in R^N, regularisation eps > 0, cost c(x,y) = |x - y|^2 / 2.
+ *
+ *   J(psi)        = sum_q m_q eps ln sum_j nu_j exp((psi_j - c(x_q,y_j))/eps)
+ *                   - sum_j psi_j nu_j                       (Eq. discretized_functional)
+ *   dJ/dpsi_k     = sum_q m_q p_k(x_q|psi) - nu_k            (Eq. discretized_gradient)
+ *   p_k(x|psi)    = nu_k e^{(psi_k - c(x,y_k))/eps} / sum_j nu_j e^{(psi_j - c(x,y_j))/eps}
+ *                                                            (Eq. final_plan_density)
+ *
+ * Truncation (Sec. 4.1, Algorithm 2) keeps, for each point, only the targets
+ * with c(x_q, y_j) < C, i.e. |x_q - y_j| < radius with radius = sqrt(2 C).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are plain pointers.  Unless a comment says otherwise a
+ *     pointer may address host memory or device memory of the current CUDA
+ *     device (the library copies with cudaMemcpyDefault); row-major layout;
+ *     the caller owns every buffer it passes and keeps ownership.
+ *   - Outputs are written only when the call returns RSOT_OK.
+ *   - Calls are synchronous with respect to their host-visible outputs and
+ *     run on the stream set by rsot_set_stream (default: the legacy stream).
+ *   - No call throws; errors are status codes.  A handle is not thread-safe.
+ */
+#ifndef RSOT_H
+#define RSOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsot_problem rsot_problem;   /* opaque; owns its device memory */
+
+typedef enum {
+    RSOT_OK = 0,
+    RSOT_ERR_ARG = 1,                 /* invalid argument (sizes, eps <= 0, null) */
+    RSOT_ERR_CUDA = 2,                /* a CUDA runtime call failed              */
+    RSOT_ERR_NONFINITE = 3,           /* psi, J or the gradient is not finite     */
+    RSOT_ERR_EMPTY_NEIGHBORHOOD = 4,  /* a point had no target within the radius */
+    RSOT_ERR_NOT_CONVERGED = 5,       /* the solver hit its iteration cap        */
+    RSOT_ERR_LINESEARCH = 6,          /* the line search found no Wolfe step     */
+    RSOT_ERR_TIMEOUT = 7,             /* a bounded device-side wait gave up      */
+    RSOT_ERR_NOMEM = 8                /* device allocation failed                */
+} rsot_status;
+
+typedef enum {
+    RSOT_FP64 = 0,   /* every operation in FP64                                 */
+    RSOT_MIXED = 1   /* FP32 pair arithmetic (ex2.approx), FP64 reductions       */
+} rsot_precision;
+
+/* Human-readable name of a status code (static string). */
+const char *rsot_status_string(rsot_status s);
+
+/* Version string of the library build (static string). */
+const char *rsot_version(void);
+
+/*
+ * Create a problem: the discrete source measure sum_q m_q delta_{x_q}
+ * (Remark 3.1) and the target measure sum_j nu_j delta_{y_j} (Sec. 2).
+ *   d      : dimension, 2 or 3
+ *   nq     : number of quadrature points, >= 1
+ *   x      : nq*d doubles (row-major), mass: nq doubles, m_q >= 0
+ *   n      : number of targets, >= 1
+ *   y      : n*d doubles (row-major), nu: n doubles, nu_j > 0
+ * The inputs are copied to device memory owned by the handle; the caller's
+ * buffers may be freed after the call.  Sum m_q and sum nu_j are used as
+ * given (the paper's normalisation sum = 1 is the caller's choice).
+ * Errors: RSOT_ERR_ARG, RSOT_ERR_NOMEM, RSOT_ERR_CUDA.
+ */
+rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass,
+                        int64_t n, const double *y, const double *nu,
+                        rsot_problem **out);
+
+/* Free every resource of the handle (NULL is accepted). */
+void rsot_destroy(rsot_problem *p);
+
+/* Use `stream` (a cudaStream_t; NULL = legacy default stream) for all work. */
+rsot_status rsot_set_stream(rsot_problem *p, void *stream);
+
+/*
+ * One evaluation of J(psi) and grad J(psi) -- Algorithm 2.
+ *   psi       : n doubles (host or device)
+ *   eps       : regularisation, > 0
+ *   radius    : <= 0 or +inf -> dense evaluation over all pairs (Eq.
+ *               discretized_functional / discretized_gradient);
+ *               > 0 -> truncated: only pairs with |x_q - y_j| < radius
+ *               (c < C with C = radius^2/2, Sec. 4.1)
+ *   prec      : RSOT_FP64 or RSOT_MIXED
+ *   J_out     : host pointer, 1 double
+ *   grad_out  : n doubles (host or device)
+ *   pairs_out : host pointer or NULL; receives sum_q |I_q|, the pairs whose
+ *               terms entered the sums (nq*n when dense)
+ * Errors: RSOT_ERR_ARG, RSOT_ERR_NONFINITE (psi not finite or J/grad not
+ * finite), RSOT_ERR_EMPTY_NEIGHBORHOOD (truncated and some point kept no
+ * target; Algorithm 2 skips such points and the outputs are still written
+ * for inspection, but the status reports it), RSOT_ERR_TIMEOUT, RSOT_ERR_CUDA.
+ */
+rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps,
+                                double radius, rsot_precision prec,
+                                double *J_out, double *grad_out, int64_t *pairs_out);
+
+/*
+ * Per-point log partition of the last successful rsot_eval_dual_grad call:
+ *   L_q = ln sum_{j in I_q} nu_j exp((psi_j - c(x_q, y_j))/eps)
+ * (the integrand of Eq. discretized_functional divided by eps; I_q all
+ * targets when the evaluation was dense), in the precision of that call.
+ *   L_out : nq doubles (host or device), in the caller's point order.
+ * Errors: RSOT_ERR_ARG when no evaluation has succeeded on this handle.
+ */
+rsot_status rsot_point_log_partition(rsot_problem *p, double *L_out);
+
+/*
+ * Covering cost C_0 = max_q min_j c(x_q, y_j) over the quadrature points
+ * (App. B).  Depends on geometry only; computed once and cached.
+ */
+rsot_status rsot_covering_cost(rsot_problem *p, double *C0_out);
+
+/*
+ * Truncation radius for a tail tolerance (Sec. 4.1 and App. B, applied per
+ * point): C = C_0 + Gamma + eps ln(1 / (nu_min tail)), Gamma = max psi -
+ * min psi, radius = sqrt(2 C).  With this radius no point loses all its
+ * targets, the excluded mass at every point is at most tail times the kept
+ * mass, |J - J_trunc| <= eps tail sum_q m_q, and per target
+ * |dJ/dpsi_j - dJ_trunc/dpsi_j| <= tail (sum_q m_q p~_qj + nu_j).
+ *   psi : n doubles (host or device); tail in (0, 1).
+ */
+rsot_status rsot_radius_for_tail(rsot_problem *p, const double *psi, double eps,
+                                 double tail, double *radius_out);
+
+/*
+ * Kernel tracing (no counterpart in the paper: a runtime facility).  While
+ * enabled, every kernel the library launches is bracketed by CUDA events on
+ * the handle's stream and its device time is accumulated per kernel name.
+ * rsot_kernel_times copies up to `max` entries (static name strings, total
+ * milliseconds, launch counts) and returns how many kernels have entries;
+ * rsot_kernel_timing(p, 1) also clears the totals.
+ */
+rsot_status rsot_kernel_timing(rsot_problem *p, int enable);
+int rsot_kernel_times(rsot_problem *p, const char **names, double *total_ms,
+                      int64_t *launches, int max);
+
+/*
+ * Throughput probe of the special-function unit (no counterpart in the
+ * paper): times `iters` rounds of independent ex2.approx.ftz.f32 on the
+ * current device and returns the measured ex2 results per second.  Used as
+ * the measured ceiling of the exponential-bound kernels.
+ */
+rsot_status rsot_probe_ex2_rate(int iters, double *ex2_per_s);
+
+/* Solver options (Algorithm 1 with the eps-schedule of Sec. 4.2). */
+typedef struct {
+    double eps;          /* final regularisation, > 0                              */
+    double eps_start;    /* first stage of the eps-schedule; <= eps: no schedule   */
+    double eps_factor;   /* stage ratio in (0,1), e.g. 0.5; the last stage is eps  */
+    double tail;         /* > 0: truncate with rsot_radius_for_tail each evaluation;
+                            0: dense                                               */
+    double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
+    double stage_tol_l1; /* tolerance of the intermediate stages (<=0: tol_l1)      */
+    int precision;       /* rsot_precision of the evaluations                       */
+    int refine_fp64;     /* MIXED only: finish the last stage with FP64 evaluations */
+    int lbfgs_m;         /* L-BFGS memory (<= 0: 10)                                */
+    int max_iter;        /* iteration cap per stage (<= 0: 10000)                   */
+    int verbose;         /* print one line per iteration to stderr                 */
+} rsot_options;
+
+/* Fill *o with the defaults (eps 1e-2, no schedule, dense, tol 1e-6, MIXED with
+ * FP64 refinement, m = 10, 10000 iterations). */
+void rsot_default_options(rsot_options *o);
+
+/* Per-solve statistics. */
+typedef struct {
+    double J;            /* J at the returned psi (last stage's precision)       */
+    double grad_l1;      /* ||grad J||_1 at the returned psi                      */
+    int iters;           /* L-BFGS iterations over all stages                     */
+    int evals;           /* dual evaluations over all stages                      */
+    int stages;          /* eps stages run                                        */
+    int64_t pairs;       /* pairs evaluated over all evaluations                  */
+    double seconds;      /* wall time of the call                                 */
+} rsot_solve_stats;
+
+/*
+ * Minimise J with FP64 L-BFGS on the host (two-loop recursion, strong-Wolfe
+ * line search, curvature pairs in FP64), each evaluation on the GPU
+ * (Algorithm 1), with eps-scheduling and warm start (Sec. 4.2).
+ *   psi_inout : n doubles, HOST memory: the warm start on entry, the
+ *               minimiser on return (also on NOT_CONVERGED / LINESEARCH,
+ *               where it is the last accepted iterate).
+ * Errors: RSOT_ERR_ARG, RSOT_ERR_NOT_CONVERGED, RSOT_ERR_LINESEARCH, and any
+ * error of rsot_eval_dual_grad.
+ */
+rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *opt,
+                       rsot_solve_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSOT_H */

@@ -11,6 +11,7 @@ Contents
                           strict predicate c(x_q, y_j) < C tested for every j
                           (Eq. discretized_functional / discretized_gradient).
   * ``plan``           -- the plan density p_j(x_q | psi), Eq. final_plan_density.
+  * ``point_lse``      -- the per-point log partition L_q of Eq. discretized_functional.
   * ``covering_cost``  -- C_0 of App. B over the quadrature points.
   * ``softmax_refine`` -- Eq. softmax_refinement_formula.
   * ``truncation``     -- the cutoffs C_pw, C_int, C_geom (Sec. 4.1, App. B) and
@@ -53,6 +54,8 @@ def _load():
         lib.oracle_softmax_refine.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp,
                                               ctypes.c_int64, dp, dp, dp, ctypes.c_int64, dp,
                                               ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_point_lse.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
+                                         dp, dp, ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_threads_used.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
@@ -104,6 +107,21 @@ def plan(x, y, nu, psi, eps):
     if rc != 0:
         raise ValueError("oracle_plan failed")
     return P
+
+
+def point_lse(x, y, nu, psi, eps, threads=0):
+    """L_q = ln sum_j nu_j exp((psi_j - c(x_q, y_j))/eps) for every q."""
+    lib = _load()
+    x, xp = _f64(x)
+    y, yp = _f64(y)
+    nu, nup = _f64(nu)
+    psi, pp = _f64(psi)
+    out = np.empty(x.shape[0])
+    rc = lib.oracle_point_lse(x.shape[1], x.shape[0], xp, y.shape[0], yp, nup, pp, float(eps),
+                              int(threads), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("oracle_point_lse failed")
+    return out
 
 
 def covering_cost(x, y, threads=0):

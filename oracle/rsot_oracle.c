@@ -203,6 +203,36 @@ int oracle_plan(int d, int64_t nq, const double *x, int64_t n, const double *y,
     return 0;
 }
 
+/*
+ * Per-point log partition L_q = ln sum_j nu_j exp((psi_j - c(x_q, y_j))/eps),
+ * the quantity whose eps-multiple is integrated in Eq. discretized_functional
+ * (and whose exponential is the denominator of Eq. final_plan_density),
+ * max-shifted.  Dense only.
+ */
+int oracle_point_lse(int d, int64_t nq, const double *x, int64_t n, const double *y,
+                     const double *nu, const double *psi, double eps, int threads, double *L)
+{
+    if (d < 1 || d > 3 || n < 1 || !(eps > 0.0))
+        return -1;
+    int T = nthreads_of(threads);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static)
+#endif
+    for (int64_t q = 0; q < nq; ++q) {
+        double smax = -INFINITY;
+        for (int64_t j = 0; j < n; ++j) {
+            double s = (psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]);
+            if (s > smax)
+                smax = s;
+        }
+        nsum_t S = {0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j)
+            nadd(&S, exp((psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]) - smax));
+        L[q] = smax + log(nval(&S));
+    }
+    return 0;
+}
+
 /* Covering cost C_0 = max_q min_j c(x_q, y_j) over the quadrature points
  * (App. B, the discrete counterpart of the max over the domain). */
 int oracle_covering_cost(int d, int64_t nq, const double *x, int64_t n, const double *y,

@@ -1,0 +1,262 @@
+"""Python binding of librsot (GB300 / sm_103a) -- argument marshalling only.
+
+Every step of the dual evaluation and of the solver runs in librsot.so (CUDA
+kernels plus the host L-BFGS driver in C++).  This module only converts
+arrays to pointers and status codes to exceptions.  It never computes the
+method on the CPU: when the library is missing, ``load()`` raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+CUDA tensors are passed as device pointers, so device-resident inputs and
+outputs stay on the GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+__all__ = ["load", "lib_path", "RsotError", "Problem", "SolveOptions", "SolveStats",
+           "FP64", "MIXED", "STATUS", "probe_ex2_rate"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librsot.so")
+_lib = None
+
+FP64, MIXED = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
+          4: "empty neighbourhood", 5: "not converged", 6: "line search failed",
+          7: "device wait timed out", 8: "out of device memory"}
+RSOT_ERR_EMPTY_NEIGHBORHOOD = 4
+
+
+class RsotError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"librsot: {what}: {STATUS.get(self.status, self.status)} ({self.status})")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("eps_start", ctypes.c_double),
+                ("eps_factor", ctypes.c_double), ("tail", ctypes.c_double),
+                ("tol_l1", ctypes.c_double), ("stage_tol_l1", ctypes.c_double),
+                ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
+                ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("grad_l1", ctypes.c_double), ("iters", ctypes.c_int),
+                ("evals", ctypes.c_int), ("stages", ctypes.c_int), ("pairs", ctypes.c_int64),
+                ("seconds", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class SolveOptions:
+    eps: float = 1e-2
+    eps_start: float = 0.0
+    eps_factor: float = 0.5
+    tail: float = 0.0
+    tol_l1: float = 1e-6
+    stage_tol_l1: float = 0.0
+    precision: int = MIXED
+    refine_fp64: bool = True
+    lbfgs_m: int = 10
+    max_iter: int = 10000
+    verbose: bool = False
+
+    def _c(self):
+        return _Options(self.eps, self.eps_start, self.eps_factor, self.tail, self.tol_l1,
+                        self.stage_tol_l1, int(self.precision), int(bool(self.refine_fp64)),
+                        int(self.lbfgs_m), int(self.max_iter), int(bool(self.verbose)))
+
+
+@dataclasses.dataclass
+class SolveStats:
+    status: int
+    J: float
+    grad_l1: float
+    iters: int
+    evals: int
+    stages: int
+    pairs: int
+    seconds: float
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load librsot.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"librsot.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    lib.rsot_status_string.restype = ctypes.c_char_p
+    lib.rsot_status_string.argtypes = [ctypes.c_int]
+    lib.rsot_version.restype = ctypes.c_char_p
+    lib.rsot_create.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp,
+                                ctypes.POINTER(vp)]
+    lib.rsot_destroy.argtypes = [vp]
+    lib.rsot_destroy.restype = None
+    lib.rsot_set_stream.argtypes = [vp, vp]
+    lib.rsot_eval_dual_grad.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        dp, vp, i64p]
+    lib.rsot_covering_cost.argtypes = [vp, dp]
+    lib.rsot_point_log_partition.argtypes = [vp, vp]
+    lib.rsot_radius_for_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, dp]
+    lib.rsot_default_options.argtypes = [ctypes.POINTER(_Options)]
+    lib.rsot_default_options.restype = None
+    lib.rsot_solve.argtypes = [vp, dp, ctypes.POINTER(_Options), ctypes.POINTER(_Stats)]
+    lib.rsot_kernel_timing.argtypes = [vp, ctypes.c_int]
+    lib.rsot_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), dp, i64p, ctypes.c_int]
+    lib.rsot_kernel_times.restype = ctypes.c_int
+    lib.rsot_probe_ex2_rate.argtypes = [ctypes.c_int, dp]
+    _lib = lib
+    return lib
+
+
+def probe_ex2_rate(iters: int = 20000) -> float:
+    """Measured ex2.approx results per second of the current device."""
+    v = ctypes.c_double()
+    _check(load().rsot_probe_ex2_rate(int(iters), ctypes.byref(v)), "probe_ex2_rate")
+    return v.value
+
+
+def _ptr(a):
+    """(pointer, keep-alive object) for a numpy array or a torch tensor (float64)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64:
+                a = a.to(torch.float64)
+            a = a.contiguous()
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _is_cuda(a):
+    try:
+        import torch
+        return isinstance(a, torch.Tensor) and a.is_cuda
+    except ImportError:
+        return False
+
+
+def _check(st, what):
+    if st != 0:
+        raise RsotError(st, what)
+
+
+class Problem:
+    """An RSOT problem held on the GPU: quadrature points x (nq, d), masses
+    (nq,), targets y (n, d), weights nu (n,)."""
+
+    def __init__(self, x, mass, y, nu, stream=None):
+        lib = load()
+        d = int(x.shape[1])
+        self.d, self.nq, self.n = d, int(x.shape[0]), int(y.shape[0])
+        px, kx = _ptr(x)
+        pm, km = _ptr(mass)
+        py, ky = _ptr(y)
+        pn, kn = _ptr(nu)
+        h = ctypes.c_void_p()
+        _check(lib.rsot_create(d, self.nq, px, pm, self.n, py, pn, ctypes.byref(h)), "create")
+        self._h = h
+        self._lib = lib
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        self.set_stream(stream)
+
+    def set_stream(self, stream):
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(self._lib.rsot_set_stream(self._h, ctypes.c_void_p(s or 0)), "set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rsot_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, psi, eps, radius=0.0, precision=MIXED, grad_out=None, allow_empty=False):
+        """(J, grad, pairs): Eq. discretized_functional / discretized_gradient,
+        dense when radius <= 0, else truncated at |x - y| < radius."""
+        pp, kp = _ptr(psi)
+        if grad_out is None:
+            if _is_cuda(psi):
+                import torch
+                grad_out = torch.empty(self.n, dtype=torch.float64, device=psi.device)
+            else:
+                grad_out = np.empty(self.n)
+        pg, kg = _ptr(grad_out)
+        J = ctypes.c_double()
+        pairs = ctypes.c_int64()
+        st = self._lib.rsot_eval_dual_grad(self._h, pp, float(eps), float(radius), int(precision),
+                                           ctypes.byref(J), pg, ctypes.byref(pairs))
+        if not (st == 0 or (allow_empty and st == RSOT_ERR_EMPTY_NEIGHBORHOOD)):
+            raise RsotError(st, "eval_dual_grad")
+        return J.value, grad_out, pairs.value
+
+    def point_log_partition(self, out=None):
+        """L_q of the last evaluation (numpy unless `out` is given)."""
+        if out is None:
+            out = np.empty(self.nq)
+        po, ko = _ptr(out)
+        _check(self._lib.rsot_point_log_partition(self._h, po), "point_log_partition")
+        return out
+
+    def kernel_timing(self, enable=True):
+        """Bracket every library kernel with CUDA events (clears the totals)."""
+        _check(self._lib.rsot_kernel_timing(self._h, int(bool(enable))), "kernel_timing")
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} accumulated while timing was on."""
+        k = self._lib.rsot_kernel_times(self._h, None, None, None, 0)
+        names = (ctypes.c_char_p * max(k, 1))()
+        tot = (ctypes.c_double * max(k, 1))()
+        cnt = (ctypes.c_int64 * max(k, 1))()
+        self._lib.rsot_kernel_times(self._h, names, tot, cnt, k)
+        return {names[i].decode(): (tot[i], cnt[i]) for i in range(k)}
+
+    def covering_cost(self):
+        v = ctypes.c_double()
+        _check(self._lib.rsot_covering_cost(self._h, ctypes.byref(v)), "covering_cost")
+        return v.value
+
+    def radius_for_tail(self, psi, eps, tail):
+        pp, kp = _ptr(psi)
+        v = ctypes.c_double()
+        _check(self._lib.rsot_radius_for_tail(self._h, pp, float(eps), float(tail), ctypes.byref(v)),
+               "radius_for_tail")
+        return v.value
+
+    def solve(self, psi0=None, options: Optional[SolveOptions] = None, raise_on_error=True, **kw):
+        """FP64 L-BFGS (host) over GPU evaluations; returns (psi, SolveStats)."""
+        opts = options or SolveOptions(**kw)
+        psi = np.zeros(self.n) if psi0 is None else np.array(psi0, dtype=np.float64, copy=True)
+        o = opts._c()
+        s = _Stats()
+        st = self._lib.rsot_solve(self._h, psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.byref(o), ctypes.byref(s))
+        stats = SolveStats(st, s.J, s.grad_l1, s.iters, s.evals, s.stages, s.pairs, s.seconds)
+        if raise_on_error and st != 0:
+            raise RsotError(st, "solve")
+        return psi, stats

@@ -1,0 +1,380 @@
+// C ABI of librsot: problem setup, one dual evaluation, covering cost and
+// truncation radius.  The solver lives in rsot_solve.cpp.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rsot_internal.cuh"
+
+using namespace rsot;
+
+namespace {
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+rsot_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return RSOT_OK;
+    if (e == cudaErrorMemoryAllocation) return RSOT_ERR_NOMEM;
+    return RSOT_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const T *src, size_t count) {
+    cudaError_t e = cudaMalloc(dst, count * sizeof(T));
+    if (e) return e;
+    return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+struct NSum {   // Neumaier-compensated host sum
+    double s = 0.0, c = 0.0;
+    void add(double v) {
+        const double t = s + v;
+        c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    double val() const { return s + c; }
+};
+
+}  // namespace
+
+namespace rsot {
+
+void trace_begin(rsot_problem *p, const char *name) {
+    if (!p->timing) return;
+    if ((int)p->tr_events.size() < p->tr_used + 2) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            p->tr_events.push_back(e);
+        }
+    }
+    p->tr_open.emplace_back(name, p->tr_used);
+    cudaEventRecord(p->tr_events[p->tr_used], p->stream);
+    p->tr_used += 2;
+}
+
+void trace_end(rsot_problem *p) {
+    if (!p->timing || p->tr_open.empty()) return;
+    cudaEventRecord(p->tr_events[p->tr_open.back().second + 1], p->stream);
+}
+
+void trace_collect(rsot_problem *p) {
+    for (auto &o : p->tr_open) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->tr_events[o.second], p->tr_events[o.second + 1]) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        size_t k = 0;
+        while (k < p->tr_names.size() && std::string(p->tr_names[k]) != o.first) ++k;
+        if (k == p->tr_names.size()) {
+            p->tr_names.push_back(o.first);
+            p->tr_total_ms.push_back(0.0);
+            p->tr_count.push_back(0);
+        }
+        p->tr_total_ms[k] += ms;
+        p->tr_count[k] += 1;
+    }
+    p->tr_open.clear();
+    p->tr_used = 0;
+}
+
+int64_t num_targets(const rsot_problem *p) { return p->n; }
+void copy_nu(const rsot_problem *p, double *out) {
+    cudaMemcpy(out, p->nu, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost);
+}
+}  // namespace rsot
+
+extern "C" {
+
+const char *rsot_status_string(rsot_status s) {
+    switch (s) {
+        case RSOT_OK: return "ok";
+        case RSOT_ERR_ARG: return "invalid argument";
+        case RSOT_ERR_CUDA: return "CUDA error";
+        case RSOT_ERR_NONFINITE: return "non-finite value";
+        case RSOT_ERR_EMPTY_NEIGHBORHOOD: return "a point has no target within the radius";
+        case RSOT_ERR_NOT_CONVERGED: return "iteration limit reached";
+        case RSOT_ERR_LINESEARCH: return "line search failed";
+        case RSOT_ERR_TIMEOUT: return "device wait timed out";
+        case RSOT_ERR_NOMEM: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char *rsot_version(void) { return "rsot-gb300 0.1 (sm_103a)"; }
+
+void rsot_destroy(rsot_problem *p) {
+    if (!p) return;
+    trunc_free(p);
+    dense_free(p);
+    cudaFree(p->xs);
+    cudaFree(p->x64);
+    cudaFree(p->mass);
+    cudaFree(p->lmass2);
+    cudaFree(p->y64);
+    cudaFree(p->nu);
+    cudaFree(p->lnu);
+    cudaFree(p->psi_dev);
+    cudaFree(p->grad_dev);
+    cudaFree(p->res_dev);
+    if (p->res_host) cudaFreeHost(p->res_host);
+    for (cudaEvent_t e : p->tr_events) cudaEventDestroy(e);
+    delete p;
+}
+
+rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, int64_t n,
+                        const double *y, const double *nu, rsot_problem **out) {
+    if (!out) return RSOT_ERR_ARG;
+    *out = nullptr;
+    if ((d != 2 && d != 3) || nq < 1 || n < 1 || !x || !mass || !y || !nu) return RSOT_ERR_ARG;
+    if (nq > (int64_t)1 << 31 || n > (int64_t)1 << 30) return RSOT_ERR_ARG;
+
+    std::vector<double> hx((size_t)nq * d), hm((size_t)nq), hy((size_t)n * d), hnu((size_t)n);
+    if (cudaMemcpy(hx.data(), x, hx.size() * 8, cudaMemcpyDefault) ||
+        cudaMemcpy(hm.data(), mass, hm.size() * 8, cudaMemcpyDefault) ||
+        cudaMemcpy(hy.data(), y, hy.size() * 8, cudaMemcpyDefault) ||
+        cudaMemcpy(hnu.data(), nu, hnu.size() * 8, cudaMemcpyDefault)) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nq; ++i) {
+        if (!(hm[i] >= 0.0) || !isfinite(hm[i])) return RSOT_ERR_ARG;
+        for (int k = 0; k < d; ++k) {
+            const double v = hx[i * d + k];
+            if (!isfinite(v)) return RSOT_ERR_ARG;
+            lo[k] = std::min(lo[k], v);
+            hi[k] = std::max(hi[k], v);
+        }
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        if (!(hnu[j] > 0.0) || !isfinite(hnu[j])) return RSOT_ERR_ARG;
+        for (int k = 0; k < d; ++k) {
+            const double v = hy[j * d + k];
+            if (!isfinite(v)) return RSOT_ERR_ARG;
+            lo[k] = std::min(lo[k], v);
+            hi[k] = std::max(hi[k], v);
+        }
+    }
+
+    rsot_problem *p = new rsot_problem();
+    p->d = d;
+    p->nq = nq;
+    p->n = n;
+    cudaGetDevice(&p->dev);
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->dev);
+    for (int k = 0; k < d; ++k) p->origin[k] = 0.5 * (lo[k] + hi[k]);
+    p->nq_pad = round_up(nq, 1024);
+
+    // translated coordinates (cost is translation invariant)
+    std::vector<float> xs((size_t)d * p->nq_pad, 0.0f);
+    std::vector<double> lm2((size_t)nq);
+    NSum ms, hh;
+    for (int64_t i = 0; i < nq; ++i) {
+        double r2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            const double v = hx[i * d + k] - p->origin[k];
+            hx[i * d + k] = v;
+            xs[(size_t)k * p->nq_pad + i] = (float)v;
+            r2 += v * v;
+        }
+        ms.add(hm[i]);
+        hh.add(hm[i] * 0.5 * r2);
+        lm2[i] = hm[i] > 0.0 ? log2(hm[i]) : -INFINITY;
+    }
+    p->msum = ms.val();
+    p->hx = hh.val();
+    std::vector<double> lnu((size_t)n);
+    p->nu_min = INFINITY;
+    p->nu_max = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int k = 0; k < d; ++k) hy[j * d + k] -= p->origin[k];
+        lnu[j] = log(hnu[j]);
+        p->nu_min = std::min(p->nu_min, hnu[j]);
+        p->nu_max = std::max(p->nu_max, hnu[j]);
+    }
+
+    cudaError_t e = cudaSuccess;
+    if (!e) e = upload(&p->xs, xs.data(), xs.size());
+    if (!e) e = upload(&p->x64, hx.data(), hx.size());
+    if (!e) e = upload(&p->mass, hm.data(), hm.size());
+    if (!e) e = upload(&p->lmass2, lm2.data(), lm2.size());
+    if (!e) e = upload(&p->y64, hy.data(), hy.size());
+    if (!e) e = upload(&p->nu, hnu.data(), hnu.size());
+    if (!e) e = upload(&p->lnu, lnu.data(), lnu.size());
+    if (!e) e = dense_alloc(p);
+    if (!e) e = cudaMalloc(&p->psi_dev, (size_t)n * 8);
+    if (!e) e = cudaMalloc(&p->grad_dev, (size_t)n * 8);
+    if (!e) e = cudaMalloc(&p->res_dev, sizeof(EvalResult) + 8 * sizeof(double));
+    if (!e) e = cudaMallocHost(&p->res_host, sizeof(EvalResult) + 8 * sizeof(double));
+    if (e) {
+        cudaGetLastError();
+        rsot_destroy(p);
+        return from_cuda(e);
+    }
+    p->flags = &p->res_dev->flags;
+    *out = p;
+    return RSOT_OK;
+}
+
+rsot_status rsot_set_stream(rsot_problem *p, void *stream) {
+    if (!p) return RSOT_ERR_ARG;
+    p->stream = (cudaStream_t)stream;
+    return RSOT_OK;
+}
+
+rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, double radius,
+                                rsot_precision prec, double *J_out, double *grad_out,
+                                int64_t *pairs_out) {
+    if (!p || !psi || !J_out || !grad_out) return RSOT_ERR_ARG;
+    if (!(eps > 0.0) || !isfinite(eps) || isnan(radius)) return RSOT_ERR_ARG;
+    if (prec != RSOT_FP64 && prec != RSOT_MIXED) return RSOT_ERR_ARG;
+    cudaStream_t st = p->stream;
+    const size_t nb = (size_t)p->n * sizeof(double);
+    const double *psid = psi;
+    cudaError_t e = cudaSuccess;
+    if (!is_device_ptr(psi)) {
+        e = cudaMemcpyAsync(p->psi_dev, psi, nb, cudaMemcpyHostToDevice, st);
+        psid = p->psi_dev;
+    }
+    const bool gdev = is_device_ptr(grad_out);
+    double *gd = gdev ? grad_out : p->grad_dev;
+    if (!e) e = cudaMemsetAsync(p->res_dev, 0, sizeof(EvalResult), st);
+    const bool dense = !(radius > 0.0) || isinf(radius);
+    if (!e) {
+        if (dense)
+            e = (prec == RSOT_MIXED) ? launch_dense_mixed(p, psid, eps, gd)
+                                     : launch_dense_fp64(p, psid, eps, gd);
+        else
+            e = trunc_eval(p, psid, eps, radius, prec == RSOT_MIXED, gd);
+    }
+    if (!e && !gdev) e = cudaMemcpyAsync(grad_out, gd, nb, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(EvalResult), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) {
+        cudaGetLastError();
+        p->tr_open.clear();
+        p->tr_used = 0;
+        return from_cuda(e);
+    }
+    trace_collect(p);
+    const EvalResult r = *p->res_host;
+    p->last_kind = -1;
+    if (r.flags & kErrTimeout) return RSOT_ERR_TIMEOUT;
+    if (r.flags & kErrBadCell) return RSOT_ERR_CUDA;
+    if (r.flags & kErrNonfinitePsi) return RSOT_ERR_NONFINITE;
+    if (!isfinite(r.J)) return RSOT_ERR_NONFINITE;
+    *J_out = r.J;
+    if (pairs_out) *pairs_out = dense ? p->nq * p->n : (int64_t)r.pairs;
+    p->last_kind = dense ? (prec == RSOT_MIXED ? 1 : 0) : (prec == RSOT_MIXED ? 3 : 2);
+    p->last_eps = eps;
+    if (!dense && r.empty > 0) return RSOT_ERR_EMPTY_NEIGHBORHOOD;
+    return RSOT_OK;
+}
+
+rsot_status rsot_kernel_timing(rsot_problem *p, int enable) {
+    if (!p) return RSOT_ERR_ARG;
+    p->timing = enable ? 1 : 0;
+    if (enable) {
+        p->tr_names.clear();
+        p->tr_total_ms.clear();
+        p->tr_count.clear();
+    }
+    return RSOT_OK;
+}
+
+int rsot_kernel_times(rsot_problem *p, const char **names, double *total_ms, int64_t *launches,
+                      int max) {
+    if (!p) return 0;
+    const int k = (int)p->tr_names.size();
+    for (int i = 0; i < k && i < max; ++i) {
+        if (names) names[i] = p->tr_names[i];
+        if (total_ms) total_ms[i] = p->tr_total_ms[i];
+        if (launches) launches[i] = p->tr_count[i];
+    }
+    return k;
+}
+
+rsot_status rsot_point_log_partition(rsot_problem *p, double *L_out) {
+    if (!p || !L_out || p->last_kind < 0) return RSOT_ERR_ARG;
+    const bool ddev = is_device_ptr(L_out);
+    double *tgt = ddev ? L_out : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!ddev) e = cudaMallocAsync(&tgt, (size_t)p->nq * 8, p->stream);
+    if (!e) e = (p->last_kind >= 2) ? trunc_point_L(p, tgt) : launch_point_L(p, tgt);
+    if (!e && !ddev)
+        e = cudaMemcpyAsync(L_out, tgt, (size_t)p->nq * 8, cudaMemcpyDeviceToHost, p->stream);
+    if (!ddev && tgt) cudaFreeAsync(tgt, p->stream);
+    if (!e) e = cudaStreamSynchronize(p->stream);
+    if (e) {
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    return RSOT_OK;
+}
+
+rsot_status rsot_covering_cost(rsot_problem *p, double *C0_out) {
+    if (!p || !C0_out) return RSOT_ERR_ARG;
+    if (p->C0 < 0.0) {
+        double *aux = reinterpret_cast<double *>(p->res_dev + 1);
+        cudaError_t e = launch_covering_cost(p, aux);
+        double v = 0.0;
+        if (!e) e = cudaMemcpyAsync(&v, aux, 8, cudaMemcpyDeviceToHost, p->stream);
+        if (!e) e = cudaStreamSynchronize(p->stream);
+        if (e) {
+            cudaGetLastError();
+            return from_cuda(e);
+        }
+        p->C0 = v;
+    }
+    *C0_out = p->C0;
+    return RSOT_OK;
+}
+
+rsot_status rsot_radius_for_tail(rsot_problem *p, const double *psi, double eps, double tail,
+                                 double *radius_out) {
+    if (!p || !psi || !radius_out || !(eps > 0.0) || !(tail > 0.0) || !(tail < 1.0))
+        return RSOT_ERR_ARG;
+    double C0;
+    rsot_status s = rsot_covering_cost(p, &C0);
+    if (s) return s;
+    double mx = -INFINITY, mn = INFINITY;
+    if (is_device_ptr(psi)) {
+        double *aux = reinterpret_cast<double *>(p->res_dev + 1) + 2;
+        double h[2];
+        cudaError_t e = launch_psi_stats(p, psi, aux);
+        if (!e) e = cudaMemcpyAsync(h, aux, 16, cudaMemcpyDeviceToHost, p->stream);
+        if (!e) e = cudaStreamSynchronize(p->stream);
+        if (e) {
+            cudaGetLastError();
+            return from_cuda(e);
+        }
+        mx = h[0];
+        mn = h[1];
+    } else {
+        for (int64_t j = 0; j < p->n; ++j) {
+            mx = std::max(mx, psi[j]);
+            mn = std::min(mn, psi[j]);
+        }
+    }
+    if (!isfinite(mx) || !isfinite(mn)) return RSOT_ERR_NONFINITE;
+    const double C = C0 + (mx - mn) + eps * log(1.0 / (p->nu_min * tail));
+    *radius_out = sqrt(2.0 * C);
+    return RSOT_OK;
+}
+
+}  // extern "C"

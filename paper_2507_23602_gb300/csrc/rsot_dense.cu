@@ -1,0 +1,884 @@
+// Dense dual + gradient evaluation (Algorithm 2 with I_q = all targets).
+//
+// Mixed precision (FP32 pair arithmetic, FP64 reductions), log2 domain.
+// With translated coordinates x' = x - o, y' = y - o, a centre psi_c = psi_0,
+// k = log2(e) / (2 eps):
+//     b_j = ((psi_j - psi_c)/eps + ln nu_j) log2 e
+//     w_j = 2 k y'_j,  c_j = b_j - k |y'_j|^2           (per target, FP32)
+//     r_qj = c_j + x'_q . w_j                           (d FFMA per pair)
+//     log2( nu_j e^{(psi_j - c(x_q,y_j))/eps} ) = log2e psi_c/eps + r_qj - k |x'_q|^2
+// so with R_q = log2 sum_j 2^{r_qj} (pass 1):
+//     eps L_q = psi_c + eps ln2 R_q - |x'_q|^2 / 2
+//     J = psi_c sum m - sum_q m_q |x'_q|^2/2 + eps ln2 sum_q m_q R_q - sum_j psi_j nu_j
+//     m_q p_qj = 2^{ r_qj + log2 m_q - R_q }            (pass 2)
+// which are Eq. discretized_functional and Eq. discretized_gradient.
+//
+// Pass 1 (K-LSE) is point-parallel: each thread holds 8 points as 4 float2
+// pairs, target tiles are staged into shared memory by bulk async copies
+// (cp.async.bulk + mbarrier, double buffered), and the running max / sum is
+// kept per point with an integral shift M (lazy rescale when a sub-tile's
+// max exceeds M + 32), ex2.approx.ftz per pair, FP64 flush per stage.
+// Pass 2 (K-GRAD) is target-parallel: each thread holds 2*TPP targets as
+// float2 pairs in registers, point records are staged into shared memory the
+// same way, and each target accumulates sum_q m_q p_qj with no shuffles and
+// no atomics; split partials over point chunks are summed in FP64 by a
+// final kernel in a fixed order (deterministic).
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "rsot_internal.cuh"
+
+namespace rsot {
+namespace {
+
+constexpr int P1_THREADS = 128;
+constexpr int P1_PP = 4;                               // point pairs per thread
+constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // 1024 points per CTA
+constexpr int P1_TS = 256;                             // targets per stage
+constexpr int P1_STAGES = 2;
+constexpr int P1_TT = 8;                               // targets per max sub-tile
+constexpr float P1_THR = 32.0f;                        // lazy-rescale threshold (log2)
+
+constexpr int P2_THREADS = 128;
+constexpr int P2_TS = 256;                             // points per stage
+constexpr int P2_STAGES = 2;
+
+constexpr int CB_THREADS = 256;                        // combine / prep kernels
+
+constexpr int F_THREADS = 128;                         // FP64 kernels
+constexpr int F_TS = 128;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ----------------------------------------------------------------------------
+// Per-target records (step a1): dup records for pass 1, pair records for
+// pass 2, and the block partials of sum_j psi_j nu_j.
+// ----------------------------------------------------------------------------
+__global__ void k_prep_mixed(const double *__restrict__ psi, const double *__restrict__ y64,
+                             const double *__restrict__ lnu, const double *__restrict__ nu,
+                             int64_t n, int64_t n_alloc, int d, double eps,
+                             Rec8 *__restrict__ tdup, Rec8 *__restrict__ tpair,
+                             double *__restrict__ psinu_part, int *__restrict__ flags) {
+    __shared__ double sh[32];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double psic = psi[0];
+    const double k = kLog2e / (2.0 * eps);
+    double contrib = 0.0;
+    if (j < n_alloc) {
+        float w[3] = {0.f, 0.f, 0.f};
+        float c = kPadC;
+        if (j < n) {
+            const double ps = psi[j];
+            if (!isfinite(ps)) atomicOr(flags, kErrNonfinitePsi);
+            const double b = ((ps - psic) / eps + lnu[j]) * kLog2e;
+            double yy = 0.0;
+            for (int t = 0; t < d; ++t) {
+                const double yt = y64[j * d + t];
+                w[t] = (float)(2.0 * k * yt);
+                yy += yt * yt;
+            }
+            c = (float)(b - k * yy);
+            contrib = ps * nu[j];
+        }
+        Rec8 r;
+        r.a = make_float4(w[0], w[0], w[1], w[1]);
+        r.b = make_float4(w[2], w[2], c, c);
+        tdup[j] = r;
+        float *pr = reinterpret_cast<float *>(tpair + (j >> 1));
+        const int l = (int)(j & 1);
+        pr[0 + l] = w[0];
+        pr[2 + l] = w[1];
+        pr[4 + l] = w[2];
+        pr[6 + l] = c;
+    }
+    const double s = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
+}
+
+// ----------------------------------------------------------------------------
+// Pass 1: per-point log-sum-exp over one target chunk (step a2).
+// ----------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(P1_THREADS, 3)
+    k_lse_mixed(const float *__restrict__ xs, int64_t nq_pad, const Rec8 *__restrict__ tdup,
+                int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags) {
+    __shared__ __align__(128) Rec8 sm[P1_STAGES][P1_TS];
+    __shared__ __align__(8) uint64_t full[P1_STAGES];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.x * P1_TILE;
+    const int kc = blockIdx.y;
+    const int t_begin = kc * chunk;
+    const int t_count = min(chunk, n_p1 - t_begin);
+    const int ntile = t_count / P1_TS;
+
+    float2 X[P1_PP][3];
+#pragma unroll
+    for (int pp = 0; pp < P1_PP; ++pp) {
+        const int64_t q = q0 + 2 * (pp * P1_THREADS + tid);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            X[pp][k] = (k < D) ? *reinterpret_cast<const float2 *>(xs + k * nq_pad + q)
+                               : make_float2(0.f, 0.f);
+    }
+    float2 M[P1_PP], Sf[P1_PP];
+    double2 Sd[P1_PP];
+#pragma unroll
+    for (int pp = 0; pp < P1_PP; ++pp) {
+        M[pp] = make_float2(kPadC, kPadC);
+        Sf[pp] = make_float2(0.f, 0.f);
+        Sd[pp] = make_double2(0.0, 0.0);
+    }
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < P1_STAGES; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < P1_STAGES && s < ntile; ++s) {
+            mbar_expect_tx(&full[s], P1_TS * sizeof(Rec8));
+            bulk_g2s(sm[s], tdup + t_begin + s * P1_TS, P1_TS * sizeof(Rec8), &full[s]);
+        }
+    }
+
+    int issued = min(P1_STAGES, ntile);
+    for (int it = 0; it < ntile; ++it) {
+        const int s = it % P1_STAGES;
+        const unsigned ph = (unsigned)(it / P1_STAGES) & 1u;
+        const bool ok = mbar_wait(&full[s], ph);
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(flags, kErrTimeout);
+        } else {
+            const Rec8 *T = sm[s];
+#pragma unroll 1
+            for (int t0 = 0; t0 < P1_TS; t0 += P1_TT) {
+                float2 r[P1_PP][P1_TT];
+#pragma unroll
+                for (int t = 0; t < P1_TT; ++t) {
+                    const float4 a = T[t0 + t].a;
+                    const float4 b = T[t0 + t].b;
+                    const float2 w0 = make_float2(a.x, a.y), w1 = make_float2(a.z, a.w);
+                    const float2 w2 = make_float2(b.x, b.y), c = make_float2(b.z, b.w);
+#pragma unroll
+                    for (int pp = 0; pp < P1_PP; ++pp) {
+                        float2 acc = c;
+                        if (D == 3) acc = __ffma2_rn(X[pp][2], w2, acc);
+                        acc = __ffma2_rn(X[pp][1], w1, acc);
+                        acc = __ffma2_rn(X[pp][0], w0, acc);
+                        r[pp][t] = acc;
+                    }
+                }
+#pragma unroll
+                for (int pp = 0; pp < P1_PP; ++pp) {
+                    float mx = r[pp][0].x, my = r[pp][0].y;
+#pragma unroll
+                    for (int t = 1; t + 1 < P1_TT; t += 2) {
+                        mx = max3f(mx, r[pp][t].x, r[pp][t + 1].x);
+                        my = max3f(my, r[pp][t].y, r[pp][t + 1].y);
+                    }
+                    if ((P1_TT & 1) == 0) {
+                        mx = fmaxf(mx, r[pp][P1_TT - 1].x);
+                        my = fmaxf(my, r[pp][P1_TT - 1].y);
+                    }
+                    if (mx > M[pp].x + P1_THR) {
+                        const float mn = ceilf(mx);
+                        const float dlt = M[pp].x - mn;
+                        Sf[pp].x *= pow2_int_f(dlt);
+                        Sd[pp].x *= pow2_int_d(dlt);
+                        M[pp].x = mn;
+                    }
+                    if (my > M[pp].y + P1_THR) {
+                        const float mn = ceilf(my);
+                        const float dlt = M[pp].y - mn;
+                        Sf[pp].y *= pow2_int_f(dlt);
+                        Sd[pp].y *= pow2_int_d(dlt);
+                        M[pp].y = mn;
+                    }
+                    const float2 nm = make_float2(-M[pp].x, -M[pp].y);
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int t = 0; t < P1_TT; ++t) {
+                        const float2 e = __fadd2_rn(r[pp][t], nm);
+                        acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                    }
+                    Sf[pp] = __fadd2_rn(Sf[pp], acc);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && it + P1_STAGES < ntile) {
+            mbar_expect_tx(&full[s], P1_TS * sizeof(Rec8));
+            bulk_g2s(sm[s], tdup + t_begin + (it + P1_STAGES) * P1_TS, P1_TS * sizeof(Rec8),
+                     &full[s]);
+            ++issued;
+        }
+#pragma unroll
+        for (int pp = 0; pp < P1_PP; ++pp) {
+            Sd[pp].x += (double)Sf[pp].x;
+            Sd[pp].y += (double)Sf[pp].y;
+            Sf[pp] = make_float2(0.f, 0.f);
+        }
+    }
+    if (s_abort) {
+        // drain copies still in flight (bounded) before the CTA exits
+        if (tid == 0) {
+            for (int it = 0; it < issued; ++it) {
+                const int s = it % P1_STAGES;
+                (void)mbar_wait(&full[s], (unsigned)(it / P1_STAGES) & 1u);
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int pp = 0; pp < P1_PP; ++pp) {
+        const int64_t q = q0 + 2 * (pp * P1_THREADS + tid);
+        *reinterpret_cast<float4 *>(part + (int64_t)kc * nq_pad + q) =
+            make_float4(M[pp].x, (float)Sd[pp].x, M[pp].y, (float)Sd[pp].y);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Merge the pass-1 chunk partials into R_q, write the pass-2 point records
+// (x', u_q = log2 m_q - R_q) and the block partials of sum_q m_q R_q.
+// ----------------------------------------------------------------------------
+__global__ void k_combine(const float2 *__restrict__ part, int k1, int64_t nq_pad, int64_t nq,
+                          const float *__restrict__ xs, int d, const double *__restrict__ lmass2,
+                          const double *__restrict__ mass, Rec8 *__restrict__ pdup,
+                          double *__restrict__ blockJ, double *__restrict__ lse_buf) {
+    __shared__ double sh[32];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double contrib = 0.0;
+    if (q < nq_pad) {
+        float x[3] = {0.f, 0.f, 0.f};
+        float u = kPadC;
+        if (q < nq) {
+            float mx = kPadC;
+            for (int k = 0; k < k1; ++k) mx = fmaxf(mx, part[(int64_t)k * nq_pad + q].x);
+            double tot = 0.0;
+            for (int k = 0; k < k1; ++k) {
+                const float2 v = part[(int64_t)k * nq_pad + q];
+                tot += (double)v.y * pow2_int_d(v.x - mx);
+            }
+            const double R = (double)mx + log2(tot);
+            lse_buf[q] = R;
+            const double lm = lmass2[q];
+            if (mass[q] > 0.0) {
+                contrib = mass[q] * R;
+                u = (float)fmax(lm - R, -1.0e30);
+            }
+            for (int t = 0; t < d; ++t) x[t] = xs[t * nq_pad + q];
+        }
+        Rec8 r;
+        r.a = make_float4(x[0], x[0], x[1], x[1]);
+        r.b = make_float4(x[2], x[2], u, u);
+        pdup[q] = r;
+    }
+    const double s = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) blockJ[blockIdx.x] = s;
+}
+
+// ----------------------------------------------------------------------------
+// Pass 2: per-target sum over one point chunk of m_q p_qj (step a3).
+// ----------------------------------------------------------------------------
+template <int D, int TPP>
+__global__ void __launch_bounds__(P2_THREADS)
+    k_grad_mixed(const Rec8 *__restrict__ tpair, const Rec8 *__restrict__ pdup, int64_t nq_pad,
+                 int64_t chunk, double *__restrict__ part2, int64_t stride,
+                 int *__restrict__ flags) {
+    __shared__ __align__(128) Rec8 sm[P2_STAGES][P2_TS];
+    __shared__ __align__(8) uint64_t full[P2_STAGES];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int64_t g0 = (int64_t)blockIdx.x * P2_THREADS * TPP;
+    float2 W0[TPP], W1[TPP], W2[TPP], C[TPP];
+#pragma unroll
+    for (int tp = 0; tp < TPP; ++tp) {
+        const Rec8 r = tpair[g0 + tp * P2_THREADS + tid];
+        W0[tp] = make_float2(r.a.x, r.a.y);
+        W1[tp] = make_float2(r.a.z, r.a.w);
+        W2[tp] = make_float2(r.b.x, r.b.y);
+        C[tp] = make_float2(r.b.z, r.b.w);
+    }
+    const int64_t p_begin = (int64_t)blockIdx.y * chunk;
+    const int64_t p_count = min(chunk, nq_pad - p_begin);
+    const int ntile = (int)(p_count / P2_TS);
+
+    double2 acc64[TPP];
+#pragma unroll
+    for (int tp = 0; tp < TPP; ++tp) acc64[tp] = make_double2(0.0, 0.0);
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < P2_STAGES; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < P2_STAGES && s < ntile; ++s) {
+            mbar_expect_tx(&full[s], P2_TS * sizeof(Rec8));
+            bulk_g2s(sm[s], pdup + p_begin + (int64_t)s * P2_TS, P2_TS * sizeof(Rec8), &full[s]);
+        }
+    }
+    int issued = min(P2_STAGES, ntile);
+    for (int it = 0; it < ntile; ++it) {
+        const int s = it % P2_STAGES;
+        const unsigned ph = (unsigned)(it / P2_STAGES) & 1u;
+        const bool ok = mbar_wait(&full[s], ph);
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(flags, kErrTimeout);
+        } else {
+            const Rec8 *T = sm[s];
+            float2 acc[TPP];
+#pragma unroll
+            for (int tp = 0; tp < TPP; ++tp) acc[tp] = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int i = 0; i < P2_TS; ++i) {
+                const float4 a = T[i].a;
+                const float4 b = T[i].b;
+                const float2 x0 = make_float2(a.x, a.y), x1 = make_float2(a.z, a.w);
+                const float2 x2 = make_float2(b.x, b.y), u = make_float2(b.z, b.w);
+#pragma unroll
+                for (int tp = 0; tp < TPP; ++tp) {
+                    float2 t = C[tp];
+                    if (D == 3) t = __ffma2_rn(x2, W2[tp], t);
+                    t = __ffma2_rn(x1, W1[tp], t);
+                    t = __ffma2_rn(x0, W0[tp], t);
+                    t = __fadd2_rn(t, u);
+                    acc[tp] = __fadd2_rn(acc[tp], make_float2(ex2_approx(t.x), ex2_approx(t.y)));
+                }
+            }
+#pragma unroll
+            for (int tp = 0; tp < TPP; ++tp) {
+                acc64[tp].x += (double)acc[tp].x;
+                acc64[tp].y += (double)acc[tp].y;
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && it + P2_STAGES < ntile) {
+            mbar_expect_tx(&full[s], P2_TS * sizeof(Rec8));
+            bulk_g2s(sm[s], pdup + p_begin + (int64_t)(it + P2_STAGES) * P2_TS,
+                     P2_TS * sizeof(Rec8), &full[s]);
+            ++issued;
+        }
+    }
+    if (s_abort) {
+        if (tid == 0) {
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % P2_STAGES], (unsigned)(it / P2_STAGES) & 1u);
+        }
+        return;
+    }
+#pragma unroll
+    for (int tp = 0; tp < TPP; ++tp) {
+        const int64_t j = 2 * (g0 + tp * P2_THREADS + tid);
+        *reinterpret_cast<double2 *>(part2 + (int64_t)blockIdx.y * stride + j) = acc64[tp];
+    }
+}
+
+// grad_j = sum_s part2[s][j] - nu_j  (fixed order: deterministic)
+__global__ void k_finalize_grad(const double *__restrict__ part2, int s2, int64_t stride,
+                                const double *__restrict__ nu, int64_t n,
+                                double *__restrict__ grad) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double g = 0.0;
+    for (int s = 0; s < s2; ++s) g += part2[(int64_t)s * stride + j];
+    grad[j] = g - nu[j];
+}
+
+// J from the block partials (one block).
+__global__ void k_finalize_J(const double *__restrict__ blockJ, int nbj,
+                             const double *__restrict__ psinu, int npn,
+                             const double *__restrict__ psi, double eps, double msum, double hx,
+                             int mixed, EvalResult *__restrict__ res) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nbj; i += blockDim.x) a += blockJ[i];
+    for (int i = threadIdx.x; i < npn; i += blockDim.x) b += psinu[i];
+    const double sa = block_sum_d(a, sh);
+    const double sb = block_sum_d(b, sh);
+    if (threadIdx.x == 0) {
+        const double psic = psi[0];
+        res->psic = psic;
+        res->J = mixed ? (psic * msum - hx + eps * kLn2 * sa - sb) : (psic * msum + eps * sa - sb);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// FP64 path: same passes with FP64 arithmetic and CUDA's exp/log.
+// ----------------------------------------------------------------------------
+__global__ void k_prep_fp64(const double *__restrict__ psi, const double *__restrict__ lnu,
+                            const double *__restrict__ nu, int64_t n, int64_t n_alloc, double eps,
+                            double *__restrict__ a64, double *__restrict__ psinu_part,
+                            int *__restrict__ flags) {
+    __shared__ double sh[32];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double contrib = 0.0;
+    if (j < n_alloc) {
+        double a = -INFINITY;
+        if (j < n) {
+            const double ps = psi[j];
+            if (!isfinite(ps)) atomicOr(flags, kErrNonfinitePsi);
+            a = (ps - psi[0]) / eps + lnu[j];
+            contrib = ps * nu[j];
+        }
+        a64[j] = a;
+    }
+    const double s = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(F_THREADS)
+    k_lse_fp64(const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
+               const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
+               double inv_eps, const double *__restrict__ mass, double *__restrict__ prec64,
+               double *__restrict__ blockJ, double *__restrict__ lse_buf) {
+    __shared__ double sy[F_TS][4];
+    __shared__ double sh[32];
+    const int64_t q = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
+    double x[3] = {0.0, 0.0, 0.0};
+    if (q < nq)
+        for (int t = 0; t < D; ++t) x[t] = x64[q * D + t];
+    double M = -INFINITY, S = 0.0;
+    for (int64_t t0 = 0; t0 < n; t0 += F_TS) {
+        for (int i = threadIdx.x; i < F_TS; i += F_THREADS) {
+            const int64_t j = t0 + i;
+            if (j < n) {
+                for (int t = 0; t < D; ++t) sy[i][t] = y64[j * D + t];
+                sy[i][3] = a64[j];
+            } else {
+                sy[i][3] = -INFINITY;
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)F_TS, n - t0);
+        for (int i = 0; i < cnt; ++i) {
+            double c = 0.0;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const double dd = x[t] - sy[i][t];
+                c += dd * dd;
+            }
+            const double s = sy[i][3] - 0.5 * c * inv_eps;
+            const double dlt = s - M;
+            const double e = exp(-fabs(dlt));
+            if (dlt > 0.0) {
+                S = S * e + 1.0;
+                M = s;
+            } else {
+                S += e;
+            }
+        }
+        __syncthreads();
+    }
+    double contrib = 0.0;
+    if (q < nq_pad) {
+        double u = -INFINITY;
+        if (q < nq) {
+            const double L = M + log(S);
+            lse_buf[q] = L;
+            if (mass[q] > 0.0) {
+                contrib = mass[q] * L;
+                u = log(mass[q]) - L;
+            }
+        }
+        double *r = prec64 + q * 4;
+        r[0] = x[0];
+        r[1] = x[1];
+        r[2] = x[2];
+        r[3] = u;
+    }
+    const double s = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) blockJ[blockIdx.x] = s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(F_THREADS)
+    k_grad_fp64(const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
+                const double *__restrict__ prec64, int64_t nq_pad, int64_t chunk, double inv_eps,
+                double *__restrict__ part2, int64_t stride) {
+    __shared__ double sp[F_TS][4];
+    const int64_t j = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
+    double y[3] = {0.0, 0.0, 0.0};
+    double a = -INFINITY;
+    if (j < n) {
+        for (int t = 0; t < D; ++t) y[t] = y64[j * D + t];
+        a = a64[j];
+    }
+    const int64_t p_begin = (int64_t)blockIdx.y * chunk;
+    const int64_t p_end = min(nq_pad, p_begin + chunk);
+    double acc = 0.0;
+    for (int64_t p0 = p_begin; p0 < p_end; p0 += F_TS) {
+        for (int i = threadIdx.x; i < F_TS * 4; i += F_THREADS) {
+            const int64_t idx = p0 * 4 + i;
+            (&sp[0][0])[i] = (idx < p_end * 4) ? prec64[idx] : (((i & 3) == 3) ? -INFINITY : 0.0);
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)F_TS, p_end - p0);
+        for (int i = 0; i < cnt; ++i) {
+            double c = 0.0;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const double dd = sp[i][t] - y[t];
+                c += dd * dd;
+            }
+            acc += exp(a - 0.5 * c * inv_eps + sp[i][3]);
+        }
+        __syncthreads();
+    }
+    if (j < stride) part2[(int64_t)blockIdx.y * stride + j] = acc;
+}
+
+// ----------------------------------------------------------------------------
+// Covering cost: max_q min_j |x_q - y_j|^2 / 2 (FP32 distances, brute force).
+// ----------------------------------------------------------------------------
+__global__ void k_cover(const float *__restrict__ xs, int64_t nq, int64_t nq_pad,
+                        const double *__restrict__ y64, int64_t n, int d,
+                        float *__restrict__ block_max) {
+    __shared__ float sy[256][3];
+    __shared__ float smax[32];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float x[3] = {0.f, 0.f, 0.f};
+    if (q < nq)
+        for (int t = 0; t < d; ++t) x[t] = xs[t * nq_pad + q];
+    float best = INFINITY;
+    for (int64_t t0 = 0; t0 < n; t0 += 256) {
+        const int64_t j = t0 + threadIdx.x;
+        for (int t = 0; t < 3; ++t) sy[threadIdx.x][t] = (j < n && t < d) ? (float)y64[j * d + t] : 0.f;
+        __syncthreads();
+        const int cnt = (int)min((int64_t)256, n - t0);
+        for (int i = 0; i < cnt; ++i) {
+            const float a = x[0] - sy[i][0], b = x[1] - sy[i][1], c = x[2] - sy[i][2];
+            best = fminf(best, fmaf(a, a, fmaf(b, b, c * c)));
+        }
+        __syncthreads();
+    }
+    float v = (q < nq) ? best : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, smax[w]);
+        block_max[blockIdx.x] = m;
+    }
+}
+
+__global__ void k_max_f(const float *__restrict__ v, int nb, double *__restrict__ out) {
+    __shared__ float s[256];
+    float m = 0.f;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmaxf(m, v[i]);
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 0.5 * (double)s[0];
+}
+
+// L_q from the stored per-point quantity of the last dense evaluation.
+//   mixed : L_q = psi_c/eps + ln2 R_q - |x'_q|^2 / (2 eps)
+//   FP64  : L_q = psi_c/eps + L'_q
+__global__ void k_point_L(const double *__restrict__ lse_buf, const double *__restrict__ x64,
+                          int64_t nq, int d, int kind, double eps,
+                          const EvalResult *__restrict__ res, double *__restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double base = res->psic / eps;
+    if (kind == 1) {
+        double r2 = 0.0;
+        for (int t = 0; t < d; ++t) r2 += x64[q * d + t] * x64[q * d + t];
+        out[q] = base + kLn2 * lse_buf[q] - 0.5 * r2 / eps;
+    } else {
+        out[q] = base + lse_buf[q];
+    }
+}
+
+// max psi, min psi (one block)
+__global__ void k_psi_stats(const double *__restrict__ psi, int64_t n, double *__restrict__ out) {
+    __shared__ double smx[256], smn[256];
+    double mx = -INFINITY, mn = INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        mx = fmax(mx, psi[i]);
+        mn = fmin(mn, psi[i]);
+    }
+    smx[threadIdx.x] = mx;
+    smn[threadIdx.x] = mn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+            smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = smx[0];
+        out[1] = smn[0];
+    }
+}
+
+// Split count s in [1, max_split] such that units * s work items fill the
+// resident slots evenly (<= 5% idle in the last wave), smallest such s.
+int pick_split(int64_t units, int64_t max_split, int64_t slots) {
+    if (max_split < 1) max_split = 1;
+    int best = 1;
+    double best_eff = 0.0;
+    for (int64_t s = 1; s <= max_split && s <= 256; ++s) {
+        const int64_t items = units * s;
+        const int64_t waves = (items + slots - 1) / slots;
+        const double eff = (double)items / (double)(waves * slots);
+        if (eff > best_eff + 0.01) {
+            best_eff = eff;
+            best = (int)s;
+        }
+        if (items >= slots && eff >= 0.95) return (int)s;
+    }
+    return best;
+}
+
+int occupancy(const void *fn, int threads, size_t dyn_smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, dyn_smem) != cudaSuccess ||
+        nb < 1)
+        nb = 1;
+    return nb;
+}
+
+int pick_tpp(int64_t n) {
+    // targets per pass-2 CTA = 128 * 2 * TPP; pick the largest TPP that wastes
+    // at most 1/8 of the lanes on padding
+    for (int tpp : {4, 2}) {
+        const int64_t blk = (int64_t)P2_THREADS * 2 * tpp;
+        if (round_up(n, blk) - n <= n / 8) return tpp;
+    }
+    return 1;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// allocation of the dense scratch
+// ----------------------------------------------------------------------------
+cudaError_t dense_alloc(rsot_problem *p) {
+    cudaError_t e;
+    const int64_t n_alloc = round_up(p->n, 1024);
+    p->n_pad = n_alloc;
+    const int64_t n_p1 = round_up(p->n, P1_TS);
+    // pass-1 split over target chunks
+    const int64_t tiles1 = p->nq_pad / P1_TILE;
+    const void *f1 = (p->d == 3) ? (const void *)k_lse_mixed<3> : (const void *)k_lse_mixed<2>;
+    const int64_t slots1 = (int64_t)p->num_sms * occupancy(f1, P1_THREADS, 0);
+    p->k1 = pick_split(tiles1, n_p1 / P1_TS, slots1);
+    p->chunk1 = (int)round_up((n_p1 + p->k1 - 1) / p->k1, P1_TS);
+    p->k1 = (int)((n_p1 + p->chunk1 - 1) / p->chunk1);
+    // pass-2 split over point chunks
+    const int tpp = pick_tpp(p->n);
+    const int64_t blk2 = (int64_t)P2_THREADS * 2 * tpp;
+    const int64_t units2 = (p->n + blk2 - 1) / blk2;
+    const void *f2 = (p->d == 3) ? (const void *)k_grad_mixed<3, 4> : (const void *)k_grad_mixed<2, 4>;
+    const int64_t slots2 = (int64_t)p->num_sms * occupancy(f2, P2_THREADS, 0);
+    p->s2 = pick_split(units2, p->nq_pad / P2_TS, slots2);
+    p->chunk2 = round_up((p->nq_pad + p->s2 - 1) / p->s2, P2_TS);
+    p->s2 = (int)((p->nq_pad + p->chunk2 - 1) / p->chunk2);
+    // FP64 split
+    const int64_t units64 = (p->n + F_THREADS - 1) / F_THREADS;
+    p->s2_64 = pick_split(units64, p->nq_pad / F_TS, (int64_t)p->num_sms * 8);
+    p->chunk2_64 = round_up((p->nq_pad + p->s2_64 - 1) / p->s2_64, F_TS);
+    p->s2_64 = (int)((p->nq_pad + p->chunk2_64 - 1) / p->chunk2_64);
+
+    p->nblk_comb = (int)((p->nq_pad + CB_THREADS - 1) / CB_THREADS);
+    p->nblk_prep = (int)((n_alloc + CB_THREADS - 1) / CB_THREADS);
+    const int nbj = std::max<int64_t>(p->nblk_comb, (p->nq_pad + F_THREADS - 1) / F_THREADS);
+
+    if ((e = cudaMalloc(&p->tdup, n_alloc * sizeof(Rec8)))) return e;
+    if ((e = cudaMalloc(&p->tpair, (n_alloc / 2) * sizeof(Rec8)))) return e;
+    if ((e = cudaMalloc(&p->part1, (size_t)p->k1 * p->nq_pad * sizeof(float2)))) return e;
+    if ((e = cudaMalloc(&p->pdup, p->nq_pad * sizeof(Rec8)))) return e;
+    if ((e = cudaMalloc(&p->part2, (size_t)p->s2 * n_alloc * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->part2_64, (size_t)p->s2_64 * n_alloc * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->blockJ, (size_t)nbj * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->psinu, (size_t)p->nblk_prep * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->a64, n_alloc * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->prec64, (size_t)p->nq_pad * 4 * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->lse_buf, (size_t)p->nq_pad * sizeof(double)))) return e;
+    return cudaSuccess;
+}
+
+void dense_free(rsot_problem *p) {
+    cudaFree(p->tdup);
+    cudaFree(p->tpair);
+    cudaFree(p->part1);
+    cudaFree(p->pdup);
+    cudaFree(p->part2);
+    cudaFree(p->part2_64);
+    cudaFree(p->blockJ);
+    cudaFree(p->psinu);
+    cudaFree(p->a64);
+    cudaFree(p->prec64);
+    cudaFree(p->lse_buf);
+}
+
+template <int D>
+static cudaError_t launch_mixed_d(rsot_problem *p, const double *psi, double eps, double *grad) {
+    cudaStream_t st = p->stream;
+    const int64_t n_p1 = round_up(p->n, P1_TS);
+    trace_begin(p, "prep_targets_mixed");
+    k_prep_mixed<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad,
+                                                      p->d, eps, p->tdup, p->tpair, p->psinu,
+                                                      p->flags);
+    trace_end(p);
+    dim3 g1((unsigned)(p->nq_pad / P1_TILE), (unsigned)p->k1);
+    trace_begin(p, "lse_mixed");
+    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(p->xs, p->nq_pad, p->tdup, (int)n_p1, p->chunk1,
+                                              p->part1, p->flags);
+    trace_end(p);
+    trace_begin(p, "combine_mixed");
+    k_combine<<<p->nblk_comb, CB_THREADS, 0, st>>>(p->part1, p->k1, p->nq_pad, p->nq, p->xs, p->d,
+                                                   p->lmass2, p->mass, p->pdup, p->blockJ,
+                                                   p->lse_buf);
+    trace_end(p);
+    const int tpp = pick_tpp(p->n);
+    const int64_t blk2 = (int64_t)P2_THREADS * 2 * tpp;
+    dim3 g2((unsigned)((p->n + blk2 - 1) / blk2), (unsigned)p->s2);
+    trace_begin(p, "grad_mixed");
+    if (tpp == 4)
+        k_grad_mixed<D, 4><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, p->chunk2,
+                                                      p->part2, p->n_pad, p->flags);
+    else if (tpp == 2)
+        k_grad_mixed<D, 2><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, p->chunk2,
+                                                      p->part2, p->n_pad, p->flags);
+    else
+        k_grad_mixed<D, 1><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, p->chunk2,
+                                                      p->part2, p->n_pad, p->flags);
+    trace_end(p);
+    trace_begin(p, "finalize_grad");
+    k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(p->part2, p->s2, p->n_pad,
+                                                                    p->nu, p->n, grad);
+    trace_end(p);
+    trace_begin(p, "finalize_J");
+    k_finalize_J<<<1, 256, 0, st>>>(p->blockJ, p->nblk_comb, p->psinu, p->nblk_prep, psi, eps,
+                                    p->msum, p->hx, 1, p->res_dev);
+    trace_end(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi, double eps, double *grad) {
+    return p->d == 3 ? launch_mixed_d<3>(p, psi, eps, grad) : launch_mixed_d<2>(p, psi, eps, grad);
+}
+
+template <int D>
+static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps, double *grad) {
+    cudaStream_t st = p->stream;
+    trace_begin(p, "prep_targets_fp64");
+    k_prep_fp64<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->lnu, p->nu, p->n, p->n_pad, eps,
+                                                     p->a64, p->psinu, p->flags);
+    trace_end(p);
+    const unsigned nb1 = (unsigned)((p->nq_pad + F_THREADS - 1) / F_THREADS);
+    trace_begin(p, "lse_fp64");
+    k_lse_fp64<D><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64, p->n,
+                                             1.0 / eps, p->mass, p->prec64, p->blockJ,
+                                             p->lse_buf);
+    trace_end(p);
+    dim3 g2((unsigned)((p->n + F_THREADS - 1) / F_THREADS), (unsigned)p->s2_64);
+    trace_begin(p, "grad_fp64");
+    k_grad_fp64<D><<<g2, F_THREADS, 0, st>>>(p->y64, p->a64, p->n, p->prec64, p->nq_pad,
+                                             p->chunk2_64, 1.0 / eps, p->part2_64, p->n_pad);
+    trace_end(p);
+    trace_begin(p, "finalize_grad");
+    k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(p->part2_64, p->s2_64,
+                                                                    p->n_pad, p->nu, p->n, grad);
+    trace_end(p);
+    trace_begin(p, "finalize_J");
+    k_finalize_J<<<1, 256, 0, st>>>(p->blockJ, (int)nb1, p->psinu, p->nblk_prep, psi, eps, p->msum,
+                                    0.0, 0, p->res_dev);
+    trace_end(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_fp64(rsot_problem *p, const double *psi, double eps, double *grad) {
+    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad) : launch_fp64_d<2>(p, psi, eps, grad);
+}
+
+cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev) {
+    const int nb = (int)((p->nq + 255) / 256);
+    float *bm = nullptr;
+    cudaError_t e = cudaMallocAsync(&bm, (size_t)nb * sizeof(float), p->stream);
+    if (e) return e;
+    k_cover<<<nb, 256, 0, p->stream>>>(p->xs, p->nq, p->nq_pad, p->y64, p->n, p->d, bm);
+    k_max_f<<<1, 256, 0, p->stream>>>(bm, nb, C0_dev);
+    e = cudaGetLastError();
+    cudaFreeAsync(bm, p->stream);
+    return e;
+}
+
+cudaError_t launch_point_L(rsot_problem *p, double *L_dev) {
+    k_point_L<<<(unsigned)((p->nq + 255) / 256), 256, 0, p->stream>>>(
+        p->lse_buf, p->x64, p->nq, p->d, p->last_kind, p->last_eps, p->res_dev, L_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi_stats(rsot_problem *p, const double *psi, double *out2) {
+    k_psi_stats<<<1, 256, 0, p->stream>>>(psi, p->n, out2);
+    return cudaGetLastError();
+}
+
+}  // namespace rsot
+
+namespace {
+// 8 independent chains x <- ex2(x) / 2 per thread keep x in [1/2, 1].
+__global__ void k_probe_ex2(float *out, int iters) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.5f + 0.05f * k + 1e-6f * threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = rsot::ex2_approx(a[k]) * 0.5f;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == 123.456f) out[threadIdx.x] = s;   // keeps the chains alive
+}
+}  // namespace
+
+extern "C" rsot_status rsot_probe_ex2_rate(int iters, double *ex2_per_s) {
+    if (iters < 1 || !ex2_per_s) return RSOT_ERR_ARG;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float *out = nullptr;
+    cudaEvent_t a, b;
+    if (cudaMalloc(&out, 1024 * sizeof(float))) return RSOT_ERR_NOMEM;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int blocks = sms * 8, threads = 256;
+    k_probe_ex2<<<blocks, threads>>>(out, iters);   // warm-up
+    cudaEventRecord(a);
+    k_probe_ex2<<<blocks, threads>>>(out, iters);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (!e) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (e || ms <= 0.f) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    *ex2_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+    return RSOT_OK;
+}

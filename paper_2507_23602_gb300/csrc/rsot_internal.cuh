@@ -1,0 +1,231 @@
+// Internal declarations shared by the librsot translation units.
+//
+// Layout in HBM (all device buffers owned by rsot_problem):
+//   points  : FP32 translated coordinates, SoA xs[k * nq_pad + q] (k < d),
+//             zero-padded to nq_pad (a multiple of the pass-1 point tile);
+//             FP64 translated coordinates x64[q * d + k]; masses m_q (FP64)
+//             and log2 m_q (FP64).
+//   targets : FP64 translated coordinates y64[j * d + k], nu_j, ln nu_j.
+//   per evaluation (mixed precision, log2 domain, see rsot_dense.cu):
+//             target "dup" records  TRecDup[j]  = (w0,w0,w1,w1,w2,w2,c,c)
+//             target "pair" records TRecPair[g] = (w0a,w0b,w1a,w1b,w2a,w2b,ca,cb)
+//             pass-1 partials (M, S) per point and target chunk
+//             point "dup" records   (x0,x0,x1,x1,x2,x2,u,u) for pass 2
+//             pass-2 FP64 partial sums per point chunk and target
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsot.h"
+
+namespace rsot {
+
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kPadC = -1.0e30f;            // exponent of a padding target: ex2 -> 0
+
+// Error bits written by kernels into ProblemDev::flags.
+enum : int {
+    kErrTimeout = 1,        // an mbarrier wait exceeded its iteration limit
+    kErrNonfinitePsi = 2,   // psi had a NaN / Inf entry
+    kErrBadCell = 4,        // a cell index fell outside the grid (truncated path)
+};
+
+struct __align__(16) Rec8 {   // 32-byte record: two float4
+    float4 a;
+    float4 b;
+};
+
+// Result block copied back to the host after each evaluation.
+struct EvalResult {
+    double J;
+    double psic;        // psi_0 of the evaluation (the potential centre)
+    long long pairs;
+    long long empty;
+    int flags;
+    int pad;
+};
+
+struct Grid;  // truncated-path cell grid (rsot_trunc.cu)
+
+}  // namespace rsot
+
+struct rsot_problem {
+    int d = 0;
+    int dev = 0;
+    int64_t nq = 0, n = 0;
+    int64_t nq_pad = 0, n_pad = 0;
+    cudaStream_t stream = nullptr;
+    double origin[3] = {0, 0, 0};
+    double msum = 0.0;          // sum_q m_q
+    double hx = 0.0;            // sum_q m_q |x'_q|^2 / 2 (translated coordinates)
+    double nu_min = 0.0, nu_max = 0.0;
+    int num_sms = 0;
+
+    // static device data
+    float *xs = nullptr;        // [d][nq_pad]
+    double *x64 = nullptr;      // [nq][d]
+    double *mass = nullptr;     // [nq]
+    double *lmass2 = nullptr;   // [nq] log2 m_q (-inf if m_q == 0)
+    double *y64 = nullptr;      // [n][d]
+    double *nu = nullptr;       // [n]
+    double *lnu = nullptr;      // [n] ln nu_j
+
+    // per-evaluation scratch (mixed)
+    rsot::Rec8 *tdup = nullptr;     // [n_pad]
+    rsot::Rec8 *tpair = nullptr;    // [n_pad / 2]
+    float2 *part1 = nullptr;        // [k1][nq_pad]
+    rsot::Rec8 *pdup = nullptr;     // [nq_pad]
+    double *part2 = nullptr;        // [s2][n_pad]
+    double *blockJ = nullptr;       // [nblk_j]
+    double *psinu = nullptr;        // [nblk_psi]
+    int k1 = 0, chunk1 = 0;         // pass-1 target chunks
+    int s2 = 0;                     // pass-2 point splits
+    int64_t chunk2 = 0;
+    int nblk_comb = 0, nblk_prep = 0;
+    // FP64 path scratch
+    double *a64 = nullptr;          // [n_pad]   psi_j/eps + ln nu_j
+    double *prec64 = nullptr;       // [nq_pad][4] (x0,x1,x2,u)
+    int s2_64 = 0;
+    int64_t chunk2_64 = 0;
+    double *part2_64 = nullptr;     // [s2_64][n_pad]
+
+    // staging for host psi / grad
+    double *psi_dev = nullptr;      // [n]
+    double *grad_dev = nullptr;     // [n]
+    rsot::EvalResult *res_dev = nullptr;
+    rsot::EvalResult *res_host = nullptr;   // pinned
+    int *flags = nullptr;           // device error bits (inside res_dev)
+
+    // per-point log partition of the last evaluation (see rsot_point_log_partition)
+    double *lse_buf = nullptr;      // [nq_pad]: R_q (mixed, log2) or L'_q (FP64, natural)
+    int last_kind = -1;             // -1 none, 0 FP64 dense, 1 mixed dense, 2/3 truncated
+    double last_eps = 0.0;
+
+    // covering cost cache
+    double C0 = -1.0;
+
+    // truncated path
+    rsot::Grid *grid = nullptr;
+
+    // kernel tracing (rsot_kernel_timing)
+    int timing = 0;
+    std::vector<cudaEvent_t> tr_events;                 // pool, reused
+    std::vector<std::pair<const char *, int>> tr_open;  // (name, first event index)
+    int tr_used = 0;
+    std::vector<const char *> tr_names;
+    std::vector<double> tr_total_ms;
+    std::vector<int64_t> tr_count;
+};
+
+namespace rsot {
+
+// ---- kernel tracing (rsot_api.cu) -------------------------------------------
+// trace_begin/trace_end bracket one launch with events on p->stream when
+// tracing is on; trace_collect (after a stream sync) accumulates durations.
+void trace_begin(rsot_problem *p, const char *name);
+void trace_end(rsot_problem *p);
+void trace_collect(rsot_problem *p);
+
+// ---- launch helpers implemented in rsot_dense.cu --------------------------
+cudaError_t dense_alloc(rsot_problem *p);
+void dense_free(rsot_problem *p);
+cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi_dev, double eps,
+                               double *grad_dev);
+cudaError_t launch_dense_fp64(rsot_problem *p, const double *psi_dev, double eps,
+                              double *grad_dev);
+cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev);
+cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out3_dev);
+cudaError_t launch_point_L(rsot_problem *p, double *L_dev);
+
+// ---- truncated path (rsot_trunc.cu) ----------------------------------------
+cudaError_t trunc_eval(rsot_problem *p, const double *psi_dev, double eps, double radius,
+                       int mixed, double *grad_dev);
+void trunc_free(rsot_problem *p);
+cudaError_t trunc_point_L(rsot_problem *p, double *L_dev);
+
+// ---- device helpers ----------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// 2^k for an integer-valued float k <= 0 (exact; 0 below the normal range).
+__device__ __forceinline__ float pow2_int_f(float k) {
+    return k < -126.0f ? 0.0f : __int_as_float(((int)k + 127) << 23);
+}
+__device__ __forceinline__ double pow2_int_d(float k) {
+    return k < -1022.0f ? 0.0 : __longlong_as_double((long long)((int)k + 1023) << 52);
+}
+
+// ---- mbarrier + bulk-copy (TMA) wrappers ------------------------------------
+constexpr long long kWaitLimit = 1ll << 24;   // bounded spin: ~seconds at most
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *smem, const void *gmem, unsigned bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(smem)),
+        "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false when the limit is reached (the caller records an error).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// Block-wide FP64 sum (blockDim.x a multiple of 32, <= 1024); result in thread 0.
+__device__ __forceinline__ double block_sum_d(double v, double *sh /* >= 32 */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+}  // namespace rsot

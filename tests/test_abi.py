@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/*.h declares (no compute call: this runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(rsot_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_23602_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("rsot_create", "rsot_eval_dual_grad", "rsot_solve", "rsot_radius_for_tail",
+              "rsot_destroy", "rsot_status_string", "rsot_covering_cost"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so, path = lib
+    for name in sorted(declared_functions()):
+        assert hasattr(so, name), f"{name} declared in include/ but not exported by {path}"
+
+
+def test_exports_are_unmangled_c_symbols(lib):
+    _, path = lib
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    for name in declared_functions():
+        assert name in exported
+
+
+def test_status_strings_without_gpu(lib):
+    so, _ = lib
+    so.rsot_status_string.restype = ctypes.c_char_p
+    so.rsot_version.restype = ctypes.c_char_p
+    assert so.rsot_status_string(0) == b"ok"
+    assert b"line search" in so.rsot_status_string(6)
+    assert b"sm_103a" in so.rsot_version()
+
+
+def test_argument_errors_need_no_gpu(lib):
+    so, _ = lib
+    h = ctypes.c_void_p()
+    # d = 4 is rejected before any CUDA call
+    assert so.rsot_create(4, 10, None, None, 5, None, None, ctypes.byref(h)) == 1
+    assert so.rsot_create(2, 0, None, None, 5, None, None, ctypes.byref(h)) == 1
+    assert so.rsot_eval_dual_grad(None, None, ctypes.c_double(0.1), ctypes.c_double(0.0), 1,
+                                  None, None, None) == 1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_2507_23602_gb300 as rs
+    monkeypatch.setattr(rs, "_LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(rs, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        rs.load()

@@ -103,6 +103,18 @@ def test_plan_coincident_targets():
     assert np.allclose(P, ref[None, :], rtol=1e-13)
 
 
+def test_point_lse_matches_library_logsumexp_and_J():
+    """L_q equals scipy's logsumexp of (psi_j - c_qj)/eps with weights nu_j,
+    and sum_q m_q eps L_q - psi.nu reproduces J."""
+    x, m, y, nu, psi, eps = tiny_problem(20, d=3, nq=40, n=9, eps=0.02)
+    L = oracle.point_lse(x, y, nu, psi, eps)
+    C = 0.5 * ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)
+    ref = scipy.special.logsumexp((psi[None, :] - C) / eps, b=nu[None, :], axis=1)
+    assert np.allclose(L, ref, rtol=1e-14, atol=1e-13)
+    J, _, _, _ = oracle.dual_grad(x, m, y, nu, psi, eps)
+    assert abs(np.sum(m * eps * L) - psi @ nu - J) < 1e-15
+
+
 # ----------------------------------------------------- dual value / grad ---
 
 def test_single_target_closed_form():
