@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(P1_THREADS, 3)
                 int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags) {
     __shared__ __align__(128) Rec8 sm[P1_STAGES][P1_TS];
     __shared__ __align__(8) uint64_t full[P1_STAGES];
-    __shared__ int s_abort;
+    __shared__ int s_abort[2];   // indexed by iteration parity
 
     const int tid = threadIdx.x;
     const int64_t q0 = (int64_t)blockIdx.x * P1_TILE;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(P1_THREADS, 3)
     }
 
     if (tid == 0) {
-        s_abort = 0;
+        s_abort[0] = s_abort[1] = 0;
         for (int s = 0; s < P1_STAGES; ++s) mbar_init(&full[s], 1);
         fence_barrier_init();
     }
@@ -147,12 +147,13 @@ __global__ void __launch_bounds__(P1_THREADS, 3)
     }
 
     int issued = min(P1_STAGES, ntile);
+    bool aborted = false;
     for (int it = 0; it < ntile; ++it) {
         const int s = it % P1_STAGES;
         const unsigned ph = (unsigned)(it / P1_STAGES) & 1u;
         const bool ok = mbar_wait(&full[s], ph);
         if (!ok) {
-            s_abort = 1;
+            s_abort[it & 1] = 1;
             atomicOr(flags, kErrTimeout);
         } else {
             const Rec8 *T = sm[s];
@@ -212,7 +213,8 @@ __global__ void __launch_bounds__(P1_THREADS, 3)
             }
         }
         __syncthreads();
-        if (s_abort) break;
+        aborted = s_abort[it & 1] != 0;
+        if (aborted) break;
         if (tid == 0 && it + P1_STAGES < ntile) {
             mbar_expect_tx(&full[s], P1_TS * sizeof(Rec8));
             bulk_g2s(sm[s], tdup + t_begin + (it + P1_STAGES) * P1_TS, P1_TS * sizeof(Rec8),
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(P1_THREADS, 3)
             Sf[pp] = make_float2(0.f, 0.f);
         }
     }
-    if (s_abort) {
+    if (aborted) {
         // drain copies still in flight (bounded) before the CTA exits
         if (tid == 0) {
             for (int it = 0; it < issued; ++it) {
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(P2_THREADS)
                  int *__restrict__ flags) {
     __shared__ __align__(128) Rec8 sm[P2_STAGES][P2_TS];
     __shared__ __align__(8) uint64_t full[P2_STAGES];
-    __shared__ int s_abort;
+    __shared__ int s_abort[2];   // indexed by iteration parity
 
     const int tid = threadIdx.x;
     const int64_t g0 = (int64_t)blockIdx.x * P2_THREADS * TPP;
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(P2_THREADS)
     for (int tp = 0; tp < TPP; ++tp) acc64[tp] = make_double2(0.0, 0.0);
 
     if (tid == 0) {
-        s_abort = 0;
+        s_abort[0] = s_abort[1] = 0;
         for (int s = 0; s < P2_STAGES; ++s) mbar_init(&full[s], 1);
         fence_barrier_init();
     }
@@ -328,12 +330,13 @@ __global__ void __launch_bounds__(P2_THREADS)
         }
     }
     int issued = min(P2_STAGES, ntile);
+    bool aborted = false;
     for (int it = 0; it < ntile; ++it) {
         const int s = it % P2_STAGES;
         const unsigned ph = (unsigned)(it / P2_STAGES) & 1u;
         const bool ok = mbar_wait(&full[s], ph);
         if (!ok) {
-            s_abort = 1;
+            s_abort[it & 1] = 1;
             atomicOr(flags, kErrTimeout);
         } else {
             const Rec8 *T = sm[s];
@@ -363,7 +366,8 @@ __global__ void __launch_bounds__(P2_THREADS)
             }
         }
         __syncthreads();
-        if (s_abort) break;
+        aborted = s_abort[it & 1] != 0;
+        if (aborted) break;
         if (tid == 0 && it + P2_STAGES < ntile) {
             mbar_expect_tx(&full[s], P2_TS * sizeof(Rec8));
             bulk_g2s(sm[s], pdup + p_begin + (int64_t)(it + P2_STAGES) * P2_TS,
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(P2_THREADS)
             ++issued;
         }
     }
-    if (s_abort) {
+    if (aborted) {
         if (tid == 0) {
             for (int it = 0; it < issued; ++it)
                 (void)mbar_wait(&full[it % P2_STAGES], (unsigned)(it / P2_STAGES) & 1u);
