@@ -178,6 +178,8 @@ rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, 
     cudaGetDevice(&p->dev);
     cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->dev);
     for (int k = 0; k < d; ++k) p->origin[k] = 0.5 * (lo[k] + hi[k]);
+    p->diam2 = 0.0;
+    for (int k = 0; k < d; ++k) p->diam2 += (hi[k] - lo[k]) * (hi[k] - lo[k]);
     p->nq_pad = round_up(nq, 1024);
 
     // translated coordinates (cost is translation invariant)
@@ -254,7 +256,8 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, 
     const bool gdev = is_device_ptr(grad_out);
     double *gd = gdev ? grad_out : p->grad_dev;
     if (!e) e = cudaMemsetAsync(p->res_dev, 0, sizeof(EvalResult), st);
-    const bool dense = !(radius > 0.0) || isinf(radius);
+    // a radius beyond the diameter of the data keeps every pair: dense
+    const bool dense = !(radius > 0.0) || isinf(radius) || radius * radius > p->diam2 * (1.0 + 1e-12);
     if (!e) {
         if (dense)
             e = (prec == RSOT_MIXED) ? launch_dense_mixed(p, psid, eps, gd)

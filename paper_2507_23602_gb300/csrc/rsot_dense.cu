@@ -442,19 +442,26 @@ __global__ void k_prep_fp64(const double *__restrict__ psi, const double *__rest
     if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
 }
 
+// cutoff = +inf: dense; otherwise only pairs with c(x_q, y_j) < cutoff enter
+// (Algorithm 2), the number of such pairs and of empty points is counted.
 template <int D>
 __global__ void __launch_bounds__(F_THREADS)
     k_lse_fp64(const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
                const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
-               double inv_eps, const double *__restrict__ mass, double *__restrict__ prec64,
-               double *__restrict__ blockJ, double *__restrict__ lse_buf) {
+               double inv_eps, double cutoff, const double *__restrict__ mass,
+               double *__restrict__ prec64, double *__restrict__ blockJ,
+               double *__restrict__ lse_buf, EvalResult *__restrict__ res) {
     __shared__ double sy[F_TS][4];
     __shared__ double sh[32];
+    __shared__ unsigned long long s_cnt, s_empty;
+    if (threadIdx.x == 0) s_cnt = s_empty = 0;
     const int64_t q = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
     double x[3] = {0.0, 0.0, 0.0};
     if (q < nq)
         for (int t = 0; t < D; ++t) x[t] = x64[q * D + t];
     double M = -INFINITY, S = 0.0;
+    unsigned long long npair = 0;
+    __syncthreads();
     for (int64_t t0 = 0; t0 < n; t0 += F_TS) {
         for (int i = threadIdx.x; i < F_TS; i += F_THREADS) {
             const int64_t j = t0 + i;
@@ -474,7 +481,10 @@ __global__ void __launch_bounds__(F_THREADS)
                 const double dd = x[t] - sy[i][t];
                 c += dd * dd;
             }
-            const double s = sy[i][3] - 0.5 * c * inv_eps;
+            c *= 0.5;
+            if (!(c < cutoff)) continue;
+            ++npair;
+            const double s = sy[i][3] - c * inv_eps;
             const double dlt = s - M;
             const double e = exp(-fabs(dlt));
             if (dlt > 0.0) {
@@ -490,12 +500,18 @@ __global__ void __launch_bounds__(F_THREADS)
     if (q < nq_pad) {
         double u = -INFINITY;
         if (q < nq) {
-            const double L = M + log(S);
-            lse_buf[q] = L;
-            if (mass[q] > 0.0) {
-                contrib = mass[q] * L;
-                u = log(mass[q]) - L;
+            if (S > 0.0) {
+                const double L = M + log(S);
+                lse_buf[q] = L;
+                if (mass[q] > 0.0) {
+                    contrib = mass[q] * L;
+                    u = log(mass[q]) - L;
+                }
+            } else {   // empty I_q: skipped by Algorithm 2
+                lse_buf[q] = -INFINITY;
+                atomicAdd(&s_empty, 1ull);
             }
+            atomicAdd(&s_cnt, npair);
         }
         double *r = prec64 + q * 4;
         r[0] = x[0];
@@ -504,14 +520,18 @@ __global__ void __launch_bounds__(F_THREADS)
         r[3] = u;
     }
     const double s = block_sum_d(contrib, sh);
-    if (threadIdx.x == 0) blockJ[blockIdx.x] = s;
+    if (threadIdx.x == 0) {
+        blockJ[blockIdx.x] = s;
+        if (s_cnt) atomicAdd(reinterpret_cast<unsigned long long *>(&res->pairs), s_cnt);
+        if (s_empty) atomicAdd(reinterpret_cast<unsigned long long *>(&res->empty), s_empty);
+    }
 }
 
 template <int D>
 __global__ void __launch_bounds__(F_THREADS)
     k_grad_fp64(const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
                 const double *__restrict__ prec64, int64_t nq_pad, int64_t chunk, double inv_eps,
-                double *__restrict__ part2, int64_t stride) {
+                double cutoff, double *__restrict__ part2, int64_t stride) {
     __shared__ double sp[F_TS][4];
     const int64_t j = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
     double y[3] = {0.0, 0.0, 0.0};
@@ -534,10 +554,11 @@ __global__ void __launch_bounds__(F_THREADS)
             double c = 0.0;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
-                const double dd = sp[i][t] - y[t];
+                const double dd = sp[i][t] - y[t];   // x - y, as in pass 1
                 c += dd * dd;
             }
-            acc += exp(a - 0.5 * c * inv_eps + sp[i][3]);
+            c *= 0.5;
+            if (c < cutoff) acc += exp(a - c * inv_eps + sp[i][3]);
         }
         __syncthreads();
     }
@@ -784,7 +805,8 @@ cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi, double eps, d
 }
 
 template <int D>
-static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps, double *grad) {
+static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps, double *grad,
+                                 double cutoff) {
     cudaStream_t st = p->stream;
     trace_begin(p, "prep_targets_fp64");
     k_prep_fp64<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->lnu, p->nu, p->n, p->n_pad, eps,
@@ -793,13 +815,14 @@ static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps,
     const unsigned nb1 = (unsigned)((p->nq_pad + F_THREADS - 1) / F_THREADS);
     trace_begin(p, "lse_fp64");
     k_lse_fp64<D><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64, p->n,
-                                             1.0 / eps, p->mass, p->prec64, p->blockJ,
-                                             p->lse_buf);
+                                             1.0 / eps, cutoff, p->mass, p->prec64, p->blockJ,
+                                             p->lse_buf, p->res_dev);
     trace_end(p);
     dim3 g2((unsigned)((p->n + F_THREADS - 1) / F_THREADS), (unsigned)p->s2_64);
     trace_begin(p, "grad_fp64");
     k_grad_fp64<D><<<g2, F_THREADS, 0, st>>>(p->y64, p->a64, p->n, p->prec64, p->nq_pad,
-                                             p->chunk2_64, 1.0 / eps, p->part2_64, p->n_pad);
+                                             p->chunk2_64, 1.0 / eps, cutoff, p->part2_64,
+                                             p->n_pad);
     trace_end(p);
     trace_begin(p, "finalize_grad");
     k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(p->part2_64, p->s2_64,
@@ -813,7 +836,14 @@ static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps,
 }
 
 cudaError_t launch_dense_fp64(rsot_problem *p, const double *psi, double eps, double *grad) {
-    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad) : launch_fp64_d<2>(p, psi, eps, grad);
+    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad, INFINITY)
+                     : launch_fp64_d<2>(p, psi, eps, grad, INFINITY);
+}
+
+cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi, double eps, double cutoff,
+                              double *grad) {
+    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad, cutoff)
+                     : launch_fp64_d<2>(p, psi, eps, grad, cutoff);
 }
 
 cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev) {

@@ -64,6 +64,7 @@ struct rsot_problem {
     double msum = 0.0;          // sum_q m_q
     double hx = 0.0;            // sum_q m_q |x'_q|^2 / 2 (translated coordinates)
     double nu_min = 0.0, nu_max = 0.0;
+    double diam2 = 0.0;         // squared diameter of the bounding box of points and targets
     int num_sms = 0;
 
     // static device data
@@ -137,6 +138,8 @@ void dense_free(rsot_problem *p);
 cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi_dev, double eps,
                                double *grad_dev);
 cudaError_t launch_dense_fp64(rsot_problem *p, const double *psi_dev, double eps,
+                              double *grad_dev);
+cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi_dev, double eps, double cutoff,
                               double *grad_dev);
 cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev);
 cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out3_dev);

@@ -1,10 +1,938 @@
-// Truncated evaluation (placeholder until the cell-list kernels land).
+// Truncated dual + gradient evaluation (Algorithm 2 with I_q = {j : c(x_q,y_j) < C}).
+//
+// Spatial index (replaces the paper's R-tree, Sec. 4.1): a uniform grid of
+// 2^b cells per axis over the bounding box of points and targets.  Points and
+// targets are ordered by the Morton (Z-order) index of their cell, ties by
+// their input index (a deterministic bitonic sort on the GPU, built once per
+// problem).  Consecutive runs of the sorted order form tiles -- 1024 points or
+// 256 targets -- that are spatially compact; each tile carries its bounding
+// box.  Per evaluation, a (point tile, target tile) pair is a candidate when
+// the boxes are closer than the radius; every candidate pair of points and
+// targets is then tested exactly (c < C, strict) inside the kernels, so the
+// sums run over I_q exactly as in Algorithm 2.
+//
+// Work is a queue of items (point tile, chunk of candidate target tiles) for
+// pass 1 and (target tile, chunk of candidate point tiles) for pass 2,
+// consumed by persistent CTAs through an atomic counter.  Partial results are
+// stored per item and merged in a fixed order, so results do not depend on
+// which CTA ran which item.
+//
+// Mixed precision uses the log2-domain quantities of the dense path
+// (rsot_dense.cu): r_qj = c_j + x'_q.w_j, and the truncation test
+//   k |x'_q - y'_j|^2 < k C   <=>   r_qj - b_j > k |x'_q|^2 - k C  (=: A_q).
+// The FP64 truncated evaluation reuses the dense FP64 kernels with the
+// predicate (rsot_dense.cu).
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
 #include "rsot_internal.cuh"
 
 namespace rsot {
-cudaError_t trunc_eval(rsot_problem *, const double *, double, double, int, double *) {
-    return cudaErrorNotSupported;
+
+struct __align__(16) Rec12 {
+    float4 a, b, c;
+};
+
+struct Grid {
+    int b = 0, G = 0;
+    double lo[3] = {0, 0, 0};
+    double h = 0.0;
+    int64_t nqt = 0, nt = 0;             // padded sorted counts
+    int ptiles = 0, ttiles = 0, tw = 0, pw = 0;
+    int ch1 = 0, ch2 = 0;
+    int64_t items1_max = 0, items2_max = 0;
+    int slots1 = 0, slots2 = 0;
+    int *perm_q = nullptr, *perm_t = nullptr;
+    float *xs = nullptr;                  // [d][nqt]
+    double *x64 = nullptr, *mass = nullptr, *lm2 = nullptr;
+    double *y64 = nullptr, *nu = nullptr, *lnu = nullptr;
+    float *pbox = nullptr, *tbox = nullptr;
+    uint32_t *bits_pt = nullptr, *bits_tp = nullptr;
+    int *cnt1 = nullptr, *cnt2 = nullptr, *off1 = nullptr, *off2 = nullptr, *counters = nullptr;
+    float *Aq = nullptr;
+    Rec12 *tdup = nullptr, *ppair = nullptr;
+    float2 *part1 = nullptr;
+    double *part2 = nullptr;
+    double *lse_s = nullptr;
+    double *blockJ = nullptr;
+    int nblk_comb = 0;
+};
+
+namespace {
+
+constexpr int PT = 1024;          // points per tile
+constexpr int TT = 256;           // targets per tile
+constexpr int L_THREADS = 128;    // pass-1 CTA (8 points / thread)
+constexpr int L_PP = 4;
+constexpr int L_SUB = 8;          // targets per max sub-tile
+constexpr float L_THR = 32.0f;
+constexpr int G_THREADS = 64;     // pass-2 CTA (4 targets / thread)
+constexpr int G_TPT = 4;
+constexpr int G_STAGE = 256;      // point-pair records per pass-2 stage (512 points)
+constexpr int MAX_CH = 64;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------- grid build
+__device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every 3rd bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
 }
-void trunc_free(rsot_problem *) {}
-cudaError_t trunc_point_L(rsot_problem *, double *) { return cudaErrorNotSupported; }
+__device__ __forceinline__ unsigned spread2(unsigned v) {   // 15 bits -> every 2nd bit
+    v &= 0x7fffu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__global__ void k_morton_keys(const double *__restrict__ c64, int64_t cnt, int64_t npow2, int d,
+                              double lo0, double lo1, double lo2, double inv_h, int G,
+                              unsigned long long *__restrict__ keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npow2) return;
+    if (i >= cnt) {
+        keys[i] = ~0ull;
+        return;
+    }
+    const double lo[3] = {lo0, lo1, lo2};
+    unsigned cell[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) {
+        double t = (c64[i * d + k] - lo[k]) * inv_h;
+        int ci = (int)floor(t);
+        ci = ci < 0 ? 0 : (ci >= G ? G - 1 : ci);
+        cell[k] = (unsigned)ci;
+    }
+    const unsigned code = (d == 3) ? (spread3(cell[0]) | (spread3(cell[1]) << 1) | (spread3(cell[2]) << 2))
+                                   : (spread2(cell[0]) | (spread2(cell[1]) << 1));
+    keys[i] = ((unsigned long long)code << 32) | (unsigned long long)i;
+}
+
+__global__ void k_bitonic_step(unsigned long long *__restrict__ a, int64_t n, int64_t j, int64_t k) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t ixj = i ^ j;
+    if (ixj > i) {
+        const bool up = (i & k) == 0;
+        const unsigned long long x = a[i], y = a[ixj];
+        if ((x > y) == up) {
+            a[i] = y;
+            a[ixj] = x;
+        }
+    }
+}
+
+// sorted position s -> original index; gather FP32/FP64 copies in sorted order
+__global__ void k_gather_points(const unsigned long long *__restrict__ keys, int64_t nq, int64_t nqt,
+                                int d, const double *__restrict__ x64, const double *__restrict__ mass,
+                                const double *__restrict__ lm2, int *__restrict__ perm, float *__restrict__ xs,
+                                double *__restrict__ x64s, double *__restrict__ mass_s,
+                                double *__restrict__ lm2_s) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nqt) return;
+    if (s < nq) {
+        const int64_t o = (int64_t)(keys[s] & 0xffffffffull);
+        perm[s] = (int)o;
+        for (int k = 0; k < d; ++k) {
+            const double v = x64[o * d + k];
+            x64s[s * d + k] = v;
+            xs[k * nqt + s] = (float)v;
+        }
+        mass_s[s] = mass[o];
+        lm2_s[s] = lm2[o];
+    } else {
+        perm[s] = -1;
+        for (int k = 0; k < d; ++k) {
+            x64s[s * d + k] = 0.0;
+            xs[k * nqt + s] = 0.0f;
+        }
+        mass_s[s] = 0.0;
+        lm2_s[s] = -INFINITY;
+    }
+}
+
+__global__ void k_gather_targets(const unsigned long long *__restrict__ keys, int64_t n, int64_t nt,
+                                 int d, const double *__restrict__ y64, const double *__restrict__ nu,
+                                 const double *__restrict__ lnu, int *__restrict__ perm,
+                                 double *__restrict__ y64s, double *__restrict__ nu_s,
+                                 double *__restrict__ lnu_s) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nt) return;
+    if (s < n) {
+        const int64_t o = (int64_t)(keys[s] & 0xffffffffull);
+        perm[s] = (int)o;
+        for (int k = 0; k < d; ++k) y64s[s * d + k] = y64[o * d + k];
+        nu_s[s] = nu[o];
+        lnu_s[s] = lnu[o];
+    } else {
+        perm[s] = -1;
+        for (int k = 0; k < d; ++k) y64s[s * d + k] = 0.0;
+        nu_s[s] = 0.0;
+        lnu_s[s] = -INFINITY;
+    }
+}
+
+// bounding box of each tile over its real members (FP32 coordinates)
+__global__ void k_tile_boxes(const double *__restrict__ c64s, int64_t cnt, int d, int tile,
+                             int ntiles, float *__restrict__ box) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const int64_t a = (int64_t)t * tile, e = min((int64_t)(t + 1) * tile, cnt);
+    for (int64_t s = a; s < e; ++s)
+        for (int k = 0; k < d; ++k) {
+            const float v = (float)c64s[s * d + k];
+            lo[k] = fminf(lo[k], v);
+            hi[k] = fmaxf(hi[k], v);
+        }
+    for (int k = 0; k < 3; ++k) {
+        if (k >= d) {
+            lo[k] = 0.f;
+            hi[k] = 0.f;
+        }
+        box[t * 6 + k] = lo[k];
+        box[t * 6 + 3 + k] = hi[k];
+    }
+}
+
+// ------------------------------------------------------------- per evaluation
+// A_q = k |x'_q|^2 - k C (FP32, computed once so that both passes agree)
+__global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt, int d, float k,
+                          float kC, float *__restrict__ Aq) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nqt) return;
+    if (s >= nq) {
+        Aq[s] = INFINITY;
+        return;
+    }
+    float r2 = 0.f;
+    for (int t = 0; t < d; ++t) {
+        const float v = xs[t * nqt + s];
+        r2 = fmaf(v, v, r2);
+    }
+    Aq[s] = fmaf(k, r2, -kC);
+}
+
+__device__ __forceinline__ float box_dist2(const float *a, const float *b) {
+    float s = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        const float g = fmaxf(0.f, fmaxf(a[k] - b[3 + k], b[k] - a[3 + k]));
+        s = fmaf(g, g, s);
+    }
+    return s;
+}
+
+// candidate (point tile, target tile) pairs: bit matrices in both orientations
+__global__ void k_tile_pairs(const float *__restrict__ pbox, const float *__restrict__ tbox,
+                             int ptiles, int ttiles, int tw, int pw, float r2,
+                             uint32_t *__restrict__ bits_pt, uint32_t *__restrict__ bits_tp,
+                             int *__restrict__ cnt1, int *__restrict__ cnt2) {
+    __shared__ int s_cnt;
+    const int p = blockIdx.x;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    float pb[6];
+    for (int k = 0; k < 6; ++k) pb[k] = pbox[p * 6 + k];
+    const bool pempty = !(pb[0] <= pb[3]);
+    int mine = 0;
+    for (int t0 = 0; t0 < tw * 32; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        bool cand = false;
+        if (t < ttiles && !pempty) {
+            float tb[6];
+            for (int k = 0; k < 6; ++k) tb[k] = tbox[t * 6 + k];
+            cand = (tb[0] <= tb[3]) && box_dist2(pb, tb) < r2;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if ((threadIdx.x & 31) == 0 && t < tw * 32) bits_pt[(size_t)p * tw + t / 32] = bal;
+        if (cand) {
+            atomicOr(&bits_tp[(size_t)t * pw + p / 32], 1u << (p & 31));
+            atomicAdd(&cnt2[t], 1);
+            ++mine;
+        }
+    }
+    atomicAdd(&s_cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt1[p] = s_cnt;
+}
+
+// item offsets: off[i] = sum_{i' < i} ceil(cnt[i'] / ch); one block
+__global__ void k_item_offsets(const int *__restrict__ cnt1, int ptiles, int ch1,
+                               const int *__restrict__ cnt2, int ttiles, int ch2,
+                               int *__restrict__ off1, int *__restrict__ off2,
+                               int *__restrict__ counters) {
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int i = 0; i < ptiles; ++i) {
+            off1[i] = s;
+            s += (cnt1[i] + ch1 - 1) / ch1;
+        }
+        off1[ptiles] = s;
+        counters[0] = 0;
+    } else if (threadIdx.x == 32) {
+        int s = 0;
+        for (int i = 0; i < ttiles; ++i) {
+            off2[i] = s;
+            s += (cnt2[i] + ch2 - 1) / ch2;
+        }
+        off2[ttiles] = s;
+        counters[1] = 0;
+    }
+}
+
+// target records in sorted order: (w0,w0,w1,w1) (w2,w2,c,c) (-b,-b,0,0)
+__global__ void k_prep_trunc(const double *__restrict__ psi, const int *__restrict__ perm_t,
+                             const double *__restrict__ y64s, const double *__restrict__ lnu_s,
+                             int64_t n, int64_t nt, int d, double eps, Rec12 *__restrict__ tdup,
+                             double *__restrict__ psinu_part, const double *__restrict__ nu_s,
+                             int *__restrict__ flags) {
+    __shared__ double sh[32];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double psic = psi[0];
+    const double k = kLog2e / (2.0 * eps);
+    double contrib = 0.0;
+    if (s < nt) {
+        float w[3] = {0.f, 0.f, 0.f};
+        float c = kPadC, nb = kPadC;
+        if (s < n) {
+            const double ps = psi[perm_t[s]];
+            if (!isfinite(ps)) atomicOr(flags, kErrNonfinitePsi);
+            const double b = ((ps - psic) / eps + lnu_s[s]) * kLog2e;
+            double yy = 0.0;
+            for (int t = 0; t < d; ++t) {
+                const double yt = y64s[s * d + t];
+                w[t] = (float)(2.0 * k * yt);
+                yy += yt * yt;
+            }
+            c = (float)(b - k * yy);
+            nb = (float)(-b);
+            contrib = ps * nu_s[s];
+        }
+        Rec12 r;
+        r.a = make_float4(w[0], w[0], w[1], w[1]);
+        r.b = make_float4(w[2], w[2], c, c);
+        r.c = make_float4(nb, nb, 0.f, 0.f);
+        tdup[s] = r;
+    }
+    const double v = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) psinu_part[blockIdx.x] = v;
+}
+
+// k-th chunk of set bits of a bit row -> list (thread 0 only)
+__device__ int collect_bits(const uint32_t *__restrict__ row, int words, int skip, int ch, int *list) {
+    int got = 0;
+    for (int w = 0; w < words && got < ch; ++w) {
+        uint32_t bits = row[w];
+        const int pc = __popc(bits);
+        if (skip >= pc) {
+            skip -= pc;
+            continue;
+        }
+        while (bits && got < ch) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (skip > 0) {
+                --skip;
+                continue;
+            }
+            list[got++] = w * 32 + b;
+        }
+    }
+    return got;
+}
+
+__device__ __forceinline__ int find_row(const int *__restrict__ off, int rows, int item) {
+    int lo = 0, hi = rows;   // off[lo] <= item < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------- pass 1
+template <int D>
+__global__ void __launch_bounds__(L_THREADS, 3)
+    k_lse_trunc(const float *__restrict__ xs, int64_t nqt, const float *__restrict__ Aq,
+                const Rec12 *__restrict__ tdup, const uint32_t *__restrict__ bits_pt, int tw,
+                const int *__restrict__ off1, int ptiles, int ch1, int *__restrict__ counter,
+                float2 *__restrict__ part1, unsigned long long *__restrict__ pairs,
+                int *__restrict__ flags) {
+    __shared__ __align__(128) Rec12 sm[2][TT];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int s_item, s_p, s_cnt, s_abort[2];
+    __shared__ int s_list[MAX_CH];
+    __shared__ unsigned long long s_pairs;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+        s_abort[0] = s_abort[1] = 0;
+        s_pairs = 0;
+    }
+    __syncthreads();
+    const int total = off1[ptiles];
+    unsigned git = 0;
+    unsigned long long mycnt = 0;
+    bool aborted = false;
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(counter, 1);
+            s_item = it;
+            if (it < total) {
+                const int p = find_row(off1, ptiles, it);
+                s_p = p;
+                s_cnt = collect_bits(bits_pt + (size_t)p * tw, tw, (it - off1[p]) * ch1, ch1, s_list);
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int p = s_p, cnt = s_cnt;
+        if (tid == 0) {
+            for (int s = 0; s < 2 && s < cnt; ++s) {
+                const unsigned slot = (git + s) & 1u;
+                mbar_expect_tx(&full[slot], TT * sizeof(Rec12));
+                bulk_g2s(sm[slot], tdup + (int64_t)s_list[s] * TT, TT * sizeof(Rec12), &full[slot]);
+            }
+        }
+        const int64_t q0 = (int64_t)p * PT;
+        float2 X[L_PP][3], A[L_PP];
+#pragma unroll
+        for (int pp = 0; pp < L_PP; ++pp) {
+            const int64_t q = q0 + 2 * (pp * L_THREADS + tid);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                X[pp][k] = (k < D) ? *reinterpret_cast<const float2 *>(xs + k * nqt + q)
+                                   : make_float2(0.f, 0.f);
+            A[pp] = *reinterpret_cast<const float2 *>(Aq + q);
+        }
+        float2 M[L_PP], Sf[L_PP];
+        double2 Sd[L_PP];
+#pragma unroll
+        for (int pp = 0; pp < L_PP; ++pp) {
+            M[pp] = make_float2(kPadC, kPadC);
+            Sf[pp] = make_float2(0.f, 0.f);
+            Sd[pp] = make_double2(0.0, 0.0);
+        }
+        unsigned icnt = 0;
+        for (int it = 0; it < cnt; ++it) {
+            const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
+            if (!mbar_wait(&full[slot], ph)) {
+                s_abort[it & 1] = 1;
+                atomicOr(flags, kErrTimeout);
+            } else {
+                const Rec12 *T = sm[slot];
+#pragma unroll 1
+                for (int t0 = 0; t0 < TT; t0 += L_SUB) {
+                    float2 r[L_PP][L_SUB];
+#pragma unroll
+                    for (int t = 0; t < L_SUB; ++t) {
+                        const float4 a = T[t0 + t].a, b = T[t0 + t].b, e = T[t0 + t].c;
+                        const float2 w0 = make_float2(a.x, a.y), w1 = make_float2(a.z, a.w);
+                        const float2 w2 = make_float2(b.x, b.y), c = make_float2(b.z, b.w);
+                        const float2 nb = make_float2(e.x, e.y);
+#pragma unroll
+                        for (int pp = 0; pp < L_PP; ++pp) {
+                            float2 acc = c;
+                            if (D == 3) acc = __ffma2_rn(X[pp][2], w2, acc);
+                            acc = __ffma2_rn(X[pp][1], w1, acc);
+                            acc = __ffma2_rn(X[pp][0], w0, acc);
+                            const float2 v = __fadd2_rn(acc, nb);
+                            const bool px = v.x > A[pp].x, py = v.y > A[pp].y;
+                            icnt += (unsigned)px + (unsigned)py;
+                            r[pp][t] = make_float2(px ? acc.x : -INFINITY, py ? acc.y : -INFINITY);
+                        }
+                    }
+#pragma unroll
+                    for (int pp = 0; pp < L_PP; ++pp) {
+                        float mx = r[pp][0].x, my = r[pp][0].y;
+#pragma unroll
+                        for (int t = 1; t + 1 < L_SUB; t += 2) {
+                            mx = max3f(mx, r[pp][t].x, r[pp][t + 1].x);
+                            my = max3f(my, r[pp][t].y, r[pp][t + 1].y);
+                        }
+                        mx = fmaxf(mx, r[pp][L_SUB - 1].x);
+                        my = fmaxf(my, r[pp][L_SUB - 1].y);
+                        if (mx > M[pp].x + L_THR) {
+                            const float mn = ceilf(mx), dl = M[pp].x - mn;
+                            Sf[pp].x *= pow2_int_f(dl);
+                            Sd[pp].x *= pow2_int_d(dl);
+                            M[pp].x = mn;
+                        }
+                        if (my > M[pp].y + L_THR) {
+                            const float mn = ceilf(my), dl = M[pp].y - mn;
+                            Sf[pp].y *= pow2_int_f(dl);
+                            Sd[pp].y *= pow2_int_d(dl);
+                            M[pp].y = mn;
+                        }
+                        const float2 nm = make_float2(-M[pp].x, -M[pp].y);
+                        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int t = 0; t < L_SUB; ++t) {
+                            const float2 e = __fadd2_rn(r[pp][t], nm);
+                            acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                        }
+                        Sf[pp] = __fadd2_rn(Sf[pp], acc);
+                    }
+                }
+            }
+            __syncthreads();
+            aborted = s_abort[it & 1] != 0;
+            if (aborted) break;
+            if (tid == 0 && it + 2 < cnt) {
+                mbar_expect_tx(&full[slot], TT * sizeof(Rec12));
+                bulk_g2s(sm[slot], tdup + (int64_t)s_list[it + 2] * TT, TT * sizeof(Rec12), &full[slot]);
+            }
+#pragma unroll
+            for (int pp = 0; pp < L_PP; ++pp) {
+                Sd[pp].x += (double)Sf[pp].x;
+                Sd[pp].y += (double)Sf[pp].y;
+                Sf[pp] = make_float2(0.f, 0.f);
+            }
+        }
+        if (aborted) break;
+        git += cnt;
+        mycnt += icnt;
+#pragma unroll
+        for (int pp = 0; pp < L_PP; ++pp) {
+            const int l = 2 * (pp * L_THREADS + tid);
+            *reinterpret_cast<float4 *>(part1 + (int64_t)item * PT + l) =
+                make_float4(M[pp].x, (float)Sd[pp].x, M[pp].y, (float)Sd[pp].y);
+        }
+        __syncthreads();
+    }
+    atomicAdd(&s_pairs, mycnt);
+    __syncthreads();
+    if (tid == 0) {
+        if (s_pairs) atomicAdd(pairs, s_pairs);
+        if (aborted) {   // bounded drain of copies that may still be in flight
+            for (int s = 0; s < 2; ++s) (void)mbar_wait(&full[s], 0u), (void)mbar_wait(&full[s], 1u);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ combine
+// Merge the item partials of each point; write pass-2 point-pair records
+// (x0a,x0b,x1a,x1b) (x2a,x2b,ua,ub) (Aa,Ab,0,0); sum m_q eps L_q over the
+// points with a non-empty I_q (Algorithm 2 skips the others).
+__global__ void k_combine_trunc(const float2 *__restrict__ part1, const int *__restrict__ off1,
+                                int64_t nq, int64_t nqt, const float *__restrict__ xs,
+                                const double *__restrict__ x64s, const double *__restrict__ mass_s,
+                                const double *__restrict__ lm2_s, const float *__restrict__ Aq,
+                                const double *__restrict__ psi, double eps, int d,
+                                Rec12 *__restrict__ ppair, double *__restrict__ lse_s,
+                                double *__restrict__ blockJ, EvalResult *__restrict__ res) {
+    __shared__ double sh[32];
+    __shared__ int s_empty;
+    if (threadIdx.x == 0) s_empty = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // point pair
+    double contrib = 0.0;
+    int empty = 0;
+    if (2 * i < nqt) {
+        const double psic = psi[0];
+        float x[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, u[2] = {kPadC, kPadC}, A[2];
+        for (int h = 0; h < 2; ++h) {
+            const int64_t q = 2 * i + h;
+            A[h] = Aq[q];
+            for (int t = 0; t < d; ++t) x[h][t] = xs[t * nqt + q];
+            if (q >= nq) continue;
+            const int p = (int)(q / PT), l = (int)(q % PT);
+            const int a = off1[p], e = off1[p + 1];
+            float mx = -INFINITY;
+            for (int it = a; it < e; ++it) mx = fmaxf(mx, part1[(int64_t)it * PT + l].x);
+            double tot = 0.0;
+            for (int it = a; it < e; ++it) {
+                const float2 v = part1[(int64_t)it * PT + l];
+                if (v.y > 0.f) tot += (double)v.y * pow2_int_d(v.x - mx);
+            }
+            if (tot > 0.0) {
+                const double R = (double)mx + log2(tot);
+                lse_s[q] = R;
+                if (mass_s[q] > 0.0) {
+                    double r2 = 0.0;
+                    for (int t = 0; t < d; ++t) r2 += x64s[q * d + t] * x64s[q * d + t];
+                    contrib += mass_s[q] * (psic + eps * kLn2 * R - 0.5 * r2);
+                    u[h] = (float)fmax(lm2_s[q] - R, -1.0e30);
+                }
+            } else {
+                lse_s[q] = -INFINITY;
+                ++empty;
+            }
+        }
+        Rec12 r;
+        r.a = make_float4(x[0][0], x[1][0], x[0][1], x[1][1]);
+        r.b = make_float4(x[0][2], x[1][2], u[0], u[1]);
+        r.c = make_float4(A[0], A[1], 0.f, 0.f);
+        ppair[i] = r;
+    }
+    if (empty) atomicAdd(&s_empty, empty);
+    const double s = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) {
+        blockJ[blockIdx.x] = s;
+        if (s_empty) atomicAdd(reinterpret_cast<unsigned long long *>(&res->empty), (unsigned long long)s_empty);
+    }
+}
+
+// ------------------------------------------------------------------- pass 2
+template <int D>
+__global__ void __launch_bounds__(G_THREADS)
+    k_grad_trunc(const Rec12 *__restrict__ ppair, const Rec12 *__restrict__ tdup,
+                 const uint32_t *__restrict__ bits_tp, int pw, const int *__restrict__ off2,
+                 int ttiles, int ch2, int *__restrict__ counter, double *__restrict__ part2,
+                 int *__restrict__ flags) {
+    __shared__ __align__(128) Rec12 sm[2][G_STAGE];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int s_item, s_t, s_cnt, s_abort[2];
+    __shared__ int s_list[MAX_CH];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+        s_abort[0] = s_abort[1] = 0;
+    }
+    __syncthreads();
+    const int total = off2[ttiles];
+    unsigned git = 0;
+    bool aborted = false;
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(counter, 1);
+            s_item = it;
+            if (it < total) {
+                const int t = find_row(off2, ttiles, it);
+                s_t = t;
+                s_cnt = collect_bits(bits_tp + (size_t)t * pw, pw, (it - off2[t]) * ch2, ch2, s_list);
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int t = s_t;
+        const int nst = 2 * s_cnt;   // two stages (512 points each) per point tile
+        if (tid == 0) {
+            for (int s = 0; s < 2 && s < nst; ++s) {
+                const unsigned slot = (git + s) & 1u;
+                mbar_expect_tx(&full[slot], G_STAGE * sizeof(Rec12));
+                bulk_g2s(sm[slot], ppair + (int64_t)s_list[s >> 1] * (PT / 2) + (s & 1) * G_STAGE,
+                         G_STAGE * sizeof(Rec12), &full[slot]);
+            }
+        }
+        float2 W0[G_TPT], W1[G_TPT], W2[G_TPT], C[G_TPT], NB[G_TPT];
+        double acc64[G_TPT];
+#pragma unroll
+        for (int i = 0; i < G_TPT; ++i) {
+            const Rec12 r = tdup[(int64_t)t * TT + i * G_THREADS + tid];
+            W0[i] = make_float2(r.a.x, r.a.y);
+            W1[i] = make_float2(r.a.z, r.a.w);
+            W2[i] = make_float2(r.b.x, r.b.y);
+            C[i] = make_float2(r.b.z, r.b.w);
+            NB[i] = make_float2(r.c.x, r.c.y);
+            acc64[i] = 0.0;
+        }
+        for (int it = 0; it < nst; ++it) {
+            const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
+            if (!mbar_wait(&full[slot], ph)) {
+                s_abort[it & 1] = 1;
+                atomicOr(flags, kErrTimeout);
+            } else {
+                const Rec12 *P = sm[slot];
+                float2 acc[G_TPT];
+#pragma unroll
+                for (int i = 0; i < G_TPT; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 2
+                for (int k = 0; k < G_STAGE; ++k) {
+                    const float4 a = P[k].a, b = P[k].b, e = P[k].c;
+                    const float2 x0 = make_float2(a.x, a.y), x1 = make_float2(a.z, a.w);
+                    const float2 x2 = make_float2(b.x, b.y), u = make_float2(b.z, b.w);
+                    const float2 A = make_float2(e.x, e.y);
+#pragma unroll
+                    for (int i = 0; i < G_TPT; ++i) {
+                        float2 r = C[i];
+                        if (D == 3) r = __ffma2_rn(x2, W2[i], r);
+                        r = __ffma2_rn(x1, W1[i], r);
+                        r = __ffma2_rn(x0, W0[i], r);
+                        const float2 v = __fadd2_rn(r, NB[i]);
+                        const float2 tt = __fadd2_rn(r, u);
+                        const float ex = v.x > A.x ? ex2_approx(tt.x) : 0.f;
+                        const float ey = v.y > A.y ? ex2_approx(tt.y) : 0.f;
+                        acc[i] = __fadd2_rn(acc[i], make_float2(ex, ey));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < G_TPT; ++i) acc64[i] += (double)acc[i].x + (double)acc[i].y;
+            }
+            __syncthreads();
+            aborted = s_abort[it & 1] != 0;
+            if (aborted) break;
+            if (tid == 0 && it + 2 < nst) {
+                const int s = it + 2;
+                mbar_expect_tx(&full[slot], G_STAGE * sizeof(Rec12));
+                bulk_g2s(sm[slot], ppair + (int64_t)s_list[s >> 1] * (PT / 2) + (s & 1) * G_STAGE,
+                         G_STAGE * sizeof(Rec12), &full[slot]);
+            }
+        }
+        if (aborted) break;
+        git += nst;
+#pragma unroll
+        for (int i = 0; i < G_TPT; ++i) part2[(int64_t)item * TT + i * G_THREADS + tid] = acc64[i];
+        __syncthreads();
+    }
+    if (aborted && tid == 0)
+        for (int s = 0; s < 2; ++s) (void)mbar_wait(&full[s], 0u), (void)mbar_wait(&full[s], 1u);
+}
+
+__global__ void k_finalize_grad_trunc(const double *__restrict__ part2, const int *__restrict__ off2,
+                                      int64_t n, const int *__restrict__ perm_t,
+                                      const double *__restrict__ nu_s, double *__restrict__ grad) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int t = (int)(s / TT), l = (int)(s % TT);
+    double g = 0.0;
+    for (int it = off2[t]; it < off2[t + 1]; ++it) g += part2[(int64_t)it * TT + l];
+    grad[perm_t[s]] = g - nu_s[s];
+}
+
+__global__ void k_finalize_J_trunc(const double *__restrict__ blockJ, int nbj,
+                                   const double *__restrict__ psinu, int npn,
+                                   const double *__restrict__ psi, EvalResult *__restrict__ res) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nbj; i += blockDim.x) a += blockJ[i];
+    for (int i = threadIdx.x; i < npn; i += blockDim.x) b += psinu[i];
+    const double sa = block_sum_d(a, sh);
+    const double sb = block_sum_d(b, sh);
+    if (threadIdx.x == 0) {
+        res->psic = psi[0];
+        res->J = sa - sb;
+    }
+}
+
+// L_q for the caller's point order from the sorted R_q
+__global__ void k_point_L_trunc(const double *__restrict__ lse_s, const int *__restrict__ perm_q,
+                                const double *__restrict__ x64s, int64_t nq, int d, double eps,
+                                const EvalResult *__restrict__ res, double *__restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nq) return;
+    const double R = lse_s[s];
+    double v = -INFINITY;
+    if (isfinite(R)) {
+        double r2 = 0.0;
+        for (int t = 0; t < d; ++t) r2 += x64s[s * d + t] * x64s[s * d + t];
+        v = res->psic / eps + kLn2 * R - 0.5 * r2 / eps;
+    }
+    out[perm_q[s]] = v;
+}
+
+int occupancy_of(const void *fn, int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+cudaError_t sort_keys(unsigned long long *keys, int64_t npow2, cudaStream_t st) {
+    const int thr = 256;
+    const unsigned blocks = (unsigned)((npow2 + thr - 1) / thr);
+    for (int64_t k = 2; k <= npow2; k <<= 1)
+        for (int64_t j = k >> 1; j > 0; j >>= 1)
+            k_bitonic_step<<<blocks, thr, 0, st>>>(keys, npow2, j, k);
+    return cudaGetLastError();
+}
+
+int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+// Build the grid, the sorted copies and the tile boxes (once per problem).
+static cudaError_t grid_build(rsot_problem *p) {
+    Grid *g = new Grid();
+    p->grid = g;
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    const int d = p->d;
+    // common bounding box (translated coordinates), on the host from the FP64 copies
+    std::vector<double> hx((size_t)p->nq * d), hy((size_t)p->n * d);
+    if ((e = cudaMemcpy(hx.data(), p->x64, hx.size() * 8, cudaMemcpyDeviceToHost))) return e;
+    if ((e = cudaMemcpy(hy.data(), p->y64, hy.size() * 8, cudaMemcpyDeviceToHost))) return e;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (size_t i = 0; i < hx.size(); ++i) {
+        lo[i % d] = std::min(lo[i % d], hx[i]);
+        hi[i % d] = std::max(hi[i % d], hx[i]);
+    }
+    for (size_t i = 0; i < hy.size(); ++i) {
+        lo[i % d] = std::min(lo[i % d], hy[i]);
+        hi[i % d] = std::max(hi[i % d], hy[i]);
+    }
+    double ext = 0.0;
+    for (int k = 0; k < d; ++k) ext = std::max(ext, hi[k] - lo[k]);
+    if (!(ext > 0.0)) ext = 1.0;
+    const double target_cells = std::max<double>(2.0, (double)std::max(p->nq, p->n) / 2.0);
+    int b = (int)ceil(log2(target_cells) / d);
+    b = std::max(1, std::min(b, d == 3 ? 10 : 15));
+    g->b = b;
+    g->G = 1 << b;
+    g->h = ext / g->G * (1.0 + 1e-9);
+    for (int k = 0; k < 3; ++k) g->lo[k] = k < d ? lo[k] : 0.0;
+
+    g->nqt = round_up(p->nq, PT);
+    g->nt = round_up(p->n, TT);
+    g->ptiles = (int)(g->nqt / PT);
+    g->ttiles = (int)(g->nt / TT);
+    g->tw = (g->ttiles + 31) / 32;
+    g->pw = (g->ptiles + 31) / 32;
+    g->ch1 = std::min(MAX_CH, std::max(16, (g->ttiles + 31) / 32));
+    g->ch2 = std::min(MAX_CH, std::max(16, (g->ptiles + 31) / 32));
+    g->items1_max = (int64_t)g->ptiles * ((g->ttiles + g->ch1 - 1) / g->ch1);
+    g->items2_max = (int64_t)g->ttiles * ((g->ptiles + g->ch2 - 1) / g->ch2);
+    g->nblk_comb = (int)((g->nqt / 2 + 255) / 256);
+
+    const int64_t npq = next_pow2(p->nq), npt = next_pow2(p->n);
+    unsigned long long *kq = nullptr, *kt = nullptr;
+    if ((e = cudaMalloc(&kq, npq * 8))) return e;
+    if ((e = cudaMalloc(&kt, npt * 8))) return e;
+    const double inv_h = 1.0 / g->h;
+    k_morton_keys<<<(unsigned)((npq + 255) / 256), 256, 0, st>>>(p->x64, p->nq, npq, d, g->lo[0],
+                                                                 g->lo[1], g->lo[2], inv_h, g->G, kq);
+    k_morton_keys<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(p->y64, p->n, npt, d, g->lo[0],
+                                                                 g->lo[1], g->lo[2], inv_h, g->G, kt);
+    if ((e = sort_keys(kq, npq, st))) return e;
+    if ((e = sort_keys(kt, npt, st))) return e;
+
+#define ALLOC(ptr, count) \
+    if ((e = cudaMalloc(&(ptr), (size_t)(count) * sizeof(*(ptr))))) return e
+    ALLOC(g->perm_q, g->nqt);
+    ALLOC(g->perm_t, g->nt);
+    ALLOC(g->xs, (int64_t)d * g->nqt);
+    ALLOC(g->x64, (int64_t)d * g->nqt);
+    ALLOC(g->mass, g->nqt);
+    ALLOC(g->lm2, g->nqt);
+    ALLOC(g->y64, (int64_t)d * g->nt);
+    ALLOC(g->nu, g->nt);
+    ALLOC(g->lnu, g->nt);
+    ALLOC(g->pbox, (int64_t)g->ptiles * 6);
+    ALLOC(g->tbox, (int64_t)g->ttiles * 6);
+    ALLOC(g->bits_pt, (int64_t)g->ptiles * g->tw);
+    ALLOC(g->bits_tp, (int64_t)g->ttiles * g->pw);
+    ALLOC(g->cnt1, g->ptiles);
+    ALLOC(g->cnt2, g->ttiles);
+    ALLOC(g->off1, g->ptiles + 1);
+    ALLOC(g->off2, g->ttiles + 1);
+    ALLOC(g->counters, 4);
+    ALLOC(g->Aq, g->nqt);
+    ALLOC(g->tdup, g->nt);
+    ALLOC(g->ppair, g->nqt / 2);
+    ALLOC(g->part1, g->items1_max * PT);
+    ALLOC(g->part2, g->items2_max * TT);
+    ALLOC(g->lse_s, g->nqt);
+    ALLOC(g->blockJ, g->nblk_comb);
+#undef ALLOC
+    k_gather_points<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(
+        kq, p->nq, g->nqt, d, p->x64, p->mass, p->lmass2, g->perm_q, g->xs, g->x64, g->mass, g->lm2);
+    k_gather_targets<<<(unsigned)((g->nt + 255) / 256), 256, 0, st>>>(
+        kt, p->n, g->nt, d, p->y64, p->nu, p->lnu, g->perm_t, g->y64, g->nu, g->lnu);
+    k_tile_boxes<<<(g->ptiles + 127) / 128, 128, 0, st>>>(g->x64, p->nq, d, PT, g->ptiles, g->pbox);
+    k_tile_boxes<<<(g->ttiles + 127) / 128, 128, 0, st>>>(g->y64, p->n, d, TT, g->ttiles, g->tbox);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    cudaFree(kq);
+    cudaFree(kt);
+    const void *f1 = d == 3 ? (const void *)k_lse_trunc<3> : (const void *)k_lse_trunc<2>;
+    const void *f2 = d == 3 ? (const void *)k_grad_trunc<3> : (const void *)k_grad_trunc<2>;
+    g->slots1 = p->num_sms * occupancy_of(f1, L_THREADS);
+    g->slots2 = p->num_sms * occupancy_of(f2, G_THREADS);
+    return cudaSuccess;
+}
+
+template <int D>
+static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, double radius,
+                               double *grad) {
+    Grid *g = p->grid;
+    cudaStream_t st = p->stream;
+    const double C = 0.5 * radius * radius;
+    const double k = kLog2e / (2.0 * eps);
+    const float r_test = (float)(radius * (1.0 + 1e-5) + 1e-6);
+    trace_begin(p, "trunc_setup");
+    k_trunc_A<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(g->xs, p->nq, g->nqt, D, (float)k,
+                                                                (float)(k * C), g->Aq);
+    cudaMemsetAsync(g->bits_tp, 0, (size_t)g->ttiles * g->pw * 4, st);
+    cudaMemsetAsync(g->cnt2, 0, (size_t)g->ttiles * 4, st);
+    k_tile_pairs<<<g->ptiles, 256, 0, st>>>(g->pbox, g->tbox, g->ptiles, g->ttiles, g->tw, g->pw,
+                                            r_test * r_test, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2);
+    k_item_offsets<<<1, 64, 0, st>>>(g->cnt1, g->ptiles, g->ch1, g->cnt2, g->ttiles, g->ch2, g->off1,
+                                     g->off2, g->counters);
+    const int nbp = (int)((g->nt + 255) / 256);
+    k_prep_trunc<<<nbp, 256, 0, st>>>(psi, g->perm_t, g->y64, g->lnu, p->n, g->nt, D, eps, g->tdup,
+                                      p->psinu, g->nu, p->flags);
+    trace_end(p);
+    trace_begin(p, "lse_trunc_mixed");
+    k_lse_trunc<D><<<g->slots1, L_THREADS, 0, st>>>(g->xs, g->nqt, g->Aq, g->tdup, g->bits_pt, g->tw,
+                                                    g->off1, g->ptiles, g->ch1, g->counters,
+                                                    g->part1,
+                                                    reinterpret_cast<unsigned long long *>(&p->res_dev->pairs),
+                                                    p->flags);
+    trace_end(p);
+    trace_begin(p, "combine_trunc_mixed");
+    k_combine_trunc<<<g->nblk_comb, 256, 0, st>>>(g->part1, g->off1, p->nq, g->nqt, g->xs, g->x64,
+                                                  g->mass, g->lm2, g->Aq, psi, eps, D, g->ppair,
+                                                  g->lse_s, g->blockJ, p->res_dev);
+    trace_end(p);
+    trace_begin(p, "grad_trunc_mixed");
+    k_grad_trunc<D><<<g->slots2, G_THREADS, 0, st>>>(g->ppair, g->tdup, g->bits_tp, g->pw, g->off2,
+                                                     g->ttiles, g->ch2, g->counters + 1, g->part2,
+                                                     p->flags);
+    trace_end(p);
+    trace_begin(p, "finalize_trunc");
+    k_finalize_grad_trunc<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(g->part2, g->off2, p->n,
+                                                                          g->perm_t, g->nu, grad);
+    k_finalize_J_trunc<<<1, 256, 0, st>>>(g->blockJ, g->nblk_comb, p->psinu, nbp, psi, p->res_dev);
+    trace_end(p);
+    return cudaGetLastError();
+}
+
+cudaError_t trunc_eval(rsot_problem *p, const double *psi, double eps, double radius, int mixed,
+                       double *grad) {
+    if (!mixed) return launch_trunc_fp64(p, psi, eps, 0.5 * radius * radius, grad);
+    if (!p->grid) {
+        cudaError_t e = grid_build(p);
+        if (e) return e;
+    }
+    // the target prep writes one psi.nu partial per 256 sorted targets
+    if ((int64_t)p->nblk_prep * 256 < p->grid->nt) return cudaErrorInvalidValue;
+    return p->d == 3 ? trunc_mixed<3>(p, psi, eps, radius, grad)
+                     : trunc_mixed<2>(p, psi, eps, radius, grad);
+}
+
+cudaError_t trunc_point_L(rsot_problem *p, double *L) {
+    if (p->last_kind == 2) return launch_point_L(p, L);
+    Grid *g = p->grid;
+    k_point_L_trunc<<<(unsigned)((p->nq + 255) / 256), 256, 0, p->stream>>>(
+        g->lse_s, g->perm_q, g->x64, p->nq, p->d, p->last_eps, p->res_dev, L);
+    return cudaGetLastError();
+}
+
+void trunc_free(rsot_problem *p) {
+    Grid *g = p->grid;
+    if (!g) return;
+    void *ptrs[] = {g->perm_q, g->perm_t, g->xs, g->x64, g->mass, g->lm2, g->y64, g->nu, g->lnu,
+                    g->pbox, g->tbox, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2, g->off1, g->off2,
+                    g->counters, g->Aq, g->tdup, g->ppair, g->part1, g->part2, g->lse_s, g->blockJ};
+    for (void *q : ptrs) cudaFree(q);
+    delete g;
+    p->grid = nullptr;
+}
+
 }  // namespace rsot
