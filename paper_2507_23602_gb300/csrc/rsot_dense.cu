@@ -414,7 +414,8 @@ __global__ void k_finalize_J(const double *__restrict__ blockJ, int nbj,
     if (threadIdx.x == 0) {
         const double psic = psi[0];
         res->psic = psic;
-        res->J = mixed ? (psic * msum - hx + eps * kLn2 * sa - sb) : (psic * msum + eps * sa - sb);
+        // mixed: sa = sum_q m_q R_q (log2, translated frame); FP64: sa = sum_q m_q eps L_q
+        res->J = mixed ? (psic * msum - hx + eps * kLn2 * sa - sb) : (sa - sb);
     }
 }
 
@@ -448,9 +449,10 @@ template <int D>
 __global__ void __launch_bounds__(F_THREADS)
     k_lse_fp64(const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
                const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
-               double inv_eps, double cutoff, const double *__restrict__ mass,
-               double *__restrict__ prec64, double *__restrict__ blockJ,
-               double *__restrict__ lse_buf, EvalResult *__restrict__ res) {
+               double inv_eps, double cutoff, const double *__restrict__ psi, double eps,
+               const double *__restrict__ mass, double *__restrict__ prec64,
+               double *__restrict__ blockJ, double *__restrict__ lse_buf,
+               EvalResult *__restrict__ res) {
     __shared__ double sy[F_TS][4];
     __shared__ double sh[32];
     __shared__ unsigned long long s_cnt, s_empty;
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(F_THREADS)
                 const double L = M + log(S);
                 lse_buf[q] = L;
                 if (mass[q] > 0.0) {
-                    contrib = mass[q] * L;
+                    contrib = mass[q] * (psi[0] + eps * L);   // m_q eps L_q
                     u = log(mass[q]) - L;
                 }
             } else {   // empty I_q: skipped by Algorithm 2
@@ -815,8 +817,8 @@ static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps,
     const unsigned nb1 = (unsigned)((p->nq_pad + F_THREADS - 1) / F_THREADS);
     trace_begin(p, "lse_fp64");
     k_lse_fp64<D><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64, p->n,
-                                             1.0 / eps, cutoff, p->mass, p->prec64, p->blockJ,
-                                             p->lse_buf, p->res_dev);
+                                             1.0 / eps, cutoff, psi, eps, p->mass, p->prec64,
+                                             p->blockJ, p->lse_buf, p->res_dev);
     trace_end(p);
     dim3 g2((unsigned)((p->n + F_THREADS - 1) / F_THREADS), (unsigned)p->s2_64);
     trace_begin(p, "grad_fp64");

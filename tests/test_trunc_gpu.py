@@ -1,0 +1,151 @@
+"""Parity of the truncated (cell-list) CUDA path with the oracle's truncated
+evaluation (Algorithm 2 with I_q = {j : c(x_q, y_j) < C}, every j tested).
+
+Tolerances: as for the dense path (mixed: J 1e-5 relative, gradient 1e-6
+absolute per entry; FP64: 1e-10).  Pairs within FP32 rounding of the cutoff
+may be classified differently by the two sides (their terms are bounded by the
+tail), so the pair counts must agree to a few boundary pairs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import truncation
+import rsot_inputs as ri
+
+pytestmark = pytest.mark.gpu
+
+
+def rs():
+    import paper_2507_23602_gb300 as m
+    return m
+
+
+def case(seed, d, nq, n, eps, scale):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (nq, d))
+    m = rng.uniform(0.5, 1.5, nq)
+    m /= m.sum()
+    y = rng.uniform(0, 1, (n, d))
+    nu = rng.uniform(0.5, 1.5, n)
+    nu /= nu.sum()
+    return x, m, y, nu, scale * rng.standard_normal(n), eps
+
+
+def compare(P, x, m, y, nu, psi, eps, radius, precs=(1, 0), allow_empty=False):
+    C = 0.5 * radius * radius
+    Jo, go, po, eo = oracle.dual_grad(x, m, y, nu, psi, eps, cutoff=C)
+    out = {}
+    for prec in precs:
+        J, g, pairs = P.eval(psi, eps, radius, prec, allow_empty=allow_empty)
+        assert abs(pairs - po) <= 16 + 1e-6 * po, (pairs, po)
+        if prec == 0:
+            assert abs(J - Jo) <= 1e-10 * abs(Jo)
+            assert np.max(np.abs(g - go)) <= 1e-10 * max(np.max(np.abs(go)), np.max(nu))
+        else:
+            assert abs(J - Jo) <= 1e-5 * abs(Jo), (J, Jo)
+            assert np.max(np.abs(g - go)) <= 1e-6
+        out[prec] = (J, g, pairs)
+    return out, (Jo, go, po, eo)
+
+
+@pytest.mark.parametrize("d,nq,n,eps,scale,tail", [
+    (2, 5000, 1500, 0.01, 0.01, 1e-12),
+    (3, 6000, 2000, 0.005, 0.005, 1e-12),
+    (3, 3000, 700, 0.02, 0.02, 1e-4),
+    (2, 2100, 300, 0.002, 0.002, 1e-8),
+])
+def test_trunc_parity_tail_radius(d, nq, n, eps, scale, tail):
+    x, m, y, nu, psi, eps = case(d * 31 + nq, d, nq, n, eps, scale)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        R = P.radius_for_tail(psi, eps, tail)
+        C0 = oracle.covering_cost(x, y)
+        Ro = truncation.radius_of_cutoff(truncation.cutoff_tail(psi, nu, eps, tail, C0))
+        assert abs(R - Ro) <= 1e-6 * Ro
+        res, (Jo, go, po, eo) = compare(P, x, m, y, nu, psi, eps, R)
+        assert eo == 0
+        assert po < x.shape[0] * y.shape[0]      # the radius really truncates
+        # against the dense oracle: within the tail bound (plus FP32 noise)
+        Jd, gd, _, _ = oracle.dual_grad(x, m, y, nu, psi, eps)
+        J64, g64, _ = res[0]
+        assert abs(J64 - Jd) <= eps * tail + 1e-12 * abs(Jd)
+        assert np.all(np.abs(g64 - gd) <= tail * (g64 + 2 * nu) + 1e-13)
+    finally:
+        P.close()
+
+
+def test_trunc_small_radius_reports_empty_points_and_skips_them():
+    x, m, y, nu, psi, eps = case(77, 2, 3000, 200, 0.01, 0.01)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        R = 0.02   # far below the covering radius of 200 targets
+        with pytest.raises(rs().RsotError) as ei:
+            P.eval(psi, eps, R, 1)
+        assert ei.value.status == 4
+        res, (Jo, go, po, eo) = compare(P, x, m, y, nu, psi, eps, R, allow_empty=True)
+        assert eo > 0
+    finally:
+        P.close()
+
+
+def test_trunc_huge_radius_is_dense():
+    x, m, y, nu, psi, eps = case(78, 3, 2000, 500, 0.02, 0.02)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        for prec in (0, 1):
+            Jd, gd, pd = P.eval(psi, eps, 0.0, prec)
+            Jt, gt, pt = P.eval(psi, eps, 10.0, prec)
+            assert Jd == Jt and np.array_equal(gd, gt) and pd == pt == 2000 * 500
+    finally:
+        P.close()
+
+
+def test_trunc_radius_changes_reuse_the_grid_and_repeat_bitwise():
+    x, m, y, nu, psi, eps = case(79, 3, 4100, 1300, 0.01, 0.01)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        for R in (0.35, 0.2, 0.5, 0.2):
+            compare(P, x, m, y, nu, psi, eps, R, precs=(1,))
+        a = P.eval(psi, eps, 0.3, 1)
+        b = P.eval(psi, eps, 0.3, 1)
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
+        L = P.point_log_partition()
+        # L_q of the truncated evaluation: ln of the truncated sum, caller's order
+        Ld = oracle.point_lse(x, y, nu, psi, eps)
+        assert np.all(L <= Ld + 1e-4)
+    finally:
+        P.close()
+
+
+def test_trunc_mixture_workload_reduced_mesh():
+    """Cube workload (mixture targets, random nu) on a 12^3 mesh, eps 1e-3, tail 1e-12."""
+    p = ri.cube_3d(mesh_n=12, n_targets=8192, eps=1e-3)
+    psi = 0.002 * np.random.default_rng(80).standard_normal(p.n)
+    P = rs().Problem(p.x, p.mass, p.y, p.nu)
+    try:
+        R = P.radius_for_tail(psi, p.eps, 1e-12)
+        compare(P, p.x, p.mass, p.y, p.nu, psi, p.eps, R, precs=(1,))
+    finally:
+        P.close()
+
+
+def test_trunc_full_size_against_dense_gpu():
+    """Full cube workload: the truncated evaluation at tail 1e-12 agrees with the
+    dense one within the tail bound plus the mixed-precision tolerance, and its
+    mass balance holds."""
+    p = ri.cube_3d()
+    psi = 0.002 * np.random.default_rng(81).standard_normal(p.n)
+    P = rs().Problem(p.x, p.mass, p.y, p.nu)
+    try:
+        R = P.radius_for_tail(psi, p.eps, 1e-12)
+        Jt, gt, pt = P.eval(psi, p.eps, R, 1)
+        Jd, gd, pd = P.eval(psi, p.eps, 0.0, 1)
+        assert pt < pd
+        assert abs(Jt - Jd) <= 1e-5 * abs(Jd)
+        assert np.max(np.abs(gt - gd)) <= 1e-6
+        assert abs(gt.sum()) <= 5e-7
+    finally:
+        P.close()
