@@ -31,7 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-SFU_EX2_PER_CLK_PER_SM = 16          # MUFU.EX2 results / clock / SM (CUDA throughput table)
+# ex2.approx.f32 results per clock per SM on GB300.  Blackwell-era throughput
+# tables give 16 per SM per clock for the special-function unit; GB300 doubles
+# it: the probe kernel of librsot (rsot_probe_ex2_rate) measures 9.99e12 ex2/s
+# on 152 SMs at ~2.05 GHz, i.e. 32 per SM per clock.  The roofline uses 32.
+SFU_EX2_PER_CLK_PER_SM = 32
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -294,7 +298,7 @@ def main():
     roof = {"bound": "alu", "unit": "Gex2/s", "kernel": dom, "achieved": achieved, "peak": peak,
             "frac": achieved / peak,
             "peak_basis": f"{SFU_EX2_PER_CLK_PER_SM} ex2/clk/SM x {sms} SMs x {sm_max:.0f} MHz "
-                          "(nominal unit count at the maximum SM clock)",
+                          "(unit count measured by the ex2 probe, at the maximum SM clock)",
             "probe_ex2_gps": probe,
             "frac_of_probe": (achieved / probe) if probe else None,
             "traffic": traffic_for(dom, workload),
