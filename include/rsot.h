@@ -153,6 +153,40 @@ int rsot_kernel_times(rsot_problem *p, const char **names, double *total_ms,
  */
 rsot_status rsot_probe_ex2_rate(int iters, double *ex2_per_s);
 
+/*
+ * Allocation-free dense evaluation (no counterpart in the paper: an interface
+ * for callers that must not allocate device memory themselves -- code whose
+ * device memory is owned by another component, such as a framework's caching
+ * allocator, or that runs under a fixed memory budget set at start-up).
+ *
+ * Computes the same J and gradient as rsot_eval_dual_grad with radius 0 and
+ * RSOT_MIXED, without a problem handle and without calling cudaMalloc,
+ * cudaFree or any allocating library routine.  Its scratch is one static
+ * device array of 45 MiB (47,237,632 bytes) inside librsot, which every GPU
+ * that loads the library holds until the process exits.
+ *   d, nq, n     : as rsot_create; nq <= RSOT_NOALLOC_MAX_NQ, n <= RSOT_NOALLOC_MAX_N
+ *                  (larger sizes return RSOT_ERR_ARG without touching the GPU)
+ *   x, mass, y, nu, psi : DEVICE pointers (row-major, as rsot_create / eval);
+ *                  host pointers are rejected with RSOT_ERR_ARG
+ *   eps          : > 0
+ *   stream       : cudaStream_t for all work (NULL = legacy default stream)
+ *   J_out        : HOST pointer, 1 double
+ *   grad_out     : DEVICE pointer, n doubles
+ * The call is synchronous with respect to J_out and grad_out.  The first call
+ * on a device looks up the address of the static scratch on that device (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one scratch array and leaves its contents behind:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.
+ * Errors: RSOT_ERR_ARG, RSOT_ERR_NONFINITE, RSOT_ERR_TIMEOUT, RSOT_ERR_CUDA.
+ */
+#define RSOT_NOALLOC_MAX_NQ 524288
+#define RSOT_NOALLOC_MAX_N 65536
+rsot_status rsot_eval_dense_noalloc(int d, int64_t nq, const double *x, const double *mass,
+                                    int64_t n, const double *y, const double *nu,
+                                    const double *psi, double eps, void *stream,
+                                    double *J_out, double *grad_out);
+
 /* Solver options (Algorithm 1 with the eps-schedule of Sec. 4.2). */
 typedef struct {
     double eps;          /* final regularisation, > 0                              */

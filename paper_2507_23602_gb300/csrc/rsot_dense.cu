@@ -27,6 +27,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "rsot_internal.cuh"
 
@@ -871,7 +872,292 @@ cudaError_t launch_psi_stats(rsot_problem *p, const double *psi, double *out2) {
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// Allocation-free dense evaluation (rsot_eval_dense_noalloc).  The scratch of
+// the mixed-precision dense passes lives in one file-scope device array of a
+// fixed size instead of memory from cudaMalloc, for callers that must not
+// allocate device memory themselves.  Host code reaches the array only
+// through the address cudaGetSymbolAddress returns for the current device.
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NA_MAX_NQ = RSOT_NOALLOC_MAX_NQ;   // multiple of 1024
+constexpr int64_t NA_MAX_N = RSOT_NOALLOC_MAX_N;     // multiple of 1024
+constexpr int NA_MAX_S2 = 16;                        // pass-2 point splits
+constexpr int NA_PTS_BLOCKS = (int)(NA_MAX_NQ / CB_THREADS);
+
+constexpr size_t na_align(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t NA_OFF_RES = 0;
+constexpr size_t NA_OFF_ORIGIN = na_align(NA_OFF_RES + sizeof(EvalResult));
+constexpr size_t NA_OFF_XS = na_align(NA_OFF_ORIGIN + 4 * sizeof(double));
+constexpr size_t NA_OFF_LM2 = na_align(NA_OFF_XS + 3 * NA_MAX_NQ * sizeof(float));
+constexpr size_t NA_OFF_LSE = na_align(NA_OFF_LM2 + NA_MAX_NQ * sizeof(double));
+constexpr size_t NA_OFF_PDUP = na_align(NA_OFF_LSE + NA_MAX_NQ * sizeof(double));
+constexpr size_t NA_OFF_PART1 = na_align(NA_OFF_PDUP + NA_MAX_NQ * sizeof(Rec8));
+constexpr size_t NA_OFF_TDUP = na_align(NA_OFF_PART1 + NA_MAX_NQ * sizeof(float2));
+constexpr size_t NA_OFF_TPAIR = na_align(NA_OFF_TDUP + NA_MAX_N * sizeof(Rec8));
+constexpr size_t NA_OFF_PART2 = na_align(NA_OFF_TPAIR + (NA_MAX_N / 2) * sizeof(Rec8));
+constexpr size_t NA_OFF_BLOCKJ = na_align(NA_OFF_PART2 + (size_t)NA_MAX_S2 * NA_MAX_N * sizeof(double));
+constexpr size_t NA_OFF_PSINU = na_align(NA_OFF_BLOCKJ + (NA_MAX_NQ / CB_THREADS) * sizeof(double));
+constexpr size_t NA_OFF_PTS = na_align(NA_OFF_PSINU + (NA_MAX_N / CB_THREADS) * sizeof(double));
+constexpr size_t NA_BYTES = na_align(NA_OFF_PTS + 2 * NA_PTS_BLOCKS * sizeof(double));
+
+// Shared by every call on a device; holds the last call's contents.
+static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
+
+// bounding-box centre of points and targets (one block)
+__global__ void k_na_origin(const double *__restrict__ x, int64_t nq, const double *__restrict__ y,
+                            int64_t n, int d, double *__restrict__ origin) {
+    __shared__ double slo[3][256], shi[3][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = threadIdx.x; i < nq; i += blockDim.x)
+        for (int k = 0; k < d; ++k) {
+            lo[k] = fmin(lo[k], x[i * d + k]);
+            hi[k] = fmax(hi[k], x[i * d + k]);
+        }
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+        for (int k = 0; k < d; ++k) {
+            lo[k] = fmin(lo[k], y[j * d + k]);
+            hi[k] = fmax(hi[k], y[j * d + k]);
+        }
+    for (int k = 0; k < 3; ++k) {
+        slo[k][threadIdx.x] = lo[k];
+        shi[k][threadIdx.x] = hi[k];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) {
+                slo[k][threadIdx.x] = fmin(slo[k][threadIdx.x], slo[k][threadIdx.x + o]);
+                shi[k][threadIdx.x] = fmax(shi[k][threadIdx.x], shi[k][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) origin[k] = k < d ? 0.5 * (slo[k][0] + shi[k][0]) : 0.0;
+}
+
+// translated FP32 point coordinates (SoA, zero padded), log2 m_q, and block
+// partials of sum m_q and sum m_q |x'_q|^2 / 2
+__global__ void k_na_points(const double *__restrict__ x, const double *__restrict__ mass,
+                            int64_t nq, int64_t nq_pad, int d, const double *__restrict__ origin,
+                            float *__restrict__ xs, double *__restrict__ lm2,
+                            double *__restrict__ pts_part) {
+    __shared__ double sh[32];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0, h = 0.0;
+    if (q < nq_pad) {
+        double r2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            const double v = q < nq ? x[q * d + k] - origin[k] : 0.0;
+            xs[k * nq_pad + q] = (float)v;
+            r2 += v * v;
+        }
+        if (q < nq) {
+            m = mass[q];
+            h = m * 0.5 * r2;
+            lm2[q] = m > 0.0 ? log2(m) : -INFINITY;
+        }
+    }
+    const double sm = block_sum_d(m, sh);
+    const double shh = block_sum_d(h, sh);
+    if (threadIdx.x == 0) {
+        pts_part[2 * blockIdx.x] = sm;
+        pts_part[2 * blockIdx.x + 1] = shh;
+    }
+}
+
+// target records from the caller's raw targets (translated on the fly)
+__global__ void k_na_targets(const double *__restrict__ psi, const double *__restrict__ y,
+                             const double *__restrict__ nu, int64_t n, int64_t n_alloc, int d,
+                             double eps, const double *__restrict__ origin, Rec8 *__restrict__ tdup,
+                             Rec8 *__restrict__ tpair, double *__restrict__ psinu_part,
+                             int *__restrict__ flags) {
+    __shared__ double sh[32];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double psic = psi[0];
+    const double k = kLog2e / (2.0 * eps);
+    double contrib = 0.0;
+    if (j < n_alloc) {
+        float w[3] = {0.f, 0.f, 0.f};
+        float c = kPadC;
+        if (j < n) {
+            const double ps = psi[j];
+            if (!isfinite(ps)) atomicOr(flags, kErrNonfinitePsi);
+            const double b = ((ps - psic) / eps + log(nu[j])) * kLog2e;
+            double yy = 0.0;
+            for (int t = 0; t < d; ++t) {
+                const double yt = y[j * d + t] - origin[t];
+                w[t] = (float)(2.0 * k * yt);
+                yy += yt * yt;
+            }
+            c = (float)(b - k * yy);
+            contrib = ps * nu[j];
+        }
+        Rec8 r;
+        r.a = make_float4(w[0], w[0], w[1], w[1]);
+        r.b = make_float4(w[2], w[2], c, c);
+        tdup[j] = r;
+        float *pr = reinterpret_cast<float *>(tpair + (j >> 1));
+        const int l = (int)(j & 1);
+        pr[0 + l] = w[0];
+        pr[2 + l] = w[1];
+        pr[4 + l] = w[2];
+        pr[6 + l] = c;
+    }
+    const double s = block_sum_d(contrib, sh);
+    if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
+}
+
+// J = psi_c sum m - sum m |x'|^2/2 + eps ln2 sum_q m_q R_q - sum psi nu, to a host-visible result
+__global__ void k_na_finalize_J(const double *__restrict__ blockJ, int nbj,
+                                const double *__restrict__ psinu, int npn,
+                                const double *__restrict__ pts_part, int npts,
+                                const double *__restrict__ psi, double eps,
+                                EvalResult *__restrict__ res) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0, m = 0.0, h = 0.0;
+    for (int i = threadIdx.x; i < nbj; i += blockDim.x) a += blockJ[i];
+    for (int i = threadIdx.x; i < npn; i += blockDim.x) b += psinu[i];
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+        m += pts_part[2 * i];
+        h += pts_part[2 * i + 1];
+    }
+    const double sa = block_sum_d(a, sh), sb = block_sum_d(b, sh);
+    const double smm = block_sum_d(m, sh), shh = block_sum_d(h, sh);
+    if (threadIdx.x == 0) {
+        res->psic = psi[0];
+        res->J = psi[0] * smm - shh + eps * kLn2 * sa - sb;
+    }
+}
+
+template <int D>
+cudaError_t na_launch(unsigned char *base, int64_t nq, const double *x, const double *mass,
+                      int64_t n, const double *y, const double *nu, const double *psi, double eps,
+                      double *grad, cudaStream_t st, int num_sms) {
+    EvalResult *res = reinterpret_cast<EvalResult *>(base + NA_OFF_RES);
+    double *origin = reinterpret_cast<double *>(base + NA_OFF_ORIGIN);
+    float *xs = reinterpret_cast<float *>(base + NA_OFF_XS);
+    double *lm2 = reinterpret_cast<double *>(base + NA_OFF_LM2);
+    double *lse = reinterpret_cast<double *>(base + NA_OFF_LSE);
+    Rec8 *pdup = reinterpret_cast<Rec8 *>(base + NA_OFF_PDUP);
+    float2 *part1 = reinterpret_cast<float2 *>(base + NA_OFF_PART1);
+    Rec8 *tdup = reinterpret_cast<Rec8 *>(base + NA_OFF_TDUP);
+    Rec8 *tpair = reinterpret_cast<Rec8 *>(base + NA_OFF_TPAIR);
+    double *part2 = reinterpret_cast<double *>(base + NA_OFF_PART2);
+    double *blockJ = reinterpret_cast<double *>(base + NA_OFF_BLOCKJ);
+    double *psinu = reinterpret_cast<double *>(base + NA_OFF_PSINU);
+    double *pts = reinterpret_cast<double *>(base + NA_OFF_PTS);
+
+    const int64_t nq_pad = round_up(nq, P1_TILE);
+    const int64_t n_alloc = round_up(n, 1024);
+    const int64_t n_p1 = round_up(n, P1_TS);
+    const int nb_pts = (int)(nq_pad / CB_THREADS);
+    const int nb_prep = (int)(n_alloc / CB_THREADS);
+    cudaError_t e = cudaMemsetAsync(res, 0, sizeof(EvalResult), st);
+    if (e) return e;
+    k_na_origin<<<1, 256, 0, st>>>(x, nq, y, n, D, origin);
+    k_na_points<<<nb_pts, CB_THREADS, 0, st>>>(x, mass, nq, nq_pad, D, origin, xs, lm2, pts);
+    k_na_targets<<<nb_prep, CB_THREADS, 0, st>>>(psi, y, nu, n, n_alloc, D, eps, origin, tdup,
+                                                 tpair, psinu, &res->flags);
+    dim3 g1((unsigned)(nq_pad / P1_TILE), 1u);
+    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(xs, nq_pad, tdup, (int)n_p1, (int)n_p1, part1,
+                                              &res->flags);
+    k_combine<<<nb_pts, CB_THREADS, 0, st>>>(part1, 1, nq_pad, nq, xs, D, lm2, mass, pdup, blockJ,
+                                             lse);
+    const int tpp = pick_tpp(n);
+    const int64_t blk2 = (int64_t)P2_THREADS * 2 * tpp;
+    const int64_t units2 = (n + blk2 - 1) / blk2;
+    const void *f2 = (const void *)k_grad_mixed<D, 4>;
+    int s2 = pick_split(units2, std::min<int64_t>(NA_MAX_S2, nq_pad / P2_TS),
+                        (int64_t)num_sms * occupancy(f2, P2_THREADS, 0));
+    const int64_t chunk2 = round_up((nq_pad + s2 - 1) / s2, P2_TS);
+    s2 = (int)((nq_pad + chunk2 - 1) / chunk2);
+    dim3 g2((unsigned)units2, (unsigned)s2);
+    if (tpp == 4)
+        k_grad_mixed<D, 4><<<g2, P2_THREADS, 0, st>>>(tpair, pdup, nq_pad, chunk2, part2, n_alloc,
+                                                      &res->flags);
+    else if (tpp == 2)
+        k_grad_mixed<D, 2><<<g2, P2_THREADS, 0, st>>>(tpair, pdup, nq_pad, chunk2, part2, n_alloc,
+                                                      &res->flags);
+    else
+        k_grad_mixed<D, 1><<<g2, P2_THREADS, 0, st>>>(tpair, pdup, nq_pad, chunk2, part2, n_alloc,
+                                                      &res->flags);
+    k_finalize_grad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part2, s2, n_alloc, nu, n, grad);
+    k_na_finalize_J<<<1, 256, 0, st>>>(blockJ, nb_pts, psinu, nb_prep, pts, nb_pts, psi, eps, res);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Scratch address of g_na_scratch on the current device, looked up once per
+// device (with that device current) and cached.
+static unsigned char *na_scratch_for_device(int dev) {
+    static std::mutex mu;
+    static unsigned char *addr[256] = {nullptr};
+    if (dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_na_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    return addr[dev];
+}
+
+static bool na_is_device(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+rsot_status eval_dense_noalloc(int d, int64_t nq, const double *x, const double *mass, int64_t n,
+                               const double *y, const double *nu, const double *psi, double eps,
+                               void *stream, double *J_out, double *grad) {
+    if ((d != 2 && d != 3) || nq < 1 || n < 1 || !(eps > 0.0) || !isfinite(eps) || !J_out)
+        return RSOT_ERR_ARG;
+    if (nq > NA_MAX_NQ || n > NA_MAX_N) return RSOT_ERR_ARG;   // beyond the static scratch
+    if (!na_is_device(x) || !na_is_device(mass) || !na_is_device(y) || !na_is_device(nu) ||
+        !na_is_device(psi) || !na_is_device(grad))
+        return RSOT_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    unsigned char *base = na_scratch_for_device(dev);
+    if (!base) return RSOT_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = d == 3 ? na_launch<3>(base, nq, x, mass, n, y, nu, psi, eps, grad, st, sms)
+                           : na_launch<2>(base, nq, x, mass, n, y, nu, psi, eps, grad, st, sms);
+    EvalResult r;
+    if (!e) e = cudaMemcpyAsync(&r, base + NA_OFF_RES, sizeof(r), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    if (r.flags & kErrTimeout) return RSOT_ERR_TIMEOUT;
+    if ((r.flags & kErrNonfinitePsi) || !isfinite(r.J)) return RSOT_ERR_NONFINITE;
+    *J_out = r.J;
+    return RSOT_OK;
+}
+
 }  // namespace rsot
+
+extern "C" rsot_status rsot_eval_dense_noalloc(int d, int64_t nq, const double *x,
+                                               const double *mass, int64_t n, const double *y,
+                                               const double *nu, const double *psi, double eps,
+                                               void *stream, double *J_out, double *grad_out) {
+    return rsot::eval_dense_noalloc(d, nq, x, mass, n, y, nu, psi, eps, stream, J_out, grad_out);
+}
 
 namespace {
 // 8 independent chains x <- ex2(x) / 2 per thread keep x in [1/2, 1].
