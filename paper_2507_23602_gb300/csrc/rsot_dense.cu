@@ -39,8 +39,8 @@ constexpr int P1_PP = 4;                               // point pairs per thread
 constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // 1024 points per CTA
 constexpr int P1_TS = 256;                             // targets per stage
 constexpr int P1_STAGES = 2;
-constexpr int P1_TT = 8;                               // targets per max sub-tile
-constexpr float P1_THR = 32.0f;                        // lazy-rescale threshold (log2)
+constexpr int P1_SUB = 16;                             // targets per optimistic sub-tile
+constexpr float P1_BIG = 1.152921504606846976e18f;     // 2^60: a sub-tile sum above it is redone
 
 constexpr int P2_THREADS = 128;
 constexpr int P2_TS = 256;                             // points per stage
@@ -101,8 +101,52 @@ __global__ void k_prep_mixed(const double *__restrict__ psi, const double *__res
 // ----------------------------------------------------------------------------
 // Pass 1: per-point log-sum-exp over one target chunk (step a2).
 // ----------------------------------------------------------------------------
+// Exact sub-tile for one point pair: maximum of r over the sub-tile, shift M
+// raised to ceil(max) when the maximum exceeds it (rescaling the running sums
+// by an exact power of two), then the sum of 2^(r - M).
 template <int D>
-__global__ void __launch_bounds__(P1_THREADS, 3)
+__device__ __forceinline__ float2 lse_exact_subtile(const Rec8 *T, const float2 (&X)[3], float2 &M,
+                                                    float2 &Sf, double2 &Sd) {
+    float mx = -INFINITY, my = -INFINITY;
+#pragma unroll 4
+    for (int t = 0; t < P1_SUB; ++t) {
+        const float4 a = T[t].a, b = T[t].b;
+        float2 r = make_float2(b.z, b.w);
+        if (D == 3) r = __ffma2_rn(X[2], make_float2(b.x, b.y), r);
+        r = __ffma2_rn(X[1], make_float2(a.z, a.w), r);
+        r = __ffma2_rn(X[0], make_float2(a.x, a.y), r);
+        mx = fmaxf(mx, r.x);
+        my = fmaxf(my, r.y);
+    }
+    if (mx > M.x) {
+        const float mn = ceilf(mx), dl = M.x - mn;
+        Sf.x *= pow2_int_f(dl);
+        Sd.x *= pow2_int_d(dl);
+        M.x = mn;
+    }
+    if (my > M.y) {
+        const float mn = ceilf(my), dl = M.y - mn;
+        Sf.y *= pow2_int_f(dl);
+        Sd.y *= pow2_int_d(dl);
+        M.y = mn;
+    }
+    const float2 nm = make_float2(-M.x, -M.y);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int t = 0; t < P1_SUB; ++t) {
+        const float4 a = T[t].a, b = T[t].b;
+        float2 r = make_float2(b.z, b.w);
+        if (D == 3) r = __ffma2_rn(X[2], make_float2(b.x, b.y), r);
+        r = __ffma2_rn(X[1], make_float2(a.z, a.w), r);
+        r = __ffma2_rn(X[0], make_float2(a.x, a.y), r);
+        const float2 e = __fadd2_rn(r, nm);
+        acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+    }
+    return acc;
+}
+
+template <int D>
+__global__ void __launch_bounds__(P1_THREADS, 4)
     k_lse_mixed(const float *__restrict__ xs, int64_t nq_pad, const Rec8 *__restrict__ tdup,
                 int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags) {
     __shared__ __align__(128) Rec8 sm[P1_STAGES][P1_TS];
@@ -159,57 +203,41 @@ __global__ void __launch_bounds__(P1_THREADS, 3)
         } else {
             const Rec8 *T = sm[s];
 #pragma unroll 1
-            for (int t0 = 0; t0 < P1_TS; t0 += P1_TT) {
-                float2 r[P1_PP][P1_TT];
+            for (int t0 = 0; t0 < P1_TS; t0 += P1_SUB) {
+                // optimistic sub-tile: exponentials against the running shift M
+                float2 acc0[P1_PP], acc1[P1_PP], nm[P1_PP];
 #pragma unroll
-                for (int t = 0; t < P1_TT; ++t) {
+                for (int pp = 0; pp < P1_PP; ++pp) {
+                    acc0[pp] = make_float2(0.f, 0.f);
+                    acc1[pp] = make_float2(0.f, 0.f);
+                    nm[pp] = make_float2(-M[pp].x, -M[pp].y);
+                }
+#pragma unroll
+                for (int t = 0; t < P1_SUB; ++t) {
                     const float4 a = T[t0 + t].a;
                     const float4 b = T[t0 + t].b;
                     const float2 w0 = make_float2(a.x, a.y), w1 = make_float2(a.z, a.w);
                     const float2 w2 = make_float2(b.x, b.y), c = make_float2(b.z, b.w);
 #pragma unroll
                     for (int pp = 0; pp < P1_PP; ++pp) {
-                        float2 acc = c;
-                        if (D == 3) acc = __ffma2_rn(X[pp][2], w2, acc);
-                        acc = __ffma2_rn(X[pp][1], w1, acc);
-                        acc = __ffma2_rn(X[pp][0], w0, acc);
-                        r[pp][t] = acc;
+                        float2 r = c;
+                        if (D == 3) r = __ffma2_rn(X[pp][2], w2, r);
+                        r = __ffma2_rn(X[pp][1], w1, r);
+                        r = __ffma2_rn(X[pp][0], w0, r);
+                        const float2 e = __fadd2_rn(r, nm[pp]);
+                        const float2 v = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                        if (t & 1) acc1[pp] = __fadd2_rn(acc1[pp], v);
+                        else acc0[pp] = __fadd2_rn(acc0[pp], v);
                     }
                 }
 #pragma unroll
                 for (int pp = 0; pp < P1_PP; ++pp) {
-                    float mx = r[pp][0].x, my = r[pp][0].y;
-#pragma unroll
-                    for (int t = 1; t + 1 < P1_TT; t += 2) {
-                        mx = max3f(mx, r[pp][t].x, r[pp][t + 1].x);
-                        my = max3f(my, r[pp][t].y, r[pp][t + 1].y);
-                    }
-                    if ((P1_TT & 1) == 0) {
-                        mx = fmaxf(mx, r[pp][P1_TT - 1].x);
-                        my = fmaxf(my, r[pp][P1_TT - 1].y);
-                    }
-                    if (mx > M[pp].x + P1_THR) {
-                        const float mn = ceilf(mx);
-                        const float dlt = M[pp].x - mn;
-                        Sf[pp].x *= pow2_int_f(dlt);
-                        Sd[pp].x *= pow2_int_d(dlt);
-                        M[pp].x = mn;
-                    }
-                    if (my > M[pp].y + P1_THR) {
-                        const float mn = ceilf(my);
-                        const float dlt = M[pp].y - mn;
-                        Sf[pp].y *= pow2_int_f(dlt);
-                        Sd[pp].y *= pow2_int_d(dlt);
-                        M[pp].y = mn;
-                    }
-                    const float2 nm = make_float2(-M[pp].x, -M[pp].y);
-                    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int t = 0; t < P1_TT; ++t) {
-                        const float2 e = __fadd2_rn(r[pp][t], nm);
-                        acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-                    }
-                    Sf[pp] = __fadd2_rn(Sf[pp], acc);
+                    float2 sub = __fadd2_rn(acc0[pp], acc1[pp]);
+                    // a term far above the shift (first sub-tile, or a new maximum):
+                    // redo the sub-tile with its exact maximum, raising M
+                    if (!(fmaxf(sub.x, sub.y) <= P1_BIG))
+                        sub = lse_exact_subtile<D>(T + t0, X[pp], M[pp], Sf[pp], Sd[pp]);
+                    Sf[pp] = __fadd2_rn(Sf[pp], sub);
                 }
             }
         }

@@ -19,7 +19,8 @@
 //
 // Mixed precision uses the log2-domain quantities of the dense path
 // (rsot_dense.cu): r_qj = c_j + x'_q.w_j, and the truncation test
-//   k |x'_q - y'_j|^2 < k C   <=>   r_qj - b_j > k |x'_q|^2 - k C  (=: A_q).
+// c < C with c = |x'_q - y'_j|^2 / 2 and C = R^2 / 2:
+//   k |x'_q - y'_j|^2 < k R^2   <=>   r_qj - b_j > k |x'_q|^2 - k R^2  (=: A_q).
 // The FP64 truncated evaluation reuses the dense FP64 kernels with the
 // predicate (rsot_dense.cu).
 #include <math.h>
@@ -203,9 +204,9 @@ __global__ void k_tile_boxes(const double *__restrict__ c64s, int64_t cnt, int d
 }
 
 // ------------------------------------------------------------- per evaluation
-// A_q = k |x'_q|^2 - k C (FP32, computed once so that both passes agree)
+// A_q = k |x'_q|^2 - k R^2 (FP32, computed once so that both passes agree)
 __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt, int d, float k,
-                          float kC, float *__restrict__ Aq) {
+                          float kR2, float *__restrict__ Aq) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nqt) return;
     if (s >= nq) {
@@ -217,7 +218,7 @@ __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt,
         const float v = xs[t * nqt + s];
         r2 = fmaf(v, v, r2);
     }
-    Aq[s] = fmaf(k, r2, -kC);
+    Aq[s] = fmaf(k, r2, -kR2);
 }
 
 __device__ __forceinline__ float box_dist2(const float *a, const float *b) {
@@ -862,12 +863,12 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
                                double *grad) {
     Grid *g = p->grid;
     cudaStream_t st = p->stream;
-    const double C = 0.5 * radius * radius;
+    // c(x,y) = |x-y|^2/2 < C = radius^2/2  <=>  k |x'-y'|^2 < k radius^2
     const double k = kLog2e / (2.0 * eps);
     const float r_test = (float)(radius * (1.0 + 1e-5) + 1e-6);
     trace_begin(p, "trunc_setup");
     k_trunc_A<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(g->xs, p->nq, g->nqt, D, (float)k,
-                                                                (float)(k * C), g->Aq);
+                                                                (float)(k * radius * radius), g->Aq);
     cudaMemsetAsync(g->bits_tp, 0, (size_t)g->ttiles * g->pw * 4, st);
     cudaMemsetAsync(g->cnt2, 0, (size_t)g->ttiles * 4, st);
     k_tile_pairs<<<g->ptiles, 256, 0, st>>>(g->pbox, g->tbox, g->ptiles, g->ttiles, g->tw, g->pw,
