@@ -231,6 +231,79 @@ typedef struct {
 rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *opt,
                        rsot_solve_stats *stats);
 
+/* ---------------------------------------------------------------------------
+ * Batched problems: many RSOT problems of uneven size evaluated together.
+ * One evaluation round is one CUDA graph: copy the potentials in, one
+ * persistent launch per pass over a work queue of (problem, tile, chunk)
+ * items, copy the gradients and J out.  The batched solver runs one L-BFGS
+ * (Algorithm 1) per problem on the host, in lockstep: every round evaluates
+ * the pending trial point of every unfinished problem.
+ * ------------------------------------------------------------------------- */
+typedef struct rsot_batch rsot_batch;   /* opaque; owns its device memory */
+
+typedef struct {
+    int d;                 /* 2 or 3                                              */
+    int64_t nq;            /* quadrature points                                   */
+    const double *x;       /* nq*d (host or device)                               */
+    const double *mass;    /* nq                                                  */
+    int64_t n;             /* targets                                             */
+    const double *y;       /* n*d                                                 */
+    const double *nu;      /* n                                                   */
+} rsot_problem_desc;
+
+/* Create a batch of `count` problems (inputs copied; buffers may be freed after). */
+rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_batch **out);
+void rsot_batch_destroy(rsot_batch *b);
+rsot_status rsot_batch_set_stream(rsot_batch *b, void *stream);
+
+/* Total number of targets (length of the concatenated psi / gradient vectors). */
+int64_t rsot_batch_total_targets(const rsot_batch *b);
+
+/*
+ * Autotuner (no counterpart in the paper): times one batched evaluation per
+ * candidate work-item size at the given eps (count doubles, host) and psi
+ * (concatenated, host), keeps the fastest, and rebuilds the CUDA graph.
+ * *choice_out (nullable) receives the chosen pairs-per-item exponent.
+ */
+rsot_status rsot_batch_tune(rsot_batch *b, const double *psi_all, const double *eps,
+                            int *choice_out);
+
+/*
+ * One batched dense mixed-precision evaluation (Eq. discretized_functional /
+ * discretized_gradient for every problem).  All arrays are HOST memory:
+ *   psi_all : concatenated potentials (problem order), total_targets doubles
+ *   eps     : count doubles;  active: count bytes (NULL = all), 0 = skip problem
+ *   J_out   : count doubles;  grad_all: total_targets doubles
+ * Skipped problems' outputs are left untouched.
+ */
+rsot_status rsot_batch_eval(rsot_batch *b, const double *psi_all, const double *eps,
+                            const unsigned char *active, double *J_out, double *grad_all);
+
+/* Per-batch solve statistics. */
+typedef struct {
+    double seconds;            /* wall time of the call                               */
+    double seconds_mixed;      /* batched mixed-precision rounds                      */
+    double seconds_refine;     /* FP64 refinement                                     */
+    int rounds;                /* batched evaluation rounds                           */
+    int converged;             /* problems that reached tol_l1                        */
+    double max_grad_l1;        /* largest final ||grad J||_1                          */
+    int64_t evals;             /* evaluations summed over problems                    */
+} rsot_batch_stats;
+
+/*
+ * Solve every problem: per-problem final eps (count doubles, host), the
+ * eps-schedule of `opt` (eps_start/eps_factor; a problem whose final eps is
+ * above eps_start runs only its final stage), tol_l1, lbfgs_m, max_iter.
+ * opt->precision = RSOT_MIXED runs the batched mixed rounds and then, with
+ * refine_fp64, finishes each problem with FP64 evaluations through its own
+ * problem handle; RSOT_FP64 solves each problem in turn with FP64 evaluations
+ * (no batching).  psi_all: host, concatenated warm start in / solution out.
+ * status_out (nullable): count ints; grad_l1_out (nullable): count doubles.
+ */
+rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
+                             const rsot_options *opt, int *status_out, double *grad_l1_out,
+                             rsot_batch_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

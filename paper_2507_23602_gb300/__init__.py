@@ -18,7 +18,7 @@ from typing import Optional
 
 import numpy as np
 
-__all__ = ["load", "lib_path", "RsotError", "Problem", "SolveOptions", "SolveStats",
+__all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "SolveOptions", "SolveStats",
            "FP64", "MIXED", "STATUS", "probe_ex2_rate"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,6 +44,19 @@ class _Options(ctypes.Structure):
                 ("tol_l1", ctypes.c_double), ("stage_tol_l1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
                 ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("nq", ctypes.c_int64), ("x", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("n", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("nu", ctypes.c_void_p)]
+
+
+class _BStats(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("seconds_mixed", ctypes.c_double),
+                ("seconds_refine", ctypes.c_double), ("rounds", ctypes.c_int),
+                ("converged", ctypes.c_int), ("max_grad_l1", ctypes.c_double),
+                ("evals", ctypes.c_int64)]
 
 
 class _Stats(ctypes.Structure):
@@ -117,6 +130,15 @@ def load():
     lib.rsot_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), dp, i64p, ctypes.c_int]
     lib.rsot_kernel_times.restype = ctypes.c_int
     lib.rsot_probe_ex2_rate.argtypes = [ctypes.c_int, dp]
+    lib.rsot_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
+    lib.rsot_batch_destroy.argtypes = [vp]
+    lib.rsot_batch_destroy.restype = None
+    lib.rsot_batch_total_targets.argtypes = [vp]
+    lib.rsot_batch_total_targets.restype = ctypes.c_int64
+    lib.rsot_batch_eval.argtypes = [vp, dp, dp, ctypes.c_char_p, dp, dp]
+    lib.rsot_batch_tune.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int)]
+    lib.rsot_batch_solve.argtypes = [vp, dp, dp, ctypes.POINTER(_Options),
+                                     ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(_BStats)]
     _lib = lib
     return lib
 
@@ -259,4 +281,86 @@ class Problem:
         stats = SolveStats(st, s.J, s.grad_l1, s.iters, s.evals, s.stages, s.pairs, s.seconds)
         if raise_on_error and st != 0:
             raise RsotError(st, "solve")
+        return psi, stats
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Batch:
+    """Many RSOT problems evaluated and solved together.  `problems` is a list of
+    (x, mass, y, nu) tuples (numpy, host).  Potentials and gradients are the
+    concatenation of the problems' vectors in list order."""
+
+    def __init__(self, problems):
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        descs = (_Desc * len(problems))()
+        self.sizes = []
+        for i, (x, m, y, nu) in enumerate(problems):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, m, y, nu)]
+            self._keep.append(arrs)
+            x, m, y, nu = arrs
+            descs[i] = _Desc(x.shape[1], x.shape[0], x.ctypes.data, m.ctypes.data, y.shape[0],
+                             y.ctypes.data, nu.ctypes.data)
+            self.sizes.append(y.shape[0])
+        h = ctypes.c_void_p()
+        _check(lib.rsot_batch_create(len(problems), descs, ctypes.byref(h)), "batch_create")
+        self._keep = None
+        self._h = h
+        self.count = len(problems)
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.total = int(lib.rsot_batch_total_targets(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rsot_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def split(self, v):
+        return [v[self.offsets[i]:self.offsets[i + 1]] for i in range(self.count)]
+
+    def eval(self, psi_all, eps, active=None):
+        psi_all = np.ascontiguousarray(psi_all, dtype=np.float64)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        J = np.full(self.count, np.nan)
+        g = np.full(self.total, np.nan)
+        act = None if active is None else bytes(np.asarray(active, dtype=np.uint8))
+        _check(self._lib.rsot_batch_eval(self._h, _dp(psi_all), _dp(eps), act, _dp(J), _dp(g)),
+               "batch_eval")
+        return J, g
+
+    def tune(self, psi_all, eps):
+        psi_all = np.ascontiguousarray(psi_all, dtype=np.float64)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        c = ctypes.c_int()
+        _check(self._lib.rsot_batch_tune(self._h, _dp(psi_all), _dp(eps), ctypes.byref(c)),
+               "batch_tune")
+        return c.value
+
+    def solve(self, eps, psi0=None, options: Optional[SolveOptions] = None, raise_on_error=True,
+              **kw):
+        opts = options or SolveOptions(**kw)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        psi = np.zeros(self.total) if psi0 is None else np.array(psi0, dtype=np.float64)
+        st = (ctypes.c_int * self.count)()
+        gl1 = np.zeros(self.count)
+        s = _BStats()
+        o = opts._c()
+        rc = self._lib.rsot_batch_solve(self._h, _dp(psi), _dp(eps), ctypes.byref(o), st,
+                                        _dp(gl1), ctypes.byref(s))
+        if raise_on_error and rc != 0:
+            raise RsotError(rc, "batch_solve")
+        stats = {"status": rc, "statuses": list(st), "grad_l1": gl1, "seconds": s.seconds,
+                 "seconds_mixed": s.seconds_mixed, "seconds_refine": s.seconds_refine,
+                 "rounds": s.rounds, "converged": s.converged, "max_grad_l1": s.max_grad_l1,
+                 "evals": s.evals}
         return psi, stats

@@ -30,21 +30,10 @@
 #include <mutex>
 
 #include "rsot_internal.cuh"
+#include "rsot_inner.cuh"
 
 namespace rsot {
 namespace {
-
-constexpr int P1_THREADS = 128;
-constexpr int P1_PP = 4;                               // point pairs per thread
-constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // 1024 points per CTA
-constexpr int P1_TS = 256;                             // targets per stage
-constexpr int P1_STAGES = 2;
-constexpr int P1_SUB = 16;                             // targets per optimistic sub-tile
-constexpr float P1_BIG = 1.152921504606846976e18f;     // 2^60: a sub-tile sum above it is redone
-
-constexpr int P2_THREADS = 128;
-constexpr int P2_TS = 256;                             // points per stage
-constexpr int P2_STAGES = 2;
 
 constexpr int CB_THREADS = 256;                        // combine / prep kernels
 
@@ -101,50 +90,6 @@ __global__ void k_prep_mixed(const double *__restrict__ psi, const double *__res
 // ----------------------------------------------------------------------------
 // Pass 1: per-point log-sum-exp over one target chunk (step a2).
 // ----------------------------------------------------------------------------
-// Exact sub-tile for one point pair: maximum of r over the sub-tile, shift M
-// raised to ceil(max) when the maximum exceeds it (rescaling the running sums
-// by an exact power of two), then the sum of 2^(r - M).
-template <int D>
-__device__ __forceinline__ float2 lse_exact_subtile(const Rec8 *T, const float2 (&X)[3], float2 &M,
-                                                    float2 &Sf, double2 &Sd) {
-    float mx = -INFINITY, my = -INFINITY;
-#pragma unroll 4
-    for (int t = 0; t < P1_SUB; ++t) {
-        const float4 a = T[t].a, b = T[t].b;
-        float2 r = make_float2(b.z, b.w);
-        if (D == 3) r = __ffma2_rn(X[2], make_float2(b.x, b.y), r);
-        r = __ffma2_rn(X[1], make_float2(a.z, a.w), r);
-        r = __ffma2_rn(X[0], make_float2(a.x, a.y), r);
-        mx = fmaxf(mx, r.x);
-        my = fmaxf(my, r.y);
-    }
-    if (mx > M.x) {
-        const float mn = ceilf(mx), dl = M.x - mn;
-        Sf.x *= pow2_int_f(dl);
-        Sd.x *= pow2_int_d(dl);
-        M.x = mn;
-    }
-    if (my > M.y) {
-        const float mn = ceilf(my), dl = M.y - mn;
-        Sf.y *= pow2_int_f(dl);
-        Sd.y *= pow2_int_d(dl);
-        M.y = mn;
-    }
-    const float2 nm = make_float2(-M.x, -M.y);
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int t = 0; t < P1_SUB; ++t) {
-        const float4 a = T[t].a, b = T[t].b;
-        float2 r = make_float2(b.z, b.w);
-        if (D == 3) r = __ffma2_rn(X[2], make_float2(b.x, b.y), r);
-        r = __ffma2_rn(X[1], make_float2(a.z, a.w), r);
-        r = __ffma2_rn(X[0], make_float2(a.x, a.y), r);
-        const float2 e = __fadd2_rn(r, nm);
-        acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-    }
-    return acc;
-}
-
 template <int D>
 __global__ void __launch_bounds__(P1_THREADS, 4)
     k_lse_mixed(const float *__restrict__ xs, int64_t nq_pad, const Rec8 *__restrict__ tdup,
@@ -201,45 +146,7 @@ __global__ void __launch_bounds__(P1_THREADS, 4)
             s_abort[it & 1] = 1;
             atomicOr(flags, kErrTimeout);
         } else {
-            const Rec8 *T = sm[s];
-#pragma unroll 1
-            for (int t0 = 0; t0 < P1_TS; t0 += P1_SUB) {
-                // optimistic sub-tile: exponentials against the running shift M
-                float2 acc0[P1_PP], acc1[P1_PP], nm[P1_PP];
-#pragma unroll
-                for (int pp = 0; pp < P1_PP; ++pp) {
-                    acc0[pp] = make_float2(0.f, 0.f);
-                    acc1[pp] = make_float2(0.f, 0.f);
-                    nm[pp] = make_float2(-M[pp].x, -M[pp].y);
-                }
-#pragma unroll
-                for (int t = 0; t < P1_SUB; ++t) {
-                    const float4 a = T[t0 + t].a;
-                    const float4 b = T[t0 + t].b;
-                    const float2 w0 = make_float2(a.x, a.y), w1 = make_float2(a.z, a.w);
-                    const float2 w2 = make_float2(b.x, b.y), c = make_float2(b.z, b.w);
-#pragma unroll
-                    for (int pp = 0; pp < P1_PP; ++pp) {
-                        float2 r = c;
-                        if (D == 3) r = __ffma2_rn(X[pp][2], w2, r);
-                        r = __ffma2_rn(X[pp][1], w1, r);
-                        r = __ffma2_rn(X[pp][0], w0, r);
-                        const float2 e = __fadd2_rn(r, nm[pp]);
-                        const float2 v = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                        if (t & 1) acc1[pp] = __fadd2_rn(acc1[pp], v);
-                        else acc0[pp] = __fadd2_rn(acc0[pp], v);
-                    }
-                }
-#pragma unroll
-                for (int pp = 0; pp < P1_PP; ++pp) {
-                    float2 sub = __fadd2_rn(acc0[pp], acc1[pp]);
-                    // a term far above the shift (first sub-tile, or a new maximum):
-                    // redo the sub-tile with its exact maximum, raising M
-                    if (!(fmaxf(sub.x, sub.y) <= P1_BIG))
-                        sub = lse_exact_subtile<D>(T + t0, X[pp], M[pp], Sf[pp], Sd[pp]);
-                    Sf[pp] = __fadd2_rn(Sf[pp], sub);
-                }
-            }
+            lse_stage<D, P1_PP>(sm[s], X, M, Sf, Sd);
         }
         __syncthreads();
         aborted = s_abort[it & 1] != 0;
@@ -368,31 +275,7 @@ __global__ void __launch_bounds__(P2_THREADS)
             s_abort[it & 1] = 1;
             atomicOr(flags, kErrTimeout);
         } else {
-            const Rec8 *T = sm[s];
-            float2 acc[TPP];
-#pragma unroll
-            for (int tp = 0; tp < TPP; ++tp) acc[tp] = make_float2(0.f, 0.f);
-#pragma unroll 4
-            for (int i = 0; i < P2_TS; ++i) {
-                const float4 a = T[i].a;
-                const float4 b = T[i].b;
-                const float2 x0 = make_float2(a.x, a.y), x1 = make_float2(a.z, a.w);
-                const float2 x2 = make_float2(b.x, b.y), u = make_float2(b.z, b.w);
-#pragma unroll
-                for (int tp = 0; tp < TPP; ++tp) {
-                    float2 t = C[tp];
-                    if (D == 3) t = __ffma2_rn(x2, W2[tp], t);
-                    t = __ffma2_rn(x1, W1[tp], t);
-                    t = __ffma2_rn(x0, W0[tp], t);
-                    t = __fadd2_rn(t, u);
-                    acc[tp] = __fadd2_rn(acc[tp], make_float2(ex2_approx(t.x), ex2_approx(t.y)));
-                }
-            }
-#pragma unroll
-            for (int tp = 0; tp < TPP; ++tp) {
-                acc64[tp].x += (double)acc[tp].x;
-                acc64[tp].y += (double)acc[tp].y;
-            }
+            grad_stage<D, TPP>(sm[s], W0, W1, W2, C, acc64);
         }
         __syncthreads();
         aborted = s_abort[it & 1] != 0;
