@@ -304,6 +304,78 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                              const rsot_options *opt, int *status_out, double *grad_l1_out,
                              rsot_batch_stats *stats);
 
+/* ---------------------------------------------------------------------------
+ * Multilevel acceleration (Sec. 5).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Weighted k-means of n points (Sec. 5.2: coarse targets are cluster
+ * centroids, coarse weights the summed weights of the cluster).  Seeded
+ * initial centres (a random subset of the points), `iters` Lloyd iterations:
+ * assignment on the GPU (nearest centre in FP32, lowest index on ties),
+ * update on the host in FP64 (deterministic).  The returned centres are the
+ * weighted centroids of the final assignment.
+ *   y: n*d, w: n (host or device); centers_out: k*d, weights_out: k (host);
+ *   assign_out: n (host, nullable).
+ */
+rsot_status rsot_kmeans(int d, int64_t n, const double *y, const double *w, int64_t k, int iters,
+                        uint64_t seed, double *centers_out, double *weights_out,
+                        int64_t *assign_out);
+
+/*
+ * Softmax refinement (Eq. softmax_refinement_formula): from the potential
+ * psi_coarse on the targets of problem p (the coarse level, on p's source
+ * points), the initial potential of the n_fine targets y_fine:
+ *   psi_k = -eps ln sum_q m_q exp(-c(x_q, y_k)/eps) / S_c(x_q),
+ *   S_c(x) = sum_j nu_j exp((psi_j - c(x, y_j))/eps).
+ * Mixed precision (pass 1 of the coarse problem, a pass 2 over the fine
+ * targets, FP64 sums).  psi_coarse, y_fine, psi_fine_out: host or device.
+ */
+rsot_status rsot_softmax_refine(rsot_problem *p, const double *psi_coarse, double eps,
+                                int64_t n_fine, const double *y_fine, double *psi_fine_out);
+
+#define RSOT_MAX_LEVELS 16
+
+typedef struct {
+    int d;
+    int64_t nq;
+    const double *x;      /* nq*d */
+    const double *mass;   /* nq   */
+} rsot_source_level;
+
+typedef struct {
+    int64_t n;
+    const double *y;      /* n*d  */
+    const double *nu;     /* n    */
+} rsot_target_level;
+
+typedef struct {
+    int levels;                          /* L_max + 1                               */
+    int src_level[RSOT_MAX_LEVELS];      /* i_s(l)                                  */
+    int tgt_level[RSOT_MAX_LEVELS];      /* i_t(l)                                  */
+    int transfer[RSOT_MAX_LEVELS];       /* 0 start, 1 injection, 2 softmax refine  */
+    int iters[RSOT_MAX_LEVELS];
+    int evals[RSOT_MAX_LEVELS];
+    double seconds[RSOT_MAX_LEVELS];
+    double grad_l1;                      /* final ||grad J||_1                      */
+    double total_seconds;
+} rsot_multilevel_stats;
+
+/*
+ * Combined multilevel solve (Sec. 5.3): source levels 0..L_mu (coarse to fine)
+ * and target levels 0..L_nu (coarse to fine); at step l = 0..L_max the
+ * problem (T_{i_s(l)}, nu^{i_t(l)}) with i_s = max(0, l - (L_max - L_mu)),
+ * i_t = max(0, l - (L_max - L_nu)) is solved at eps_levels[l] (L_max + 1
+ * values) by rsot_solve with `opt` (its eps-schedule applies to step 0 only);
+ * the potential moves to the next step by softmax refinement when i_t
+ * increases and by injection otherwise.  psi_out: host, n of the finest
+ * target level.
+ */
+rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n_tgt,
+                                  const rsot_target_level *tgt, const double *eps_levels,
+                                  const rsot_options *opt, double *psi_out,
+                                  rsot_multilevel_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

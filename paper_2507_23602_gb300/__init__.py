@@ -59,6 +59,26 @@ class _BStats(ctypes.Structure):
                 ("evals", ctypes.c_int64)]
 
 
+class _SrcLevel(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("nq", ctypes.c_int64), ("x", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p)]
+
+
+class _TgtLevel(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("y", ctypes.c_void_p), ("nu", ctypes.c_void_p)]
+
+
+MAX_LEVELS = 16
+
+
+class _MLStats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("src_level", ctypes.c_int * MAX_LEVELS),
+                ("tgt_level", ctypes.c_int * MAX_LEVELS), ("transfer", ctypes.c_int * MAX_LEVELS),
+                ("iters", ctypes.c_int * MAX_LEVELS), ("evals", ctypes.c_int * MAX_LEVELS),
+                ("seconds", ctypes.c_double * MAX_LEVELS), ("grad_l1", ctypes.c_double),
+                ("total_seconds", ctypes.c_double)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("J", ctypes.c_double), ("grad_l1", ctypes.c_double), ("iters", ctypes.c_int),
                 ("evals", ctypes.c_int), ("stages", ctypes.c_int), ("pairs", ctypes.c_int64),
@@ -130,6 +150,12 @@ def load():
     lib.rsot_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), dp, i64p, ctypes.c_int]
     lib.rsot_kernel_times.restype = ctypes.c_int
     lib.rsot_probe_ex2_rate.argtypes = [ctypes.c_int, dp]
+    lib.rsot_kmeans.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, ctypes.c_int,
+                                ctypes.c_uint64, dp, dp, i64p]
+    lib.rsot_softmax_refine.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, vp, vp]
+    lib.rsot_multilevel_solve.argtypes = [ctypes.c_int, ctypes.POINTER(_SrcLevel), ctypes.c_int,
+                                          ctypes.POINTER(_TgtLevel), dp, ctypes.POINTER(_Options),
+                                          dp, ctypes.POINTER(_MLStats)]
     lib.rsot_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
     lib.rsot_batch_destroy.argtypes = [vp]
     lib.rsot_batch_destroy.restype = None
@@ -243,6 +269,17 @@ class Problem:
             out = np.empty(self.nq)
         po, ko = _ptr(out)
         _check(self._lib.rsot_point_log_partition(self._h, po), "point_log_partition")
+        return out
+
+    def softmax_refine(self, psi_coarse, eps, y_fine):
+        """Initial potential on the targets y_fine from psi_coarse on this
+        problem's targets (Eq. softmax_refinement_formula)."""
+        pc, kc = _ptr(psi_coarse)
+        yf = np.ascontiguousarray(y_fine, dtype=np.float64)
+        out = np.empty(yf.shape[0])
+        _check(self._lib.rsot_softmax_refine(self._h, pc, float(eps), yf.shape[0],
+                                             ctypes.c_void_p(yf.ctypes.data),
+                                             ctypes.c_void_p(out.ctypes.data)), "softmax_refine")
         return out
 
     def kernel_timing(self, enable=True):
@@ -364,3 +401,54 @@ class Batch:
                  "rounds": s.rounds, "converged": s.converged, "max_grad_l1": s.max_grad_l1,
                  "evals": s.evals}
         return psi, stats
+
+
+def kmeans(y, w, k, iters=20, seed=6):
+    """(centres, weights, assignment) of a weighted k-means (GPU assignment)."""
+    lib = load()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    d = y.shape[1]
+    C = np.empty((k, d))
+    W = np.empty(k)
+    a = np.empty(y.shape[0], dtype=np.int64)
+    _check(lib.rsot_kmeans(d, y.shape[0], ctypes.c_void_p(y.ctypes.data), ctypes.c_void_p(w.ctypes.data),
+                           int(k), int(iters), int(seed), _dp(C), _dp(W),
+                           a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "kmeans")
+    return C, W, a
+
+
+def multilevel_solve(sources, targets, eps_levels, options: Optional[SolveOptions] = None,
+                     raise_on_error=True, **kw):
+    """Combined multilevel solve (Sec. 5.3).  sources: list of (x, mass) coarse
+    to fine; targets: list of (y, nu) coarse to fine; eps_levels: L_max + 1."""
+    lib = load()
+    keep = []
+    S = (_SrcLevel * len(sources))()
+    for i, (x, m) in enumerate(sources):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        keep += [x, m]
+        S[i] = _SrcLevel(x.shape[1], x.shape[0], x.ctypes.data, m.ctypes.data)
+    T = (_TgtLevel * len(targets))()
+    for i, (y, nu) in enumerate(targets):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        nu = np.ascontiguousarray(nu, dtype=np.float64)
+        keep += [y, nu]
+        T[i] = _TgtLevel(y.shape[0], y.ctypes.data, nu.ctypes.data)
+    eps = np.ascontiguousarray(eps_levels, dtype=np.float64)
+    opts = options or SolveOptions(**kw)
+    o = opts._c()
+    psi = np.zeros(T[len(targets) - 1].n)
+    st = _MLStats()
+    rc = lib.rsot_multilevel_solve(len(sources), S, len(targets), T, _dp(eps), ctypes.byref(o),
+                                   _dp(psi), ctypes.byref(st))
+    if raise_on_error and rc != 0:
+        raise RsotError(rc, "multilevel_solve")
+    L = st.levels
+    stats = {"status": rc, "levels": L, "src_level": list(st.src_level[:L]),
+             "tgt_level": list(st.tgt_level[:L]), "transfer": list(st.transfer[:L]),
+             "iters": list(st.iters[:L]), "evals": list(st.evals[:L]),
+             "seconds": list(st.seconds[:L]), "grad_l1": st.grad_l1,
+             "total_seconds": st.total_seconds}
+    return psi, stats

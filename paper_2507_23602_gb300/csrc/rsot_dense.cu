@@ -714,6 +714,92 @@ static cudaError_t launch_mixed_d(rsot_problem *p, const double *psi, double eps
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// Softmax refinement (Eq. softmax_refinement_formula): with the coarse
+// problem's pass 1 at psi (R_q, u_q = log2 m_q - R_q), the fine potential is
+//   psi_k = -eps ln sum_q m_q exp(-c(x_q, y_k)/eps) / S_c(x_q)
+//         = psi_c - eps ln sum_q 2^( -k|y'_k|^2 + x'_q.(2k y'_k) + u_q )
+// i.e. a pass 2 over the fine targets with target records of b_k = 0.
+// ----------------------------------------------------------------------------
+__global__ void k_prep_fine(const double *__restrict__ yf, int64_t nf, int64_t nf_alloc, int d,
+                            const double *__restrict__ origin3, double eps, Rec8 *__restrict__ tpair) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nf_alloc) return;
+    const double k = kLog2e / (2.0 * eps);
+    float w[3] = {0.f, 0.f, 0.f};
+    float c = kPadC;
+    if (j < nf) {
+        double yy = 0.0;
+        for (int t = 0; t < d; ++t) {
+            const double yt = yf[j * d + t] - origin3[t];
+            w[t] = (float)(2.0 * k * yt);
+            yy += yt * yt;
+        }
+        c = (float)(-k * yy);
+    }
+    float *pr = reinterpret_cast<float *>(tpair + (j >> 1));
+    const int l = (int)(j & 1);
+    pr[0 + l] = w[0];
+    pr[2 + l] = w[1];
+    pr[4 + l] = w[2];
+    pr[6 + l] = c;
+}
+
+__global__ void k_refine_final(const double *__restrict__ part2, int s2, int64_t stride, int64_t nf,
+                               const double *__restrict__ psi_coarse, double eps,
+                               double *__restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nf) return;
+    double s = 0.0;
+    for (int i = 0; i < s2; ++i) s += part2[(int64_t)i * stride + j];
+    out[j] = psi_coarse[0] - eps * log(s);
+}
+
+template <int D>
+static cudaError_t softmax_refine_d(rsot_problem *p, const double *psi, double eps, int64_t nf,
+                                    const double *yf, double *out) {
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    const int64_t n_p1 = round_up(p->n, P1_TS);
+    k_prep_mixed<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad,
+                                                      p->d, eps, p->tdup, p->tpair, p->psinu,
+                                                      p->flags);
+    dim3 g1((unsigned)(p->nq_pad / P1_TILE), (unsigned)p->k1);
+    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(p->xs, p->nq_pad, p->tdup, (int)n_p1, p->chunk1,
+                                              p->part1, p->flags);
+    k_combine<<<p->nblk_comb, CB_THREADS, 0, st>>>(p->part1, p->k1, p->nq_pad, p->nq, p->xs, p->d,
+                                                   p->lmass2, p->mass, p->pdup, p->blockJ,
+                                                   p->lse_buf);
+    const int64_t nf_alloc = round_up(nf, 1024);
+    const int64_t blocks = nf_alloc / 1024;
+    const void *f2 = (const void *)k_grad_mixed<D, 4>;
+    int s2 = pick_split(blocks, p->nq_pad / P2_TS, (int64_t)p->num_sms * occupancy(f2, P2_THREADS, 0));
+    const int64_t chunk2 = round_up((p->nq_pad + s2 - 1) / s2, P2_TS);
+    s2 = (int)((p->nq_pad + chunk2 - 1) / chunk2);
+    Rec8 *tpf = nullptr;
+    double *part = nullptr, *org = nullptr;
+    if ((e = cudaMallocAsync(&tpf, (nf_alloc / 2) * sizeof(Rec8), st))) return e;
+    if ((e = cudaMallocAsync(&part, (size_t)s2 * nf_alloc * sizeof(double), st))) return e;
+    if ((e = cudaMallocAsync(&org, 3 * sizeof(double), st))) return e;
+    if ((e = cudaMemcpyAsync(org, p->origin, 3 * sizeof(double), cudaMemcpyHostToDevice, st))) return e;
+    k_prep_fine<<<(unsigned)((nf_alloc + 255) / 256), 256, 0, st>>>(yf, nf, nf_alloc, p->d, org, eps, tpf);
+    dim3 g2((unsigned)blocks, (unsigned)s2);
+    k_grad_mixed<D, 4><<<g2, P2_THREADS, 0, st>>>(tpf, p->pdup, p->nq_pad, chunk2, part, nf_alloc,
+                                                  p->flags);
+    k_refine_final<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(part, s2, nf_alloc, nf, psi, eps, out);
+    e = cudaGetLastError();
+    cudaFreeAsync(tpf, st);
+    cudaFreeAsync(part, st);
+    cudaFreeAsync(org, st);
+    return e;
+}
+
+cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double eps, int64_t nf,
+                                  const double *yf_dev, double *out_dev) {
+    return p->d == 3 ? softmax_refine_d<3>(p, psi_dev, eps, nf, yf_dev, out_dev)
+                     : softmax_refine_d<2>(p, psi_dev, eps, nf, yf_dev, out_dev);
+}
+
 cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi, double eps, double *grad) {
     return p->d == 3 ? launch_mixed_d<3>(p, psi, eps, grad) : launch_mixed_d<2>(p, psi, eps, grad);
 }

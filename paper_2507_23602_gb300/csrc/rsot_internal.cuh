@@ -144,6 +144,8 @@ cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi_dev, double eps
 cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev);
 cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out3_dev);
 cudaError_t launch_point_L(rsot_problem *p, double *L_dev);
+cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double eps, int64_t nf,
+                                  const double *yf_dev, double *out_dev);
 
 // ---- truncated path (rsot_trunc.cu) ----------------------------------------
 cudaError_t trunc_eval(rsot_problem *p, const double *psi_dev, double eps, double radius,
