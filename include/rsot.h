@@ -197,10 +197,14 @@ typedef struct {
     double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
     double stage_tol_l1; /* tolerance of the intermediate stages (<=0: tol_l1)      */
     int precision;       /* rsot_precision of the evaluations                       */
-    int refine_fp64;     /* MIXED only: finish the last stage with FP64 evaluations */
+    int refine_fp64;     /* MIXED only: finish the last stage with FP64-corrected
+                            refinement (see rsot_solve)                            */
     int lbfgs_m;         /* L-BFGS memory (<= 0: 10)                                */
     int max_iter;        /* iteration cap per stage (<= 0: 10000)                   */
-    int verbose;         /* print one line per iteration to stderr                 */
+    int verbose;         /* print one line per run to stderr                        */
+    double mixed_tol_l1; /* MIXED + refine_fp64: the mixed phase of the last stage
+                            stops here, FP64-corrected refinement takes over
+                            (<= 0: 1e-5)                                           */
 } rsot_options;
 
 /* Fill *o with the defaults (eps 1e-2, no schedule, dense, tol 1e-6, MIXED with
@@ -313,8 +317,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
  * centroids, coarse weights the summed weights of the cluster).  Seeded
  * initial centres (a random subset of the points), `iters` Lloyd iterations:
  * assignment on the GPU (nearest centre in FP32, lowest index on ties),
- * update on the host in FP64 (deterministic).  The returned centres are the
- * weighted centroids of the final assignment.
+ * update on the host in FP64 (deterministic); a cluster left empty restarts at
+ * the point farthest from its centre.  The returned centres are the weighted
+ * centroids of the final assignment (a cluster still empty after the last
+ * iteration returns weight 0 and its last centre).
  *   y: n*d, w: n (host or device); centers_out: k*d, weights_out: k (host);
  *   assign_out: n (host, nullable).
  */

@@ -43,7 +43,8 @@ class _Options(ctypes.Structure):
                 ("eps_factor", ctypes.c_double), ("tail", ctypes.c_double),
                 ("tol_l1", ctypes.c_double), ("stage_tol_l1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
-                ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("mixed_tol_l1", ctypes.c_double)]
 
 
 class _Desc(ctypes.Structure):
@@ -98,11 +99,13 @@ class SolveOptions:
     lbfgs_m: int = 10
     max_iter: int = 10000
     verbose: bool = False
+    mixed_tol_l1: float = 1e-5
 
     def _c(self):
         return _Options(self.eps, self.eps_start, self.eps_factor, self.tail, self.tol_l1,
                         self.stage_tol_l1, int(self.precision), int(bool(self.refine_fp64)),
-                        int(self.lbfgs_m), int(self.max_iter), int(bool(self.verbose)))
+                        int(self.lbfgs_m), int(self.max_iter), int(bool(self.verbose)),
+                        float(self.mixed_tol_l1))
 
 
 @dataclasses.dataclass

@@ -756,6 +756,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
     const int m = opt->lbfgs_m > 0 ? opt->lbfgs_m : 10;
     const int max_iter = opt->max_iter > 0 ? opt->max_iter : 10000;
     const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : opt->tol_l1;
+    // with FP64 refinement the batched mixed phase stops above the FP32 floor
+    const double final_tol = (opt->precision == RSOT_MIXED && opt->refine_fp64)
+                                 ? std::max(opt->tol_l1, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5)
+                                 : opt->tol_l1;
     std::vector<int> st(P, RSOT_OK);
     std::vector<double> gl1(P, 0.0);
     int rounds = 0;
@@ -784,7 +788,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
         std::vector<int> si(P, 0);
         for (int p = 0; p < P; ++p) {
             const double e = stages[p][0];
-            mc[p].start(xvec(p), stages[p].size() == 1 ? opt->tol_l1 : stage_tol, m, max_iter,
+            mc[p].start(xvec(p), stages[p].size() == 1 ? final_tol : stage_tol, m, max_iter,
                         Dvec(p, e), 1e-6);
             b->eps_h[p] = e;
         }
@@ -815,7 +819,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                         ++si[p];
                         const double e = stages[p][si[p]];
                         const bool fin = si[p] + 1 == (int)stages[p].size();
-                        mc[p].start(mc[p].x(), fin ? opt->tol_l1 : stage_tol, m, max_iter,
+                        mc[p].start(mc[p].x(), fin ? final_tol : stage_tol, m, max_iter,
                                     Dvec(p, e), 1e-6);
                     } else {
                         st[p] = mc[p].status();
@@ -832,8 +836,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                 if (!(st[p] == RSOT_OK || st[p] == RSOT_ERR_LINESEARCH)) continue;
                 rsot_options o = *opt;
                 o.eps = eps[p];
-                o.eps_start = 0.0;
-                o.precision = RSOT_FP64;
+                o.eps_start = 0.0;   // FP64-corrected refinement of the batched result
                 rsot_solve_stats ss;
                 const BProb &Q = b->hp[p];
                 st[p] = rsot_solve(b->handles[p], psi_all + Q.psi_off, &o, &ss);

@@ -140,6 +140,27 @@ rsot_status rsot_kmeans(int d, int64_t n, const double *y, const double *w, int6
         for (int64_t c = 0; c < k; ++c)
             if (W[c] > 0.0)
                 for (int t = 0; t < d; ++t) C[c * 3 + t] = S[c * 3 + t] / W[c];
+        // empty clusters restart at the points farthest from their centres
+        // (largest distance first, lowest index on ties; each point used once)
+        std::vector<int64_t> empty;
+        for (int64_t c = 0; c < k; ++c)
+            if (!(W[c] > 0.0)) empty.push_back(c);
+        if (!empty.empty()) {
+            std::vector<std::pair<double, int64_t>> far(n);
+            for (int64_t i = 0; i < n; ++i) {
+                double r = 0.0;
+                for (int t = 0; t < d; ++t) {
+                    const double v = hy[i * d + t] - o[t] - C[(size_t)a[i] * 3 + t];
+                    r += v * v;
+                }
+                far[i] = {-r, i};
+            }
+            const size_t take = std::min(empty.size(), (size_t)n);
+            std::partial_sort(far.begin(), far.begin() + take, far.end());
+            for (size_t e2 = 0; e2 < take; ++e2)
+                for (int t = 0; t < d; ++t)
+                    C[empty[e2] * 3 + t] = hy[far[e2].second * d + t] - o[t];
+        }
     }
     cudaFree(dx);
     cudaFree(dc);

@@ -15,9 +15,12 @@
 //     tolJ = 1e-13 |J| for FP64, 1e-6 |J| for mixed precision), Hager &
 //     Zhang's approximate Wolfe test sigma d0 <= d <= (2 c1 - 1) d0
 //     replaces sufficient decrease.
-// With MIXED precision and refine_fp64, the last stage switches to FP64
-// evaluations when it converges under mixed precision or when the mixed
-// line search stalls, and finishes there.
+// With MIXED precision and refine_fp64, the last stage runs mixed evaluations
+// down to mixed_tol_l1 (default 1e-5, above the FP32 rounding floor of the
+// gradient), then refines with FP64 corrections: an FP64 and a mixed
+// evaluation at the iterate give the systematic mixed-precision error, and
+// mixed L-BFGS continues on the corrected objective until the FP64 gradient
+// meets tol_l1 (plain FP64 L-BFGS is the fallback after 8 corrections).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -61,6 +64,35 @@ struct Evaluator {
     }
 };
 
+// Mixed-precision evaluation plus a linear correction measured once against
+// FP64 at psi0: J'(psi) = J_m(psi) + dJ + b.(psi - psi0), g'(psi) = g_m(psi) + b,
+// with b = g_64(psi0) - g_m(psi0), dJ = J_64(psi0) - J_m(psi0).  The
+// systematic part of the FP32 rounding (per-target constants) is nearly
+// constant near the minimiser, so J' has FP64 accuracy there and the
+// minimiser of J' is refined by mixed evaluations only.
+struct CorrectedEvaluator {
+    Evaluator &mixed;
+    std::vector<double> b, psi0;
+    double dJ = 0.0;
+    int64_t n;
+    double eps;
+    rsot_precision prec = RSOT_MIXED;
+    int evals = 0;
+
+    rsot_status operator()(const std::vector<double> &psi, double &J, std::vector<double> &g) {
+        rsot_status s = mixed(psi, J, g);
+        ++evals;
+        if (s) return s;
+        double lin = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            g[j] += b[j];
+            lin += b[j] * (psi[j] - psi0[j]);
+        }
+        J += dJ + lin;
+        return RSOT_OK;
+    }
+};
+
 double norm1(const std::vector<double> &a) {
     double s = 0.0;
     for (double v : a) s += fabs(v);
@@ -68,7 +100,8 @@ double norm1(const std::vector<double> &a) {
 }
 
 // Drive one L-BFGS run with GPU evaluations until it stops.
-rsot_status run_machine(Evaluator &ev, rsot::LbfgsMachine &mc, int verbose) {
+template <class Ev>
+rsot_status run_machine(Ev &ev, rsot::LbfgsMachine &mc, int verbose) {
     std::vector<double> g(ev.n);
     double f = 0.0;
     while (mc.wants_eval()) {
@@ -101,6 +134,7 @@ void rsot_default_options(rsot_options *o) {
     o->lbfgs_m = 10;
     o->max_iter = 10000;
     o->verbose = 0;
+    o->mixed_tol_l1 = 1e-5;
 }
 
 rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *opt,
@@ -137,7 +171,10 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         for (int64_t j = 0; j < n; ++j) D[j] = eps / nu[j];
         Evaluator ev{p, n, eps, opt->tail, (rsot_precision)opt->precision};
         rsot::LbfgsMachine mc;
-        mc.start(x, tol, m, max_iter, D, opt->precision == RSOT_FP64 ? 1e-13 : 1e-6);
+        double tol_run = tol;
+        if (last && opt->precision == RSOT_MIXED && opt->refine_fp64)
+            tol_run = std::max(tol, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5);
+        mc.start(x, tol_run, m, max_iter, D, opt->precision == RSOT_FP64 ? 1e-13 : 1e-6);
         ++stages;
         st = run_machine(ev, mc, opt->verbose);
         x = mc.x();
@@ -148,16 +185,47 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         pairs += ev.pairs;
         const bool refine = last && opt->precision == RSOT_MIXED && opt->refine_fp64;
         if (refine && (st == RSOT_OK || st == RSOT_ERR_LINESEARCH)) {
+            // FP64-corrected refinement: one FP64 and one mixed evaluation per
+            // correction, mixed L-BFGS on the corrected objective in between
             Evaluator ev64{p, n, eps, opt->tail, RSOT_FP64};
-            rsot::LbfgsMachine mc64;
-            mc64.start(x, tol, m, max_iter, D, 1e-13);
-            st = run_machine(ev64, mc64, opt->verbose);
-            x = mc64.x();
-            f = mc64.f();
-            g = mc64.g();
-            iters += mc64.iters();
-            evals += ev64.evals;
-            pairs += ev64.pairs;
+            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
+            bool done = false;
+            st = RSOT_OK;
+            for (int corr = 0; corr < 8 && !done; ++corr) {
+                double f64 = 0.0, fm = 0.0;
+                std::vector<double> g64(n), gm(n);
+                if ((st = ev64(x, f64, g64))) break;
+                f = f64;
+                g = g64;
+                if (norm1(g64) <= tol) {
+                    done = true;
+                    break;
+                }
+                if ((st = evm(x, fm, gm))) break;
+                CorrectedEvaluator ce{evm, std::vector<double>(n), x, f64 - fm, n, eps};
+                for (int64_t j = 0; j < n; ++j) ce.b[j] = g64[j] - gm[j];
+                rsot::LbfgsMachine mcc;
+                mcc.start_from(x, f64, g64, 0.5 * tol, m, max_iter, D, 1e-6);
+                rsot_status sc = run_machine(ce, mcc, opt->verbose);
+                if (sc && sc != RSOT_ERR_LINESEARCH && sc != RSOT_ERR_NOT_CONVERGED) {
+                    st = sc;
+                    break;
+                }
+                iters += mcc.iters();
+                x = mcc.x();
+            }
+            if (!done && st == RSOT_OK) {
+                // fall back to FP64 L-BFGS from the corrected iterate
+                rsot::LbfgsMachine mc64;
+                mc64.start(x, tol, m, max_iter, D, 1e-13);
+                st = run_machine(ev64, mc64, opt->verbose);
+                x = mc64.x();
+                f = mc64.f();
+                g = mc64.g();
+                iters += mc64.iters();
+            }
+            evals += ev64.evals + evm.evals;
+            pairs += ev64.pairs + evm.pairs;
         }
         if (st != RSOT_OK && !(st == RSOT_ERR_LINESEARCH && !last)) break;
         st = RSOT_OK;
