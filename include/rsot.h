@@ -382,6 +382,32 @@ rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n
                                   const rsot_options *opt, double *psi_out,
                                   rsot_multilevel_stats *stats);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper): an MLP psi_j ~ f(theta,
+ * y_j) of width W with three SiLU hidden layers and a linear head, BF16
+ * weights/activations in its GEMMs, FP32 accumulation, FP32 master weights,
+ * Adam.  All arrays are FP32, host or device; inputs are rows of in_dim
+ * values.
+ * ------------------------------------------------------------------------- */
+typedef struct rsot_mlp rsot_mlp;
+
+rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out);
+void rsot_mlp_destroy(rsot_mlp *m);
+rsot_status rsot_mlp_set_stream(rsot_mlp *m, void *stream);
+/* parameter block: W1 [W][in_pad], b1 [W], W2 [W][W], b2, W3 [W][W], b3, w4 [W], b4 [1];
+ * in_pad = in_dim rounded up to 32 (padded columns are zero) */
+int64_t rsot_mlp_num_params(const rsot_mlp *m);
+rsot_status rsot_mlp_get_params(rsot_mlp *m, float *out);
+rsot_status rsot_mlp_set_params(rsot_mlp *m, const float *in);
+/* y_out[r] = f(x[r]) for r < rows */
+rsot_status rsot_mlp_forward(rsot_mlp *m, int64_t rows, const float *x, float *y_out);
+/* loss = mean_r (f(x_r) - y_r)^2 / 2 and its gradient (grad_out nullable, num_params floats) */
+rsot_status rsot_mlp_gradients(rsot_mlp *m, int64_t rows, const float *x, const float *y,
+                               float *loss_out, float *grad_out);
+/* one Adam step (beta 0.9 / 0.999) on the loss of (x, y) with learning rate lr */
+rsot_status rsot_mlp_train_step(rsot_mlp *m, int64_t rows, const float *x, const float *y,
+                                float lr, float *loss_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ from typing import Optional
 
 import numpy as np
 
-__all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "SolveOptions", "SolveStats",
+__all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "MLP", "SolveOptions", "SolveStats",
            "FP64", "MIXED", "STATUS", "probe_ex2_rate"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -159,6 +159,18 @@ def load():
     lib.rsot_multilevel_solve.argtypes = [ctypes.c_int, ctypes.POINTER(_SrcLevel), ctypes.c_int,
                                           ctypes.POINTER(_TgtLevel), dp, ctypes.POINTER(_Options),
                                           dp, ctypes.POINTER(_MLStats)]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.rsot_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(vp)]
+    lib.rsot_mlp_destroy.argtypes = [vp]
+    lib.rsot_mlp_destroy.restype = None
+    lib.rsot_mlp_set_stream.argtypes = [vp, vp]
+    lib.rsot_mlp_num_params.argtypes = [vp]
+    lib.rsot_mlp_num_params.restype = ctypes.c_int64
+    lib.rsot_mlp_get_params.argtypes = [vp, vp]
+    lib.rsot_mlp_set_params.argtypes = [vp, vp]
+    lib.rsot_mlp_forward.argtypes = [vp, ctypes.c_int64, vp, vp]
+    lib.rsot_mlp_gradients.argtypes = [vp, ctypes.c_int64, vp, vp, fp, vp]
+    lib.rsot_mlp_train_step.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.c_float, fp]
     lib.rsot_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
     lib.rsot_batch_destroy.argtypes = [vp]
     lib.rsot_batch_destroy.restype = None
@@ -455,3 +467,84 @@ def multilevel_solve(sources, targets, eps_levels, options: Optional[SolveOption
              "seconds": list(st.seconds[:L]), "grad_l1": st.grad_l1,
              "total_seconds": st.total_seconds}
     return psi, stats
+
+
+def _fptr(a):
+    """(pointer, keep) of a float32 numpy array or torch tensor (host or CUDA)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            a = a.to(torch.float32).contiguous()
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+class MLP:
+    """The warm-start network: in_dim -> width (SiLU) x3 -> 1."""
+
+    def __init__(self, in_dim=18, width=256, seed=0, stream=None):
+        lib = load()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        _check(lib.rsot_mlp_create(int(in_dim), int(width), int(seed), ctypes.byref(h)), "mlp_create")
+        self._h = h
+        self.in_dim, self.width = in_dim, width
+        self.n_params = int(lib.rsot_mlp_num_params(h))
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(lib.rsot_mlp_set_stream(h, ctypes.c_void_p(s or 0)), "mlp_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rsot_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self._lib.rsot_mlp_get_params(self._h, ctypes.c_void_p(out.ctypes.data)), "mlp_get")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._lib.rsot_mlp_set_params(self._h, ctypes.c_void_p(p.ctypes.data)), "mlp_set")
+
+    def forward(self, x, out=None):
+        px, kx = _fptr(x)
+        rows = int(x.shape[0])
+        if out is None:
+            out = np.empty(rows, dtype=np.float32)
+        po, ko = _fptr(out)
+        _check(self._lib.rsot_mlp_forward(self._h, rows, px, po), "mlp_forward")
+        return out
+
+    def gradients(self, x, y):
+        px, kx = _fptr(x)
+        py, ky = _fptr(y)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self._lib.rsot_mlp_gradients(self._h, int(x.shape[0]), px, py, ctypes.byref(loss),
+                                            ctypes.c_void_p(g.ctypes.data)), "mlp_gradients")
+        return loss.value, g
+
+    def train_step(self, x, y, lr):
+        px, kx = _fptr(x)
+        py, ky = _fptr(y)
+        loss = ctypes.c_float()
+        _check(self._lib.rsot_mlp_train_step(self._h, int(x.shape[0]), px, py, float(lr),
+                                             ctypes.byref(loss)), "mlp_train_step")
+        return loss.value

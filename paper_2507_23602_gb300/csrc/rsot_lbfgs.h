@@ -15,7 +15,9 @@
 //     function decreases with a negative slope, then sectioning of the bracket
 //     with a safeguarded cubic fit; Hager & Zhang's approximate Wolfe test
 //     (sigma d0 <= d <= (2 c1 - 1) d0) replaces sufficient decrease where J
-//     moves less than its evaluation noise (noise_rel |J|).
+//     moves less than its evaluation noise (noise_rel |J|);
+//   * a failed search first restarts from the scaled gradient (curvature
+//     history dropped, at most 5 times per run), then reports failure.
 #pragma once
 
 #include <math.h>
@@ -44,6 +46,7 @@ class LbfgsMachine {
         hist_.clear();
         iters_ = 0;
         evals_ = 0;
+        restarts_ = 0;
         status_ = RSOT_OK;
         xt_ = x_;
         state_ = kNeedF0;
@@ -164,6 +167,13 @@ class LbfgsMachine {
 
     void finish_search() {
         if (lo_.a > 0.0 && lo_.f < f0_) return accept(lo_);
+        // no acceptable step: drop the curvature history and retry along
+        // -D g (a few times per run) before reporting a failed search
+        if (!hist_.empty() && restarts_ < kMaxRestarts) {
+            ++restarts_;
+            hist_.clear();
+            return next_iteration();
+        }
         status_ = RSOT_ERR_LINESEARCH;
         state_ = kDone;
     }
@@ -246,6 +256,8 @@ class LbfgsMachine {
     }
 
     static constexpr double kC1 = 1e-4, kC2 = 0.9;
+    static constexpr int kMaxRestarts = 5;
+    int restarts_ = 0;
     size_t n_ = 0;
     double tol_ = 0.0, noise_rel_ = 0.0, noise_ = 0.0;
     int m_ = 10, max_iter_ = 10000;

@@ -1,0 +1,543 @@
+// Learned warm start: a small MLP psi_j ~ f(theta, y_j) (density parameters
+// theta in R^16, target coordinates y_j in R^2), trained on potentials that
+// the solver itself produced.  Layers: in -> W (SiLU) -> W (SiLU) -> W (SiLU)
+// -> 1, BF16 weights and activations for the GEMMs, FP32 accumulation, FP32
+// master weights and Adam.
+//
+// GEMM kernel: C[m][n] = sum_k A(m,k) B(n,k) with A(m,k) = A[m*lda+k] or, when
+// transposed, A[k*lda+m] (likewise B); CTA tile 128 x 128 x 32, 8 warps of
+// 64 x 32, warp-level BF16 tensor-core MMA (m16n8k16, FP32 accumulate),
+// operands staged K-contiguous in shared memory (transposed sources are
+// transposed on the way in) and read with ldmatrix.  Epilogues: plain FP32,
+// bias + SiLU (writes the FP32 pre-activation and the BF16 activation), and
+// multiplication by SiLU'(Z) for back-propagation (writes BF16).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "rsot_internal.cuh"
+
+namespace rsot {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int GM = 128, GN = 128, GK = 32, GPAD = 8;   // tile, K step, smem row padding
+constexpr int G_THREADS = 256;
+
+enum { EPI_F32 = 0, EPI_BIAS_SILU = 1, EPI_DSILU = 2 };
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
+                                        const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned &r0, unsigned &r1, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Load a (rows x GK) K-contiguous tile into smem T[rows][GK+GPAD] from either a
+// K-contiguous source (src[r*ld + k]) or an r-contiguous one (src[k*ld + r]).
+template <bool TRANS, int ROWS>
+__device__ __forceinline__ void load_tile(bf16 (*T)[GK + GPAD], const bf16 *__restrict__ src, int ld,
+                                          int r0, int rows_total, int k0, int k_total) {
+    const bf16 zero = __float2bfloat16(0.0f);
+    if (!TRANS) {
+        // ROWS * GK / 8 chunks of 8 elements
+        for (int c = threadIdx.x; c < ROWS * GK / 8; c += G_THREADS) {
+            const int r = c / (GK / 8), kk = (c % (GK / 8)) * 8;
+            const int gr = r0 + r, gk = k0 + kk;
+            if (gr < rows_total && gk + 8 <= k_total) {
+                *reinterpret_cast<uint4 *>(&T[r][kk]) =
+                    *reinterpret_cast<const uint4 *>(src + (int64_t)gr * ld + gk);
+            } else {
+                for (int e = 0; e < 8; ++e)
+                    T[r][kk + e] = (gr < rows_total && gk + e < k_total) ? src[(int64_t)gr * ld + gk + e]
+                                                                       : zero;
+            }
+        }
+    } else {
+        // chunks of 8 consecutive rows at one k
+        for (int c = threadIdx.x; c < ROWS * GK / 8; c += G_THREADS) {
+            const int kk = c / (ROWS / 8), r = (c % (ROWS / 8)) * 8;
+            const int gr = r0 + r, gk = k0 + kk;
+            bf16 v[8];
+            if (gk < k_total && gr + 8 <= rows_total) {
+                *reinterpret_cast<uint4 *>(v) =
+                    *reinterpret_cast<const uint4 *>(src + (int64_t)gk * ld + gr);
+            } else {
+                for (int e = 0; e < 8; ++e)
+                    v[e] = (gk < k_total && gr + e < rows_total) ? src[(int64_t)gk * ld + gr + e] : zero;
+            }
+            for (int e = 0; e < 8; ++e) T[r + e][kk] = v[e];
+        }
+    }
+}
+
+template <bool AT, bool BT, int EPI>
+__global__ void __launch_bounds__(G_THREADS)
+    k_gemm_bf16(int M, int N, int K, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B,
+                int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias,
+                bf16 *__restrict__ H, int ldh, const float *__restrict__ Z, int ldz) {
+    __shared__ __align__(16) bf16 As[GM][GK + GPAD];
+    __shared__ __align__(16) bf16 Bs[GN][GK + GPAD];
+    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;   // 2 x 4 warps of 64 x 32
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        load_tile<AT, GM>(As, A, lda, m0, M, k0, K);
+        load_tile<BT, GN>(Bs, B, ldb, n0, N, k0, K);
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < GK; ks += 16) {
+            unsigned a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = wm + i * 16 + (lane & 15);
+                const int c = ks + (lane >> 4) * 8;
+                ldsm_x4(a[i][0], a[i][1], a[i][2], a[i][3], &As[r][c]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                unsigned b0, b1;
+                const int r = wn + j * 8 + (lane & 7);
+                const int c = ks + ((lane >> 3) & 1) * 8;
+                ldsm_x2(b0, b1, &Bs[r][c]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) mma_bf16(acc[i][j], a[i], b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = m0 + wm + i * 16 + g + h * 8;
+                const int col = n0 + wn + j * 8 + t4 * 2;
+                if (row >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int cc = col + e;
+                    if (cc >= N) continue;
+                    float v = acc[i][j][h * 2 + e];
+                    if (EPI == EPI_F32) {
+                        C[(int64_t)row * ldc + cc] = v;
+                    } else if (EPI == EPI_BIAS_SILU) {
+                        v += bias[cc];
+                        C[(int64_t)row * ldc + cc] = v;                        // pre-activation
+                        H[(int64_t)row * ldh + cc] = __float2bfloat16(silu(v));  // activation
+                    } else {
+                        H[(int64_t)row * ldh + cc] =
+                            __float2bfloat16(v * dsilu(Z[(int64_t)row * ldz + cc]));
+                    }
+                }
+            }
+}
+
+// out[b] = sum_i H3[b][i] w4[i] + b4 (FP32), one warp per row
+__global__ void k_head(const bf16 *__restrict__ H, int width, int64_t rows, const float *__restrict__ w,
+                       const float *__restrict__ b, float *__restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.f;
+    for (int i = lane; i < width; i += 32) s += __bfloat162float(H[r * width + i]) * w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s + b[0];
+}
+
+// d_out = (out - y) / B (loss = mean (out - y)^2 / 2), per-row loss terms;
+// dZ3 = d_out w4 * SiLU'(Z3) (BF16)
+__global__ void k_head_back(const float *__restrict__ out, const float *__restrict__ y, int64_t rows,
+                            int64_t valid, float inv_b, const float *__restrict__ w4,
+                            const float *__restrict__ Z3, int width, float *__restrict__ dout,
+                            bf16 *__restrict__ dZ3, float *__restrict__ loss_terms) {
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float e = r < valid ? out[r] - y[r] : 0.f;
+    const float d = e * inv_b;
+    if (lane == 0) {
+        dout[r] = d;
+        loss_terms[r] = 0.5f * e * e;
+    }
+    for (int i = lane; i < width; i += 32)
+        dZ3[r * width + i] = __float2bfloat16(d * w4[i] * dsilu(Z3[r * width + i]));
+}
+
+// column sums over rows of a BF16 (or FP32 when F) matrix: out[c] = sum_r X[r][c]
+template <typename T>
+__global__ void k_colsum(const T *__restrict__ X, int64_t rows, int cols, float *__restrict__ out) {
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+        if constexpr (sizeof(T) == 2) s += __bfloat162float(X[r * cols + c]);
+        else s += (float)X[r * cols + c];
+    }
+    __shared__ float sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+// dw4[i] = sum_r dout[r] H3[r][i]
+__global__ void k_head_wgrad(const bf16 *__restrict__ H, const float *__restrict__ dout, int64_t rows,
+                             int width, float *__restrict__ dw) {
+    const int i = blockIdx.x;
+    float s = 0.f;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += dout[r] * __bfloat162float(H[r * width + i]);
+    __shared__ float sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dw[i] = sh[0];
+}
+
+__global__ void k_sum(const float *__restrict__ v, int64_t n, float *__restrict__ out) {
+    __shared__ float sh[256];
+    float s = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// Adam on the FP32 master parameters (bias-corrected moments)
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of a weight matrix W[rows][cols] (FP32): row-major and transposed
+__global__ void k_to_bf16(const float *__restrict__ W, int rows, int cols, bf16 *__restrict__ Wb,
+                          bf16 *__restrict__ WbT) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * cols) return;
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    const bf16 v = __float2bfloat16(W[i]);
+    Wb[i] = v;
+    if (WbT) WbT[(int64_t)c * rows + r] = v;
+}
+
+__global__ void k_input_bf16(const float *__restrict__ x, int64_t rows, int in_dim, int in_pad,
+                             bf16 *__restrict__ X0) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * in_pad) return;
+    const int64_t r = i / in_pad;
+    const int c = (int)(i % in_pad);
+    X0[i] = __float2bfloat16(c < in_dim ? x[r * in_dim + c] : 0.f);
+}
+
+template <bool AT, bool BT, int EPI>
+void gemm(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
+          float *C, int ldc, const float *bias, bf16 *H, int ldh, const float *Z, int ldz) {
+    dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
+    k_gemm_bf16<AT, BT, EPI><<<grid, G_THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, H,
+                                                         ldh, Z, ldz);
+}
+
+uint64_t mix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+}  // namespace rsot
+
+using rsot::bf16;
+
+struct rsot_mlp {
+    int in_dim = 0, in_pad = 0, width = 0;
+    int64_t cap = 0;   // rows of the activation buffers
+    cudaStream_t stream = nullptr;
+    // parameter block (FP32): W1 [w][in_pad], b1 [w], W2 [w][w], b2, W3 [w][w], b3, w4 [w], b4 [1]
+    int64_t off[8] = {0}, n_params = 0;
+    float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
+    int64_t step = 0;
+    bf16 *W1b = nullptr, *W1bT = nullptr, *W2b = nullptr, *W2bT = nullptr, *W3b = nullptr, *W3bT = nullptr;
+    // activations
+    bf16 *X0 = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZ = nullptr, *dZ2 = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dH = nullptr, *out = nullptr, *dout = nullptr,
+          *lt = nullptr, *xin = nullptr, *yin = nullptr, *scal = nullptr;
+};
+
+namespace rsot {
+namespace {
+
+cudaError_t mlp_refresh_bf16(rsot_mlp *m) {
+    const int w = m->width;
+    cudaStream_t st = m->stream;
+    k_to_bf16<<<(w * m->in_pad + 255) / 256, 256, 0, st>>>(m->P + m->off[0], w, m->in_pad, m->W1b, m->W1bT);
+    k_to_bf16<<<(w * w + 255) / 256, 256, 0, st>>>(m->P + m->off[2], w, w, m->W2b, m->W2bT);
+    k_to_bf16<<<(w * w + 255) / 256, 256, 0, st>>>(m->P + m->off[4], w, w, m->W3b, m->W3bT);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_reserve(rsot_mlp *m, int64_t rows) {
+    if (rows <= m->cap) return cudaSuccess;
+    const int64_t r = (rows + 127) / 128 * 128;
+    void *ptrs[] = {m->X0, m->H1, m->H2, m->H3, m->dZ, m->dZ2, m->Z1, m->Z2, m->Z3, m->dH,
+                    m->out, m->dout, m->lt, m->xin, m->yin};
+    for (void *q : ptrs) cudaFree(q);
+    const int w = m->width;
+    cudaError_t e = cudaSuccess;
+#define MA(ptr, cnt) \
+    if (!e) e = cudaMalloc(&(ptr), (size_t)(cnt) * sizeof(*(ptr)))
+    MA(m->X0, r * m->in_pad);
+    MA(m->H1, r * w);
+    MA(m->H2, r * w);
+    MA(m->H3, r * w);
+    MA(m->dZ, r * w);
+    MA(m->dZ2, r * w);
+    MA(m->Z1, r * w);
+    MA(m->Z2, r * w);
+    MA(m->Z3, r * w);
+    MA(m->dH, r * w);
+    MA(m->out, r);
+    MA(m->dout, r);
+    MA(m->lt, r);
+    MA(m->xin, r * m->in_dim);
+    MA(m->yin, r);
+#undef MA
+    if (!e) {
+        m->cap = r;
+        cudaMemset(m->X0, 0, r * m->in_pad * sizeof(bf16));
+        cudaMemset(m->xin, 0, r * m->in_dim * sizeof(float));
+        cudaMemset(m->yin, 0, r * sizeof(float));
+    }
+    return e;
+}
+
+// forward on rows (padded to 128) from m->xin; result in m->out
+void mlp_forward(rsot_mlp *m, int64_t rows) {
+    const int w = m->width, R = (int)((rows + 127) / 128 * 128);
+    cudaStream_t st = m->stream;
+    k_input_bf16<<<(unsigned)((R * (int64_t)m->in_pad + 255) / 256), 256, 0, st>>>(m->xin, R, m->in_dim,
+                                                                                 m->in_pad, m->X0);
+    gemm<false, false, EPI_BIAS_SILU>(st, R, w, m->in_pad, m->X0, m->in_pad, m->W1b, m->in_pad, m->Z1,
+                                      w, m->P + m->off[1], m->H1, w, nullptr, 0);
+    gemm<false, false, EPI_BIAS_SILU>(st, R, w, w, m->H1, w, m->W2b, w, m->Z2, w, m->P + m->off[3],
+                                      m->H2, w, nullptr, 0);
+    gemm<false, false, EPI_BIAS_SILU>(st, R, w, w, m->H2, w, m->W3b, w, m->Z3, w, m->P + m->off[5],
+                                      m->H3, w, nullptr, 0);
+    k_head<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->H3, w, R, m->P + m->off[6], m->P + m->off[7], m->out);
+}
+
+// forward + backward: gradients of loss = sum_valid (out - y)^2 / (2 rows) into m->G
+void mlp_backward(rsot_mlp *m, int64_t rows) {
+    const int w = m->width, R = (int)((rows + 127) / 128 * 128);
+    cudaStream_t st = m->stream;
+    mlp_forward(m, rows);
+    float *G = m->G;
+    k_head_back<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
+                                                         m->P + m->off[6], m->Z3, w, m->dout, m->dZ, m->lt);
+    k_head_wgrad<<<w, 256, 0, st>>>(m->H3, m->dout, R, w, G + m->off[6]);
+    k_sum<<<1, 256, 0, st>>>(m->dout, R, G + m->off[7]);
+    // layer 3: dW3 = dZ3^T H2, db3 = colsum dZ3, dZ2 = (dZ3 W3) * SiLU'(Z2)
+    gemm<true, true, EPI_F32>(st, w, w, R, m->dZ, w, m->H2, w, G + m->off[4], w, nullptr, nullptr, 0, nullptr, 0);
+    k_colsum<bf16><<<w, 256, 0, st>>>(m->dZ, R, w, G + m->off[5]);
+    gemm<false, false, EPI_DSILU>(st, R, w, w, m->dZ, w, m->W3bT, w, nullptr, 0, nullptr, m->dZ2, w, m->Z2, w);
+    // layer 2
+    gemm<true, true, EPI_F32>(st, w, w, R, m->dZ2, w, m->H1, w, G + m->off[2], w, nullptr, nullptr, 0, nullptr, 0);
+    k_colsum<bf16><<<w, 256, 0, st>>>(m->dZ2, R, w, G + m->off[3]);
+    gemm<false, false, EPI_DSILU>(st, R, w, w, m->dZ2, w, m->W2bT, w, nullptr, 0, nullptr, m->dZ, w, m->Z1, w);
+    // layer 1: dW1 = dZ1^T X0, db1 = colsum dZ1
+    gemm<true, true, EPI_F32>(st, w, m->in_pad, R, m->dZ, w, m->X0, m->in_pad, G + m->off[0], m->in_pad,
+                              nullptr, nullptr, 0, nullptr, 0);
+    k_colsum<bf16><<<w, 256, 0, st>>>(m->dZ, R, w, G + m->off[1]);
+}
+
+}  // namespace
+}  // namespace rsot
+
+using namespace rsot;
+
+extern "C" {
+
+void rsot_mlp_destroy(rsot_mlp *m) {
+    if (!m) return;
+    void *ptrs[] = {m->P, m->G, m->Mo, m->Vo, m->W1b, m->W1bT, m->W2b, m->W2bT, m->W3b, m->W3bT,
+                    m->X0, m->H1, m->H2, m->H3, m->dZ, m->dZ2, m->Z1, m->Z2, m->Z3, m->dH, m->out,
+                    m->dout, m->lt, m->xin, m->yin, m->scal};
+    for (void *q : ptrs) cudaFree(q);
+    delete m;
+}
+
+rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out) {
+    if (!out || in_dim < 1 || in_dim > 64 || width < 8 || width > 1024 || width % 8) return RSOT_ERR_ARG;
+    rsot_mlp *m = new rsot_mlp();
+    m->in_dim = in_dim;
+    m->in_pad = (in_dim + 31) / 32 * 32;
+    m->width = width;
+    const int w = width;
+    const int64_t sizes[8] = {(int64_t)w * m->in_pad, w, (int64_t)w * w, w, (int64_t)w * w, w, w, 1};
+    for (int i = 0; i < 8; ++i) {
+        m->off[i] = m->n_params;
+        m->n_params += sizes[i];
+    }
+    // initialisation: uniform(-a, a), a = sqrt(6 / fan_in) for the hidden layers (SiLU),
+    // sqrt(3 / fan_in) for the head; zero biases; padded input columns zero
+    std::vector<float> h(m->n_params, 0.f);
+    uint64_t s = seed;
+    auto uni = [&](double a) { return (float)(a * (2.0 * ((mix64(s) >> 11) * (1.0 / 9007199254740992.0)) - 1.0)); };
+    for (int r = 0; r < w; ++r)
+        for (int c = 0; c < in_dim; ++c) h[m->off[0] + (int64_t)r * m->in_pad + c] = uni(sqrt(6.0 / in_dim));
+    for (int64_t i = 0; i < (int64_t)w * w; ++i) h[m->off[2] + i] = uni(sqrt(6.0 / w));
+    for (int64_t i = 0; i < (int64_t)w * w; ++i) h[m->off[4] + i] = uni(sqrt(6.0 / w));
+    for (int i = 0; i < w; ++i) h[m->off[6] + i] = uni(sqrt(3.0 / w));
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMalloc(&m->P, m->n_params * 4);
+    if (!e) e = cudaMalloc(&m->G, m->n_params * 4);
+    if (!e) e = cudaMalloc(&m->Mo, m->n_params * 4);
+    if (!e) e = cudaMalloc(&m->Vo, m->n_params * 4);
+    if (!e) e = cudaMalloc(&m->W1b, (size_t)w * m->in_pad * 2);
+    if (!e) e = cudaMalloc(&m->W1bT, (size_t)w * m->in_pad * 2);
+    if (!e) e = cudaMalloc(&m->W2b, (size_t)w * w * 2);
+    if (!e) e = cudaMalloc(&m->W2bT, (size_t)w * w * 2);
+    if (!e) e = cudaMalloc(&m->W3b, (size_t)w * w * 2);
+    if (!e) e = cudaMalloc(&m->W3bT, (size_t)w * w * 2);
+    if (!e) e = cudaMalloc(&m->scal, 16);
+    if (!e) e = cudaMemcpy(m->P, h.data(), m->n_params * 4, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemset(m->Mo, 0, m->n_params * 4);
+    if (!e) e = cudaMemset(m->Vo, 0, m->n_params * 4);
+    if (!e) e = cudaMemset(m->G, 0, m->n_params * 4);
+    if (!e) e = mlp_refresh_bf16(m);
+    if (!e) e = cudaStreamSynchronize(m->stream);
+    if (e) {
+        cudaGetLastError();
+        rsot_mlp_destroy(m);
+        return RSOT_ERR_CUDA;
+    }
+    *out = m;
+    return RSOT_OK;
+}
+
+int64_t rsot_mlp_num_params(const rsot_mlp *m) { return m ? m->n_params : 0; }
+
+rsot_status rsot_mlp_set_stream(rsot_mlp *m, void *stream) {
+    if (!m) return RSOT_ERR_ARG;
+    m->stream = (cudaStream_t)stream;
+    return RSOT_OK;
+}
+
+rsot_status rsot_mlp_get_params(rsot_mlp *m, float *out) {
+    if (!m || !out) return RSOT_ERR_ARG;
+    return cudaMemcpy(out, m->P, m->n_params * 4, cudaMemcpyDefault) ? RSOT_ERR_CUDA : RSOT_OK;
+}
+
+rsot_status rsot_mlp_set_params(rsot_mlp *m, const float *in) {
+    if (!m || !in) return RSOT_ERR_ARG;
+    if (cudaMemcpy(m->P, in, m->n_params * 4, cudaMemcpyDefault)) return RSOT_ERR_CUDA;
+    mlp_refresh_bf16(m);
+    return cudaStreamSynchronize(m->stream) ? RSOT_ERR_CUDA : RSOT_OK;
+}
+
+rsot_status rsot_mlp_forward(rsot_mlp *m, int64_t rows, const float *x, float *y_out) {
+    if (!m || rows < 1 || !x || !y_out) return RSOT_ERR_ARG;
+    cudaError_t e = mlp_reserve(m, rows);
+    if (!e) e = cudaMemcpyAsync(m->xin, x, (size_t)rows * m->in_dim * 4, cudaMemcpyDefault, m->stream);
+    if (!e) {
+        mlp_forward(m, rows);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(y_out, m->out, (size_t)rows * 4, cudaMemcpyDefault, m->stream);
+    if (!e) e = cudaStreamSynchronize(m->stream);
+    return e ? (cudaGetLastError(), RSOT_ERR_CUDA) : RSOT_OK;
+}
+
+rsot_status rsot_mlp_gradients(rsot_mlp *m, int64_t rows, const float *x, const float *y,
+                               float *loss_out, float *grad_out) {
+    if (!m || rows < 1 || !x || !y) return RSOT_ERR_ARG;
+    cudaError_t e = mlp_reserve(m, rows);
+    const int64_t R = (rows + 127) / 128 * 128;
+    if (!e) e = cudaMemsetAsync(m->xin, 0, (size_t)R * m->in_dim * 4, m->stream);
+    if (!e) e = cudaMemsetAsync(m->yin, 0, (size_t)R * 4, m->stream);
+    if (!e) e = cudaMemcpyAsync(m->xin, x, (size_t)rows * m->in_dim * 4, cudaMemcpyDefault, m->stream);
+    if (!e) e = cudaMemcpyAsync(m->yin, y, (size_t)rows * 4, cudaMemcpyDefault, m->stream);
+    if (!e) {
+        mlp_backward(m, rows);
+        k_sum<<<1, 256, 0, m->stream>>>(m->lt, R, m->scal);
+        e = cudaGetLastError();
+    }
+    float l = 0.f;
+    if (!e) e = cudaMemcpyAsync(&l, m->scal, 4, cudaMemcpyDeviceToHost, m->stream);
+    if (!e && grad_out) e = cudaMemcpyAsync(grad_out, m->G, m->n_params * 4, cudaMemcpyDefault, m->stream);
+    if (!e) e = cudaStreamSynchronize(m->stream);
+    if (e) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    if (loss_out) *loss_out = l / (float)rows;
+    return RSOT_OK;
+}
+
+rsot_status rsot_mlp_train_step(rsot_mlp *m, int64_t rows, const float *x, const float *y, float lr,
+                                float *loss_out) {
+    rsot_status s = rsot_mlp_gradients(m, rows, x, y, loss_out, nullptr);
+    if (s) return s;
+    ++m->step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+    k_adam<<<(unsigned)((m->n_params + 255) / 256), 256, 0, m->stream>>>(m->P, m->G, m->Mo, m->Vo,
+                                                                        m->n_params, lr, b1, b2, 1e-8f,
+                                                                        c1, c2);
+    cudaError_t e = mlp_refresh_bf16(m);
+    if (!e) e = cudaStreamSynchronize(m->stream);
+    return e ? (cudaGetLastError(), RSOT_ERR_CUDA) : RSOT_OK;
+}
+
+}  // extern "C"

@@ -19,8 +19,10 @@
 // down to mixed_tol_l1 (default 1e-5, above the FP32 rounding floor of the
 // gradient), then refines with FP64 corrections: an FP64 and a mixed
 // evaluation at the iterate give the systematic mixed-precision error, and
-// mixed L-BFGS continues on the corrected objective until the FP64 gradient
-// meets tol_l1 (plain FP64 L-BFGS is the fallback after 8 corrections).
+// mixed L-BFGS continues on the corrected objective (at most 200 iterations
+// per correction) until the FP64 gradient meets tol_l1; when a correction no
+// longer halves the FP64 gradient (tol below the mixed noise floor), plain
+// FP64 L-BFGS finishes from the corrected iterate.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -191,21 +193,27 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
             bool done = false;
             st = RSOT_OK;
-            for (int corr = 0; corr < 8 && !done; ++corr) {
+            // each correction runs at most 200 mixed iterations; corrections stop when
+            // the FP64 gradient no longer halves (the mixed random noise floor is near)
+            double last64 = INFINITY;
+            for (int corr = 0; corr < 6 && !done; ++corr) {
                 double f64 = 0.0, fm = 0.0;
                 std::vector<double> g64(n), gm(n);
                 if ((st = ev64(x, f64, g64))) break;
                 f = f64;
                 g = g64;
-                if (norm1(g64) <= tol) {
+                const double n64 = norm1(g64);
+                if (n64 <= tol) {
                     done = true;
                     break;
                 }
+                if (n64 > 0.5 * last64) break;
+                last64 = n64;
                 if ((st = evm(x, fm, gm))) break;
                 CorrectedEvaluator ce{evm, std::vector<double>(n), x, f64 - fm, n, eps};
                 for (int64_t j = 0; j < n; ++j) ce.b[j] = g64[j] - gm[j];
                 rsot::LbfgsMachine mcc;
-                mcc.start_from(x, f64, g64, 0.5 * tol, m, max_iter, D, 1e-6);
+                mcc.start_from(x, f64, g64, 0.5 * tol, m, std::min(max_iter, 200), D, 1e-6);
                 rsot_status sc = run_machine(ce, mcc, opt->verbose);
                 if (sc && sc != RSOT_ERR_LINESEARCH && sc != RSOT_ERR_NOT_CONVERGED) {
                     st = sc;

@@ -317,13 +317,25 @@ def params16(rng) -> np.ndarray:
     return th.reshape(16)
 
 
+_MESH_CACHE = {}
+
+
+def _square_quadrature(mesh_n):
+    """(vertices, cells, x_q, w_q, cell ids, barycentric) of the square mesh, cached."""
+    if mesh_n not in _MESH_CACHE:
+        verts, cells = unit_square_tri_mesh(mesh_n)
+        _MESH_CACHE[mesh_n] = (verts, cells) + quadrature(verts, cells, tri_rule_deg2())
+    return _MESH_CACHE[mesh_n]
+
+
 def warmstart_problem(seed: int, mesh_n: int = 64, n_targets: int = 4096, eps: float = 5e-3):
     """d = 2, 4,096 uniform targets, eps = 5e-3, density from a seeded
     16-parameter vector.  Returns (problem, theta16)."""
     rng = np.random.default_rng(seed)
     theta = params16(rng)
-    verts, cells = unit_square_tri_mesh(mesh_n)
-    x, m = source_measure(verts, cells, tri_rule_deg2(),
-                          mixture_density(mixture_from_params16(theta), verts))
+    verts, cells, xq, wq, cid, lam = _square_quadrature(mesh_n)
+    rho_v = mixture_density(mixture_from_params16(theta), verts)
+    m = wq * np.einsum("qa,qa->q", lam, rho_v[cells[cid]])
+    x, m = xq, m / m.sum()
     y = uniform_targets(n_targets, 2, seed + 100000)
     return Problem(x, m, y, random_nu(n_targets, None), float(eps), f"warm-{seed}"), theta

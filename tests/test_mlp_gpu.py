@@ -1,0 +1,68 @@
+"""The warm-start network's own kernels (BF16 tensor-core GEMMs, FP32
+accumulation) against the FP64 MLP oracle that rounds to bfloat16 where the
+kernels do."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def rs():
+    import paper_2507_23602_gb300 as m
+    return m
+
+
+def setup(in_dim, width, rows, seed):
+    net = rs().MLP(in_dim, width, seed=seed)
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 1, (rows, in_dim)).astype(np.float32)
+    y = rng.normal(0, 1, rows).astype(np.float32)
+    return net, x, y
+
+
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 1000), (18, 256, 4096), (5, 64, 300)])
+def test_forward_matches_oracle(in_dim, width, rows):
+    net, x, y = setup(in_dim, width, rows, 7)
+    try:
+        out = net.forward(x)
+        ref, _ = omlp.forward(net.params(), x.astype(np.float64), in_dim, width)
+        assert np.max(np.abs(out - ref)) <= 5e-3 * np.max(np.abs(ref)) + 1e-4
+    finally:
+        net.close()
+
+
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300)])
+def test_gradients_match_oracle(in_dim, width, rows):
+    net, x, y = setup(in_dim, width, rows, 11)
+    try:
+        loss, g = net.gradients(x, y)
+        lo, go = omlp.loss_and_grad(net.params(), x.astype(np.float64), y.astype(np.float64),
+                                    in_dim, width)
+        assert abs(loss - lo) <= 1e-3 * abs(lo)
+        in_pad = (in_dim + 31) // 32 * 32
+        sizes = [width * in_pad, width, width * width, width, width * width, width, width, 1]
+        o = 0
+        for s in sizes:
+            a, b = g[o:o + s], go[o:o + s]
+            assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, (o, s)
+            o += s
+    finally:
+        net.close()
+
+
+def test_training_reduces_the_loss():
+    net = rs().MLP(2, 64, seed=3)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (4096, 2)).astype(np.float32)
+    y = (np.sin(2 * x[:, 0]) * np.cos(x[:, 1])).astype(np.float32)
+    try:
+        l0, _ = net.gradients(x, y)
+        for _ in range(300):
+            idx = rng.integers(0, 4096, 512)
+            net.train_step(x[idx], y[idx], 3e-3)
+        l1, _ = net.gradients(x, y)
+        assert l1 < 0.05 * l0, (l0, l1)
+    finally:
+        net.close()
