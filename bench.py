@@ -51,6 +51,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-trunc", action="store_true")
+    ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart"],
+                    default="dense",
+                    help="dense: dual+grad throughput (default); the others time solves")
+    ap.add_argument("--problems", type=int, default=32, help="batch: problems (seeds 1000..)")
+    ap.add_argument("--plain-problems", type=int, default=8,
+                    help="batch: problems also solved by the plain FP64 path")
+    ap.add_argument("--train-seeds", type=int, default=10000)
+    ap.add_argument("--eval-seeds", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -193,11 +202,125 @@ def run_reference(args, p, psi, workload):
     }))
 
 
+def solve_line(metric, value, unit, workload, extra, args, higher=False):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": 1,
+           "warmup": 0, "ms_per_step": value * 1e3 if unit == "s" else None,
+           "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": workload}}
+    out.update(extra)
+    print(json.dumps(out))
+
+
+def run_solve_workloads(args):
+    """Solve-time metrics (time to ||grad J||_1 <= tol): mixed (FP64-corrected)
+    against plain FP64, on the GPU."""
+    import numpy as np
+    import torch
+    import rsot_inputs as ri
+    import paper_2507_23602_gb300 as rs
+    torch.cuda.set_device(0)
+    if args.workload == "solve":
+        res = {}
+        p = ri.small_2d()
+        P = rs.Problem(p.x, p.mass, p.y, p.nu)
+        for name, prec in (("fp64", rs.FP64), ("mixed", rs.MIXED)):
+            t = time.perf_counter()
+            _, st = P.solve(eps=p.eps, tol_l1=1e-8, precision=prec, raise_on_error=False)
+            res["small_2d_" + name] = {"seconds": time.perf_counter() - t, "iters": st.iters,
+                                       "evals": st.evals, "grad_l1": st.grad_l1, "status": st.status}
+        P.close()
+        q = ri.cube_3d(mesh_n=args.mesh, n_targets=args.targets, eps=args.eps)
+        Q = rs.Problem(q.x, q.mass, q.y, q.nu)
+        t = time.perf_counter()
+        _, st = Q.solve(eps=q.eps, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, precision=rs.MIXED,
+                        raise_on_error=False, max_iter=20000)
+        mixed_s = time.perf_counter() - t
+        res["cube_mixed"] = {"seconds": mixed_s, "iters": st.iters, "evals": st.evals,
+                             "grad_l1": st.grad_l1, "status": st.status}
+        Q.close()
+        solve_line("solve time to ||grad||_1<=1e-6 (cube, eps 0.1->1e-3, mixed + FP64 correction)",
+                   mixed_s, "s", f"cube-{q.nq}x{q.n}-solve", {"results": res}, args)
+        return
+    if args.workload == "batch":
+        seeds = list(range(1000, 1000 + args.problems))
+        probs = [ri.batch_problem(s) for s in seeds]
+        eps = np.array([p.eps for p in probs])
+        B = rs.Batch([(p.x, p.mass, p.y, p.nu) for p in probs])
+        psi0 = np.zeros(B.total)
+        choice = B.tune(psi0, eps)
+        psi, st = B.solve(eps, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, precision=rs.MIXED,
+                          raise_on_error=False)
+        B.close()
+        k = min(args.plain_problems, len(probs))
+        sub = probs[:k]
+        B2 = rs.Batch([(p.x, p.mass, p.y, p.nu) for p in sub])
+        _, st_m = B2.solve(eps[:k], eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, precision=rs.MIXED,
+                           raise_on_error=False)
+        _, st_p = B2.solve(eps[:k], eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, precision=rs.FP64,
+                           raise_on_error=False)
+        B2.close()
+        pairs = sum(p.nq * p.n for p in probs)
+        clean = lambda s: {k2: (v.tolist() if hasattr(v, "tolist") else v) for k2, v in s.items()
+                           if k2 not in ("grad_l1", "statuses")}
+        solve_line("batched solve time to ||grad||_1<=1e-6 (mixed + FP64 correction)",
+                   st["seconds"], "s", f"batch-{len(probs)}-problems",
+                   {"pairs_per_round_all": pairs, "item_exp": choice, "batch": clean(st),
+                    "subset_problems": k, "subset_mixed_batched": clean(st_m),
+                    "subset_plain_fp64": clean(st_p),
+                    "subset_speedup": st_p["seconds"] / max(st_m["seconds"], 1e-9)}, args)
+        return
+    if args.workload == "multilevel":
+        d = 3
+        mix = ri.random_mixture(3, 5, 3)
+        ns = [9, 18, 35, 70] if args.mesh >= 32 else [4, 8, 16]
+        src = []
+        for n in ns:
+            v, c = ri.unit_cube_tet_mesh(n)
+            src.append(ri.source_measure(v, c, ri.tet_rule_deg2(), ri.mixture_density(mix, v)))
+        ysamp = ri.sample_mixture(ri.random_mixture(3, 4, 6), 1 << 20, 6)
+        wsamp = np.full(1 << 20, 1.0 / (1 << 20))
+        t = time.perf_counter()
+        levels = []
+        for k in (1 << 12, 1 << 14, 1 << 16):
+            C, W, _ = rs.kmeans(ysamp, wsamp, k, iters=10, seed=6)
+            keep = W > 0
+            levels.append((C[keep], W[keep] / W[keep].sum()))
+        t_km = time.perf_counter() - t
+        L = max(len(src), len(levels)) - 1
+        eps_levels = [args.eps * 2 ** (L - l) for l in range(L + 1)]
+        psi, st = rs.multilevel_solve(src, levels, eps_levels, tol_l1=1e-6, eps_start=0.1,
+                                      eps_factor=0.5, precision=rs.MIXED, raise_on_error=False)
+        solve_line("multilevel solve time to ||grad||_1<=1e-6 (combined source/target, Sec. 5.3)",
+                   st["total_seconds"], "s",
+                   f"multilevel-{src[-1][0].shape[0]}pts-{levels[-1][0].shape[0]}tgt",
+                   {"kmeans_seconds": t_km, "stats": st,
+                    "levels_points": [s[0].shape[0] for s in src],
+                    "levels_targets": [t2[0].shape[0] for t2 in levels]}, args)
+        return
+    if args.workload == "warmstart":
+        from paper_2507_23602_gb300 import warmstart as ws
+        X, Y, t_gen = ws.generate(list(range(10000, 10000 + args.train_seeds)))
+        net, hist, t_train = ws.train(X, Y, epochs=args.epochs)
+        res = ws.evaluate(net, list(range(20000, 20000 + args.eval_seeds)))
+        solve_line("warm-started solve time to ||grad||_1<=1e-6 (held-out problems)",
+                   res["warm_seconds"], "s", f"warmstart-{args.eval_seeds}-heldout",
+                   {"plain_seconds": res["plain_seconds"], "results": res,
+                    "train_samples": int(X.shape[0]), "gen_seconds": t_gen,
+                    "train_seconds": t_train, "loss_history": hist,
+                    "speedup": res["plain_seconds"] / max(res["warm_seconds"], 1e-9)}, args)
+        net.close()
+        return
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     import numpy as np
     import rsot_inputs as ri
+    if args.workload != "dense":
+        if rank == 0 and args.impl == "ours":
+            run_solve_workloads(args)
+        return
 
     p = ri.cube_3d(mesh_n=args.mesh, n_targets=args.targets, eps=args.eps)
     psi = 0.005 * np.random.default_rng(2024).standard_normal(p.n)
