@@ -91,7 +91,7 @@ __global__ void k_prep_mixed(const double *__restrict__ psi, const double *__res
 // Pass 1: per-point log-sum-exp over one target chunk (step a2).
 // ----------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(P1_THREADS, 4)
+__global__ void __launch_bounds__(P1_THREADS, P1_MINB)
     k_lse_mixed(const float *__restrict__ xs, int64_t nq_pad, const Rec8 *__restrict__ tdup,
                 int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags) {
     __shared__ __align__(128) Rec8 sm[P1_STAGES][P1_TS];
@@ -226,7 +226,7 @@ __global__ void k_combine(const float2 *__restrict__ part, int k1, int64_t nq_pa
 // Pass 2: per-target sum over one point chunk of m_q p_qj (step a3).
 // ----------------------------------------------------------------------------
 template <int D, int TPP>
-__global__ void __launch_bounds__(P2_THREADS)
+__global__ void __launch_bounds__(P2_THREADS, P2_MINB)
     k_grad_mixed(const Rec8 *__restrict__ tpair, const Rec8 *__restrict__ pdup, int64_t nq_pad,
                  int64_t chunk, double *__restrict__ part2, int64_t stride,
                  int *__restrict__ flags) {
@@ -599,7 +599,7 @@ int occupancy(const void *fn, int threads, size_t dyn_smem) {
 int pick_tpp(int64_t n) {
     // targets per pass-2 CTA = 128 * 2 * TPP; pick the largest TPP that wastes
     // at most 1/8 of the lanes on padding
-    for (int tpp : {4, 2}) {
+    for (int tpp : {P2_TPP_MAX, 2}) {
         const int64_t blk = (int64_t)P2_THREADS * 2 * tpp;
         if (round_up(n, blk) - n <= n / 8) return tpp;
     }

@@ -7,12 +7,31 @@
 
 namespace rsot {
 
+// Tile shapes; the build may override them (-DRSOT_P1_PP=..., etc.) to tune.
+#ifndef RSOT_P1_PP
+#define RSOT_P1_PP 4
+#endif
+#ifndef RSOT_P1_MINB
+#define RSOT_P1_MINB 4
+#endif
+#ifndef RSOT_P1_SUB
+#define RSOT_P1_SUB 16
+#endif
+#ifndef RSOT_P2_MINB
+#define RSOT_P2_MINB 1
+#endif
+#ifndef RSOT_P2_TPP
+#define RSOT_P2_TPP 4
+#endif
 inline constexpr int P1_THREADS = 128;
-inline constexpr int P1_PP = 4;                               // point pairs per thread
-inline constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // 1024 points per CTA
+inline constexpr int P1_PP = RSOT_P1_PP;                      // point pairs per thread (<= 4)
+inline constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // points per CTA (divides 1024)
+inline constexpr int P1_MINB = RSOT_P1_MINB;                  // resident CTAs per SM asked of ptxas
 inline constexpr int P1_TS = 256;                             // targets per stage
 inline constexpr int P1_STAGES = 2;
-inline constexpr int P1_SUB = 16;                             // targets per optimistic sub-tile
+inline constexpr int P1_SUB = RSOT_P1_SUB;                    // targets per optimistic sub-tile
+inline constexpr int P2_MINB = RSOT_P2_MINB;
+inline constexpr int P2_TPP_MAX = RSOT_P2_TPP;                // target pairs per thread (pass 2)
 inline constexpr float P1_BIG = 1.152921504606846976e18f;     // 2^60: a sub-tile sum above it is redone
 
 inline constexpr int P2_THREADS = 128;
