@@ -23,6 +23,12 @@ namespace rsot {
 #ifndef RSOT_P2_TPP
 #define RSOT_P2_TPP 4
 #endif
+// Issue form of the per-pair additions (shift and accumulation):
+//   0: packed FADD2 for both, 1: scalar FADD for both, 2: packed shift,
+//   scalar accumulation.  The dot products always use packed FFMA2.
+#ifndef RSOT_ADD_MODE
+#define RSOT_ADD_MODE 0
+#endif
 inline constexpr int P1_THREADS = 128;
 inline constexpr int P1_PP = RSOT_P1_PP;                      // point pairs per thread (<= 4)
 inline constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // points per CTA (divides 1024)
@@ -38,6 +44,21 @@ inline constexpr int P2_THREADS = 128;
 inline constexpr int P2_TS = 256;                             // points per stage
 inline constexpr int P2_STAGES = 2;
 
+
+__device__ __forceinline__ float2 add_shift(float2 a, float2 b) {
+#if RSOT_ADD_MODE == 1
+    return make_float2(a.x + b.x, a.y + b.y);
+#else
+    return __fadd2_rn(a, b);
+#endif
+}
+__device__ __forceinline__ float2 add_acc(float2 a, float2 b) {
+#if RSOT_ADD_MODE == 0
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
 
 // Exact sub-tile for one point pair: maximum of r over the sub-tile, shift M
 // raised to ceil(max) when the maximum exceeds it (rescaling the running sums
@@ -110,10 +131,10 @@ __device__ __forceinline__ void lse_stage(const Rec8 *__restrict__ T, const floa
                 if (D == 3) r = __ffma2_rn(X[pp][2], w2, r);
                 r = __ffma2_rn(X[pp][1], w1, r);
                 r = __ffma2_rn(X[pp][0], w0, r);
-                const float2 e = __fadd2_rn(r, nm[pp]);
+                const float2 e = add_shift(r, nm[pp]);
                 const float2 v = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                if (t & 1) acc1[pp] = __fadd2_rn(acc1[pp], v);
-                else acc0[pp] = __fadd2_rn(acc0[pp], v);
+                if (t & 1) acc1[pp] = add_acc(acc1[pp], v);
+                else acc0[pp] = add_acc(acc0[pp], v);
             }
         }
 #pragma unroll
@@ -148,8 +169,8 @@ __device__ __forceinline__ void grad_stage(const Rec8 *__restrict__ T, const flo
             if (D == 3) t = __ffma2_rn(x2, W2[tp], t);
             t = __ffma2_rn(x1, W1[tp], t);
             t = __ffma2_rn(x0, W0[tp], t);
-            t = __fadd2_rn(t, u);
-            acc[tp] = __fadd2_rn(acc[tp], make_float2(ex2_approx(t.x), ex2_approx(t.y)));
+            t = add_shift(t, u);
+            acc[tp] = add_acc(acc[tp], make_float2(ex2_approx(t.x), ex2_approx(t.y)));
         }
     }
 #pragma unroll
