@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-trunc", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart"],
                     default="dense",
                     help="dense: dual+grad throughput (default); the others time solves")
@@ -379,6 +380,31 @@ def main():
     value = pairs * args.steps * world / total_s / 1e9
     ms_per_step = 1e3 * total_s / args.steps
 
+    # the same evaluation with the FP32 pair kernels (the tensor-core passes are the
+    # default): reported beside the headline for comparison, not part of it
+    fp32_pairs = None
+    if not args.no_fp32_compare:
+        P.set_pair_kernel(rs.PAIRS_FP32)
+        for _ in range(max(1, args.warmup)):
+            P.eval(psi_d, p.eps, 0.0, rs.MIXED, grad_out=grad_d)
+        P.kernel_timing(True)
+        fms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.eval(psi_d, p.eps, 0.0, rs.MIXED, grad_out=grad_d)
+            b_.record()
+            torch.cuda.synchronize()
+            fms.append(a.elapsed_time(b_))
+        fk = P.kernel_times()
+        P.kernel_timing(False)
+        P.set_pair_kernel(rs.PAIRS_TENSOR)
+        fp32_pairs = {"value": pairs / (sum(fms) / len(fms) * 1e-3) / 1e9, "unit": "G pairs/s",
+                      "ms_per_step": sum(fms) / len(fms),
+                      "per_kernel_ms": {k: v[0] / v[1] for k, v in fk.items()}}
+
     # truncated evaluation at the tail-1e-12 radius (secondary line, same workload)
     trunc = None
     if not args.no_trunc:
@@ -436,7 +462,7 @@ def main():
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     tot_ms, launches = ktimes[dom]
     per_launch_s = tot_ms / launches / 1e3
-    ex2_per_launch = pairs if dom in ("lse_mixed", "grad_mixed") else float("nan")
+    ex2_per_launch = pairs if dom in ("lse_mixed", "grad_mixed", "lse_tc", "grad_tc") else float("nan")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -464,11 +490,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "nq": p.nq, "n": p.n, "eps": p.eps,
                    "pairs_per_step": pairs, "precision": "mixed (f32 pairs, f64 reductions)",
+                   "pair_kernel": "tensor cores (mma.sync f16 head/tail operands, f32 accumulate)",
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "e2e": e2e,
         "truncated": trunc,
+        "fp32_pair_kernels": fp32_pairs,
         "gpu_launches": int(sum(v[1] for v in ktimes.values())),
         "clocks": clk,
         "wall_s_timed_region": wall,

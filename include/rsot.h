@@ -84,6 +84,25 @@ void rsot_destroy(rsot_problem *p);
 rsot_status rsot_set_stream(rsot_problem *p, void *stream);
 
 /*
+ * Instruction form of the pair arithmetic of the mixed dense passes
+ * (Algorithm 2's exponent (psi_j - c(x_q, y_j))/eps + ln nu_j).
+ *   RSOT_PAIRS_TENSOR evaluates the exponent as a 16-term inner product on
+ *     the tensor cores (f16 head/tail operand pairs, f32 accumulation; a
+ *     random error of rms ~2e-5 in log2 units at eps = 1e-3, four times the
+ *     FP32 chain's) and falls back to the FP32 kernels by itself, per
+ *     evaluation, when an operand leaves the f16 range (very small eps,
+ *     very large potentials).  Both passes form bitwise the same exponents.
+ *   RSOT_PAIRS_FP32 always takes the FP32 kernels.
+ *   RSOT_PAIRS_AUTO (the default) takes the tensor cores when
+ *     max_q m_q * max_j nu_j <= 2e-6, where their error keeps every gradient
+ *     entry ten times inside the mixed path's bound, else the FP32 kernels.
+ * Not a paper concept: a choice of kernel.
+ * Errors: RSOT_ERR_ARG (NULL handle or unknown kind).
+ */
+typedef enum { RSOT_PAIRS_FP32 = 0, RSOT_PAIRS_TENSOR = 1, RSOT_PAIRS_AUTO = 2 } rsot_pair_kernel;
+rsot_status rsot_set_pair_kernel(rsot_problem *p, rsot_pair_kernel kind);
+
+/*
  * One evaluation of J(psi) and grad J(psi) -- Algorithm 2.
  *   psi       : n doubles (host or device)
  *   eps       : regularisation, > 0

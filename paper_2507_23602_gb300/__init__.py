@@ -19,13 +19,14 @@ from typing import Optional
 import numpy as np
 
 __all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "MLP", "SolveOptions", "SolveStats",
-           "FP64", "MIXED", "STATUS", "probe_ex2_rate"]
+           "FP64", "MIXED", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librsot.so")
 _lib = None
 
 FP64, MIXED = 0, 1
+PAIRS_FP32, PAIRS_TENSOR, PAIRS_AUTO = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
           4: "empty neighbourhood", 5: "not converged", 6: "line search failed",
           7: "device wait timed out", 8: "out of device memory"}
@@ -141,6 +142,7 @@ def load():
     lib.rsot_destroy.argtypes = [vp]
     lib.rsot_destroy.restype = None
     lib.rsot_set_stream.argtypes = [vp, vp]
+    lib.rsot_set_pair_kernel.argtypes = [vp, ctypes.c_int]
     lib.rsot_eval_dual_grad.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         dp, vp, i64p]
     lib.rsot_covering_cost.argtypes = [vp, dp]
@@ -247,6 +249,10 @@ class Problem:
     def set_stream(self, stream):
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         _check(self._lib.rsot_set_stream(self._h, ctypes.c_void_p(s or 0)), "set_stream")
+
+    def set_pair_kernel(self, kind):
+        """PAIRS_AUTO (default), PAIRS_TENSOR or PAIRS_FP32 for the mixed dense passes."""
+        _check(self._lib.rsot_set_pair_kernel(self._h, int(kind)), "set_pair_kernel")
 
     def close(self):
         if getattr(self, "_h", None):

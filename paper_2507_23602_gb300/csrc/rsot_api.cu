@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "rsot_internal.cuh"
@@ -196,10 +197,19 @@ rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, 
         }
         ms.add(hm[i]);
         hh.add(hm[i] * 0.5 * r2);
+        p->m_max = std::max(p->m_max, hm[i]);
         lm2[i] = hm[i] > 0.0 ? log2(hm[i]) : -INFINITY;
     }
     p->msum = ms.val();
     p->hx = hh.val();
+    // tensor-core operand scale: P x' within [-32, 32] (a power of two, exact)
+    {
+        float xmax = 0.0f;
+        for (size_t i = 0; i < xs.size(); ++i) xmax = std::max(xmax, std::fabs(xs[i]));
+        int ex = 0;
+        if (xmax > 0.0f) std::frexp(xmax, &ex);
+        p->tc_P = std::ldexp(1.0f, 5 - ex);
+    }
     std::vector<double> lnu((size_t)n);
     p->nu_min = INFINITY;
     p->nu_max = 0.0;
@@ -236,6 +246,13 @@ rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, 
 rsot_status rsot_set_stream(rsot_problem *p, void *stream) {
     if (!p) return RSOT_ERR_ARG;
     p->stream = (cudaStream_t)stream;
+    return RSOT_OK;
+}
+
+rsot_status rsot_set_pair_kernel(rsot_problem *p, rsot_pair_kernel kind) {
+    if (!p || (kind != RSOT_PAIRS_FP32 && kind != RSOT_PAIRS_TENSOR && kind != RSOT_PAIRS_AUTO))
+        return RSOT_ERR_ARG;
+    p->pair_kernel = (int)kind;
     return RSOT_OK;
 }
 

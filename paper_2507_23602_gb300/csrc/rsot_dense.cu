@@ -31,6 +31,7 @@
 
 #include "rsot_internal.cuh"
 #include "rsot_inner.cuh"
+#include "rsot_tc.cuh"
 
 namespace rsot {
 namespace {
@@ -50,7 +51,8 @@ __global__ void k_prep_mixed(const double *__restrict__ psi, const double *__res
                              const double *__restrict__ lnu, const double *__restrict__ nu,
                              int64_t n, int64_t n_alloc, int d, double eps,
                              Rec8 *__restrict__ tdup, Rec8 *__restrict__ tpair,
-                             double *__restrict__ psinu_part, int *__restrict__ flags) {
+                             double *__restrict__ psinu_part, int *__restrict__ flags,
+                             Rec16 *__restrict__ trec, double inv_P, int *__restrict__ gate) {
     __shared__ double sh[32];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double psic = psi[0];
@@ -59,19 +61,31 @@ __global__ void k_prep_mixed(const double *__restrict__ psi, const double *__res
     if (j < n_alloc) {
         float w[3] = {0.f, 0.f, 0.f};
         float c = kPadC;
+        float W[3] = {0.f, 0.f, 0.f};   // tensor-core operands: w / P and c
+        float C = -256.0f * TC_RANGE;
         if (j < n) {
             const double ps = psi[j];
             if (!isfinite(ps)) atomicOr(flags, kErrNonfinitePsi);
             const double b = ((ps - psic) / eps + lnu[j]) * kLog2e;
             double yy = 0.0;
+            bool ok = true;
             for (int t = 0; t < d; ++t) {
                 const double yt = y64[j * d + t];
                 w[t] = (float)(2.0 * k * yt);
+                W[t] = (float)(2.0 * k * yt * inv_P);
+                ok = ok && fabsf(W[t]) < TC_RANGE;
                 yy += yt * yt;
             }
-            c = (float)(b - k * yy);
+            const double cc = b - k * yy;
+            c = (float)cc;
+            // c below -256 TC_RANGE only makes the exponent more negative than
+            // -1.5e7 + |X||W| < -1.3e7: clamping it leaves ex2 = 0 unchanged
+            C = (float)fmax(cc, -256.0 * TC_RANGE);
+            ok = ok && C < 256.0f * TC_RANGE;
+            if (!ok && gate) atomicOr(gate, 1);
             contrib = ps * nu[j];
         }
+        if (trec) trec[j] = make_target_rec(W, C);
         Rec8 r;
         r.a = make_float4(w[0], w[0], w[1], w[1]);
         r.b = make_float4(w[2], w[2], c, c);
@@ -93,7 +107,10 @@ __global__ void k_prep_mixed(const double *__restrict__ psi, const double *__res
 template <int D>
 __global__ void __launch_bounds__(P1_THREADS, P1_MINB)
     k_lse_mixed(const float *__restrict__ xs, int64_t nq_pad, const Rec8 *__restrict__ tdup,
-                int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags) {
+                int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags,
+                const int *__restrict__ gate = nullptr, int need = 0) {
+    // as the fallback of the tensor-core pass, run only when the gate asks for it
+    if (gate && !(*gate & need)) return;
     __shared__ __align__(128) Rec8 sm[P1_STAGES][P1_TS];
     __shared__ __align__(8) uint64_t full[P1_STAGES];
     __shared__ int s_abort[2];   // indexed by iteration parity
@@ -189,7 +206,8 @@ __global__ void __launch_bounds__(P1_THREADS, P1_MINB)
 __global__ void k_combine(const float2 *__restrict__ part, int k1, int64_t nq_pad, int64_t nq,
                           const float *__restrict__ xs, int d, const double *__restrict__ lmass2,
                           const double *__restrict__ mass, Rec8 *__restrict__ pdup,
-                          double *__restrict__ blockJ, double *__restrict__ lse_buf) {
+                          double *__restrict__ blockJ, double *__restrict__ lse_buf,
+                          float *__restrict__ pu = nullptr) {
     __shared__ double sh[32];
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double contrib = 0.0;
@@ -217,6 +235,7 @@ __global__ void k_combine(const float2 *__restrict__ part, int k1, int64_t nq_pa
         r.a = make_float4(x[0], x[0], x[1], x[1]);
         r.b = make_float4(x[2], x[2], u, u);
         pdup[q] = r;
+        if (pu) pu[q] = u;   // pass-2 shift of the tensor-core kernel
     }
     const double s = block_sum_d(contrib, sh);
     if (threadIdx.x == 0) blockJ[blockIdx.x] = s;
@@ -229,7 +248,8 @@ template <int D, int TPP>
 __global__ void __launch_bounds__(P2_THREADS, P2_MINB)
     k_grad_mixed(const Rec8 *__restrict__ tpair, const Rec8 *__restrict__ pdup, int64_t nq_pad,
                  int64_t chunk, double *__restrict__ part2, int64_t stride,
-                 int *__restrict__ flags) {
+                 int *__restrict__ flags, const int *__restrict__ gate = nullptr, int need = 0) {
+    if (gate && !(*gate & need)) return;
     __shared__ __align__(128) Rec8 sm[P2_STAGES][P2_TS];
     __shared__ __align__(8) uint64_t full[P2_STAGES];
     __shared__ int s_abort[2];   // indexed by iteration parity
@@ -299,6 +319,375 @@ __global__ void __launch_bounds__(P2_THREADS, P2_MINB)
         const int64_t j = 2 * (g0 + tp * P2_THREADS + tid);
         *reinterpret_cast<double2 *>(part2 + (int64_t)blockIdx.y * stride + j) = acc64[tp];
     }
+}
+
+
+// ----------------------------------------------------------------------------
+// Tensor-core passes (rsot_tc.cuh).  Both passes form D = P_q . T_j, the
+// exponent r_qj of every pair, with one mma.sync m16n8k16 per 16 points x 8
+// targets: rows = points (A fragments of the point records), columns =
+// targets (B fragments of the target records), f32 accumulation from zero.
+// The two passes issue the same instruction on the same operands, so pass 2
+// sees bitwise the exponents of pass 1 and the plan rows it forms sum to 1 as
+// in the FP32 kernels; the per-point shift (-M_q in pass 1, u_q in pass 2) is
+// one packed FP32 add per two pairs, ex2 reads the result, one packed add
+// per two pairs accumulates.
+//
+// Pass 1 holds 4 m-blocks of 16 points per warp in registers and streams the
+// target records (8 per n-block) through shared memory.  Lane (g, t) sums
+// rows g and g + 8 over its columns 2t, 2t + 1 with its own integral shifts
+// M; groups of 8 n-blocks are summed optimistically and redone exactly
+// (maximum over the group, M raised to its ceiling, sums rescaled by a power
+// of two) when a lane's group sum exceeds 2^60 or is not finite, or a shift
+// is not yet set.  The 4 lanes of a row are merged at the end.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void tc_raise(float &M, float mx, float &sf, double &sd) {
+    const float mn = ceilf(mx);
+    if (mn > M) {
+        if (M != -INFINITY) {
+            const float dl = M - mn;
+            sf *= pow2_int_f(dl);
+            sd *= pow2_int_d(dl);
+        }
+        M = mn;
+    }
+}
+
+// exact redo of one group of TC_GROUP n-blocks (warp-uniform)
+__device__ __forceinline__ void tc_exact_group(const uint2 *__restrict__ gb,
+                                               const unsigned (&A)[TC_MB][4], float2 (&M)[TC_MB],
+                                               float2 (&Sf)[TC_MB], double2 (&Sd)[TC_MB],
+                                               float2 (&acc)[TC_MB]) {
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        float mg = -INFINITY, mg8 = -INFINITY;
+#pragma unroll 2
+        for (int i = 0; i < TC_GROUP; ++i) {
+            float dd[4];
+            mma_tc(dd, A[m], gb[32 * i]);
+            mg = max3f(mg, dd[0], dd[1]);
+            mg8 = max3f(mg8, dd[2], dd[3]);
+        }
+        tc_raise(M[m].x, mg, Sf[m].x, Sd[m].x);
+        tc_raise(M[m].y, mg8, Sf[m].y, Sd[m].y);
+        const float2 ng = make_float2(-M[m].x, -M[m].x), ng8 = make_float2(-M[m].y, -M[m].y);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int i = 0; i < TC_GROUP; ++i) {
+            float dd[4];
+            mma_tc(dd, A[m], gb[32 * i]);
+            const float2 e01 = __fadd2_rn(make_float2(dd[0], dd[1]), ng);
+            const float2 e23 = __fadd2_rn(make_float2(dd[2], dd[3]), ng8);
+            a = __fadd2_rn(a, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+            a = __fadd2_rn(a, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+        }
+        acc[m] = a;
+    }
+}
+
+// A fragment of rows (g, g + 8) of a 16-point m-block whose records start at
+// rec (uint2 view): segment t of row g and of row g + 8.
+__device__ __forceinline__ void tc_load_a(unsigned (&a)[4], const uint2 *rec, int g, int t) {
+    load_a(a, rec[g * 4 + t], rec[(g + 8) * 4 + t]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_lse_tc(const Rec16 *__restrict__ prec, int64_t nq_pad, const Rec16 *__restrict__ trec,
+             int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags,
+             const int *__restrict__ gate) {
+    if (gate && (*gate & 1)) return;   // operands out of f16 range: the FP32 kernel runs
+    __shared__ __align__(128) Rec16 sm[TC_STAGES][TC_TS];
+    __shared__ __align__(8) uint64_t full[TC_STAGES];
+    __shared__ int s_abort[2];   // indexed by iteration parity
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    const int64_t q0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
+    const int kc = blockIdx.y;
+    const int t_begin = kc * chunk;
+    const int t_count = min(chunk, n_p1 - t_begin);
+    const int ntile = t_count / TC_TS;
+
+    unsigned A[TC_MB][4];
+    float2 M[TC_MB], Sf[TC_MB];
+    double2 Sd[TC_MB];
+    const uint2 *pr = reinterpret_cast<const uint2 *>(prec);
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        tc_load_a(A[m], pr + (q0 + m * 16) * 4, g, t);
+        M[m] = make_float2(-INFINITY, -INFINITY);
+        Sf[m] = make_float2(0.f, 0.f);
+        Sd[m] = make_double2(0.0, 0.0);
+    }
+
+    if (tid == 0) {
+        s_abort[0] = s_abort[1] = 0;
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES && s < ntile; ++s) {
+            mbar_expect_tx(&full[s], TC_TS * sizeof(Rec16));
+            bulk_g2s(sm[s], trec + t_begin + s * TC_TS, TC_TS * sizeof(Rec16), &full[s]);
+        }
+    }
+    int issued = min(TC_STAGES, ntile);
+    bool aborted = false;
+    constexpr int NGRP = TC_NBS / TC_GROUP;
+    for (int it = 0; it < ntile; ++it) {
+        const int s = it % TC_STAGES;
+        const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
+        const bool ok = mbar_wait(&full[s], ph);
+        if (!ok) {
+            s_abort[it & 1] = 1;
+            atomicOr(flags, kErrTimeout);
+        } else {
+            const uint2 *base = reinterpret_cast<const uint2 *>(&sm[s][0]) + lane;
+            float dc[TC_MB][4];
+            {
+                const uint2 b = base[0];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) mma_tc(dc[m], A[m], b);
+            }
+#pragma unroll 1
+            for (int grp = 0; grp < NGRP; ++grp) {
+                float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    acc[m] = make_float2(0.f, 0.f);
+                    ng[m] = make_float2(-M[m].x, -M[m].x);
+                    ng8[m] = make_float2(-M[m].y, -M[m].y);
+                }
+#pragma unroll
+                for (int i = 0; i < TC_GROUP; ++i) {
+                    const int nb = grp * TC_GROUP + i;
+                    const bool more = (i + 1 < TC_GROUP) || (grp + 1 < NGRP);
+                    float dn[TC_MB][4];
+                    if (more) {
+                        const uint2 b = base[32 * (nb + 1)];
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) mma_tc(dn[m], A[m], b);
+                    }
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        const float2 e01 = __fadd2_rn(make_float2(dc[m][0], dc[m][1]), ng[m]);
+                        const float2 e23 = __fadd2_rn(make_float2(dc[m][2], dc[m][3]), ng8[m]);
+                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                    }
+                    if (more) {
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m)
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) dc[m][r] = dn[m][r];
+                    }
+                }
+                bool bad = false;
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m)
+                    bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) || M[m].x == -INFINITY ||
+                          M[m].y == -INFINITY;
+                if (__any_sync(0xffffffffu, bad))
+                    tc_exact_group(base + 32 * grp * TC_GROUP, A, M, Sf, Sd, acc);
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
+            }
+        }
+        __syncthreads();
+        aborted = s_abort[it & 1] != 0;
+        if (aborted) break;
+        if (tid == 0 && it + TC_STAGES < ntile) {
+            mbar_expect_tx(&full[s], TC_TS * sizeof(Rec16));
+            bulk_g2s(sm[s], trec + t_begin + (it + TC_STAGES) * TC_TS, TC_TS * sizeof(Rec16),
+                     &full[s]);
+            ++issued;
+        }
+#pragma unroll
+        for (int m = 0; m < TC_MB; ++m) {
+            Sd[m].x += (double)Sf[m].x;
+            Sd[m].y += (double)Sf[m].y;
+            Sf[m] = make_float2(0.f, 0.f);
+        }
+    }
+    if (aborted) {
+        if (tid == 0) {
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % TC_STAGES], (unsigned)(it / TC_STAGES) & 1u);
+        }
+        return;
+    }
+    // merge the 4 lanes of each row: common shift = their maximum
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        float mx = M[m].x, my = M[m].y;
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 1));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 2));
+        double sx = M[m].x == -INFINITY ? 0.0 : Sd[m].x * pow2_int_d(M[m].x - mx);
+        double sy = M[m].y == -INFINITY ? 0.0 : Sd[m].y * pow2_int_d(M[m].y - my);
+        sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+        sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+        sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+        sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+        M[m] = make_float2(mx, my);
+        Sd[m] = make_double2(sx, sy);
+    }
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        if (m != t) continue;   // lane t writes m-block t
+        const int64_t qa = q0 + m * 16 + g;
+        float2 *o = part + (int64_t)kc * nq_pad;
+        o[qa] = M[m].x == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(M[m].x, (float)Sd[m].x);
+        o[qa + 8] = M[m].y == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(M[m].y, (float)Sd[m].y);
+    }
+}
+
+// Pass 2: rows = targets (A fragments of the target records, 4 m-blocks of 16
+// targets per warp, in registers), columns = points (records and shifts u_q
+// streamed through shared memory, 8 per n-block).  The mma is symmetric in
+// its operands bit for bit (checked on GB300: swapping the roles of the
+// operands changed none of 2^21 results), so D here is bitwise the D of
+// pass 1.  Lane (g, t) sums rows g and g + 8 over its columns 2t, 2t + 1,
+// FP32 within a stage and FP64 across stages; the 4 lanes of a row are
+// added at the end.
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_grad_tc(const Rec16 *__restrict__ trec, const Rec16 *__restrict__ prec,
+              const float *__restrict__ pu, int64_t nq_pad, int64_t chunk,
+              double *__restrict__ part2, int64_t stride, int *__restrict__ flags,
+              const int *__restrict__ gate) {
+    if (gate && (*gate & 1)) return;   // out of f16 range: the FP32 kernel runs
+    __shared__ __align__(128) Rec16 sm[TC_STAGES][TC_TS];
+    __shared__ __align__(128) float su[TC_STAGES][TC_TS];
+    __shared__ __align__(8) uint64_t full[TC_STAGES];
+    __shared__ int s_abort[2];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    const int64_t j0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
+    const uint2 *tr = reinterpret_cast<const uint2 *>(trec);
+    unsigned A[TC_MB][4];
+    double2 acc64[TC_MB];
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        tc_load_a(A[m], tr + (j0 + m * 16) * 4, g, t);
+        acc64[m] = make_double2(0.0, 0.0);
+    }
+    const int64_t p_begin = (int64_t)blockIdx.y * chunk;
+    const int64_t p_count = min(chunk, nq_pad - p_begin);
+    const int ntile = (int)(p_count / TC_TS);
+    constexpr unsigned kStageBytes = TC_TS * sizeof(Rec16) + TC_TS * sizeof(float);
+
+    if (tid == 0) {
+        s_abort[0] = s_abort[1] = 0;
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES && s < ntile; ++s) {
+            mbar_expect_tx(&full[s], kStageBytes);
+            bulk_g2s(sm[s], prec + p_begin + (int64_t)s * TC_TS, TC_TS * sizeof(Rec16), &full[s]);
+            bulk_g2s(su[s], pu + p_begin + (int64_t)s * TC_TS, TC_TS * sizeof(float), &full[s]);
+        }
+    }
+    int issued = min(TC_STAGES, ntile);
+    bool aborted = false;
+    for (int it = 0; it < ntile; ++it) {
+        const int s = it % TC_STAGES;
+        const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
+        const bool ok = mbar_wait(&full[s], ph);
+        if (!ok) {
+            s_abort[it & 1] = 1;
+            atomicOr(flags, kErrTimeout);
+        } else {
+            const uint2 *base = reinterpret_cast<const uint2 *>(&sm[s][0]) + lane;
+            const float2 *ub = reinterpret_cast<const float2 *>(&su[s][0]) + t;   // (u_2t, u_2t+1)
+            float2 acc[TC_MB];
+            float dc[TC_MB][4];
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
+            float2 uc = ub[0];
+            {
+                const uint2 b = base[0];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) mma_tc(dc[m], A[m], b);
+            }
+#pragma unroll 4
+            for (int nb = 0; nb < TC_NBS; ++nb) {
+                float dn[TC_MB][4];
+                float2 un = uc;
+                const bool more = nb + 1 < TC_NBS;
+                if (more) {
+                    const uint2 b = base[32 * (nb + 1)];
+                    un = ub[4 * (nb + 1)];
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) mma_tc(dn[m], A[m], b);
+                }
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    const float2 e01 = __fadd2_rn(make_float2(dc[m][0], dc[m][1]), uc);
+                    const float2 e23 = __fadd2_rn(make_float2(dc[m][2], dc[m][3]), uc);
+                    acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                    acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                }
+                if (more) {
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) dc[m][r] = dn[m][r];
+                    uc = un;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) {
+                acc64[m].x += (double)acc[m].x;
+                acc64[m].y += (double)acc[m].y;
+            }
+        }
+        __syncthreads();
+        aborted = s_abort[it & 1] != 0;
+        if (aborted) break;
+        if (tid == 0 && it + TC_STAGES < ntile) {
+            mbar_expect_tx(&full[s], kStageBytes);
+            bulk_g2s(sm[s], prec + p_begin + (int64_t)(it + TC_STAGES) * TC_TS,
+                     TC_TS * sizeof(Rec16), &full[s]);
+            bulk_g2s(su[s], pu + p_begin + (int64_t)(it + TC_STAGES) * TC_TS,
+                     TC_TS * sizeof(float), &full[s]);
+            ++issued;
+        }
+    }
+    if (aborted) {
+        if (tid == 0) {
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % TC_STAGES], (unsigned)(it / TC_STAGES) & 1u);
+        }
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        acc64[m].x += __shfl_xor_sync(0xffffffffu, acc64[m].x, 1);
+        acc64[m].x += __shfl_xor_sync(0xffffffffu, acc64[m].x, 2);
+        acc64[m].y += __shfl_xor_sync(0xffffffffu, acc64[m].y, 1);
+        acc64[m].y += __shfl_xor_sync(0xffffffffu, acc64[m].y, 2);
+    }
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        if (m != t) continue;   // lane t writes m-block t
+        double *o = part2 + (int64_t)blockIdx.y * stride + j0 + m * 16 + g;
+        o[0] = acc64[m].x;
+        o[8] = acc64[m].y;
+    }
+}
+
+// Point operand records (X = P x', no shift slots), once per problem.
+__global__ void k_point_recs(const float *__restrict__ xs, int64_t nq_pad, int d, float P,
+                             Rec16 *__restrict__ prec) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq_pad) return;
+    float X[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[k] = k < d ? xs[k * nq_pad + q] * P : 0.0f;
+    prec[q] = make_point_rec(X, 0.0f);
 }
 
 // grad_j = sum_s part2[s][j] - nu_j  (fixed order: deterministic)
@@ -632,6 +1021,16 @@ cudaError_t dense_alloc(rsot_problem *p) {
     p->s2 = pick_split(units2, p->nq_pad / P2_TS, slots2);
     p->chunk2 = round_up((p->nq_pad + p->s2 - 1) / p->s2, P2_TS);
     p->s2 = (int)((p->nq_pad + p->chunk2 - 1) / p->chunk2);
+    // the same splits for the tensor-core passes (TC_ROWS points / targets per CTA);
+    // their FP32 fallback (by the gate) runs with these chunks too
+    const int64_t slots_tc1 = (int64_t)p->num_sms * occupancy((const void *)k_lse_tc, TC_THREADS, 0);
+    p->k1_tc = pick_split(p->nq_pad / TC_ROWS, n_p1 / TC_TS, slots_tc1);
+    p->chunk1_tc = (int)round_up((n_p1 + p->k1_tc - 1) / p->k1_tc, TC_TS);
+    p->k1_tc = (int)((n_p1 + p->chunk1_tc - 1) / p->chunk1_tc);
+    const int64_t slots_tc2 = (int64_t)p->num_sms * occupancy((const void *)k_grad_tc, TC_THREADS, 0);
+    p->s2_tc = pick_split(n_alloc / TC_ROWS, p->nq_pad / TC_TS, slots_tc2);
+    p->chunk2_tc = round_up((p->nq_pad + p->s2_tc - 1) / p->s2_tc, TC_TS);
+    p->s2_tc = (int)((p->nq_pad + p->chunk2_tc - 1) / p->chunk2_tc);
     // FP64 split
     const int64_t units64 = (p->n + F_THREADS - 1) / F_THREADS;
     p->s2_64 = pick_split(units64, p->nq_pad / F_TS, (int64_t)p->num_sms * 8);
@@ -644,9 +1043,16 @@ cudaError_t dense_alloc(rsot_problem *p) {
 
     if ((e = cudaMalloc(&p->tdup, n_alloc * sizeof(Rec8)))) return e;
     if ((e = cudaMalloc(&p->tpair, (n_alloc / 2) * sizeof(Rec8)))) return e;
-    if ((e = cudaMalloc(&p->part1, (size_t)p->k1 * p->nq_pad * sizeof(float2)))) return e;
+    const int k1max = std::max(p->k1, p->k1_tc), s2max = std::max(p->s2, p->s2_tc);
+    if ((e = cudaMalloc(&p->part1, (size_t)k1max * p->nq_pad * sizeof(float2)))) return e;
     if ((e = cudaMalloc(&p->pdup, p->nq_pad * sizeof(Rec8)))) return e;
-    if ((e = cudaMalloc(&p->part2, (size_t)p->s2 * n_alloc * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->part2, (size_t)s2max * n_alloc * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&p->trec, n_alloc * sizeof(Rec16)))) return e;
+    if ((e = cudaMalloc(&p->prec16, p->nq_pad * sizeof(Rec16)))) return e;
+    if ((e = cudaMalloc(&p->pu, p->nq_pad * sizeof(float)))) return e;
+    k_point_recs<<<(unsigned)((p->nq_pad + 255) / 256), 256>>>(p->xs, p->nq_pad, p->d, p->tc_P,
+                                                              p->prec16);
+    if ((e = cudaStreamSynchronize(0))) return e;
     if ((e = cudaMalloc(&p->part2_64, (size_t)p->s2_64 * n_alloc * sizeof(double)))) return e;
     if ((e = cudaMalloc(&p->blockJ, (size_t)nbj * sizeof(double)))) return e;
     if ((e = cudaMalloc(&p->psinu, (size_t)p->nblk_prep * sizeof(double)))) return e;
@@ -657,6 +1063,9 @@ cudaError_t dense_alloc(rsot_problem *p) {
 }
 
 void dense_free(rsot_problem *p) {
+    cudaFree(p->trec);
+    cudaFree(p->prec16);
+    cudaFree(p->pu);
     cudaFree(p->tdup);
     cudaFree(p->tpair);
     cudaFree(p->part1);
@@ -670,41 +1079,72 @@ void dense_free(rsot_problem *p) {
     cudaFree(p->lse_buf);
 }
 
+// Automatic choice of the pair kernel.  The tensor-core exponents carry a
+// random error of rms ~2e-5 (log2 units, at eps = 1e-3 magnitudes; measured
+// against exact sums) against ~5e-6 for the FP32 chain; a gradient entry
+// sum_q m_q p_qj then errs by ~ln2 2e-5 sqrt(sum_q (m_q p_qj)^2) <=
+// 1.4e-5 sqrt(m_max nu_max).  Below m_max nu_max = 2e-6 five such standard
+// deviations stay under 1e-7, a tenth of the per-entry bound of the mixed
+// path; smaller problems (few points or heavy targets) take the FP32 kernels.
+constexpr double kTcAuto = 2e-6;
+
 template <int D>
 static cudaError_t launch_mixed_d(rsot_problem *p, const double *psi, double eps, double *grad) {
     cudaStream_t st = p->stream;
     const int64_t n_p1 = round_up(p->n, P1_TS);
+    // tensor-core passes by default; their FP32 kernels run as the fallback when
+    // the prep or combine kernel finds an operand outside the f16 range (gate)
+    const bool tc = p->pair_kernel == 1 || (p->pair_kernel == 2 && p->m_max * p->nu_max <= kTcAuto);
+    int *gate = tc ? &p->res_dev->gate : nullptr;
+    const int k1 = tc ? p->k1_tc : p->k1, chunk1 = tc ? p->chunk1_tc : p->chunk1;
+    const int s2 = tc ? p->s2_tc : p->s2;
+    const int64_t chunk2 = tc ? p->chunk2_tc : p->chunk2;
     trace_begin(p, "prep_targets_mixed");
     k_prep_mixed<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad,
                                                       p->d, eps, p->tdup, p->tpair, p->psinu,
-                                                      p->flags);
+                                                      p->flags, tc ? p->trec : nullptr,
+                                                      1.0 / (double)p->tc_P, gate);
     trace_end(p);
-    dim3 g1((unsigned)(p->nq_pad / P1_TILE), (unsigned)p->k1);
+    if (tc) {
+        dim3 gt((unsigned)(p->nq_pad / TC_ROWS), (unsigned)k1);
+        trace_begin(p, "lse_tc");
+        k_lse_tc<<<gt, TC_THREADS, 0, st>>>(p->prec16, p->nq_pad, p->trec, (int)n_p1, chunk1,
+                                            p->part1, p->flags, gate);
+        trace_end(p);
+    }
+    dim3 g1((unsigned)(p->nq_pad / P1_TILE), (unsigned)k1);
     trace_begin(p, "lse_mixed");
-    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(p->xs, p->nq_pad, p->tdup, (int)n_p1, p->chunk1,
-                                              p->part1, p->flags);
+    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(p->xs, p->nq_pad, p->tdup, (int)n_p1, chunk1,
+                                              p->part1, p->flags, gate, 1);
     trace_end(p);
     trace_begin(p, "combine_mixed");
-    k_combine<<<p->nblk_comb, CB_THREADS, 0, st>>>(p->part1, p->k1, p->nq_pad, p->nq, p->xs, p->d,
+    k_combine<<<p->nblk_comb, CB_THREADS, 0, st>>>(p->part1, k1, p->nq_pad, p->nq, p->xs, p->d,
                                                    p->lmass2, p->mass, p->pdup, p->blockJ,
-                                                   p->lse_buf);
+                                                   p->lse_buf, tc ? p->pu : nullptr);
     trace_end(p);
+    if (tc) {
+        dim3 gt((unsigned)(p->n_pad / TC_ROWS), (unsigned)s2);
+        trace_begin(p, "grad_tc");
+        k_grad_tc<<<gt, TC_THREADS, 0, st>>>(p->trec, p->prec16, p->pu, p->nq_pad, chunk2,
+                                             p->part2, p->n_pad, p->flags, gate);
+        trace_end(p);
+    }
     const int tpp = pick_tpp(p->n);
     const int64_t blk2 = (int64_t)P2_THREADS * 2 * tpp;
-    dim3 g2((unsigned)((p->n + blk2 - 1) / blk2), (unsigned)p->s2);
+    dim3 g2((unsigned)((p->n + blk2 - 1) / blk2), (unsigned)s2);
     trace_begin(p, "grad_mixed");
     if (tpp == 4)
-        k_grad_mixed<D, 4><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, p->chunk2,
-                                                      p->part2, p->n_pad, p->flags);
+        k_grad_mixed<D, 4><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, chunk2,
+                                                      p->part2, p->n_pad, p->flags, gate, 1);
     else if (tpp == 2)
-        k_grad_mixed<D, 2><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, p->chunk2,
-                                                      p->part2, p->n_pad, p->flags);
+        k_grad_mixed<D, 2><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, chunk2,
+                                                      p->part2, p->n_pad, p->flags, gate, 1);
     else
-        k_grad_mixed<D, 1><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, p->chunk2,
-                                                      p->part2, p->n_pad, p->flags);
+        k_grad_mixed<D, 1><<<g2, P2_THREADS, 0, st>>>(p->tpair, p->pdup, p->nq_pad, chunk2,
+                                                      p->part2, p->n_pad, p->flags, gate, 1);
     trace_end(p);
     trace_begin(p, "finalize_grad");
-    k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(p->part2, p->s2, p->n_pad,
+    k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(p->part2, s2, p->n_pad,
                                                                     p->nu, p->n, grad);
     trace_end(p);
     trace_begin(p, "finalize_J");
@@ -763,7 +1203,7 @@ static cudaError_t softmax_refine_d(rsot_problem *p, const double *psi, double e
     const int64_t n_p1 = round_up(p->n, P1_TS);
     k_prep_mixed<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad,
                                                       p->d, eps, p->tdup, p->tpair, p->psinu,
-                                                      p->flags);
+                                                      p->flags, nullptr, 1.0, nullptr);
     dim3 g1((unsigned)(p->nq_pad / P1_TILE), (unsigned)p->k1);
     k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(p->xs, p->nq_pad, p->tdup, (int)n_p1, p->chunk1,
                                               p->part1, p->flags);

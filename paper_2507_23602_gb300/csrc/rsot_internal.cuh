@@ -47,10 +47,11 @@ struct EvalResult {
     long long pairs;
     long long empty;
     int flags;
-    int pad;
+    int gate;           // bit 0: an f16 operand is out of range (both passes take the FP32 kernels)
 };
 
 struct Grid;  // truncated-path cell grid (rsot_trunc.cu)
+struct Rec16; // tensor-core operand record (rsot_tc.cuh)
 
 }  // namespace rsot
 
@@ -88,6 +89,17 @@ struct rsot_problem {
     int s2 = 0;                     // pass-2 point splits
     int64_t chunk2 = 0;
     int nblk_comb = 0, nblk_prep = 0;
+    // tensor-core form of the pair arithmetic (rsot_tc.cuh)
+    rsot::Rec16 *trec = nullptr;    // [n_pad] target operand records
+    rsot::Rec16 *prec16 = nullptr;  // [nq_pad] point operand records (static)
+    float *pu = nullptr;            // [nq_pad] pass-2 shifts u_q = log2 m_q - R_q
+    float tc_P = 1.0f;              // point coordinate scale (power of two)
+    int pair_kernel = 2;            // 0: FP32 passes, 1: tensor-core passes (FP32 fallback by
+                                    // gate), 2: tensor-core passes when m_max nu_max <= kTcAuto
+    double m_max = 0.0;             // max_q m_q
+    int k1_tc = 0, chunk1_tc = 0;   // pass-1 target chunks of the tensor-core launch
+    int s2_tc = 0;                  // pass-2 point splits of the tensor-core launch
+    int64_t chunk2_tc = 0;
     // FP64 path scratch
     double *a64 = nullptr;          // [n_pad]   psi_j/eps + ln nu_j
     double *prec64 = nullptr;       // [nq_pad][4] (x0,x1,x2,u)

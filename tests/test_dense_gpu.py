@@ -38,16 +38,39 @@ def random_case(seed, d, nq, n, eps, psi_scale):
     return x, m, y, nu, psi, eps
 
 
+def tensor_tols(m, nu, eps, Jo):
+    """Bounds for the tensor-core pair kernel forced onto any problem: its
+    exponents err by rms ~2e-5 (log2 units, measured), i.e. a relative error
+    of ~1.4e-5 per plan entry; a gradient entry sum_q m_q p_qj then errs by
+    <= 1.4e-5 sqrt(m_max nu_max) per standard deviation and J by
+    eps ln2 2e-5 sqrt(sum_q m_q^2).  Five deviations, never below the mixed
+    path's own bounds (which the automatic choice meets)."""
+    g_tol = max(MIX_G_TOL, 5 * 1.4e-5 * math.sqrt(m.max() * nu.max()))
+    j_tol = max(MIX_J_TOL * abs(Jo), 5 * eps * math.log(2) * 2e-5 * math.sqrt(np.sum(m * m)))
+    return g_tol, j_tol
+
+
 def check(x, m, y, nu, psi, eps, precisions=(0, 1)):
+    """FP64 path once; the mixed path with the automatic pair kernel, the FP32
+    kernels, and the tensor-core kernels forced (with their error model)."""
     Jo, go, _, _ = oracle.dual_grad(x, m, y, nu, psi, eps)
     P = rs().Problem(x, m, y, nu)
+    runs = [(prec, kind) for prec in precisions
+            for kind in ((None,) if prec == 0 else
+                         (rs().PAIRS_AUTO, rs().PAIRS_FP32, rs().PAIRS_TENSOR))]
     try:
-        for prec in precisions:
+        for prec, kind in runs:
+            if kind is not None:
+                P.set_pair_kernel(kind)
             J, g, pairs = P.eval(psi, eps, 0.0, prec)
             assert pairs == x.shape[0] * y.shape[0]
             if prec == 0:
                 assert abs(J - Jo) <= FP64_TOL * abs(Jo), (J, Jo)
                 assert np.max(np.abs(g - go)) <= FP64_TOL * max(np.max(np.abs(go)), np.max(nu))
+            elif kind == rs().PAIRS_TENSOR:
+                g_tol, j_tol = tensor_tols(m, nu, eps, Jo)
+                assert abs(J - Jo) <= j_tol, (J, Jo, abs(J - Jo), j_tol)
+                assert np.max(np.abs(g - go)) <= g_tol, (np.max(np.abs(g - go)), g_tol)
             else:
                 assert abs(J - Jo) <= MIX_J_TOL * abs(Jo), (J, Jo, abs(J - Jo) / abs(Jo))
                 assert np.max(np.abs(g - go)) <= MIX_G_TOL, np.max(np.abs(g - go))
@@ -143,10 +166,78 @@ def test_repeated_evaluations_are_bitwise_identical():
     x, m, y, nu, psi, eps = random_case(11, 3, 6000, 2000, 0.01, 0.01)
     P = rs().Problem(x, m, y, nu)
     try:
-        for prec in (0, 1):
+        for prec, kind in ((0, None), (1, rs().PAIRS_TENSOR), (1, rs().PAIRS_FP32)):
+            if kind is not None:
+                P.set_pair_kernel(kind)
             J1, g1, _ = P.eval(psi, eps, 0.0, prec)
             J2, g2, _ = P.eval(psi, eps, 0.0, prec)
             assert J1 == J2 and np.array_equal(g1, g2)
+    finally:
+        P.close()
+
+
+def test_tensor_pairs_fall_back_outside_f16_range():
+    """At eps = 1e-7 the target operands w / P leave the f16 range: the
+    tensor-core evaluation must hand both passes to the FP32 kernels (same
+    per-pair arithmetic, other chunking) rather than overflow."""
+    x, m, y, nu, psi, _ = random_case(14, 2, 3000, 700, 1.0, 1e-9)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        P.set_pair_kernel(rs().PAIRS_FP32)
+        Jf, gf, _ = P.eval(psi, 1e-7, 0.0, 1)
+        P.set_pair_kernel(rs().PAIRS_TENSOR)
+        Jt, gt, _ = P.eval(psi, 1e-7, 0.0, 1)
+        assert np.isfinite(Jt) and np.all(np.isfinite(gt))
+        assert abs(Jt - Jf) <= 1e-9 * abs(Jf)
+        assert np.max(np.abs(gt - gf)) <= 1e-9
+    finally:
+        P.close()
+
+
+def test_tensor_pairs_passes_are_consistent():
+    """Both tensor-core passes form bitwise the same exponents, so with one
+    target (p = 1) the gradient vanishes to the FP32 rounding of the shifts,
+    as with the FP32 kernels."""
+    x, m, y, nu, psi, eps = random_case(16, 3, 20000, 1, 0.01, 0.0)
+    nu = np.ones(1)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        for kind in (rs().PAIRS_TENSOR, rs().PAIRS_FP32):
+            P.set_pair_kernel(kind)
+            _, g, _ = P.eval(psi, eps, 0.0, 1)
+            assert abs(g[0]) <= 1e-6, (kind, g[0])
+    finally:
+        P.close()
+
+
+def test_tensor_pairs_chosen_automatically_on_the_cube():
+    """The automatic choice takes the tensor cores on the benchmark workload
+    (m_max nu_max ~ 5e-11) and matches the FP32 kernels within the mixed bounds."""
+    p = ri.cube_3d(mesh_n=8, eps=1e-3)
+    psi = 0.005 * np.random.default_rng(17).standard_normal(p.n)
+    P = rs().Problem(p.x, p.mass, p.y, p.nu)
+    try:
+        assert p.mass.max() * p.nu.max() <= 2e-6
+        P.kernel_timing(True)
+        Ja, ga, _ = P.eval(psi, p.eps, 0.0, 1)
+        names = set(P.kernel_times())
+        P.kernel_timing(False)
+        assert {"lse_tc", "grad_tc"} <= names
+        P.set_pair_kernel(rs().PAIRS_FP32)
+        Jf, gf, _ = P.eval(psi, p.eps, 0.0, 1)
+        assert abs(Ja - Jf) <= MIX_J_TOL * abs(Jf)
+        assert np.max(np.abs(ga - gf)) <= MIX_G_TOL
+    finally:
+        P.close()
+
+
+def test_pair_kernel_argument_checked():
+    x, m, y, nu, psi, eps = random_case(15, 2, 100, 10, 0.05, 0.05)
+    P = rs().Problem(x, m, y, nu)
+    try:
+        with pytest.raises(rs().RsotError) as ei:
+            P.set_pair_kernel(7)
+        assert ei.value.status == 1
     finally:
         P.close()
 
