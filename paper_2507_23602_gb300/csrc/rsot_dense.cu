@@ -391,12 +391,13 @@ __device__ __forceinline__ void tc_load_a(unsigned (&a)[4], const uint2 *rec, in
     load_a(a, rec[g * 4 + t], rec[(g + 8) * 4 + t]);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     k_lse_tc(const Rec16 *__restrict__ prec, int64_t nq_pad, const Rec16 *__restrict__ trec,
              int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags,
              const int *__restrict__ gate) {
     if (gate && (*gate & 1)) return;   // operands out of f16 range: the FP32 kernel runs
-    __shared__ __align__(128) Rec16 sm[TC_STAGES][TC_TS];
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    Rec16 (*sm)[TC_TS] = reinterpret_cast<Rec16 (*)[TC_TS]>(tc_smem);   // [TC_STAGES][TC_TS]
     __shared__ __align__(8) uint64_t full[TC_STAGES];
     __shared__ int s_abort[2];   // indexed by iteration parity
 
@@ -551,14 +552,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 // pass 1.  Lane (g, t) sums rows g and g + 8 over its columns 2t, 2t + 1,
 // FP32 within a stage and FP64 across stages; the 4 lanes of a row are
 // added at the end.
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     k_grad_tc(const Rec16 *__restrict__ trec, const Rec16 *__restrict__ prec,
               const float *__restrict__ pu, int64_t nq_pad, int64_t chunk,
               double *__restrict__ part2, int64_t stride, int *__restrict__ flags,
               const int *__restrict__ gate) {
     if (gate && (*gate & 1)) return;   // out of f16 range: the FP32 kernel runs
-    __shared__ __align__(128) Rec16 sm[TC_STAGES][TC_TS];
-    __shared__ __align__(128) float su[TC_STAGES][TC_TS];
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    Rec16 (*sm)[TC_TS] = reinterpret_cast<Rec16 (*)[TC_TS]>(tc_smem);   // [TC_STAGES][TC_TS]
+    float (*su)[TC_TS] = reinterpret_cast<float (*)[TC_TS]>(tc_smem + TC_SMEM1);
     __shared__ __align__(8) uint64_t full[TC_STAGES];
     __shared__ int s_abort[2];
 
@@ -1023,11 +1025,18 @@ cudaError_t dense_alloc(rsot_problem *p) {
     p->s2 = (int)((p->nq_pad + p->chunk2 - 1) / p->chunk2);
     // the same splits for the tensor-core passes (TC_ROWS points / targets per CTA);
     // their FP32 fallback (by the gate) runs with these chunks too
-    const int64_t slots_tc1 = (int64_t)p->num_sms * occupancy((const void *)k_lse_tc, TC_THREADS, 0);
-    p->k1_tc = pick_split(p->nq_pad / TC_ROWS, n_p1 / TC_TS, slots_tc1);
-    p->chunk1_tc = (int)round_up((n_p1 + p->k1_tc - 1) / p->k1_tc, TC_TS);
-    p->k1_tc = (int)((n_p1 + p->chunk1_tc - 1) / p->chunk1_tc);
-    const int64_t slots_tc2 = (int64_t)p->num_sms * occupancy((const void *)k_grad_tc, TC_THREADS, 0);
+    const int64_t n_tc = round_up(p->n, TC_TS);
+    if ((e = cudaFuncSetAttribute((const void *)k_lse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TC_SMEM1)))
+        return e;
+    if ((e = cudaFuncSetAttribute((const void *)k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TC_SMEM2)))
+        return e;
+    const int64_t slots_tc1 = (int64_t)p->num_sms * occupancy((const void *)k_lse_tc, TC_THREADS, TC_SMEM1);
+    p->k1_tc = pick_split(p->nq_pad / TC_ROWS, n_tc / TC_TS, slots_tc1);
+    p->chunk1_tc = (int)round_up((n_tc + p->k1_tc - 1) / p->k1_tc, TC_TS);
+    p->k1_tc = (int)((n_tc + p->chunk1_tc - 1) / p->chunk1_tc);
+    const int64_t slots_tc2 = (int64_t)p->num_sms * occupancy((const void *)k_grad_tc, TC_THREADS, TC_SMEM2);
     p->s2_tc = pick_split(n_alloc / TC_ROWS, p->nq_pad / TC_TS, slots_tc2);
     p->chunk2_tc = round_up((p->nq_pad + p->s2_tc - 1) / p->s2_tc, TC_TS);
     p->s2_tc = (int)((p->nq_pad + p->chunk2_tc - 1) / p->chunk2_tc);
@@ -1108,8 +1117,9 @@ static cudaError_t launch_mixed_d(rsot_problem *p, const double *psi, double eps
     if (tc) {
         dim3 gt((unsigned)(p->nq_pad / TC_ROWS), (unsigned)k1);
         trace_begin(p, "lse_tc");
-        k_lse_tc<<<gt, TC_THREADS, 0, st>>>(p->prec16, p->nq_pad, p->trec, (int)n_p1, chunk1,
-                                            p->part1, p->flags, gate);
+        k_lse_tc<<<gt, TC_THREADS, TC_SMEM1, st>>>(p->prec16, p->nq_pad, p->trec,
+                                            (int)round_up(p->n, TC_TS), chunk1, p->part1,
+                                            p->flags, gate);
         trace_end(p);
     }
     dim3 g1((unsigned)(p->nq_pad / P1_TILE), (unsigned)k1);
@@ -1125,7 +1135,7 @@ static cudaError_t launch_mixed_d(rsot_problem *p, const double *psi, double eps
     if (tc) {
         dim3 gt((unsigned)(p->n_pad / TC_ROWS), (unsigned)s2);
         trace_begin(p, "grad_tc");
-        k_grad_tc<<<gt, TC_THREADS, 0, st>>>(p->trec, p->prec16, p->pu, p->nq_pad, chunk2,
+        k_grad_tc<<<gt, TC_THREADS, TC_SMEM2, st>>>(p->trec, p->prec16, p->pu, p->nq_pad, chunk2,
                                              p->part2, p->n_pad, p->flags, gate);
         trace_end(p);
     }

@@ -36,14 +36,29 @@ struct __align__(32) Rec16 {
     uint2 s[4];
 };
 
+// Shapes; the build may override them (-DRSOT_TC_TS=..., etc.) to tune.
+#ifndef RSOT_TC_TS
+#define RSOT_TC_TS 1024
+#endif
+#ifndef RSOT_TC_STAGES
+#define RSOT_TC_STAGES 2
+#endif
+#ifndef RSOT_TC_MINB
+#define RSOT_TC_MINB 2
+#endif
 inline constexpr int TC_THREADS = 256;               // 8 warps
 inline constexpr int TC_WARPS = TC_THREADS / 32;
 inline constexpr int TC_MB = 4;                       // 16-row m-blocks per warp
 inline constexpr int TC_ROWS = TC_WARPS * TC_MB * 16; // points (pass 1) / targets (pass 2) per CTA
-inline constexpr int TC_TS = 256;                     // records per stage
-inline constexpr int TC_STAGES = 2;
-inline constexpr int TC_NBS = TC_TS / 8;              // n-blocks per stage (32)
+inline constexpr int TC_TS = RSOT_TC_TS;              // records per stage (multiple of 256)
+inline constexpr int TC_STAGES = RSOT_TC_STAGES;
+inline constexpr int TC_MINB = RSOT_TC_MINB;          // resident CTAs per SM asked of ptxas
+inline constexpr int TC_NBS = TC_TS / 8;              // n-blocks per stage
 inline constexpr int TC_GROUP = 8;                    // n-blocks per optimistic group
+static_assert(TC_TS % 256 == 0 && 1024 % TC_TS == 0, "stages tile the 1024-padded arrays");
+// dynamic shared memory: pass 1 stages target records; pass 2 point records and shifts
+inline constexpr size_t TC_SMEM1 = (size_t)TC_STAGES * TC_TS * 32;
+inline constexpr size_t TC_SMEM2 = TC_SMEM1 + (size_t)TC_STAGES * TC_TS * sizeof(float);
 inline constexpr float TC_RANGE = 60000.0f;           // |f16 operand| bound (f16 max 65504)
 inline constexpr float TC_BIG = 1.152921504606846976e18f;  // 2^60
 
