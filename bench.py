@@ -122,10 +122,13 @@ class Clocks:
 
 
 def kernel_source_hash():
+    """Hash of the sources the dense kernels are built from (their file and the
+    shared device headers)."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2507_23602_gb300", "csrc"))):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(ROOT, "paper_2507_23602_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2507_23602_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f == "rsot_dense.cu" or f.endswith(".cuh"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -97,6 +97,8 @@ int64_t num_targets(const rsot_problem *p) { return p->n; }
 void copy_nu(const rsot_problem *p, double *out) {
     cudaMemcpy(out, p->nu, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost);
 }
+int pair_kernel_of(const rsot_problem *p) { return p->pair_kernel; }
+
 }  // namespace rsot
 
 extern "C" {

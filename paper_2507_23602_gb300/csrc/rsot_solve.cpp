@@ -38,6 +38,7 @@
 namespace rsot {
 int64_t num_targets(const rsot_problem *p);
 void copy_nu(const rsot_problem *p, double *out);
+int pair_kernel_of(const rsot_problem *p);
 }  // namespace rsot
 
 namespace {
@@ -191,6 +192,12 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             // correction, mixed L-BFGS on the corrected objective in between
             Evaluator ev64{p, n, eps, opt->tail, RSOT_FP64};
             Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
+            // the refinement works below the random rounding noise of the
+            // tensor-core exponents (rms ~2e-5 per pair, several 1e-6 in the L1
+            // norm of a large gradient): its mixed evaluations take the FP32
+            // kernels, whose noise is four times lower
+            const int kernel_before = rsot::pair_kernel_of(p);
+            rsot_set_pair_kernel(p, RSOT_PAIRS_FP32);
             bool done = false;
             st = RSOT_OK;
             // each correction runs at most 200 mixed iterations; corrections stop when
@@ -232,6 +239,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
                 g = mc64.g();
                 iters += mc64.iters();
             }
+            rsot_set_pair_kernel(p, (rsot_pair_kernel)kernel_before);
             evals += ev64.evals + evm.evals;
             pairs += ev64.pairs + evm.pairs;
         }
