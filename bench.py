@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-trunc", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--pair-kernel", choices=["auto", "tensor", "fp32"], default="auto",
+                    help="dense workload: pair kernel of the timed evaluations")
+    ap.add_argument("--tail", type=float, default=0.0,
+                    help="multilevel: truncation tail of every evaluation (0: dense)")
     ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart"],
                     default="dense",
                     help="dense: dual+grad throughput (default); the others time solves")
@@ -293,11 +297,12 @@ def run_solve_workloads(args):
         L = max(len(src), len(levels)) - 1
         eps_levels = [args.eps * 2 ** (L - l) for l in range(L + 1)]
         psi, st = rs.multilevel_solve(src, levels, eps_levels, tol_l1=1e-6, eps_start=0.1,
-                                      eps_factor=0.5, precision=rs.MIXED, raise_on_error=False)
+                                      eps_factor=0.5, precision=rs.MIXED, raise_on_error=False,
+                                      tail=args.tail)
         solve_line("multilevel solve time to ||grad||_1<=1e-6 (combined source/target, Sec. 5.3)",
                    st["total_seconds"], "s",
                    f"multilevel-{src[-1][0].shape[0]}pts-{levels[-1][0].shape[0]}tgt",
-                   {"kmeans_seconds": t_km, "stats": st,
+                   {"kmeans_seconds": t_km, "stats": st, "tail": args.tail,
                     "levels_points": [s[0].shape[0] for s in src],
                     "levels_targets": [t2[0].shape[0] for t2 in levels]}, args)
         return
@@ -348,6 +353,8 @@ def main():
         torch.cuda.synchronize()
 
     P = rs.Problem(p.x, p.mass, p.y, p.nu, stream=torch.cuda.current_stream())
+    kind = {"auto": rs.PAIRS_AUTO, "tensor": rs.PAIRS_TENSOR, "fp32": rs.PAIRS_FP32}[args.pair_kernel]
+    P.set_pair_kernel(kind)
     psi_d = torch.tensor(psi, device=dev)
     grad_d = torch.empty(p.n, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -403,7 +410,7 @@ def main():
             fms.append(a.elapsed_time(b_))
         fk = P.kernel_times()
         P.kernel_timing(False)
-        P.set_pair_kernel(rs.PAIRS_TENSOR)
+        P.set_pair_kernel(kind)
         fp32_pairs = {"value": pairs / (sum(fms) / len(fms) * 1e-3) / 1e9, "unit": "G pairs/s",
                       "ms_per_step": sum(fms) / len(fms),
                       "per_kernel_ms": {k: v[0] / v[1] for k, v in fk.items()}}
@@ -493,7 +500,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "nq": p.nq, "n": p.n, "eps": p.eps,
                    "pairs_per_step": pairs, "precision": "mixed (f32 pairs, f64 reductions)",
-                   "pair_kernel": "tensor cores (mma.sync f16 head/tail operands, f32 accumulate)",
+                   "pair_kernel": args.pair_kernel + (" (tensor cores on this workload: mma.sync f16 "
+                                                      "head/tail operands, f32 accumulate)"
+                                                      if args.pair_kernel != "fp32" else ""),
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,

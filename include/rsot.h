@@ -391,10 +391,11 @@ typedef struct {
  * and target levels 0..L_nu (coarse to fine); at step l = 0..L_max the
  * problem (T_{i_s(l)}, nu^{i_t(l)}) with i_s = max(0, l - (L_max - L_mu)),
  * i_t = max(0, l - (L_max - L_nu)) is solved at eps_levels[l] (L_max + 1
- * values) by rsot_solve with `opt` (its eps-schedule applies to step 0 only);
- * the potential moves to the next step by softmax refinement when i_t
- * increases and by injection otherwise.  psi_out: host, n of the finest
- * target level.
+ * values) by rsot_solve with `opt` (its eps-schedule applies to step 0 only;
+ * steps before the last only warm-start the next one and stop at
+ * max(tol_l1, mixed_tol_l1) without FP64 refinement); the potential moves to
+ * the next step by softmax refinement when i_t increases and by injection
+ * otherwise.  psi_out: host, n of the finest target level.
  */
 rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n_tgt,
                                   const rsot_target_level *tgt, const double *eps_levels,

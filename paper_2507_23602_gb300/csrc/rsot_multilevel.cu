@@ -260,6 +260,12 @@ rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n
         rsot_options o = *opt;
         o.eps = eps;
         if (l > 0) o.eps_start = 0.0;   // later levels start warm at their own eps
+        if (l < Lmax) {
+            // coarser levels only provide the warm start of the next one: mixed
+            // evaluations, stopped at the mixed tolerance (no FP64 refinement)
+            o.refine_fp64 = 0;
+            o.tol_l1 = std::max(opt->tol_l1, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5);
+        }
         rsot_solve_stats ss;
         s = rsot_solve(p, psi.data(), &o, &ss);
         rsot_destroy(p);
