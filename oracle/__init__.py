@@ -57,6 +57,11 @@ def _load():
         lib.oracle_point_lse.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
                                          dp, dp, ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_threads_used.argtypes = [ctypes.c_int]
+        lib.oracle_transport_maps.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
+                                              dp, dp, ctypes.c_double, ctypes.c_int, dp,
+                                              ctypes.POINTER(ctypes.c_int64)]
+        lib.oracle_centroids.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp,
+                                         dp, dp, ctypes.c_double, dp, dp]
         _lib = lib
     return _lib
 
@@ -151,3 +156,45 @@ def softmax_refine(x, mass, y_coarse, nu_coarse, psi_coarse, y_fine, eps, thread
     if rc != 0:
         raise ValueError("oracle_softmax_refine failed")
     return out
+
+
+def transport_maps(x, y, nu, psi, eps, threads=0):
+    """Sec. 6.3: barycentric map T_bary(x_q) = sum_j p_qj y_j (Eq.
+    barycentric_map_registration) and modal assignment j*(q) = argmax_j s_qj
+    (Eq. modal_map_registration, first maximum on ties).  Returns (T_bary [nq, d],
+    jstar [nq] int64)."""
+    lib = _load()
+    x, xp = _f64(x)
+    y, yp = _f64(y)
+    nu, nup = _f64(nu)
+    psi, pp = _f64(psi)
+    nq, d = x.shape
+    T = np.zeros((nq, d))
+    js = np.zeros(nq, dtype=np.int64)
+    rc = lib.oracle_transport_maps(d, nq, xp, y.shape[0], yp, nup, pp, float(eps), int(threads),
+                                   T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   js.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc:
+        raise ValueError(f"oracle_transport_maps failed ({rc})")
+    return T, js
+
+
+def centroids(x, mass, y, nu, psi, eps):
+    """Eq. barycenter_fixed_point: T_j = (1/nu_j) sum_q m_q p_qj x_q and the
+    transported mass a_j = sum_q m_q p_qj.  Returns (T [n, d], a [n])."""
+    lib = _load()
+    x, xp = _f64(x)
+    mass, mp = _f64(mass)
+    y, yp = _f64(y)
+    nu, nup = _f64(nu)
+    psi, pp = _f64(psi)
+    nq, d = x.shape
+    n = y.shape[0]
+    T = np.zeros((n, d))
+    a = np.zeros(n)
+    rc = lib.oracle_centroids(d, nq, xp, mp, n, yp, nup, pp, float(eps),
+                              T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc:
+        raise ValueError(f"oracle_centroids failed ({rc})")
+    return T, a

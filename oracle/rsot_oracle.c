@@ -315,3 +315,98 @@ int oracle_softmax_refine(int d, int64_t nq, const double *x, const double *mass
     free(lnS);
     return 0;
 }
+
+/*
+ * Transport maps of Sec. 6.3 for every quadrature point (dense):
+ *   T_bary(x_q) = sum_j p_qj y_j        (Eq. barycentric_map_registration)
+ *   j*(q)       = argmax_j s_qj,  s_qj = (psi_j - c(x_q, y_j))/eps + ln nu_j
+ *                                       (Eq. modal_map_registration; the
+ *                                       first maximal j on ties)
+ * p_qj is the plan density of Eq. final_plan_density, max-shifted; the
+ * weighted sum uses Neumaier compensation per coordinate.
+ * Outputs: Tbary[q*d + k] (may be NULL), jstar[q] (may be NULL).
+ */
+int oracle_transport_maps(int d, int64_t nq, const double *x, int64_t n, const double *y,
+                          const double *nu, const double *psi, double eps, int threads,
+                          double *Tbary, int64_t *jstar)
+{
+    if (d < 1 || d > 3 || n < 1 || !(eps > 0.0))
+        return -1;
+    int T = nthreads_of(threads);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static)
+#endif
+    for (int64_t q = 0; q < nq; ++q) {
+        double smax = -INFINITY;
+        int64_t arg = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            double s = (psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]);
+            if (s > smax) {
+                smax = s;
+                arg = j;
+            }
+        }
+        if (jstar)
+            jstar[q] = arg;
+        if (!Tbary)
+            continue;
+        nsum_t S = {0.0, 0.0}, W[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        for (int64_t j = 0; j < n; ++j) {
+            double e = exp((psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]) - smax);
+            nadd(&S, e);
+            for (int k = 0; k < d; ++k)
+                nadd(&W[k], e * y[j * d + k]);
+        }
+        for (int k = 0; k < d; ++k)
+            Tbary[q * d + k] = nval(&W[k]) / nval(&S);
+    }
+    return 0;
+}
+
+/*
+ * Conditional centroids of the plan (Eq. barycenter_fixed_point):
+ *   T_j = (1/nu_j) sum_q m_q p_qj x_q,   and the transported mass
+ *   a_j = sum_q m_q p_qj (= nu_j at the optimum, Eq. gradient_compact_expanded).
+ * Dense.  Outputs: T[j*d + k], a[j] (may be NULL).
+ */
+int oracle_centroids(int d, int64_t nq, const double *x, const double *mass, int64_t n,
+                     const double *y, const double *nu, const double *psi, double eps,
+                     double *Tc, double *a_out)
+{
+    if (d < 1 || d > 3 || n < 1 || !(eps > 0.0))
+        return -1;
+    nsum_t *A = (nsum_t *)calloc((size_t)n * 4, sizeof(nsum_t));
+    double *row = (double *)malloc((size_t)n * sizeof(double));
+    if (!A || !row) {
+        free(A);
+        free(row);
+        return -2;
+    }
+    for (int64_t q = 0; q < nq; ++q) {
+        double smax = -INFINITY;
+        for (int64_t j = 0; j < n; ++j) {
+            row[j] = (psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]);
+            if (row[j] > smax)
+                smax = row[j];
+        }
+        nsum_t S = {0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j)
+            nadd(&S, exp(row[j] - smax));
+        const double lnS = smax + log(nval(&S));
+        for (int64_t j = 0; j < n; ++j) {
+            const double w = mass[q] * exp(row[j] - lnS);   /* m_q p_qj */
+            nadd(&A[j * 4 + 3], w);
+            for (int k = 0; k < d; ++k)
+                nadd(&A[j * 4 + k], w * x[q * d + k]);
+        }
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        for (int k = 0; k < d; ++k)
+            Tc[j * d + k] = nval(&A[j * 4 + k]) / nu[j];
+        if (a_out)
+            a_out[j] = nval(&A[j * 4 + 3]);
+    }
+    free(A);
+    free(row);
+    return 0;
+}
