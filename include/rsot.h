@@ -403,6 +403,55 @@ rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n
                                   rsot_multilevel_stats *stats);
 
 /* ---------------------------------------------------------------------------
+ * Transport maps, centroids and barycenters (Sec. 6.2-6.3).  Each runs one
+ * dense mixed evaluation at (psi, eps) and then one sum over its plan
+ * p_qj (Eq. final_plan_density), FP32 pair arithmetic, FP64 across tiles.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Transport maps of a plan (Sec. 6.3):
+ *   T_out[q*d + k] = T_bary(x_q)_k = sum_j p_qj y_jk   (Eq. barycentric_map_registration)
+ *   jstar_out[q]   = argmax_j p_qj                    (Eq. modal_map_registration;
+ *                    the modal map is y_{jstar}; ties in FP32 go to the lowest j)
+ * Either output may be NULL (not both); host or device memory.
+ * Errors: RSOT_ERR_ARG, those of rsot_eval_dual_grad, RSOT_ERR_CUDA.
+ */
+rsot_status rsot_transport_maps(rsot_problem *p, const double *psi, double eps, double *T_out,
+                                int64_t *jstar_out);
+
+/*
+ * Conditional centroids of a plan (Eq. barycenter_fixed_point):
+ *   T_out[j*d + k] = (1/nu_j) sum_q m_q p_qj x_qk,  mass_out[j] = sum_q m_q p_qj
+ * (mass_out may be NULL).  Host or device memory.
+ * Errors: RSOT_ERR_ARG, those of rsot_eval_dual_grad, RSOT_ERR_CUDA.
+ */
+rsot_status rsot_centroids(rsot_problem *p, const double *psi, double eps, double *T_out,
+                           double *mass_out);
+
+typedef struct {
+    int iterations;            /* Lloyd updates made                                */
+    int converged;             /* 1 when the last RMS displacement <= tol_rms       */
+    double rms_last;           /* RMS displacement of the last update               */
+    int solve_iters, solve_evals;   /* summed over all RSOT solves                  */
+    double seconds_solve, seconds_centroids, seconds_total;
+} rsot_barycenter_stats;
+
+/*
+ * Barycenter with fixed weights nu by the damped Lloyd iteration of Sec. 6.2
+ * (Eq. damped_lloyd): y <- (1 - theta) y + theta sum_i lambda_i T_i, T_i the
+ * centroids of the optimal plan between source i (src[i], K sources of one
+ * dimension d) and (y, nu), solved by rsot_solve with `opt` (its eps-schedule
+ * on the first iteration only; later solves start from the previous
+ * potential).  Stops when the RMS displacement sqrt(sum_j |dy_j|^2 / n) <=
+ * tol_rms or after max_iter updates.  y_inout: host, n*d; nu, lambda: host.
+ * Errors: RSOT_ERR_ARG, those of rsot_create / rsot_solve / rsot_centroids.
+ */
+rsot_status rsot_barycenter(int K, const rsot_source_level *src, const double *lambda,
+                            int64_t n, double *y_inout, const double *nu,
+                            const rsot_options *opt, double theta, int max_iter, double tol_rms,
+                            rsot_barycenter_stats *stats);
+
+/* ---------------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper): an MLP psi_j ~ f(theta,
  * y_j) of width W with three SiLU hidden layers and a linear head, BF16
  * weights/activations in its GEMMs, FP32 accumulation, FP32 master weights,

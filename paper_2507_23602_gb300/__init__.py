@@ -81,6 +81,13 @@ class _MLStats(ctypes.Structure):
                 ("total_seconds", ctypes.c_double)]
 
 
+class _BaryStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rms_last", ctypes.c_double),
+                ("solve_iters", ctypes.c_int), ("solve_evals", ctypes.c_int),
+                ("seconds_solve", ctypes.c_double), ("seconds_centroids", ctypes.c_double),
+                ("seconds_total", ctypes.c_double)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("J", ctypes.c_double), ("grad_l1", ctypes.c_double), ("iters", ctypes.c_int),
                 ("evals", ctypes.c_int), ("stages", ctypes.c_int), ("pairs", ctypes.c_int64),
@@ -161,6 +168,11 @@ def load():
     lib.rsot_multilevel_solve.argtypes = [ctypes.c_int, ctypes.POINTER(_SrcLevel), ctypes.c_int,
                                           ctypes.POINTER(_TgtLevel), dp, ctypes.POINTER(_Options),
                                           dp, ctypes.POINTER(_MLStats)]
+    lib.rsot_transport_maps.argtypes = [vp, vp, ctypes.c_double, vp, vp]
+    lib.rsot_centroids.argtypes = [vp, vp, ctypes.c_double, vp, vp]
+    lib.rsot_barycenter.argtypes = [ctypes.c_int, ctypes.POINTER(_SrcLevel), dp, ctypes.c_int64, dp,
+                                    dp, ctypes.POINTER(_Options), ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_double, ctypes.POINTER(_BaryStats)]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.rsot_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.rsot_mlp_destroy.argtypes = [vp]
@@ -291,6 +303,27 @@ class Problem:
         po, ko = _ptr(out)
         _check(self._lib.rsot_point_log_partition(self._h, po), "point_log_partition")
         return out
+
+    def transport_maps(self, psi, eps, bary=True, modal=True):
+        """Sec. 6.3: (T_bary [nq, d] or None, j* [nq] int64 or None); the modal
+        map is y[j*]."""
+        pp, kp = _ptr(psi)
+        T = np.empty((self.nq, self.d)) if bary else None
+        js = np.empty(self.nq, dtype=np.int64) if modal else None
+        _check(self._lib.rsot_transport_maps(self._h, pp, float(eps),
+                                             ctypes.c_void_p(T.ctypes.data) if bary else None,
+                                             ctypes.c_void_p(js.ctypes.data) if modal else None),
+               "transport_maps")
+        return T, js
+
+    def centroids(self, psi, eps):
+        """Eq. barycenter_fixed_point: (T [n, d], transported mass a [n])."""
+        pp, kp = _ptr(psi)
+        T = np.empty((self.n, self.d))
+        a = np.empty(self.n)
+        _check(self._lib.rsot_centroids(self._h, pp, float(eps), ctypes.c_void_p(T.ctypes.data),
+                                        ctypes.c_void_p(a.ctypes.data)), "centroids")
+        return T, a
 
     def softmax_refine(self, psi_coarse, eps, y_fine):
         """Initial potential on the targets y_fine from psi_coarse on this
@@ -554,3 +587,31 @@ class MLP:
         _check(self._lib.rsot_mlp_train_step(self._h, int(x.shape[0]), px, py, float(lr),
                                              ctypes.byref(loss)), "mlp_train_step")
         return loss.value
+
+
+def barycenter(sources, weights, y0, nu, theta=0.5, max_iter=50, tol_rms=1e-6,
+               options: Optional[SolveOptions] = None, raise_on_error=True, **kw):
+    """Damped Lloyd barycenter (Sec. 6.2, Eq. damped_lloyd): sources = list of
+    (x, mass) of one dimension, weights = lambda_i, y0 (n, d) the initial
+    support with fixed weights nu.  Returns (y, stats)."""
+    lib = load()
+    keep = []
+    S = (_SrcLevel * len(sources))()
+    for i, (x, m) in enumerate(sources):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        keep += [x, m]
+        S[i] = _SrcLevel(x.shape[1], x.shape[0], x.ctypes.data, m.ctypes.data)
+    lam = np.ascontiguousarray(weights, dtype=np.float64)
+    y = np.array(y0, dtype=np.float64, order="C", copy=True)
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    opts = options or SolveOptions(**kw)
+    o = opts._c()
+    st = _BaryStats()
+    rc = lib.rsot_barycenter(len(sources), S, _dp(lam), y.shape[0], _dp(y), _dp(nu), ctypes.byref(o),
+                             float(theta), int(max_iter), float(tol_rms), ctypes.byref(st))
+    if raise_on_error and rc != 0:
+        raise RsotError(rc, "barycenter")
+    stats = {f: getattr(st, f) for f, _ in _BaryStats._fields_}
+    stats["status"] = rc
+    return y, stats

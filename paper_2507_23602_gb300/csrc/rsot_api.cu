@@ -349,6 +349,62 @@ rsot_status rsot_point_log_partition(rsot_problem *p, double *L_out) {
     return RSOT_OK;
 }
 
+// Runs a dense mixed evaluation at (psi, eps) -- its records feed the maps and
+// centroid kernels -- then `what` (0: maps, 1: centroids) into device or host
+// outputs.
+static rsot_status plan_sums(rsot_problem *p, const double *psi, double eps, int what, double *T_out,
+                             int64_t *j_out, double *mass_out) {
+    double J = 0.0;
+    rsot_status s = rsot_eval_dual_grad(p, psi, eps, 0.0, RSOT_MIXED, &J, p->grad_dev, nullptr);
+    if (s) return s;
+    cudaStream_t st = p->stream;
+    const int64_t rows = what == 0 ? p->nq : p->n;
+    const size_t tb = (size_t)rows * p->d * sizeof(double);
+    const bool tdev = !T_out || is_device_ptr(T_out);
+    const bool jdev = !j_out || is_device_ptr(j_out);
+    const bool mdev = !mass_out || is_device_ptr(mass_out);
+    double *Td = tdev ? T_out : nullptr, *md = mdev ? mass_out : nullptr, *org = nullptr;
+    int64_t *jd = jdev ? j_out : nullptr;
+    cudaError_t e = cudaMallocAsync(&org, 3 * sizeof(double), st);
+    if (!e) e = cudaMemcpyAsync(org, p->origin, 3 * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (!e && !tdev) e = cudaMallocAsync(&Td, tb, st);
+    if (!e && !jdev) e = cudaMallocAsync(&jd, (size_t)rows * sizeof(int64_t), st);
+    if (!e && !mdev) e = cudaMallocAsync(&md, (size_t)rows * sizeof(double), st);
+    if (!e) {
+        trace_begin(p, what == 0 ? "maps" : "centroids");
+        e = what == 0 ? launch_maps(p, eps, Td, jd, org) : launch_centroids(p, Td, md, org);
+        trace_end(p);
+    }
+    if (!e && !tdev) e = cudaMemcpyAsync(T_out, Td, tb, cudaMemcpyDeviceToHost, st);
+    if (!e && !jdev) e = cudaMemcpyAsync(j_out, jd, (size_t)rows * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (!e && !mdev) e = cudaMemcpyAsync(mass_out, md, (size_t)rows * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (org) cudaFreeAsync(org, st);
+    if (!tdev && Td) cudaFreeAsync(Td, st);
+    if (!jdev && jd) cudaFreeAsync(jd, st);
+    if (!mdev && md) cudaFreeAsync(md, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) {
+        cudaGetLastError();
+        p->tr_open.clear();
+        p->tr_used = 0;
+        return from_cuda(e);
+    }
+    trace_collect(p);
+    return RSOT_OK;
+}
+
+rsot_status rsot_transport_maps(rsot_problem *p, const double *psi, double eps, double *T_out,
+                                int64_t *jstar_out) {
+    if (!p || !psi || (!T_out && !jstar_out) || !(eps > 0.0) || !isfinite(eps)) return RSOT_ERR_ARG;
+    return plan_sums(p, psi, eps, 0, T_out, jstar_out, nullptr);
+}
+
+rsot_status rsot_centroids(rsot_problem *p, const double *psi, double eps, double *T_out,
+                           double *mass_out) {
+    if (!p || !psi || !T_out || !(eps > 0.0) || !isfinite(eps)) return RSOT_ERR_ARG;
+    return plan_sums(p, psi, eps, 1, T_out, nullptr, mass_out);
+}
+
 rsot_status rsot_covering_cost(rsot_problem *p, double *C0_out) {
     if (!p || !C0_out) return RSOT_ERR_ARG;
     if (p->C0 < 0.0) {

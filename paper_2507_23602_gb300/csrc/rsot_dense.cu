@@ -1088,22 +1088,13 @@ void dense_free(rsot_problem *p) {
     cudaFree(p->lse_buf);
 }
 
-// Automatic choice of the pair kernel.  The tensor-core exponents carry a
-// random error of rms ~2e-5 (log2 units, at eps = 1e-3 magnitudes; measured
-// against exact sums) against ~5e-6 for the FP32 chain; a gradient entry
-// sum_q m_q p_qj then errs by ~ln2 2e-5 sqrt(sum_q (m_q p_qj)^2) <=
-// 1.4e-5 sqrt(m_max nu_max).  Below m_max nu_max = 2e-6 five such standard
-// deviations stay under 1e-7, a tenth of the per-entry bound of the mixed
-// path; smaller problems (few points or heavy targets) take the FP32 kernels.
-constexpr double kTcAuto = 2e-6;
-
 template <int D>
 static cudaError_t launch_mixed_d(rsot_problem *p, const double *psi, double eps, double *grad) {
     cudaStream_t st = p->stream;
     const int64_t n_p1 = round_up(p->n, P1_TS);
     // tensor-core passes by default; their FP32 kernels run as the fallback when
     // the prep or combine kernel finds an operand outside the f16 range (gate)
-    const bool tc = p->pair_kernel == 1 || (p->pair_kernel == 2 && p->m_max * p->nu_max <= kTcAuto);
+    const bool tc = use_tensor_pairs(p);
     int *gate = tc ? &p->res_dev->gate : nullptr;
     const int k1 = tc ? p->k1_tc : p->k1, chunk1 = tc ? p->chunk1_tc : p->chunk1;
     const int s2 = tc ? p->s2_tc : p->s2;

@@ -137,6 +137,19 @@ struct rsot_problem {
 
 namespace rsot {
 
+// Automatic choice of the pair kernel of the mixed passes.  The tensor-core
+// exponents carry a random error of rms ~2e-5 (log2 units, at eps = 1e-3
+// magnitudes; measured against exact sums) against ~5e-6 for the FP32 chain;
+// a gradient entry sum_q m_q p_qj then errs by ~ln2 2e-5 sqrt(sum_q (m_q
+// p_qj)^2) <= 1.4e-5 sqrt(m_max nu_max).  Below m_max nu_max = 2e-6 five such
+// standard deviations stay under 1e-7, a tenth of the per-entry bound of the
+// mixed path; smaller problems (few points or heavy targets) take the FP32
+// kernels.
+constexpr double kTcAuto = 2e-6;
+inline bool use_tensor_pairs(const rsot_problem *p) {
+    return p->pair_kernel == 1 || (p->pair_kernel == 2 && p->m_max * p->nu_max <= kTcAuto);
+}
+
 // ---- kernel tracing (rsot_api.cu) -------------------------------------------
 // trace_begin/trace_end bracket one launch with events on p->stream when
 // tracing is on; trace_collect (after a stream sync) accumulates durations.
@@ -158,6 +171,12 @@ cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out
 cudaError_t launch_point_L(rsot_problem *p, double *L_dev);
 cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double eps, int64_t nf,
                                   const double *yf_dev, double *out_dev);
+
+// ---- transport maps and centroids (rsot_maps.cu), after a dense mixed evaluation
+cudaError_t launch_maps(rsot_problem *p, double eps, double *T_dev, int64_t *j_dev,
+                        const double *origin_dev);
+cudaError_t launch_centroids(rsot_problem *p, double *T_dev, double *mass_dev,
+                             const double *origin_dev);
 
 // ---- truncated path (rsot_trunc.cu) ----------------------------------------
 cudaError_t trunc_eval(rsot_problem *p, const double *psi_dev, double eps, double radius,

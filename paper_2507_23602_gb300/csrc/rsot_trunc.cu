@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "rsot_internal.cuh"
+#include "rsot_tc.cuh"
 
 namespace rsot {
 
@@ -59,6 +60,12 @@ struct Grid {
     double *lse_s = nullptr;
     double *blockJ = nullptr;
     int nblk_comb = 0;
+    // tensor-core passes: block balls (centre, radius; radius < 0: no member),
+    // operand records in sorted order, per-target b_j, per-point shifts u_q
+    float4 *pball16 = nullptr, *pball8 = nullptr, *tball16 = nullptr, *tball8 = nullptr;
+    Rec16 *prec_s = nullptr, *trec_s = nullptr;
+    float *b_s = nullptr, *u_s = nullptr;
+    int slots1_tc = 0, slots2_tc = 0;
 };
 
 namespace {
@@ -203,6 +210,45 @@ __global__ void k_tile_boxes(const double *__restrict__ c64s, int64_t cnt, int d
     }
 }
 
+
+// Bounding ball (centre, radius; radius -1 for a block without members) of
+// each run of B consecutive sorted members, from the FP64 copies (translated
+// coordinates, [cnt_pad][d]).  The radius is the half diagonal of the block's
+// box, rounded up by 1e-6 relative.
+__global__ void k_block_balls(const double *__restrict__ c64s, int64_t cnt, int d, int B,
+                              int64_t nblocks, float4 *__restrict__ ball) {
+    const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bi >= nblocks) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const int64_t a = bi * B, e = min((bi + 1) * B, cnt);
+    for (int64_t q = a; q < e; ++q)
+        for (int k = 0; k < d; ++k) {
+            lo[k] = fmin(lo[k], c64s[q * d + k]);
+            hi[k] = fmax(hi[k], c64s[q * d + k]);
+        }
+    if (a >= e) {
+        ball[bi] = make_float4(0.f, 0.f, 0.f, -1.f);
+        return;
+    }
+    double c[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        c[k] = 0.5 * (lo[k] + hi[k]);
+        r2 += 0.25 * (hi[k] - lo[k]) * (hi[k] - lo[k]);
+    }
+    ball[bi] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)(sqrt(r2) * (1.0 + 1e-6) + 1e-9));
+}
+
+// tensor-core point records of the sorted points (X = P x', rsot_tc.cuh)
+__global__ void k_point_recs_s(const float *__restrict__ xs, int64_t nqt, int d, float P,
+                               Rec16 *__restrict__ prec) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nqt) return;
+    float X[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) X[k] = k < d ? xs[k * nqt + q] * P : 0.0f;
+    prec[q] = make_point_rec(X, 0.0f);
+}
+
 // ------------------------------------------------------------- per evaluation
 // A_q = k |x'_q|^2 - k R^2 (FP32, computed once so that both passes agree)
 __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt, int d, float k,
@@ -293,7 +339,8 @@ __global__ void k_prep_trunc(const double *__restrict__ psi, const int *__restri
                              const double *__restrict__ y64s, const double *__restrict__ lnu_s,
                              int64_t n, int64_t nt, int d, double eps, Rec12 *__restrict__ tdup,
                              double *__restrict__ psinu_part, const double *__restrict__ nu_s,
-                             int *__restrict__ flags) {
+                             int *__restrict__ flags, Rec16 *__restrict__ trec, float *__restrict__ bs,
+                             double inv_P, int *__restrict__ gate) {
     __shared__ double sh[32];
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double psic = psi[0];
@@ -321,6 +368,24 @@ __global__ void k_prep_trunc(const double *__restrict__ psi, const int *__restri
         r.b = make_float4(w[2], w[2], c, c);
         r.c = make_float4(nb, nb, 0.f, 0.f);
         tdup[s] = r;
+        if (trec) {
+            // tensor-core operands (rsot_tc.cuh) and b_j (+inf for padding: the
+            // truncation test r - b_j > A_q then fails)
+            float W[3] = {0.f, 0.f, 0.f};
+            float C = -256.0f * TC_RANGE;
+            bool ok = true;
+            if (s < n) {
+                for (int t = 0; t < d; ++t) {
+                    W[t] = (float)(2.0 * k * y64s[s * d + t] * inv_P);
+                    ok = ok && fabsf(W[t]) < TC_RANGE;
+                }
+                C = fmaxf(c, -256.0f * TC_RANGE);
+                ok = ok && C < 256.0f * TC_RANGE;
+            }
+            if (!ok) atomicOr(gate, 1);
+            trec[s] = make_target_rec(W, C);
+            bs[s] = s < n ? -nb : INFINITY;
+        }
     }
     const double v = block_sum_d(contrib, sh);
     if (threadIdx.x == 0) psinu_part[blockIdx.x] = v;
@@ -366,7 +431,9 @@ __global__ void __launch_bounds__(L_THREADS, 3)
                 const Rec12 *__restrict__ tdup, const uint32_t *__restrict__ bits_pt, int tw,
                 const int *__restrict__ off1, int ptiles, int ch1, int *__restrict__ counter,
                 float2 *__restrict__ part1, unsigned long long *__restrict__ pairs,
-                int *__restrict__ flags) {
+                int *__restrict__ flags, const int *__restrict__ gate = nullptr) {
+    // as the fallback of the tensor-core pass, run only when the gate asks for it
+    if (gate && !(*gate & 1)) return;
     __shared__ __align__(128) Rec12 sm[2][TT];
     __shared__ __align__(8) uint64_t full[2];
     __shared__ int s_item, s_p, s_cnt, s_abort[2];
@@ -521,6 +588,432 @@ __global__ void __launch_bounds__(L_THREADS, 3)
     }
 }
 
+
+// -------------------------------------------------- tensor-core truncated passes
+// The pair exponents come from the mma of rsot_tc.cuh (bitwise the same in
+// both passes).  A block pair -- 16 points x 8 targets in pass 1, 16 targets x
+// 8 points in pass 2 -- is classified by the bounding balls of its blocks:
+// "outside" (every pair farther than the radius: skipped), "inside" (every
+// pair nearer: no test) or "boundary" (each pair tested, r_qj - b_j > A_q, in
+// FP32 on the mma result).  The classification margins (1e-4 R) exceed the
+// rounding of the pairwise test, so a classified pair gets the decision the
+// test would give and both passes sum over the same pairs.
+constexpr int TP_THREADS1 = 512;   // pass 1: 16 warps x 4 m-blocks x 16 points = PT
+constexpr int TP_THREADS2 = 128;   // pass 2: 4 warps x 4 m-blocks x 16 targets = TT
+constexpr int TP_PST = 256;        // points per pass-2 stage
+static_assert(TP_THREADS1 / 32 * TC_MB * 16 == PT, "pass-1 CTA covers a point tile");
+static_assert(TP_THREADS2 / 32 * TC_MB * 16 == TT, "pass-2 CTA covers a target tile");
+
+__device__ __forceinline__ int tp_class(float4 a, float4 b, float Rin, float Rout) {
+    if (a.w < 0.f || b.w < 0.f) return 0;
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float dist = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    if (dist - a.w - b.w >= Rout) return 0;
+    if (dist + a.w + b.w < Rin) return 1;
+    return 2;
+}
+
+// exponents of one block pair, shifted, with excluded pairs at -inf
+// (pass 1: rows = points with shifts ng / ng8 and tests against A of the row)
+__device__ __forceinline__ void tp_lse_pair(const unsigned (&a)[4], uint2 bf, int cls, float2 ng,
+                                            float2 ng8, float2 nbb, float Ag, float Ag8, float2 &e01,
+                                            float2 &e23, unsigned &cnt) {
+    float d[4];
+    mma_tc(d, a, bf);
+    e01 = __fadd2_rn(make_float2(d[0], d[1]), ng);
+    e23 = __fadd2_rn(make_float2(d[2], d[3]), ng8);
+    if (cls == 2) {
+        const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), nbb);
+        const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), nbb);
+        const bool i0 = v01.x > Ag, i1 = v01.y > Ag, i2 = v23.x > Ag8, i3 = v23.y > Ag8;
+        e01 = make_float2(i0 ? e01.x : -INFINITY, i1 ? e01.y : -INFINITY);
+        e23 = make_float2(i2 ? e23.x : -INFINITY, i3 ? e23.y : -INFINITY);
+        cnt += (unsigned)i0 + (unsigned)i1 + (unsigned)i2 + (unsigned)i3;
+    }
+}
+
+__global__ void __launch_bounds__(TP_THREADS1, 1)
+    k_lse_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
+                   const float4 *__restrict__ pball16, const Rec16 *__restrict__ trec,
+                   const float *__restrict__ bs, const float4 *__restrict__ tball8, float Rin,
+                   float Rout, const uint32_t *__restrict__ bits_pt, int tw,
+                   const int *__restrict__ off1, int ptiles, int ch1, int *__restrict__ counter,
+                   float2 *__restrict__ part1, unsigned long long *__restrict__ pairs,
+                   int *__restrict__ flags, const int *__restrict__ gate) {
+    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernel runs
+    __shared__ __align__(128) Rec16 s_rec[2][TT];
+    __shared__ __align__(16) float s_b[2][TT];
+    __shared__ __align__(16) float4 s_ball[2][TT / 8];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int s_item, s_p, s_cnt, s_abort[2];
+    __shared__ int s_list[MAX_CH];
+    __shared__ unsigned long long s_pairs;
+    constexpr unsigned kStage = TT * sizeof(Rec16) + TT * sizeof(float) + TT / 8 * sizeof(float4);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) mbar_init(&full[st], 1);
+        fence_barrier_init();
+        s_abort[0] = s_abort[1] = 0;
+        s_pairs = 0;
+    }
+    __syncthreads();
+    const int total = off1[ptiles];
+    unsigned git = 0;
+    unsigned long long mycnt = 0;
+    bool aborted = false;
+    const uint2 *pr = reinterpret_cast<const uint2 *>(prec);
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(counter, 1);
+            s_item = it;
+            if (it < total) {
+                const int pt = find_row(off1, ptiles, it);
+                s_p = pt;
+                s_cnt = collect_bits(bits_pt + (size_t)pt * tw, tw, (it - off1[pt]) * ch1, ch1, s_list);
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int pt = s_p, cnt = s_cnt;
+        if (tid == 0) {
+            for (int st = 0; st < 2 && st < cnt; ++st) {
+                const unsigned slot = (git + st) & 1u;
+                const int64_t tt = s_list[st];
+                mbar_expect_tx(&full[slot], kStage);
+                bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
+                bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
+                bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
+            }
+        }
+        const int64_t q0 = (int64_t)pt * PT + warp * (TC_MB * 16);
+        unsigned A[TC_MB][4];
+        float Ag[TC_MB], Ag8[TC_MB];
+        float2 M[TC_MB], Sf[TC_MB];
+        double2 Sd[TC_MB];
+        float4 pb[TC_MB];
+        unsigned rv[TC_MB];   // real rows among g, g + 8 (padding has A = +inf)
+#pragma unroll
+        for (int m = 0; m < TC_MB; ++m) {
+            const int64_t qb = q0 + m * 16;
+            load_a(A[m], pr[(qb + g) * 4 + t], pr[(qb + g + 8) * 4 + t]);
+            Ag[m] = Aq[qb + g];
+            Ag8[m] = Aq[qb + g + 8];
+            rv[m] = (unsigned)(Ag[m] < INFINITY) + (unsigned)(Ag8[m] < INFINITY);
+            pb[m] = pball16[qb / 16];
+            M[m] = make_float2(-INFINITY, -INFINITY);
+            Sf[m] = make_float2(0.f, 0.f);
+            Sd[m] = make_double2(0.0, 0.0);
+        }
+        unsigned icnt = 0;
+        for (int it = 0; it < cnt; ++it) {
+            const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
+            if (!mbar_wait(&full[slot], ph)) {
+                s_abort[it & 1] = 1;
+                atomicOr(flags, kErrTimeout);
+            } else {
+                const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
+                const float2 *bp = reinterpret_cast<const float2 *>(&s_b[slot][0]) + t;
+                const float4 *balls = &s_ball[slot][0];
+#pragma unroll 1
+                for (int grp = 0; grp < TT / 8 / TC_GROUP; ++grp) {
+                    float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        acc[m] = make_float2(0.f, 0.f);
+                        ng[m] = make_float2(-M[m].x, -M[m].x);
+                        ng8[m] = make_float2(-M[m].y, -M[m].y);
+                    }
+#pragma unroll 1
+                    for (int i = 0; i < TC_GROUP; ++i) {
+                        const int nb = grp * TC_GROUP + i;
+                        const float4 tb = balls[nb];
+                        int cls[TC_MB];
+                        bool any = false;
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) {
+                            cls[m] = tp_class(pb[m], tb, Rin, Rout);
+                            any = any || cls[m] != 0;
+                        }
+                        if (!any) continue;
+                        const uint2 bf = rec[32 * nb];
+                        const float2 bb = bp[4 * nb];
+                        const float2 nbb = make_float2(-bb.x, -bb.y);
+                        const unsigned cv = (unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY);
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) {
+                            if (cls[m] == 0) continue;
+                            float2 e01, e23;
+                            tp_lse_pair(A[m], bf, cls[m], ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01, e23,
+                                        icnt);
+                            if (cls[m] == 1) icnt += rv[m] * cv;
+                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                        }
+                    }
+                    bool bad = false;
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m)
+                        bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) ||
+                              (M[m].x == -INFINITY && acc[m].x != 0.f) ||
+                              (M[m].y == -INFINITY && acc[m].y != 0.f);
+                    if (__any_sync(0xffffffffu, bad)) {
+                        // exact redo of the group: maximum over the included pairs,
+                        // shifts raised, sums recomputed (pairs are not counted again)
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) {
+                            float mg = -INFINITY, mg8 = -INFINITY;
+                            unsigned dummy = 0;
+                            const float2 z = make_float2(0.f, 0.f);
+                            for (int i = 0; i < TC_GROUP; ++i) {
+                                const int nb = grp * TC_GROUP + i;
+                                const int c = tp_class(pb[m], balls[nb], Rin, Rout);
+                                if (c == 0) continue;
+                                const float2 bb = bp[4 * nb];
+                                float2 e01, e23;
+                                tp_lse_pair(A[m], rec[32 * nb], c, z, z, make_float2(-bb.x, -bb.y),
+                                            Ag[m], Ag8[m], e01, e23, dummy);
+                                mg = max3f(mg, e01.x, e01.y);
+                                mg8 = max3f(mg8, e23.x, e23.y);
+                            }
+                            if (mg > -INFINITY) {
+                                const float mn = ceilf(mg);
+                                if (mn > M[m].x) {
+                                    if (M[m].x != -INFINITY) {
+                                        Sf[m].x *= pow2_int_f(M[m].x - mn);
+                                        Sd[m].x *= pow2_int_d(M[m].x - mn);
+                                    }
+                                    M[m].x = mn;
+                                }
+                            }
+                            if (mg8 > -INFINITY) {
+                                const float mn = ceilf(mg8);
+                                if (mn > M[m].y) {
+                                    if (M[m].y != -INFINITY) {
+                                        Sf[m].y *= pow2_int_f(M[m].y - mn);
+                                        Sd[m].y *= pow2_int_d(M[m].y - mn);
+                                    }
+                                    M[m].y = mn;
+                                }
+                            }
+                            const float2 g1 = make_float2(-M[m].x, -M[m].x), g8 = make_float2(-M[m].y, -M[m].y);
+                            float2 a2 = make_float2(0.f, 0.f);
+                            for (int i = 0; i < TC_GROUP; ++i) {
+                                const int nb = grp * TC_GROUP + i;
+                                const int c = tp_class(pb[m], balls[nb], Rin, Rout);
+                                if (c == 0) continue;
+                                const float2 bb = bp[4 * nb];
+                                float2 e01, e23;
+                                tp_lse_pair(A[m], rec[32 * nb], c, g1, g8, make_float2(-bb.x, -bb.y),
+                                            Ag[m], Ag8[m], e01, e23, dummy);
+                                a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                                a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                            }
+                            acc[m] = a2;
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
+                }
+            }
+            __syncthreads();
+            aborted = s_abort[it & 1] != 0;
+            if (aborted) break;
+            if (tid == 0 && it + 2 < cnt) {
+                const int64_t tt = s_list[it + 2];
+                mbar_expect_tx(&full[slot], kStage);
+                bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
+                bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
+                bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
+            }
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) {
+                Sd[m].x += (double)Sf[m].x;
+                Sd[m].y += (double)Sf[m].y;
+                Sf[m] = make_float2(0.f, 0.f);
+            }
+        }
+        if (aborted) break;
+        git += cnt;
+        mycnt += icnt;
+        // merge the 4 lanes of each row (common shift = their maximum)
+#pragma unroll
+        for (int m = 0; m < TC_MB; ++m) {
+            float mx = M[m].x, my = M[m].y;
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 1));
+            my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 2));
+            double sx = M[m].x == -INFINITY ? 0.0 : Sd[m].x * pow2_int_d(M[m].x - mx);
+            double sy = M[m].y == -INFINITY ? 0.0 : Sd[m].y * pow2_int_d(M[m].y - my);
+            sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+            sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+            sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+            sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+            if (m == t) {
+                const int l = warp * (TC_MB * 16) + m * 16 + g;
+                float2 *o = part1 + (int64_t)item * PT;
+                o[l] = mx == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(mx, (float)sx);
+                o[l + 8] = my == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(my, (float)sy);
+            }
+        }
+        __syncthreads();
+    }
+    atomicAdd(&s_pairs, mycnt);
+    __syncthreads();
+    if (tid == 0) {
+        if (s_pairs) atomicAdd(pairs, s_pairs);
+        if (aborted) {   // bounded drain of copies that may still be in flight
+            for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TP_THREADS2)
+    k_grad_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
+                    const float *__restrict__ us, const float4 *__restrict__ pball8,
+                    const Rec16 *__restrict__ trec, const float *__restrict__ bs,
+                    const float4 *__restrict__ tball16, float Rin, float Rout,
+                    const uint32_t *__restrict__ bits_tp, int pw, const int *__restrict__ off2,
+                    int ttiles, int ch2, int *__restrict__ counter, double *__restrict__ part2,
+                    int *__restrict__ flags, const int *__restrict__ gate) {
+    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernel runs
+    __shared__ __align__(128) Rec16 s_rec[2][TP_PST];
+    __shared__ __align__(16) float s_u[2][TP_PST];
+    __shared__ __align__(16) float s_A[2][TP_PST];
+    __shared__ __align__(16) float4 s_ball[2][TP_PST / 8];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int s_item, s_t, s_cnt, s_abort[2];
+    __shared__ int s_list[MAX_CH];
+    constexpr unsigned kStage = TP_PST * (sizeof(Rec16) + 2 * sizeof(float)) + TP_PST / 8 * sizeof(float4);
+    constexpr int SPT = PT / TP_PST;   // stages per point tile
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) mbar_init(&full[st], 1);
+        fence_barrier_init();
+        s_abort[0] = s_abort[1] = 0;
+    }
+    __syncthreads();
+    const int total = off2[ttiles];
+    unsigned git = 0;
+    bool aborted = false;
+    const uint2 *tr = reinterpret_cast<const uint2 *>(trec);
+    auto issue = [&](int st, unsigned slot) {
+        const int64_t q = (int64_t)s_list[st / SPT] * PT + (st % SPT) * TP_PST;
+        mbar_expect_tx(&full[slot], kStage);
+        bulk_g2s(s_rec[slot], prec + q, TP_PST * sizeof(Rec16), &full[slot]);
+        bulk_g2s(s_u[slot], us + q, TP_PST * sizeof(float), &full[slot]);
+        bulk_g2s(s_A[slot], Aq + q, TP_PST * sizeof(float), &full[slot]);
+        bulk_g2s(s_ball[slot], pball8 + q / 8, TP_PST / 8 * sizeof(float4), &full[slot]);
+    };
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(counter, 1);
+            s_item = it;
+            if (it < total) {
+                const int tt = find_row(off2, ttiles, it);
+                s_t = tt;
+                s_cnt = collect_bits(bits_tp + (size_t)tt * pw, pw, (it - off2[tt]) * ch2, ch2, s_list);
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int tt = s_t;
+        const int nst = SPT * s_cnt;
+        if (tid == 0)
+            for (int st = 0; st < 2 && st < nst; ++st) issue(st, (git + st) & 1u);
+        const int64_t j0 = (int64_t)tt * TT + warp * (TC_MB * 16);
+        unsigned A[TC_MB][4];
+        float2 bgg[TC_MB];   // (-b_g, -b_g) and (-b_g+8, -b_g+8) as two pairs
+        float2 bg8[TC_MB];
+        float4 tb[TC_MB];
+        double2 acc64[TC_MB];
+#pragma unroll
+        for (int m = 0; m < TC_MB; ++m) {
+            const int64_t jb = j0 + m * 16;
+            load_a(A[m], tr[(jb + g) * 4 + t], tr[(jb + g + 8) * 4 + t]);
+            const float b0 = bs[jb + g], b8 = bs[jb + g + 8];
+            bgg[m] = make_float2(-b0, -b0);
+            bg8[m] = make_float2(-b8, -b8);
+            tb[m] = tball16[jb / 16];
+            acc64[m] = make_double2(0.0, 0.0);
+        }
+        for (int it = 0; it < nst; ++it) {
+            const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
+            if (!mbar_wait(&full[slot], ph)) {
+                s_abort[it & 1] = 1;
+                atomicOr(flags, kErrTimeout);
+            } else {
+                const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
+                const float2 *up = reinterpret_cast<const float2 *>(&s_u[slot][0]) + t;
+                const float2 *ap = reinterpret_cast<const float2 *>(&s_A[slot][0]) + t;
+                float2 acc[TC_MB];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
+#pragma unroll 1
+                for (int nb = 0; nb < TP_PST / 8; ++nb) {
+                    const float4 pbl = s_ball[slot][nb];
+                    int cls[TC_MB];
+                    bool any = false;
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        cls[m] = tp_class(tb[m], pbl, Rin, Rout);
+                        any = any || cls[m] != 0;
+                    }
+                    if (!any) continue;
+                    const uint2 bf = rec[32 * nb];
+                    const float2 u = up[4 * nb];     // (u_2t, u_2t+1)
+                    const float2 Ac = ap[4 * nb];    // (A_2t, A_2t+1)
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        if (cls[m] == 0) continue;
+                        float d[4];
+                        mma_tc(d, A[m], bf);
+                        float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
+                        float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
+                        if (cls[m] == 2) {
+                            const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), bgg[m]);
+                            const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), bg8[m]);
+                            e01 = make_float2(v01.x > Ac.x ? e01.x : -INFINITY, v01.y > Ac.y ? e01.y : -INFINITY);
+                            e23 = make_float2(v23.x > Ac.x ? e23.x : -INFINITY, v23.y > Ac.y ? e23.y : -INFINITY);
+                        }
+                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    acc64[m].x += (double)acc[m].x;
+                    acc64[m].y += (double)acc[m].y;
+                }
+            }
+            __syncthreads();
+            aborted = s_abort[it & 1] != 0;
+            if (aborted) break;
+            if (tid == 0 && it + 2 < nst) issue(it + 2, slot);
+        }
+        if (aborted) break;
+        git += nst;
+#pragma unroll
+        for (int m = 0; m < TC_MB; ++m) {
+            double x = acc64[m].x, y = acc64[m].y;
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            y += __shfl_xor_sync(0xffffffffu, y, 1);
+            y += __shfl_xor_sync(0xffffffffu, y, 2);
+            if (m == t) {
+                const int l = warp * (TC_MB * 16) + m * 16 + g;
+                part2[(int64_t)item * TT + l] = x;
+                part2[(int64_t)item * TT + l + 8] = y;
+            }
+        }
+        __syncthreads();
+    }
+    if (aborted && tid == 0)
+        for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
+}
+
 // ------------------------------------------------------------------ combine
 // Merge the item partials of each point; write pass-2 point-pair records
 // (x0a,x0b,x1a,x1b) (x2a,x2b,ua,ub) (Aa,Ab,0,0); sum m_q eps L_q over the
@@ -531,7 +1024,8 @@ __global__ void k_combine_trunc(const float2 *__restrict__ part1, const int *__r
                                 const double *__restrict__ lm2_s, const float *__restrict__ Aq,
                                 const double *__restrict__ psi, double eps, int d,
                                 Rec12 *__restrict__ ppair, double *__restrict__ lse_s,
-                                double *__restrict__ blockJ, EvalResult *__restrict__ res) {
+                                double *__restrict__ blockJ, EvalResult *__restrict__ res,
+                                float *__restrict__ u_s = nullptr) {
     __shared__ double sh[32];
     __shared__ int s_empty;
     if (threadIdx.x == 0) s_empty = 0;
@@ -575,6 +1069,7 @@ __global__ void k_combine_trunc(const float2 *__restrict__ part1, const int *__r
         r.b = make_float4(x[0][2], x[1][2], u[0], u[1]);
         r.c = make_float4(A[0], A[1], 0.f, 0.f);
         ppair[i] = r;
+        if (u_s) *reinterpret_cast<float2 *>(u_s + 2 * i) = make_float2(u[0], u[1]);
     }
     if (empty) atomicAdd(&s_empty, empty);
     const double s = block_sum_d(contrib, sh);
@@ -590,7 +1085,8 @@ __global__ void __launch_bounds__(G_THREADS)
     k_grad_trunc(const Rec12 *__restrict__ ppair, const Rec12 *__restrict__ tdup,
                  const uint32_t *__restrict__ bits_tp, int pw, const int *__restrict__ off2,
                  int ttiles, int ch2, int *__restrict__ counter, double *__restrict__ part2,
-                 int *__restrict__ flags) {
+                 int *__restrict__ flags, const int *__restrict__ gate = nullptr) {
+    if (gate && !(*gate & 1)) return;
     __shared__ __align__(128) Rec12 sm[2][G_STAGE];
     __shared__ __align__(8) uint64_t full[2];
     __shared__ int s_item, s_t, s_cnt, s_abort[2];
@@ -840,6 +1336,14 @@ static cudaError_t grid_build(rsot_problem *p) {
     ALLOC(g->part2, g->items2_max * TT);
     ALLOC(g->lse_s, g->nqt);
     ALLOC(g->blockJ, g->nblk_comb);
+    ALLOC(g->pball16, g->nqt / 16);
+    ALLOC(g->pball8, g->nqt / 8);
+    ALLOC(g->tball16, g->nt / 16);
+    ALLOC(g->tball8, g->nt / 8);
+    ALLOC(g->prec_s, g->nqt);
+    ALLOC(g->trec_s, g->nt);
+    ALLOC(g->b_s, g->nt);
+    ALLOC(g->u_s, g->nqt);
 #undef ALLOC
     k_gather_points<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(
         kq, p->nq, g->nqt, d, p->x64, p->mass, p->lmass2, g->perm_q, g->xs, g->x64, g->mass, g->lm2);
@@ -847,6 +1351,11 @@ static cudaError_t grid_build(rsot_problem *p) {
         kt, p->n, g->nt, d, p->y64, p->nu, p->lnu, g->perm_t, g->y64, g->nu, g->lnu);
     k_tile_boxes<<<(g->ptiles + 127) / 128, 128, 0, st>>>(g->x64, p->nq, d, PT, g->ptiles, g->pbox);
     k_tile_boxes<<<(g->ttiles + 127) / 128, 128, 0, st>>>(g->y64, p->n, d, TT, g->ttiles, g->tbox);
+    k_block_balls<<<(unsigned)((g->nqt / 16 + 127) / 128), 128, 0, st>>>(g->x64, p->nq, d, 16, g->nqt / 16, g->pball16);
+    k_block_balls<<<(unsigned)((g->nqt / 8 + 127) / 128), 128, 0, st>>>(g->x64, p->nq, d, 8, g->nqt / 8, g->pball8);
+    k_block_balls<<<(unsigned)((g->nt / 16 + 127) / 128), 128, 0, st>>>(g->y64, p->n, d, 16, g->nt / 16, g->tball16);
+    k_block_balls<<<(unsigned)((g->nt / 8 + 127) / 128), 128, 0, st>>>(g->y64, p->n, d, 8, g->nt / 8, g->tball8);
+    k_point_recs_s<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(g->xs, g->nqt, d, p->tc_P, g->prec_s);
     if ((e = cudaGetLastError())) return e;
     if ((e = cudaStreamSynchronize(st))) return e;
     cudaFree(kq);
@@ -855,6 +1364,8 @@ static cudaError_t grid_build(rsot_problem *p) {
     const void *f2 = d == 3 ? (const void *)k_grad_trunc<3> : (const void *)k_grad_trunc<2>;
     g->slots1 = p->num_sms * occupancy_of(f1, L_THREADS);
     g->slots2 = p->num_sms * occupancy_of(f2, G_THREADS);
+    g->slots1_tc = p->num_sms * occupancy_of((const void *)k_lse_trunc_tc, TP_THREADS1);
+    g->slots2_tc = p->num_sms * occupancy_of((const void *)k_grad_trunc_tc, TP_THREADS2);
     return cudaSuccess;
 }
 
@@ -876,25 +1387,47 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     k_item_offsets<<<1, 64, 0, st>>>(g->cnt1, g->ptiles, g->ch1, g->cnt2, g->ttiles, g->ch2, g->off1,
                                      g->off2, g->counters);
     const int nbp = (int)((g->nt + 255) / 256);
+    // tensor-core passes (the automatic choice of the dense path), FP32 passes as
+    // their fallback when an operand leaves the f16 range (gate)
+    const bool tc = use_tensor_pairs(p);
+    int *gate = tc ? &p->res_dev->gate : nullptr;
     k_prep_trunc<<<nbp, 256, 0, st>>>(psi, g->perm_t, g->y64, g->lnu, p->n, g->nt, D, eps, g->tdup,
-                                      p->psinu, g->nu, p->flags);
+                                      p->psinu, g->nu, p->flags, tc ? g->trec_s : nullptr, g->b_s,
+                                      1.0 / (double)p->tc_P, gate);
     trace_end(p);
+    unsigned long long *pairs = reinterpret_cast<unsigned long long *>(&p->res_dev->pairs);
+    // pairs at distance < Rin are inside the radius and pairs at >= Rout outside
+    // it for the pairwise FP32 test too (its rounding is far below 1e-4 R)
+    const float Rin = (float)(radius * (1.0 - 1e-4) - 1e-6), Rout = (float)(radius * (1.0 + 1e-4) + 1e-6);
+    if (tc) {
+        trace_begin(p, "lse_trunc_tc");
+        k_lse_trunc_tc<<<g->slots1_tc, TP_THREADS1, 0, st>>>(
+            g->prec_s, g->Aq, g->pball16, g->trec_s, g->b_s, g->tball8, Rin, Rout, g->bits_pt, g->tw,
+            g->off1, g->ptiles, g->ch1, g->counters, g->part1, pairs, p->flags, gate);
+        trace_end(p);
+    }
     trace_begin(p, "lse_trunc_mixed");
     k_lse_trunc<D><<<g->slots1, L_THREADS, 0, st>>>(g->xs, g->nqt, g->Aq, g->tdup, g->bits_pt, g->tw,
                                                     g->off1, g->ptiles, g->ch1, g->counters,
-                                                    g->part1,
-                                                    reinterpret_cast<unsigned long long *>(&p->res_dev->pairs),
-                                                    p->flags);
+                                                    g->part1, pairs, p->flags, gate);
     trace_end(p);
     trace_begin(p, "combine_trunc_mixed");
     k_combine_trunc<<<g->nblk_comb, 256, 0, st>>>(g->part1, g->off1, p->nq, g->nqt, g->xs, g->x64,
                                                   g->mass, g->lm2, g->Aq, psi, eps, D, g->ppair,
-                                                  g->lse_s, g->blockJ, p->res_dev);
+                                                  g->lse_s, g->blockJ, p->res_dev,
+                                                  tc ? g->u_s : nullptr);
     trace_end(p);
+    if (tc) {
+        trace_begin(p, "grad_trunc_tc");
+        k_grad_trunc_tc<<<g->slots2_tc, TP_THREADS2, 0, st>>>(
+            g->prec_s, g->Aq, g->u_s, g->pball8, g->trec_s, g->b_s, g->tball16, Rin, Rout,
+            g->bits_tp, g->pw, g->off2, g->ttiles, g->ch2, g->counters + 1, g->part2, p->flags, gate);
+        trace_end(p);
+    }
     trace_begin(p, "grad_trunc_mixed");
     k_grad_trunc<D><<<g->slots2, G_THREADS, 0, st>>>(g->ppair, g->tdup, g->bits_tp, g->pw, g->off2,
                                                      g->ttiles, g->ch2, g->counters + 1, g->part2,
-                                                     p->flags);
+                                                     p->flags, gate);
     trace_end(p);
     trace_begin(p, "finalize_trunc");
     k_finalize_grad_trunc<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(g->part2, g->off2, p->n,
@@ -930,7 +1463,9 @@ void trunc_free(rsot_problem *p) {
     if (!g) return;
     void *ptrs[] = {g->perm_q, g->perm_t, g->xs, g->x64, g->mass, g->lm2, g->y64, g->nu, g->lnu,
                     g->pbox, g->tbox, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2, g->off1, g->off2,
-                    g->counters, g->Aq, g->tdup, g->ppair, g->part1, g->part2, g->lse_s, g->blockJ};
+                    g->counters, g->Aq, g->tdup, g->ppair, g->part1, g->part2, g->lse_s, g->blockJ,
+                    g->pball16, g->pball8, g->tball16, g->tball8, g->prec_s, g->trec_s, g->b_s,
+                    g->u_s};
     for (void *q : ptrs) cudaFree(q);
     delete g;
     p->grid = nullptr;

@@ -34,20 +34,44 @@ def case(seed, d, nq, n, eps, scale):
     return x, m, y, nu, scale * rng.standard_normal(n), eps
 
 
+def tensor_tols(m, nu, eps, Jo):
+    """Bounds of the tensor-core pair kernel forced onto any problem (its
+    exponents err by rms ~2e-5 in log2 units): five standard deviations of the
+    resulting gradient / J errors, never below the mixed path's own bounds."""
+    g_tol = max(1e-6, 5 * 1.4e-5 * math.sqrt(m.max() * nu.max()))
+    j_tol = max(1e-5 * abs(Jo), 5 * eps * math.log(2) * 2e-5 * math.sqrt(np.sum(m * m)))
+    return g_tol, j_tol
+
+
 def compare(P, x, m, y, nu, psi, eps, radius, precs=(1, 0), allow_empty=False):
+    """The FP64 path, and the mixed path with the automatic, FP32 and forced
+    tensor-core pair kernels, against the oracle's truncated evaluation."""
     C = 0.5 * radius * radius
     Jo, go, po, eo = oracle.dual_grad(x, m, y, nu, psi, eps, cutoff=C)
     out = {}
-    for prec in precs:
-        J, g, pairs = P.eval(psi, eps, radius, prec, allow_empty=allow_empty)
-        assert abs(pairs - po) <= 16 + 1e-6 * po, (pairs, po)
-        if prec == 0:
-            assert abs(J - Jo) <= 1e-10 * abs(Jo)
-            assert np.max(np.abs(g - go)) <= 1e-10 * max(np.max(np.abs(go)), np.max(nu))
-        else:
-            assert abs(J - Jo) <= 1e-5 * abs(Jo), (J, Jo)
-            assert np.max(np.abs(g - go)) <= 1e-6
-        out[prec] = (J, g, pairs)
+    runs = [(prec, kind) for prec in precs
+            for kind in ((None,) if prec == 0 else
+                         (rs().PAIRS_AUTO, rs().PAIRS_FP32, rs().PAIRS_TENSOR))]
+    try:
+        for prec, kind in runs:
+            if kind is not None:
+                P.set_pair_kernel(kind)
+            J, g, pairs = P.eval(psi, eps, radius, prec, allow_empty=allow_empty)
+            assert abs(pairs - po) <= 16 + 1e-6 * po, (kind, pairs, po)
+            if prec == 0:
+                assert abs(J - Jo) <= 1e-10 * abs(Jo)
+                assert np.max(np.abs(g - go)) <= 1e-10 * max(np.max(np.abs(go)), np.max(nu))
+            elif kind == rs().PAIRS_TENSOR:
+                g_tol, j_tol = tensor_tols(m, nu, eps, Jo)
+                assert abs(J - Jo) <= j_tol, (J, Jo, j_tol)
+                assert np.max(np.abs(g - go)) <= g_tol, (np.max(np.abs(g - go)), g_tol)
+            else:
+                assert abs(J - Jo) <= 1e-5 * abs(Jo), (kind, J, Jo)
+                assert np.max(np.abs(g - go)) <= 1e-6, (kind, np.max(np.abs(g - go)))
+            if kind in (None, rs().PAIRS_AUTO):
+                out[prec] = (J, g, pairs)
+    finally:
+        P.set_pair_kernel(rs().PAIRS_AUTO)
     return out, (Jo, go, po, eo)
 
 
@@ -147,5 +171,11 @@ def test_trunc_full_size_against_dense_gpu():
         assert abs(Jt - Jd) <= 1e-5 * abs(Jd)
         assert np.max(np.abs(gt - gd)) <= 1e-6
         assert abs(gt.sum()) <= 5e-7
+        # the FP32 truncated kernels count the same pairs up to boundary rounding
+        P.set_pair_kernel(rs().PAIRS_FP32)
+        Jf, gf, pf = P.eval(psi, p.eps, R, 1)
+        assert abs(pf - pt) <= 1e-6 * pt
+        assert abs(Jf - Jt) <= 1e-5 * abs(Jt)
+        assert np.max(np.abs(gf - gt)) <= 1e-6
     finally:
         P.close()
