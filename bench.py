@@ -56,7 +56,8 @@ def parse():
                     help="dense workload: pair kernel of the timed evaluations")
     ap.add_argument("--tail", type=float, default=0.0,
                     help="multilevel: truncation tail of every evaluation (0: dense)")
-    ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart"],
+    ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart",
+                                           "maps", "barycenter"],
                     default="dense",
                     help="dense: dual+grad throughput (default); the others time solves")
     ap.add_argument("--problems", type=int, default=32, help="batch: problems (seeds 1000..)")
@@ -305,6 +306,51 @@ def run_solve_workloads(args):
                    {"kmeans_seconds": t_km, "stats": st, "tail": args.tail,
                     "levels_points": [s[0].shape[0] for s in src],
                     "levels_targets": [t2[0].shape[0] for t2 in levels]}, args)
+        return
+    if args.workload == "maps":
+        # transport maps (Sec. 6.3) and conditional centroids (Eq. barycenter_fixed_point)
+        p = ri.cube_3d(mesh_n=args.mesh, n_targets=args.targets, eps=args.eps)
+        psi = 0.005 * np.random.default_rng(2024).standard_normal(p.n)
+        P = rs.Problem(p.x, p.mass, p.y, p.nu)
+        for _ in range(max(1, args.warmup)):
+            P.transport_maps(psi, p.eps)
+            P.centroids(psi, p.eps)
+        P.kernel_timing(True)
+        for _ in range(args.steps):
+            P.transport_maps(psi, p.eps)
+            P.centroids(psi, p.eps)
+        kt = {k: v[0] / v[1] for k, v in P.kernel_times().items()}
+        P.kernel_timing(False)
+        P.close()
+        pairs = p.nq * p.n
+        out = {"metric": "transport maps G pairs/s (T_bary and modal map in one pass)",
+               "value": pairs / (kt["maps"] * 1e-3) / 1e9, "unit": "G pairs/s", "n_gpus": 1,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": kt["maps"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": {"workload": f"cube-{p.nq}x{p.n}-maps-eps{args.eps:g}"},
+               "centroids": {"value": pairs / (kt["centroids"] * 1e-3) / 1e9, "unit": "G pairs/s",
+                             "ms": kt["centroids"]},
+               "per_kernel_ms": kt}
+        print(json.dumps(out))
+        return
+    if args.workload == "barycenter":
+        # damped Lloyd barycenter (Sec. 6.2) of three 3-D mixture sources on 16^3 tet meshes
+        v, c = ri.unit_cube_tet_mesh(16)
+        srcs = []
+        for s in range(3):
+            mix = ri.random_mixture(3, 3, 40 + s)
+            srcs.append(ri.source_measure(v, c, ri.tet_rule_deg2(), ri.mixture_density(mix, v)))
+        n = 4096
+        y0 = np.random.default_rng(43).uniform(0.25, 0.75, (n, 3))
+        nu = np.full(n, 1.0 / n)
+        t = time.perf_counter()
+        y, st = rs.barycenter(srcs, np.full(3, 1.0 / 3), y0, nu, theta=0.5, max_iter=30,
+                              tol_rms=1e-4, eps=2e-3, eps_start=0.1, tol_l1=1e-6,
+                              raise_on_error=False)
+        wall = time.perf_counter() - t
+        solve_line("barycenter wall time (damped Lloyd, 3 sources x 98,304 points, 4,096 support points)",
+                   wall, "s", "barycenter-3x98304-4096-eps0.002",
+                   {"stats": st, "seconds_per_iteration": wall / max(1, st["iterations"])}, args)
         return
     if args.workload == "warmstart":
         from paper_2507_23602_gb300 import warmstart as ws

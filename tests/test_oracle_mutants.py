@@ -102,3 +102,89 @@ def test_unmutated_oracle_passes_compact_pins():
 def test_mutant_is_caught(name):
     lpath = _build_mutant(name)
     assert not _pins_pass(_mutant_dual_grad(lpath)), f"mutant {name} passed every pin"
+
+
+# ---- transport maps and centroids (Sec. 6.2-6.3) ---------------------------
+MUTANTS_MAPS = {
+    "maps_drop_ln_nu": ("            double s = (psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]);\n            if (s > smax) {",
+                        "            double s = (psi[j] - cost(d, x + q * d, y + j * d)) / eps;\n            if (s > smax) {"),
+    "maps_wrong_coordinate": ("nadd(&W[k], e * y[j * d + k]);", "nadd(&W[k], e * y[j * d]);"),
+    "maps_last_maximum_on_ties": ("            if (s > smax) {\n                smax = s;\n                arg = j;",
+                                  "            if (s >= smax) {\n                smax = s;\n                arg = j;"),
+    "centroids_normalised_by_mass": ("Tc[j * d + k] = nval(&A[j * 4 + k]) / nu[j];",
+                                     "Tc[j * d + k] = nval(&A[j * 4 + k]) / nval(&A[j * 4 + 3]);"),
+    "centroids_mass_not_applied": ("const double w = mass[q] * exp(row[j] - lnS);",
+                                   "const double w = exp(row[j] - lnS) / (double)nq;"),
+    "centroids_target_coordinates": ("nadd(&A[j * 4 + k], w * x[q * d + k]);",
+                                     "nadd(&A[j * 4 + k], w * y[j * d + k]);"),
+}
+
+
+def _build_mutant_maps(name):
+    src = open(obuild.SRC).read()
+    old, new = MUTANTS_MAPS[name]
+    assert src.count(old) >= 1, name
+    src = src.replace(old, new, 1)
+    tmpd = tempfile.mkdtemp(prefix="oracle_mut_")
+    cpath = os.path.join(tmpd, "m.c")
+    lpath = os.path.join(tmpd, "libm.so")
+    open(cpath, "w").write(src)
+    subprocess.run(["gcc", "-std=c99", "-O1", "-fPIC", "-shared", cpath, "-o", lpath, "-lm"], check=True)
+    return lpath
+
+
+def _mutant_maps(lpath):
+    lib = ctypes.CDLL(lpath)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_transport_maps.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp, dp,
+                                          dp, ctypes.c_double, ctypes.c_int, dp, i64p]
+    lib.oracle_centroids.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp, dp,
+                                     dp, ctypes.c_double, dp, dp]
+    F = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    P = lambda a: a.ctypes.data_as(dp)
+
+    def transport_maps(x, y, nu, psi, eps, threads=1):
+        x, y, nu, psi = F(x), F(y), F(nu), F(psi)
+        T = np.zeros(x.shape)
+        js = np.zeros(x.shape[0], dtype=np.int64)
+        assert lib.oracle_transport_maps(x.shape[1], x.shape[0], P(x), y.shape[0], P(y), P(nu), P(psi),
+                                         eps, 1, P(T), js.ctypes.data_as(i64p)) == 0
+        return T, js
+
+    def centroids(x, mass, y, nu, psi, eps):
+        x, mass, y, nu, psi = F(x), F(mass), F(y), F(nu), F(psi)
+        T = np.zeros(y.shape)
+        a = np.zeros(y.shape[0])
+        assert lib.oracle_centroids(x.shape[1], x.shape[0], P(x), P(mass), y.shape[0], P(y), P(nu),
+                                    P(psi), eps, P(T), P(a)) == 0
+        return T, a
+    return transport_maps, centroids
+
+
+def _map_pins_pass(transport_maps, centroids):
+    import test_oracle_maps as T
+    orig = (oracle.transport_maps, oracle.centroids)
+    oracle.transport_maps, oracle.centroids = transport_maps, centroids
+    try:
+        checks = [T.test_single_target_maps_everything_to_it, T.test_two_targets_closed_form,
+                  T.test_coincident_targets, T.test_modal_map_is_nearest_target_for_zero_potential,
+                  T.test_maps_and_centroids_are_dual, T.test_centroids_of_a_point_mass]
+        for c in checks:
+            try:
+                c()
+            except AssertionError:
+                return False
+        return True
+    finally:
+        oracle.transport_maps, oracle.centroids = orig
+
+
+def test_unmutated_maps_pass_compact_pins():
+    assert _map_pins_pass(oracle.transport_maps, oracle.centroids)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_MAPS))
+def test_map_mutant_is_caught(name):
+    lpath = _build_mutant_maps(name)
+    assert not _map_pins_pass(*_mutant_maps(lpath)), f"mutant {name} passed every pin"
