@@ -398,8 +398,8 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     if (gate && (*gate & 1)) return;   // operands out of f16 range: the FP32 kernel runs
     extern __shared__ __align__(128) unsigned char tc_smem[];
     Rec16 (*sm)[TC_TS] = reinterpret_cast<Rec16 (*)[TC_TS]>(tc_smem);   // [TC_STAGES][TC_TS]
-    __shared__ __align__(8) uint64_t full[TC_STAGES];
-    __shared__ int s_abort[2];   // indexed by iteration parity
+    // full[s]: the stage's bytes landed; empty[s]: every warp is done with it
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
     const int64_t q0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
@@ -421,8 +421,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     }
 
     if (tid == 0) {
-        s_abort[0] = s_abort[1] = 0;
-        for (int s = 0; s < TC_STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TC_WARPS);
+        }
         fence_barrier_init();
     }
     __syncthreads();
@@ -435,14 +437,18 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     int issued = min(TC_STAGES, ntile);
     bool aborted = false;
     constexpr int NGRP = TC_NBS / TC_GROUP;
+    // no block barrier in the loop: each warp waits for the data of a stage and
+    // releases it; thread 0 refills a stage once all warps have released it
     for (int it = 0; it < ntile; ++it) {
         const int s = it % TC_STAGES;
         const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
-        const bool ok = mbar_wait(&full[s], ph);
-        if (!ok) {
-            s_abort[it & 1] = 1;
+        // warp-uniform decisions: the mma below needs every lane
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph))) {
             atomicOr(flags, kErrTimeout);
-        } else {
+            aborted = true;
+            break;
+        }
+        {
             const uint2 *base = reinterpret_cast<const uint2 *>(&sm[s][0]) + lane;
             float dc[TC_MB][4];
             {
@@ -494,14 +500,24 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
                 for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
             }
         }
-        __syncthreads();
-        aborted = s_abort[it & 1] != 0;
-        if (aborted) break;
-        if (tid == 0 && it + TC_STAGES < ntile) {
-            mbar_expect_tx(&full[s], TC_TS * sizeof(Rec16));
-            bulk_g2s(sm[s], trec + t_begin + (it + TC_STAGES) * TC_TS, TC_TS * sizeof(Rec16),
-                     &full[s]);
-            ++issued;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (warp == 0 && it + TC_STAGES < ntile) {
+            bool ok = true;
+            if (tid == 0) {
+                ok = mbar_wait(&empty[s], ph);
+                if (ok) {
+                    mbar_expect_tx(&full[s], TC_TS * sizeof(Rec16));
+                    bulk_g2s(sm[s], trec + t_begin + (it + TC_STAGES) * TC_TS,
+                             TC_TS * sizeof(Rec16), &full[s]);
+                    ++issued;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                atomicOr(flags, kErrTimeout);
+                aborted = true;
+                break;
+            }
         }
 #pragma unroll
         for (int m = 0; m < TC_MB; ++m) {
@@ -510,11 +526,12 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
             Sf[m] = make_float2(0.f, 0.f);
         }
     }
+    // a warp whose wait expired leaves without writing (the error flag is set);
+    // thread 0 drains its copies still in flight (bounded) before the CTA ends
     if (aborted) {
-        if (tid == 0) {
+        if (tid == 0)
             for (int it = 0; it < issued; ++it)
                 (void)mbar_wait(&full[it % TC_STAGES], (unsigned)(it / TC_STAGES) & 1u);
-        }
         return;
     }
     // merge the 4 lanes of each row: common shift = their maximum
@@ -561,8 +578,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     extern __shared__ __align__(128) unsigned char tc_smem[];
     Rec16 (*sm)[TC_TS] = reinterpret_cast<Rec16 (*)[TC_TS]>(tc_smem);   // [TC_STAGES][TC_TS]
     float (*su)[TC_TS] = reinterpret_cast<float (*)[TC_TS]>(tc_smem + TC_SMEM1);
-    __shared__ __align__(8) uint64_t full[TC_STAGES];
-    __shared__ int s_abort[2];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
     const int64_t j0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
@@ -580,8 +596,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     constexpr unsigned kStageBytes = TC_TS * sizeof(Rec16) + TC_TS * sizeof(float);
 
     if (tid == 0) {
-        s_abort[0] = s_abort[1] = 0;
-        for (int s = 0; s < TC_STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TC_WARPS);
+        }
         fence_barrier_init();
     }
     __syncthreads();
@@ -597,11 +615,12 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     for (int it = 0; it < ntile; ++it) {
         const int s = it % TC_STAGES;
         const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
-        const bool ok = mbar_wait(&full[s], ph);
-        if (!ok) {
-            s_abort[it & 1] = 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph))) {
             atomicOr(flags, kErrTimeout);
-        } else {
+            aborted = true;
+            break;
+        }
+        {
             const uint2 *base = reinterpret_cast<const uint2 *>(&sm[s][0]) + lane;
             const float2 *ub = reinterpret_cast<const float2 *>(&su[s][0]) + t;   // (u_2t, u_2t+1)
             float2 acc[TC_MB];
@@ -646,23 +665,32 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
                 acc64[m].y += (double)acc[m].y;
             }
         }
-        __syncthreads();
-        aborted = s_abort[it & 1] != 0;
-        if (aborted) break;
-        if (tid == 0 && it + TC_STAGES < ntile) {
-            mbar_expect_tx(&full[s], kStageBytes);
-            bulk_g2s(sm[s], prec + p_begin + (int64_t)(it + TC_STAGES) * TC_TS,
-                     TC_TS * sizeof(Rec16), &full[s]);
-            bulk_g2s(su[s], pu + p_begin + (int64_t)(it + TC_STAGES) * TC_TS,
-                     TC_TS * sizeof(float), &full[s]);
-            ++issued;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (warp == 0 && it + TC_STAGES < ntile) {
+            bool ok = true;
+            if (tid == 0) {
+                ok = mbar_wait(&empty[s], ph);
+                if (ok) {
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    bulk_g2s(sm[s], prec + p_begin + (int64_t)(it + TC_STAGES) * TC_TS,
+                             TC_TS * sizeof(Rec16), &full[s]);
+                    bulk_g2s(su[s], pu + p_begin + (int64_t)(it + TC_STAGES) * TC_TS,
+                             TC_TS * sizeof(float), &full[s]);
+                    ++issued;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                atomicOr(flags, kErrTimeout);
+                aborted = true;
+                break;
+            }
         }
     }
     if (aborted) {
-        if (tid == 0) {
+        if (tid == 0)
             for (int it = 0; it < issued; ++it)
                 (void)mbar_wait(&full[it % TC_STAGES], (unsigned)(it / TC_STAGES) & 1u);
-        }
         return;
     }
 #pragma unroll

@@ -242,6 +242,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // Bounded wait; false when the limit is reached (the caller records an error).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
     for (long long i = 0; i < kWaitLimit; ++i)
