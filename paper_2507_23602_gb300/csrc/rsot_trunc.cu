@@ -644,14 +644,17 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
     __shared__ __align__(128) Rec16 s_rec[2][TT];
     __shared__ __align__(16) float s_b[2][TT];
     __shared__ __align__(16) float4 s_ball[2][TT / 8];
-    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ int s_item, s_p, s_cnt, s_abort[2];
     __shared__ int s_list[MAX_CH];
     __shared__ unsigned long long s_pairs;
     constexpr unsigned kStage = TT * sizeof(Rec16) + TT * sizeof(float) + TT / 8 * sizeof(float4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
     if (tid == 0) {
-        for (int st = 0; st < 2; ++st) mbar_init(&full[st], 1);
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], TP_THREADS1 / 32);
+        }
         fence_barrier_init();
         s_abort[0] = s_abort[1] = 0;
         s_pairs = 0;
@@ -706,17 +709,34 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
             Sd[m] = make_double2(0.0, 0.0);
         }
         unsigned icnt = 0;
+        bool wabort = false;
+        // no block barrier per stage: warps release stages on `empty`, thread 0
+        // refills; decisions are warp-uniform (the mma needs every lane)
         for (int it = 0; it < cnt; ++it) {
             const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
-            if (!mbar_wait(&full[slot], ph)) {
-                s_abort[it & 1] = 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+                s_abort[0] = 1;
                 atomicOr(flags, kErrTimeout);
-            } else {
+                wabort = true;
+                break;
+            }
+            {
                 const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
                 const float2 *bp = reinterpret_cast<const float2 *>(&s_b[slot][0]) + t;
-                const float4 *balls = &s_ball[slot][0];
+                // classes of this warp's 4 point m-blocks against the stage's 32
+                // target n-blocks: lane l classifies n-block l (2 bits per m-block)
+                unsigned mycls = 0;
+                {
+                    const float4 tb = s_ball[slot][lane];
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m)
+                        mycls |= (unsigned)tp_class(pb[m], tb, Rin, Rout) << (2 * m);
+                }
+                const unsigned live = __ballot_sync(0xffffffffu, mycls != 0);
 #pragma unroll 1
                 for (int grp = 0; grp < TT / 8 / TC_GROUP; ++grp) {
+                    const unsigned gmask = (live >> (grp * TC_GROUP)) & ((1u << TC_GROUP) - 1u);
+                    if (!gmask) continue;
                     float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
 #pragma unroll
                     for (int m = 0; m < TC_MB; ++m) {
@@ -724,29 +744,20 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                         ng[m] = make_float2(-M[m].x, -M[m].x);
                         ng8[m] = make_float2(-M[m].y, -M[m].y);
                     }
-#pragma unroll 1
-                    for (int i = 0; i < TC_GROUP; ++i) {
-                        const int nb = grp * TC_GROUP + i;
-                        const float4 tb = balls[nb];
-                        int cls[TC_MB];
-                        bool any = false;
-#pragma unroll
-                        for (int m = 0; m < TC_MB; ++m) {
-                            cls[m] = tp_class(pb[m], tb, Rin, Rout);
-                            any = any || cls[m] != 0;
-                        }
-                        if (!any) continue;
+                    for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                        const int nb = grp * TC_GROUP + __ffs(gm) - 1;
+                        const unsigned cl = __shfl_sync(0xffffffffu, mycls, nb);
                         const uint2 bf = rec[32 * nb];
                         const float2 bb = bp[4 * nb];
                         const float2 nbb = make_float2(-bb.x, -bb.y);
                         const unsigned cv = (unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY);
 #pragma unroll
                         for (int m = 0; m < TC_MB; ++m) {
-                            if (cls[m] == 0) continue;
+                            const int c = (int)((cl >> (2 * m)) & 3u);
+                            if (c == 0) continue;
                             float2 e01, e23;
-                            tp_lse_pair(A[m], bf, cls[m], ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01, e23,
-                                        icnt);
-                            if (cls[m] == 1) icnt += rv[m] * cv;
+                            tp_lse_pair(A[m], bf, c, ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01, e23, icnt);
+                            if (c == 1) icnt += rv[m] * cv;
                             acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
                             acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
                         }
@@ -765,9 +776,9 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                             float mg = -INFINITY, mg8 = -INFINITY;
                             unsigned dummy = 0;
                             const float2 z = make_float2(0.f, 0.f);
-                            for (int i = 0; i < TC_GROUP; ++i) {
-                                const int nb = grp * TC_GROUP + i;
-                                const int c = tp_class(pb[m], balls[nb], Rin, Rout);
+                            for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                                const int nb = grp * TC_GROUP + __ffs(gm) - 1;
+                                const int c = (int)((__shfl_sync(0xffffffffu, mycls, nb) >> (2 * m)) & 3u);
                                 if (c == 0) continue;
                                 const float2 bb = bp[4 * nb];
                                 float2 e01, e23;
@@ -798,9 +809,9 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                             }
                             const float2 g1 = make_float2(-M[m].x, -M[m].x), g8 = make_float2(-M[m].y, -M[m].y);
                             float2 a2 = make_float2(0.f, 0.f);
-                            for (int i = 0; i < TC_GROUP; ++i) {
-                                const int nb = grp * TC_GROUP + i;
-                                const int c = tp_class(pb[m], balls[nb], Rin, Rout);
+                            for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                                const int nb = grp * TC_GROUP + __ffs(gm) - 1;
+                                const int c = (int)((__shfl_sync(0xffffffffu, mycls, nb) >> (2 * m)) & 3u);
                                 if (c == 0) continue;
                                 const float2 bb = bp[4 * nb];
                                 float2 e01, e23;
@@ -816,15 +827,26 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                     for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
                 }
             }
-            __syncthreads();
-            aborted = s_abort[it & 1] != 0;
-            if (aborted) break;
-            if (tid == 0 && it + 2 < cnt) {
-                const int64_t tt = s_list[it + 2];
-                mbar_expect_tx(&full[slot], kStage);
-                bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
-                bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
-                bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (warp == 0 && it + 2 < cnt) {
+                bool ok = true;
+                if (tid == 0) {
+                    ok = mbar_wait(&empty[slot], ph);
+                    if (ok) {
+                        const int64_t tt = s_list[it + 2];
+                        mbar_expect_tx(&full[slot], kStage);
+                        bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
+                        bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
+                        bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    s_abort[0] = 1;
+                    atomicOr(flags, kErrTimeout);
+                    wabort = true;
+                    break;
+                }
             }
 #pragma unroll
             for (int m = 0; m < TC_MB; ++m) {
@@ -833,10 +855,10 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                 Sf[m] = make_float2(0.f, 0.f);
             }
         }
-        if (aborted) break;
         git += cnt;
         mycnt += icnt;
         // merge the 4 lanes of each row (common shift = their maximum)
+if (!wabort) {
 #pragma unroll
         for (int m = 0; m < TC_MB; ++m) {
             float mx = M[m].x, my = M[m].y;
@@ -857,7 +879,12 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                 o[l + 8] = my == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(my, (float)sy);
             }
         }
-        __syncthreads();
+        }
+        __syncthreads();   // end of the item: every warp is past its stages
+        if (s_abort[0]) {
+            aborted = true;
+            break;
+        }
     }
     atomicAdd(&s_pairs, mycnt);
     __syncthreads();
@@ -882,14 +909,17 @@ __global__ void __launch_bounds__(TP_THREADS2)
     __shared__ __align__(16) float s_u[2][TP_PST];
     __shared__ __align__(16) float s_A[2][TP_PST];
     __shared__ __align__(16) float4 s_ball[2][TP_PST / 8];
-    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ int s_item, s_t, s_cnt, s_abort[2];
     __shared__ int s_list[MAX_CH];
     constexpr unsigned kStage = TP_PST * (sizeof(Rec16) + 2 * sizeof(float)) + TP_PST / 8 * sizeof(float4);
     constexpr int SPT = PT / TP_PST;   // stages per point tile
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
     if (tid == 0) {
-        for (int st = 0; st < 2; ++st) mbar_init(&full[st], 1);
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], TP_THREADS2 / 32);
+        }
         fence_barrier_init();
         s_abort[0] = s_abort[1] = 0;
     }
@@ -898,14 +928,15 @@ __global__ void __launch_bounds__(TP_THREADS2)
     unsigned git = 0;
     bool aborted = false;
     const uint2 *tr = reinterpret_cast<const uint2 *>(trec);
-    auto issue = [&](int st, unsigned slot) {
-        const int64_t q = (int64_t)s_list[st / SPT] * PT + (st % SPT) * TP_PST;
-        mbar_expect_tx(&full[slot], kStage);
-        bulk_g2s(s_rec[slot], prec + q, TP_PST * sizeof(Rec16), &full[slot]);
-        bulk_g2s(s_u[slot], us + q, TP_PST * sizeof(float), &full[slot]);
-        bulk_g2s(s_A[slot], Aq + q, TP_PST * sizeof(float), &full[slot]);
-        bulk_g2s(s_ball[slot], pball8 + q / 8, TP_PST / 8 * sizeof(float4), &full[slot]);
-    };
+#define TP_ISSUE(st_, slot_)                                                                  \
+    do {                                                                                      \
+        const int64_t q_ = (int64_t)s_list[(st_) / SPT] * PT + ((st_) % SPT) * TP_PST;        \
+        mbar_expect_tx(&full[slot_], kStage);                                                 \
+        bulk_g2s(s_rec[slot_], prec + q_, TP_PST * sizeof(Rec16), &full[slot_]);              \
+        bulk_g2s(s_u[slot_], us + q_, TP_PST * sizeof(float), &full[slot_]);                  \
+        bulk_g2s(s_A[slot_], Aq + q_, TP_PST * sizeof(float), &full[slot_]);                  \
+        bulk_g2s(s_ball[slot_], pball8 + q_ / 8, TP_PST / 8 * sizeof(float4), &full[slot_]); \
+    } while (0)
     for (;;) {
         if (tid == 0) {
             const int it = atomicAdd(counter, 1);
@@ -922,7 +953,7 @@ __global__ void __launch_bounds__(TP_THREADS2)
         const int tt = s_t;
         const int nst = SPT * s_cnt;
         if (tid == 0)
-            for (int st = 0; st < 2 && st < nst; ++st) issue(st, (git + st) & 1u);
+            for (int st = 0; st < 2 && st < nst; ++st) TP_ISSUE(st, (git + st) & 1u);
         const int64_t j0 = (int64_t)tt * TT + warp * (TC_MB * 16);
         unsigned A[TC_MB][4];
         float2 bgg[TC_MB];   // (-b_g, -b_g) and (-b_g+8, -b_g+8) as two pairs
@@ -939,40 +970,46 @@ __global__ void __launch_bounds__(TP_THREADS2)
             tb[m] = tball16[jb / 16];
             acc64[m] = make_double2(0.0, 0.0);
         }
+        bool wabort = false;
         for (int it = 0; it < nst; ++it) {
             const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
-            if (!mbar_wait(&full[slot], ph)) {
-                s_abort[it & 1] = 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+                s_abort[0] = 1;
                 atomicOr(flags, kErrTimeout);
-            } else {
+                wabort = true;
+                break;
+            }
+            {
                 const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
                 const float2 *up = reinterpret_cast<const float2 *>(&s_u[slot][0]) + t;
                 const float2 *ap = reinterpret_cast<const float2 *>(&s_A[slot][0]) + t;
                 float2 acc[TC_MB];
 #pragma unroll
                 for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
-#pragma unroll 1
-                for (int nb = 0; nb < TP_PST / 8; ++nb) {
-                    const float4 pbl = s_ball[slot][nb];
-                    int cls[TC_MB];
-                    bool any = false;
+                // classes of this warp's 4 target m-blocks against the stage's 32 point
+                // n-blocks: lane l classifies n-block l (2 bits per m-block)
+                unsigned mycls = 0;
+                {
+                    const float4 pbl = s_ball[slot][lane];
 #pragma unroll
-                    for (int m = 0; m < TC_MB; ++m) {
-                        cls[m] = tp_class(tb[m], pbl, Rin, Rout);
-                        any = any || cls[m] != 0;
-                    }
-                    if (!any) continue;
+                    for (int m = 0; m < TC_MB; ++m)
+                        mycls |= (unsigned)tp_class(tb[m], pbl, Rin, Rout) << (2 * m);
+                }
+                for (unsigned live = __ballot_sync(0xffffffffu, mycls != 0); live; live &= live - 1) {
+                    const int nb = __ffs(live) - 1;
+                    const unsigned cl = __shfl_sync(0xffffffffu, mycls, nb);
                     const uint2 bf = rec[32 * nb];
                     const float2 u = up[4 * nb];     // (u_2t, u_2t+1)
                     const float2 Ac = ap[4 * nb];    // (A_2t, A_2t+1)
 #pragma unroll
                     for (int m = 0; m < TC_MB; ++m) {
-                        if (cls[m] == 0) continue;
+                        const int c = (int)((cl >> (2 * m)) & 3u);
+                        if (c == 0) continue;
                         float d[4];
                         mma_tc(d, A[m], bf);
                         float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
                         float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
-                        if (cls[m] == 2) {
+                        if (c == 2) {
                             const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), bgg[m]);
                             const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), bg8[m]);
                             e01 = make_float2(v01.x > Ac.x ? e01.x : -INFINITY, v01.y > Ac.y ? e01.y : -INFINITY);
@@ -988,13 +1025,24 @@ __global__ void __launch_bounds__(TP_THREADS2)
                     acc64[m].y += (double)acc[m].y;
                 }
             }
-            __syncthreads();
-            aborted = s_abort[it & 1] != 0;
-            if (aborted) break;
-            if (tid == 0 && it + 2 < nst) issue(it + 2, slot);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (warp == 0 && it + 2 < nst) {
+                bool ok = true;
+                if (tid == 0) {
+                    ok = mbar_wait(&empty[slot], ph);
+                    if (ok) TP_ISSUE(it + 2, slot);
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    s_abort[0] = 1;
+                    atomicOr(flags, kErrTimeout);
+                    wabort = true;
+                    break;
+                }
+            }
         }
-        if (aborted) break;
         git += nst;
+if (!wabort) {
 #pragma unroll
         for (int m = 0; m < TC_MB; ++m) {
             double x = acc64[m].x, y = acc64[m].y;
@@ -1008,11 +1056,17 @@ __global__ void __launch_bounds__(TP_THREADS2)
                 part2[(int64_t)item * TT + l + 8] = y;
             }
         }
-        __syncthreads();
+        }
+        __syncthreads();   // end of the item: every warp is past its stages
+        if (s_abort[0]) {
+            aborted = true;
+            break;
+        }
     }
     if (aborted && tid == 0)
         for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
 }
+#undef TP_ISSUE
 
 // ------------------------------------------------------------------ combine
 // Merge the item partials of each point; write pass-2 point-pair records
