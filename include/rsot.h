@@ -279,6 +279,11 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
 void rsot_batch_destroy(rsot_batch *b);
 rsot_status rsot_batch_set_stream(rsot_batch *b, void *stream);
 
+/* Pair kernel of the batched mixed passes (see rsot_set_pair_kernel); the
+ * automatic choice takes the tensor cores when every problem of the batch
+ * meets its bound.  Errors: RSOT_ERR_ARG, RSOT_ERR_CUDA. */
+rsot_status rsot_batch_set_pair_kernel(rsot_batch *b, rsot_pair_kernel kind);
+
 /* Total number of targets (length of the concatenated psi / gradient vectors). */
 int64_t rsot_batch_total_targets(const rsot_batch *b);
 

@@ -192,6 +192,7 @@ def load():
     lib.rsot_batch_total_targets.restype = ctypes.c_int64
     lib.rsot_batch_eval.argtypes = [vp, dp, dp, ctypes.c_char_p, dp, dp]
     lib.rsot_batch_tune.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int)]
+    lib.rsot_batch_set_pair_kernel.argtypes = [vp, ctypes.c_int]
     lib.rsot_batch_solve.argtypes = [vp, dp, dp, ctypes.POINTER(_Options),
                                      ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(_BStats)]
     _lib = lib
@@ -418,6 +419,10 @@ class Batch:
 
     def split(self, v):
         return [v[self.offsets[i]:self.offsets[i + 1]] for i in range(self.count)]
+
+    def set_pair_kernel(self, kind):
+        """PAIRS_AUTO (default), PAIRS_TENSOR or PAIRS_FP32 for the batched passes."""
+        _check(self._lib.rsot_batch_set_pair_kernel(self._h, int(kind)), "batch_set_pair_kernel")
 
     def eval(self, psi_all, eps, active=None):
         psi_all = np.ascontiguousarray(psi_all, dtype=np.float64)

@@ -20,11 +20,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <vector>
 
 #include "rsot_inner.cuh"
 #include "rsot_internal.cuh"
+#include "rsot_tc.cuh"
 #include "rsot_lbfgs.h"
 
 namespace rsot {
@@ -37,6 +39,7 @@ struct BProb {
     int d, nck1, chunk1, nsp2;
     int pblk_base, tblk_base;   // 256-blocks of points / targets
     double msum, hx;
+    float tcP;                  // tensor-core point coordinate scale (rsot_tc.cuh)
 };
 
 }  // namespace rsot
@@ -62,7 +65,12 @@ struct rsot_batch {
     double *part2 = nullptr, *blockJ = nullptr, *psinu = nullptr;
     double *psi_d = nullptr, *grad_d = nullptr, *eps_d = nullptr, *J_d = nullptr;
     unsigned char *active_d = nullptr;
-    int *counters = nullptr;   // [0], [1]: work counters, [2]: error flags
+    int *counters = nullptr;   // [0], [1]: work counters, [2]: error flags, [3]: f16 range gate
+    rsot::Rec16 *prec16 = nullptr, *trec = nullptr;   // tensor-core operand records
+    float *pu = nullptr;                              // pass-2 shifts u_q
+    int pair_kernel = 2;       // as rsot_problem::pair_kernel
+    bool tc_ok = false;        // every problem meets the automatic choice's bound
+    int slots1_tc = 0, slots2_tc = 0;
     double *psi_h = nullptr, *grad_h = nullptr, *eps_h = nullptr, *J_h = nullptr;
     unsigned char *active_h = nullptr;
     int *flags_h = nullptr;
@@ -93,7 +101,8 @@ __global__ void k_bprep(const BProb *__restrict__ probs, const int *__restrict__
                         const unsigned char *__restrict__ active, const double *__restrict__ y,
                         const double *__restrict__ lnu, const double *__restrict__ nu,
                         Rec8 *__restrict__ tdup, Rec8 *__restrict__ tpair,
-                        double *__restrict__ psinu, int *__restrict__ flags) {
+                        double *__restrict__ psinu, int *__restrict__ flags,
+                        Rec16 *__restrict__ trec, int *__restrict__ gate) {
     __shared__ double sh[32];
     const int b = blockIdx.x;
     const int p = blk2prob[b];
@@ -120,6 +129,18 @@ __global__ void k_bprep(const BProb *__restrict__ probs, const int *__restrict__
         c = (float)(bb - k * yy);
         contrib = ps * nu[g];
     }
+    if (trec) {   // tensor-core operands: w / P and c (padding: c at the clamp)
+        float W[3];
+        bool ok = true;
+        for (int t = 0; t < 3; ++t) {
+            W[t] = (float)((double)w[t] / (double)P.tcP);
+            ok = ok && fabsf(W[t]) < TC_RANGE;
+        }
+        const float C = fmaxf(c, -256.0f * TC_RANGE);
+        ok = ok && C < 256.0f * TC_RANGE;
+        if (!ok) atomicOr(gate, 1);
+        trec[g] = make_target_rec(W, C);
+    }
     Rec8 r;
     r.a = make_float4(w[0], w[0], w[1], w[1]);
     r.b = make_float4(w[2], w[2], c, c);
@@ -139,7 +160,9 @@ __global__ void __launch_bounds__(P1_THREADS, 4)
     k_blse(const BProb *__restrict__ probs, int count, const int64_t *__restrict__ item1_base,
            const unsigned char *__restrict__ active, const float *__restrict__ xs,
            const Rec8 *__restrict__ tdup, float2 *__restrict__ part1, int *__restrict__ counter,
-           int *__restrict__ flags) {
+           int *__restrict__ flags, const int *__restrict__ gate = nullptr) {
+    // as the fallback of the tensor-core pass, run only when the gate asks for it
+    if (gate && !(*gate & 1)) return;
     __shared__ __align__(128) Rec8 sm[P1_STAGES][P1_TS];
     __shared__ __align__(8) uint64_t full[P1_STAGES];
     __shared__ int s_abort[2];
@@ -238,7 +261,8 @@ __global__ void k_bcombine(const BProb *__restrict__ probs, const int *__restric
                            const unsigned char *__restrict__ active,
                            const float2 *__restrict__ part1, const float *__restrict__ xs,
                            const double *__restrict__ mass, const double *__restrict__ lm2,
-                           Rec8 *__restrict__ pdup, double *__restrict__ blockJ) {
+                           Rec8 *__restrict__ pdup, double *__restrict__ blockJ,
+                           float *__restrict__ pu) {
     __shared__ double sh[32];
     const int b = blockIdx.x;
     const int p = blk2prob[b];
@@ -271,8 +295,276 @@ __global__ void k_bcombine(const BProb *__restrict__ probs, const int *__restric
     r.a = make_float4(x[0], x[0], x[1], x[1]);
     r.b = make_float4(x[2], x[2], u, u);
     pdup[g] = r;
+    if (pu) pu[g] = u;
     const double s = block_sum_d(contrib, sh);
     if (threadIdx.x == 0) blockJ[b] = s;
+}
+
+// ---- tensor-core passes over the batch (rsot_tc.cuh; stage bodies shared with
+// the single-problem kernels): CTAs of 16 warps x 4 m-blocks = 1,024 points
+// (pass 1) or targets (pass 2), 256-record stages released per warp.
+constexpr int BT_THREADS = 512;
+constexpr int BT_TS = 256;
+static_assert(BT_THREADS / 32 * TC_MB * 16 == P1_TILE, "a pass-1 CTA covers a point tile");
+
+// static point operand records (X = P x')
+__global__ void k_bpoint_recs(const BProb *__restrict__ probs, const int *__restrict__ blk2prob,
+                              const float *__restrict__ xs, Rec16 *__restrict__ prec) {
+    const int b = blockIdx.x;
+    const BProb P = probs[blk2prob[b]];
+    const int64_t ql = (int64_t)(b - P.pblk_base) * B_T + threadIdx.x;
+    float X[3];
+    for (int k = 0; k < 3; ++k) X[k] = xs[3 * P.pt_base + k * P.nq_pad + ql] * P.tcP;
+    prec[P.pt_base + ql] = make_point_rec(X, 0.0f);
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 1)
+    k_blse_tc(const BProb *__restrict__ probs, int count, const int64_t *__restrict__ item1_base,
+              const unsigned char *__restrict__ active, const Rec16 *__restrict__ prec,
+              const Rec16 *__restrict__ trec, float2 *__restrict__ part1,
+              int *__restrict__ counter, int *__restrict__ flags, const int *__restrict__ gate) {
+    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernel runs
+    __shared__ __align__(128) Rec16 sm[2][BT_TS];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ long long s_item;
+    __shared__ int s_p, s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], BT_THREADS / 32);
+        }
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int64_t total = item1_base[count];
+    const uint2 *pr = reinterpret_cast<const uint2 *>(prec);
+    unsigned git = 0;
+    bool aborted = false;
+    for (;;) {
+        if (tid == 0) {
+            const long long it = atomicAdd(counter, 1);
+            s_item = it;
+            if (it < total) s_p = find_prob(item1_base, count, it);
+        }
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        const int p = s_p;
+        if (active[p]) {
+            const BProb P = probs[p];
+            const int64_t local = item - P.item1_base;
+            const int64_t tile = local / P.nck1;
+            const int c = (int)(local % P.nck1);
+            const int64_t t_begin = P.t_base + (int64_t)c * P.chunk1;
+            const int ntile = (int)(min((int64_t)P.chunk1, P.n_p1 - (int64_t)c * P.chunk1) / BT_TS);
+            if (tid == 0)
+                for (int st = 0; st < 2 && st < ntile; ++st) {
+                    const unsigned slot = (git + st) & 1u;
+                    mbar_expect_tx(&full[slot], BT_TS * sizeof(Rec16));
+                    bulk_g2s(sm[slot], trec + t_begin + (int64_t)st * BT_TS, BT_TS * sizeof(Rec16),
+                             &full[slot]);
+                }
+            const int64_t q0 = P.pt_base + tile * P1_TILE + warp * (TC_MB * 16);
+            unsigned A[TC_MB][4];
+            float2 M[TC_MB], Sf[TC_MB];
+            double2 Sd[TC_MB];
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) {
+                tc_load_a(A[m], pr + (q0 + m * 16) * 4, g, t);
+                M[m] = make_float2(-INFINITY, -INFINITY);
+                Sf[m] = make_float2(0.f, 0.f);
+                Sd[m] = make_double2(0.0, 0.0);
+            }
+            bool wabort = false;
+            for (int it = 0; it < ntile; ++it) {
+                const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
+                if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+                    s_abort = 1;
+                    atomicOr(flags, kErrTimeout);
+                    wabort = true;
+                    break;
+                }
+                tc_lse_stage<BT_TS / 8>(reinterpret_cast<const uint2 *>(&sm[slot][0]) + lane, A, M, Sf, Sd);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (warp == 0 && it + 2 < ntile) {
+                    bool ok = true;
+                    if (tid == 0) {
+                        ok = mbar_wait(&empty[slot], ph);
+                        if (ok) {
+                            mbar_expect_tx(&full[slot], BT_TS * sizeof(Rec16));
+                            bulk_g2s(sm[slot], trec + t_begin + (int64_t)(it + 2) * BT_TS,
+                                     BT_TS * sizeof(Rec16), &full[slot]);
+                        }
+                    }
+                    if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                        s_abort = 1;
+                        atomicOr(flags, kErrTimeout);
+                        wabort = true;
+                        break;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    Sd[m].x += (double)Sf[m].x;
+                    Sd[m].y += (double)Sf[m].y;
+                    Sf[m] = make_float2(0.f, 0.f);
+                }
+            }
+            git += ntile;
+            if (!wabort) {
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    float mx = M[m].x, my = M[m].y;
+                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 1));
+                    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 2));
+                    double sx = M[m].x == -INFINITY ? 0.0 : Sd[m].x * pow2_int_d(M[m].x - mx);
+                    double sy = M[m].y == -INFINITY ? 0.0 : Sd[m].y * pow2_int_d(M[m].y - my);
+                    sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+                    sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+                    if (m == t) {
+                        float2 *o = part1 + item * P1_TILE + warp * (TC_MB * 16) + m * 16 + g;
+                        o[0] = mx == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(mx, (float)sx);
+                        o[8] = my == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(my, (float)sy);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // end of the item: every warp is past its stages
+        if (s_abort) {
+            aborted = true;
+            break;
+        }
+    }
+    if (aborted && tid == 0)
+        for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 1)
+    k_bgrad_tc(const BProb *__restrict__ probs, int count, const int64_t *__restrict__ item2_base,
+               const unsigned char *__restrict__ active, const Rec16 *__restrict__ trec,
+               const Rec16 *__restrict__ prec, const float *__restrict__ pu,
+               double *__restrict__ part2, int *__restrict__ counter, int *__restrict__ flags,
+               const int *__restrict__ gate) {
+    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernel runs
+    __shared__ __align__(128) Rec16 sm[2][BT_TS];
+    __shared__ __align__(16) float su[2][BT_TS];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ long long s_item;
+    __shared__ int s_p, s_abort;
+    constexpr unsigned kStage = BT_TS * (sizeof(Rec16) + sizeof(float));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], BT_THREADS / 32);
+        }
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int64_t total = item2_base[count];
+    const uint2 *tr = reinterpret_cast<const uint2 *>(trec);
+    unsigned git = 0;
+    bool aborted = false;
+    for (;;) {
+        if (tid == 0) {
+            const long long it = atomicAdd(counter, 1);
+            s_item = it;
+            if (it < total) s_p = find_prob(item2_base, count, it);
+        }
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        const int p = s_p;
+        if (active[p]) {
+            const BProb P = probs[p];
+            const int64_t local = item - P.item2_base;
+            const int64_t blk = local / P.nsp2;
+            const int sp = (int)(local % P.nsp2);
+            const int64_t p_begin = P.pt_base + (int64_t)sp * P.chunk2;
+            const int ntile = (int)(min(P.chunk2, P.nq_pad - (int64_t)sp * P.chunk2) / BT_TS);
+            if (tid == 0)
+                for (int st = 0; st < 2 && st < ntile; ++st) {
+                    const unsigned slot = (git + st) & 1u;
+                    mbar_expect_tx(&full[slot], kStage);
+                    bulk_g2s(sm[slot], prec + p_begin + (int64_t)st * BT_TS, BT_TS * sizeof(Rec16),
+                             &full[slot]);
+                    bulk_g2s(su[slot], pu + p_begin + (int64_t)st * BT_TS, BT_TS * sizeof(float),
+                             &full[slot]);
+                }
+            const int64_t j0 = P.t_base + blk * 1024 + warp * (TC_MB * 16);
+            unsigned A[TC_MB][4];
+            double2 acc64[TC_MB];
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) {
+                tc_load_a(A[m], tr + (j0 + m * 16) * 4, g, t);
+                acc64[m] = make_double2(0.0, 0.0);
+            }
+            bool wabort = false;
+            for (int it = 0; it < ntile; ++it) {
+                const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
+                if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+                    s_abort = 1;
+                    atomicOr(flags, kErrTimeout);
+                    wabort = true;
+                    break;
+                }
+                tc_grad_stage<BT_TS / 8>(reinterpret_cast<const uint2 *>(&sm[slot][0]) + lane,
+                                         reinterpret_cast<const float2 *>(&su[slot][0]) + t, A, acc64);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (warp == 0 && it + 2 < ntile) {
+                    bool ok = true;
+                    if (tid == 0) {
+                        ok = mbar_wait(&empty[slot], ph);
+                        if (ok) {
+                            mbar_expect_tx(&full[slot], kStage);
+                            bulk_g2s(sm[slot], prec + p_begin + (int64_t)(it + 2) * BT_TS,
+                                     BT_TS * sizeof(Rec16), &full[slot]);
+                            bulk_g2s(su[slot], pu + p_begin + (int64_t)(it + 2) * BT_TS,
+                                     BT_TS * sizeof(float), &full[slot]);
+                        }
+                    }
+                    if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                        s_abort = 1;
+                        atomicOr(flags, kErrTimeout);
+                        wabort = true;
+                        break;
+                    }
+                }
+            }
+            git += ntile;
+            if (!wabort) {
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    double x = acc64[m].x, y = acc64[m].y;
+                    x += __shfl_xor_sync(0xffffffffu, x, 1);
+                    x += __shfl_xor_sync(0xffffffffu, x, 2);
+                    y += __shfl_xor_sync(0xffffffffu, y, 1);
+                    y += __shfl_xor_sync(0xffffffffu, y, 2);
+                    if (m == t) {
+                        double *o = part2 + item * 1024 + warp * (TC_MB * 16) + m * 16 + g;
+                        o[0] = x;
+                        o[8] = y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) {
+            aborted = true;
+            break;
+        }
+    }
+    if (aborted && tid == 0)
+        for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
 }
 
 constexpr int B_TPP = 4;   // pass 2: 1024 targets per block
@@ -281,7 +573,8 @@ __global__ void __launch_bounds__(P2_THREADS)
     k_bgrad(const BProb *__restrict__ probs, int count, const int64_t *__restrict__ item2_base,
             const unsigned char *__restrict__ active, const Rec8 *__restrict__ tpair,
             const Rec8 *__restrict__ pdup, double *__restrict__ part2, int *__restrict__ counter,
-            int *__restrict__ flags) {
+            int *__restrict__ flags, const int *__restrict__ gate = nullptr) {
+    if (gate && !(*gate & 1)) return;
     __shared__ __align__(128) Rec8 sm[P2_STAGES][P2_TS];
     __shared__ __align__(8) uint64_t full[P2_STAGES];
     __shared__ int s_abort[2];
@@ -468,16 +761,30 @@ cudaError_t enqueue_round(rsot_batch *b) {
     if ((e = cudaMemcpyAsync(b->psi_d, b->psi_h, b->tot_n * 8, cudaMemcpyHostToDevice, st))) return e;
     if ((e = cudaMemcpyAsync(b->eps_d, b->eps_h, b->count * 8, cudaMemcpyHostToDevice, st))) return e;
     if ((e = cudaMemcpyAsync(b->active_d, b->active_h, b->count, cudaMemcpyHostToDevice, st))) return e;
-    if ((e = cudaMemsetAsync(b->counters, 0, 3 * sizeof(int), st))) return e;
+    if ((e = cudaMemsetAsync(b->counters, 0, 4 * sizeof(int), st))) return e;
+    // tensor-core passes (automatic choice), FP32 passes as their fallback when an
+    // operand leaves the f16 range (gate)
+    const bool tc = b->pair_kernel == 1 || (b->pair_kernel == 2 && b->tc_ok);
+    int *gate = tc ? b->counters + 3 : nullptr;
     k_bprep<<<b->nblk_t, B_T, 0, st>>>(b->dp, b->blk2prob_t, b->psi_d, b->eps_d, b->active_d, b->y,
-                                      b->lnu, b->nu, b->tdup, b->tpair, b->psinu, b->counters + 2);
+                                      b->lnu, b->nu, b->tdup, b->tpair, b->psinu, b->counters + 2,
+                                      tc ? b->trec : nullptr, gate);
+    if (tc)
+        k_blse_tc<<<b->slots1_tc, BT_THREADS, 0, st>>>(b->dp, b->count, b->item1_base, b->active_d,
+                                                       b->prec16, b->trec, b->part1, b->counters,
+                                                       b->counters + 2, gate);
     k_blse<<<b->slots1, P1_THREADS, 0, st>>>(b->dp, b->count, b->item1_base, b->active_d, b->xs,
-                                             b->tdup, b->part1, b->counters, b->counters + 2);
+                                             b->tdup, b->part1, b->counters, b->counters + 2, gate);
     k_bcombine<<<b->nblk_p, B_T, 0, st>>>(b->dp, b->blk2prob_p, b->active_d, b->part1, b->xs,
-                                         b->mass, b->lm2, b->pdup, b->blockJ);
+                                         b->mass, b->lm2, b->pdup, b->blockJ,
+                                         tc ? b->pu : nullptr);
+    if (tc)
+        k_bgrad_tc<<<b->slots2_tc, BT_THREADS, 0, st>>>(b->dp, b->count, b->item2_base, b->active_d,
+                                                        b->trec, b->prec16, b->pu, b->part2,
+                                                        b->counters + 1, b->counters + 2, gate);
     k_bgrad<<<b->slots2, P2_THREADS, 0, st>>>(b->dp, b->count, b->item2_base, b->active_d,
                                               b->tpair, b->pdup, b->part2, b->counters + 1,
-                                              b->counters + 2);
+                                              b->counters + 2, gate);
     k_bfinal_grad<<<b->nblk_t, B_T, 0, st>>>(b->dp, b->blk2prob_t, b->active_d, b->part2, b->nu,
                                             b->grad_d);
     k_bfinal_J<<<b->count, B_T, 0, st>>>(b->dp, b->active_d, b->blockJ, b->psinu, b->psi_d,
@@ -527,7 +834,7 @@ void rsot_batch_destroy(rsot_batch *b) {
     void *dev[] = {b->dp, b->blk2prob_p, b->blk2prob_t, b->item1_base, b->item2_base, b->xs,
                    b->mass, b->lm2, b->y, b->nu, b->lnu, b->tdup, b->tpair, b->pdup, b->part1,
                    b->part2, b->blockJ, b->psinu, b->psi_d, b->grad_d, b->eps_d, b->J_d,
-                   b->active_d, b->counters};
+                   b->active_d, b->counters, b->prec16, b->trec, b->pu};
     for (void *q : dev) cudaFree(q);
     void *host[] = {b->psi_h, b->grad_h, b->eps_h, b->J_h, b->active_h, b->flags_h};
     for (void *q : host)
@@ -554,6 +861,7 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
     std::vector<float> hxs;
     std::vector<double> hmass, hlm2, hy, hnu, hlnu;
     std::vector<int> bp, bt;
+    bool tc_all = true;
     b->hp.resize(count);
     for (int p = 0; p < count; ++p) {
         const rsot_problem_desc &D = probs[p];
@@ -615,6 +923,18 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
         }
         P.msum = msum;
         P.hx = hxv;
+        {   // tensor-core scale: P x' within [-32, 32] (a power of two)
+            float xmax = 0.0f;
+            for (int k = 0; k < 3; ++k)
+                for (int64_t q = 0; q < D.nq; ++q) xmax = std::max(xmax, std::fabs(hxs[xs0 + k * P.nq_pad + q]));
+            int ex = 0;
+            if (xmax > 0.0f) std::frexp(xmax, &ex);
+            P.tcP = std::ldexp(1.0f, 5 - ex);
+            double mmax = 0.0, numax = 0.0;
+            for (int64_t q = 0; q < D.nq; ++q) mmax = std::max(mmax, m[q]);
+            for (int64_t j = 0; j < D.n; ++j) numax = std::max(numax, nu[j]);
+            tc_all = tc_all && mmax * numax <= kTcAuto;
+        }
         hy.resize(3 * (b->tot_t + P.n_alloc), 0.0);
         hnu.resize(b->tot_t + P.n_alloc, 0.0);
         hlnu.resize(b->tot_t + P.n_alloc, 0.0);
@@ -657,6 +977,9 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
     BALLOC(b->J_d, count);
     BALLOC(b->active_d, count);
     BALLOC(b->counters, 4);
+    BALLOC(b->prec16, b->tot_pts);
+    BALLOC(b->trec, b->tot_t);
+    BALLOC(b->pu, b->tot_pts);
 #undef BALLOC
     if (!e) e = cudaMallocHost(&b->psi_h, b->tot_n * 8);
     if (!e) e = cudaMallocHost(&b->grad_h, b->tot_n * 8);
@@ -677,8 +1000,21 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
         rsot_batch_destroy(b);
         return to_status(e);
     }
+    b->tc_ok = tc_all;
+    if (!e) e = cudaMemcpy(b->dp, b->hp.data(), b->hp.size() * sizeof(BProb), cudaMemcpyHostToDevice);
+    if (!e) {
+        k_bpoint_recs<<<b->nblk_p, B_T>>>(b->dp, b->blk2prob_p, b->xs, b->prec16);
+        e = cudaDeviceSynchronize();
+    }
+    if (e) {
+        cudaGetLastError();
+        rsot_batch_destroy(b);
+        return to_status(e);
+    }
     b->slots1 = b->num_sms * occ((const void *)k_blse, P1_THREADS);
     b->slots2 = b->num_sms * occ((const void *)k_bgrad, P2_THREADS);
+    b->slots1_tc = b->num_sms * occ((const void *)k_blse_tc, BT_THREADS);
+    b->slots2_tc = b->num_sms * occ((const void *)k_bgrad_tc, BT_THREADS);
     plan_items(b, b->item_exp);
     e = upload_plan(b);
     if (!e) e = build_graph(b);
@@ -689,6 +1025,13 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
     }
     *out = b;
     return RSOT_OK;
+}
+
+rsot_status rsot_batch_set_pair_kernel(rsot_batch *b, rsot_pair_kernel kind) {
+    if (!b || (kind != RSOT_PAIRS_FP32 && kind != RSOT_PAIRS_TENSOR && kind != RSOT_PAIRS_AUTO))
+        return RSOT_ERR_ARG;
+    b->pair_kernel = (int)kind;
+    return to_status(build_graph(b));
 }
 
 rsot_status rsot_batch_set_stream(rsot_batch *b, void *stream) {

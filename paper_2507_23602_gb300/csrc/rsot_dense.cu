@@ -341,56 +341,6 @@ __global__ void __launch_bounds__(P2_THREADS, P2_MINB)
 // of two) when a lane's group sum exceeds 2^60 or is not finite, or a shift
 // is not yet set.  The 4 lanes of a row are merged at the end.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void tc_raise(float &M, float mx, float &sf, double &sd) {
-    const float mn = ceilf(mx);
-    if (mn > M) {
-        if (M != -INFINITY) {
-            const float dl = M - mn;
-            sf *= pow2_int_f(dl);
-            sd *= pow2_int_d(dl);
-        }
-        M = mn;
-    }
-}
-
-// exact redo of one group of TC_GROUP n-blocks (warp-uniform)
-__device__ __forceinline__ void tc_exact_group(const uint2 *__restrict__ gb,
-                                               const unsigned (&A)[TC_MB][4], float2 (&M)[TC_MB],
-                                               float2 (&Sf)[TC_MB], double2 (&Sd)[TC_MB],
-                                               float2 (&acc)[TC_MB]) {
-#pragma unroll
-    for (int m = 0; m < TC_MB; ++m) {
-        float mg = -INFINITY, mg8 = -INFINITY;
-#pragma unroll 2
-        for (int i = 0; i < TC_GROUP; ++i) {
-            float dd[4];
-            mma_tc(dd, A[m], gb[32 * i]);
-            mg = max3f(mg, dd[0], dd[1]);
-            mg8 = max3f(mg8, dd[2], dd[3]);
-        }
-        tc_raise(M[m].x, mg, Sf[m].x, Sd[m].x);
-        tc_raise(M[m].y, mg8, Sf[m].y, Sd[m].y);
-        const float2 ng = make_float2(-M[m].x, -M[m].x), ng8 = make_float2(-M[m].y, -M[m].y);
-        float2 a = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int i = 0; i < TC_GROUP; ++i) {
-            float dd[4];
-            mma_tc(dd, A[m], gb[32 * i]);
-            const float2 e01 = __fadd2_rn(make_float2(dd[0], dd[1]), ng);
-            const float2 e23 = __fadd2_rn(make_float2(dd[2], dd[3]), ng8);
-            a = __fadd2_rn(a, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-            a = __fadd2_rn(a, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
-        }
-        acc[m] = a;
-    }
-}
-
-// A fragment of rows (g, g + 8) of a 16-point m-block whose records start at
-// rec (uint2 view): segment t of row g and of row g + 8.
-__device__ __forceinline__ void tc_load_a(unsigned (&a)[4], const uint2 *rec, int g, int t) {
-    load_a(a, rec[g * 4 + t], rec[(g + 8) * 4 + t]);
-}
-
 __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     k_lse_tc(const Rec16 *__restrict__ prec, int64_t nq_pad, const Rec16 *__restrict__ trec,
              int n_p1, int chunk, float2 *__restrict__ part, int *__restrict__ flags,
@@ -448,58 +398,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
             aborted = true;
             break;
         }
-        {
-            const uint2 *base = reinterpret_cast<const uint2 *>(&sm[s][0]) + lane;
-            float dc[TC_MB][4];
-            {
-                const uint2 b = base[0];
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m) mma_tc(dc[m], A[m], b);
-            }
-#pragma unroll 1
-            for (int grp = 0; grp < NGRP; ++grp) {
-                float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m) {
-                    acc[m] = make_float2(0.f, 0.f);
-                    ng[m] = make_float2(-M[m].x, -M[m].x);
-                    ng8[m] = make_float2(-M[m].y, -M[m].y);
-                }
-#pragma unroll
-                for (int i = 0; i < TC_GROUP; ++i) {
-                    const int nb = grp * TC_GROUP + i;
-                    const bool more = (i + 1 < TC_GROUP) || (grp + 1 < NGRP);
-                    float dn[TC_MB][4];
-                    if (more) {
-                        const uint2 b = base[32 * (nb + 1)];
-#pragma unroll
-                        for (int m = 0; m < TC_MB; ++m) mma_tc(dn[m], A[m], b);
-                    }
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m) {
-                        const float2 e01 = __fadd2_rn(make_float2(dc[m][0], dc[m][1]), ng[m]);
-                        const float2 e23 = __fadd2_rn(make_float2(dc[m][2], dc[m][3]), ng8[m]);
-                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
-                    }
-                    if (more) {
-#pragma unroll
-                        for (int m = 0; m < TC_MB; ++m)
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) dc[m][r] = dn[m][r];
-                    }
-                }
-                bool bad = false;
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m)
-                    bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) || M[m].x == -INFINITY ||
-                          M[m].y == -INFINITY;
-                if (__any_sync(0xffffffffu, bad))
-                    tc_exact_group(base + 32 * grp * TC_GROUP, A, M, Sf, Sd, acc);
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
-            }
-        }
+        tc_lse_stage<TC_NBS>(reinterpret_cast<const uint2 *>(&sm[s][0]) + lane, A, M, Sf, Sd);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (warp == 0 && it + TC_STAGES < ntile) {
@@ -620,51 +519,8 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
             aborted = true;
             break;
         }
-        {
-            const uint2 *base = reinterpret_cast<const uint2 *>(&sm[s][0]) + lane;
-            const float2 *ub = reinterpret_cast<const float2 *>(&su[s][0]) + t;   // (u_2t, u_2t+1)
-            float2 acc[TC_MB];
-            float dc[TC_MB][4];
-#pragma unroll
-            for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
-            float2 uc = ub[0];
-            {
-                const uint2 b = base[0];
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m) mma_tc(dc[m], A[m], b);
-            }
-#pragma unroll 4
-            for (int nb = 0; nb < TC_NBS; ++nb) {
-                float dn[TC_MB][4];
-                float2 un = uc;
-                const bool more = nb + 1 < TC_NBS;
-                if (more) {
-                    const uint2 b = base[32 * (nb + 1)];
-                    un = ub[4 * (nb + 1)];
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m) mma_tc(dn[m], A[m], b);
-                }
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m) {
-                    const float2 e01 = __fadd2_rn(make_float2(dc[m][0], dc[m][1]), uc);
-                    const float2 e23 = __fadd2_rn(make_float2(dc[m][2], dc[m][3]), uc);
-                    acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                    acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
-                }
-                if (more) {
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) dc[m][r] = dn[m][r];
-                    uc = un;
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < TC_MB; ++m) {
-                acc64[m].x += (double)acc[m].x;
-                acc64[m].y += (double)acc[m].y;
-            }
-        }
+        tc_grad_stage<TC_NBS>(reinterpret_cast<const uint2 *>(&sm[s][0]) + lane,
+                              reinterpret_cast<const float2 *>(&su[s][0]) + t, A, acc64);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (warp == 0 && it + TC_STAGES < ntile) {

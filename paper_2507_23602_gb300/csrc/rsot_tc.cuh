@@ -123,4 +123,169 @@ __device__ __forceinline__ void load_a(unsigned (&a)[4], uint2 rg, uint2 rg8) {
     a[3] = rg8.y;
 }
 
+// ---- stage bodies of the tensor-core passes (dense and batched kernels) ----
+__device__ __forceinline__ void tc_raise(float &M, float mx, float &sf, double &sd) {
+    const float mn = ceilf(mx);
+    if (mn > M) {
+        if (M != -INFINITY) {
+            const float dl = M - mn;
+            sf *= pow2_int_f(dl);
+            sd *= pow2_int_d(dl);
+        }
+        M = mn;
+    }
+}
+
+// exact redo of one group of TC_GROUP n-blocks (warp-uniform)
+__device__ __forceinline__ void tc_exact_group(const uint2 *__restrict__ gb,
+                                               const unsigned (&A)[TC_MB][4], float2 (&M)[TC_MB],
+                                               float2 (&Sf)[TC_MB], double2 (&Sd)[TC_MB],
+                                               float2 (&acc)[TC_MB]) {
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        float mg = -INFINITY, mg8 = -INFINITY;
+#pragma unroll 2
+        for (int i = 0; i < TC_GROUP; ++i) {
+            float dd[4];
+            mma_tc(dd, A[m], gb[32 * i]);
+            mg = max3f(mg, dd[0], dd[1]);
+            mg8 = max3f(mg8, dd[2], dd[3]);
+        }
+        tc_raise(M[m].x, mg, Sf[m].x, Sd[m].x);
+        tc_raise(M[m].y, mg8, Sf[m].y, Sd[m].y);
+        const float2 ng = make_float2(-M[m].x, -M[m].x), ng8 = make_float2(-M[m].y, -M[m].y);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int i = 0; i < TC_GROUP; ++i) {
+            float dd[4];
+            mma_tc(dd, A[m], gb[32 * i]);
+            const float2 e01 = __fadd2_rn(make_float2(dd[0], dd[1]), ng);
+            const float2 e23 = __fadd2_rn(make_float2(dd[2], dd[3]), ng8);
+            a = __fadd2_rn(a, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+            a = __fadd2_rn(a, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+        }
+        acc[m] = a;
+    }
+}
+
+// A fragment of rows (g, g + 8) of a 16-point m-block whose records start at
+// rec (uint2 view): segment t of row g and of row g + 8.
+__device__ __forceinline__ void tc_load_a(unsigned (&a)[4], const uint2 *rec, int g, int t) {
+    load_a(a, rec[g * 4 + t], rec[(g + 8) * 4 + t]);
+}
+
+
+// One stage of pass 1: NBS n-blocks of target records (uint2 view of the
+// staged records, already offset by the lane), optimistic groups of
+// TC_GROUP n-blocks with the exact redo; sums go to Sf (FP32, this stage).
+template <int NBS>
+__device__ __forceinline__ void tc_lse_stage(const uint2 *__restrict__ base,
+                                             const unsigned (&A)[TC_MB][4], float2 (&M)[TC_MB],
+                                             float2 (&Sf)[TC_MB], double2 (&Sd)[TC_MB]) {
+    constexpr int NGRP_ = NBS / TC_GROUP;
+    static_assert(NBS % TC_GROUP == 0, "whole groups per stage");
+
+            float dc[TC_MB][4];
+            {
+                const uint2 b = base[0];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) mma_tc(dc[m], A[m], b);
+            }
+#pragma unroll 1
+            for (int grp = 0; grp < NGRP_; ++grp) {
+                float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    acc[m] = make_float2(0.f, 0.f);
+                    ng[m] = make_float2(-M[m].x, -M[m].x);
+                    ng8[m] = make_float2(-M[m].y, -M[m].y);
+                }
+#pragma unroll
+                for (int i = 0; i < TC_GROUP; ++i) {
+                    const int nb = grp * TC_GROUP + i;
+                    const bool more = (i + 1 < TC_GROUP) || (grp + 1 < NGRP_);
+                    float dn[TC_MB][4];
+                    if (more) {
+                        const uint2 b = base[32 * (nb + 1)];
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) mma_tc(dn[m], A[m], b);
+                    }
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        const float2 e01 = __fadd2_rn(make_float2(dc[m][0], dc[m][1]), ng[m]);
+                        const float2 e23 = __fadd2_rn(make_float2(dc[m][2], dc[m][3]), ng8[m]);
+                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                    }
+                    if (more) {
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m)
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) dc[m][r] = dn[m][r];
+                    }
+                }
+                bool bad = false;
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m)
+                    bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) || M[m].x == -INFINITY ||
+                          M[m].y == -INFINITY;
+                if (__any_sync(0xffffffffu, bad))
+                    tc_exact_group(base + 32 * grp * TC_GROUP, A, M, Sf, Sd, acc);
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
+            }
+        }
+
+// One stage of pass 2: NBS n-blocks of point records (uint2 view, offset by
+// the lane) with their shifts (ub: float2 view of u offset by t, so that
+// ub[4 nb] = (u_2t, u_2t+1) of n-block nb); FP32 within the stage, FP64 in acc64.
+template <int NBS>
+__device__ __forceinline__ void tc_grad_stage(const uint2 *__restrict__ base,
+                                              const float2 *__restrict__ ub,
+                                              const unsigned (&A)[TC_MB][4],
+                                              double2 (&acc64)[TC_MB]) {
+
+            float2 acc[TC_MB];
+            float dc[TC_MB][4];
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
+            float2 uc = ub[0];
+            {
+                const uint2 b = base[0];
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) mma_tc(dc[m], A[m], b);
+            }
+#pragma unroll 4
+            for (int nb = 0; nb < NBS; ++nb) {
+                float dn[TC_MB][4];
+                float2 un = uc;
+                const bool more = nb + 1 < NBS;
+                if (more) {
+                    const uint2 b = base[32 * (nb + 1)];
+                    un = ub[4 * (nb + 1)];
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) mma_tc(dn[m], A[m], b);
+                }
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) {
+                    const float2 e01 = __fadd2_rn(make_float2(dc[m][0], dc[m][1]), uc);
+                    const float2 e23 = __fadd2_rn(make_float2(dc[m][2], dc[m][3]), uc);
+                    acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                    acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                }
+                if (more) {
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) dc[m][r] = dn[m][r];
+                    uc = un;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) {
+                acc64[m].x += (double)acc[m].x;
+                acc64[m].y += (double)acc[m].y;
+            }
+        }
+
 }  // namespace rsot

@@ -57,6 +57,30 @@ def test_batch_eval_matches_single_problem_and_oracle():
         B.close()
 
 
+def test_batch_pair_kernels_agree_with_the_oracle():
+    """The batched tensor-core passes (the automatic choice on these problems) and
+    the batched FP32 passes both meet the mixed bounds against the oracle."""
+    probs, eps = small_batch(seed0=400, count=5)
+    B = rs().Batch([(p.x, p.mass, p.y, p.nu) for p in probs])
+    rng = np.random.default_rng(2)
+    psis = [0.02 * rng.standard_normal(p.n) for p in probs]
+    try:
+        ref = [oracle.dual_grad(p.x, p.mass, p.y, p.nu, psi, eps[i])[:2]
+               for i, (p, psi) in enumerate(zip(probs, psis))]
+        for kind in (rs().PAIRS_TENSOR, rs().PAIRS_FP32, rs().PAIRS_AUTO):
+            B.set_pair_kernel(kind)
+            J, g = B.eval(np.concatenate(psis), eps)
+            for i, (Jo, go) in enumerate(ref):
+                p = probs[i]
+                tol_g = 1e-6
+                if kind == rs().PAIRS_TENSOR:   # the forced form's error model
+                    tol_g = max(1e-6, 5 * 1.4e-5 * np.sqrt(p.mass.max() * p.nu.max()))
+                assert abs(J[i] - Jo) <= 1e-5 * abs(Jo), (kind, i, J[i], Jo)
+                assert np.max(np.abs(B.split(g)[i] - go)) <= tol_g, (kind, i)
+    finally:
+        B.close()
+
+
 def test_batch_solve_mixed_with_refinement_reaches_tolerance():
     probs, eps = small_batch(400, 5)
     B = rs().Batch([(p.x, p.mass, p.y, p.nu) for p in probs])
