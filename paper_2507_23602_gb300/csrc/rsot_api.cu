@@ -98,6 +98,12 @@ void copy_nu(const rsot_problem *p, double *out) {
     cudaMemcpy(out, p->nu, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost);
 }
 int pair_kernel_of(const rsot_problem *p) { return p->pair_kernel; }
+// A solver near convergence: the next mixed evaluations take the FP32 kernels
+// when the gradient's L1 norm is within kTcNoiseFactor of the tensor-core noise.
+void pair_kernel_for_gradient(rsot_problem *p, double grad_l1) {
+    p->pair_fp32_now = grad_l1 < kTcNoiseFactor * p->tc_noise_l1 ? 1 : 0;
+}
+double tc_noise_l1_of(const rsot_problem *p) { return p->tc_noise_l1; }
 
 }  // namespace rsot
 
@@ -215,6 +221,11 @@ rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, 
     std::vector<double> lnu((size_t)n);
     p->nu_min = INFINITY;
     p->nu_max = 0.0;
+    {
+        double sq = 0.0;
+        for (int64_t j = 0; j < n; ++j) sq += sqrt(hnu[j]);
+        p->tc_noise_l1 = 1.4e-5 * sqrt(p->m_max) * sq;
+    }
     for (int64_t j = 0; j < n; ++j) {
         for (int k = 0; k < d; ++k) hy[j * d + k] -= p->origin[k];
         lnu[j] = log(hnu[j]);

@@ -74,8 +74,10 @@ struct rsot_batch {
     double *psi_h = nullptr, *grad_h = nullptr, *eps_h = nullptr, *J_h = nullptr;
     unsigned char *active_h = nullptr;
     int *flags_h = nullptr;
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr, graph32 = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec32 = nullptr;   // the same round on the FP32 pair kernels
+    std::vector<double> tc_noise;       // per problem, as rsot_problem::tc_noise_l1
     int item_exp = 22;
 };
 
@@ -755,7 +757,7 @@ cudaError_t upload_plan(rsot_batch *b) {
 }
 
 // Record one evaluation round on b->stream (graph capture or direct launch).
-cudaError_t enqueue_round(rsot_batch *b) {
+cudaError_t enqueue_round(rsot_batch *b, bool force_fp32 = false) {
     cudaStream_t st = b->stream;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(b->psi_d, b->psi_h, b->tot_n * 8, cudaMemcpyHostToDevice, st))) return e;
@@ -764,7 +766,7 @@ cudaError_t enqueue_round(rsot_batch *b) {
     if ((e = cudaMemsetAsync(b->counters, 0, 4 * sizeof(int), st))) return e;
     // tensor-core passes (automatic choice), FP32 passes as their fallback when an
     // operand leaves the f16 range (gate)
-    const bool tc = b->pair_kernel == 1 || (b->pair_kernel == 2 && b->tc_ok);
+    const bool tc = !force_fp32 && (b->pair_kernel == 1 || (b->pair_kernel == 2 && b->tc_ok));
     int *gate = tc ? b->counters + 3 : nullptr;
     k_bprep<<<b->nblk_t, B_T, 0, st>>>(b->dp, b->blk2prob_t, b->psi_d, b->eps_d, b->active_d, b->y,
                                       b->lnu, b->nu, b->tdup, b->tpair, b->psinu, b->counters + 2,
@@ -795,23 +797,33 @@ cudaError_t enqueue_round(rsot_batch *b) {
     return cudaMemcpyAsync(b->flags_h, b->counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
 }
 
+cudaError_t capture(rsot_batch *b, bool force_fp32, cudaGraph_t *g, cudaGraphExec_t *x) {
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    cudaError_t e2 = enqueue_round(b, force_fp32);
+    e = cudaStreamEndCapture(b->stream, g);
+    if (e2) return e2;
+    if (e) return e;
+    return cudaGraphInstantiate(x, *g, 0);
+}
+
 cudaError_t build_graph(rsot_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    b->exec = nullptr;
-    b->graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    if (e) return e;
-    cudaError_t e2 = enqueue_round(b);
-    e = cudaStreamEndCapture(b->stream, &b->graph);
-    if (e2) return e2;
-    if (e) return e;
-    return cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (b->exec32) cudaGraphExecDestroy(b->exec32);
+    if (b->graph32) cudaGraphDestroy(b->graph32);
+    b->exec = b->exec32 = nullptr;
+    b->graph = b->graph32 = nullptr;
+    cudaError_t e = capture(b, false, &b->graph, &b->exec);
+    if (!e) e = capture(b, true, &b->graph32, &b->exec32);
+    return e;
 }
 
-// One round with the current host staging buffers (psi_h, eps_h, active_h).
-rsot_status run_round(rsot_batch *b) {
-    cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, b->stream) : enqueue_round(b);
+// One round with the current host staging buffers (psi_h, eps_h, active_h);
+// fp32: on the FP32 pair kernels whatever the automatic choice.
+rsot_status run_round(rsot_batch *b, bool fp32 = false) {
+    cudaGraphExec_t x = fp32 ? b->exec32 : b->exec;
+    cudaError_t e = x ? cudaGraphLaunch(x, b->stream) : enqueue_round(b, fp32);
     if (!e) e = cudaStreamSynchronize(b->stream);
     if (e) return to_status(e);
     if (*b->flags_h & kErrTimeout) return RSOT_ERR_TIMEOUT;
@@ -830,6 +842,8 @@ void rsot_batch_destroy(rsot_batch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->exec32) cudaGraphExecDestroy(b->exec32);
+    if (b->graph32) cudaGraphDestroy(b->graph32);
     for (rsot_problem *h : b->handles) rsot_destroy(h);
     void *dev[] = {b->dp, b->blk2prob_p, b->blk2prob_t, b->item1_base, b->item2_base, b->xs,
                    b->mass, b->lm2, b->y, b->nu, b->lnu, b->tdup, b->tpair, b->pdup, b->part1,
@@ -932,8 +946,13 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
             P.tcP = std::ldexp(1.0f, 5 - ex);
             double mmax = 0.0, numax = 0.0;
             for (int64_t q = 0; q < D.nq; ++q) mmax = std::max(mmax, m[q]);
-            for (int64_t j = 0; j < D.n; ++j) numax = std::max(numax, nu[j]);
+            double sq = 0.0;
+            for (int64_t j = 0; j < D.n; ++j) {
+                numax = std::max(numax, nu[j]);
+                sq += std::sqrt(nu[j]);
+            }
             tc_all = tc_all && mmax * numax <= kTcAuto;
+            b->tc_noise.push_back(1.4e-5 * std::sqrt(mmax) * sq);
         }
         hy.resize(3 * (b->tot_t + P.n_alloc), 0.0);
         hnu.resize(b->tot_t + P.n_alloc, 0.0);
@@ -1129,6 +1148,9 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
     if (opt->precision == RSOT_MIXED) {
         std::vector<LbfgsMachine> mc(P);
         std::vector<int> si(P, 0);
+        // latest gradient norm per problem: a round takes the tensor-core pair
+        // kernels only while every active problem is far above their noise
+        std::vector<double> last_l1(P, INFINITY);
         for (int p = 0; p < P; ++p) {
             const double e = stages[p][0];
             mc[p].start(xvec(p), stages[p].size() == 1 ? final_tol : stage_tol, m, max_iter,
@@ -1147,7 +1169,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                 }
             }
             if (!any) break;
-            rsot_status s = run_round(b);
+            bool fp32 = false;
+            for (int p = 0; p < P; ++p)
+                if (b->active_h[p] && last_l1[p] < kTcNoiseFactor * b->tc_noise[p]) fp32 = true;
+            rsot_status s = run_round(b, fp32);
             if (s) return s;
             ++rounds;
             for (int p = 0; p < P; ++p) {
@@ -1155,6 +1180,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                 const BProb &Q = b->hp[p];
                 std::vector<double> g(b->grad_h + Q.psi_off, b->grad_h + Q.psi_off + Q.n);
                 mc[p].feed(b->J_h[p], g);
+                last_l1[p] = mc[p].grad_l1();
                 ++evals;
                 if (mc[p].done()) {
                     const bool last = si[p] + 1 == (int)stages[p].size();

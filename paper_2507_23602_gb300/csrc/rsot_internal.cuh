@@ -97,6 +97,11 @@ struct rsot_problem {
     int pair_kernel = 2;            // 0: FP32 passes, 1: tensor-core passes (FP32 fallback by
                                     // gate), 2: tensor-core passes when m_max nu_max <= kTcAuto
     double m_max = 0.0;             // max_q m_q
+    // estimated L1 norm of the tensor-core rounding noise of a gradient,
+    // 1.4e-5 sqrt(m_max) sum_j sqrt(nu_j) (see kTcAuto); solvers take the FP32
+    // kernels once the gradient is within kTcNoiseFactor of it
+    double tc_noise_l1 = 0.0;
+    int pair_fp32_now = 0;          // set by a solver: this evaluation takes the FP32 kernels
     int k1_tc = 0, chunk1_tc = 0;   // pass-1 target chunks of the tensor-core launch
     int s2_tc = 0;                  // pass-2 point splits of the tensor-core launch
     int64_t chunk2_tc = 0;
@@ -146,8 +151,10 @@ namespace rsot {
 // mixed path; smaller problems (few points or heavy targets) take the FP32
 // kernels.
 constexpr double kTcAuto = 2e-6;
+constexpr double kTcNoiseFactor = 30.0;
 inline bool use_tensor_pairs(const rsot_problem *p) {
-    return p->pair_kernel == 1 || (p->pair_kernel == 2 && p->m_max * p->nu_max <= kTcAuto);
+    if (p->pair_kernel == 1) return true;
+    return p->pair_kernel == 2 && !p->pair_fp32_now && p->m_max * p->nu_max <= kTcAuto;
 }
 
 // ---- kernel tracing (rsot_api.cu) -------------------------------------------

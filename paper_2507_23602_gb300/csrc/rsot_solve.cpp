@@ -39,6 +39,7 @@ namespace rsot {
 int64_t num_targets(const rsot_problem *p);
 void copy_nu(const rsot_problem *p, double *out);
 int pair_kernel_of(const rsot_problem *p);
+void pair_kernel_for_gradient(rsot_problem *p, double grad_l1);
 }  // namespace rsot
 
 namespace {
@@ -104,13 +105,15 @@ double norm1(const std::vector<double> &a) {
 
 // Drive one L-BFGS run with GPU evaluations until it stops.
 template <class Ev>
-rsot_status run_machine(Ev &ev, rsot::LbfgsMachine &mc, int verbose) {
+rsot_status run_machine(Ev &ev, rsot::LbfgsMachine &mc, int verbose, rsot_problem *p) {
     std::vector<double> g(ev.n);
     double f = 0.0;
     while (mc.wants_eval()) {
         rsot_status s = ev(mc.trial(), f, g);
         if (s) return s;
         mc.feed(f, g);
+        // tensor-core pair kernels only while the gradient is far above their noise
+        rsot::pair_kernel_for_gradient(p, mc.grad_l1());
         if (verbose && !mc.wants_eval())
             fprintf(stderr, "[rsot] eps=%.3g %s stop after %d it: J=%.15g |g|_1=%.3e evals=%d\n",
                     ev.eps, ev.prec == RSOT_FP64 ? "fp64" : "mixed", mc.iters(), mc.f(),
@@ -162,6 +165,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     const int max_iter = opt->max_iter > 0 ? opt->max_iter : 10000;
     const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : opt->tol_l1;
 
+    rsot::pair_kernel_for_gradient(p, INFINITY);
     std::vector<double> x(psi_inout, psi_inout + n), g(n, 0.0), D(n);
     double f = 0.0;
     int iters = 0, evals = 0, stages = 0;
@@ -179,7 +183,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             tol_run = std::max(tol, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5);
         mc.start(x, tol_run, m, max_iter, D, opt->precision == RSOT_FP64 ? 1e-13 : 1e-6);
         ++stages;
-        st = run_machine(ev, mc, opt->verbose);
+        st = run_machine(ev, mc, opt->verbose, p);
         x = mc.x();
         f = mc.f();
         g = mc.g();
@@ -221,7 +225,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
                 for (int64_t j = 0; j < n; ++j) ce.b[j] = g64[j] - gm[j];
                 rsot::LbfgsMachine mcc;
                 mcc.start_from(x, f64, g64, 0.5 * tol, m, std::min(max_iter, 200), D, 1e-6);
-                rsot_status sc = run_machine(ce, mcc, opt->verbose);
+                rsot_status sc = run_machine(ce, mcc, opt->verbose, p);
                 if (sc && sc != RSOT_ERR_LINESEARCH && sc != RSOT_ERR_NOT_CONVERGED) {
                     st = sc;
                     break;
@@ -233,7 +237,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
                 // fall back to FP64 L-BFGS from the corrected iterate
                 rsot::LbfgsMachine mc64;
                 mc64.start(x, tol, m, max_iter, D, 1e-13);
-                st = run_machine(ev64, mc64, opt->verbose);
+                st = run_machine(ev64, mc64, opt->verbose, p);
                 x = mc64.x();
                 f = mc64.f();
                 g = mc64.g();
@@ -246,6 +250,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         if (st != RSOT_OK && !(st == RSOT_ERR_LINESEARCH && !last)) break;
         st = RSOT_OK;
     }
+    rsot::pair_kernel_for_gradient(p, INFINITY);
     std::copy(x.begin(), x.end(), psi_inout);
     if (stats) {
         stats->J = f;

@@ -632,6 +632,22 @@ __device__ __forceinline__ void tp_lse_pair(const unsigned (&a)[4], uint2 bf, in
     }
 }
 
+// the epilogue of tp_lse_pair on a given mma result d
+__device__ __forceinline__ void tp_lse_epi(const float (&d)[4], int cls, float2 ng, float2 ng8,
+                                           float2 nbb, float Ag, float Ag8, float2 &e01,
+                                           float2 &e23, unsigned &cnt) {
+    e01 = __fadd2_rn(make_float2(d[0], d[1]), ng);
+    e23 = __fadd2_rn(make_float2(d[2], d[3]), ng8);
+    if (cls == 2) {
+        const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), nbb);
+        const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), nbb);
+        const bool i0 = v01.x > Ag, i1 = v01.y > Ag, i2 = v23.x > Ag8, i3 = v23.y > Ag8;
+        e01 = make_float2(i0 ? e01.x : -INFINITY, i1 ? e01.y : -INFINITY);
+        e23 = make_float2(i2 ? e23.x : -INFINITY, i3 ? e23.y : -INFINITY);
+        cnt += (unsigned)i0 + (unsigned)i1 + (unsigned)i2 + (unsigned)i3;
+    }
+}
+
 __global__ void __launch_bounds__(TP_THREADS1, 1)
     k_lse_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
                    const float4 *__restrict__ pball16, const Rec16 *__restrict__ trec,
@@ -744,22 +760,41 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                         ng[m] = make_float2(-M[m].x, -M[m].x);
                         ng8[m] = make_float2(-M[m].y, -M[m].y);
                     }
-                    for (unsigned gm = gmask; gm; gm &= gm - 1) {
-                        const int nb = grp * TC_GROUP + __ffs(gm) - 1;
-                        const unsigned cl = __shfl_sync(0xffffffffu, mycls, nb);
-                        const uint2 bf = rec[32 * nb];
-                        const float2 bb = bp[4 * nb];
-                        const float2 nbb = make_float2(-bb.x, -bb.y);
-                        const unsigned cv = (unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY);
+                    // two live n-blocks per step: their mma are issued before either
+                    // epilogue, so the latency of one hides behind the other's work
+                    for (unsigned gm = gmask; gm;) {
+                        const int nb0 = grp * TC_GROUP + __ffs(gm) - 1;
+                        gm &= gm - 1;
+                        const bool two = gm != 0;
+                        const int nb1 = two ? grp * TC_GROUP + __ffs(gm) - 1 : nb0;
+                        if (two) gm &= gm - 1;
+                        const unsigned cl0 = __shfl_sync(0xffffffffu, mycls, nb0);
+                        const unsigned cl1 = two ? __shfl_sync(0xffffffffu, mycls, nb1) : 0u;
+                        const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
+                        const float2 bb0 = bp[4 * nb0], bb1 = bp[4 * nb1];
+                        float d0[TC_MB][4], d1[TC_MB][4];
 #pragma unroll
                         for (int m = 0; m < TC_MB; ++m) {
-                            const int c = (int)((cl >> (2 * m)) & 3u);
-                            if (c == 0) continue;
-                            float2 e01, e23;
-                            tp_lse_pair(A[m], bf, c, ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01, e23, icnt);
-                            if (c == 1) icnt += rv[m] * cv;
-                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                            if ((cl0 >> (2 * m)) & 3u) mma_tc(d0[m], A[m], bf0);
+                            if ((cl1 >> (2 * m)) & 3u) mma_tc(d1[m], A[m], bf1);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const unsigned cl = h ? cl1 : cl0;
+                            const float2 bb = h ? bb1 : bb0;
+                            const float2 nbb = make_float2(-bb.x, -bb.y);
+                            const unsigned cv = (unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY);
+#pragma unroll
+                            for (int m = 0; m < TC_MB; ++m) {
+                                const int c = (int)((cl >> (2 * m)) & 3u);
+                                if (c == 0) continue;
+                                float2 e01, e23;
+                                tp_lse_epi(h ? d1[m] : d0[m], c, ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01,
+                                           e23, icnt);
+                                if (c == 1) icnt += rv[m] * cv;
+                                acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                                acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                            }
                         }
                     }
                     bool bad = false;
@@ -995,28 +1030,44 @@ __global__ void __launch_bounds__(TP_THREADS2)
                     for (int m = 0; m < TC_MB; ++m)
                         mycls |= (unsigned)tp_class(tb[m], pbl, Rin, Rout) << (2 * m);
                 }
-                for (unsigned live = __ballot_sync(0xffffffffu, mycls != 0); live; live &= live - 1) {
-                    const int nb = __ffs(live) - 1;
-                    const unsigned cl = __shfl_sync(0xffffffffu, mycls, nb);
-                    const uint2 bf = rec[32 * nb];
-                    const float2 u = up[4 * nb];     // (u_2t, u_2t+1)
-                    const float2 Ac = ap[4 * nb];    // (A_2t, A_2t+1)
+                // two live n-blocks per step (mma of both before either epilogue)
+                for (unsigned live = __ballot_sync(0xffffffffu, mycls != 0); live;) {
+                    const int nb0 = __ffs(live) - 1;
+                    live &= live - 1;
+                    const bool two = live != 0;
+                    const int nb1 = two ? __ffs(live) - 1 : nb0;
+                    if (two) live &= live - 1;
+                    const unsigned cl0 = __shfl_sync(0xffffffffu, mycls, nb0);
+                    const unsigned cl1 = two ? __shfl_sync(0xffffffffu, mycls, nb1) : 0u;
+                    const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
+                    float d0[TC_MB][4], d1[TC_MB][4];
 #pragma unroll
                     for (int m = 0; m < TC_MB; ++m) {
-                        const int c = (int)((cl >> (2 * m)) & 3u);
-                        if (c == 0) continue;
-                        float d[4];
-                        mma_tc(d, A[m], bf);
-                        float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
-                        float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
-                        if (c == 2) {
-                            const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), bgg[m]);
-                            const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), bg8[m]);
-                            e01 = make_float2(v01.x > Ac.x ? e01.x : -INFINITY, v01.y > Ac.y ? e01.y : -INFINITY);
-                            e23 = make_float2(v23.x > Ac.x ? e23.x : -INFINITY, v23.y > Ac.y ? e23.y : -INFINITY);
+                        if ((cl0 >> (2 * m)) & 3u) mma_tc(d0[m], A[m], bf0);
+                        if ((cl1 >> (2 * m)) & 3u) mma_tc(d1[m], A[m], bf1);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int nb = h ? nb1 : nb0;
+                        const unsigned cl = h ? cl1 : cl0;
+                        const float2 u = up[4 * nb];     // (u_2t, u_2t+1)
+                        const float2 Ac = ap[4 * nb];    // (A_2t, A_2t+1)
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) {
+                            const int c = (int)((cl >> (2 * m)) & 3u);
+                            if (c == 0) continue;
+                            const float(&d)[4] = h ? d1[m] : d0[m];
+                            float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
+                            float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
+                            if (c == 2) {
+                                const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), bgg[m]);
+                                const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), bg8[m]);
+                                e01 = make_float2(v01.x > Ac.x ? e01.x : -INFINITY, v01.y > Ac.y ? e01.y : -INFINITY);
+                                e23 = make_float2(v23.x > Ac.x ? e23.x : -INFINITY, v23.y > Ac.y ? e23.y : -INFINITY);
+                            }
+                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
                         }
-                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
                     }
                 }
 #pragma unroll
