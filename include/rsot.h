@@ -50,9 +50,17 @@ typedef enum {
 } rsot_status;
 
 typedef enum {
-    RSOT_FP64 = 0,   /* every operation in FP64                                 */
-    RSOT_MIXED = 1   /* FP32 pair arithmetic (ex2.approx), FP64 reductions       */
+    RSOT_FP64 = 0,        /* every operation in FP64                            */
+    RSOT_MIXED = 1,       /* FP32 pair arithmetic (ex2.approx), FP64 reductions  */
+    RSOT_COMPENSATED = 2  /* pair exponents as double-float FP32 pairs, ex2.approx,
+                             compensated sums: ||g - grad J||_1 <= 6.5e-7 sum m_q
+                             (RSOT_COMPENSATED_GRAD_REL), at FP32 throughput     */
 } rsot_precision;
+
+/* Bound of ||g - grad J||_1 / sum_q m_q for a gradient g computed with
+ * RSOT_COMPENSATED, for any sizes, eps and potentials (the per-term error
+ * budget of ex2.approx and of the compensated sums). */
+#define RSOT_COMPENSATED_GRAD_REL 6.5e-7
 
 /* Human-readable name of a status code (static string). */
 const char *rsot_status_string(rsot_status s);
@@ -110,7 +118,8 @@ rsot_status rsot_set_pair_kernel(rsot_problem *p, rsot_pair_kernel kind);
  *               discretized_functional / discretized_gradient);
  *               > 0 -> truncated: only pairs with |x_q - y_j| < radius
  *               (c < C with C = radius^2/2, Sec. 4.1)
- *   prec      : RSOT_FP64 or RSOT_MIXED
+ *   prec      : RSOT_FP64, RSOT_MIXED or RSOT_COMPENSATED (the truncated
+ *               form decides membership c < C exactly as the FP64 path)
  *   J_out     : host pointer, 1 double
  *   grad_out  : n doubles (host or device)
  *   pairs_out : host pointer or NULL; receives sum_q |I_q|, the pairs whose
@@ -224,10 +233,16 @@ typedef struct {
     double mixed_tol_l1; /* MIXED + refine_fp64: the mixed phase of the last stage
                             stops here, FP64-corrected refinement takes over
                             (<= 0: 1e-5)                                           */
+    int refine_precision;/* reference evaluations of the refinement (and of the last
+                            stage when precision is RSOT_COMPENSATED):
+                            RSOT_COMPENSATED (default) stops at ||g||_1 <= tol_l1 -
+                            RSOT_COMPENSATED_GRAD_REL sum m_q, which certifies
+                            ||grad J||_1 <= tol_l1; it is used while that bound is
+                            at most 0.8 tol_l1, else FP64.  RSOT_FP64: always FP64 */
 } rsot_options;
 
 /* Fill *o with the defaults (eps 1e-2, no schedule, dense, tol 1e-6, MIXED with
- * FP64 refinement, m = 10, 10000 iterations). */
+ * refinement against compensated evaluations, m = 10, 10000 iterations). */
 void rsot_default_options(rsot_options *o);
 
 /* Per-solve statistics. */
@@ -248,6 +263,10 @@ typedef struct {
  *   psi_inout : n doubles, HOST memory: the warm start on entry, the
  *               minimiser on return (also on NOT_CONVERGED / LINESEARCH,
  *               where it is the last accepted iterate).
+ * precision RSOT_COMPENSATED runs every stage with compensated evaluations
+ * (the last one to the certified tolerance, see refine_precision).
+ * stats->grad_l1 is the L1 norm of the last gradient in the precision that
+ * decided the stop.
  * Errors: RSOT_ERR_ARG, RSOT_ERR_NOT_CONVERGED, RSOT_ERR_LINESEARCH, and any
  * error of rsot_eval_dual_grad.
  */

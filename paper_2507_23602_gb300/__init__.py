@@ -19,13 +19,15 @@ from typing import Optional
 import numpy as np
 
 __all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "MLP", "SolveOptions", "SolveStats",
-           "FP64", "MIXED", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate"]
+           "FP64", "MIXED", "COMPENSATED", "COMPENSATED_GRAD_REL", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librsot.so")
 _lib = None
 
-FP64, MIXED = 0, 1
+FP64, MIXED, COMPENSATED = 0, 1, 2
+# ||g - grad J||_1 <= COMPENSATED_GRAD_REL * sum_q m_q for a COMPENSATED gradient
+COMPENSATED_GRAD_REL = 6.5e-7
 PAIRS_FP32, PAIRS_TENSOR, PAIRS_AUTO = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
           4: "empty neighbourhood", 5: "not converged", 6: "line search failed",
@@ -45,7 +47,7 @@ class _Options(ctypes.Structure):
                 ("tol_l1", ctypes.c_double), ("stage_tol_l1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
                 ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("mixed_tol_l1", ctypes.c_double)]
+                ("mixed_tol_l1", ctypes.c_double), ("refine_precision", ctypes.c_int)]
 
 
 class _Desc(ctypes.Structure):
@@ -108,12 +110,13 @@ class SolveOptions:
     max_iter: int = 10000
     verbose: bool = False
     mixed_tol_l1: float = 1e-5
+    refine_precision: int = COMPENSATED
 
     def _c(self):
         return _Options(self.eps, self.eps_start, self.eps_factor, self.tail, self.tol_l1,
                         self.stage_tol_l1, int(self.precision), int(bool(self.refine_fp64)),
                         int(self.lbfgs_m), int(self.max_iter), int(bool(self.verbose)),
-                        float(self.mixed_tol_l1))
+                        float(self.mixed_tol_l1), int(self.refine_precision))
 
 
 @dataclasses.dataclass

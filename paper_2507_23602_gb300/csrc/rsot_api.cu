@@ -94,6 +94,7 @@ void trace_collect(rsot_problem *p) {
 }
 
 int64_t num_targets(const rsot_problem *p) { return p->n; }
+double mass_sum(const rsot_problem *p) { return p->msum; }
 void copy_nu(const rsot_problem *p, double *out) {
     cudaMemcpy(out, p->nu, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost);
 }
@@ -129,6 +130,7 @@ const char *rsot_version(void) { return "rsot-gb300 0.1 (sm_103a)"; }
 void rsot_destroy(rsot_problem *p) {
     if (!p) return;
     trunc_free(p);
+    compensated_free(p);
     dense_free(p);
     cudaFree(p->xs);
     cudaFree(p->x64);
@@ -274,7 +276,7 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, 
                                 int64_t *pairs_out) {
     if (!p || !psi || !J_out || !grad_out) return RSOT_ERR_ARG;
     if (!(eps > 0.0) || !isfinite(eps) || isnan(radius)) return RSOT_ERR_ARG;
-    if (prec != RSOT_FP64 && prec != RSOT_MIXED) return RSOT_ERR_ARG;
+    if (prec != RSOT_FP64 && prec != RSOT_MIXED && prec != RSOT_COMPENSATED) return RSOT_ERR_ARG;
     cudaStream_t st = p->stream;
     const size_t nb = (size_t)p->n * sizeof(double);
     const double *psid = psi;
@@ -289,7 +291,9 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, 
     // a radius beyond the diameter of the data keeps every pair: dense
     const bool dense = !(radius > 0.0) || isinf(radius) || radius * radius > p->diam2 * (1.0 + 1e-12);
     if (!e) {
-        if (dense)
+        if (prec == RSOT_COMPENSATED)
+            e = launch_compensated(p, psid, eps, dense ? INFINITY : 0.5 * radius * radius, gd);
+        else if (dense)
             e = (prec == RSOT_MIXED) ? launch_dense_mixed(p, psid, eps, gd)
                                      : launch_dense_fp64(p, psid, eps, gd);
         else
@@ -313,7 +317,9 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, 
     if (!isfinite(r.J)) return RSOT_ERR_NONFINITE;
     *J_out = r.J;
     if (pairs_out) *pairs_out = dense ? p->nq * p->n : (int64_t)r.pairs;
-    p->last_kind = dense ? (prec == RSOT_MIXED ? 1 : 0) : (prec == RSOT_MIXED ? 3 : 2);
+    p->last_kind = prec == RSOT_COMPENSATED ? (dense ? 4 : 5)
+                                            : dense ? (prec == RSOT_MIXED ? 1 : 0)
+                                                    : (prec == RSOT_MIXED ? 3 : 2);
     p->last_eps = eps;
     if (!dense && r.empty > 0) return RSOT_ERR_EMPTY_NEIGHBORHOOD;
     return RSOT_OK;
@@ -348,7 +354,9 @@ rsot_status rsot_point_log_partition(rsot_problem *p, double *L_out) {
     double *tgt = ddev ? L_out : nullptr;
     cudaError_t e = cudaSuccess;
     if (!ddev) e = cudaMallocAsync(&tgt, (size_t)p->nq * 8, p->stream);
-    if (!e) e = (p->last_kind >= 2) ? trunc_point_L(p, tgt) : launch_point_L(p, tgt);
+    // the mixed truncated path keeps R_q in its sorted grid order; every other
+    // path in lse_buf
+    if (!e) e = (p->last_kind == 3) ? trunc_point_L(p, tgt) : launch_point_L(p, tgt);
     if (!e && !ddev)
         e = cudaMemcpyAsync(L_out, tgt, (size_t)p->nq * 8, cudaMemcpyDeviceToHost, p->stream);
     if (!ddev && tgt) cudaFreeAsync(tgt, p->stream);

@@ -811,7 +811,7 @@ __global__ void k_point_L(const double *__restrict__ lse_buf, const double *__re
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     const double base = res->psic / eps;
-    if (kind == 1) {
+    if (kind == 1 || kind >= 4) {   // log2-domain R_q (mixed and compensated)
         double r2 = 0.0;
         for (int t = 0; t < d; ++t) r2 += x64[q * d + t] * x64[q * d + t];
         out[q] = base + kLn2 * lse_buf[q] - 0.5 * r2 / eps;
@@ -1123,6 +1123,22 @@ cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double
                                   const double *yf_dev, double *out_dev) {
     return p->d == 3 ? softmax_refine_d<3>(p, psi_dev, eps, nf, yf_dev, out_dev)
                      : softmax_refine_d<2>(p, psi_dev, eps, nf, yf_dev, out_dev);
+}
+
+// gradient and log2-domain J from pass-2 partials [s2][n_pad] and nbj pass-1
+// block partials of sum_q m_q R_q (the compensated path's finalisation)
+cudaError_t launch_finalize_log2(rsot_problem *p, const double *psi, double eps,
+                                 const double *part2, int s2, int nbj, double *grad) {
+    cudaStream_t st = p->stream;
+    trace_begin(p, "finalize_grad");
+    k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(part2, s2, p->n_pad, p->nu,
+                                                                    p->n, grad);
+    trace_end(p);
+    trace_begin(p, "finalize_J");
+    k_finalize_J<<<1, 256, 0, st>>>(p->blockJ, nbj, p->psinu, p->nblk_prep, psi, eps, p->msum,
+                                    p->hx, 1, p->res_dev);
+    trace_end(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi, double eps, double *grad) {

@@ -111,6 +111,10 @@ struct rsot_problem {
     int s2_64 = 0;
     int64_t chunk2_64 = 0;
     double *part2_64 = nullptr;     // [s2_64][n_pad]
+    // compensated path scratch (rsot_df.cu), allocated on first use
+    void *df_prec = nullptr;        // [nq_pad] point head/tail records (32 B)
+    void *df_trec = nullptr;        // [n_pad] target head/tail records (32 B)
+    float *df_ys = nullptr;         // [3][n_pad] FP32 target coordinates
 
     // staging for host psi / grad
     double *psi_dev = nullptr;      // [n]
@@ -122,6 +126,7 @@ struct rsot_problem {
     // per-point log partition of the last evaluation (see rsot_point_log_partition)
     double *lse_buf = nullptr;      // [nq_pad]: R_q (mixed, log2) or L'_q (FP64, natural)
     int last_kind = -1;             // -1 none, 0 FP64 dense, 1 mixed dense, 2/3 truncated
+                                    // FP64/mixed, 4/5 compensated dense/truncated
     double last_eps = 0.0;
 
     // covering cost cache
@@ -178,6 +183,13 @@ cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out
 cudaError_t launch_point_L(rsot_problem *p, double *L_dev);
 cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double eps, int64_t nf,
                                   const double *yf_dev, double *out_dev);
+
+// ---- compensated path (rsot_df.cu): cutoff = +inf dense, else truncated
+cudaError_t launch_compensated(rsot_problem *p, const double *psi_dev, double eps, double cutoff,
+                               double *grad_dev);
+void compensated_free(rsot_problem *p);
+// Bound of ||g - grad J||_1 / sum_q m_q for a compensated gradient g (rsot_df.cu)
+constexpr double kCompGradRel = 6.5e-7;
 
 // ---- transport maps and centroids (rsot_maps.cu), after a dense mixed evaluation
 cudaError_t launch_maps(rsot_problem *p, double eps, double *T_dev, int64_t *j_dev,

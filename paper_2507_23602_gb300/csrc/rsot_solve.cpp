@@ -17,12 +17,16 @@
 //     replaces sufficient decrease.
 // With MIXED precision and refine_fp64, the last stage runs mixed evaluations
 // down to mixed_tol_l1 (default 1e-5, above the FP32 rounding floor of the
-// gradient), then refines with FP64 corrections: an FP64 and a mixed
-// evaluation at the iterate give the systematic mixed-precision error, and
-// mixed L-BFGS continues on the corrected objective (at most 200 iterations
-// per correction) until the FP64 gradient meets tol_l1; when a correction no
-// longer halves the FP64 gradient (tol below the mixed noise floor), plain
-// FP64 L-BFGS finishes from the corrected iterate.
+// gradient), then refines with corrections from a reference evaluation: a
+// reference and a mixed evaluation at the iterate give the systematic
+// mixed-precision error, and mixed L-BFGS continues on the corrected objective
+// (at most 200 iterations per correction) until the reference gradient meets
+// the tolerance; when a correction no longer halves the reference gradient
+// (tol below the mixed noise floor), plain L-BFGS on reference evaluations
+// finishes from the corrected iterate.  The reference is the compensated
+// evaluation (rsot_df.cu), stopped at tol - B with B = 6.5e-7 sum m_q its
+// certified gradient error, so that ||grad J||_1 <= tol holds; FP64 where B
+// leaves too little room under tol or on request.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -37,6 +41,7 @@
 
 namespace rsot {
 int64_t num_targets(const rsot_problem *p);
+double mass_sum(const rsot_problem *p);
 void copy_nu(const rsot_problem *p, double *out);
 int pair_kernel_of(const rsot_problem *p);
 void pair_kernel_for_gradient(rsot_problem *p, double grad_l1);
@@ -116,7 +121,7 @@ rsot_status run_machine(Ev &ev, rsot::LbfgsMachine &mc, int verbose, rsot_proble
         rsot::pair_kernel_for_gradient(p, mc.grad_l1());
         if (verbose && !mc.wants_eval())
             fprintf(stderr, "[rsot] eps=%.3g %s stop after %d it: J=%.15g |g|_1=%.3e evals=%d\n",
-                    ev.eps, ev.prec == RSOT_FP64 ? "fp64" : "mixed", mc.iters(), mc.f(),
+                    ev.eps, ev.prec == RSOT_FP64 ? "fp64" : ev.prec == RSOT_MIXED ? "mixed" : "compensated", mc.iters(), mc.f(),
                     mc.grad_l1(), ev.evals);
     }
     return mc.status();
@@ -141,6 +146,7 @@ void rsot_default_options(rsot_options *o) {
     o->max_iter = 10000;
     o->verbose = 0;
     o->mixed_tol_l1 = 1e-5;
+    o->refine_precision = RSOT_COMPENSATED;
 }
 
 rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *opt,
@@ -148,7 +154,11 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     if (!p || !psi_inout || !opt) return RSOT_ERR_ARG;
     if (!(opt->eps > 0.0) || !(opt->tol_l1 > 0.0) || opt->tail < 0.0 || opt->tail >= 1.0)
         return RSOT_ERR_ARG;
-    if (opt->precision != RSOT_FP64 && opt->precision != RSOT_MIXED) return RSOT_ERR_ARG;
+    if (opt->precision != RSOT_FP64 && opt->precision != RSOT_MIXED &&
+        opt->precision != RSOT_COMPENSATED)
+        return RSOT_ERR_ARG;
+    if (opt->refine_precision != RSOT_FP64 && opt->refine_precision != RSOT_COMPENSATED)
+        return RSOT_ERR_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t n = rsot::num_targets(p);
     std::vector<double> nu(n);
@@ -164,6 +174,13 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     const int m = opt->lbfgs_m > 0 ? opt->lbfgs_m : 10;
     const int max_iter = opt->max_iter > 0 ? opt->max_iter : 10000;
     const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : opt->tol_l1;
+    // reference evaluations of the final stop: compensated with its certified
+    // bound subtracted from tol where the bound leaves room, else FP64
+    const double comp_bound = RSOT_COMPENSATED_GRAD_REL * rsot::mass_sum(p);
+    const bool comp_ref = opt->refine_precision == RSOT_COMPENSATED && comp_bound <= 0.8 * opt->tol_l1;
+    const rsot_precision ref_prec = comp_ref ? RSOT_COMPENSATED : RSOT_FP64;
+    const double ref_tol = comp_ref ? opt->tol_l1 - comp_bound : opt->tol_l1;
+    const double ref_noise = comp_ref ? 1e-6 : 1e-13;
 
     rsot::pair_kernel_for_gradient(p, INFINITY);
     std::vector<double> x(psi_inout, psi_inout + n), g(n, 0.0), D(n);
@@ -176,12 +193,17 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         const bool last = si + 1 == eps_list.size();
         const double tol = last ? opt->tol_l1 : stage_tol;
         for (int64_t j = 0; j < n; ++j) D[j] = eps / nu[j];
-        Evaluator ev{p, n, eps, opt->tail, (rsot_precision)opt->precision};
+        // a COMPENSATED solve whose bound leaves no room finishes in FP64
+        const rsot_precision prec = (opt->precision == RSOT_COMPENSATED && last && !comp_ref)
+                                        ? RSOT_FP64
+                                        : (rsot_precision)opt->precision;
+        Evaluator ev{p, n, eps, opt->tail, prec};
         rsot::LbfgsMachine mc;
         double tol_run = tol;
         if (last && opt->precision == RSOT_MIXED && opt->refine_fp64)
             tol_run = std::max(tol, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5);
-        mc.start(x, tol_run, m, max_iter, D, opt->precision == RSOT_FP64 ? 1e-13 : 1e-6);
+        if (last && prec == RSOT_COMPENSATED) tol_run = ref_tol;
+        mc.start(x, tol_run, m, max_iter, D, prec == RSOT_FP64 ? 1e-13 : 1e-6);
         ++stages;
         st = run_machine(ev, mc, opt->verbose, p);
         x = mc.x();
@@ -192,9 +214,9 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         pairs += ev.pairs;
         const bool refine = last && opt->precision == RSOT_MIXED && opt->refine_fp64;
         if (refine && (st == RSOT_OK || st == RSOT_ERR_LINESEARCH)) {
-            // FP64-corrected refinement: one FP64 and one mixed evaluation per
+            // corrected refinement: one reference and one mixed evaluation per
             // correction, mixed L-BFGS on the corrected objective in between
-            Evaluator ev64{p, n, eps, opt->tail, RSOT_FP64};
+            Evaluator ev64{p, n, eps, opt->tail, ref_prec};
             Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
             // the refinement works below the random rounding noise of the
             // tensor-core exponents (rms ~2e-5 per pair, several 1e-6 in the L1
@@ -214,7 +236,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
                 f = f64;
                 g = g64;
                 const double n64 = norm1(g64);
-                if (n64 <= tol) {
+                if (n64 <= ref_tol) {
                     done = true;
                     break;
                 }
@@ -224,7 +246,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
                 CorrectedEvaluator ce{evm, std::vector<double>(n), x, f64 - fm, n, eps};
                 for (int64_t j = 0; j < n; ++j) ce.b[j] = g64[j] - gm[j];
                 rsot::LbfgsMachine mcc;
-                mcc.start_from(x, f64, g64, 0.5 * tol, m, std::min(max_iter, 200), D, 1e-6);
+                mcc.start_from(x, f64, g64, 0.5 * ref_tol, m, std::min(max_iter, 200), D, 1e-6);
                 rsot_status sc = run_machine(ce, mcc, opt->verbose, p);
                 if (sc && sc != RSOT_ERR_LINESEARCH && sc != RSOT_ERR_NOT_CONVERGED) {
                     st = sc;
@@ -234,9 +256,9 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
                 x = mcc.x();
             }
             if (!done && st == RSOT_OK) {
-                // fall back to FP64 L-BFGS from the corrected iterate
+                // fall back to L-BFGS on reference evaluations from the corrected iterate
                 rsot::LbfgsMachine mc64;
-                mc64.start(x, tol, m, max_iter, D, 1e-13);
+                mc64.start(x, ref_tol, m, max_iter, D, ref_noise);
                 st = run_machine(ev64, mc64, opt->verbose, p);
                 x = mc64.x();
                 f = mc64.f();

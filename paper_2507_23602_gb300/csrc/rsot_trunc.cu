@@ -1556,7 +1556,7 @@ cudaError_t trunc_eval(rsot_problem *p, const double *psi, double eps, double ra
 }
 
 cudaError_t trunc_point_L(rsot_problem *p, double *L) {
-    if (p->last_kind == 2) return launch_point_L(p, L);
+    if (p->last_kind != 3 || !p->grid) return launch_point_L(p, L);
     Grid *g = p->grid;
     k_point_L_trunc<<<(unsigned)((p->nq + 255) / 256), 256, 0, p->stream>>>(
         g->lse_s, g->perm_q, g->x64, p->nq, p->d, p->last_eps, p->res_dev, L);
