@@ -247,7 +247,7 @@ def run_solve_workloads(args):
         res["cube_mixed"] = {"seconds": mixed_s, "iters": st.iters, "evals": st.evals,
                              "grad_l1": st.grad_l1, "status": st.status}
         Q.close()
-        solve_line("solve time to ||grad||_1<=1e-6 (cube, eps 0.1->1e-3, mixed + FP64 correction)",
+        solve_line("solve time to ||grad||_1<=1e-6 (cube, eps 0.1->1e-3, mixed + compensated correction)",
                    mixed_s, "s", f"cube-{q.nq}x{q.n}-solve", {"results": res}, args)
         return
     if args.workload == "batch":
@@ -271,7 +271,7 @@ def run_solve_workloads(args):
         pairs = sum(p.nq * p.n for p in probs)
         clean = lambda s: {k2: (v.tolist() if hasattr(v, "tolist") else v) for k2, v in s.items()
                            if k2 not in ("grad_l1", "statuses")}
-        solve_line("batched solve time to ||grad||_1<=1e-6 (mixed + FP64 correction)",
+        solve_line("batched solve time to ||grad||_1<=1e-6 (mixed + compensated correction)",
                    st["seconds"], "s", f"batch-{len(probs)}-problems",
                    {"pairs_per_round_all": pairs, "item_exp": choice, "batch": clean(st),
                     "subset_problems": k, "subset_mixed_batched": clean(st_m),

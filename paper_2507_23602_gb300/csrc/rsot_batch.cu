@@ -1155,6 +1155,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
             const double e = stages[p][0];
             mc[p].start(xvec(p), stages[p].size() == 1 ? final_tol : stage_tol, m, max_iter,
                         Dvec(p, e), 1e-6);
+            mc[p].set_stall_window(kMixedStallWindow);
             b->eps_h[p] = e;
         }
         for (;;) {
@@ -1190,6 +1191,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                         const bool fin = si[p] + 1 == (int)stages[p].size();
                         mc[p].start(mc[p].x(), fin ? final_tol : stage_tol, m, max_iter,
                                     Dvec(p, e), 1e-6);
+                        mc[p].set_stall_window(kMixedStallWindow);
                     } else {
                         st[p] = mc[p].status();
                         gl1[p] = mc[p].grad_l1();
@@ -1200,9 +1202,11 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
         }
         t_mixed = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (opt->refine_fp64) {
-            // FP64 evaluations through each problem's own handle, from the mixed solution
+            // corrected refinement through each problem's own handle, from the mixed solution
             for (int p = 0; p < P; ++p) {
-                if (!(st[p] == RSOT_OK || st[p] == RSOT_ERR_LINESEARCH)) continue;
+                if (!(st[p] == RSOT_OK || st[p] == RSOT_ERR_LINESEARCH ||
+                      st[p] == RSOT_ERR_NOT_CONVERGED))
+                    continue;
                 rsot_options o = *opt;
                 o.eps = eps[p];
                 o.eps_start = 0.0;   // FP64-corrected refinement of the batched result

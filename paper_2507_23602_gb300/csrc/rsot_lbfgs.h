@@ -30,6 +30,11 @@
 
 namespace rsot {
 
+// iterations without halving the gradient's L1 norm after which a run on
+// mixed-precision evaluations stops at their rounding floor (a refinement on
+// reference evaluations takes over)
+inline constexpr int kMixedStallWindow = 300;
+
 class LbfgsMachine {
    public:
     enum State { kIdle, kNeedF0, kSearch, kDone };
@@ -47,10 +52,17 @@ class LbfgsMachine {
         iters_ = 0;
         evals_ = 0;
         restarts_ = 0;
+        best_l1_ = INFINITY;
+        best_iter_ = 0;
         status_ = RSOT_OK;
         xt_ = x_;
         state_ = kNeedF0;
     }
+
+    // Noisy evaluations (mixed precision): stop with RSOT_ERR_LINESEARCH when
+    // the gradient's L1 norm has not halved within `window` iterations -- the
+    // rounding floor of the evaluation is reached.  0 (default): never.
+    void set_stall_window(int window) { stall_window_ = window; }
 
     // Continue from a known (x, f, g) (e.g. after a change of precision).
     void start_from(const std::vector<double> &x, double f, const std::vector<double> &g, double tol,
@@ -215,6 +227,17 @@ class LbfgsMachine {
             state_ = kDone;
             return;
         }
+        if (stall_window_ > 0) {
+            const double gn = norm1(g_);
+            if (gn < 0.5 * best_l1_) {
+                best_l1_ = gn;
+                best_iter_ = iters_;
+            } else if (iters_ - best_iter_ >= stall_window_) {
+                status_ = RSOT_ERR_LINESEARCH;
+                state_ = kDone;
+                return;
+            }
+        }
         // two-loop recursion
         std::vector<double> q = g_;
         const int k = (int)hist_.size();
@@ -258,6 +281,8 @@ class LbfgsMachine {
     static constexpr double kC1 = 1e-4, kC2 = 0.9;
     static constexpr int kMaxRestarts = 5;
     int restarts_ = 0;
+    int stall_window_ = 0, best_iter_ = 0;
+    double best_l1_ = INFINITY;
     size_t n_ = 0;
     double tol_ = 0.0, noise_rel_ = 0.0, noise_ = 0.0;
     int m_ = 10, max_iter_ = 10000;

@@ -204,6 +204,8 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             tol_run = std::max(tol, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5);
         if (last && prec == RSOT_COMPENSATED) tol_run = ref_tol;
         mc.start(x, tol_run, m, max_iter, D, prec == RSOT_FP64 ? 1e-13 : 1e-6);
+        // mixed evaluations: stop at their rounding floor instead of the cap
+        if (prec == RSOT_MIXED) mc.set_stall_window(rsot::kMixedStallWindow);
         ++stages;
         st = run_machine(ev, mc, opt->verbose, p);
         x = mc.x();
@@ -213,7 +215,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         evals += ev.evals;
         pairs += ev.pairs;
         const bool refine = last && opt->precision == RSOT_MIXED && opt->refine_fp64;
-        if (refine && (st == RSOT_OK || st == RSOT_ERR_LINESEARCH)) {
+        if (refine && (st == RSOT_OK || st == RSOT_ERR_LINESEARCH || st == RSOT_ERR_NOT_CONVERGED)) {
             // corrected refinement: one reference and one mixed evaluation per
             // correction, mixed L-BFGS on the corrected objective in between
             Evaluator ev64{p, n, eps, opt->tail, ref_prec};
