@@ -36,6 +36,12 @@ if ROOT not in sys.path:
 # it: the probe kernel of librsot (rsot_probe_ex2_rate) measures 9.99e12 ex2/s
 # on 152 SMs at ~2.05 GHz, i.e. 32 per SM per clock.  The roofline uses 32.
 SFU_EX2_PER_CLK_PER_SM = 32
+# FP32 lane-operations (add, mul, fma each one; packed f32x2 instructions two)
+# per clock per SM: 4 sub-partitions x 32 lanes
+FP32_LANE_OPS_PER_CLK_PER_SM = 128
+# FP32 lane-operations per pair of the compensated passes, counted from their
+# source: double-float exponent 3 x 12 + 3, shift TwoSum 6, Kahan 4, tail 2-3
+COMP_FP32_OPS_PER_PAIR = {"lse_df": 51, "grad_df": 52}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -52,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-trunc", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-compensated", action="store_true")
     ap.add_argument("--pair-kernel", choices=["auto", "tensor", "fp32"], default="auto",
                     help="dense workload: pair kernel of the timed evaluations")
     ap.add_argument("--tail", type=float, default=0.0,
@@ -461,6 +468,42 @@ def main():
                       "ms_per_step": sum(fms) / len(fms),
                       "per_kernel_ms": {k: v[0] / v[1] for k, v in fk.items()}}
 
+    # the compensated evaluation (double-float pair exponents, certified gradient
+    # bound): a secondary line, with its own roofline on the FP32 pipe
+    comp = None
+    if not args.no_compensated:
+        for _ in range(max(1, min(args.warmup, 2))):
+            P.eval(psi_d, p.eps, 0.0, rs.COMPENSATED, grad_out=grad_d)
+        P.kernel_timing(True)
+        cms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.eval(psi_d, p.eps, 0.0, rs.COMPENSATED, grad_out=grad_d)
+            b_.record()
+            torch.cuda.synchronize()
+            cms.append(a.elapsed_time(b_))
+        ck = {k: v[0] / v[1] for k, v in P.kernel_times().items()}
+        P.kernel_timing(False)
+        sms_c = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_max_c = float(measured_peaks().get("sm_max_mhz", 2070.0))
+        peak_ops = FP32_LANE_OPS_PER_CLK_PER_SM * sms_c * sm_max_c * 1e6 / 1e12
+        dom_c = max(("lse_df", "grad_df"), key=lambda k: ck.get(k, 0.0))
+        ops = COMP_FP32_OPS_PER_PAIR[dom_c] * pairs
+        ach = ops / (ck[dom_c] * 1e-3) / 1e12
+        comp = {"metric": "dual+grad G pairs/s (dense, compensated: double-float pair exponents)",
+                "value": pairs / (sum(cms) / len(cms) * 1e-3) / 1e9, "unit": "G pairs/s",
+                "ms_per_step": sum(cms) / len(cms), "per_kernel_ms": ck,
+                "grad_l1_error_bound": rs.COMPENSATED_GRAD_REL * float(p.mass.sum()),
+                "roofline": {"bound": "alu", "unit": "T FP32 lane-ops/s", "kernel": dom_c,
+                             "achieved": ach, "peak": peak_ops, "frac": ach / peak_ops,
+                             "peak_basis": f"{FP32_LANE_OPS_PER_CLK_PER_SM} FP32 lane-ops/clk/SM x "
+                                           f"{sms_c} SMs x {sm_max_c:.0f} MHz; "
+                                           f"{COMP_FP32_OPS_PER_PAIR[dom_c]} lane-ops per pair",
+                             "traffic": None}}
+
     # truncated evaluation at the tail-1e-12 radius (secondary line, same workload)
     trunc = None
     if not args.no_trunc:
@@ -555,6 +598,7 @@ def main():
         "e2e": e2e,
         "truncated": trunc,
         "fp32_pair_kernels": fp32_pairs,
+        "compensated": comp,
         "gpu_launches": int(sum(v[1] for v in ktimes.values())),
         "clocks": clk,
         "wall_s_timed_region": wall,

@@ -5,13 +5,19 @@
 // Log2 domain and translated coordinates as the mixed passes (rsot_dense.cu):
 // r_qj = c_j + x'_q.w_j with w_j = 2k y'_j, c_j = b_j - k|y'_j|^2, k =
 // log2(e)/(2 eps), every operand rounded from its FP64 value to head + tail.
-// Each product x.w is formed exactly as ph + pe (pe = fma(x, w, -ph)) plus the
-// cross terms x_h w_t + x_t w_h; the heads are summed with TwoSum, so r comes
-// with an absolute error of a few 2^-44 |c| instead of 2^-24 |c|.  The shift by
-// the running maximum (pass 1) or by u_q = log2 m_q - R_q (pass 2) is also a
-// TwoSum, so 2^(r - M) = ex2.approx(a_h) (1 + a_t ln2 + O(a_t^2)) with the tail
-// a_t folded in as a separately accumulated first-order correction.  Sums are
-// Kahan-compensated in FP32 within a tile and FP64 across tiles.
+// Each product x.w is formed exactly as ph + pe (pe = fma(x_h, w_h, -ph)) plus
+// the cross terms x_h w_t + x_t w_h; the heads are summed with TwoSum, so r
+// comes with an absolute error of a few 2^-44 |c| instead of 2^-24 |c|.  The
+// shift by the running maximum (pass 1) or by u_q = log2 m_q - R_q (pass 2) is
+// also a TwoSum, so 2^(r - M) = ex2.approx(a_h) (1 + a_t ln2 + O(a_t^2)), the
+// tail a_t folded in as a separately accumulated first-order correction.  Sums
+// are Kahan-compensated in FP32 within a tile and FP64 across tiles.
+//
+// Every step is an explicitly rounded add / mul / fma (no contraction), and
+// each thread carries two pairs in the two lanes of the packed FP32x2
+// instructions (add/sub/mul/fma .f32x2): two points per thread in pass 1, two
+// targets in pass 2; the shared-memory records of the other side hold each
+// value twice so that one 16-byte load gives both lanes' operand.
 //
 // Error budget, relative to each term (ex2.approx: measured <= 2^-22.71 over
 // 3 x 2^30 arguments; the budget takes 2^-22.5):
@@ -41,20 +47,73 @@ cudaError_t launch_finalize_log2(rsot_problem *p, const double *psi, double eps,
 
 namespace {
 
-constexpr int D_THREADS = 128;   // one point (pass 1) / one target (pass 2) per thread
-constexpr int D_TS = 256;        // records per shared-memory tile (divides n_pad and nq_pad)
-constexpr int D_SUB = 16;        // targets per max sub-tile (pass 1)
+constexpr int D_THREADS = 128;            // threads per block
+constexpr int D_ROWS = 2 * D_THREADS;     // points (pass 1) / targets (pass 2) per block
+constexpr int D_TS = 128;                 // records per shared-memory tile
+constexpr int D_SUB = 8;                  // targets per max sub-tile (pass 1)
 constexpr float kExcl = -1.0e30f;
 
-struct __align__(16) DRec {      // head/tail pairs (v0h, v0t, v1h, v1t), (v2h, v2t, sh, st)
-    float4 a, b;
+// 64-byte record, every value twice: (v0h, v0h, v0t, v0t), (v1h, ...), (v2h, ...),
+// (sh, sh, st, st) -- v = w (targets) or x' (points), s = c (targets) or u (points)
+struct __align__(16) DRec {
+    float4 a, b, c, d;
 };
 
-// s + e = a + b exactly (Knuth's TwoSum; no ordering requirement)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+typedef float2 f2;
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b rounded once: the product b * -1 is exact
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ f2 lo2(float4 v) { return make_float2(v.x, v.y); }   // heads
+__device__ __forceinline__ f2 hi2(float4 v) { return make_float2(v.z, v.w); }   // tails
+
+// s + e = a + b exactly in each lane (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum2(f2 a, f2 b, f2 &s, f2 &e) {
+    s = add2(a, b);
+    const f2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// s + e = a - b exactly in each lane (TwoSum of a and -b)
+__device__ __forceinline__ void two_diff2(f2 a, f2 b, f2 &s, f2 &e) {
+    s = sub2(a, b);
+    const f2 bb = sub2(s, a);
+    e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+__device__ __forceinline__ void kahan2(f2 &sum, f2 &comp, f2 v) {
+    const f2 y = sub2(v, comp);
+    const f2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
+// Operand held by the thread for its two lanes: head, tail, negated head.
+struct Op2 {
+    f2 h, t, nh;
+};
+
+// One coordinate: (s, lo) += R B with R the thread's operand and (Bh, Bt) the
+// shared one: ph = R_h B_h exactly as -nph, pe = R_h B_h - ph, cross terms.
+__device__ __forceinline__ void df_term2(const Op2 &R, f2 Bh, f2 Bt, f2 &s, f2 &lo) {
+    const f2 nph = mul2(R.nh, Bh);
+    const f2 pe = fma2(R.h, Bh, nph);
+    lo = fma2(R.h, Bt, lo);
+    lo = fma2(R.t, Bh, lo);
+    lo = add2(lo, pe);
+    f2 e;
+    two_diff2(s, nph, s, e);
+    lo = add2(lo, e);
+}
+
+template <int D>
+__device__ __forceinline__ void df_exponent2(const Op2 *R, const DRec &B, f2 sh, f2 st, f2 &rh,
+                                             f2 &rt) {
+    f2 s = sh, lo = st;
+    df_term2(R[0], lo2(B.a), hi2(B.a), s, lo);
+    df_term2(R[1], lo2(B.b), hi2(B.b), s, lo);
+    if (D == 3) df_term2(R[2], lo2(B.c), hi2(B.c), s, lo);
+    rh = add2(s, lo);                // |lo| << |s|: Fast2Sum renormalisation
+    rt = sub2(lo, sub2(rh, s));
 }
 
 __device__ __forceinline__ void split_f(double v, float &h, float &t) {
@@ -62,35 +121,25 @@ __device__ __forceinline__ void split_f(double v, float &h, float &t) {
     t = (float)(v - (double)h);
 }
 
-// one coordinate's contribution x w = ph + (pe + x_h w_t + x_t w_h)
-__device__ __forceinline__ void df_term(float xh, float xt, float wh, float wt, float &s,
-                                        float &lo) {
-    const float ph = xh * wh;
-    const float pe = fmaf(xh, wh, -ph);
-    lo += fmaf(xh, wt, fmaf(xt, wh, pe));
-    float sn, se;
-    two_sum(s, ph, sn, se);
-    s = sn;
-    lo += se;
+__device__ __forceinline__ DRec make_drec(const float *v /* 8: h,t pairs */) {
+    DRec r;
+    r.a = make_float4(v[0], v[0], v[1], v[1]);
+    r.b = make_float4(v[2], v[2], v[3], v[3]);
+    r.c = make_float4(v[4], v[4], v[5], v[5]);
+    r.d = make_float4(v[6], v[6], v[7], v[7]);
+    return r;
 }
 
-// r = c + sum_t x_t w_t as (rh, rt); x from a point record, (w, c) from a
-// target record
-template <int D>
-__device__ __forceinline__ void df_exponent(const DRec &x, const DRec &t, float &rh, float &rt) {
-    float s = t.b.z, lo = t.b.w;
-    df_term(x.a.x, x.a.y, t.a.x, t.a.y, s, lo);
-    df_term(x.a.z, x.a.w, t.a.z, t.a.w, s, lo);
-    if (D == 3) df_term(x.b.x, x.b.y, t.b.x, t.b.y, s, lo);
-    rh = s + lo;                 // |lo| << |s|: Fast2Sum renormalisation
-    rt = lo - (rh - s);
-}
-
-__device__ __forceinline__ void kahan(float &sum, float &comp, float v) {
-    const float y = v - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
+// the two lanes' operands from two records (lane 0 from r0, lane 1 from r1)
+__device__ __forceinline__ void load_ops(const DRec &r0, const DRec &r1, Op2 *R, f2 &sh, f2 &st) {
+    const float4 *a0 = &r0.a, *a1 = &r1.a;
+    for (int t = 0; t < 3; ++t) {
+        R[t].h = make_float2(a0[t].x, a1[t].x);
+        R[t].t = make_float2(a0[t].z, a1[t].z);
+        R[t].nh = make_float2(-a0[t].x, -a1[t].x);
+    }
+    sh = make_float2(r0.d.x, r1.d.x);
+    st = make_float2(r0.d.z, r1.d.z);
 }
 
 // FP32 distance test c(x, y) < C with the margin; the FP64 test of the FP64
@@ -140,10 +189,7 @@ __global__ void k_prep_df(const double *__restrict__ psi, const double *__restri
             split_f(fmax(b - k * yy, -1.0e29), v[6], v[7]);
             contrib = ps * nu[j];
         }
-        DRec r;
-        r.a = make_float4(v[0], v[1], v[2], v[3]);
-        r.b = make_float4(v[4], v[5], v[6], v[7]);
-        trec[j] = r;
+        trec[j] = make_drec(v);
     }
     const double s = block_sum_d(contrib, sh);
     if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
@@ -156,13 +202,10 @@ __global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t 
                             DRec *__restrict__ prec, float *__restrict__ ys) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nq_pad) {
-        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kExcl, 0.f};
         if (i < nq)
             for (int t = 0; t < d; ++t) split_f(x64[i * d + t], v[2 * t], v[2 * t + 1]);
-        DRec r;
-        r.a = make_float4(v[0], v[1], v[2], v[3]);
-        r.b = make_float4(v[4], v[5], kExcl, 0.f);
-        prec[i] = r;
+        prec[i] = make_drec(v);
     }
     if (i < n_alloc)
         for (int t = 0; t < 3; ++t)
@@ -170,7 +213,8 @@ __global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t 
 }
 
 // Pass 1: R_q = log2 sum_{j in I_q} 2^{r_qj} with an integral running shift M,
-// u_q = log2 m_q - R_q into the point record, sum_q m_q R_q by block.
+// u_q = log2 m_q - R_q into the point record, sum_q m_q R_q by block.  Lane l
+// of a thread is point blockIdx.x * D_ROWS + l * D_THREADS + threadIdx.x.
 template <int D, bool TRUNC>
 __global__ void __launch_bounds__(D_THREADS)
     k_lse_df(DRec *__restrict__ prec, const float *__restrict__ xs, const double *__restrict__ x64,
@@ -185,15 +229,20 @@ __global__ void __launch_bounds__(D_THREADS)
     __shared__ double sh[32];
     __shared__ unsigned long long s_cnt, s_empty;
     if (threadIdx.x == 0) s_cnt = s_empty = 0;
-    const int64_t q = (int64_t)blockIdx.x * D_THREADS + threadIdx.x;   // < nq_pad
-    const DRec pr = prec[q];
-    float xf[3] = {0.f, 0.f, 0.f};
+    int64_t q[2];
+    q[0] = (int64_t)blockIdx.x * D_ROWS + threadIdx.x;   // < nq_pad
+    q[1] = q[0] + D_THREADS;
+    const DRec p0 = prec[q[0]], p1 = prec[q[1]];
+    Op2 X[3];
+    f2 unused_h, unused_t;
+    load_ops(p0, p1, X, unused_h, unused_t);
+    float xf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     if (TRUNC)
-        for (int t = 0; t < D; ++t) xf[t] = xs[t * nq_pad + q];
-    const int64_t qx = q < nq ? q : 0;   // FP64 coordinates for the rare exact test
+        for (int l = 0; l < 2; ++l)
+            for (int t = 0; t < D; ++t) xf[l][t] = xs[t * nq_pad + q[l]];
     const int64_t n_rec = (n + D_TS - 1) / D_TS * D_TS;
-    float M = -INFINITY;
-    double S = 0.0;
+    float M[2] = {-INFINITY, -INFINITY};
+    double S[2] = {0.0, 0.0};
     unsigned long long npair = 0;
     for (int64_t t0 = 0; t0 < n_rec; t0 += D_TS) {
         __syncthreads();
@@ -203,74 +252,96 @@ __global__ void __launch_bounds__(D_THREADS)
                 for (int t = 0; t < 3; ++t) sy[t][i] = ys[t * n_alloc + t0 + i];
         }
         __syncthreads();
-        float s = 0.f, comp = 0.f, cs = 0.f;
+        f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
         for (int u0 = 0; u0 < D_TS; u0 += D_SUB) {
-            float rh[D_SUB], rt[D_SUB];
-            float mx = -INFINITY;
+            f2 rh[D_SUB], rt[D_SUB];
+            float mx0 = -INFINITY, mx1 = -INFINITY;
 #pragma unroll
             for (int i = 0; i < D_SUB; ++i) {
-                df_exponent<D>(pr, sm[u0 + i], rh[i], rt[i]);
+                const DRec &B = sm[u0 + i];
+                df_exponent2<D>(X, B, lo2(B.d), hi2(B.d), rh[i], rt[i]);
                 if (TRUNC) {
                     const float yf[3] = {sy[0][u0 + i], sy[1][u0 + i], sy[2][u0 + i]};
                     const int64_t j = t0 + u0 + i;
-                    const bool k = j < n && q < nq &&
-                                   keep_pair<D>(xf, yf, C, margin, x64 + qx * D, y64 + j * D, C64);
-                    if (k) {
-                        ++npair;
-                    } else {
-                        rh[i] = kExcl;
-                        rt[i] = 0.f;
+                    for (int l = 0; l < 2; ++l) {
+                        const bool k = j < n && q[l] < nq &&
+                                       keep_pair<D>(xf[l], yf, C, margin, x64 + q[l] * D, y64 + j * D, C64);
+                        if (k) {
+                            ++npair;
+                        } else if (l == 0) {
+                            rh[i].x = kExcl;
+                            rt[i].x = 0.f;
+                        } else {
+                            rh[i].y = kExcl;
+                            rt[i].y = 0.f;
+                        }
                     }
                 }
-                mx = fmaxf(mx, rh[i]);
+                mx0 = fmaxf(mx0, rh[i].x);
+                mx1 = fmaxf(mx1, rh[i].y);
             }
-            if (mx > M && mx > -1.0e29f) {   // raise the shift to ceil(max): exact rescaling
-                const float mn = ceilf(mx);
-                if (M != -INFINITY) {
-                    const float f = pow2_int_f(M - mn);
-                    s *= f;
-                    comp *= f;
-                    cs *= f;
-                    S *= pow2_int_d(M - mn);
+            if (mx0 > M[0] || mx1 > M[1]) {   // raise a shift to ceil(max): exact rescaling
+                float f[2] = {1.f, 1.f};
+                const float mx[2] = {mx0, mx1};
+                for (int l = 0; l < 2; ++l) {
+                    if (mx[l] > M[l] && mx[l] > -1.0e29f) {
+                        const float mn = ceilf(mx[l]);
+                        if (M[l] != -INFINITY) {
+                            f[l] = pow2_int_f(M[l] - mn);
+                            S[l] *= pow2_int_d(M[l] - mn);
+                        }
+                        M[l] = mn;
+                    }
                 }
-                M = mn;
+                const f2 ff = make_float2(f[0], f[1]);
+                s = mul2(s, ff);
+                comp = mul2(comp, ff);
+                cs = mul2(cs, ff);
             }
-            if (M == -INFINITY) continue;    // no pair kept so far
+            // a lane with no kept pair yet subtracts a huge shift: its terms are 0
+            const f2 Me = make_float2(M[0] == -INFINITY ? 1.0e30f : M[0],
+                                      M[1] == -INFINITY ? 1.0e30f : M[1]);
 #pragma unroll
             for (int i = 0; i < D_SUB; ++i) {
-                float ah, ae;
-                two_sum(rh[i], -M, ah, ae);
-                const float e = ex2_approx(ah);
-                kahan(s, comp, e);
-                cs = fmaf(e, ae + rt[i], cs);
+                f2 ah, ae;
+                two_diff2(rh[i], Me, ah, ae);
+                const f2 e = make_float2(ex2_approx(ah.x), ex2_approx(ah.y));
+                kahan2(s, comp, e);
+                cs = fma2(e, add2(ae, rt[i]), cs);
             }
         }
-        S += ((double)s - (double)comp) + kLn2 * (double)cs;
+        S[0] += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
+        S[1] += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
     }
     double contrib = 0.0;
-    float uh = kExcl, ut = 0.f;
-    if (q < nq) {
-        if (S > 0.0) {
-            const double R = (double)M + log2(S);
-            lse_buf[q] = R;
-            if (mass[q] > 0.0) {
-                contrib = mass[q] * R;
-                split_f(lmass2[q] - R, uh, ut);
-            }
-        } else {   // empty I_q: skipped by Algorithm 2
-            lse_buf[q] = -INFINITY;
-            atomicAdd(&s_empty, 1ull);
-            // the finalisation adds psi_c m_q - m_q |x'_q|^2 / 2 for every point
-            // (sum m_q, hx): cancel this point's share in the log2 sum it scales
-            if (mass[q] > 0.0) {
-                double r2 = 0.0;
-                for (int t = 0; t < D; ++t) r2 += x64[q * D + t] * x64[q * D + t];
-                contrib = -mass[q] * (psi[0] - 0.5 * r2) / (eps * kLn2);
+    int empties = 0;
+    for (int l = 0; l < 2; ++l) {
+        const int64_t qq = q[l];
+        float uh = kExcl, ut = 0.f;
+        if (qq < nq) {
+            if (S[l] > 0.0) {
+                const double R = (double)M[l] + log2(S[l]);
+                lse_buf[qq] = R;
+                if (mass[qq] > 0.0) {
+                    contrib += mass[qq] * R;
+                    split_f(lmass2[qq] - R, uh, ut);
+                }
+            } else {   // empty I_q: skipped by Algorithm 2
+                lse_buf[qq] = -INFINITY;
+                ++empties;
+                // the finalisation adds psi_c m_q - m_q |x'_q|^2 / 2 for every point
+                // (sum m_q, hx): cancel this point's share in the log2 sum it scales
+                if (mass[qq] > 0.0) {
+                    double r2 = 0.0;
+                    for (int t = 0; t < D; ++t) r2 += x64[qq * D + t] * x64[qq * D + t];
+                    contrib -= mass[qq] * (psi[0] - 0.5 * r2) / (eps * kLn2);
+                }
             }
         }
-        if (TRUNC) atomicAdd(&s_cnt, npair);
+        prec[qq].d = make_float4(uh, uh, ut, ut);
     }
-    prec[q].b = make_float4(pr.b.x, pr.b.y, uh, ut);
+    if (TRUNC && npair) atomicAdd(&s_cnt, npair);
+    if (empties) atomicAdd(&s_empty, (unsigned long long)empties);
     const double sum = block_sum_d(contrib, sh);
     if (threadIdx.x == 0) {
         blockJ[blockIdx.x] = sum;
@@ -280,6 +351,7 @@ __global__ void __launch_bounds__(D_THREADS)
 }
 
 // Pass 2: per target, sum over one point chunk of 2^{r_qj + u_q} = m_q p_qj.
+// Lane l of a thread is target blockIdx.x * D_ROWS + l * D_THREADS + threadIdx.x.
 template <int D, bool TRUNC>
 __global__ void __launch_bounds__(D_THREADS)
     k_grad_df(const DRec *__restrict__ trec, const float *__restrict__ ys,
@@ -289,15 +361,19 @@ __global__ void __launch_bounds__(D_THREADS)
               float margin, double C64, double *__restrict__ part2) {
     __shared__ DRec sm[D_TS];
     __shared__ float sx[TRUNC ? 3 : 1][D_TS];
-    const int64_t j = (int64_t)blockIdx.x * D_THREADS + threadIdx.x;   // < n_alloc
-    const DRec tr = trec[j];
-    float yf[3] = {0.f, 0.f, 0.f};
+    int64_t j[2];
+    j[0] = (int64_t)blockIdx.x * D_ROWS + threadIdx.x;   // < n_alloc
+    j[1] = j[0] + D_THREADS;
+    Op2 W[3];
+    f2 Ch, Ct;
+    load_ops(trec[j[0]], trec[j[1]], W, Ch, Ct);
+    float yf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     if (TRUNC)
-        for (int t = 0; t < D; ++t) yf[t] = ys[t * n_alloc + j];
-    const int64_t jy = j < n ? j : 0;
+        for (int l = 0; l < 2; ++l)
+            for (int t = 0; t < D; ++t) yf[l][t] = ys[t * n_alloc + j[l]];
     const int64_t p_begin = (int64_t)blockIdx.y * chunk;
     const int64_t p_end = min(nq_pad, p_begin + chunk);
-    double acc = 0.0;
+    double acc0 = 0.0, acc1 = 0.0;
     for (int64_t p0 = p_begin; p0 < p_end; p0 += D_TS) {
         __syncthreads();
         for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
@@ -306,27 +382,39 @@ __global__ void __launch_bounds__(D_THREADS)
                 for (int t = 0; t < 3; ++t) sx[t][i] = t < D ? xs[t * nq_pad + p0 + i] : 0.f;
         }
         __syncthreads();
-        float s = 0.f, comp = 0.f, cs = 0.f;
-#pragma unroll 4
+        f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
+#pragma unroll 2
         for (int i = 0; i < D_TS; ++i) {
-            float rh, rt;
-            df_exponent<D>(sm[i], tr, rh, rt);
-            float th, te;
-            two_sum(rh, sm[i].b.z, th, te);
-            float e = ex2_approx(th);
+            const DRec &B = sm[i];
+            f2 rh, rt;
+            df_exponent2<D>(W, B, Ch, Ct, rh, rt);
+            f2 th, te;
+            two_sum2(rh, lo2(B.d), th, te);
+            f2 e = make_float2(ex2_approx(th.x), ex2_approx(th.y));
             if (TRUNC) {
                 const float xf[3] = {sx[0][i], sx[1][i], sx[2][i]};
                 const int64_t qq = p0 + i;
-                const bool k = qq < nq && j < n &&
-                               keep_pair<D>(xf, yf, C, margin, x64 + qq * D, y64 + jy * D, C64);
-                if (!k) e = 0.f;
+                if (!(qq < nq && j[0] < n &&
+                      keep_pair<D>(xf, yf[0], C, margin, x64 + qq * D, y64 + j[0] * D, C64)))
+                    e.x = 0.f;
+                if (!(qq < nq && j[1] < n &&
+                      keep_pair<D>(xf, yf[1], C, margin, x64 + qq * D, y64 + j[1] * D, C64)))
+                    e.y = 0.f;
             }
-            kahan(s, comp, e);
-            cs = fmaf(e, te + rt + sm[i].b.w, cs);
+            kahan2(s, comp, e);
+            cs = fma2(e, add2(add2(te, rt), hi2(B.d)), cs);
         }
-        acc += ((double)s - (double)comp) + kLn2 * (double)cs;
+        acc0 += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
+        acc1 += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
     }
-    part2[(int64_t)blockIdx.y * n_alloc + j] = acc;
+    part2[(int64_t)blockIdx.y * n_alloc + j[0]] = acc0;
+    part2[(int64_t)blockIdx.y * n_alloc + j[1]] = acc1;
+}
+
+int occupancy_df(const void *f) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, D_THREADS, 0);
+    return std::max(b, 1);
 }
 
 template <int D>
@@ -334,6 +422,15 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
                           double *grad) {
     cudaStream_t st = p->stream;
     cudaError_t e;
+    const bool trunc = cutoff < INFINITY;
+    // point chunks of whole tiles for pass 2: enough blocks for four waves
+    const int64_t tblocks = p->n_pad / D_ROWS, tiles = p->nq_pad / D_TS;
+    const void *f2p = trunc ? (const void *)k_grad_df<D, true> : (const void *)k_grad_df<D, false>;
+    const int64_t want = 4LL * p->num_sms * occupancy_df(f2p);
+    int64_t s2 = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(tiles, 64),
+                                                        (want + tblocks - 1) / tblocks));
+    const int64_t chunk = (tiles + s2 - 1) / s2 * D_TS;
+    s2 = (p->nq_pad + chunk - 1) / chunk;
     if (!p->df_prec) {
         if ((e = cudaMalloc(&p->df_prec, (size_t)p->nq_pad * sizeof(DRec)))) return e;
         if ((e = cudaMalloc(&p->df_trec, (size_t)p->n_pad * sizeof(DRec)))) return e;
@@ -344,9 +441,15 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
             reinterpret_cast<DRec *>(p->df_prec), p->df_ys);
         if ((e = cudaGetLastError())) return e;
     }
+    if (p->df_s2 < s2) {
+        cudaFree(p->df_part2);
+        p->df_part2 = nullptr;
+        p->df_s2 = 0;
+        if ((e = cudaMalloc(&p->df_part2, (size_t)s2 * p->n_pad * sizeof(double)))) return e;
+        p->df_s2 = (int)s2;
+    }
     DRec *prec = reinterpret_cast<DRec *>(p->df_prec);
     DRec *trec = reinterpret_cast<DRec *>(p->df_trec);
-    const bool trunc = cutoff < INFINITY;
     // |c_32 - c| <= 2^-19 max|coord|^2 + 2^-23 c (FP32 rounding of the translated
     // coordinates, their differences and squares); the margin is 4x that
     const float C = trunc ? (float)cutoff : 0.f;
@@ -355,7 +458,7 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
     k_prep_df<<<p->nblk_prep, 256, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad, p->d, eps,
                                            trec, p->psinu, p->flags);
     trace_end(p);
-    const unsigned nb1 = (unsigned)(p->nq_pad / D_THREADS);
+    const unsigned nb1 = (unsigned)(p->nq_pad / D_ROWS);
     trace_begin(p, "lse_df");
     if (trunc)
         k_lse_df<D, true><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec,
@@ -368,23 +471,19 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
                                                       cutoff, p->lmass2, p->mass, psi, eps,
                                                       p->blockJ, p->lse_buf, p->res_dev);
     trace_end(p);
-    // point chunks of whole tiles, at most s2_64 of them (the FP64 partials buffer)
-    const int64_t tiles = p->nq_pad / D_TS;
-    const int64_t chunk = (tiles + p->s2_64 - 1) / p->s2_64 * D_TS;
-    const int s2 = (int)((p->nq_pad + chunk - 1) / chunk);
-    dim3 g2((unsigned)(p->n_pad / D_THREADS), (unsigned)s2);
+    dim3 g2((unsigned)tblocks, (unsigned)s2);
     trace_begin(p, "grad_df");
     if (trunc)
         k_grad_df<D, true><<<g2, D_THREADS, 0, st>>>(trec, p->df_ys, p->y64, p->n, p->n_pad, prec,
                                                      p->xs, p->x64, p->nq, p->nq_pad, chunk, C,
-                                                     margin, cutoff, p->part2_64);
+                                                     margin, cutoff, p->df_part2);
     else
         k_grad_df<D, false><<<g2, D_THREADS, 0, st>>>(trec, p->df_ys, p->y64, p->n, p->n_pad, prec,
                                                       p->xs, p->x64, p->nq, p->nq_pad, chunk, C,
-                                                      margin, cutoff, p->part2_64);
+                                                      margin, cutoff, p->df_part2);
     trace_end(p);
     if ((e = cudaGetLastError())) return e;
-    return launch_finalize_log2(p, psi, eps, p->part2_64, s2, (int)nb1, grad);
+    return launch_finalize_log2(p, psi, eps, p->df_part2, (int)s2, (int)nb1, grad);
 }
 
 }  // namespace
@@ -401,8 +500,11 @@ void compensated_free(rsot_problem *p) {
     cudaFree(p->df_prec);
     cudaFree(p->df_trec);
     cudaFree(p->df_ys);
+    cudaFree(p->df_part2);
     p->df_prec = p->df_trec = nullptr;
     p->df_ys = nullptr;
+    p->df_part2 = nullptr;
+    p->df_s2 = 0;
 }
 
 }  // namespace rsot

@@ -112,9 +112,11 @@ struct rsot_problem {
     int64_t chunk2_64 = 0;
     double *part2_64 = nullptr;     // [s2_64][n_pad]
     // compensated path scratch (rsot_df.cu), allocated on first use
-    void *df_prec = nullptr;        // [nq_pad] point head/tail records (32 B)
-    void *df_trec = nullptr;        // [n_pad] target head/tail records (32 B)
+    void *df_prec = nullptr;        // [nq_pad] point head/tail records (64 B)
+    void *df_trec = nullptr;        // [n_pad] target head/tail records (64 B)
     float *df_ys = nullptr;         // [3][n_pad] FP32 target coordinates
+    double *df_part2 = nullptr;     // [df_s2][n_pad] pass-2 partials
+    int df_s2 = 0;
 
     // staging for host psi / grad
     double *psi_dev = nullptr;      // [n]

@@ -17,16 +17,19 @@
 //     replaces sufficient decrease.
 // With MIXED precision and refine_fp64, the last stage runs mixed evaluations
 // down to mixed_tol_l1 (default 1e-5, above the FP32 rounding floor of the
-// gradient), then refines with corrections from a reference evaluation: a
-// reference and a mixed evaluation at the iterate give the systematic
-// mixed-precision error, and mixed L-BFGS continues on the corrected objective
-// (at most 200 iterations per correction) until the reference gradient meets
-// the tolerance; when a correction no longer halves the reference gradient
-// (tol below the mixed noise floor), plain L-BFGS on reference evaluations
-// finishes from the corrected iterate.  The reference is the compensated
-// evaluation (rsot_df.cu), stopped at tol - B with B = 6.5e-7 sum m_q its
-// certified gradient error, so that ||grad J||_1 <= tol holds; FP64 where B
-// leaves too little room under tol or on request.
+// gradient), then refines on reference evaluations.  The reference is the
+// compensated evaluation (rsot_df.cu), stopped at tol - B with B = 6.5e-7
+// sum m_q its certified gradient error, so that ||grad J||_1 <= tol holds.  At
+// about ten mixed evaluations per compensated one, one correction (as below)
+// runs mixed L-BFGS on the corrected objective until its rounding noise stops
+// it, then L-BFGS on compensated evaluations finishes.  Where B leaves too
+// little room under tol (or on request) the reference is FP64, three hundred
+// times dearer than a mixed evaluation; then a reference and a mixed
+// evaluation at the iterate give the
+// systematic mixed-precision error, mixed L-BFGS continues on the corrected
+// objective (at most 200 iterations per correction) until the FP64 gradient
+// meets tol, and when a correction no longer halves the FP64 gradient (tol
+// below the mixed noise floor) plain FP64 L-BFGS finishes.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -101,6 +104,10 @@ struct CorrectedEvaluator {
         return RSOT_OK;
     }
 };
+
+// iterations without halving the corrected objective's gradient after which
+// a correction's mixed run stops at its rounding noise
+constexpr int kCorrStallWindow = 25;
 
 double norm1(const std::vector<double> &a) {
     double s = 0.0;
@@ -215,7 +222,51 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         evals += ev.evals;
         pairs += ev.pairs;
         const bool refine = last && opt->precision == RSOT_MIXED && opt->refine_fp64;
-        if (refine && (st == RSOT_OK || st == RSOT_ERR_LINESEARCH || st == RSOT_ERR_NOT_CONVERGED)) {
+        const bool refine_ok = st == RSOT_OK || st == RSOT_ERR_LINESEARCH || st == RSOT_ERR_NOT_CONVERGED;
+        if (refine && refine_ok && ref_prec == RSOT_COMPENSATED) {
+            // a compensated evaluation costs about ten mixed ones.  One correction
+            // first: the compensated and the mixed gradient at the iterate give
+            // the systematic mixed error, and mixed L-BFGS on the corrected
+            // objective runs until its own rounding noise stops it (no halving
+            // in kCorrStallWindow iterations); then L-BFGS on compensated
+            // evaluations finishes from there (the D-scaled first step is
+            // Newton-like near the optimum: a few iterations)
+            Evaluator evc{p, n, eps, opt->tail, RSOT_COMPENSATED};
+            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
+            const int kernel_before = rsot::pair_kernel_of(p);
+            rsot_set_pair_kernel(p, RSOT_PAIRS_FP32);
+            double fc = 0.0, fm = 0.0;
+            std::vector<double> gc(n), gm(n);
+            st = evc(x, fc, gc);
+            if (!st) st = evm(x, fm, gm);
+            const bool corrected = !st && norm1(gc) > ref_tol;
+            if (corrected) {
+                CorrectedEvaluator ce{evm, std::vector<double>(n), x, fc - fm, n, eps};
+                for (int64_t j = 0; j < n; ++j) ce.b[j] = gc[j] - gm[j];
+                rsot::LbfgsMachine mcc;
+                mcc.start_from(x, fc, gc, 0.5 * ref_tol, m, std::min(max_iter, 200), D, 1e-6);
+                mcc.set_stall_window(kCorrStallWindow);
+                const rsot_status sc = run_machine(ce, mcc, opt->verbose, p);
+                if (sc && sc != RSOT_ERR_LINESEARCH && sc != RSOT_ERR_NOT_CONVERGED) st = sc;
+                iters += mcc.iters();
+                x = mcc.x();
+            }
+            rsot_set_pair_kernel(p, (rsot_pair_kernel)kernel_before);
+            if (!st) {
+                rsot::LbfgsMachine mcr;
+                if (corrected)
+                    mcr.start(x, ref_tol, m, max_iter, D, ref_noise);
+                else
+                    mcr.start_from(x, fc, gc, ref_tol, m, max_iter, D, ref_noise);
+                st = run_machine(evc, mcr, opt->verbose, p);
+                x = mcr.x();
+                f = mcr.f();
+                g = mcr.g();
+                iters += mcr.iters();
+            }
+            evals += evc.evals + evm.evals;
+            pairs += evc.pairs + evm.pairs;
+        } else if (refine && refine_ok) {
             // corrected refinement: one reference and one mixed evaluation per
             // correction, mixed L-BFGS on the corrected objective in between
             Evaluator ev64{p, n, eps, opt->tail, ref_prec};
