@@ -10,6 +10,9 @@ Contents
   * ``dual_grad``      -- Algorithm 2, dense (cutoff=inf) or truncated with the
                           strict predicate c(x_q, y_j) < C tested for every j
                           (Eq. discretized_functional / discretized_gradient).
+  * ``dual_grad_sep``  -- the same with a separable cutoff per pair,
+                          c(x_q, y_j) < alpha_q + beta_j.
+  * ``nearest``        -- the nearest target of every point (brute force).
   * ``plan``           -- the plan density p_j(x_q | psi), Eq. final_plan_density.
   * ``point_lse``      -- the per-point log partition L_q of Eq. discretized_functional.
   * ``covering_cost``  -- C_0 of App. B over the quadrature points.
@@ -62,6 +65,11 @@ def _load():
                                               ctypes.POINTER(ctypes.c_int64)]
         lib.oracle_centroids.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp,
                                          dp, dp, ctypes.c_double, dp, dp]
+        lib.oracle_dual_grad_sep.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64,
+                                             dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int, dp,
+                                             dp, i64p, i64p]
+        lib.oracle_nearest.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
+                                       ctypes.c_int, i64p, dp]
         _lib = lib
     return _lib
 
@@ -96,6 +104,49 @@ def dual_grad(x, mass, y, nu, psi, eps, cutoff=math.inf, threads=0):
     if rc != 0:
         raise ValueError(f"oracle_dual_grad failed ({rc})")
     return J.value, grad, pairs.value, empty.value
+
+
+def dual_grad_sep(x, mass, y, nu, psi, eps, alpha, beta, threads=0):
+    """(J, grad, pairs, empty) of Algorithm 2 with the separable cutoff
+    I_q = {j : c(x_q, y_j) < alpha_q + beta_j} (see truncation.separable_cutoffs)."""
+    lib = _load()
+    x, xp = _f64(x)
+    y, yp = _f64(y)
+    mass, mp = _f64(mass)
+    nu, nup = _f64(nu)
+    psi, pp = _f64(psi)
+    alpha, ap = _f64(alpha)
+    beta, bp = _f64(beta)
+    d = x.shape[1] if x.ndim == 2 else 1
+    n = y.shape[0]
+    grad = np.empty(n)
+    J = ctypes.c_double()
+    pairs = ctypes.c_int64()
+    empty = ctypes.c_int64()
+    rc = lib.oracle_dual_grad_sep(d, x.shape[0], xp, mp, n, yp, nup, pp, float(eps), ap, bp,
+                                  int(threads), ctypes.byref(J),
+                                  grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.byref(pairs), ctypes.byref(empty))
+    if rc != 0:
+        raise ValueError(f"oracle_dual_grad_sep failed ({rc})")
+    return J.value, grad, pairs.value, empty.value
+
+
+def nearest(x, y, threads=0):
+    """(j, c): the nearest target of every point (lowest index among equal
+    costs) and its cost c(x_q, y_j), brute force in FP64."""
+    lib = _load()
+    x, xp = _f64(x)
+    y, yp = _f64(y)
+    nq, d = x.shape
+    js = np.zeros(nq, dtype=np.int64)
+    cs = np.zeros(nq)
+    rc = lib.oracle_nearest(d, nq, xp, y.shape[0], yp, int(threads),
+                            js.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            cs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc:
+        raise ValueError(f"oracle_nearest failed ({rc})")
+    return js, cs
 
 
 def plan(x, y, nu, psi, eps):

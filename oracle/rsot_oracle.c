@@ -77,14 +77,17 @@ int oracle_threads_used(int requested) { return nthreads_of(requested); }
 /*
  * Algorithm 2 (dense when cutoff = +inf).
  * x: nq*d row-major, mass: nq, y: n*d row-major, nu: n, psi: n.
+ * Membership: c(x_q, y_j) < cutoff, or, when alpha and beta are given,
+ * c(x_q, y_j) < alpha_q + beta_j (a cutoff per pair, separable).
  * Outputs: *J_out, grad_out[n]; optional pairs_out = sum_q |I_q|,
  * empty_out = number of points with an empty I_q.
  * Returns 0 on success, -1 on bad arguments, -2 on allocation failure.
  */
-int oracle_dual_grad(int d, int64_t nq, const double *x, const double *mass,
-                     int64_t n, const double *y, const double *nu, const double *psi,
-                     double eps, double cutoff, int threads,
-                     double *J_out, double *grad_out, int64_t *pairs_out, int64_t *empty_out)
+static int dual_grad_impl(int d, int64_t nq, const double *x, const double *mass,
+                          int64_t n, const double *y, const double *nu, const double *psi,
+                          double eps, double cutoff, const double *alpha, const double *beta,
+                          int threads, double *J_out, double *grad_out, int64_t *pairs_out,
+                          int64_t *empty_out)
 {
     if (d < 1 || d > 3 || nq < 0 || n < 1 || !(eps > 0.0))
         return -1;
@@ -122,7 +125,7 @@ int oracle_dual_grad(int d, int64_t nq, const double *x, const double *mass,
             int64_t cnt = 0;
             for (int64_t j = 0; j < n; ++j) {
                 double c = cost(d, xq, y + j * d);
-                in[j] = (unsigned char)(c < cutoff);
+                in[j] = (unsigned char)(alpha ? c < alpha[q] + beta[j] : c < cutoff);
                 if (in[j]) {
                     s[j] = (psi[j] - c) / eps + log(nu[j]);
                     if (s[j] > smax)
@@ -173,6 +176,57 @@ int oracle_dual_grad(int d, int64_t nq, const double *x, const double *mass,
         *empty_out = e;
     }
     free(gpart); free(jpart); free(ppart); free(epart); free(sbuf); free(inbuf);
+    return 0;
+}
+
+int oracle_dual_grad(int d, int64_t nq, const double *x, const double *mass,
+                     int64_t n, const double *y, const double *nu, const double *psi,
+                     double eps, double cutoff, int threads,
+                     double *J_out, double *grad_out, int64_t *pairs_out, int64_t *empty_out)
+{
+    return dual_grad_impl(d, nq, x, mass, n, y, nu, psi, eps, cutoff, NULL, NULL, threads,
+                          J_out, grad_out, pairs_out, empty_out);
+}
+
+/* Algorithm 2 with I_q = { j : c(x_q, y_j) < alpha_q + beta_j }. */
+int oracle_dual_grad_sep(int d, int64_t nq, const double *x, const double *mass,
+                         int64_t n, const double *y, const double *nu, const double *psi,
+                         double eps, const double *alpha, const double *beta, int threads,
+                         double *J_out, double *grad_out, int64_t *pairs_out, int64_t *empty_out)
+{
+    if (!alpha || !beta)
+        return -1;
+    return dual_grad_impl(d, nq, x, mass, n, y, nu, psi, eps, INFINITY, alpha, beta, threads,
+                          J_out, grad_out, pairs_out, empty_out);
+}
+
+/*
+ * Nearest target of every point: j_out[q] = argmin_j c(x_q, y_j) (the lowest
+ * index among equal costs), c_out[q] = that cost.  Brute force in FP64.
+ */
+int oracle_nearest(int d, int64_t nq, const double *x, int64_t n, const double *y, int threads,
+                   int64_t *j_out, double *c_out)
+{
+    if (d < 1 || d > 3 || nq < 0 || n < 1)
+        return -1;
+    int T = nthreads_of(threads);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static)
+#endif
+    for (int64_t q = 0; q < nq; ++q) {
+        double best = INFINITY;
+        int64_t bj = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            double c = cost(d, x + q * d, y + j * d);
+            if (c < best) {
+                best = c;
+                bj = j;
+            }
+        }
+        j_out[q] = bj;
+        c_out[q] = best;
+    }
+    (void)T;
     return 0;
 }
 

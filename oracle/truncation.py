@@ -16,6 +16,19 @@ Sec. 4.1 and App. B define the cost cutoff C used in I_q = {j : c(x_q,y_j) < C}.
     point, |J - J_trunc| <= eps * tail * sum_q m_q, and per target
     |dJ/dpsi_j - dJ_trunc/dpsi_j| <= tail * (sum_q m_q p~_qj + nu_j).
 
+  * separable (psi-aware, per pair; the cell-list pruning uses it):
+        c(x_q, y_j) < alpha_q + beta_j,
+        alpha_q = c(x_q, y_n) - psi_n - eps ln nu_n   (n = n(q), a nearest target of x_q),
+        beta_j  = psi_j + eps ln(1 / tail).
+    The same geometric argument with the point's own nearest target as the
+    anchor: s_qn = (psi_n - c(x_q, y_n))/eps + ln nu_n is a term of S_trunc(x_q)
+    (its pair is kept: alpha_q + beta_n - c_qn = eps ln(1/(nu_n tail)) > 0), and
+    every excluded term has exp(s_qj) <= tail nu_j exp(s_qn), so the excluded
+    mass is at most
+    tail * sum_j nu_j * S_trunc(x) at every point: the guarantees of C_tail
+    with sum nu in place of 1.  alpha_q + beta_j <= C_tail for every pair, so
+    the separable cutoff keeps a subset of the global one's pairs.
+
 M = max psi, m = min psi, Gamma = M - m, C_0 = max_q min_j c(x_q, y_j).
 """
 from __future__ import annotations
@@ -47,3 +60,14 @@ def cutoff_tail(psi, nu, eps, tail, C0):
 def radius_of_cutoff(C):
     """c(x,y) = |x-y|^2 / 2 < C  <=>  |x - y| < sqrt(2 C)."""
     return math.sqrt(2.0 * C)
+
+
+def separable_cutoffs(x, y, nu, psi, eps, tail):
+    """(alpha [nq], beta [n]) of the separable cutoff c(x_q, y_j) < alpha_q + beta_j."""
+    from . import nearest
+    jn, cn = nearest(x, y)
+    psi = np.asarray(psi, dtype=np.float64)
+    nu = np.asarray(nu, dtype=np.float64)
+    alpha = cn - psi[jn] - eps * np.log(nu[jn])
+    beta = psi + eps * math.log(1.0 / tail)
+    return alpha, beta

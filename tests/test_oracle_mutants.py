@@ -25,7 +25,7 @@ MUTANTS = {
     "unnormalised_plan": ("nadd(&g[j], mass[q] * exp(s[j] - lnS));", "nadd(&g[j], mass[q] * exp(s[j] - smax));"),
     "no_eps_in_J": ("nadd(&jpart[t], mass[q] * eps * lnS);", "nadd(&jpart[t], mass[q] * lnS);"),
     "swapped_cost_index": ("double c = cost(d, xq, y + j * d);", "double c = cost(d, xq, y + (n - 1 - j) * d);"),
-    "non_strict_cutoff": ("in[j] = (unsigned char)(c < cutoff);", "in[j] = (unsigned char)(c <= cutoff + 1e-3);"),
+    "non_strict_cutoff": (": c < cutoff);", ": c <= cutoff + 1e-3);"),
     "mass_not_applied": ("nadd(&g[j], mass[q] * exp(s[j] - lnS));", "nadd(&g[j], exp(s[j] - lnS) / (double)nq);"),
 }
 
@@ -188,3 +188,102 @@ def test_unmutated_maps_pass_compact_pins():
 def test_map_mutant_is_caught(name):
     lpath = _build_mutant_maps(name)
     assert not _map_pins_pass(*_mutant_maps(lpath)), f"mutant {name} passed every pin"
+
+
+# ---- separable (psi-aware) truncation ----------------------------------------
+MUTANTS_SEP = {
+    "sep_minus_beta": ("alpha ? c < alpha[q] + beta[j]", "alpha ? c < alpha[q] - beta[j]"),
+    "sep_point_index_for_target": ("alpha ? c < alpha[q] + beta[j]", "alpha ? c < alpha[q] + beta[q % n]"),
+    "nearest_last_on_ties": ("            if (c < best) {\n                best = c;\n                bj = j;",
+                             "            if (c <= best) {\n                best = c;\n                bj = j;"),
+}
+
+
+def _mutant_sep(lpath):
+    lib = ctypes.CDLL(lpath)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_dual_grad_sep.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp, dp,
+                                         dp, ctypes.c_double, dp, dp, ctypes.c_int, dp, dp, i64p, i64p]
+    lib.oracle_nearest.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp, ctypes.c_int,
+                                   i64p, dp]
+    F = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    P = lambda a: a.ctypes.data_as(dp)
+
+    def dual_grad_sep(x, mass, y, nu, psi, eps, alpha, beta, threads=1):
+        x, mass, y, nu, psi, alpha, beta = (F(a) for a in (x, mass, y, nu, psi, alpha, beta))
+        g = np.empty(y.shape[0])
+        J = ctypes.c_double()
+        pr = ctypes.c_int64()
+        em = ctypes.c_int64()
+        assert lib.oracle_dual_grad_sep(x.shape[1], x.shape[0], P(x), P(mass), y.shape[0], P(y), P(nu),
+                                        P(psi), eps, P(alpha), P(beta), 1, ctypes.byref(J), P(g),
+                                        ctypes.byref(pr), ctypes.byref(em)) == 0
+        return J.value, g, pr.value, em.value
+
+    def nearest(x, y, threads=1):
+        x, y = F(x), F(y)
+        js = np.zeros(x.shape[0], dtype=np.int64)
+        cs = np.zeros(x.shape[0])
+        assert lib.oracle_nearest(x.shape[1], x.shape[0], P(x), y.shape[0], P(y), 1,
+                                  js.ctypes.data_as(i64p), P(cs)) == 0
+        return js, cs
+    return dual_grad_sep, nearest
+
+
+def _sep_pins_pass(dual_grad_sep, nearest):
+    import test_oracle_separable as T
+    orig = (oracle.dual_grad_sep, oracle.nearest)
+    oracle.dual_grad_sep, oracle.nearest = dual_grad_sep, nearest
+    try:
+        checks = [lambda: T.test_nearest_matches_kdtree(2), T.test_nearest_takes_the_lowest_index_on_ties,
+                  lambda: T.test_separable_matches_the_definition(2, 1e-3),
+                  T.test_uniform_separable_cutoff_is_the_scalar_cutoff,
+                  lambda: T.test_tail_guarantee_against_dense(1, 2, 0.01, 0.03, 1e-2, 0.5)]
+        for c in checks:
+            try:
+                c()
+            except AssertionError:
+                return False
+        return True
+    finally:
+        oracle.dual_grad_sep, oracle.nearest = orig
+
+
+def test_unmutated_separable_passes_compact_pins():
+    assert _sep_pins_pass(oracle.dual_grad_sep, oracle.nearest)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_SEP))
+def test_separable_mutant_is_caught(name):
+    src = open(obuild.SRC).read()
+    old, new = MUTANTS_SEP[name]
+    assert src.count(old) >= 1, name
+    tmpd = tempfile.mkdtemp(prefix="oracle_mut_")
+    cpath = os.path.join(tmpd, "m.c")
+    lpath = os.path.join(tmpd, "libm.so")
+    open(cpath, "w").write(src.replace(old, new, 1))
+    subprocess.run(["gcc", "-std=c99", "-O1", "-fPIC", "-shared", cpath, "-o", lpath, "-lm"], check=True)
+    assert not _sep_pins_pass(*_mutant_sep(lpath)), f"mutant {name} passed every pin"
+
+
+@pytest.mark.parametrize("wrong", ["drop_ln_nu_n", "global_min_psi"])
+def test_wrong_separable_cutoffs_break_the_tail_guarantee(wrong, monkeypatch):
+    """Plausible mistakes in the alpha/beta formula (Python side) are caught."""
+    import test_oracle_separable as T
+
+    def bad(x, y, nu, psi, eps, tail):
+        jn, cn = oracle.nearest(x, y)
+        if wrong == "drop_ln_nu_n":
+            alpha = cn - psi[jn]
+        else:
+            alpha = cn - np.max(psi) - eps * np.log(nu[jn]) - 0.05
+        return alpha, psi + eps * math.log(1.0 / tail)
+    monkeypatch.setattr(T.truncation, "separable_cutoffs", bad)
+    caught = False
+    for args in [(1, 2, 0.01, 0.03, 1e-2, 0.5), (2, 3, 0.005, 0.01, 1e-4, 0.9), (3, 2, 0.002, 0.05, 1e-6, 0.9)]:
+        try:
+            T.test_tail_guarantee_against_dense(*args)
+        except AssertionError:
+            caught = True
+    assert caught
