@@ -134,6 +134,25 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps,
                                 double *J_out, double *grad_out, int64_t *pairs_out);
 
 /*
+ * One evaluation truncated by psi-aware cutoffs per pair (Sec. 4.1, App. B):
+ *   I_q = { j : c(x_q, y_j) < alpha_q + beta_j },
+ *   alpha_q = c(x_q, y_n) - psi_n - eps ln nu_n  (n = the nearest target of x_q,
+ *             the lowest index among equal costs, found once per problem),
+ *   beta_j  = psi_j + eps ln(1/tail).
+ * The nearest target is always kept and each point's excluded terms sum to at
+ * most tail * sum_j nu_j times its kept ones, so |J - J~| <= eps tail sum(nu)
+ * sum(m) and |dJ/dpsi_j - dJ~/dpsi_j| <= tail (sum(nu) (dJ~/dpsi_j + nu_j) +
+ * nu_j sum(m)) -- the guarantees of the radius of rsot_radius_for_tail, whose
+ * cutoff bounds alpha_q + beta_j from above, with fewer pairs.
+ *   tail : in (0, 1)
+ * Other arguments, outputs and errors as rsot_eval_dual_grad (never
+ * RSOT_ERR_EMPTY_NEIGHBORHOOD: every point keeps its nearest target).
+ */
+rsot_status rsot_eval_dual_grad_tail(rsot_problem *p, const double *psi, double eps,
+                                     double tail, rsot_precision prec,
+                                     double *J_out, double *grad_out, int64_t *pairs_out);
+
+/*
  * Per-point log partition of the last successful rsot_eval_dual_grad call:
  *   L_q = ln sum_{j in I_q} nu_j exp((psi_j - c(x_q, y_j))/eps)
  * (the integrand of Eq. discretized_functional divided by eps; I_q all
@@ -220,7 +239,8 @@ typedef struct {
     double eps;          /* final regularisation, > 0                              */
     double eps_start;    /* first stage of the eps-schedule; <= eps: no schedule   */
     double eps_factor;   /* stage ratio in (0,1), e.g. 0.5; the last stage is eps  */
-    double tail;         /* > 0: truncate with rsot_radius_for_tail each evaluation;
+    double tail;         /* > 0: truncate every evaluation with the psi-aware
+                            cutoffs of this tail (rsot_eval_dual_grad_tail);
                             0: dense                                               */
     double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
     double stage_tol_l1; /* tolerance of the intermediate stages (<=0: tol_l1)      */

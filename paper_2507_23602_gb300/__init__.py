@@ -155,6 +155,8 @@ def load():
     lib.rsot_set_pair_kernel.argtypes = [vp, ctypes.c_int]
     lib.rsot_eval_dual_grad.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         dp, vp, i64p]
+    lib.rsot_eval_dual_grad_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        dp, vp, i64p]
     lib.rsot_covering_cost.argtypes = [vp, dp]
     lib.rsot_point_log_partition.argtypes = [vp, vp]
     lib.rsot_radius_for_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, dp]
@@ -298,6 +300,25 @@ class Problem:
                                            ctypes.byref(J), pg, ctypes.byref(pairs))
         if not (st == 0 or (allow_empty and st == RSOT_ERR_EMPTY_NEIGHBORHOOD)):
             raise RsotError(st, "eval_dual_grad")
+        return J.value, grad_out, pairs.value
+
+    def eval_tail(self, psi, eps, tail, precision=MIXED, grad_out=None):
+        """(J, grad, pairs): Algorithm 2 truncated by the psi-aware cutoffs
+        c(x_q, y_j) < alpha_q + beta_j of the given tail tolerance."""
+        pp, kp = _ptr(psi)
+        if grad_out is None:
+            if _is_cuda(psi):
+                import torch
+                grad_out = torch.empty(self.n, dtype=torch.float64, device=psi.device)
+            else:
+                grad_out = np.empty(self.n)
+        pg, kg = _ptr(grad_out)
+        J = ctypes.c_double()
+        pairs = ctypes.c_int64()
+        st = self._lib.rsot_eval_dual_grad_tail(self._h, pp, float(eps), float(tail), int(precision),
+                                                ctypes.byref(J), pg, ctypes.byref(pairs))
+        if st != 0:
+            raise RsotError(st, "eval_dual_grad_tail")
         return J.value, grad_out, pairs.value
 
     def point_log_partition(self, out=None):

@@ -131,6 +131,7 @@ void rsot_destroy(rsot_problem *p) {
     if (!p) return;
     trunc_free(p);
     compensated_free(p);
+    cutoff_free(p);
     dense_free(p);
     cudaFree(p->xs);
     cudaFree(p->x64);
@@ -271,11 +272,14 @@ rsot_status rsot_set_pair_kernel(rsot_problem *p, rsot_pair_kernel kind) {
     return RSOT_OK;
 }
 
-rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, double radius,
-                                rsot_precision prec, double *J_out, double *grad_out,
-                                int64_t *pairs_out) {
+// One evaluation: dense (mode 0), truncated by a radius (mode 1, cutoff C =
+// arg^2 / 2 for every pair) or by the separable psi-aware cutoffs (mode 2,
+// tail = arg, rsot_cutoff.cu).
+static rsot_status eval_impl(rsot_problem *p, const double *psi, double eps, int mode, double arg,
+                             rsot_precision prec, double *J_out, double *grad_out,
+                             int64_t *pairs_out) {
     if (!p || !psi || !J_out || !grad_out) return RSOT_ERR_ARG;
-    if (!(eps > 0.0) || !isfinite(eps) || isnan(radius)) return RSOT_ERR_ARG;
+    if (!(eps > 0.0) || !isfinite(eps) || isnan(arg)) return RSOT_ERR_ARG;
     if (prec != RSOT_FP64 && prec != RSOT_MIXED && prec != RSOT_COMPENSATED) return RSOT_ERR_ARG;
     cudaStream_t st = p->stream;
     const size_t nb = (size_t)p->n * sizeof(double);
@@ -289,15 +293,17 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, 
     double *gd = gdev ? grad_out : p->grad_dev;
     if (!e) e = cudaMemsetAsync(p->res_dev, 0, sizeof(EvalResult), st);
     // a radius beyond the diameter of the data keeps every pair: dense
-    const bool dense = !(radius > 0.0) || isinf(radius) || radius * radius > p->diam2 * (1.0 + 1e-12);
+    const bool dense = mode == 0 || (mode == 1 && (!(arg > 0.0) || isinf(arg) ||
+                                                    arg * arg > p->diam2 * (1.0 + 1e-12)));
+    if (!e && !dense) e = mode == 1 ? cutoffs_uniform(p, 0.5 * arg * arg) : cutoffs_separable(p, psid, eps, arg);
     if (!e) {
         if (prec == RSOT_COMPENSATED)
-            e = launch_compensated(p, psid, eps, dense ? INFINITY : 0.5 * radius * radius, gd);
+            e = launch_compensated(p, psid, eps, !dense, gd);
         else if (dense)
             e = (prec == RSOT_MIXED) ? launch_dense_mixed(p, psid, eps, gd)
                                      : launch_dense_fp64(p, psid, eps, gd);
         else
-            e = trunc_eval(p, psid, eps, radius, prec == RSOT_MIXED, gd);
+            e = trunc_eval(p, psid, eps, prec == RSOT_MIXED, gd);
     }
     if (!e && !gdev) e = cudaMemcpyAsync(grad_out, gd, nb, cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(EvalResult), cudaMemcpyDeviceToHost, st);
@@ -323,6 +329,19 @@ rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, 
     p->last_eps = eps;
     if (!dense && r.empty > 0) return RSOT_ERR_EMPTY_NEIGHBORHOOD;
     return RSOT_OK;
+}
+
+rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps, double radius,
+                                rsot_precision prec, double *J_out, double *grad_out,
+                                int64_t *pairs_out) {
+    return eval_impl(p, psi, eps, 1, radius, prec, J_out, grad_out, pairs_out);
+}
+
+rsot_status rsot_eval_dual_grad_tail(rsot_problem *p, const double *psi, double eps, double tail,
+                                     rsot_precision prec, double *J_out, double *grad_out,
+                                     int64_t *pairs_out) {
+    if (!(tail > 0.0) || !(tail < 1.0)) return RSOT_ERR_ARG;
+    return eval_impl(p, psi, eps, 2, tail, prec, J_out, grad_out, pairs_out);
 }
 
 rsot_status rsot_kernel_timing(rsot_problem *p, int enable) {

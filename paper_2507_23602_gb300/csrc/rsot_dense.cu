@@ -630,17 +630,19 @@ __global__ void k_prep_fp64(const double *__restrict__ psi, const double *__rest
     if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
 }
 
-// cutoff = +inf: dense; otherwise only pairs with c(x_q, y_j) < cutoff enter
-// (Algorithm 2), the number of such pairs and of empty points is counted.
+// alpha = nullptr: dense; otherwise only pairs with c(x_q, y_j) < alpha_q +
+// beta_j enter (Algorithm 2 with a cutoff per pair, rsot_cutoff.cu), the
+// number of such pairs and of empty points is counted.
 template <int D>
 __global__ void __launch_bounds__(F_THREADS)
     k_lse_fp64(const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
                const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
-               double inv_eps, double cutoff, const double *__restrict__ psi, double eps,
+               double inv_eps, const double *__restrict__ alpha, const double *__restrict__ beta,
+               const double *__restrict__ psi, double eps,
                const double *__restrict__ mass, double *__restrict__ prec64,
                double *__restrict__ blockJ, double *__restrict__ lse_buf,
                EvalResult *__restrict__ res) {
-    __shared__ double sy[F_TS][4];
+    __shared__ double sy[F_TS][5];
     __shared__ double sh[32];
     __shared__ unsigned long long s_cnt, s_empty;
     if (threadIdx.x == 0) s_cnt = s_empty = 0;
@@ -648,6 +650,7 @@ __global__ void __launch_bounds__(F_THREADS)
     double x[3] = {0.0, 0.0, 0.0};
     if (q < nq)
         for (int t = 0; t < D; ++t) x[t] = x64[q * D + t];
+    const double aq = alpha && q < nq ? alpha[q] : INFINITY;
     double M = -INFINITY, S = 0.0;
     unsigned long long npair = 0;
     __syncthreads();
@@ -657,8 +660,10 @@ __global__ void __launch_bounds__(F_THREADS)
             if (j < n) {
                 for (int t = 0; t < D; ++t) sy[i][t] = y64[j * D + t];
                 sy[i][3] = a64[j];
+                sy[i][4] = alpha ? beta[j] : 0.0;
             } else {
                 sy[i][3] = -INFINITY;
+                sy[i][4] = 0.0;
             }
         }
         __syncthreads();
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(F_THREADS)
                 c += dd * dd;
             }
             c *= 0.5;
-            if (!(c < cutoff)) continue;
+            if (!(c < aq + sy[i][4])) continue;
             ++npair;
             const double s = sy[i][3] - c * inv_eps;
             const double dlt = s - M;
@@ -720,14 +725,17 @@ template <int D>
 __global__ void __launch_bounds__(F_THREADS)
     k_grad_fp64(const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
                 const double *__restrict__ prec64, int64_t nq_pad, int64_t chunk, double inv_eps,
-                double cutoff, double *__restrict__ part2, int64_t stride) {
+                const double *__restrict__ alpha, const double *__restrict__ beta,
+                double *__restrict__ part2, int64_t stride) {
     __shared__ double sp[F_TS][4];
+    __shared__ double sa[F_TS];
     const int64_t j = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
     double y[3] = {0.0, 0.0, 0.0};
-    double a = -INFINITY;
+    double a = -INFINITY, bj = 0.0;
     if (j < n) {
         for (int t = 0; t < D; ++t) y[t] = y64[j * D + t];
         a = a64[j];
+        if (alpha) bj = beta[j];
     }
     const int64_t p_begin = (int64_t)blockIdx.y * chunk;
     const int64_t p_end = min(nq_pad, p_begin + chunk);
@@ -737,6 +745,8 @@ __global__ void __launch_bounds__(F_THREADS)
             const int64_t idx = p0 * 4 + i;
             (&sp[0][0])[i] = (idx < p_end * 4) ? prec64[idx] : (((i & 3) == 3) ? -INFINITY : 0.0);
         }
+        for (int i = threadIdx.x; i < F_TS; i += F_THREADS)
+            sa[i] = !alpha ? INFINITY : (p0 + i < p_end ? alpha[p0 + i] : -INFINITY);
         __syncthreads();
         const int cnt = (int)min((int64_t)F_TS, p_end - p0);
         for (int i = 0; i < cnt; ++i) {
@@ -747,7 +757,7 @@ __global__ void __launch_bounds__(F_THREADS)
                 c += dd * dd;
             }
             c *= 0.5;
-            if (c < cutoff) acc += exp(a - c * inv_eps + sp[i][3]);
+            if (c < sa[i] + bj) acc += exp(a - c * inv_eps + sp[i][3]);
         }
         __syncthreads();
     }
@@ -1147,7 +1157,7 @@ cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi, double eps, d
 
 template <int D>
 static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps, double *grad,
-                                 double cutoff) {
+                                 const double *alpha, const double *beta) {
     cudaStream_t st = p->stream;
     trace_begin(p, "prep_targets_fp64");
     k_prep_fp64<<<p->nblk_prep, CB_THREADS, 0, st>>>(psi, p->lnu, p->nu, p->n, p->n_pad, eps,
@@ -1156,13 +1166,13 @@ static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps,
     const unsigned nb1 = (unsigned)((p->nq_pad + F_THREADS - 1) / F_THREADS);
     trace_begin(p, "lse_fp64");
     k_lse_fp64<D><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64, p->n,
-                                             1.0 / eps, cutoff, psi, eps, p->mass, p->prec64,
+                                             1.0 / eps, alpha, beta, psi, eps, p->mass, p->prec64,
                                              p->blockJ, p->lse_buf, p->res_dev);
     trace_end(p);
     dim3 g2((unsigned)((p->n + F_THREADS - 1) / F_THREADS), (unsigned)p->s2_64);
     trace_begin(p, "grad_fp64");
     k_grad_fp64<D><<<g2, F_THREADS, 0, st>>>(p->y64, p->a64, p->n, p->prec64, p->nq_pad,
-                                             p->chunk2_64, 1.0 / eps, cutoff, p->part2_64,
+                                             p->chunk2_64, 1.0 / eps, alpha, beta, p->part2_64,
                                              p->n_pad);
     trace_end(p);
     trace_begin(p, "finalize_grad");
@@ -1177,14 +1187,14 @@ static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps,
 }
 
 cudaError_t launch_dense_fp64(rsot_problem *p, const double *psi, double eps, double *grad) {
-    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad, INFINITY)
-                     : launch_fp64_d<2>(p, psi, eps, grad, INFINITY);
+    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad, nullptr, nullptr)
+                     : launch_fp64_d<2>(p, psi, eps, grad, nullptr, nullptr);
 }
 
-cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi, double eps, double cutoff,
-                              double *grad) {
-    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad, cutoff)
-                     : launch_fp64_d<2>(p, psi, eps, grad, cutoff);
+// the cutoffs alpha_q + beta_j prepared in p->alpha / p->beta (rsot_cutoff.cu)
+cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi, double eps, double *grad) {
+    return p->d == 3 ? launch_fp64_d<3>(p, psi, eps, grad, p->alpha, p->beta)
+                     : launch_fp64_d<2>(p, psi, eps, grad, p->alpha, p->beta);
 }
 
 cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev) {

@@ -30,10 +30,11 @@
 // solver certifies ||grad J||_1 <= tol from this evaluation (rsot_solve.cpp).
 // J errs by <= eps 3e-7 sum_q m_q.
 //
-// Truncated form (Algorithm 2 with I_q = {j : c(x_q, y_j) < C}): membership is
-// decided in FP32 where |c_32 - C| exceeds a margin that bounds the FP32
-// distance error, else by the FP64 test of the FP64 path (same expression,
-// same translated coordinates), so both paths keep the same pairs.
+// Truncated form (Algorithm 2 with I_q = {j : c(x_q, y_j) < alpha_q + beta_j},
+// rsot_cutoff.cu): membership is decided in FP32 where |c_32 - C_qj| exceeds a
+// margin that bounds the FP32 distance and cutoff errors, else by the FP64 test
+// of the FP64 path (same expression, same translated coordinates), so both
+// paths keep the same pairs.
 #include <math.h>
 
 #include <algorithm>
@@ -142,11 +143,14 @@ __device__ __forceinline__ void load_ops(const DRec &r0, const DRec &r1, Op2 *R,
     st = make_float2(r0.d.z, r1.d.z);
 }
 
-// FP32 distance test c(x, y) < C with the margin; the FP64 test of the FP64
-// path decides pairs inside the margin
+// FP32 test c(x, y) < alpha + beta outside a margin that bounds the FP32
+// errors (|c_32 - c| <= 2^-19 |coords|^2 + 2^-23 c from the rounded translated
+// coordinates, their differences and squares; 2^-23 (|alpha| + |beta|) from the
+// rounded cutoff; taken 4x); the FP64 test of the FP64 path decides inside it
 template <int D>
-__device__ __forceinline__ bool keep_pair(const float *xf, const float *yf, float C, float margin,
-                                          const double *x64, const double *y64, double C64) {
+__device__ __forceinline__ bool keep_pair(const float *xf, const float *yf, float af, float bf,
+                                          float span2, const double *x64, const double *y64,
+                                          double a64, const double *b64) {
     float c2 = 0.f;
 #pragma unroll
     for (int t = 0; t < D; ++t) {
@@ -154,6 +158,8 @@ __device__ __forceinline__ bool keep_pair(const float *xf, const float *yf, floa
         c2 = fmaf(dd, dd, c2);
     }
     const float c32 = 0.5f * c2;
+    const float C = af + bf;
+    const float margin = fmaf(0x1p-17f, span2 + fabsf(C), 0x1p-21f * (fabsf(af) + fabsf(bf)));
     if (fabsf(c32 - C) > margin) return c32 < C;
     double c = 0.0;
 #pragma unroll
@@ -162,7 +168,7 @@ __device__ __forceinline__ bool keep_pair(const float *xf, const float *yf, floa
         c += dd * dd;
     }
     c *= 0.5;
-    return c < C64;
+    return c < a64 + *b64;
 }
 
 // per-target records (rounded from FP64) and the block partials of sum psi nu
@@ -220,12 +226,12 @@ __global__ void __launch_bounds__(D_THREADS)
     k_lse_df(DRec *__restrict__ prec, const float *__restrict__ xs, const double *__restrict__ x64,
              int64_t nq, int64_t nq_pad, const DRec *__restrict__ trec,
              const float *__restrict__ ys, const double *__restrict__ y64, int64_t n,
-             int64_t n_alloc, float C, float margin, double C64,
-             const double *__restrict__ lmass2, const double *__restrict__ mass,
+             int64_t n_alloc, const double *__restrict__ alpha, const double *__restrict__ beta,
+             float span2, const double *__restrict__ lmass2, const double *__restrict__ mass,
              const double *__restrict__ psi, double eps, double *__restrict__ blockJ,
              double *__restrict__ lse_buf, EvalResult *__restrict__ res) {
     __shared__ DRec sm[D_TS];
-    __shared__ float sy[TRUNC ? 3 : 1][D_TS];
+    __shared__ float sy[TRUNC ? 4 : 1][D_TS];
     __shared__ double sh[32];
     __shared__ unsigned long long s_cnt, s_empty;
     if (threadIdx.x == 0) s_cnt = s_empty = 0;
@@ -237,9 +243,12 @@ __global__ void __launch_bounds__(D_THREADS)
     f2 unused_h, unused_t;
     load_ops(p0, p1, X, unused_h, unused_t);
     float xf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    double a64[2] = {0.0, 0.0};
     if (TRUNC)
-        for (int l = 0; l < 2; ++l)
+        for (int l = 0; l < 2; ++l) {
             for (int t = 0; t < D; ++t) xf[l][t] = xs[t * nq_pad + q[l]];
+            a64[l] = alpha[q[l]];
+        }
     const int64_t n_rec = (n + D_TS - 1) / D_TS * D_TS;
     float M[2] = {-INFINITY, -INFINITY};
     double S[2] = {0.0, 0.0};
@@ -248,8 +257,10 @@ __global__ void __launch_bounds__(D_THREADS)
         __syncthreads();
         for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
             sm[i] = trec[t0 + i];
-            if (TRUNC)
+            if (TRUNC) {
                 for (int t = 0; t < 3; ++t) sy[t][i] = ys[t * n_alloc + t0 + i];
+                sy[3][i] = (float)beta[t0 + i];
+            }
         }
         __syncthreads();
         f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
@@ -265,7 +276,8 @@ __global__ void __launch_bounds__(D_THREADS)
                     const int64_t j = t0 + u0 + i;
                     for (int l = 0; l < 2; ++l) {
                         const bool k = j < n && q[l] < nq &&
-                                       keep_pair<D>(xf[l], yf, C, margin, x64 + q[l] * D, y64 + j * D, C64);
+                                       keep_pair<D>(xf[l], yf, (float)a64[l], sy[3][u0 + i], span2,
+                                                    x64 + q[l] * D, y64 + j * D, a64[l], beta + j);
                         if (k) {
                             ++npair;
                         } else if (l == 0) {
@@ -357,10 +369,11 @@ __global__ void __launch_bounds__(D_THREADS)
     k_grad_df(const DRec *__restrict__ trec, const float *__restrict__ ys,
               const double *__restrict__ y64, int64_t n, int64_t n_alloc,
               const DRec *__restrict__ prec, const float *__restrict__ xs,
-              const double *__restrict__ x64, int64_t nq, int64_t nq_pad, int64_t chunk, float C,
-              float margin, double C64, double *__restrict__ part2) {
+              const double *__restrict__ x64, int64_t nq, int64_t nq_pad, int64_t chunk,
+              const double *__restrict__ alpha, const double *__restrict__ beta, float span2,
+              double *__restrict__ part2) {
     __shared__ DRec sm[D_TS];
-    __shared__ float sx[TRUNC ? 3 : 1][D_TS];
+    __shared__ float sx[TRUNC ? 4 : 1][D_TS];
     int64_t j[2];
     j[0] = (int64_t)blockIdx.x * D_ROWS + threadIdx.x;   // < n_alloc
     j[1] = j[0] + D_THREADS;
@@ -368,9 +381,12 @@ __global__ void __launch_bounds__(D_THREADS)
     f2 Ch, Ct;
     load_ops(trec[j[0]], trec[j[1]], W, Ch, Ct);
     float yf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float bf[2] = {0.f, 0.f};
     if (TRUNC)
-        for (int l = 0; l < 2; ++l)
+        for (int l = 0; l < 2; ++l) {
             for (int t = 0; t < D; ++t) yf[l][t] = ys[t * n_alloc + j[l]];
+            bf[l] = (float)beta[j[l]];
+        }
     const int64_t p_begin = (int64_t)blockIdx.y * chunk;
     const int64_t p_end = min(nq_pad, p_begin + chunk);
     double acc0 = 0.0, acc1 = 0.0;
@@ -378,8 +394,10 @@ __global__ void __launch_bounds__(D_THREADS)
         __syncthreads();
         for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
             sm[i] = prec[p0 + i];
-            if (TRUNC)
+            if (TRUNC) {
                 for (int t = 0; t < 3; ++t) sx[t][i] = t < D ? xs[t * nq_pad + p0 + i] : 0.f;
+                sx[3][i] = (float)alpha[p0 + i];
+            }
         }
         __syncthreads();
         f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
@@ -395,10 +413,12 @@ __global__ void __launch_bounds__(D_THREADS)
                 const float xf[3] = {sx[0][i], sx[1][i], sx[2][i]};
                 const int64_t qq = p0 + i;
                 if (!(qq < nq && j[0] < n &&
-                      keep_pair<D>(xf, yf[0], C, margin, x64 + qq * D, y64 + j[0] * D, C64)))
+                      keep_pair<D>(xf, yf[0], sx[3][i], bf[0], span2, x64 + qq * D, y64 + j[0] * D,
+                                   alpha[qq], beta + j[0])))
                     e.x = 0.f;
                 if (!(qq < nq && j[1] < n &&
-                      keep_pair<D>(xf, yf[1], C, margin, x64 + qq * D, y64 + j[1] * D, C64)))
+                      keep_pair<D>(xf, yf[1], sx[3][i], bf[1], span2, x64 + qq * D, y64 + j[1] * D,
+                                   alpha[qq], beta + j[1])))
                     e.y = 0.f;
             }
             kahan2(s, comp, e);
@@ -418,11 +438,10 @@ int occupancy_df(const void *f) {
 }
 
 template <int D>
-cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double cutoff,
+cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, bool trunc,
                           double *grad) {
     cudaStream_t st = p->stream;
     cudaError_t e;
-    const bool trunc = cutoff < INFINITY;
     // point chunks of whole tiles for pass 2: enough blocks for four waves
     const int64_t tblocks = p->n_pad / D_ROWS, tiles = p->nq_pad / D_TS;
     const void *f2p = trunc ? (const void *)k_grad_df<D, true> : (const void *)k_grad_df<D, false>;
@@ -450,10 +469,9 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
     }
     DRec *prec = reinterpret_cast<DRec *>(p->df_prec);
     DRec *trec = reinterpret_cast<DRec *>(p->df_trec);
-    // |c_32 - c| <= 2^-19 max|coord|^2 + 2^-23 c (FP32 rounding of the translated
-    // coordinates, their differences and squares); the margin is 4x that
-    const float C = trunc ? (float)cutoff : 0.f;
-    const float margin = trunc ? (float)std::ldexp(p->diam2 + cutoff, -17) : 0.f;
+    // squared extent of the translated coordinates: bounds their FP32 rounding
+    const float span2 = (float)p->diam2;
+    const double *alpha = trunc ? p->alpha : nullptr, *beta = trunc ? p->beta : nullptr;
     trace_begin(p, "prep_df");
     k_prep_df<<<p->nblk_prep, 256, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad, p->d, eps,
                                            trec, p->psinu, p->flags);
@@ -462,25 +480,25 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
     trace_begin(p, "lse_df");
     if (trunc)
         k_lse_df<D, true><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec,
-                                                     p->df_ys, p->y64, p->n, p->n_pad, C, margin,
-                                                     cutoff, p->lmass2, p->mass, psi, eps,
+                                                     p->df_ys, p->y64, p->n, p->n_pad, alpha, beta,
+                                                     span2, p->lmass2, p->mass, psi, eps,
                                                      p->blockJ, p->lse_buf, p->res_dev);
     else
         k_lse_df<D, false><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec,
-                                                      p->df_ys, p->y64, p->n, p->n_pad, C, margin,
-                                                      cutoff, p->lmass2, p->mass, psi, eps,
+                                                      p->df_ys, p->y64, p->n, p->n_pad, alpha, beta,
+                                                      span2, p->lmass2, p->mass, psi, eps,
                                                       p->blockJ, p->lse_buf, p->res_dev);
     trace_end(p);
     dim3 g2((unsigned)tblocks, (unsigned)s2);
     trace_begin(p, "grad_df");
     if (trunc)
         k_grad_df<D, true><<<g2, D_THREADS, 0, st>>>(trec, p->df_ys, p->y64, p->n, p->n_pad, prec,
-                                                     p->xs, p->x64, p->nq, p->nq_pad, chunk, C,
-                                                     margin, cutoff, p->df_part2);
+                                                     p->xs, p->x64, p->nq, p->nq_pad, chunk, alpha,
+                                                     beta, span2, p->df_part2);
     else
         k_grad_df<D, false><<<g2, D_THREADS, 0, st>>>(trec, p->df_ys, p->y64, p->n, p->n_pad, prec,
-                                                      p->xs, p->x64, p->nq, p->nq_pad, chunk, C,
-                                                      margin, cutoff, p->df_part2);
+                                                      p->xs, p->x64, p->nq, p->nq_pad, chunk, alpha,
+                                                      beta, span2, p->df_part2);
     trace_end(p);
     if ((e = cudaGetLastError())) return e;
     return launch_finalize_log2(p, psi, eps, p->df_part2, (int)s2, (int)nb1, grad);
@@ -488,12 +506,12 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, double
 
 }  // namespace
 
-// cutoff = +inf: dense (Eq. discretized_functional / discretized_gradient);
-// else the truncated sums over c(x_q, y_j) < cutoff.
-cudaError_t launch_compensated(rsot_problem *p, const double *psi, double eps, double cutoff,
+// dense (Eq. discretized_functional / discretized_gradient), or the truncated
+// sums over c(x_q, y_j) < alpha_q + beta_j (p->alpha, p->beta)
+cudaError_t launch_compensated(rsot_problem *p, const double *psi, double eps, bool trunc,
                                double *grad) {
-    return p->d == 3 ? compensated_d<3>(p, psi, eps, cutoff, grad)
-                     : compensated_d<2>(p, psi, eps, cutoff, grad);
+    return p->d == 3 ? compensated_d<3>(p, psi, eps, trunc, grad)
+                     : compensated_d<2>(p, psi, eps, trunc, grad);
 }
 
 void compensated_free(rsot_problem *p) {

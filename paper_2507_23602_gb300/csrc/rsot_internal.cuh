@@ -118,6 +118,12 @@ struct rsot_problem {
     double *df_part2 = nullptr;     // [df_s2][n_pad] pass-2 partials
     int df_s2 = 0;
 
+    // truncation cutoffs per pair, c(x_q, y_j) < alpha_q + beta_j (rsot_cutoff.cu)
+    int *nn = nullptr;              // [nq] nearest target of each point (once per problem)
+    double *nn_c = nullptr;         // [nq] its cost
+    double *alpha = nullptr;        // [nq_pad] per evaluation (-inf for padding)
+    double *beta = nullptr;         // [n_pad]  per evaluation (-inf for padding)
+
     // staging for host psi / grad
     double *psi_dev = nullptr;      // [n]
     double *grad_dev = nullptr;     // [n]
@@ -178,16 +184,20 @@ cudaError_t launch_dense_mixed(rsot_problem *p, const double *psi_dev, double ep
                                double *grad_dev);
 cudaError_t launch_dense_fp64(rsot_problem *p, const double *psi_dev, double eps,
                               double *grad_dev);
-cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi_dev, double eps, double cutoff,
-                              double *grad_dev);
+cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi_dev, double eps, double *grad_dev);
 cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev);
 cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out3_dev);
 cudaError_t launch_point_L(rsot_problem *p, double *L_dev);
 cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double eps, int64_t nf,
                                   const double *yf_dev, double *out_dev);
 
-// ---- compensated path (rsot_df.cu): cutoff = +inf dense, else truncated
-cudaError_t launch_compensated(rsot_problem *p, const double *psi_dev, double eps, double cutoff,
+// ---- truncation cutoffs (rsot_cutoff.cu): fill p->alpha / p->beta
+cudaError_t cutoffs_uniform(rsot_problem *p, double C);
+cudaError_t cutoffs_separable(rsot_problem *p, const double *psi_dev, double eps, double tail);
+void cutoff_free(rsot_problem *p);
+
+// ---- compensated path (rsot_df.cu): dense, or truncated by p->alpha / p->beta
+cudaError_t launch_compensated(rsot_problem *p, const double *psi_dev, double eps, bool trunc,
                                double *grad_dev);
 void compensated_free(rsot_problem *p);
 // Bound of ||g - grad J||_1 / sum_q m_q for a compensated gradient g (rsot_df.cu)
@@ -200,8 +210,9 @@ cudaError_t launch_centroids(rsot_problem *p, double *T_dev, double *mass_dev,
                              const double *origin_dev);
 
 // ---- truncated path (rsot_trunc.cu) ----------------------------------------
-cudaError_t trunc_eval(rsot_problem *p, const double *psi_dev, double eps, double radius,
-                       int mixed, double *grad_dev);
+// truncated by the cutoffs in p->alpha / p->beta
+cudaError_t trunc_eval(rsot_problem *p, const double *psi_dev, double eps, int mixed,
+                       double *grad_dev);
 void trunc_free(rsot_problem *p);
 cudaError_t trunc_point_L(rsot_problem *p, double *L_dev);
 

@@ -63,13 +63,11 @@ struct Evaluator {
     rsot_status last = RSOT_OK;
 
     rsot_status operator()(const std::vector<double> &psi, double &J, std::vector<double> &g) {
-        double radius = 0.0;
-        if (tail > 0.0) {
-            rsot_status s = rsot_radius_for_tail(p, psi.data(), eps, tail, &radius);
-            if (s) return last = s;
-        }
+        // tail > 0: the psi-aware cutoffs of that tail tolerance (Sec. 4.1, App. B)
         int64_t pr = 0;
-        rsot_status s = rsot_eval_dual_grad(p, psi.data(), eps, radius, prec, &J, g.data(), &pr);
+        rsot_status s = tail > 0.0
+                            ? rsot_eval_dual_grad_tail(p, psi.data(), eps, tail, prec, &J, g.data(), &pr)
+                            : rsot_eval_dual_grad(p, psi.data(), eps, 0.0, prec, &J, g.data(), &pr);
         ++evals;
         pairs += pr;
         return last = s;

@@ -7,9 +7,9 @@
 // problem).  Consecutive runs of the sorted order form tiles -- 1024 points or
 // 256 targets -- that are spatially compact; each tile carries its bounding
 // box.  Per evaluation, a (point tile, target tile) pair is a candidate when
-// the boxes are closer than the radius; every candidate pair of points and
-// targets is then tested exactly (c < C, strict) inside the kernels, so the
-// sums run over I_q exactly as in Algorithm 2.
+// the boxes are closer than the largest cutoff radius of their members; every
+// candidate pair of points and targets is then tested (c < C_qj, strict)
+// inside the kernels, so the sums run over I_q as in Algorithm 2.
 //
 // Work is a queue of items (point tile, chunk of candidate target tiles) for
 // pass 1 and (target tile, chunk of candidate point tiles) for pass 2,
@@ -17,12 +17,16 @@
 // stored per item and merged in a fixed order, so results do not depend on
 // which CTA ran which item.
 //
-// Mixed precision uses the log2-domain quantities of the dense path
-// (rsot_dense.cu): r_qj = c_j + x'_q.w_j, and the truncation test
-// c < C with c = |x'_q - y'_j|^2 / 2 and C = R^2 / 2:
-//   k |x'_q - y'_j|^2 < k R^2   <=>   r_qj - b_j > k |x'_q|^2 - k R^2  (=: A_q).
-// The FP64 truncated evaluation reuses the dense FP64 kernels with the
-// predicate (rsot_dense.cu).
+// The cutoff is per pair, c(x_q, y_j) < alpha_q + beta_j (rsot_cutoff.cu:
+// alpha_q = C, beta_j = 0 for a radius; the separable psi-aware cutoff
+// otherwise).  Mixed precision uses the log2-domain quantities of the dense
+// path (rsot_dense.cu): r_qj = c_j + x'_q.w_j, and with c = |x'_q - y'_j|^2 / 2
+//   k |x'_q - y'_j|^2 < 2k (alpha_q + beta_j)
+//     <=>   r_qj - (b_j - 2k beta_j) > k |x'_q|^2 - 2k alpha_q  (=: A_q),
+// b_j - 2k beta_j being the per-target test constant.  Blocks and tiles carry
+// the ranges of alpha and beta over their members for the culling.  The FP64
+// truncated evaluation reuses the dense FP64 kernels with the predicate
+// (rsot_dense.cu).
 #include <math.h>
 #include <stdio.h>
 
@@ -65,6 +69,10 @@ struct Grid {
     float4 *pball16 = nullptr, *pball8 = nullptr, *tball16 = nullptr, *tball8 = nullptr;
     Rec16 *prec_s = nullptr, *trec_s = nullptr;
     float *b_s = nullptr, *u_s = nullptr;
+    // per evaluation: (min, max) of alpha over point blocks of 16 / 8 and of
+    // beta over target blocks of 8 / 16, maxima over point / target tiles
+    float2 *pal16 = nullptr, *pal8 = nullptr, *tbe8 = nullptr, *tbe16 = nullptr;
+    float *ptmax = nullptr, *ttmax = nullptr;
     int slots1_tc = 0, slots2_tc = 0;
 };
 
@@ -250,9 +258,10 @@ __global__ void k_point_recs_s(const float *__restrict__ xs, int64_t nqt, int d,
 }
 
 // ------------------------------------------------------------- per evaluation
-// A_q = k |x'_q|^2 - k R^2 (FP32, computed once so that both passes agree)
+// A_q = k |x'_q|^2 - 2k alpha_q (FP32, computed once so that both passes agree)
 __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt, int d, float k,
-                          float kR2, float *__restrict__ Aq) {
+                          const double *__restrict__ alpha, const int *__restrict__ perm_q,
+                          double k2, float *__restrict__ Aq) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nqt) return;
     if (s >= nq) {
@@ -264,7 +273,40 @@ __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt,
         const float v = xs[t * nqt + s];
         r2 = fmaf(v, v, r2);
     }
-    Aq[s] = fmaf(k, r2, -kR2);
+    Aq[s] = fmaf(k, r2, -(float)(k2 * alpha[perm_q[s]]));
+}
+
+// (min, max) of v[perm[s]] over runs of 8 sorted members (real members only:
+// (+inf, -inf) for a block without any)
+__global__ void k_ranges8(const double *__restrict__ v, const int *__restrict__ perm, int64_t cnt,
+                          int64_t nblocks, float2 *__restrict__ out) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t s = b * 8; s < min((b + 1) * 8, cnt); ++s) {
+        const double a = v[perm[s]];
+        lo = fmin(lo, a);
+        hi = fmax(hi, a);
+    }
+    // rounded outwards to FP32
+    float flo = (float)lo, fhi = (float)hi;
+    if ((double)flo > lo) flo = nextafterf(flo, -INFINITY);
+    if ((double)fhi < hi) fhi = nextafterf(fhi, INFINITY);
+    out[b] = make_float2(flo, fhi);
+}
+
+// merge runs of f consecutive ranges; optionally only the maxima
+__global__ void k_ranges_merge(const float2 *__restrict__ in, int64_t nin, int f,
+                               float2 *__restrict__ out, float *__restrict__ out_max, int64_t nout) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nout) return;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = b * f; i < min((b + 1) * f, nin); ++i) {
+        lo = fminf(lo, in[i].x);
+        hi = fmaxf(hi, in[i].y);
+    }
+    if (out) out[b] = make_float2(lo, hi);
+    if (out_max) out_max[b] = hi;
 }
 
 __device__ __forceinline__ float box_dist2(const float *a, const float *b) {
@@ -277,8 +319,11 @@ __device__ __forceinline__ float box_dist2(const float *a, const float *b) {
 }
 
 // candidate (point tile, target tile) pairs: bit matrices in both orientations
+// a pair is a candidate when its boxes are closer than the largest cutoff radius
+// of its members, sqrt(2 (max alpha + max beta)), widened by 1e-5 relative
 __global__ void k_tile_pairs(const float *__restrict__ pbox, const float *__restrict__ tbox,
-                             int ptiles, int ttiles, int tw, int pw, float r2,
+                             int ptiles, int ttiles, int tw, int pw, const float *__restrict__ ptmax,
+                             const float *__restrict__ ttmax,
                              uint32_t *__restrict__ bits_pt, uint32_t *__restrict__ bits_tp,
                              int *__restrict__ cnt1, int *__restrict__ cnt2) {
     __shared__ int s_cnt;
@@ -288,6 +333,7 @@ __global__ void k_tile_pairs(const float *__restrict__ pbox, const float *__rest
     float pb[6];
     for (int k = 0; k < 6; ++k) pb[k] = pbox[p * 6 + k];
     const bool pempty = !(pb[0] <= pb[3]);
+    const float pa = ptmax[p];
     int mine = 0;
     for (int t0 = 0; t0 < tw * 32; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
@@ -295,7 +341,8 @@ __global__ void k_tile_pairs(const float *__restrict__ pbox, const float *__rest
         if (t < ttiles && !pempty) {
             float tb[6];
             for (int k = 0; k < 6; ++k) tb[k] = tbox[t * 6 + k];
-            cand = (tb[0] <= tb[3]) && box_dist2(pb, tb) < r2;
+            const float rr = sqrtf(fmaxf(0.f, 2.f * (pa + ttmax[t]))) * (1.0f + 1e-5f) + 1e-6f;
+            cand = (tb[0] <= tb[3]) && box_dist2(pb, tb) < rr * rr;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
         if ((threadIdx.x & 31) == 0 && t < tw * 32) bits_pt[(size_t)p * tw + t / 32] = bal;
@@ -340,7 +387,7 @@ __global__ void k_prep_trunc(const double *__restrict__ psi, const int *__restri
                              int64_t n, int64_t nt, int d, double eps, Rec12 *__restrict__ tdup,
                              double *__restrict__ psinu_part, const double *__restrict__ nu_s,
                              int *__restrict__ flags, Rec16 *__restrict__ trec, float *__restrict__ bs,
-                             double inv_P, int *__restrict__ gate) {
+                             double inv_P, int *__restrict__ gate, const double *__restrict__ beta) {
     __shared__ double sh[32];
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double psic = psi[0];
@@ -360,7 +407,8 @@ __global__ void k_prep_trunc(const double *__restrict__ psi, const int *__restri
                 yy += yt * yt;
             }
             c = (float)(b - k * yy);
-            nb = (float)(-b);
+            // test constant b_j - 2k beta_j (cutoff c < alpha_q + beta_j)
+            nb = (float)(2.0 * k * beta[perm_t[s]] - b);
             contrib = ps * nu_s[s];
         }
         Rec12 r;
@@ -604,11 +652,16 @@ constexpr int TP_PST = 256;        // points per pass-2 stage
 static_assert(TP_THREADS1 / 32 * TC_MB * 16 == PT, "pass-1 CTA covers a point tile");
 static_assert(TP_THREADS2 / 32 * TC_MB * 16 == TT, "pass-2 CTA covers a target tile");
 
-__device__ __forceinline__ int tp_class(float4 a, float4 b, float Rin, float Rout) {
+// a, b: the balls; ra, rb: (min, max) of alpha / beta over their members.
+// Every pair of the two blocks has a cutoff radius sqrt(2 (alpha_q + beta_j))
+// between sqrt(2 (ra.x + rb.x)) and sqrt(2 (ra.y + rb.y)).
+__device__ __forceinline__ int tp_class(float4 a, float4 b, float2 ra, float2 rb) {
     if (a.w < 0.f || b.w < 0.f) return 0;
     const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
     const float dist = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float Rout = sqrtf(fmaxf(0.f, 2.f * (ra.y + rb.y))) * (1.0f + 1e-4f) + 1e-6f;
     if (dist - a.w - b.w >= Rout) return 0;
+    const float Rin = sqrtf(fmaxf(0.f, 2.f * (ra.x + rb.x))) * (1.0f - 1e-4f) - 1e-6f;
     if (dist + a.w + b.w < Rin) return 1;
     return 2;
 }
@@ -650,9 +703,10 @@ __device__ __forceinline__ void tp_lse_epi(const float (&d)[4], int cls, float2 
 
 __global__ void __launch_bounds__(TP_THREADS1, 1)
     k_lse_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
-                   const float4 *__restrict__ pball16, const Rec16 *__restrict__ trec,
-                   const float *__restrict__ bs, const float4 *__restrict__ tball8, float Rin,
-                   float Rout, const uint32_t *__restrict__ bits_pt, int tw,
+                   const float4 *__restrict__ pball16, const float2 *__restrict__ pal16,
+                   const Rec16 *__restrict__ trec, const float *__restrict__ bs,
+                   const float4 *__restrict__ tball8, const float2 *__restrict__ tbe8,
+                   const uint32_t *__restrict__ bits_pt, int tw,
                    const int *__restrict__ off1, int ptiles, int ch1, int *__restrict__ counter,
                    float2 *__restrict__ part1, unsigned long long *__restrict__ pairs,
                    int *__restrict__ flags, const int *__restrict__ gate) {
@@ -660,11 +714,13 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
     __shared__ __align__(128) Rec16 s_rec[2][TT];
     __shared__ __align__(16) float s_b[2][TT];
     __shared__ __align__(16) float4 s_ball[2][TT / 8];
+    __shared__ __align__(16) float2 s_be[2][TT / 8];
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ int s_item, s_p, s_cnt, s_abort[2];
     __shared__ int s_list[MAX_CH];
     __shared__ unsigned long long s_pairs;
-    constexpr unsigned kStage = TT * sizeof(Rec16) + TT * sizeof(float) + TT / 8 * sizeof(float4);
+    constexpr unsigned kStage =
+        TT * sizeof(Rec16) + TT * sizeof(float) + TT / 8 * (sizeof(float4) + sizeof(float2));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
     if (tid == 0) {
         for (int st = 0; st < 2; ++st) {
@@ -703,6 +759,7 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                 bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
                 bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
                 bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
+                bulk_g2s(s_be[slot], tbe8 + tt * (TT / 8), TT / 8 * sizeof(float2), &full[slot]);
             }
         }
         const int64_t q0 = (int64_t)pt * PT + warp * (TC_MB * 16);
@@ -744,9 +801,10 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                 unsigned mycls = 0;
                 {
                     const float4 tb = s_ball[slot][lane];
+                    const float2 tr2 = s_be[slot][lane];
 #pragma unroll
-                    for (int m = 0; m < TC_MB; ++m)
-                        mycls |= (unsigned)tp_class(pb[m], tb, Rin, Rout) << (2 * m);
+                    for (int m = 0; m < TC_MB; ++m)   // alpha ranges from L1: fewer registers
+                        mycls |= (unsigned)tp_class(pb[m], tb, pal16[q0 / 16 + m], tr2) << (2 * m);
                 }
                 const unsigned live = __ballot_sync(0xffffffffu, mycls != 0);
 #pragma unroll 1
@@ -874,6 +932,7 @@ __global__ void __launch_bounds__(TP_THREADS1, 1)
                         bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
                         bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
                         bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
+                        bulk_g2s(s_be[slot], tbe8 + tt * (TT / 8), TT / 8 * sizeof(float2), &full[slot]);
                     }
                 }
                 if (!__shfl_sync(0xffffffffu, ok, 0)) {
@@ -934,8 +993,9 @@ if (!wabort) {
 __global__ void __launch_bounds__(TP_THREADS2)
     k_grad_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
                     const float *__restrict__ us, const float4 *__restrict__ pball8,
-                    const Rec16 *__restrict__ trec, const float *__restrict__ bs,
-                    const float4 *__restrict__ tball16, float Rin, float Rout,
+                    const float2 *__restrict__ pal8, const Rec16 *__restrict__ trec,
+                    const float *__restrict__ bs, const float4 *__restrict__ tball16,
+                    const float2 *__restrict__ tbe16,
                     const uint32_t *__restrict__ bits_tp, int pw, const int *__restrict__ off2,
                     int ttiles, int ch2, int *__restrict__ counter, double *__restrict__ part2,
                     int *__restrict__ flags, const int *__restrict__ gate) {
@@ -944,10 +1004,12 @@ __global__ void __launch_bounds__(TP_THREADS2)
     __shared__ __align__(16) float s_u[2][TP_PST];
     __shared__ __align__(16) float s_A[2][TP_PST];
     __shared__ __align__(16) float4 s_ball[2][TP_PST / 8];
+    __shared__ __align__(16) float2 s_al[2][TP_PST / 8];
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ int s_item, s_t, s_cnt, s_abort[2];
     __shared__ int s_list[MAX_CH];
-    constexpr unsigned kStage = TP_PST * (sizeof(Rec16) + 2 * sizeof(float)) + TP_PST / 8 * sizeof(float4);
+    constexpr unsigned kStage = TP_PST * (sizeof(Rec16) + 2 * sizeof(float)) +
+                                TP_PST / 8 * (sizeof(float4) + sizeof(float2));
     constexpr int SPT = PT / TP_PST;   // stages per point tile
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
     if (tid == 0) {
@@ -971,6 +1033,7 @@ __global__ void __launch_bounds__(TP_THREADS2)
         bulk_g2s(s_u[slot_], us + q_, TP_PST * sizeof(float), &full[slot_]);                  \
         bulk_g2s(s_A[slot_], Aq + q_, TP_PST * sizeof(float), &full[slot_]);                  \
         bulk_g2s(s_ball[slot_], pball8 + q_ / 8, TP_PST / 8 * sizeof(float4), &full[slot_]); \
+        bulk_g2s(s_al[slot_], pal8 + q_ / 8, TP_PST / 8 * sizeof(float2), &full[slot_]);     \
     } while (0)
     for (;;) {
         if (tid == 0) {
@@ -994,6 +1057,7 @@ __global__ void __launch_bounds__(TP_THREADS2)
         float2 bgg[TC_MB];   // (-b_g, -b_g) and (-b_g+8, -b_g+8) as two pairs
         float2 bg8[TC_MB];
         float4 tb[TC_MB];
+        float2 tbr[TC_MB];
         double2 acc64[TC_MB];
 #pragma unroll
         for (int m = 0; m < TC_MB; ++m) {
@@ -1003,6 +1067,7 @@ __global__ void __launch_bounds__(TP_THREADS2)
             bgg[m] = make_float2(-b0, -b0);
             bg8[m] = make_float2(-b8, -b8);
             tb[m] = tball16[jb / 16];
+            tbr[m] = tbe16[jb / 16];
             acc64[m] = make_double2(0.0, 0.0);
         }
         bool wabort = false;
@@ -1026,9 +1091,10 @@ __global__ void __launch_bounds__(TP_THREADS2)
                 unsigned mycls = 0;
                 {
                     const float4 pbl = s_ball[slot][lane];
+                    const float2 pal = s_al[slot][lane];
 #pragma unroll
                     for (int m = 0; m < TC_MB; ++m)
-                        mycls |= (unsigned)tp_class(tb[m], pbl, Rin, Rout) << (2 * m);
+                        mycls |= (unsigned)tp_class(tb[m], pbl, tbr[m], pal) << (2 * m);
                 }
                 // two live n-blocks per step (mma of both before either epilogue)
                 for (unsigned live = __ballot_sync(0xffffffffu, mycls != 0); live;) {
@@ -1449,6 +1515,12 @@ static cudaError_t grid_build(rsot_problem *p) {
     ALLOC(g->trec_s, g->nt);
     ALLOC(g->b_s, g->nt);
     ALLOC(g->u_s, g->nqt);
+    ALLOC(g->pal8, g->nqt / 8);
+    ALLOC(g->pal16, g->nqt / 16);
+    ALLOC(g->ptmax, g->ptiles);
+    ALLOC(g->tbe8, g->nt / 8);
+    ALLOC(g->tbe16, g->nt / 16);
+    ALLOC(g->ttmax, g->ttiles);
 #undef ALLOC
     k_gather_points<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(
         kq, p->nq, g->nqt, d, p->x64, p->mass, p->lmass2, g->perm_q, g->xs, g->x64, g->mass, g->lm2);
@@ -1475,20 +1547,28 @@ static cudaError_t grid_build(rsot_problem *p) {
 }
 
 template <int D>
-static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, double radius,
-                               double *grad) {
+static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, double *grad) {
     Grid *g = p->grid;
     cudaStream_t st = p->stream;
-    // c(x,y) = |x-y|^2/2 < C = radius^2/2  <=>  k |x'-y'|^2 < k radius^2
+    // c(x,y) = |x-y|^2/2 < alpha_q + beta_j  <=>  k |x'-y'|^2 < 2k (alpha_q + beta_j)
     const double k = kLog2e / (2.0 * eps);
-    const float r_test = (float)(radius * (1.0 + 1e-5) + 1e-6);
+    auto nb_of = [](int64_t m) { return (unsigned)((m + 255) / 256); };
     trace_begin(p, "trunc_setup");
-    k_trunc_A<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(g->xs, p->nq, g->nqt, D, (float)k,
-                                                                (float)(k * radius * radius), g->Aq);
+    k_trunc_A<<<nb_of(g->nqt), 256, 0, st>>>(g->xs, p->nq, g->nqt, D, (float)k, p->alpha, g->perm_q,
+                                             2.0 * k, g->Aq);
+    // cutoff ranges of blocks and tiles (sorted order)
+    k_ranges8<<<nb_of(g->nqt / 8), 256, 0, st>>>(p->alpha, g->perm_q, p->nq, g->nqt / 8, g->pal8);
+    k_ranges_merge<<<nb_of(g->nqt / 16), 256, 0, st>>>(g->pal8, g->nqt / 8, 2, g->pal16, nullptr, g->nqt / 16);
+    k_ranges_merge<<<nb_of(g->ptiles), 256, 0, st>>>(g->pal16, g->nqt / 16, PT / 16, nullptr, g->ptmax,
+                                                    g->ptiles);
+    k_ranges8<<<nb_of(g->nt / 8), 256, 0, st>>>(p->beta, g->perm_t, p->n, g->nt / 8, g->tbe8);
+    k_ranges_merge<<<nb_of(g->nt / 16), 256, 0, st>>>(g->tbe8, g->nt / 8, 2, g->tbe16, nullptr, g->nt / 16);
+    k_ranges_merge<<<nb_of(g->ttiles), 256, 0, st>>>(g->tbe16, g->nt / 16, TT / 16, nullptr, g->ttmax,
+                                                    g->ttiles);
     cudaMemsetAsync(g->bits_tp, 0, (size_t)g->ttiles * g->pw * 4, st);
     cudaMemsetAsync(g->cnt2, 0, (size_t)g->ttiles * 4, st);
     k_tile_pairs<<<g->ptiles, 256, 0, st>>>(g->pbox, g->tbox, g->ptiles, g->ttiles, g->tw, g->pw,
-                                            r_test * r_test, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2);
+                                            g->ptmax, g->ttmax, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2);
     k_item_offsets<<<1, 64, 0, st>>>(g->cnt1, g->ptiles, g->ch1, g->cnt2, g->ttiles, g->ch2, g->off1,
                                      g->off2, g->counters);
     const int nbp = (int)((g->nt + 255) / 256);
@@ -1498,17 +1578,16 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     int *gate = tc ? &p->res_dev->gate : nullptr;
     k_prep_trunc<<<nbp, 256, 0, st>>>(psi, g->perm_t, g->y64, g->lnu, p->n, g->nt, D, eps, g->tdup,
                                       p->psinu, g->nu, p->flags, tc ? g->trec_s : nullptr, g->b_s,
-                                      1.0 / (double)p->tc_P, gate);
+                                      1.0 / (double)p->tc_P, gate, p->beta);
     trace_end(p);
     unsigned long long *pairs = reinterpret_cast<unsigned long long *>(&p->res_dev->pairs);
-    // pairs at distance < Rin are inside the radius and pairs at >= Rout outside
-    // it for the pairwise FP32 test too (its rounding is far below 1e-4 R)
-    const float Rin = (float)(radius * (1.0 - 1e-4) - 1e-6), Rout = (float)(radius * (1.0 + 1e-4) + 1e-6);
+    // block pairs are classified against their members' cutoff radii widened /
+    // narrowed by 1e-4 relative: the pairwise FP32 test's rounding is far below
     if (tc) {
         trace_begin(p, "lse_trunc_tc");
         k_lse_trunc_tc<<<g->slots1_tc, TP_THREADS1, 0, st>>>(
-            g->prec_s, g->Aq, g->pball16, g->trec_s, g->b_s, g->tball8, Rin, Rout, g->bits_pt, g->tw,
-            g->off1, g->ptiles, g->ch1, g->counters, g->part1, pairs, p->flags, gate);
+            g->prec_s, g->Aq, g->pball16, g->pal16, g->trec_s, g->b_s, g->tball8, g->tbe8, g->bits_pt,
+            g->tw, g->off1, g->ptiles, g->ch1, g->counters, g->part1, pairs, p->flags, gate);
         trace_end(p);
     }
     trace_begin(p, "lse_trunc_mixed");
@@ -1525,7 +1604,7 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     if (tc) {
         trace_begin(p, "grad_trunc_tc");
         k_grad_trunc_tc<<<g->slots2_tc, TP_THREADS2, 0, st>>>(
-            g->prec_s, g->Aq, g->u_s, g->pball8, g->trec_s, g->b_s, g->tball16, Rin, Rout,
+            g->prec_s, g->Aq, g->u_s, g->pball8, g->pal8, g->trec_s, g->b_s, g->tball16, g->tbe16,
             g->bits_tp, g->pw, g->off2, g->ttiles, g->ch2, g->counters + 1, g->part2, p->flags, gate);
         trace_end(p);
     }
@@ -1542,17 +1621,15 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     return cudaGetLastError();
 }
 
-cudaError_t trunc_eval(rsot_problem *p, const double *psi, double eps, double radius, int mixed,
-                       double *grad) {
-    if (!mixed) return launch_trunc_fp64(p, psi, eps, 0.5 * radius * radius, grad);
+cudaError_t trunc_eval(rsot_problem *p, const double *psi, double eps, int mixed, double *grad) {
+    if (!mixed) return launch_trunc_fp64(p, psi, eps, grad);
     if (!p->grid) {
         cudaError_t e = grid_build(p);
         if (e) return e;
     }
     // the target prep writes one psi.nu partial per 256 sorted targets
     if ((int64_t)p->nblk_prep * 256 < p->grid->nt) return cudaErrorInvalidValue;
-    return p->d == 3 ? trunc_mixed<3>(p, psi, eps, radius, grad)
-                     : trunc_mixed<2>(p, psi, eps, radius, grad);
+    return p->d == 3 ? trunc_mixed<3>(p, psi, eps, grad) : trunc_mixed<2>(p, psi, eps, grad);
 }
 
 cudaError_t trunc_point_L(rsot_problem *p, double *L) {
@@ -1570,7 +1647,7 @@ void trunc_free(rsot_problem *p) {
                     g->pbox, g->tbox, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2, g->off1, g->off2,
                     g->counters, g->Aq, g->tdup, g->ppair, g->part1, g->part2, g->lse_s, g->blockJ,
                     g->pball16, g->pball8, g->tball16, g->tball8, g->prec_s, g->trec_s, g->b_s,
-                    g->u_s};
+                    g->u_s, g->pal8, g->pal16, g->ptmax, g->tbe8, g->tbe16, g->ttmax};
     for (void *q : ptrs) cudaFree(q);
     delete g;
     p->grid = nullptr;
