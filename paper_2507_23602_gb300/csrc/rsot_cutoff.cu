@@ -136,6 +136,7 @@ cudaError_t cutoffs_uniform(rsot_problem *p, double C) {
     const int64_t m = std::max(p->nq_pad, p->n_pad);
     k_uniform<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->nq, p->nq_pad, p->n, p->n_pad, C,
                                                                  p->alpha, p->beta);
+    p->cut_anchored = 0;
     return cudaGetLastError();
 }
 
@@ -167,6 +168,7 @@ cudaError_t cutoffs_separable(rsot_problem *p, const double *psi, double eps, do
     k_separable<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p->nn, p->nn_c, psi, p->lnu, p->nq,
                                                             p->nq_pad, p->n, p->n_pad, eps,
                                                             eps * log(1.0 / tail), p->alpha, p->beta);
+    p->cut_anchored = 1;
     return cudaGetLastError();
 }
 

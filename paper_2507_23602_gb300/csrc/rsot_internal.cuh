@@ -123,6 +123,7 @@ struct rsot_problem {
     double *nn_c = nullptr;         // [nq] its cost
     double *alpha = nullptr;        // [nq_pad] per evaluation (-inf for padding)
     double *beta = nullptr;         // [n_pad]  per evaluation (-inf for padding)
+    int cut_anchored = 0;           // alpha is anchored at the nearest targets (psi-aware)
 
     // staging for host psi / grad
     double *psi_dev = nullptr;      // [n]

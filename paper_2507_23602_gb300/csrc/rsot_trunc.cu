@@ -66,14 +66,25 @@ struct Grid {
     int nblk_comb = 0;
     // tensor-core passes: block balls (centre, radius; radius < 0: no member),
     // operand records in sorted order, per-target b_j, per-point shifts u_q
-    float4 *pball16 = nullptr, *pball8 = nullptr, *tball16 = nullptr, *tball8 = nullptr;
+    float4 *pball64 = nullptr, *pball8 = nullptr, *tball64 = nullptr, *tball8 = nullptr;
     Rec16 *prec_s = nullptr, *trec_s = nullptr;
     float *b_s = nullptr, *u_s = nullptr;
     // per evaluation: (min, max) of alpha over point blocks of 16 / 8 and of
     // beta over target blocks of 8 / 16, maxima over point / target tiles
-    float2 *pal16 = nullptr, *pal8 = nullptr, *tbe8 = nullptr, *tbe16 = nullptr;
+    float2 *pal64 = nullptr, *pal8 = nullptr, *tbe8 = nullptr, *tbe64 = nullptr;
     float *ptmax = nullptr, *ttmax = nullptr;
-    int slots1_tc = 0, slots2_tc = 0;
+    // initial pass-1 shift per point: ceil of the exponent of its nearest target
+    // (psi-aware cutoffs: a kept term, a lower bound of the maximum), -inf else
+    float *m0_s = nullptr;
+    // block-skip tensor-core passes: boxes of 512-point / 512- and 1024-target
+    // runs (once), maxima of alpha / beta over them (per evaluation), partials
+    // in the item layout (tile * chunks + chunk) and its offsets
+    float *pbox512 = nullptr, *tbox512 = nullptr, *tbox1024 = nullptr;
+    float *pa512 = nullptr, *tb512 = nullptr, *tb1024 = nullptr;
+    float2 *part1b = nullptr;
+    double *part2b = nullptr;
+    int *off1b = nullptr, *off2b = nullptr;
+    int k1b = 0, k2b = 0;
 };
 
 namespace {
@@ -258,14 +269,19 @@ __global__ void k_point_recs_s(const float *__restrict__ xs, int64_t nqt, int d,
 }
 
 // ------------------------------------------------------------- per evaluation
-// A_q = k |x'_q|^2 - 2k alpha_q (FP32, computed once so that both passes agree)
+// A_q = k |x'_q|^2 - 2k alpha_q (FP32, computed once so that both passes agree).
+// With anchored (psi-aware) cutoffs alpha_q = c_qn - psi_n - eps ln nu_n, the
+// exponent of the anchor pair is r_qn = b_n + k|x'_q|^2 - 2k c_qn = A_q - 2k psi_c:
+// M0 = ceil(r_qn) starts the pass-1 running maximum there.
 __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt, int d, float k,
                           const double *__restrict__ alpha, const int *__restrict__ perm_q,
-                          double k2, float *__restrict__ Aq) {
+                          double k2, const double *__restrict__ psi, int anchored,
+                          float *__restrict__ Aq, float *__restrict__ M0) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nqt) return;
     if (s >= nq) {
         Aq[s] = INFINITY;
+        M0[s] = -INFINITY;
         return;
     }
     float r2 = 0.f;
@@ -273,7 +289,9 @@ __global__ void k_trunc_A(const float *__restrict__ xs, int64_t nq, int64_t nqt,
         const float v = xs[t * nqt + s];
         r2 = fmaf(v, v, r2);
     }
-    Aq[s] = fmaf(k, r2, -(float)(k2 * alpha[perm_q[s]]));
+    const double a = alpha[perm_q[s]];
+    Aq[s] = fmaf(k, r2, -(float)(k2 * a));
+    M0[s] = anchored ? ceilf(fmaf(k, r2, -(float)(k2 * (a + psi[0])))) : -INFINITY;
 }
 
 // (min, max) of v[perm[s]] over runs of 8 sorted members (real members only:
@@ -640,21 +658,13 @@ __global__ void __launch_bounds__(L_THREADS, 3)
 // -------------------------------------------------- tensor-core truncated passes
 // The pair exponents come from the mma of rsot_tc.cuh (bitwise the same in
 // both passes).  A block pair -- 16 points x 8 targets in pass 1, 16 targets x
-// 8 points in pass 2 -- is classified by the bounding balls of its blocks:
+// 8 points in pass 2 -- is classified by the bounding balls of its blocks and
+// the ranges of the cutoffs of their members:
 // "outside" (every pair farther than the radius: skipped), "inside" (every
 // pair nearer: no test) or "boundary" (each pair tested, r_qj - b_j > A_q, in
 // FP32 on the mma result).  The classification margins (1e-4 R) exceed the
 // rounding of the pairwise test, so a classified pair gets the decision the
 // test would give and both passes sum over the same pairs.
-constexpr int TP_THREADS1 = 512;   // pass 1: 16 warps x 4 m-blocks x 16 points = PT
-constexpr int TP_THREADS2 = 128;   // pass 2: 4 warps x 4 m-blocks x 16 targets = TT
-constexpr int TP_PST = 256;        // points per pass-2 stage
-static_assert(TP_THREADS1 / 32 * TC_MB * 16 == PT, "pass-1 CTA covers a point tile");
-static_assert(TP_THREADS2 / 32 * TC_MB * 16 == TT, "pass-2 CTA covers a target tile");
-
-// a, b: the balls; ra, rb: (min, max) of alpha / beta over their members.
-// Every pair of the two blocks has a cutoff radius sqrt(2 (alpha_q + beta_j))
-// between sqrt(2 (ra.x + rb.x)) and sqrt(2 (ra.y + rb.y)).
 __device__ __forceinline__ int tp_class(float4 a, float4 b, float2 ra, float2 rb) {
     if (a.w < 0.f || b.w < 0.f) return 0;
     const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
@@ -701,427 +711,402 @@ __device__ __forceinline__ void tp_lse_epi(const float (&d)[4], int cls, float2 
     }
 }
 
-__global__ void __launch_bounds__(TP_THREADS1, 1)
-    k_lse_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
-                   const float4 *__restrict__ pball16, const float2 *__restrict__ pal16,
-                   const Rec16 *__restrict__ trec, const float *__restrict__ bs,
-                   const float4 *__restrict__ tball8, const float2 *__restrict__ tbe8,
-                   const uint32_t *__restrict__ bits_pt, int tw,
-                   const int *__restrict__ off1, int ptiles, int ch1, int *__restrict__ counter,
-                   float2 *__restrict__ part1, unsigned long long *__restrict__ pairs,
-                   int *__restrict__ flags, const int *__restrict__ gate) {
-    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernel runs
-    __shared__ __align__(128) Rec16 s_rec[2][TT];
-    __shared__ __align__(16) float s_b[2][TT];
-    __shared__ __align__(16) float4 s_ball[2][TT / 8];
-    __shared__ __align__(16) float2 s_be[2][TT / 8];
-    __shared__ __align__(8) uint64_t full[2], empty[2];
-    __shared__ int s_item, s_p, s_cnt, s_abort[2];
-    __shared__ int s_list[MAX_CH];
+// --------------------------------------------- block-skip tensor-core passes
+// The pipeline of the dense tensor-core passes (rsot_dense.cu: 256 threads,
+// 4 m-blocks of 16 rows per warp in registers, stages of TC_TS = 1024 records
+// in shared memory filled by bulk copies, released per warp on an `empty`
+// mbarrier) over the Morton-sorted points and targets, with the truncation:
+//   * per CTA, only the stages whose box lies within the largest cutoff
+//     radius of the CTA's rows are copied (a box test against the maxima of
+//     alpha and beta);
+//   * per block pair (16 rows x 8 columns) the class of tp_class: outside
+//     pairs skip the mma, boundary pairs test every pair on the mma result.
+// Each CTA covers TC_ROWS = 512 rows and one chunk of stages; the partials
+// land in the item layout of the queue kernels (items of PT points or TT
+// targets, numbered tile * chunks + chunk), so that the same merge kernels
+// read them.
+constexpr int BS_CHUNK = 8;   // stages per CTA chunk
+constexpr size_t BS_SMEM1 =
+    (size_t)TC_STAGES * (TC_TS * sizeof(Rec16) + TC_TS * sizeof(float) + TC_NBS * (sizeof(float4) + sizeof(float2)));
+constexpr size_t BS_SMEM2 =
+    (size_t)TC_STAGES * (TC_TS * sizeof(Rec16) + 2 * TC_TS * sizeof(float) + TC_NBS * (sizeof(float4) + sizeof(float2)));
+static_assert(TC_ROWS == 512 && TC_TS == 1024 && PT == 2 * TC_ROWS && TC_ROWS == 2 * TT,
+              "block-skip layout: a CTA is half a point tile / two target tiles");
+
+// candidate stages of one CTA: box of its rows (6 floats) and their largest
+// alpha / beta against each stage's box and largest beta / alpha
+__device__ __forceinline__ int bs_list(const float *__restrict__ rbox, float rmax,
+                                       const float *__restrict__ sbox, const float *__restrict__ smax,
+                                       int st0, int st1, int *list) {
+    float rb[6];
+    for (int k = 0; k < 6; ++k) rb[k] = rbox[k];
+    int c = 0;
+    if (!(rb[0] <= rb[3])) return 0;
+    for (int s = st0; s < st1; ++s) {
+        float sb[6];
+        for (int k = 0; k < 6; ++k) sb[k] = sbox[s * 6 + k];
+        if (!(sb[0] <= sb[3])) continue;
+        const float rr = sqrtf(fmaxf(0.f, 2.f * (rmax + smax[s]))) * (1.0f + 1e-5f) + 1e-6f;
+        if (box_dist2(rb, sb) < rr * rr) list[c++] = s;
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, TC_MINB)
+    k_lse_tcb(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
+              const float *__restrict__ M0, const float4 *__restrict__ pball64,
+              const float2 *__restrict__ pal64, const float *__restrict__ pbox512,
+              const float *__restrict__ pa512, const Rec16 *__restrict__ trec,
+              const float *__restrict__ bs, const float4 *__restrict__ tball8,
+              const float2 *__restrict__ tbe8, const float *__restrict__ tbox1024,
+              const float *__restrict__ tb1024, int nstages, int k1, float2 *__restrict__ part1,
+              unsigned long long *__restrict__ pairs, int *__restrict__ flags,
+              const int *__restrict__ gate) {
+    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernels run
+    extern __shared__ __align__(128) unsigned char bs_smem[];
+    constexpr size_t oB = TC_STAGES * TC_TS * sizeof(Rec16);
+    constexpr size_t oBall = oB + TC_STAGES * TC_TS * sizeof(float);
+    constexpr size_t oBe = oBall + TC_STAGES * TC_NBS * sizeof(float4);
+    Rec16 (*s_rec)[TC_TS] = reinterpret_cast<Rec16 (*)[TC_TS]>(bs_smem);
+    float (*s_b)[TC_TS] = reinterpret_cast<float (*)[TC_TS]>(bs_smem + oB);
+    float4 (*s_ball)[TC_NBS] = reinterpret_cast<float4 (*)[TC_NBS]>(bs_smem + oBall);
+    float2 (*s_be)[TC_NBS] = reinterpret_cast<float2 (*)[TC_NBS]>(bs_smem + oBe);
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
+    __shared__ int s_list[BS_CHUNK], s_cnt;
     __shared__ unsigned long long s_pairs;
-    constexpr unsigned kStage =
-        TT * sizeof(Rec16) + TT * sizeof(float) + TT / 8 * (sizeof(float4) + sizeof(float2));
+    __shared__ int s_ab;
+    constexpr unsigned kStage = TC_TS * (sizeof(Rec16) + sizeof(float)) + TC_NBS * (sizeof(float4) + sizeof(float2));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    const int kc = blockIdx.y;
     if (tid == 0) {
-        for (int st = 0; st < 2; ++st) {
+        s_cnt = bs_list(pbox512 + (size_t)blockIdx.x * 6, pa512[blockIdx.x], tbox1024, tb1024,
+                        kc * BS_CHUNK, min(nstages, (kc + 1) * BS_CHUNK), s_list);
+        s_pairs = 0;
+        s_ab = 0;
+        for (int st = 0; st < TC_STAGES; ++st) {
             mbar_init(&full[st], 1);
-            mbar_init(&empty[st], TP_THREADS1 / 32);
+            mbar_init(&empty[st], TC_WARPS);
         }
         fence_barrier_init();
-        s_abort[0] = s_abort[1] = 0;
-        s_pairs = 0;
     }
     __syncthreads();
-    const int total = off1[ptiles];
-    unsigned git = 0;
-    unsigned long long mycnt = 0;
-    bool aborted = false;
+    const int cnt = s_cnt;
+#define BS_ISSUE1(it_)                                                                               \
+    do {                                                                                             \
+        const int sl_ = (it_) % TC_STAGES;                                                           \
+        const int64_t j_ = (int64_t)s_list[it_] * TC_TS;                                             \
+        mbar_expect_tx(&full[sl_], kStage);                                                          \
+        bulk_g2s(s_rec[sl_], trec + j_, TC_TS * sizeof(Rec16), &full[sl_]);                          \
+        bulk_g2s(s_b[sl_], bs + j_, TC_TS * sizeof(float), &full[sl_]);                              \
+        bulk_g2s(s_ball[sl_], tball8 + j_ / 8, TC_NBS * sizeof(float4), &full[sl_]);                 \
+        bulk_g2s(s_be[sl_], tbe8 + j_ / 8, TC_NBS * sizeof(float2), &full[sl_]);                     \
+    } while (0)
+    if (tid == 0)
+        for (int it = 0; it < TC_STAGES && it < cnt; ++it) BS_ISSUE1(it);
+    int issued = min(TC_STAGES, cnt);
+    const int64_t q0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
     const uint2 *pr = reinterpret_cast<const uint2 *>(prec);
-    for (;;) {
-        if (tid == 0) {
-            const int it = atomicAdd(counter, 1);
-            s_item = it;
-            if (it < total) {
-                const int pt = find_row(off1, ptiles, it);
-                s_p = pt;
-                s_cnt = collect_bits(bits_pt + (size_t)pt * tw, tw, (it - off1[pt]) * ch1, ch1, s_list);
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) break;
-        const int pt = s_p, cnt = s_cnt;
-        if (tid == 0) {
-            for (int st = 0; st < 2 && st < cnt; ++st) {
-                const unsigned slot = (git + st) & 1u;
-                const int64_t tt = s_list[st];
-                mbar_expect_tx(&full[slot], kStage);
-                bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
-                bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
-                bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
-                bulk_g2s(s_be[slot], tbe8 + tt * (TT / 8), TT / 8 * sizeof(float2), &full[slot]);
-            }
-        }
-        const int64_t q0 = (int64_t)pt * PT + warp * (TC_MB * 16);
-        unsigned A[TC_MB][4];
-        float Ag[TC_MB], Ag8[TC_MB];
-        float2 M[TC_MB], Sf[TC_MB];
-        double2 Sd[TC_MB];
-        float4 pb[TC_MB];
-        unsigned rv[TC_MB];   // real rows among g, g + 8 (padding has A = +inf)
+    unsigned A[TC_MB][4];
+    float Ag[TC_MB], Ag8[TC_MB];
+    float2 M[TC_MB], Sf[TC_MB];
+    double2 Sd[TC_MB];
+    unsigned rvs = 0;   // real rows of this lane (rows g, g + 8 of the 4 m-blocks; padding has A = +inf)
 #pragma unroll
-        for (int m = 0; m < TC_MB; ++m) {
-            const int64_t qb = q0 + m * 16;
-            load_a(A[m], pr[(qb + g) * 4 + t], pr[(qb + g + 8) * 4 + t]);
-            Ag[m] = Aq[qb + g];
-            Ag8[m] = Aq[qb + g + 8];
-            rv[m] = (unsigned)(Ag[m] < INFINITY) + (unsigned)(Ag8[m] < INFINITY);
-            pb[m] = pball16[qb / 16];
-            M[m] = make_float2(-INFINITY, -INFINITY);
-            Sf[m] = make_float2(0.f, 0.f);
-            Sd[m] = make_double2(0.0, 0.0);
-        }
-        unsigned icnt = 0;
-        bool wabort = false;
-        // no block barrier per stage: warps release stages on `empty`, thread 0
-        // refills; decisions are warp-uniform (the mma needs every lane)
-        for (int it = 0; it < cnt; ++it) {
-            const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
-                s_abort[0] = 1;
-                atomicOr(flags, kErrTimeout);
-                wabort = true;
-                break;
-            }
-            {
-                const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
-                const float2 *bp = reinterpret_cast<const float2 *>(&s_b[slot][0]) + t;
-                // classes of this warp's 4 point m-blocks against the stage's 32
-                // target n-blocks: lane l classifies n-block l (2 bits per m-block)
-                unsigned mycls = 0;
-                {
-                    const float4 tb = s_ball[slot][lane];
-                    const float2 tr2 = s_be[slot][lane];
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m)   // alpha ranges from L1: fewer registers
-                        mycls |= (unsigned)tp_class(pb[m], tb, pal16[q0 / 16 + m], tr2) << (2 * m);
-                }
-                const unsigned live = __ballot_sync(0xffffffffu, mycls != 0);
-#pragma unroll 1
-                for (int grp = 0; grp < TT / 8 / TC_GROUP; ++grp) {
-                    const unsigned gmask = (live >> (grp * TC_GROUP)) & ((1u << TC_GROUP) - 1u);
-                    if (!gmask) continue;
-                    float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m) {
-                        acc[m] = make_float2(0.f, 0.f);
-                        ng[m] = make_float2(-M[m].x, -M[m].x);
-                        ng8[m] = make_float2(-M[m].y, -M[m].y);
-                    }
-                    // two live n-blocks per step: their mma are issued before either
-                    // epilogue, so the latency of one hides behind the other's work
-                    for (unsigned gm = gmask; gm;) {
-                        const int nb0 = grp * TC_GROUP + __ffs(gm) - 1;
-                        gm &= gm - 1;
-                        const bool two = gm != 0;
-                        const int nb1 = two ? grp * TC_GROUP + __ffs(gm) - 1 : nb0;
-                        if (two) gm &= gm - 1;
-                        const unsigned cl0 = __shfl_sync(0xffffffffu, mycls, nb0);
-                        const unsigned cl1 = two ? __shfl_sync(0xffffffffu, mycls, nb1) : 0u;
-                        const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
-                        const float2 bb0 = bp[4 * nb0], bb1 = bp[4 * nb1];
-                        float d0[TC_MB][4], d1[TC_MB][4];
-#pragma unroll
-                        for (int m = 0; m < TC_MB; ++m) {
-                            if ((cl0 >> (2 * m)) & 3u) mma_tc(d0[m], A[m], bf0);
-                            if ((cl1 >> (2 * m)) & 3u) mma_tc(d1[m], A[m], bf1);
-                        }
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const unsigned cl = h ? cl1 : cl0;
-                            const float2 bb = h ? bb1 : bb0;
-                            const float2 nbb = make_float2(-bb.x, -bb.y);
-                            const unsigned cv = (unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY);
-#pragma unroll
-                            for (int m = 0; m < TC_MB; ++m) {
-                                const int c = (int)((cl >> (2 * m)) & 3u);
-                                if (c == 0) continue;
-                                float2 e01, e23;
-                                tp_lse_epi(h ? d1[m] : d0[m], c, ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01,
-                                           e23, icnt);
-                                if (c == 1) icnt += rv[m] * cv;
-                                acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                                acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
-                            }
-                        }
-                    }
-                    bool bad = false;
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m)
-                        bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) ||
-                              (M[m].x == -INFINITY && acc[m].x != 0.f) ||
-                              (M[m].y == -INFINITY && acc[m].y != 0.f);
-                    if (__any_sync(0xffffffffu, bad)) {
-                        // exact redo of the group: maximum over the included pairs,
-                        // shifts raised, sums recomputed (pairs are not counted again)
-#pragma unroll
-                        for (int m = 0; m < TC_MB; ++m) {
-                            float mg = -INFINITY, mg8 = -INFINITY;
-                            unsigned dummy = 0;
-                            const float2 z = make_float2(0.f, 0.f);
-                            for (unsigned gm = gmask; gm; gm &= gm - 1) {
-                                const int nb = grp * TC_GROUP + __ffs(gm) - 1;
-                                const int c = (int)((__shfl_sync(0xffffffffu, mycls, nb) >> (2 * m)) & 3u);
-                                if (c == 0) continue;
-                                const float2 bb = bp[4 * nb];
-                                float2 e01, e23;
-                                tp_lse_pair(A[m], rec[32 * nb], c, z, z, make_float2(-bb.x, -bb.y),
-                                            Ag[m], Ag8[m], e01, e23, dummy);
-                                mg = max3f(mg, e01.x, e01.y);
-                                mg8 = max3f(mg8, e23.x, e23.y);
-                            }
-                            if (mg > -INFINITY) {
-                                const float mn = ceilf(mg);
-                                if (mn > M[m].x) {
-                                    if (M[m].x != -INFINITY) {
-                                        Sf[m].x *= pow2_int_f(M[m].x - mn);
-                                        Sd[m].x *= pow2_int_d(M[m].x - mn);
-                                    }
-                                    M[m].x = mn;
-                                }
-                            }
-                            if (mg8 > -INFINITY) {
-                                const float mn = ceilf(mg8);
-                                if (mn > M[m].y) {
-                                    if (M[m].y != -INFINITY) {
-                                        Sf[m].y *= pow2_int_f(M[m].y - mn);
-                                        Sd[m].y *= pow2_int_d(M[m].y - mn);
-                                    }
-                                    M[m].y = mn;
-                                }
-                            }
-                            const float2 g1 = make_float2(-M[m].x, -M[m].x), g8 = make_float2(-M[m].y, -M[m].y);
-                            float2 a2 = make_float2(0.f, 0.f);
-                            for (unsigned gm = gmask; gm; gm &= gm - 1) {
-                                const int nb = grp * TC_GROUP + __ffs(gm) - 1;
-                                const int c = (int)((__shfl_sync(0xffffffffu, mycls, nb) >> (2 * m)) & 3u);
-                                if (c == 0) continue;
-                                const float2 bb = bp[4 * nb];
-                                float2 e01, e23;
-                                tp_lse_pair(A[m], rec[32 * nb], c, g1, g8, make_float2(-bb.x, -bb.y),
-                                            Ag[m], Ag8[m], e01, e23, dummy);
-                                a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                                a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
-                            }
-                            acc[m] = a2;
-                        }
-                    }
-#pragma unroll
-                    for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            if (warp == 0 && it + 2 < cnt) {
-                bool ok = true;
-                if (tid == 0) {
-                    ok = mbar_wait(&empty[slot], ph);
-                    if (ok) {
-                        const int64_t tt = s_list[it + 2];
-                        mbar_expect_tx(&full[slot], kStage);
-                        bulk_g2s(s_rec[slot], trec + tt * TT, TT * sizeof(Rec16), &full[slot]);
-                        bulk_g2s(s_b[slot], bs + tt * TT, TT * sizeof(float), &full[slot]);
-                        bulk_g2s(s_ball[slot], tball8 + tt * (TT / 8), TT / 8 * sizeof(float4), &full[slot]);
-                        bulk_g2s(s_be[slot], tbe8 + tt * (TT / 8), TT / 8 * sizeof(float2), &full[slot]);
-                    }
-                }
-                if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                    s_abort[0] = 1;
-                    atomicOr(flags, kErrTimeout);
-                    wabort = true;
-                    break;
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < TC_MB; ++m) {
-                Sd[m].x += (double)Sf[m].x;
-                Sd[m].y += (double)Sf[m].y;
-                Sf[m] = make_float2(0.f, 0.f);
-            }
-        }
-        git += cnt;
-        mycnt += icnt;
-        // merge the 4 lanes of each row (common shift = their maximum)
-if (!wabort) {
-#pragma unroll
-        for (int m = 0; m < TC_MB; ++m) {
-            float mx = M[m].x, my = M[m].y;
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 1));
-            my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 2));
-            double sx = M[m].x == -INFINITY ? 0.0 : Sd[m].x * pow2_int_d(M[m].x - mx);
-            double sy = M[m].y == -INFINITY ? 0.0 : Sd[m].y * pow2_int_d(M[m].y - my);
-            sx += __shfl_xor_sync(0xffffffffu, sx, 1);
-            sx += __shfl_xor_sync(0xffffffffu, sx, 2);
-            sy += __shfl_xor_sync(0xffffffffu, sy, 1);
-            sy += __shfl_xor_sync(0xffffffffu, sy, 2);
-            if (m == t) {
-                const int l = warp * (TC_MB * 16) + m * 16 + g;
-                float2 *o = part1 + (int64_t)item * PT;
-                o[l] = mx == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(mx, (float)sx);
-                o[l + 8] = my == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(my, (float)sy);
-            }
-        }
-        }
-        __syncthreads();   // end of the item: every warp is past its stages
-        if (s_abort[0]) {
+    for (int m = 0; m < TC_MB; ++m) {
+        const int64_t qb = q0 + m * 16;
+        tc_load_a(A[m], pr + qb * 4, g, t);
+        Ag[m] = Aq[qb + g];
+        Ag8[m] = Aq[qb + g + 8];
+        rvs += (unsigned)(Ag[m] < INFINITY) + (unsigned)(Ag8[m] < INFINITY);
+        M[m] = make_float2(M0[qb + g], M0[qb + g + 8]);
+        Sf[m] = make_float2(0.f, 0.f);
+        Sd[m] = make_double2(0.0, 0.0);
+    }
+    // the warp's 64 rows are classified together against each n-block
+    const float4 wball = pball64[q0 / 64];
+    const float2 wal = pal64[q0 / 64];
+    unsigned icnt = 0;
+    bool aborted = false;
+    for (int it = 0; it < cnt; ++it) {
+        const int slot = it % TC_STAGES;
+        const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+            atomicOr(flags, kErrTimeout);
             aborted = true;
             break;
         }
-    }
-    atomicAdd(&s_pairs, mycnt);
-    __syncthreads();
-    if (tid == 0) {
-        if (s_pairs) atomicAdd(pairs, s_pairs);
-        if (aborted) {   // bounded drain of copies that may still be in flight
-            for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(TP_THREADS2)
-    k_grad_trunc_tc(const Rec16 *__restrict__ prec, const float *__restrict__ Aq,
-                    const float *__restrict__ us, const float4 *__restrict__ pball8,
-                    const float2 *__restrict__ pal8, const Rec16 *__restrict__ trec,
-                    const float *__restrict__ bs, const float4 *__restrict__ tball16,
-                    const float2 *__restrict__ tbe16,
-                    const uint32_t *__restrict__ bits_tp, int pw, const int *__restrict__ off2,
-                    int ttiles, int ch2, int *__restrict__ counter, double *__restrict__ part2,
-                    int *__restrict__ flags, const int *__restrict__ gate) {
-    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernel runs
-    __shared__ __align__(128) Rec16 s_rec[2][TP_PST];
-    __shared__ __align__(16) float s_u[2][TP_PST];
-    __shared__ __align__(16) float s_A[2][TP_PST];
-    __shared__ __align__(16) float4 s_ball[2][TP_PST / 8];
-    __shared__ __align__(16) float2 s_al[2][TP_PST / 8];
-    __shared__ __align__(8) uint64_t full[2], empty[2];
-    __shared__ int s_item, s_t, s_cnt, s_abort[2];
-    __shared__ int s_list[MAX_CH];
-    constexpr unsigned kStage = TP_PST * (sizeof(Rec16) + 2 * sizeof(float)) +
-                                TP_PST / 8 * (sizeof(float4) + sizeof(float2));
-    constexpr int SPT = PT / TP_PST;   // stages per point tile
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-    if (tid == 0) {
-        for (int st = 0; st < 2; ++st) {
-            mbar_init(&full[st], 1);
-            mbar_init(&empty[st], TP_THREADS2 / 32);
-        }
-        fence_barrier_init();
-        s_abort[0] = s_abort[1] = 0;
-    }
-    __syncthreads();
-    const int total = off2[ttiles];
-    unsigned git = 0;
-    bool aborted = false;
-    const uint2 *tr = reinterpret_cast<const uint2 *>(trec);
-#define TP_ISSUE(st_, slot_)                                                                  \
-    do {                                                                                      \
-        const int64_t q_ = (int64_t)s_list[(st_) / SPT] * PT + ((st_) % SPT) * TP_PST;        \
-        mbar_expect_tx(&full[slot_], kStage);                                                 \
-        bulk_g2s(s_rec[slot_], prec + q_, TP_PST * sizeof(Rec16), &full[slot_]);              \
-        bulk_g2s(s_u[slot_], us + q_, TP_PST * sizeof(float), &full[slot_]);                  \
-        bulk_g2s(s_A[slot_], Aq + q_, TP_PST * sizeof(float), &full[slot_]);                  \
-        bulk_g2s(s_ball[slot_], pball8 + q_ / 8, TP_PST / 8 * sizeof(float4), &full[slot_]); \
-        bulk_g2s(s_al[slot_], pal8 + q_ / 8, TP_PST / 8 * sizeof(float2), &full[slot_]);     \
-    } while (0)
-    for (;;) {
-        if (tid == 0) {
-            const int it = atomicAdd(counter, 1);
-            s_item = it;
-            if (it < total) {
-                const int tt = find_row(off2, ttiles, it);
-                s_t = tt;
-                s_cnt = collect_bits(bits_tp + (size_t)tt * pw, pw, (it - off2[tt]) * ch2, ch2, s_list);
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) break;
-        const int tt = s_t;
-        const int nst = SPT * s_cnt;
-        if (tid == 0)
-            for (int st = 0; st < 2 && st < nst; ++st) TP_ISSUE(st, (git + st) & 1u);
-        const int64_t j0 = (int64_t)tt * TT + warp * (TC_MB * 16);
-        unsigned A[TC_MB][4];
-        float2 bgg[TC_MB];   // (-b_g, -b_g) and (-b_g+8, -b_g+8) as two pairs
-        float2 bg8[TC_MB];
-        float4 tb[TC_MB];
-        float2 tbr[TC_MB];
-        double2 acc64[TC_MB];
+        {
+            const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
+            const float2 *bp = reinterpret_cast<const float2 *>(&s_b[slot][0]) + t;
+            // classes of the warp's 64 rows against n-blocks lane + 32 i (2 bits at 2 i)
+            unsigned cls = 0;
 #pragma unroll
-        for (int m = 0; m < TC_MB; ++m) {
-            const int64_t jb = j0 + m * 16;
-            load_a(A[m], tr[(jb + g) * 4 + t], tr[(jb + g + 8) * 4 + t]);
-            const float b0 = bs[jb + g], b8 = bs[jb + g + 8];
-            bgg[m] = make_float2(-b0, -b0);
-            bg8[m] = make_float2(-b8, -b8);
-            tb[m] = tball16[jb / 16];
-            tbr[m] = tbe16[jb / 16];
-            acc64[m] = make_double2(0.0, 0.0);
-        }
-        bool wabort = false;
-        for (int it = 0; it < nst; ++it) {
-            const unsigned gs = git + it, slot = gs & 1u, ph = (gs >> 1) & 1u;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
-                s_abort[0] = 1;
-                atomicOr(flags, kErrTimeout);
-                wabort = true;
-                break;
-            }
-            {
-                const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
-                const float2 *up = reinterpret_cast<const float2 *>(&s_u[slot][0]) + t;
-                const float2 *ap = reinterpret_cast<const float2 *>(&s_A[slot][0]) + t;
-                float2 acc[TC_MB];
+            for (int i = 0; i < 4; ++i)
+                cls |= (unsigned)tp_class(wball, s_ball[slot][lane + 32 * i], wal, s_be[slot][lane + 32 * i]) << (2 * i);
+            unsigned lv[4];
 #pragma unroll
-                for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
-                // classes of this warp's 4 target m-blocks against the stage's 32 point
-                // n-blocks: lane l classifies n-block l (2 bits per m-block)
-                unsigned mycls = 0;
-                {
-                    const float4 pbl = s_ball[slot][lane];
-                    const float2 pal = s_al[slot][lane];
+            for (int i = 0; i < 4; ++i) lv[i] = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) != 0u);
+#pragma unroll 1
+            for (int grp = 0; grp < TC_NBS / TC_GROUP; ++grp) {
+                const int sh2 = 2 * (grp >> 2);
+                const unsigned gmask = (lv[grp >> 2] >> ((grp & 3) * 8)) & 0xffu;
+                if (!gmask) continue;
+                float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
 #pragma unroll
-                    for (int m = 0; m < TC_MB; ++m)
-                        mycls |= (unsigned)tp_class(tb[m], pbl, tbr[m], pal) << (2 * m);
+                for (int m = 0; m < TC_MB; ++m) {
+                    acc[m] = make_float2(0.f, 0.f);
+                    ng[m] = make_float2(-M[m].x, -M[m].x);
+                    ng8[m] = make_float2(-M[m].y, -M[m].y);
                 }
-                // two live n-blocks per step (mma of both before either epilogue)
-                for (unsigned live = __ballot_sync(0xffffffffu, mycls != 0); live;) {
-                    const int nb0 = __ffs(live) - 1;
-                    live &= live - 1;
-                    const bool two = live != 0;
-                    const int nb1 = two ? __ffs(live) - 1 : nb0;
-                    if (two) live &= live - 1;
-                    const unsigned cl0 = __shfl_sync(0xffffffffu, mycls, nb0);
-                    const unsigned cl1 = two ? __shfl_sync(0xffffffffu, mycls, nb1) : 0u;
+                for (unsigned gm = gmask; gm;) {
+                    const int nb0 = grp * TC_GROUP + __ffs(gm) - 1;
+                    gm &= gm - 1;
+                    const bool two = gm != 0;
+                    const int nb1 = two ? grp * TC_GROUP + __ffs(gm) - 1 : nb0;
+                    if (two) gm &= gm - 1;
+                    const int c0 = (int)((__shfl_sync(0xffffffffu, cls, nb0 & 31) >> sh2) & 3u);
+                    const int c1 = two ? (int)((__shfl_sync(0xffffffffu, cls, nb1 & 31) >> sh2) & 3u) : 0;
                     const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
                     float d0[TC_MB][4], d1[TC_MB][4];
 #pragma unroll
                     for (int m = 0; m < TC_MB; ++m) {
-                        if ((cl0 >> (2 * m)) & 3u) mma_tc(d0[m], A[m], bf0);
-                        if ((cl1 >> (2 * m)) & 3u) mma_tc(d1[m], A[m], bf1);
+                        mma_tc(d0[m], A[m], bf0);
+                        if (two) mma_tc(d1[m], A[m], bf1);
                     }
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int nb = h ? nb1 : nb0;
-                        const unsigned cl = h ? cl1 : cl0;
-                        const float2 u = up[4 * nb];     // (u_2t, u_2t+1)
-                        const float2 Ac = ap[4 * nb];    // (A_2t, A_2t+1)
+                        if (h && !two) break;
+                        const int c = h ? c1 : c0;
+                        const float2 bb = bp[4 * (h ? nb1 : nb0)];
+                        const float2 nbb = make_float2(-bb.x, -bb.y);
+                        if (c == 1) icnt += rvs * ((unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY));
 #pragma unroll
                         for (int m = 0; m < TC_MB; ++m) {
-                            const int c = (int)((cl >> (2 * m)) & 3u);
-                            if (c == 0) continue;
+                            float2 e01, e23;
+                            tp_lse_epi(h ? d1[m] : d0[m], c, ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01, e23, icnt);
+                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                        }
+                    }
+                }
+                bool bad = false;
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m)
+                    bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) ||
+                          (M[m].x == -INFINITY && acc[m].x != 0.f) || (M[m].y == -INFINITY && acc[m].y != 0.f);
+                if (__any_sync(0xffffffffu, bad)) {
+                    // exact redo of the group: maximum over the included pairs,
+                    // shifts raised, sums recomputed (pairs are not counted again)
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        float mg = -INFINITY, mg8 = -INFINITY;
+                        unsigned dummy = 0;
+                        const float2 z = make_float2(0.f, 0.f);
+                        for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                            const int nb = grp * TC_GROUP + __ffs(gm) - 1;
+                            const int c = (int)((__shfl_sync(0xffffffffu, cls, nb & 31) >> sh2) & 3u);
+                            const float2 bb = bp[4 * nb];
+                            float2 e01, e23;
+                            tp_lse_pair(A[m], rec[32 * nb], c, z, z, make_float2(-bb.x, -bb.y), Ag[m], Ag8[m],
+                                        e01, e23, dummy);
+                            mg = max3f(mg, e01.x, e01.y);
+                            mg8 = max3f(mg8, e23.x, e23.y);
+                        }
+                        if (mg > -INFINITY) tc_raise(M[m].x, mg, Sf[m].x, Sd[m].x);
+                        if (mg8 > -INFINITY) tc_raise(M[m].y, mg8, Sf[m].y, Sd[m].y);
+                        const float2 g1 = make_float2(-M[m].x, -M[m].x), g8 = make_float2(-M[m].y, -M[m].y);
+                        float2 a2 = make_float2(0.f, 0.f);
+                        for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                            const int nb = grp * TC_GROUP + __ffs(gm) - 1;
+                            const int c = (int)((__shfl_sync(0xffffffffu, cls, nb & 31) >> sh2) & 3u);
+                            const float2 bb = bp[4 * nb];
+                            float2 e01, e23;
+                            tp_lse_pair(A[m], rec[32 * nb], c, g1, g8, make_float2(-bb.x, -bb.y), Ag[m], Ag8[m],
+                                        e01, e23, dummy);
+                            a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
+                            a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                        }
+                        acc[m] = a2;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (warp == 0 && it + TC_STAGES < cnt) {
+            bool ok = true;
+            if (tid == 0) {
+                ok = mbar_wait(&empty[slot], ph);
+                if (ok) {
+                    BS_ISSUE1(it + TC_STAGES);
+                    ++issued;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                atomicOr(flags, kErrTimeout);
+                aborted = true;
+                break;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < TC_MB; ++m) {
+            Sd[m].x += (double)Sf[m].x;
+            Sd[m].y += (double)Sf[m].y;
+            Sf[m] = make_float2(0.f, 0.f);
+        }
+    }
+#undef BS_ISSUE1
+    // a warp whose wait expired writes nothing (the error flag is set) but still
+    // reaches the closing barrier; thread 0 then drains its copies (bounded)
+    if (aborted && lane == 0) s_ab = 1;
+    // merge the 4 lanes of each row (common shift = their maximum); item layout
+    float2 *o = part1 + ((int64_t)(blockIdx.x >> 1) * k1 + kc) * PT + (blockIdx.x & 1) * TC_ROWS;
+#pragma unroll
+    for (int m = 0; m < TC_MB && !aborted; ++m) {
+        float mx = M[m].x, my = M[m].y;
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 1));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 2));
+        double sx = M[m].x == -INFINITY ? 0.0 : Sd[m].x * pow2_int_d(M[m].x - mx);
+        double sy = M[m].y == -INFINITY ? 0.0 : Sd[m].y * pow2_int_d(M[m].y - my);
+        sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+        sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+        sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+        sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+        if (m == t) {
+            const int l = warp * (TC_MB * 16) + m * 16 + g;
+            o[l] = mx == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(mx, (float)sx);
+            o[l + 8] = my == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(my, (float)sy);
+        }
+    }
+    atomicAdd(&s_pairs, (unsigned long long)icnt);
+    __syncthreads();
+    if (tid == 0) {
+        if (s_pairs) atomicAdd(pairs, s_pairs);
+        if (s_ab)
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % TC_STAGES], (unsigned)(it / TC_STAGES) & 1u);
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, TC_MINB)
+    k_grad_tcb(const Rec16 *__restrict__ trec, const float *__restrict__ bs,
+               const float4 *__restrict__ tball64, const float2 *__restrict__ tbe64,
+               const float *__restrict__ tbox512, const float *__restrict__ tb512,
+               const Rec16 *__restrict__ prec, const float *__restrict__ us,
+               const float *__restrict__ Aq, const float4 *__restrict__ pball8,
+               const float2 *__restrict__ pal8, const float *__restrict__ pbox1024,
+               const float *__restrict__ pa1024, int nstages, int k2, double *__restrict__ part2,
+               int *__restrict__ flags, const int *__restrict__ gate) {
+    if (*gate & 1) return;   // operands out of f16 range: the FP32 kernels run
+    extern __shared__ __align__(128) unsigned char bs_smem[];
+    constexpr size_t oU = TC_STAGES * TC_TS * sizeof(Rec16);
+    constexpr size_t oA = oU + TC_STAGES * TC_TS * sizeof(float);
+    constexpr size_t oBall = oA + TC_STAGES * TC_TS * sizeof(float);
+    constexpr size_t oAl = oBall + TC_STAGES * TC_NBS * sizeof(float4);
+    Rec16 (*s_rec)[TC_TS] = reinterpret_cast<Rec16 (*)[TC_TS]>(bs_smem);
+    float (*s_u)[TC_TS] = reinterpret_cast<float (*)[TC_TS]>(bs_smem + oU);
+    float (*s_A)[TC_TS] = reinterpret_cast<float (*)[TC_TS]>(bs_smem + oA);
+    float4 (*s_ball)[TC_NBS] = reinterpret_cast<float4 (*)[TC_NBS]>(bs_smem + oBall);
+    float2 (*s_al)[TC_NBS] = reinterpret_cast<float2 (*)[TC_NBS]>(bs_smem + oAl);
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
+    __shared__ int s_list[BS_CHUNK], s_cnt;
+    constexpr unsigned kStage = TC_TS * (sizeof(Rec16) + 2 * sizeof(float)) + TC_NBS * (sizeof(float4) + sizeof(float2));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    const int kc = blockIdx.y;
+    if (tid == 0) {
+        s_cnt = bs_list(tbox512 + (size_t)blockIdx.x * 6, tb512[blockIdx.x], pbox1024, pa1024,
+                        kc * BS_CHUNK, min(nstages, (kc + 1) * BS_CHUNK), s_list);
+        for (int st = 0; st < TC_STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], TC_WARPS);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+#define BS_ISSUE2(it_)                                                                               \
+    do {                                                                                             \
+        const int sl_ = (it_) % TC_STAGES;                                                           \
+        const int64_t q_ = (int64_t)s_list[it_] * TC_TS;                                             \
+        mbar_expect_tx(&full[sl_], kStage);                                                          \
+        bulk_g2s(s_rec[sl_], prec + q_, TC_TS * sizeof(Rec16), &full[sl_]);                          \
+        bulk_g2s(s_u[sl_], us + q_, TC_TS * sizeof(float), &full[sl_]);                              \
+        bulk_g2s(s_A[sl_], Aq + q_, TC_TS * sizeof(float), &full[sl_]);                              \
+        bulk_g2s(s_ball[sl_], pball8 + q_ / 8, TC_NBS * sizeof(float4), &full[sl_]);                 \
+        bulk_g2s(s_al[sl_], pal8 + q_ / 8, TC_NBS * sizeof(float2), &full[sl_]);                     \
+    } while (0)
+    if (tid == 0)
+        for (int it = 0; it < TC_STAGES && it < cnt; ++it) BS_ISSUE2(it);
+    int issued = min(TC_STAGES, cnt);
+    const int64_t j0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
+    const uint2 *tr = reinterpret_cast<const uint2 *>(trec);
+    unsigned A[TC_MB][4];
+    float2 bgg[TC_MB], bg8[TC_MB];   // (-b_g, -b_g), (-b_g+8, -b_g+8)
+    double2 acc64[TC_MB];
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        const int64_t jb = j0 + m * 16;
+        tc_load_a(A[m], tr + jb * 4, g, t);
+        const float b0 = bs[jb + g], b8 = bs[jb + g + 8];
+        bgg[m] = make_float2(-b0, -b0);
+        bg8[m] = make_float2(-b8, -b8);
+        acc64[m] = make_double2(0.0, 0.0);
+    }
+    // the warp's 64 rows are classified together against each n-block
+    const float4 wball = tball64[j0 / 64];
+    const float2 wbe = tbe64[j0 / 64];
+    bool aborted = false;
+    for (int it = 0; it < cnt; ++it) {
+        const int slot = it % TC_STAGES;
+        const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+            atomicOr(flags, kErrTimeout);
+            aborted = true;
+            break;
+        }
+        {
+            const uint2 *rec = reinterpret_cast<const uint2 *>(&s_rec[slot][0]) + lane;
+            const float2 *up = reinterpret_cast<const float2 *>(&s_u[slot][0]) + t;
+            const float2 *ap = reinterpret_cast<const float2 *>(&s_A[slot][0]) + t;
+            float2 acc[TC_MB];
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
+            unsigned cls = 0;   // 2 bits at 2 i: n-block lane + 32 i against the warp's 64 rows
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                cls |= (unsigned)tp_class(wball, s_ball[slot][lane + 32 * i], wbe, s_al[slot][lane + 32 * i]) << (2 * i);
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+                // two live n-blocks per step (mma of both before either epilogue)
+                for (unsigned live = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) != 0u); live;) {
+                    const int l0 = __ffs(live) - 1;
+                    live &= live - 1;
+                    const bool two = live != 0;
+                    const int l1 = two ? __ffs(live) - 1 : l0;
+                    if (two) live &= live - 1;
+                    const int nb0 = 32 * i + l0, nb1 = 32 * i + l1;
+                    const int c0 = (int)((__shfl_sync(0xffffffffu, cls, l0) >> (2 * i)) & 3u);
+                    const int c1 = two ? (int)((__shfl_sync(0xffffffffu, cls, l1) >> (2 * i)) & 3u) : 0;
+                    const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
+                    float d0[TC_MB][4], d1[TC_MB][4];
+#pragma unroll
+                    for (int m = 0; m < TC_MB; ++m) {
+                        mma_tc(d0[m], A[m], bf0);
+                        if (two) mma_tc(d1[m], A[m], bf1);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h && !two) break;
+                        const int nb = h ? nb1 : nb0;
+                        const int c = h ? c1 : c0;
+                        const float2 u = up[4 * nb];    // (u_2t, u_2t+1)
+                        const float2 Ac = ap[4 * nb];   // (A_2t, A_2t+1)
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) {
                             const float(&d)[4] = h ? d1[m] : d0[m];
                             float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
                             float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
@@ -1136,54 +1121,61 @@ __global__ void __launch_bounds__(TP_THREADS2)
                         }
                     }
                 }
+            }
 #pragma unroll
-                for (int m = 0; m < TC_MB; ++m) {
-                    acc64[m].x += (double)acc[m].x;
-                    acc64[m].y += (double)acc[m].y;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            if (warp == 0 && it + 2 < nst) {
-                bool ok = true;
-                if (tid == 0) {
-                    ok = mbar_wait(&empty[slot], ph);
-                    if (ok) TP_ISSUE(it + 2, slot);
-                }
-                if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                    s_abort[0] = 1;
-                    atomicOr(flags, kErrTimeout);
-                    wabort = true;
-                    break;
-                }
+            for (int m = 0; m < TC_MB; ++m) {
+                acc64[m].x += (double)acc[m].x;
+                acc64[m].y += (double)acc[m].y;
             }
         }
-        git += nst;
-if (!wabort) {
-#pragma unroll
-        for (int m = 0; m < TC_MB; ++m) {
-            double x = acc64[m].x, y = acc64[m].y;
-            x += __shfl_xor_sync(0xffffffffu, x, 1);
-            x += __shfl_xor_sync(0xffffffffu, x, 2);
-            y += __shfl_xor_sync(0xffffffffu, y, 1);
-            y += __shfl_xor_sync(0xffffffffu, y, 2);
-            if (m == t) {
-                const int l = warp * (TC_MB * 16) + m * 16 + g;
-                part2[(int64_t)item * TT + l] = x;
-                part2[(int64_t)item * TT + l + 8] = y;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (warp == 0 && it + TC_STAGES < cnt) {
+            bool ok = true;
+            if (tid == 0) {
+                ok = mbar_wait(&empty[slot], ph);
+                if (ok) {
+                    BS_ISSUE2(it + TC_STAGES);
+                    ++issued;
+                }
             }
-        }
-        }
-        __syncthreads();   // end of the item: every warp is past its stages
-        if (s_abort[0]) {
-            aborted = true;
-            break;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                atomicOr(flags, kErrTimeout);
+                aborted = true;
+                break;
+            }
         }
     }
-    if (aborted && tid == 0)
-        for (int st = 0; st < 2; ++st) (void)mbar_wait(&full[st], 0u), (void)mbar_wait(&full[st], 1u);
+#undef BS_ISSUE2
+    if (aborted) {
+        if (tid == 0)
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % TC_STAGES], (unsigned)(it / TC_STAGES) & 1u);
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < TC_MB; ++m) {
+        double x = acc64[m].x, y = acc64[m].y;
+        x += __shfl_xor_sync(0xffffffffu, x, 1);
+        x += __shfl_xor_sync(0xffffffffu, x, 2);
+        y += __shfl_xor_sync(0xffffffffu, y, 1);
+        y += __shfl_xor_sync(0xffffffffu, y, 2);
+        if (m == t) {
+            // target tile of TT: two per CTA; item = tile * k2 + chunk
+            const int l = warp * (TC_MB * 16) + m * 16 + g;   // < 512
+            const int64_t tile = (int64_t)blockIdx.x * 2 + l / TT;
+            double *o = part2 + (tile * k2 + kc) * TT + (l % TT);
+            o[0] = x;
+            o[8] = y;
+        }
+    }
 }
-#undef TP_ISSUE
+
+// off[i] = i * k for i <= rows: the item offsets of the block-skip layout
+__global__ void k_offsets_uniform(int *__restrict__ off, int rows, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= rows) off[i] = i * k;
+}
 
 // ------------------------------------------------------------------ combine
 // Merge the item partials of each point; write pass-2 point-pair records
@@ -1196,7 +1188,9 @@ __global__ void k_combine_trunc(const float2 *__restrict__ part1, const int *__r
                                 const double *__restrict__ psi, double eps, int d,
                                 Rec12 *__restrict__ ppair, double *__restrict__ lse_s,
                                 double *__restrict__ blockJ, EvalResult *__restrict__ res,
-                                float *__restrict__ u_s = nullptr) {
+                                float *__restrict__ u_s, const int *__restrict__ gate, int want) {
+    // gate: run only when its bit 0 (FP32 fallback) equals `want`
+    if (gate && (*gate & 1) != want) return;
     __shared__ double sh[32];
     __shared__ int s_empty;
     if (threadIdx.x == 0) s_empty = 0;
@@ -1361,7 +1355,9 @@ __global__ void __launch_bounds__(G_THREADS)
 
 __global__ void k_finalize_grad_trunc(const double *__restrict__ part2, const int *__restrict__ off2,
                                       int64_t n, const int *__restrict__ perm_t,
-                                      const double *__restrict__ nu_s, double *__restrict__ grad) {
+                                      const double *__restrict__ nu_s, double *__restrict__ grad,
+                                      const int *__restrict__ gate, int want) {
+    if (gate && (*gate & 1) != want) return;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int t = (int)(s / TT), l = (int)(s % TT);
@@ -1457,7 +1453,7 @@ static cudaError_t grid_build(rsot_problem *p) {
     for (int k = 0; k < 3; ++k) g->lo[k] = k < d ? lo[k] : 0.0;
 
     g->nqt = round_up(p->nq, PT);
-    g->nt = round_up(p->n, TT);
+    g->nt = round_up(p->n, TC_TS);   // whole stages of the block-skip passes
     g->ptiles = (int)(g->nqt / PT);
     g->ttiles = (int)(g->nt / TT);
     g->tw = (g->ttiles + 31) / 32;
@@ -1507,20 +1503,33 @@ static cudaError_t grid_build(rsot_problem *p) {
     ALLOC(g->part2, g->items2_max * TT);
     ALLOC(g->lse_s, g->nqt);
     ALLOC(g->blockJ, g->nblk_comb);
-    ALLOC(g->pball16, g->nqt / 16);
+    ALLOC(g->pball64, g->nqt / 64);
     ALLOC(g->pball8, g->nqt / 8);
-    ALLOC(g->tball16, g->nt / 16);
+    ALLOC(g->tball64, g->nt / 64);
     ALLOC(g->tball8, g->nt / 8);
     ALLOC(g->prec_s, g->nqt);
     ALLOC(g->trec_s, g->nt);
     ALLOC(g->b_s, g->nt);
     ALLOC(g->u_s, g->nqt);
     ALLOC(g->pal8, g->nqt / 8);
-    ALLOC(g->pal16, g->nqt / 16);
+    ALLOC(g->pal64, g->nqt / 64);
     ALLOC(g->ptmax, g->ptiles);
     ALLOC(g->tbe8, g->nt / 8);
-    ALLOC(g->tbe16, g->nt / 16);
+    ALLOC(g->tbe64, g->nt / 64);
     ALLOC(g->ttmax, g->ttiles);
+    ALLOC(g->m0_s, g->nqt);
+    g->k1b = (int)((g->nt / TC_TS + BS_CHUNK - 1) / BS_CHUNK);
+    g->k2b = (int)((g->nqt / TC_TS + BS_CHUNK - 1) / BS_CHUNK);
+    ALLOC(g->pbox512, g->nqt / TC_ROWS * 6);
+    ALLOC(g->tbox512, g->nt / TC_ROWS * 6);
+    ALLOC(g->tbox1024, g->nt / TC_TS * 6);
+    ALLOC(g->pa512, g->nqt / TC_ROWS);
+    ALLOC(g->tb512, g->nt / TC_ROWS);
+    ALLOC(g->tb1024, g->nt / TC_TS);
+    ALLOC(g->part1b, (int64_t)g->ptiles * g->k1b * PT);
+    ALLOC(g->part2b, (int64_t)g->ttiles * g->k2b * TT);
+    ALLOC(g->off1b, g->ptiles + 1);
+    ALLOC(g->off2b, g->ttiles + 1);
 #undef ALLOC
     k_gather_points<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(
         kq, p->nq, g->nqt, d, p->x64, p->mass, p->lmass2, g->perm_q, g->xs, g->x64, g->mass, g->lm2);
@@ -1528,9 +1537,23 @@ static cudaError_t grid_build(rsot_problem *p) {
         kt, p->n, g->nt, d, p->y64, p->nu, p->lnu, g->perm_t, g->y64, g->nu, g->lnu);
     k_tile_boxes<<<(g->ptiles + 127) / 128, 128, 0, st>>>(g->x64, p->nq, d, PT, g->ptiles, g->pbox);
     k_tile_boxes<<<(g->ttiles + 127) / 128, 128, 0, st>>>(g->y64, p->n, d, TT, g->ttiles, g->tbox);
-    k_block_balls<<<(unsigned)((g->nqt / 16 + 127) / 128), 128, 0, st>>>(g->x64, p->nq, d, 16, g->nqt / 16, g->pball16);
+    {
+        const int n512p = (int)(g->nqt / TC_ROWS), n512t = (int)(g->nt / TC_ROWS), n1024t = (int)(g->nt / TC_TS);
+        k_tile_boxes<<<(n512p + 127) / 128, 128, 0, st>>>(g->x64, p->nq, d, TC_ROWS, n512p, g->pbox512);
+        k_tile_boxes<<<(n512t + 127) / 128, 128, 0, st>>>(g->y64, p->n, d, TC_ROWS, n512t, g->tbox512);
+        k_tile_boxes<<<(n1024t + 127) / 128, 128, 0, st>>>(g->y64, p->n, d, TC_TS, n1024t, g->tbox1024);
+        k_offsets_uniform<<<(g->ptiles + 256) / 256, 256, 0, st>>>(g->off1b, g->ptiles, g->k1b);
+        k_offsets_uniform<<<(g->ttiles + 256) / 256, 256, 0, st>>>(g->off2b, g->ttiles, g->k2b);
+        if ((e = cudaFuncSetAttribute((const void *)k_lse_tcb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)BS_SMEM1)))
+            return e;
+        if ((e = cudaFuncSetAttribute((const void *)k_grad_tcb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)BS_SMEM2)))
+            return e;
+    }
+    k_block_balls<<<(unsigned)((g->nqt / 64 + 127) / 128), 128, 0, st>>>(g->x64, p->nq, d, 64, g->nqt / 64, g->pball64);
     k_block_balls<<<(unsigned)((g->nqt / 8 + 127) / 128), 128, 0, st>>>(g->x64, p->nq, d, 8, g->nqt / 8, g->pball8);
-    k_block_balls<<<(unsigned)((g->nt / 16 + 127) / 128), 128, 0, st>>>(g->y64, p->n, d, 16, g->nt / 16, g->tball16);
+    k_block_balls<<<(unsigned)((g->nt / 64 + 127) / 128), 128, 0, st>>>(g->y64, p->n, d, 64, g->nt / 64, g->tball64);
     k_block_balls<<<(unsigned)((g->nt / 8 + 127) / 128), 128, 0, st>>>(g->y64, p->n, d, 8, g->nt / 8, g->tball8);
     k_point_recs_s<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(g->xs, g->nqt, d, p->tc_P, g->prec_s);
     if ((e = cudaGetLastError())) return e;
@@ -1541,8 +1564,6 @@ static cudaError_t grid_build(rsot_problem *p) {
     const void *f2 = d == 3 ? (const void *)k_grad_trunc<3> : (const void *)k_grad_trunc<2>;
     g->slots1 = p->num_sms * occupancy_of(f1, L_THREADS);
     g->slots2 = p->num_sms * occupancy_of(f2, G_THREADS);
-    g->slots1_tc = p->num_sms * occupancy_of((const void *)k_lse_trunc_tc, TP_THREADS1);
-    g->slots2_tc = p->num_sms * occupancy_of((const void *)k_grad_trunc_tc, TP_THREADS2);
     return cudaSuccess;
 }
 
@@ -1555,16 +1576,22 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     auto nb_of = [](int64_t m) { return (unsigned)((m + 255) / 256); };
     trace_begin(p, "trunc_setup");
     k_trunc_A<<<nb_of(g->nqt), 256, 0, st>>>(g->xs, p->nq, g->nqt, D, (float)k, p->alpha, g->perm_q,
-                                             2.0 * k, g->Aq);
+                                             2.0 * k, psi, p->cut_anchored, g->Aq, g->m0_s);
     // cutoff ranges of blocks and tiles (sorted order)
     k_ranges8<<<nb_of(g->nqt / 8), 256, 0, st>>>(p->alpha, g->perm_q, p->nq, g->nqt / 8, g->pal8);
-    k_ranges_merge<<<nb_of(g->nqt / 16), 256, 0, st>>>(g->pal8, g->nqt / 8, 2, g->pal16, nullptr, g->nqt / 16);
-    k_ranges_merge<<<nb_of(g->ptiles), 256, 0, st>>>(g->pal16, g->nqt / 16, PT / 16, nullptr, g->ptmax,
+    k_ranges_merge<<<nb_of(g->nqt / 64), 256, 0, st>>>(g->pal8, g->nqt / 8, 8, g->pal64, nullptr, g->nqt / 64);
+    k_ranges_merge<<<nb_of(g->ptiles), 256, 0, st>>>(g->pal64, g->nqt / 64, PT / 64, nullptr, g->ptmax,
                                                     g->ptiles);
     k_ranges8<<<nb_of(g->nt / 8), 256, 0, st>>>(p->beta, g->perm_t, p->n, g->nt / 8, g->tbe8);
-    k_ranges_merge<<<nb_of(g->nt / 16), 256, 0, st>>>(g->tbe8, g->nt / 8, 2, g->tbe16, nullptr, g->nt / 16);
-    k_ranges_merge<<<nb_of(g->ttiles), 256, 0, st>>>(g->tbe16, g->nt / 16, TT / 16, nullptr, g->ttmax,
+    k_ranges_merge<<<nb_of(g->nt / 64), 256, 0, st>>>(g->tbe8, g->nt / 8, 8, g->tbe64, nullptr, g->nt / 64);
+    k_ranges_merge<<<nb_of(g->ttiles), 256, 0, st>>>(g->tbe64, g->nt / 64, TT / 64, nullptr, g->ttmax,
                                                     g->ttiles);
+    k_ranges_merge<<<nb_of(g->nqt / TC_ROWS), 256, 0, st>>>(g->pal64, g->nqt / 64, TC_ROWS / 64, nullptr,
+                                                           g->pa512, g->nqt / TC_ROWS);
+    k_ranges_merge<<<nb_of(g->nt / TC_ROWS), 256, 0, st>>>(g->tbe64, g->nt / 64, TC_ROWS / 64, nullptr,
+                                                          g->tb512, g->nt / TC_ROWS);
+    k_ranges_merge<<<nb_of(g->nt / TC_TS), 256, 0, st>>>(g->tbe64, g->nt / 64, TC_TS / 64, nullptr,
+                                                        g->tb1024, g->nt / TC_TS);
     cudaMemsetAsync(g->bits_tp, 0, (size_t)g->ttiles * g->pw * 4, st);
     cudaMemsetAsync(g->cnt2, 0, (size_t)g->ttiles * 4, st);
     k_tile_pairs<<<g->ptiles, 256, 0, st>>>(g->pbox, g->tbox, g->ptiles, g->ttiles, g->tw, g->pw,
@@ -1585,9 +1612,10 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     // narrowed by 1e-4 relative: the pairwise FP32 test's rounding is far below
     if (tc) {
         trace_begin(p, "lse_trunc_tc");
-        k_lse_trunc_tc<<<g->slots1_tc, TP_THREADS1, 0, st>>>(
-            g->prec_s, g->Aq, g->pball16, g->pal16, g->trec_s, g->b_s, g->tball8, g->tbe8, g->bits_pt,
-            g->tw, g->off1, g->ptiles, g->ch1, g->counters, g->part1, pairs, p->flags, gate);
+        k_lse_tcb<<<dim3((unsigned)(g->nqt / TC_ROWS), (unsigned)g->k1b), TC_THREADS, BS_SMEM1, st>>>(
+            g->prec_s, g->Aq, g->m0_s, g->pball64, g->pal64, g->pbox512, g->pa512, g->trec_s, g->b_s,
+            g->tball8, g->tbe8, g->tbox1024, g->tb1024, (int)(g->nt / TC_TS), g->k1b, g->part1b, pairs,
+            p->flags, gate);
         trace_end(p);
     }
     trace_begin(p, "lse_trunc_mixed");
@@ -1596,16 +1624,20 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
                                                     g->part1, pairs, p->flags, gate);
     trace_end(p);
     trace_begin(p, "combine_trunc_mixed");
+    if (tc)
+        k_combine_trunc<<<g->nblk_comb, 256, 0, st>>>(g->part1b, g->off1b, p->nq, g->nqt, g->xs, g->x64,
+                                                      g->mass, g->lm2, g->Aq, psi, eps, D, g->ppair,
+                                                      g->lse_s, g->blockJ, p->res_dev, g->u_s, gate, 0);
     k_combine_trunc<<<g->nblk_comb, 256, 0, st>>>(g->part1, g->off1, p->nq, g->nqt, g->xs, g->x64,
                                                   g->mass, g->lm2, g->Aq, psi, eps, D, g->ppair,
                                                   g->lse_s, g->blockJ, p->res_dev,
-                                                  tc ? g->u_s : nullptr);
+                                                  tc ? g->u_s : nullptr, gate, 1);
     trace_end(p);
     if (tc) {
         trace_begin(p, "grad_trunc_tc");
-        k_grad_trunc_tc<<<g->slots2_tc, TP_THREADS2, 0, st>>>(
-            g->prec_s, g->Aq, g->u_s, g->pball8, g->pal8, g->trec_s, g->b_s, g->tball16, g->tbe16,
-            g->bits_tp, g->pw, g->off2, g->ttiles, g->ch2, g->counters + 1, g->part2, p->flags, gate);
+        k_grad_tcb<<<dim3((unsigned)(g->nt / TC_ROWS), (unsigned)g->k2b), TC_THREADS, BS_SMEM2, st>>>(
+            g->trec_s, g->b_s, g->tball64, g->tbe64, g->tbox512, g->tb512, g->prec_s, g->u_s, g->Aq,
+            g->pball8, g->pal8, g->pbox, g->ptmax, (int)(g->nqt / TC_TS), g->k2b, g->part2b, p->flags, gate);
         trace_end(p);
     }
     trace_begin(p, "grad_trunc_mixed");
@@ -1614,8 +1646,11 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
                                                      p->flags, gate);
     trace_end(p);
     trace_begin(p, "finalize_trunc");
+    if (tc)
+        k_finalize_grad_trunc<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(g->part2b, g->off2b, p->n,
+                                                                              g->perm_t, g->nu, grad, gate, 0);
     k_finalize_grad_trunc<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(g->part2, g->off2, p->n,
-                                                                          g->perm_t, g->nu, grad);
+                                                                          g->perm_t, g->nu, grad, gate, 1);
     k_finalize_J_trunc<<<1, 256, 0, st>>>(g->blockJ, g->nblk_comb, p->psinu, nbp, psi, p->res_dev);
     trace_end(p);
     return cudaGetLastError();
@@ -1646,8 +1681,10 @@ void trunc_free(rsot_problem *p) {
     void *ptrs[] = {g->perm_q, g->perm_t, g->xs, g->x64, g->mass, g->lm2, g->y64, g->nu, g->lnu,
                     g->pbox, g->tbox, g->bits_pt, g->bits_tp, g->cnt1, g->cnt2, g->off1, g->off2,
                     g->counters, g->Aq, g->tdup, g->ppair, g->part1, g->part2, g->lse_s, g->blockJ,
-                    g->pball16, g->pball8, g->tball16, g->tball8, g->prec_s, g->trec_s, g->b_s,
-                    g->u_s, g->pal8, g->pal16, g->ptmax, g->tbe8, g->tbe16, g->ttmax};
+                    g->pball64, g->pball8, g->tball64, g->tball8, g->prec_s, g->trec_s, g->b_s,
+                    g->u_s, g->pal8, g->pal64, g->ptmax, g->tbe8, g->tbe64, g->ttmax, g->m0_s,
+                    g->pbox512, g->tbox512, g->tbox1024, g->pa512, g->tb512, g->tb1024, g->part1b,
+                    g->part2b, g->off1b, g->off2b};
     for (void *q : ptrs) cudaFree(q);
     delete g;
     p->grid = nullptr;
