@@ -15,6 +15,8 @@ Contents
   * ``nearest``        -- the nearest target of every point (brute force).
   * ``plan``           -- the plan density p_j(x_q | psi), Eq. final_plan_density.
   * ``point_lse``      -- the per-point log partition L_q of Eq. discretized_functional.
+  * ``integrated_D``   -- ln D(psi, C) = ln sum_q m_q / S_trunc(x_q) of Eq.
+                          truncation_cutoff_int.
   * ``covering_cost``  -- C_0 of App. B over the quadrature points.
   * ``softmax_refine`` -- Eq. softmax_refinement_formula.
   * ``truncation``     -- the cutoffs C_pw, C_int, C_geom (Sec. 4.1, App. B) and
@@ -59,6 +61,9 @@ def _load():
                                               ctypes.c_double, ctypes.c_int, dp]
         lib.oracle_point_lse.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
                                          dp, dp, ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_point_lse_cut.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
+                                             dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                             dp]
         lib.oracle_threads_used.argtypes = [ctypes.c_int]
         lib.oracle_transport_maps.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp,
                                               dp, dp, ctypes.c_double, ctypes.c_int, dp,
@@ -178,6 +183,30 @@ def point_lse(x, y, nu, psi, eps, threads=0):
     if rc != 0:
         raise ValueError("oracle_point_lse failed")
     return out
+
+
+def integrated_D(x, mass, y, nu, psi, eps, cutoff=math.inf, threads=0):
+    """ln D(psi, C) with D = sum_q m_q / S_trunc(x_q, psi; C), the discrete
+    integral of the inverse truncated sum (Sec. 4.1, Eq. truncation_cutoff_int);
+    +inf when some point with m_q > 0 has an empty I_q."""
+    lib = _load()
+    x, xp = _f64(x)
+    y, yp = _f64(y)
+    nu, nup = _f64(nu)
+    psi, pp = _f64(psi)
+    L = np.empty(x.shape[0])
+    rc = lib.oracle_point_lse_cut(x.shape[1], x.shape[0], xp, y.shape[0], yp, nup, pp, float(eps),
+                                  float(cutoff), int(threads),
+                                  L.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("oracle_point_lse_cut failed")
+    mass = np.asarray(mass, dtype=np.float64)
+    keep = mass > 0
+    if np.any(~np.isfinite(L[keep])):
+        return math.inf
+    v = np.log(mass[keep]) - L[keep]
+    vmax = float(np.max(v))
+    return vmax + math.log(float(np.sum(np.exp(v - vmax))))
 
 
 def covering_cost(x, y, threads=0):

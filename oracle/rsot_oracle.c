@@ -263,8 +263,11 @@ int oracle_plan(int d, int64_t nq, const double *x, int64_t n, const double *y,
  * (and whose exponential is the denominator of Eq. final_plan_density),
  * max-shifted.  Dense only.
  */
-int oracle_point_lse(int d, int64_t nq, const double *x, int64_t n, const double *y,
-                     const double *nu, const double *psi, double eps, int threads, double *L)
+/* L_q = ln S_trunc(x_q) = ln sum_{j : c(x_q, y_j) < cutoff} nu_j exp((psi_j - c)/eps)
+ * (-inf for an empty I_q; cutoff = +inf: every j). */
+int oracle_point_lse_cut(int d, int64_t nq, const double *x, int64_t n, const double *y,
+                         const double *nu, const double *psi, double eps, double cutoff,
+                         int threads, double *L)
 {
     if (d < 1 || d > 3 || n < 1 || !(eps > 0.0))
         return -1;
@@ -275,16 +278,32 @@ int oracle_point_lse(int d, int64_t nq, const double *x, int64_t n, const double
     for (int64_t q = 0; q < nq; ++q) {
         double smax = -INFINITY;
         for (int64_t j = 0; j < n; ++j) {
-            double s = (psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]);
+            double c = cost(d, x + q * d, y + j * d);
+            if (!(c < cutoff))
+                continue;
+            double s = (psi[j] - c) / eps + log(nu[j]);
             if (s > smax)
                 smax = s;
         }
+        if (smax == -INFINITY) {
+            L[q] = -INFINITY;
+            continue;
+        }
         nsum_t S = {0.0, 0.0};
-        for (int64_t j = 0; j < n; ++j)
-            nadd(&S, exp((psi[j] - cost(d, x + q * d, y + j * d)) / eps + log(nu[j]) - smax));
+        for (int64_t j = 0; j < n; ++j) {
+            double c = cost(d, x + q * d, y + j * d);
+            if (c < cutoff)
+                nadd(&S, exp((psi[j] - c) / eps + log(nu[j]) - smax));
+        }
         L[q] = smax + log(nval(&S));
     }
     return 0;
+}
+
+int oracle_point_lse(int d, int64_t nq, const double *x, int64_t n, const double *y,
+                     const double *nu, const double *psi, double eps, int threads, double *L)
+{
+    return oracle_point_lse_cut(d, nq, x, n, y, nu, psi, eps, INFINITY, threads, L);
 }
 
 /* Covering cost C_0 = max_q min_j c(x_q, y_j) over the quadrature points

@@ -287,3 +287,28 @@ def test_wrong_separable_cutoffs_break_the_tail_guarantee(wrong, monkeypatch):
         except AssertionError:
             caught = True
     assert caught
+
+
+# ---- integrated cutoff (Sec. 4.1, Eq. truncation_cutoff_int) ---------------------
+@pytest.mark.parametrize("wrong", ["mass_not_applied", "log_partition_not_negated", "cutoff_ignored"])
+def test_wrong_integrated_D_is_caught(wrong, monkeypatch):
+    import test_oracle_integral as T
+    good = oracle.integrated_D
+
+    def bad(x, mass, y, nu, psi, eps, cutoff=math.inf, threads=0):
+        if wrong == "cutoff_ignored":
+            return good(x, mass, y, nu, psi, eps)
+        lnD = good(x, mass, y, nu, psi, eps, cutoff)
+        if wrong == "mass_not_applied":
+            return lnD + math.log(len(mass)) + 0.0 * lnD
+        m = np.asarray(mass)
+        return -lnD + 2.0 * math.log(float(m.sum()))
+    monkeypatch.setattr(oracle, "integrated_D", bad)
+    caught = False
+    for c in (T.test_single_target_closed_form, T.test_definition_by_brute_force,
+              T.test_D_decreases_with_the_cutoff):
+        try:
+            c()
+        except AssertionError:
+            caught = True
+    assert caught
