@@ -163,6 +163,17 @@ rsot_status rsot_eval_dual_grad_tail(rsot_problem *p, const double *psi, double 
 rsot_status rsot_point_log_partition(rsot_problem *p, double *L_out);
 
 /*
+ * ln D of the last successful evaluation, D = sum_q m_q / S_trunc(x_q) with
+ * S_trunc(x_q) = exp(L_q) its (dense or truncated) per-point sum: the integrated
+ * quantity of the integral cutoff (Sec. 4.1, Eq. truncation_cutoff_int)
+ *   C_int = max_j psi_j + eps ln(eps D / (tau |J|)),
+ * which keeps |J - J_trunc| <= tau |J| when D is taken at that cutoff (App. B).
+ * +inf when a point with m_q > 0 had no target within the cutoff.
+ * Errors: RSOT_ERR_ARG when no evaluation has succeeded on this handle.
+ */
+rsot_status rsot_log_integrated_D(rsot_problem *p, double *lnD_out);
+
+/*
  * Covering cost C_0 = max_q min_j c(x_q, y_j) over the quadrature points
  * (App. B).  Depends on geometry only; computed once and cached.
  */
@@ -259,6 +270,10 @@ typedef struct {
                             RSOT_COMPENSATED_GRAD_REL sum m_q, which certifies
                             ||grad J||_1 <= tol_l1; it is used while that bound is
                             at most 0.8 tol_l1, else FP64.  RSOT_FP64: always FP64 */
+    double tau_int;      /* > 0 (with tail = 0): truncate each evaluation at the
+                            integral cutoff C_int of this relative J tolerance,
+                            D and J from the previous evaluation of the stage
+                            (Sec. 4.1); the first evaluation of a stage is dense */
 } rsot_options;
 
 /* Fill *o with the defaults (eps 1e-2, no schedule, dense, tol 1e-6, MIXED with

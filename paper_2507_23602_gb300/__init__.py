@@ -47,7 +47,8 @@ class _Options(ctypes.Structure):
                 ("tol_l1", ctypes.c_double), ("stage_tol_l1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
                 ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("mixed_tol_l1", ctypes.c_double), ("refine_precision", ctypes.c_int)]
+                ("mixed_tol_l1", ctypes.c_double), ("refine_precision", ctypes.c_int),
+                ("tau_int", ctypes.c_double)]
 
 
 class _Desc(ctypes.Structure):
@@ -111,12 +112,13 @@ class SolveOptions:
     verbose: bool = False
     mixed_tol_l1: float = 1e-5
     refine_precision: int = COMPENSATED
+    tau_int: float = 0.0
 
     def _c(self):
         return _Options(self.eps, self.eps_start, self.eps_factor, self.tail, self.tol_l1,
                         self.stage_tol_l1, int(self.precision), int(bool(self.refine_fp64)),
                         int(self.lbfgs_m), int(self.max_iter), int(bool(self.verbose)),
-                        float(self.mixed_tol_l1), int(self.refine_precision))
+                        float(self.mixed_tol_l1), int(self.refine_precision), float(self.tau_int))
 
 
 @dataclasses.dataclass
@@ -157,6 +159,7 @@ def load():
                                         dp, vp, i64p]
     lib.rsot_eval_dual_grad_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         dp, vp, i64p]
+    lib.rsot_log_integrated_D.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.rsot_covering_cost.argtypes = [vp, dp]
     lib.rsot_point_log_partition.argtypes = [vp, vp]
     lib.rsot_radius_for_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, dp]
@@ -320,6 +323,12 @@ class Problem:
         if st != 0:
             raise RsotError(st, "eval_dual_grad_tail")
         return J.value, grad_out, pairs.value
+
+    def log_integrated_D(self):
+        """ln D = ln sum_q m_q / S_trunc(x_q) of the last evaluation (Sec. 4.1)."""
+        v = ctypes.c_double()
+        _check(self._lib.rsot_log_integrated_D(self._h, ctypes.byref(v)), "log_integrated_D")
+        return v.value
 
     def point_log_partition(self, out=None):
         """L_q of the last evaluation (numpy unless `out` is given)."""

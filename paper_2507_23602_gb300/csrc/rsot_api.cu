@@ -344,6 +344,21 @@ rsot_status rsot_eval_dual_grad_tail(rsot_problem *p, const double *psi, double 
     return eval_impl(p, psi, eps, 2, tail, prec, J_out, grad_out, pairs_out);
 }
 
+rsot_status rsot_log_integrated_D(rsot_problem *p, double *lnD_out) {
+    if (!p || !lnD_out || p->last_kind < 0) return RSOT_ERR_ARG;
+    double *L = nullptr;
+    cudaError_t e = cudaMallocAsync(&L, (size_t)p->nq * sizeof(double), p->stream);
+    if (!e) e = (p->last_kind == 3) ? trunc_point_L(p, L) : launch_point_L(p, L);
+    if (!e) e = launch_log_D(p, L, lnD_out);
+    if (L) cudaFreeAsync(L, p->stream);
+    if (!e) e = cudaStreamSynchronize(p->stream);
+    if (e) {
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    return RSOT_OK;
+}
+
 rsot_status rsot_kernel_timing(rsot_problem *p, int enable) {
     if (!p) return RSOT_ERR_ARG;
     p->timing = enable ? 1 : 0;

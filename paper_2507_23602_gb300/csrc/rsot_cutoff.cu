@@ -172,6 +172,66 @@ cudaError_t cutoffs_separable(rsot_problem *p, const double *psi, double eps, do
     return cudaGetLastError();
 }
 
+// ln D with D = sum_q m_q exp(-L_q) (Sec. 4.1, Eq. truncation_cutoff_int):
+// per-block (max, scaled sum) of v_q = ln m_q - L_q over points with m_q > 0;
+// an empty point (L_q = -inf) with mass gives +inf
+__global__ void k_log_D(const double *__restrict__ L, const double *__restrict__ mass, int64_t nq,
+                        double2 *__restrict__ part) {
+    __shared__ double smax[256], ssum[256];
+    double mx = -INFINITY, sm = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (!(mass[q] > 0.0)) continue;
+        const double v = log(mass[q]) - L[q];
+        if (v > mx) {
+            sm = (mx == -INFINITY ? 0.0 : sm * exp(mx - v)) + 1.0;
+            mx = v;
+        } else {
+            sm += exp(v - mx);
+        }
+    }
+    smax[threadIdx.x] = mx;
+    ssum[threadIdx.x] = sm;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double a = smax[threadIdx.x], b = smax[threadIdx.x + o];
+            const double m2 = fmax(a, b);
+            double s2 = 0.0;
+            if (a != -INFINITY) s2 += ssum[threadIdx.x] * (a == INFINITY ? 1.0 : exp(a - m2));
+            if (b != -INFINITY) s2 += ssum[threadIdx.x + o] * (b == INFINITY ? 1.0 : exp(b - m2));
+            smax[threadIdx.x] = m2;
+            ssum[threadIdx.x] = s2;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(smax[0], ssum[0]);
+}
+
+cudaError_t launch_log_D(rsot_problem *p, const double *L_dev, double *lnD) {
+    constexpr int NB = 120;
+    double2 *part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, NB * sizeof(double2), p->stream);
+    if (e) return e;
+    k_log_D<<<NB, 256, 0, p->stream>>>(L_dev, p->mass, p->nq, part);
+    double2 h[NB];
+    e = cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, p->stream);
+    cudaFreeAsync(part, p->stream);
+    if (!e) e = cudaStreamSynchronize(p->stream);
+    if (e) return e;
+    double mx = -INFINITY;
+    for (int i = 0; i < NB; ++i) mx = fmax(mx, h[i].x);
+    if (!isfinite(mx)) {
+        *lnD = mx;
+        return cudaSuccess;
+    }
+    double s = 0.0;
+    for (int i = 0; i < NB; ++i)
+        if (h[i].x != -INFINITY) s += h[i].y * exp(h[i].x - mx);
+    *lnD = mx + log(s);
+    return cudaSuccess;
+}
+
 void cutoff_free(rsot_problem *p) {
     cudaFree(p->nn);
     cudaFree(p->nn_c);

@@ -196,6 +196,8 @@ cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double
 cudaError_t cutoffs_uniform(rsot_problem *p, double C);
 cudaError_t cutoffs_separable(rsot_problem *p, const double *psi_dev, double eps, double tail);
 void cutoff_free(rsot_problem *p);
+// ln sum_q m_q exp(-L_q) from natural per-point log partitions on the device
+cudaError_t launch_log_D(rsot_problem *p, const double *L_dev, double *lnD);
 
 // ---- compensated path (rsot_df.cu): dense, or truncated by p->alpha / p->beta
 cudaError_t launch_compensated(rsot_problem *p, const double *psi_dev, double eps, bool trunc,

@@ -58,16 +58,41 @@ struct Evaluator {
     double eps;
     double tail;
     rsot_precision prec;
+    double tau_int = 0.0;
     int evals = 0;
     int64_t pairs = 0;
     rsot_status last = RSOT_OK;
+    bool have_prev = false;   // integral cutoff: ln D and J of the previous evaluation
+    double lnD_prev = 0.0, J_prev = 0.0;
 
     rsot_status operator()(const std::vector<double> &psi, double &J, std::vector<double> &g) {
-        // tail > 0: the psi-aware cutoffs of that tail tolerance (Sec. 4.1, App. B)
         int64_t pr = 0;
-        rsot_status s = tail > 0.0
-                            ? rsot_eval_dual_grad_tail(p, psi.data(), eps, tail, prec, &J, g.data(), &pr)
-                            : rsot_eval_dual_grad(p, psi.data(), eps, 0.0, prec, &J, g.data(), &pr);
+        rsot_status s;
+        if (tail > 0.0) {
+            // the psi-aware cutoffs of that tail tolerance (Sec. 4.1, App. B)
+            s = rsot_eval_dual_grad_tail(p, psi.data(), eps, tail, prec, &J, g.data(), &pr);
+        } else {
+            double radius = 0.0;   // dense
+            if (tau_int > 0.0 && have_prev) {
+                // C_int = M + eps ln(eps D / (tau |J|)) (Eq. truncation_cutoff_int) with D
+                // and J of the previous evaluation, kept above the covering cost so that
+                // every point keeps its nearest target
+                double M = -INFINITY;
+                for (double v : psi) M = std::max(M, v);
+                double C0 = 0.0;
+                if ((s = rsot_covering_cost(p, &C0))) return last = s;
+                double C = M + eps * (log(eps) + lnD_prev - log(tau_int) - log(fabs(J_prev)));
+                if (isfinite(C)) radius = sqrt(2.0 * std::max(C, C0 * (1.0 + 1e-5) + 1e-12));
+            }
+            s = rsot_eval_dual_grad(p, psi.data(), eps, radius, prec, &J, g.data(), &pr);
+            if (!s && tau_int > 0.0) {
+                double lnD = INFINITY;
+                if ((s = rsot_log_integrated_D(p, &lnD))) return last = s;
+                lnD_prev = lnD;
+                J_prev = J;
+                have_prev = J != 0.0;
+            }
+        }
         ++evals;
         pairs += pr;
         return last = s;
@@ -164,6 +189,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         return RSOT_ERR_ARG;
     if (opt->refine_precision != RSOT_FP64 && opt->refine_precision != RSOT_COMPENSATED)
         return RSOT_ERR_ARG;
+    if (opt->tau_int < 0.0 || (opt->tau_int > 0.0 && opt->tail > 0.0)) return RSOT_ERR_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t n = rsot::num_targets(p);
     std::vector<double> nu(n);
@@ -202,7 +228,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         const rsot_precision prec = (opt->precision == RSOT_COMPENSATED && last && !comp_ref)
                                         ? RSOT_FP64
                                         : (rsot_precision)opt->precision;
-        Evaluator ev{p, n, eps, opt->tail, prec};
+        Evaluator ev{p, n, eps, opt->tail, prec, opt->tau_int};
         rsot::LbfgsMachine mc;
         double tol_run = tol;
         if (last && opt->precision == RSOT_MIXED && opt->refine_fp64)
@@ -229,8 +255,8 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             // in kCorrStallWindow iterations); then L-BFGS on compensated
             // evaluations finishes from there (the D-scaled first step is
             // Newton-like near the optimum: a few iterations)
-            Evaluator evc{p, n, eps, opt->tail, RSOT_COMPENSATED};
-            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
+            Evaluator evc{p, n, eps, opt->tail, RSOT_COMPENSATED, opt->tau_int};
+            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
             const int kernel_before = rsot::pair_kernel_of(p);
             rsot_set_pair_kernel(p, RSOT_PAIRS_FP32);
             double fc = 0.0, fm = 0.0;
@@ -267,8 +293,8 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         } else if (refine && refine_ok) {
             // corrected refinement: one reference and one mixed evaluation per
             // correction, mixed L-BFGS on the corrected objective in between
-            Evaluator ev64{p, n, eps, opt->tail, ref_prec};
-            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED};
+            Evaluator ev64{p, n, eps, opt->tail, ref_prec, opt->tau_int};
+            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
             // the refinement works below the random rounding noise of the
             // tensor-core exponents (rms ~2e-5 per pair, several 1e-6 in the L1
             // norm of a large gradient): its mixed evaluations take the FP32
