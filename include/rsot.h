@@ -254,7 +254,8 @@ typedef struct {
                             cutoffs of this tail (rsot_eval_dual_grad_tail);
                             0: dense                                               */
     double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
-    double stage_tol_l1; /* tolerance of the intermediate stages (<=0: tol_l1)      */
+    double stage_tol_l1; /* tolerance of the intermediate stages (<=0: 100 tol_l1:
+                            they only warm-start the next stage)                 */
     int precision;       /* rsot_precision of the evaluations                       */
     int refine_fp64;     /* MIXED only: finish the last stage with FP64-corrected
                             refinement (see rsot_solve)                            */

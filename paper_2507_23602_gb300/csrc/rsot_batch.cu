@@ -20,6 +20,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <chrono>
 #include <vector>
@@ -85,6 +87,7 @@ namespace rsot {
 namespace {
 
 constexpr int B_T = 256;   // threads of the per-target / per-point kernels
+constexpr int kRefineThreads = 8;   // host threads of the per-problem refinement
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -1117,7 +1120,8 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
     const int P = b->count;
     const int m = opt->lbfgs_m > 0 ? opt->lbfgs_m : 10;
     const int max_iter = opt->max_iter > 0 ? opt->max_iter : 10000;
-    const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : opt->tol_l1;
+    // intermediate eps stages only warm-start the next one: 100 tol_l1 unless given
+    const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : rsot::kStageTolFactor * opt->tol_l1;
     // with FP64 refinement the batched mixed phase stops above the FP32 floor
     const double final_tol = (opt->precision == RSOT_MIXED && opt->refine_fp64)
                                  ? std::max(opt->tol_l1, opt->mixed_tol_l1 > 0.0 ? opt->mixed_tol_l1 : 1e-5)
@@ -1202,19 +1206,45 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
         }
         t_mixed = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (opt->refine_fp64) {
-            // corrected refinement through each problem's own handle, from the mixed solution
-            for (int p = 0; p < P; ++p) {
-                if (!(st[p] == RSOT_OK || st[p] == RSOT_ERR_LINESEARCH ||
-                      st[p] == RSOT_ERR_NOT_CONVERGED))
-                    continue;
-                rsot_options o = *opt;
-                o.eps = eps[p];
-                o.eps_start = 0.0;   // FP64-corrected refinement of the batched result
-                rsot_solve_stats ss;
-                const BProb &Q = b->hp[p];
-                st[p] = rsot_solve(b->handles[p], psi_all + Q.psi_off, &o, &ss);
-                gl1[p] = ss.grad_l1;
-                evals += ss.evals;
+            // refinement (rsot_solve) of each problem through its own handle, from the
+            // mixed solution: host threads take the problems largest first, each on
+            // its own stream, so that the GPU runs several small problems at once
+            std::vector<int> order;
+            for (int p = 0; p < P; ++p)
+                if (st[p] == RSOT_OK || st[p] == RSOT_ERR_LINESEARCH || st[p] == RSOT_ERR_NOT_CONVERGED)
+                    order.push_back(p);
+            std::sort(order.begin(), order.end(), [&](int a, int c) {
+                return b->hp[a].nq * b->hp[a].n > b->hp[c].nq * b->hp[c].n;
+            });
+            const int nw = std::max(1, std::min<int>(kRefineThreads, (int)order.size()));
+            std::vector<cudaStream_t> streams(nw, nullptr);
+            for (int w = 0; w < nw; ++w)
+                if (cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess)
+                    streams[w] = nullptr;
+            std::atomic<int> next{0};
+            std::vector<int64_t> wevals(nw, 0);
+            auto worker = [&](int w) {
+                for (int i = next++; i < (int)order.size(); i = next++) {
+                    const int p = order[i];
+                    rsot_set_stream(b->handles[p], streams[w]);
+                    rsot_options o = *opt;
+                    o.eps = eps[p];
+                    o.eps_start = 0.0;   // refinement of the batched result at the final eps
+                    rsot_solve_stats ss;
+                    const BProb &Q = b->hp[p];
+                    st[p] = rsot_solve(b->handles[p], psi_all + Q.psi_off, &o, &ss);
+                    gl1[p] = ss.grad_l1;
+                    wevals[w] += ss.evals;
+                    rsot_set_stream(b->handles[p], nullptr);
+                }
+            };
+            std::vector<std::thread> pool;
+            for (int w = 1; w < nw; ++w) pool.emplace_back(worker, w);
+            worker(0);
+            for (auto &th : pool) th.join();
+            for (int w = 0; w < nw; ++w) {
+                evals += wevals[w];
+                if (streams[w]) cudaStreamDestroy(streams[w]);
             }
             t_ref = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - t_mixed;
         }

@@ -35,6 +35,10 @@ namespace rsot {
 // reference evaluations takes over)
 inline constexpr int kMixedStallWindow = 300;
 
+// default tolerance of intermediate eps stages, as a multiple of the final one
+// (their solutions only warm-start the next stage, Sec. 4.2)
+inline constexpr double kStageTolFactor = 100.0;
+
 class LbfgsMachine {
    public:
     enum State { kIdle, kNeedF0, kSearch, kDone };

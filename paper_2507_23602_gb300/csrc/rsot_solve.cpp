@@ -204,7 +204,8 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
 
     const int m = opt->lbfgs_m > 0 ? opt->lbfgs_m : 10;
     const int max_iter = opt->max_iter > 0 ? opt->max_iter : 10000;
-    const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : opt->tol_l1;
+    // intermediate eps stages only warm-start the next one: 100 tol_l1 unless given
+    const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : rsot::kStageTolFactor * opt->tol_l1;
     // reference evaluations of the final stop: compensated with its certified
     // bound subtracted from tol where the bound leaves room, else FP64
     const double comp_bound = RSOT_COMPENSATED_GRAD_REL * rsot::mass_sum(p);
