@@ -228,8 +228,8 @@ def solve_line(metric, value, unit, workload, extra, args, higher=False):
 
 
 def run_solve_workloads(args):
-    """Solve-time metrics (time to ||grad J||_1 <= tol): mixed (FP64-corrected)
-    against plain FP64, on the GPU."""
+    """Solve-time metrics (time to ||grad J||_1 <= tol): mixed with the
+    refinement on compensated evaluations against plain FP64, on the GPU."""
     import numpy as np
     import torch
     import rsot_inputs as ri

@@ -257,14 +257,13 @@ typedef struct {
     double stage_tol_l1; /* tolerance of the intermediate stages (<=0: 100 tol_l1:
                             they only warm-start the next stage)                 */
     int precision;       /* rsot_precision of the evaluations                       */
-    int refine_fp64;     /* MIXED only: finish the last stage with FP64-corrected
-                            refinement (see rsot_solve)                            */
+    int refine_fp64;     /* MIXED only: finish the last stage with the refinement on
+                            reference evaluations (refine_precision; rsot_solve) */
     int lbfgs_m;         /* L-BFGS memory (<= 0: 10)                                */
     int max_iter;        /* iteration cap per stage (<= 0: 10000)                   */
     int verbose;         /* print one line per run to stderr                        */
     double mixed_tol_l1; /* MIXED + refine_fp64: the mixed phase of the last stage
-                            stops here, FP64-corrected refinement takes over
-                            (<= 0: 1e-5)                                           */
+                            stops here, the refinement takes over (<= 0: 1e-5)   */
     int refine_precision;/* reference evaluations of the refinement (and of the last
                             stage when precision is RSOT_COMPENSATED):
                             RSOT_COMPENSATED (default) stops at ||g||_1 <= tol_l1 -
@@ -378,9 +377,10 @@ typedef struct {
  * eps-schedule of `opt` (eps_start/eps_factor; a problem whose final eps is
  * above eps_start runs only its final stage), tol_l1, lbfgs_m, max_iter.
  * opt->precision = RSOT_MIXED runs the batched mixed rounds and then, with
- * refine_fp64, finishes each problem with FP64 evaluations through its own
- * problem handle; RSOT_FP64 solves each problem in turn with FP64 evaluations
- * (no batching).  psi_all: host, concatenated warm start in / solution out.
+ * refine_fp64, finishes each problem with the refinement of rsot_solve
+ * (reference evaluations of opt->refine_precision) through its own problem
+ * handle, problems spread over host threads with a stream each; RSOT_FP64
+ * solves each problem in turn with FP64 evaluations (no batching).  psi_all: host, concatenated warm start in / solution out.
  * status_out (nullable): count ints; grad_l1_out (nullable): count doubles.
  */
 rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,

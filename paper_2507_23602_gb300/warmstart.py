@@ -91,8 +91,8 @@ def predict(net: MLP, theta, y, nu) -> np.ndarray:
 
 def evaluate(net: MLP, seeds: Sequence[int], mesh_n=64, n_targets=4096, eps=5e-3, tol_l1=1e-6,
              chunk=128, eps_start=0.1) -> Dict[str, float]:
-    """Solve the held-out problems twice with the batched solver and FP64-corrected
-    refinement to tol_l1: from psi = 0 with the eps-schedule (the fallback and
+    """Solve the held-out problems twice with the batched solver and its
+    refinement (compensated reference evaluations) to tol_l1: from psi = 0 with the eps-schedule (the fallback and
     judge), and from the network's psi directly at eps.  Returns totals."""
     res = {"plain_seconds": 0.0, "warm_seconds": 0.0, "plain_rounds": 0, "warm_rounds": 0,
            "plain_evals": 0, "warm_evals": 0, "plain_converged": 0, "warm_converged": 0,
