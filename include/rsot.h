@@ -250,9 +250,11 @@ typedef struct {
     double eps;          /* final regularisation, > 0                              */
     double eps_start;    /* first stage of the eps-schedule; <= eps: no schedule   */
     double eps_factor;   /* stage ratio in (0,1), e.g. 0.5; the last stage is eps  */
-    double tail;         /* > 0: truncate every evaluation with the psi-aware
-                            cutoffs of this tail (rsot_eval_dual_grad_tail);
-                            0: dense                                               */
+    double tail;         /* > 0: truncate the mixed (and FP64 / compensated stage)
+                            evaluations with the psi-aware cutoffs of this tail
+                            (rsot_eval_dual_grad_tail); the refinement's reference
+                            evaluations stay dense, so a refined stop holds for the
+                            untruncated J.  0: dense                           */
     double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
     double stage_tol_l1; /* tolerance of the intermediate stages (<=0: 100 tol_l1:
                             they only warm-start the next stage)                 */

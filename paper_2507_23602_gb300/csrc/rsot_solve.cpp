@@ -17,7 +17,9 @@
 //     replaces sufficient decrease.
 // With MIXED precision and refine_fp64, the last stage runs mixed evaluations
 // down to mixed_tol_l1 (default 1e-5, above the FP32 rounding floor of the
-// gradient), then refines on reference evaluations.  The reference is the
+// gradient), then refines on reference evaluations, always dense (the stop
+// holds for the untruncated J whatever truncation the mixed phase used; the
+// correction absorbs the difference).  The reference is the
 // compensated evaluation (rsot_df.cu), stopped at tol - B with B = 6.5e-7
 // sum m_q its certified gradient error, so that ||grad J||_1 <= tol holds.  At
 // about ten mixed evaluations per compensated one, one correction (as below)
@@ -256,7 +258,10 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             // in kCorrStallWindow iterations); then L-BFGS on compensated
             // evaluations finishes from there (the D-scaled first step is
             // Newton-like near the optimum: a few iterations)
-            Evaluator evc{p, n, eps, opt->tail, RSOT_COMPENSATED, opt->tau_int};
+            // reference evaluations are dense: the stop holds for the untruncated J
+            // (a truncated mixed phase differs by tail-level terms, which the
+            // correction absorbs)
+            Evaluator evc{p, n, eps, 0.0, RSOT_COMPENSATED, 0.0};
             Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
             const int kernel_before = rsot::pair_kernel_of(p);
             rsot_set_pair_kernel(p, RSOT_PAIRS_FP32);
@@ -294,7 +299,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         } else if (refine && refine_ok) {
             // corrected refinement: one reference and one mixed evaluation per
             // correction, mixed L-BFGS on the corrected objective in between
-            Evaluator ev64{p, n, eps, opt->tail, ref_prec, opt->tau_int};
+            Evaluator ev64{p, n, eps, 0.0, ref_prec, 0.0};   // dense reference, as above
             Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
             // the refinement works below the random rounding noise of the
             // tensor-core exponents (rms ~2e-5 per pair, several 1e-6 in the L1

@@ -72,3 +72,28 @@ def test_solve_reports_iteration_cap():
         assert st.status == 5 and st.iters == 3
     finally:
         P.close()
+
+
+def test_concurrent_solves_on_separate_handles_match_sequential():
+    """Handles are independent: solves of two problems from two host threads (as
+    the batched refinement runs them) give bitwise the results of sequential
+    solves."""
+    import threading
+    probs = [ri.make_problem(2, 16, 300, 0.01, src_seed=81 + k, src_k=2, tgt_seed=82 + k) for k in range(2)]
+    handles = [rs().Problem(q.x, q.mass, q.y, q.nu) for q in probs]
+    try:
+        seq = [h.solve(eps=q.eps, eps_start=0.1, tol_l1=1e-6)[0] for h, q in zip(handles, probs)]
+        out = [None, None]
+
+        def run(k):
+            out[k] = handles[k].solve(eps=probs[k].eps, eps_start=0.1, tol_l1=1e-6)[0]
+        ths = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for k in range(2):
+            assert np.array_equal(out[k], seq[k])
+    finally:
+        for h in handles:
+            h.close()
