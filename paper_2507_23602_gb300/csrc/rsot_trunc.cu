@@ -676,38 +676,61 @@ __device__ __forceinline__ int tp_class(float4 a, float4 b, float2 ra, float2 rb
     return 2;
 }
 
-// exponents of one block pair, shifted, with excluded pairs at -inf
-// (pass 1: rows = points with shifts ng / ng8 and tests against A of the row)
-__device__ __forceinline__ void tp_lse_pair(const unsigned (&a)[4], uint2 bf, int cls, float2 ng,
-                                            float2 ng8, float2 nbb, float Ag, float Ag8, float2 &e01,
-                                            float2 &e23, unsigned &cnt) {
+// The per-pair test of a boundary block, on the FMA pipe.  A pair is kept when
+// its test value v = r_qj - (b_j - 2k beta_j) exceeds A_q = k|x'_q|^2 - 2k alpha_q;
+// y = sat(v 2^64 - A_q 2^64) is one fused multiply-add of v with the exact
+// -A_q 2^64 (nAS).  y = 1 for v - A_q >= 2^-64, 0 for v <= A_q, and a fraction
+// only for 0 < v - A_q < 2^-64, which needs |v|, |A_q| < 2^-40 (the pair then
+// keeps that fraction of its weight).  The weights multiply the exponentials
+// (y ex2(e) in one fma), and both passes form v and A_q from the same FP32
+// operands, so they weigh every pair alike.
+constexpr float TP_S = 18446744073709551616.f;   // 2^64
+__device__ __forceinline__ float tp_incl(float v, float nAS) {
+    float y;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(v), "f"(TP_S), "f"(nAS));
+    return y;
+}
+
+// exponents and weights of one block pair (pass 1: rows = points with shifts
+// ng / ng8 and the scaled tests nAS / nAS8 of rows g / g + 8); y = 1 for the
+// pairs of an inside block (bnd false)
+__device__ __forceinline__ void tp_lse_pair(const unsigned (&a)[4], uint2 bf, bool bnd, float2 ng,
+                                            float2 ng8, float2 nbb, float nAS, float nAS8, float2 &e01,
+                                            float2 &e23, float2 &y01, float2 &y23) {
     float d[4];
     mma_tc(d, a, bf);
     e01 = __fadd2_rn(make_float2(d[0], d[1]), ng);
     e23 = __fadd2_rn(make_float2(d[2], d[3]), ng8);
-    if (cls == 2) {
+    y01 = y23 = make_float2(1.f, 1.f);
+    if (bnd) {
         const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), nbb);
         const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), nbb);
-        const bool i0 = v01.x > Ag, i1 = v01.y > Ag, i2 = v23.x > Ag8, i3 = v23.y > Ag8;
-        e01 = make_float2(i0 ? e01.x : -INFINITY, i1 ? e01.y : -INFINITY);
-        e23 = make_float2(i2 ? e23.x : -INFINITY, i3 ? e23.y : -INFINITY);
-        cnt += (unsigned)i0 + (unsigned)i1 + (unsigned)i2 + (unsigned)i3;
+        y01 = make_float2(tp_incl(v01.x, nAS), tp_incl(v01.y, nAS));
+        y23 = make_float2(tp_incl(v23.x, nAS8), tp_incl(v23.y, nAS8));
     }
 }
 
-// the epilogue of tp_lse_pair on a given mma result d
-__device__ __forceinline__ void tp_lse_epi(const float (&d)[4], int cls, float2 ng, float2 ng8,
-                                           float2 nbb, float Ag, float Ag8, float2 &e01,
-                                           float2 &e23, unsigned &cnt) {
-    e01 = __fadd2_rn(make_float2(d[0], d[1]), ng);
-    e23 = __fadd2_rn(make_float2(d[2], d[3]), ng8);
-    if (cls == 2) {
+// the pass-1 epilogue of one block pair on its mma result d: acc (rows g, g + 8)
+// += y ex2(d - M); cnt += the weights of a boundary block.  An excluded pair
+// whose exponential overflows gives inf * 0 = NaN, which the caller's check
+// sends to the exact redo.
+__device__ __forceinline__ void tp_lse_epi(const float (&d)[4], bool bnd, float2 ng, float2 ng8,
+                                           float2 nbb, float nAS, float nAS8, float2 &acc, float2 &cnt) {
+    const float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), ng);
+    const float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), ng8);
+    const float2 p0 = make_float2(ex2_approx(e01.x), ex2_approx(e23.x));
+    const float2 p1 = make_float2(ex2_approx(e01.y), ex2_approx(e23.y));
+    if (bnd) {
         const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), nbb);
         const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), nbb);
-        const bool i0 = v01.x > Ag, i1 = v01.y > Ag, i2 = v23.x > Ag8, i3 = v23.y > Ag8;
-        e01 = make_float2(i0 ? e01.x : -INFINITY, i1 ? e01.y : -INFINITY);
-        e23 = make_float2(i2 ? e23.x : -INFINITY, i3 ? e23.y : -INFINITY);
-        cnt += (unsigned)i0 + (unsigned)i1 + (unsigned)i2 + (unsigned)i3;
+        const float2 y0 = make_float2(tp_incl(v01.x, nAS), tp_incl(v23.x, nAS8));
+        const float2 y1 = make_float2(tp_incl(v01.y, nAS), tp_incl(v23.y, nAS8));
+        acc = __ffma2_rn(p0, y0, acc);
+        acc = __ffma2_rn(p1, y1, acc);
+        cnt = __fadd2_rn(cnt, __fadd2_rn(y0, y1));
+    } else {
+        acc = __fadd2_rn(acc, p0);
+        acc = __fadd2_rn(acc, p1);
     }
 }
 
@@ -807,7 +830,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     const int64_t q0 = (int64_t)blockIdx.x * TC_ROWS + warp * (TC_MB * 16);
     const uint2 *pr = reinterpret_cast<const uint2 *>(prec);
     unsigned A[TC_MB][4];
-    float Ag[TC_MB], Ag8[TC_MB];
+    float nAS[TC_MB], nAS8[TC_MB];   // -A_q 2^64 of rows g, g + 8 (tp_incl)
     float2 M[TC_MB], Sf[TC_MB];
     double2 Sd[TC_MB];
     unsigned rvs = 0;   // real rows of this lane (rows g, g + 8 of the 4 m-blocks; padding has A = +inf)
@@ -815,9 +838,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     for (int m = 0; m < TC_MB; ++m) {
         const int64_t qb = q0 + m * 16;
         tc_load_a(A[m], pr + qb * 4, g, t);
-        Ag[m] = Aq[qb + g];
-        Ag8[m] = Aq[qb + g + 8];
-        rvs += (unsigned)(Ag[m] < INFINITY) + (unsigned)(Ag8[m] < INFINITY);
+        const float ag = Aq[qb + g], ag8 = Aq[qb + g + 8];
+        nAS[m] = ag * -TP_S;
+        nAS8[m] = ag8 * -TP_S;
+        rvs += (unsigned)(ag < INFINITY) + (unsigned)(ag8 < INFINITY);
         M[m] = make_float2(M0[qb + g], M0[qb + g + 8]);
         Sf[m] = make_float2(0.f, 0.f);
         Sd[m] = make_double2(0.0, 0.0);
@@ -825,7 +849,8 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     // the warp's 64 rows are classified together against each n-block
     const float4 wball = pball64[q0 / 64];
     const float2 wal = pal64[q0 / 64];
-    unsigned icnt = 0;
+    unsigned icnt = 0;    // pairs of inside blocks
+    float2 cntf = make_float2(0.f, 0.f);   // weights of boundary-block pairs (<= 2^14 a lane)
     bool aborted = false;
     for (int it = 0; it < cnt; ++it) {
         const int slot = it % TC_STAGES;
@@ -843,94 +868,93 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 cls |= (unsigned)tp_class(wball, s_ball[slot][lane + 32 * i], wal, s_be[slot][lane + 32 * i]) << (2 * i);
-            unsigned lv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) lv[i] = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) != 0u);
 #pragma unroll 1
-            for (int grp = 0; grp < TC_NBS / TC_GROUP; ++grp) {
-                const int sh2 = 2 * (grp >> 2);
-                const unsigned gmask = (lv[grp >> 2] >> ((grp & 3) * 8)) & 0xffu;
-                if (!gmask) continue;
-                float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
-#pragma unroll
-                for (int m = 0; m < TC_MB; ++m) {
-                    acc[m] = make_float2(0.f, 0.f);
-                    ng[m] = make_float2(-M[m].x, -M[m].x);
-                    ng8[m] = make_float2(-M[m].y, -M[m].y);
-                }
-                for (unsigned gm = gmask; gm;) {
-                    const int nb0 = grp * TC_GROUP + __ffs(gm) - 1;
-                    gm &= gm - 1;
-                    const bool two = gm != 0;
-                    const int nb1 = two ? grp * TC_GROUP + __ffs(gm) - 1 : nb0;
-                    if (two) gm &= gm - 1;
-                    const int c0 = (int)((__shfl_sync(0xffffffffu, cls, nb0 & 31) >> sh2) & 3u);
-                    const int c1 = two ? (int)((__shfl_sync(0xffffffffu, cls, nb1 & 31) >> sh2) & 3u) : 0;
-                    const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
-                    float d0[TC_MB][4], d1[TC_MB][4];
+            for (int i = 0; i < 4; ++i) {
+                // n-blocks 32 i + l: live (class 1 or 2) and boundary (class 2) bit maps
+                const unsigned lvi = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) != 0u);
+                const unsigned bmi = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) == 2u);
+#pragma unroll 1
+                for (int gq = 0; gq < 32 / TC_GROUP; ++gq) {
+                    const int grp = i * (32 / TC_GROUP) + gq;
+                    const unsigned gmask = (lvi >> (gq * TC_GROUP)) & 0xffu;
+                    if (!gmask) continue;
+                    const unsigned bmask = (bmi >> (gq * TC_GROUP)) & 0xffu;
+                    float2 acc[TC_MB], ng[TC_MB], ng8[TC_MB];
 #pragma unroll
                     for (int m = 0; m < TC_MB; ++m) {
-                        mma_tc(d0[m], A[m], bf0);
-                        if (two) mma_tc(d1[m], A[m], bf1);
+                        acc[m] = make_float2(0.f, 0.f);
+                        ng[m] = make_float2(-M[m].x, -M[m].x);
+                        ng8[m] = make_float2(-M[m].y, -M[m].y);
                     }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (h && !two) break;
-                        const int c = h ? c1 : c0;
-                        const float2 bb = bp[4 * (h ? nb1 : nb0)];
-                        const float2 nbb = make_float2(-bb.x, -bb.y);
-                        if (c == 1) icnt += rvs * ((unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY));
+                    for (unsigned gm = gmask; gm;) {
+                        const int b0 = __ffs(gm) - 1;
+                        gm &= gm - 1;
+                        const bool two = gm != 0;
+                        const int b1 = two ? __ffs(gm) - 1 : b0;
+                        if (two) gm &= gm - 1;
+                        const int nb0 = grp * TC_GROUP + b0, nb1 = grp * TC_GROUP + b1;
+                        const bool x0 = (bmask >> b0) & 1u, x1 = (bmask >> b1) & 1u;
+                        const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
+                        float d0[TC_MB][4], d1[TC_MB][4];
 #pragma unroll
                         for (int m = 0; m < TC_MB; ++m) {
-                            float2 e01, e23;
-                            tp_lse_epi(h ? d1[m] : d0[m], c, ng[m], ng8[m], nbb, Ag[m], Ag8[m], e01, e23, icnt);
-                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                            mma_tc(d0[m], A[m], bf0);
+                            if (two) mma_tc(d1[m], A[m], bf1);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (h && !two) break;
+                            const bool bnd = h ? x1 : x0;
+                            const float2 bb = bp[4 * (h ? nb1 : nb0)];
+                            const float2 nbb = make_float2(-bb.x, -bb.y);
+                            if (!bnd) icnt += rvs * ((unsigned)(bb.x < INFINITY) + (unsigned)(bb.y < INFINITY));
+#pragma unroll
+                            for (int m = 0; m < TC_MB; ++m)
+                                tp_lse_epi(h ? d1[m] : d0[m], bnd, ng[m], ng8[m], nbb, nAS[m], nAS8[m], acc[m], cntf);
                         }
                     }
-                }
-                bool bad = false;
+                    bool bad = false;
 #pragma unroll
-                for (int m = 0; m < TC_MB; ++m)
-                    bad = bad || !(fmaxf(acc[m].x, acc[m].y) <= TC_BIG) ||
-                          (M[m].x == -INFINITY && acc[m].x != 0.f) || (M[m].y == -INFINITY && acc[m].y != 0.f);
-                if (__any_sync(0xffffffffu, bad)) {
-                    // exact redo of the group: maximum over the included pairs,
-                    // shifts raised, sums recomputed (pairs are not counted again)
+                    for (int m = 0; m < TC_MB; ++m)
+                        bad = bad || !(acc[m].x <= TC_BIG) || !(acc[m].y <= TC_BIG) ||
+                              (M[m].x == -INFINITY && acc[m].x != 0.f) || (M[m].y == -INFINITY && acc[m].y != 0.f);
+                    if (__any_sync(0xffffffffu, bad)) {
+                        // exact redo of the group: maximum over the kept pairs (weight > 0),
+                        // shifts raised, sums recomputed (pairs are not counted again)
 #pragma unroll
-                    for (int m = 0; m < TC_MB; ++m) {
-                        float mg = -INFINITY, mg8 = -INFINITY;
-                        unsigned dummy = 0;
-                        const float2 z = make_float2(0.f, 0.f);
-                        for (unsigned gm = gmask; gm; gm &= gm - 1) {
-                            const int nb = grp * TC_GROUP + __ffs(gm) - 1;
-                            const int c = (int)((__shfl_sync(0xffffffffu, cls, nb & 31) >> sh2) & 3u);
-                            const float2 bb = bp[4 * nb];
-                            float2 e01, e23;
-                            tp_lse_pair(A[m], rec[32 * nb], c, z, z, make_float2(-bb.x, -bb.y), Ag[m], Ag8[m],
-                                        e01, e23, dummy);
-                            mg = max3f(mg, e01.x, e01.y);
-                            mg8 = max3f(mg8, e23.x, e23.y);
+                        for (int m = 0; m < TC_MB; ++m) {
+                            float mg = -INFINITY, mg8 = -INFINITY;
+                            const float2 z = make_float2(0.f, 0.f);
+                            for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                                const int b = __ffs(gm) - 1, nb = grp * TC_GROUP + b;
+                                const float2 bb = bp[4 * nb];
+                                float2 e01, e23, y01, y23;
+                                tp_lse_pair(A[m], rec[32 * nb], (bmask >> b) & 1u, z, z, make_float2(-bb.x, -bb.y),
+                                            nAS[m], nAS8[m], e01, e23, y01, y23);
+                                mg = max3f(mg, y01.x > 0.f ? e01.x : -INFINITY, y01.y > 0.f ? e01.y : -INFINITY);
+                                mg8 = max3f(mg8, y23.x > 0.f ? e23.x : -INFINITY, y23.y > 0.f ? e23.y : -INFINITY);
+                            }
+                            if (mg > -INFINITY) tc_raise(M[m].x, mg, Sf[m].x, Sd[m].x);
+                            if (mg8 > -INFINITY) tc_raise(M[m].y, mg8, Sf[m].y, Sd[m].y);
+                            const float2 g1 = make_float2(-M[m].x, -M[m].x), g8 = make_float2(-M[m].y, -M[m].y);
+                            float2 a2 = make_float2(0.f, 0.f);
+                            for (unsigned gm = gmask; gm; gm &= gm - 1) {
+                                const int b = __ffs(gm) - 1, nb = grp * TC_GROUP + b;
+                                const float2 bb = bp[4 * nb];
+                                float2 e01, e23, y01, y23;
+                                tp_lse_pair(A[m], rec[32 * nb], (bmask >> b) & 1u, g1, g8, make_float2(-bb.x, -bb.y),
+                                            nAS[m], nAS8[m], e01, e23, y01, y23);
+                                a2.x += (y01.x > 0.f ? y01.x * ex2_approx(e01.x) : 0.f) +
+                                        (y01.y > 0.f ? y01.y * ex2_approx(e01.y) : 0.f);
+                                a2.y += (y23.x > 0.f ? y23.x * ex2_approx(e23.x) : 0.f) +
+                                        (y23.y > 0.f ? y23.y * ex2_approx(e23.y) : 0.f);
+                            }
+                            acc[m] = a2;
                         }
-                        if (mg > -INFINITY) tc_raise(M[m].x, mg, Sf[m].x, Sd[m].x);
-                        if (mg8 > -INFINITY) tc_raise(M[m].y, mg8, Sf[m].y, Sd[m].y);
-                        const float2 g1 = make_float2(-M[m].x, -M[m].x), g8 = make_float2(-M[m].y, -M[m].y);
-                        float2 a2 = make_float2(0.f, 0.f);
-                        for (unsigned gm = gmask; gm; gm &= gm - 1) {
-                            const int nb = grp * TC_GROUP + __ffs(gm) - 1;
-                            const int c = (int)((__shfl_sync(0xffffffffu, cls, nb & 31) >> sh2) & 3u);
-                            const float2 bb = bp[4 * nb];
-                            float2 e01, e23;
-                            tp_lse_pair(A[m], rec[32 * nb], c, g1, g8, make_float2(-bb.x, -bb.y), Ag[m], Ag8[m],
-                                        e01, e23, dummy);
-                            a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                            a2 = __fadd2_rn(a2, make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
-                        }
-                        acc[m] = a2;
                     }
-                }
 #pragma unroll
-                for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
+                    for (int m = 0; m < TC_MB; ++m) Sf[m] = __fadd2_rn(Sf[m], acc[m]);
+                }
             }
         }
         __syncwarp();
@@ -982,7 +1006,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
             o[l + 8] = my == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(my, (float)sy);
         }
     }
-    atomicAdd(&s_pairs, (unsigned long long)icnt);
+    atomicAdd(&s_pairs, (unsigned long long)icnt + (unsigned long long)__float2uint_rn(cntf.x + cntf.y));
     __syncthreads();
     if (tid == 0) {
         if (s_pairs) atomicAdd(pairs, s_pairs);
@@ -1081,6 +1105,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
                 cls |= (unsigned)tp_class(wball, s_ball[slot][lane + 32 * i], wbe, s_al[slot][lane + 32 * i]) << (2 * i);
 #pragma unroll 1
             for (int i = 0; i < 4; ++i) {
+                const unsigned bmi = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) == 2u);
                 // two live n-blocks per step (mma of both before either epilogue)
                 for (unsigned live = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) != 0u); live;) {
                     const int l0 = __ffs(live) - 1;
@@ -1089,8 +1114,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
                     const int l1 = two ? __ffs(live) - 1 : l0;
                     if (two) live &= live - 1;
                     const int nb0 = 32 * i + l0, nb1 = 32 * i + l1;
-                    const int c0 = (int)((__shfl_sync(0xffffffffu, cls, l0) >> (2 * i)) & 3u);
-                    const int c1 = two ? (int)((__shfl_sync(0xffffffffu, cls, l1) >> (2 * i)) & 3u) : 0;
+                    const bool x0 = (bmi >> l0) & 1u, x1 = (bmi >> l1) & 1u;
                     const uint2 bf0 = rec[32 * nb0], bf1 = rec[32 * nb1];
                     float d0[TC_MB][4], d1[TC_MB][4];
 #pragma unroll
@@ -1102,22 +1126,64 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
                     for (int h = 0; h < 2; ++h) {
                         if (h && !two) break;
                         const int nb = h ? nb1 : nb0;
-                        const int c = h ? c1 : c0;
-                        const float2 u = up[4 * nb];    // (u_2t, u_2t+1)
-                        const float2 Ac = ap[4 * nb];   // (A_2t, A_2t+1)
+                        const bool bnd = h ? x1 : x0;
+                        const float2 u = up[4 * nb];   // (u_2t, u_2t+1)
+                        float2 nAc = make_float2(0.f, 0.f);
+                        if (bnd) {
+                            const float2 Ac = ap[4 * nb];   // (A_2t, A_2t+1)
+                            nAc = make_float2(Ac.x * -TP_S, Ac.y * -TP_S);
+                        }
 #pragma unroll
                         for (int m = 0; m < TC_MB; ++m) {
                             const float(&d)[4] = h ? d1[m] : d0[m];
-                            float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
-                            float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
-                            if (c == 2) {
+                            const float2 e01 = __fadd2_rn(make_float2(d[0], d[1]), u);
+                            const float2 e23 = __fadd2_rn(make_float2(d[2], d[3]), u);
+                            const float2 p0 = make_float2(ex2_approx(e01.x), ex2_approx(e23.x));
+                            const float2 p1 = make_float2(ex2_approx(e01.y), ex2_approx(e23.y));
+                            if (bnd) {
                                 const float2 v01 = __fadd2_rn(make_float2(d[0], d[1]), bgg[m]);
                                 const float2 v23 = __fadd2_rn(make_float2(d[2], d[3]), bg8[m]);
-                                e01 = make_float2(v01.x > Ac.x ? e01.x : -INFINITY, v01.y > Ac.y ? e01.y : -INFINITY);
-                                e23 = make_float2(v23.x > Ac.x ? e23.x : -INFINITY, v23.y > Ac.y ? e23.y : -INFINITY);
+                                acc[m] = __ffma2_rn(p0, make_float2(tp_incl(v01.x, nAc.x), tp_incl(v23.x, nAc.x)), acc[m]);
+                                acc[m] = __ffma2_rn(p1, make_float2(tp_incl(v01.y, nAc.y), tp_incl(v23.y, nAc.y)), acc[m]);
+                            } else {
+                                acc[m] = __fadd2_rn(acc[m], p0);
+                                acc[m] = __fadd2_rn(acc[m], p1);
                             }
-                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.x), ex2_approx(e23.x)));
-                            acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(e01.y), ex2_approx(e23.y)));
+                        }
+                    }
+                }
+            }
+            bool bad = false;
+#pragma unroll
+            for (int m = 0; m < TC_MB; ++m) bad = bad || !(acc[m].x < INFINITY) || !(acc[m].y < INFINITY);
+            if (__any_sync(0xffffffffu, bad)) {
+                // an excluded pair whose exponential overflowed (inf * 0): the
+                // stage again, with the excluded pairs' exponentials dropped
+#pragma unroll
+                for (int m = 0; m < TC_MB; ++m) acc[m] = make_float2(0.f, 0.f);
+                for (int i = 0; i < 4; ++i) {
+                    const unsigned bmi = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) == 2u);
+                    for (unsigned live = __ballot_sync(0xffffffffu, ((cls >> (2 * i)) & 3u) != 0u); live;
+                         live &= live - 1) {
+                        const int l = __ffs(live) - 1, nb = 32 * i + l;
+                        const bool bnd = (bmi >> l) & 1u;
+                        const float2 u = up[4 * nb], Ac = ap[4 * nb];
+                        const float2 nAc = make_float2(Ac.x * -TP_S, Ac.y * -TP_S);
+#pragma unroll
+                        for (int m = 0; m < TC_MB; ++m) {
+                            float d[4];
+                            mma_tc(d, A[m], rec[32 * nb]);
+                            const float e[4] = {d[0] + u.x, d[1] + u.y, d[2] + u.x, d[3] + u.y};
+                            const float bg[4] = {bgg[m].x, bgg[m].x, bg8[m].x, bg8[m].x};
+                            const float na[4] = {nAc.x, nAc.y, nAc.x, nAc.y};
+                            float p[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const float y = bnd ? tp_incl(d[k] + bg[k], na[k]) : 1.f;
+                                p[k] = y > 0.f ? y * ex2_approx(e[k]) : 0.f;
+                            }
+                            acc[m].x += p[0] + p[1];
+                            acc[m].y += p[2] + p[3];
                         }
                     }
                 }
