@@ -662,16 +662,24 @@ __global__ void __launch_bounds__(L_THREADS, 3)
 // the ranges of the cutoffs of their members:
 // "outside" (every pair farther than the radius: skipped), "inside" (every
 // pair nearer: no test) or "boundary" (each pair tested, r_qj - b_j > A_q, in
-// FP32 on the mma result).  The classification margins (1e-4 R) exceed the
+// FP32 on the mma result, as the weight of tp_incl).  The classification margins (1e-4 R) exceed the
 // rounding of the pairwise test, so a classified pair gets the decision the
 // test would give and both passes sum over the same pairs.
+// square root on the SFU (sqrt.approx, relative error about 2^-23): far inside
+// the classification margins of 1e-4 relative
+__device__ __forceinline__ float sqrt_sfu(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ int tp_class(float4 a, float4 b, float2 ra, float2 rb) {
     if (a.w < 0.f || b.w < 0.f) return 0;
     const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    const float dist = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float Rout = sqrtf(fmaxf(0.f, 2.f * (ra.y + rb.y))) * (1.0f + 1e-4f) + 1e-6f;
+    const float dist = sqrt_sfu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float Rout = sqrt_sfu(fmaxf(0.f, 2.f * (ra.y + rb.y))) * (1.0f + 1e-4f) + 1e-6f;
     if (dist - a.w - b.w >= Rout) return 0;
-    const float Rin = sqrtf(fmaxf(0.f, 2.f * (ra.x + rb.x))) * (1.0f - 1e-4f) - 1e-6f;
+    const float Rin = sqrt_sfu(fmaxf(0.f, 2.f * (ra.x + rb.x))) * (1.0f - 1e-4f) - 1e-6f;
     if (dist + a.w + b.w < Rin) return 1;
     return 2;
 }
@@ -832,7 +840,9 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     unsigned A[TC_MB][4];
     float nAS[TC_MB], nAS8[TC_MB];   // -A_q 2^64 of rows g, g + 8 (tp_incl)
     float2 M[TC_MB], Sf[TC_MB];
-    double2 Sd[TC_MB];
+    // FP64 sums of the lane (added once per stage) in shared memory
+    __shared__ double2 s_Sd[TC_WARPS][32][TC_MB];
+    double2 (&Sd)[TC_MB] = s_Sd[warp][lane];
     unsigned rvs = 0;   // real rows of this lane (rows g, g + 8 of the 4 m-blocks; padding has A = +inf)
 #pragma unroll
     for (int m = 0; m < TC_MB; ++m) {
