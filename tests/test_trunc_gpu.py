@@ -179,3 +179,24 @@ def test_trunc_full_size_against_dense_gpu():
         assert np.max(np.abs(gf - gt)) <= 1e-6
     finally:
         P.close()
+
+
+def test_trunc_excluded_exponent_overflow():
+    """A target with a potential far above the others, outside the radius of
+    most points: its excluded terms' exponentials overflow FP32 in those points'
+    shifts (weight 0 times inf in the tensor-core passes), which must drop them
+    (exact redo in pass 1, the stage again in pass 2) and match the oracle."""
+    x, m, y, nu, psi, eps = case(82, 2, 4000, 900, 0.01, 0.01)
+    y[0] = (0.05, 0.05)
+    psi[0] = 5.0              # (psi_0 - c) / eps ~ 480 >> 88 for every point
+    P = rs().Problem(x, m, y, nu)
+    try:
+        res, (Jo, go, po, eo) = compare(P, x, m, y, nu, psi, eps, 0.3)
+        assert eo == 0
+        # most points exclude target 0, and its own cell takes most of the mass
+        far = np.sum(np.sum((x - y[0]) ** 2, axis=1) >= 0.09)
+        assert far > 0.5 * x.shape[0]
+        J, g, pairs = res[1]
+        assert np.isfinite(J) and np.all(np.isfinite(g))
+    finally:
+        P.close()
