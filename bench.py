@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--tail", type=float, default=0.0,
                     help="multilevel: truncation tail of every evaluation (0: dense)")
     ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart",
-                                           "maps", "barycenter"],
+                                           "maps", "barycenter", "mlp"],
                     default="dense",
                     help="dense: dual+grad throughput (default); the others time solves")
     ap.add_argument("--problems", type=int, default=32, help="batch: problems (seeds 1000..)")
@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--train-seeds", type=int, default=10000)
     ap.add_argument("--eval-seeds", type=int, default=512)
     ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--mlp-rows", type=int, default=65536, help="mlp: rows per gradients call")
     return ap.parse_args()
 
 
@@ -358,6 +359,47 @@ def run_solve_workloads(args):
         solve_line("barycenter wall time (damped Lloyd, 3 sources x 98,304 points, 4,096 support points)",
                    wall, "s", "barycenter-3x98304-4096-eps0.002",
                    {"stats": st, "seconds_per_iteration": wall / max(1, st["iterations"])}, args)
+        return
+    if args.workload == "mlp":
+        # the warm-start network's training step (forward, back-propagation, weight
+        # gradients) on device-resident rows, with each GEMM kernel; value: GEMM
+        # FLOP/s of the whole gradients call (host copy of the gradient included)
+        rows, in_dim, w = args.mlp_rows, 18, 256
+        in_pad = 32
+        flops = 2.0 * rows * (2 * in_pad * w + 6 * w * w)
+        rng = np.random.default_rng(0)
+        x = torch.tensor(rng.normal(0, 1, (rows, in_dim)).astype(np.float32), device="cuda")
+        yv = torch.tensor(rng.normal(0, 1, rows).astype(np.float32), device="cuda")
+        res = {}
+        for name, kind in (("tcgen05", rs.GEMM_TCGEN05), ("mma_sync", rs.GEMM_MMA_SYNC)):
+            net = rs.MLP(in_dim, w, seed=1)
+            net.set_gemm_kernel(kind)
+            for _ in range(max(3, args.warmup)):
+                net.gradients(x, yv)
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(args.steps):
+                net.gradients(x, yv)
+            b_.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b_) / args.steps
+            res[name] = {"ms_per_step": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+            net.close()
+        peak = measured_peaks().get("bf16_tflops")
+        out = {"metric": "MLP training step TFLOP/s (GEMM FLOPs per gradients call, tcgen05 GEMMs)",
+               "value": res["tcgen05"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+               "warmup": max(3, args.warmup), "ms_per_step": res["tcgen05"]["ms_per_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+               "data": "synthetic",
+               "config": {"workload": f"mlp-{in_dim}x{w}x3-rows{rows}", "flops_per_step": flops},
+               "mma_sync": res["mma_sync"],
+               "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": res["tcgen05"]["tflops"],
+                            "peak": peak, "frac": (res["tcgen05"]["tflops"] / peak) if peak else None,
+                            "note": "whole call (activation writes, column sums, host copy of the "
+                                    "gradient included), not the GEMM kernels alone"}}
+        print(json.dumps(out))
         return
     if args.workload == "warmstart":
         from paper_2507_23602_gb300 import warmstart as ws

@@ -19,7 +19,8 @@ from typing import Optional
 import numpy as np
 
 __all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "MLP", "SolveOptions", "SolveStats",
-           "FP64", "MIXED", "COMPENSATED", "COMPENSATED_GRAD_REL", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate"]
+           "FP64", "MIXED", "COMPENSATED", "COMPENSATED_GRAD_REL", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate",
+           "GEMM_TCGEN05", "GEMM_MMA_SYNC"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "librsot.so")
@@ -29,6 +30,8 @@ FP64, MIXED, COMPENSATED = 0, 1, 2
 # ||g - grad J||_1 <= COMPENSATED_GRAD_REL * sum_q m_q for a COMPENSATED gradient
 COMPENSATED_GRAD_REL = 6.5e-7
 PAIRS_FP32, PAIRS_TENSOR, PAIRS_AUTO = 0, 1, 2
+# GEMM kernels of the warm-start network (rsot_mlp_set_gemm_kernel)
+GEMM_TCGEN05, GEMM_MMA_SYNC = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
           4: "empty neighbourhood", 5: "not converged", 6: "line search failed",
           7: "device wait timed out", 8: "out of device memory"}
@@ -186,6 +189,7 @@ def load():
     lib.rsot_mlp_destroy.argtypes = [vp]
     lib.rsot_mlp_destroy.restype = None
     lib.rsot_mlp_set_stream.argtypes = [vp, vp]
+    lib.rsot_mlp_set_gemm_kernel.argtypes = [vp, ctypes.c_int]
     lib.rsot_mlp_num_params.argtypes = [vp]
     lib.rsot_mlp_num_params.restype = ctypes.c_int64
     lib.rsot_mlp_get_params.argtypes = [vp, vp]
@@ -579,6 +583,10 @@ class MLP:
                 stream = None
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         _check(lib.rsot_mlp_set_stream(h, ctypes.c_void_p(s or 0)), "mlp_set_stream")
+
+    def set_gemm_kernel(self, kind):
+        """GEMM_TCGEN05 (default) or GEMM_MMA_SYNC for the layers' GEMMs."""
+        _check(self._lib.rsot_mlp_set_gemm_kernel(self._h, int(kind)), "mlp_set_gemm_kernel")
 
     def close(self):
         if getattr(self, "_h", None):

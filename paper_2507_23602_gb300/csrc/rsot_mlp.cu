@@ -16,6 +16,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "rsot_internal.cuh"
@@ -96,9 +97,10 @@ __device__ __forceinline__ void load_tile(bf16 (*T)[GK + GPAD], const bf16 *__re
 
 template <bool AT, bool BT, int EPI>
 __global__ void __launch_bounds__(G_THREADS)
-    k_gemm_bf16(int M, int N, int K, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B,
-                int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias,
-                bf16 *__restrict__ H, int ldh, const float *__restrict__ Z, int ldz) {
+    k_gemm_bf16(int M, int N, int K, int kslice, const bf16 *__restrict__ A, int lda,
+                const bf16 *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                const float *__restrict__ bias, bf16 *__restrict__ H, int ldh, const float *__restrict__ Z,
+                int ldz) {
     __shared__ __align__(16) bf16 As[GM][GK + GPAD];
     __shared__ __align__(16) bf16 Bs[GN][GK + GPAD];
     const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
@@ -112,9 +114,12 @@ __global__ void __launch_bounds__(G_THREADS)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
 
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        load_tile<AT, GM>(As, A, lda, m0, M, k0, K);
-        load_tile<BT, GN>(Bs, B, ldb, n0, N, k0, K);
+    // split K: slice z covers [z kslice, (z + 1) kslice) and writes its own partial C
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    if (EPI == EPI_F32) C += (int64_t)blockIdx.z * M * ldc;
+    for (int k0 = kb; k0 < ke; k0 += GK) {
+        load_tile<AT, GM>(As, A, lda, m0, M, k0, ke);
+        load_tile<BT, GN>(Bs, B, ldb, n0, N, k0, ke);
         __syncthreads();
 #pragma unroll
         for (int ks = 0; ks < GK; ks += 16) {
@@ -167,6 +172,230 @@ __global__ void __launch_bounds__(G_THREADS)
             }
 }
 
+// ---------------------------------------------------------------------------
+// The same GEMM on the fifth-generation tensor cores.  One thread issues
+// tcgen05.mma (kind::f16: BF16 operands, FP32 accumulator in tensor memory),
+// CTA tile 128 x 128 (256 threads), K in stages of 64 (four MMAs of K = 16),
+// two stages in shared memory: the MMAs of a stage are issued as soon as its
+// operands have landed, and the next stage is copied while they run (into the
+// other buffer, once the commit of the MMAs that last read it has arrived).
+// Operands sit in the canonical K-major layout without swizzle: 8 x 8 core
+// matrices (8 rows of 16 bytes, 128 contiguous bytes), consecutive along K
+// (LBO = 128 B), 8-row groups 1,040 B apart (SBO), so a stage tile of 128 rows
+// x 64 K takes 16,640 B and no descriptor offset can leave it.  K-contiguous sources
+// arrive by 16-byte cp.async (zero-filled outside the matrix); a transposed
+// source is transposed on the way in by the threads.  The accumulator (128
+// lanes x 128 FP32 columns) is read back by tcgen05.ld: warp w takes lanes
+// 32 (w % 4) .. + 31 and columns 64 (w / 4) .. + 63, transposes each 32 x 32
+// block through shared memory and stores whole rows (coalesced), for the
+// epilogues of the warp-level kernel above.  Every wait is bounded (flag
+// kErrTimeout).
+constexpr int T5_M = 128, T5_N = 128, T5_K = 64, T5_THREADS = 256;
+// 8-row groups 1,040 B apart (1,024 + 16: successive groups start in other
+// shared-memory banks, for the transposing loads)
+constexpr uint32_t T5_LBO = 128, T5_SBO = 1040;
+constexpr int T5_TILE = 16 * T5_SBO;       // bytes of one operand tile of a stage (16 row groups)
+constexpr int T5_SMEM = 2 * 2 * T5_TILE;   // two stages of A and B: 65 KB
+static_assert(T5_THREADS / 32 * 32 * 33 * 4 <= T5_SMEM, "epilogue transpose fits in the stage buffers");
+// instruction descriptor of kind::f16: F32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t T5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T5_N >> 3) << 17) |
+                              ((uint32_t)(T5_M >> 4) << 24);
+
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), LBO >> 4
+// (bits 16-29), SBO >> 4 (bits 32-45), the fixed value 1 at bits 46-48, base
+// offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(T5_LBO >> 4) << 16) |
+           ((uint64_t)(T5_SBO >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// element (r, k) of a 128 x 64 stage tile at byte (r / 8) SBO + (k / 8) LBO +
+// (r % 8) 16 + (k % 8) 2; rows r0 + r >= rows_total and k0 + k >= k_total are zero
+template <bool TRANS>
+__device__ __forceinline__ void t5_load(unsigned char *T, const bf16 *__restrict__ src, int ld, int r0,
+                                        int rows_total, int k0, int k_total) {
+    const bf16 zero = __float2bfloat16(0.0f);
+    if (!TRANS) {
+        // src[r * ld + k]: 16-byte chunks of 8 consecutive k, asynchronous (zero-filled
+        // when the chunk lies outside; a chunk cut by k_total is assembled here)
+        for (int c = threadIdx.x; c < 128 * (T5_K / 8); c += T5_THREADS) {
+            const int r = c / (T5_K / 8), kc = c % (T5_K / 8);
+            const int gr = r0 + r, gk = k0 + kc * 8;
+            unsigned char *dst = T + (r >> 3) * T5_SBO + kc * T5_LBO + (r & 7) * 16;
+            if (gr < rows_total && gk < k_total && gk + 8 > k_total) {
+                bf16 e[8];
+                for (int i = 0; i < 8; ++i) e[i] = gk + i < k_total ? src[(int64_t)gr * ld + gk + i] : zero;
+                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(e);
+            } else {
+                const bool in = gr < rows_total && gk + 8 <= k_total;
+                cp_async16(dst, in ? (const void *)(src + (int64_t)gr * ld + gk) : (const void *)src,
+                           in ? 16u : 0u);
+            }
+        }
+    } else {
+        // src[k * ld + r]: 8 consecutive rows at one k per load, spread over one 8-row group
+        for (int c = threadIdx.x; c < 128 * T5_K / 8; c += T5_THREADS) {
+            const int k = c / 16, rg = c % 16;
+            const int gk = k0 + k, gr = r0 + rg * 8;
+            bf16 v[8];
+            if (gk < k_total && gr + 8 <= rows_total) {
+                *reinterpret_cast<uint4 *>(v) = *reinterpret_cast<const uint4 *>(src + (int64_t)gk * ld + gr);
+            } else {
+                for (int i = 0; i < 8; ++i)
+                    v[i] = (gk < k_total && gr + i < rows_total) ? src[(int64_t)gk * ld + gr + i] : zero;
+            }
+            unsigned char *base = T + rg * T5_SBO + (k >> 3) * T5_LBO + (k & 7) * 2;
+            for (int i = 0; i < 8; ++i) *reinterpret_cast<bf16 *>(base + i * 16) = v[i];
+        }
+    }
+}
+
+// 32 consecutive FP32 columns of the thread's tensor-memory lane
+__device__ __forceinline__ void t5_ld32(uint32_t (&v)[32], uint32_t taddr) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+template <bool AT, bool BT, int EPI>
+__global__ void __launch_bounds__(T5_THREADS)
+    k_gemm_t5(int M, int N, int K, int kslice, const bf16 *__restrict__ A, int lda,
+              const bf16 *__restrict__ B, int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias,
+              bf16 *__restrict__ H, int ldh, const float *__restrict__ Z, int ldz,
+              int *__restrict__ flags) {
+    extern __shared__ __align__(1024) unsigned char t5_smem[];
+    __shared__ __align__(8) uint64_t done[2];   // commit of the MMAs that read stage buffer s
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * T5_M, n0 = blockIdx.x * T5_N;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(T5_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        mbar_init(&done[0], 1);
+        mbar_init(&done[1], 1);
+        fence_barrier_init();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    // split K: slice z covers [z kslice, (z + 1) kslice) and writes its own partial C
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    if (EPI == EPI_F32) C += (int64_t)blockIdx.z * M * ldc;
+    const int nk = ke > kb ? (ke - kb + T5_K - 1) / T5_K : 0;
+    bool ok = true;
+    if (nk > 0) {
+        t5_load<AT>(t5_smem, A, lda, m0, M, kb, ke);
+        t5_load<BT>(t5_smem + T5_TILE, B, ldb, n0, N, kb, ke);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt & 1;
+        unsigned char *As = t5_smem + s * 2 * T5_TILE, *Bs = As + T5_TILE;
+        // stage kt has landed (the thread's copies, then every thread's); its
+        // stores become visible to the tensor core (async proxy)
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int kk = 0; kk < T5_K / 16; ++kk) {
+                const uint64_t ad = t5_desc(a0 + kk * 2 * T5_LBO), bd = t5_desc(b0 + kk * 2 * T5_LBO);
+                const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(T5_IDESC), "r"(accum)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&done[s]))
+                         : "memory");
+        }
+        if (kt + 1 < nk) {
+            // the other buffer was last read by the MMAs of stage kt - 1
+            if (kt >= 1) ok = mbar_wait(&done[s ^ 1], (unsigned)((kt - 1) >> 1) & 1u) && ok;
+            unsigned char *An = t5_smem + (s ^ 1) * 2 * T5_TILE;
+            t5_load<AT>(An, A, lda, m0, M, kb + (kt + 1) * T5_K, ke);
+            t5_load<BT>(An + T5_TILE, B, ldb, n0, N, kb + (kt + 1) * T5_K, ke);
+            cp_async_commit();
+        }
+    }
+    if (nk > 0) ok = mbar_wait(&done[(nk - 1) & 1], (unsigned)((nk - 1) >> 1) & 1u) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // every MMA is done: the stage buffers hold the epilogue's transposes
+    float *T = reinterpret_cast<float *>(t5_smem) + warp * 32 * 33;
+    const int q = warp & 3, cb = (warp >> 2) * 64;   // lanes 32 q .. + 31, columns cb .. + 63
+#pragma unroll 1
+    for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+        uint32_t v[32];
+        t5_ld32(v, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) T[lane * 33 + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        if (ok && nk > 0 && col < N) {
+            const float bc = EPI == EPI_BIAS_SILU ? bias[col] : 0.f;
+            // eight rows at a time: their SiLU'(Z) operands are loaded before the stores
+#pragma unroll 1
+            for (int r8 = 0; r8 < 32; r8 += 8) {
+                float zr[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = m0 + 32 * q + r8 + i;
+                    zr[i] = (EPI == EPI_DSILU && row < M) ? Z[(int64_t)row * ldz + col] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = m0 + 32 * q + r8 + i;
+                    if (row >= M) break;
+                    float x = T[(r8 + i) * 33 + lane];
+                    if (EPI == EPI_F32) {
+                        C[(int64_t)row * ldc + col] = x;
+                    } else if (EPI == EPI_BIAS_SILU) {
+                        x += bc;
+                        C[(int64_t)row * ldc + col] = x;                        // pre-activation
+                        H[(int64_t)row * ldh + col] = __float2bfloat16(silu(x));  // activation
+                    } else {
+                        H[(int64_t)row * ldh + col] = __float2bfloat16(x * dsilu(zr[i]));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (!ok && tid == 0) atomicOr(flags, kErrTimeout);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T5_N) : "memory");
+}
+
 // out[b] = sum_i H3[b][i] w4[i] + b4 (FP32), one warp per row
 __global__ void k_head(const bf16 *__restrict__ H, int width, int64_t rows, const float *__restrict__ w,
                        const float *__restrict__ b, float *__restrict__ out) {
@@ -199,51 +428,48 @@ __global__ void k_head_back(const float *__restrict__ out, const float *__restri
 }
 
 // column sums over rows of a BF16 (or FP32 when F) matrix: out[c] = sum_r X[r][c]
+// Column sums over rows, two passes in a fixed order (deterministic):
+// part[k][c] = sum of wgt[r] X[r][c] over the rows r of chunk k (wgt null: 1),
+// 32 columns x 8 row lanes per block (coalesced along the columns); then
+// out[c] = sum_k part[k][c].
+constexpr int RED_CHUNKS = 64;
 template <typename T>
-__global__ void k_colsum(const T *__restrict__ X, int64_t rows, int cols, float *__restrict__ out) {
-    const int c = blockIdx.x;
+__global__ void k_colsum_part(const T *__restrict__ X, const float *__restrict__ wgt, int64_t rows, int cols,
+                              float *__restrict__ part) {
+    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cx;
+    const int64_t per = (rows + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = (int64_t)blockIdx.y * per, r1 = min(rows, r0 + per);
     float s = 0.f;
-    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
-        if constexpr (sizeof(T) == 2) s += __bfloat162float(X[r * cols + c]);
-        else s += (float)X[r * cols + c];
-    }
-    __shared__ float sh[256];
-    sh[threadIdx.x] = s;
+    if (c < cols)
+        for (int64_t r = r0 + ry; r < r1; r += 8) {
+            float x;
+            if constexpr (sizeof(T) == 2) x = __bfloat162float(X[r * cols + c]);
+            else x = (float)X[r * cols + c];
+            s += wgt ? wgt[r] * x : x;
+        }
+    __shared__ float sh[8][33];
+    sh[ry][cx] = s;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
+    if (ry == 0 && c < cols) {
+        float t = 0.f;
+        for (int i = 0; i < 8; ++i) t += sh[i][cx];
+        part[(int64_t)blockIdx.y * cols + c] = t;
     }
-    if (threadIdx.x == 0) out[c] = sh[0];
 }
-
-// dw4[i] = sum_r dout[r] H3[r][i]
-__global__ void k_head_wgrad(const bf16 *__restrict__ H, const float *__restrict__ dout, int64_t rows,
-                             int width, float *__restrict__ dw) {
-    const int i = blockIdx.x;
-    float s = 0.f;
-    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += dout[r] * __bfloat162float(H[r * width + i]);
-    __shared__ float sh[256];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) dw[i] = sh[0];
+__global__ void k_colsum_fin(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float t = 0.f;
+    for (int k = 0; k < chunks; ++k) t += part[(int64_t)k * cols + c];
+    out[c] = t;
 }
-
-__global__ void k_sum(const float *__restrict__ v, int64_t n, float *__restrict__ out) {
-    __shared__ float sh[256];
-    float s = 0.f;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = sh[0];
+// out[c] = sum_r wgt[r] X[r][c]; part: RED_CHUNKS x cols floats
+template <typename T>
+void colsum(cudaStream_t st, const T *X, const float *wgt, int64_t rows, int cols, float *part, float *out) {
+    const int ch = (int)std::min<int64_t>(RED_CHUNKS, std::max<int64_t>(1, rows / 256));
+    k_colsum_part<T><<<dim3((unsigned)((cols + 31) / 32), (unsigned)ch), 256, 0, st>>>(X, wgt, rows, cols, part);
+    k_colsum_fin<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(part, ch, cols, out);
 }
 
 // Adam on the FP32 master parameters (bias-corrected moments)
@@ -280,12 +506,49 @@ __global__ void k_input_bf16(const float *__restrict__ x, int64_t rows, int in_d
     X0[i] = __float2bfloat16(c < in_dim ? x[r * in_dim + c] : 0.f);
 }
 
+// C[r][c] = sum_z ws[z][r][c] (the split-K partials, in slice order)
+__global__ void k_split_sum(const float *__restrict__ ws, int S, int M, int N, int ldc, float *__restrict__ C) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * N) return;
+    const int64_t o = (i / N) * ldc + i % N, zs = (int64_t)M * ldc;
+    float v = 0.f;
+    for (int z = 0; z < S; ++z) v += ws[z * zs + o];
+    C[o] = v;
+}
+
+constexpr int SPLIT_MAX = 128;   // split-K slices at most (workspace SPLIT_MAX x M x ldc floats)
+
+// kind 0: tcgen05 kernel, 1: warp-level mma.sync kernel (same operands, epilogues).
+// A plain-FP32 GEMM with a long K and few output tiles (the weight gradients,
+// K = rows) is split along K over about two CTAs per SM, its partials summed
+// by k_split_sum in a fixed order (ws: SPLIT_MAX x M x ldc floats).
 template <bool AT, bool BT, int EPI>
-void gemm(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
-          float *C, int ldc, const float *bias, bf16 *H, int ldh, const float *Z, int ldz) {
-    dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
-    k_gemm_bf16<AT, BT, EPI><<<grid, G_THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, H,
-                                                         ldh, Z, ldz);
+void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int N, int K, const bf16 *A,
+          int lda, const bf16 *B, int ldb, float *C, int ldc, const float *bias, bf16 *H, int ldh,
+          const float *Z, int ldz) {
+    const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
+    int S = 1;
+    if (EPI == EPI_F32 && ws) S = std::max(1, std::min({K / 512, 2 * sms / std::max(1, tiles), SPLIT_MAX}));
+    const int kslice = S > 1 ? (K + S - 1) / S / 64 * 64 + 64 : K;
+    if (S > 1) S = (K + kslice - 1) / kslice;
+    float *Cw = S > 1 ? ws : C;
+    if (kind == 0) {
+        static bool attr = false;   // 64 KB of dynamic shared memory, set once per instance
+        if (!attr) {
+            cudaFuncSetAttribute((const void *)k_gemm_t5<AT, BT, EPI>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, T5_SMEM);
+            attr = true;
+        }
+        dim3 grid((N + T5_N - 1) / T5_N, (M + T5_M - 1) / T5_M, S);
+        k_gemm_t5<AT, BT, EPI><<<grid, T5_THREADS, T5_SMEM, st>>>(M, N, K, kslice, A, lda, B, ldb, Cw, ldc,
+                                                                   bias, H, ldh, Z, ldz, flags);
+    } else {
+        dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, S);
+        k_gemm_bf16<AT, BT, EPI><<<grid, G_THREADS, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, Cw, ldc, bias,
+                                                             H, ldh, Z, ldz);
+    }
+    if (S > 1)
+        k_split_sum<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, st>>>(ws, S, M, N, ldc, C);
 }
 
 uint64_t mix64(uint64_t &s) {
@@ -313,6 +576,11 @@ struct rsot_mlp {
     bf16 *X0 = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZ = nullptr, *dZ2 = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dH = nullptr, *out = nullptr, *dout = nullptr,
           *lt = nullptr, *xin = nullptr, *yin = nullptr, *scal = nullptr;
+    int gemm_kind = 0;       // 0: tcgen05 GEMM kernel, 1: mma.sync GEMM kernel
+    float *ws = nullptr;     // split-K partials of the weight-gradient GEMMs
+    float *red = nullptr;    // partials of the column sums (RED_CHUNKS x width)
+    int sms = 1;
+    int *flags = nullptr;    // device error flags of the GEMM kernels (kErrTimeout)
 };
 
 namespace rsot {
@@ -362,17 +630,24 @@ cudaError_t mlp_reserve(rsot_mlp *m, int64_t rows) {
     return e;
 }
 
+// a GEMM wait that gave up (flag read with the call's results): cleared, reported
+rsot_status mlp_take_flags(rsot_mlp *m, int fl) {
+    if (!fl) return RSOT_OK;
+    cudaMemset(m->flags, 0, sizeof(int));
+    return RSOT_ERR_TIMEOUT;
+}
+
 // forward on rows (padded to 128) from m->xin; result in m->out
 void mlp_forward(rsot_mlp *m, int64_t rows) {
     const int w = m->width, R = (int)((rows + 127) / 128 * 128);
     cudaStream_t st = m->stream;
     k_input_bf16<<<(unsigned)((R * (int64_t)m->in_pad + 255) / 256), 256, 0, st>>>(m->xin, R, m->in_dim,
                                                                                  m->in_pad, m->X0);
-    gemm<false, false, EPI_BIAS_SILU>(st, R, w, m->in_pad, m->X0, m->in_pad, m->W1b, m->in_pad, m->Z1,
+    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, m->in_pad, m->X0, m->in_pad, m->W1b, m->in_pad, m->Z1,
                                       w, m->P + m->off[1], m->H1, w, nullptr, 0);
-    gemm<false, false, EPI_BIAS_SILU>(st, R, w, w, m->H1, w, m->W2b, w, m->Z2, w, m->P + m->off[3],
+    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H1, w, m->W2b, w, m->Z2, w, m->P + m->off[3],
                                       m->H2, w, nullptr, 0);
-    gemm<false, false, EPI_BIAS_SILU>(st, R, w, w, m->H2, w, m->W3b, w, m->Z3, w, m->P + m->off[5],
+    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H2, w, m->W3b, w, m->Z3, w, m->P + m->off[5],
                                       m->H3, w, nullptr, 0);
     k_head<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->H3, w, R, m->P + m->off[6], m->P + m->off[7], m->out);
 }
@@ -385,20 +660,20 @@ void mlp_backward(rsot_mlp *m, int64_t rows) {
     float *G = m->G;
     k_head_back<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
                                                          m->P + m->off[6], m->Z3, w, m->dout, m->dZ, m->lt);
-    k_head_wgrad<<<w, 256, 0, st>>>(m->H3, m->dout, R, w, G + m->off[6]);
-    k_sum<<<1, 256, 0, st>>>(m->dout, R, G + m->off[7]);
+    colsum<bf16>(st, m->H3, m->dout, R, w, m->red, G + m->off[6]);   // dw4 = sum_r dout_r H3[r]
+    colsum<float>(st, m->dout, nullptr, R, 1, m->red, G + m->off[7]);
     // layer 3: dW3 = dZ3^T H2, db3 = colsum dZ3, dZ2 = (dZ3 W3) * SiLU'(Z2)
-    gemm<true, true, EPI_F32>(st, w, w, R, m->dZ, w, m->H2, w, G + m->off[4], w, nullptr, nullptr, 0, nullptr, 0);
-    k_colsum<bf16><<<w, 256, 0, st>>>(m->dZ, R, w, G + m->off[5]);
-    gemm<false, false, EPI_DSILU>(st, R, w, w, m->dZ, w, m->W3bT, w, nullptr, 0, nullptr, m->dZ2, w, m->Z2, w);
+    gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, w, R, m->dZ, w, m->H2, w, G + m->off[4], w, nullptr, nullptr, 0, nullptr, 0);
+    colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[5]);
+    gemm<false, false, EPI_DSILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->dZ, w, m->W3bT, w, nullptr, 0, nullptr, m->dZ2, w, m->Z2, w);
     // layer 2
-    gemm<true, true, EPI_F32>(st, w, w, R, m->dZ2, w, m->H1, w, G + m->off[2], w, nullptr, nullptr, 0, nullptr, 0);
-    k_colsum<bf16><<<w, 256, 0, st>>>(m->dZ2, R, w, G + m->off[3]);
-    gemm<false, false, EPI_DSILU>(st, R, w, w, m->dZ2, w, m->W2bT, w, nullptr, 0, nullptr, m->dZ, w, m->Z1, w);
+    gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, w, R, m->dZ2, w, m->H1, w, G + m->off[2], w, nullptr, nullptr, 0, nullptr, 0);
+    colsum<bf16>(st, m->dZ2, nullptr, R, w, m->red, G + m->off[3]);
+    gemm<false, false, EPI_DSILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->dZ2, w, m->W2bT, w, nullptr, 0, nullptr, m->dZ, w, m->Z1, w);
     // layer 1: dW1 = dZ1^T X0, db1 = colsum dZ1
-    gemm<true, true, EPI_F32>(st, w, m->in_pad, R, m->dZ, w, m->X0, m->in_pad, G + m->off[0], m->in_pad,
+    gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, m->in_pad, R, m->dZ, w, m->X0, m->in_pad, G + m->off[0], m->in_pad,
                               nullptr, nullptr, 0, nullptr, 0);
-    k_colsum<bf16><<<w, 256, 0, st>>>(m->dZ, R, w, G + m->off[1]);
+    colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[1]);
 }
 
 }  // namespace
@@ -412,7 +687,7 @@ void rsot_mlp_destroy(rsot_mlp *m) {
     if (!m) return;
     void *ptrs[] = {m->P, m->G, m->Mo, m->Vo, m->W1b, m->W1bT, m->W2b, m->W2bT, m->W3b, m->W3bT,
                     m->X0, m->H1, m->H2, m->H3, m->dZ, m->dZ2, m->Z1, m->Z2, m->Z3, m->dH, m->out,
-                    m->dout, m->lt, m->xin, m->yin, m->scal};
+                    m->dout, m->lt, m->xin, m->yin, m->scal, m->flags, m->ws, m->red};
     for (void *q : ptrs) cudaFree(q);
     delete m;
 }
@@ -451,6 +726,13 @@ rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out
     if (!e) e = cudaMalloc(&m->W3b, (size_t)w * w * 2);
     if (!e) e = cudaMalloc(&m->W3bT, (size_t)w * w * 2);
     if (!e) e = cudaMalloc(&m->scal, 16);
+    if (!e) e = cudaMalloc(&m->flags, sizeof(int));
+    if (!e) e = cudaMalloc(&m->ws, (size_t)SPLIT_MAX * w * std::max(w, m->in_pad) * sizeof(float));
+    if (!e) e = cudaMalloc(&m->red, (size_t)RED_CHUNKS * w * sizeof(float));
+    int dev = 0;
+    if (!e) e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaMemset(m->flags, 0, sizeof(int));
     if (!e) e = cudaMemcpy(m->P, h.data(), m->n_params * 4, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(m->Mo, 0, m->n_params * 4);
     if (!e) e = cudaMemset(m->Vo, 0, m->n_params * 4);
@@ -467,6 +749,12 @@ rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out
 }
 
 int64_t rsot_mlp_num_params(const rsot_mlp *m) { return m ? m->n_params : 0; }
+
+rsot_status rsot_mlp_set_gemm_kernel(rsot_mlp *m, int kind) {
+    if (!m || kind < 0 || kind > 1) return RSOT_ERR_ARG;
+    m->gemm_kind = kind;
+    return RSOT_OK;
+}
 
 rsot_status rsot_mlp_set_stream(rsot_mlp *m, void *stream) {
     if (!m) return RSOT_ERR_ARG;
@@ -495,8 +783,14 @@ rsot_status rsot_mlp_forward(rsot_mlp *m, int64_t rows, const float *x, float *y
         e = cudaGetLastError();
     }
     if (!e) e = cudaMemcpyAsync(y_out, m->out, (size_t)rows * 4, cudaMemcpyDefault, m->stream);
+    int fl = 0;
+    if (!e) e = cudaMemcpyAsync(&fl, m->flags, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
     if (!e) e = cudaStreamSynchronize(m->stream);
-    return e ? (cudaGetLastError(), RSOT_ERR_CUDA) : RSOT_OK;
+    if (e) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    return mlp_take_flags(m, fl);
 }
 
 rsot_status rsot_mlp_gradients(rsot_mlp *m, int64_t rows, const float *x, const float *y,
@@ -510,17 +804,21 @@ rsot_status rsot_mlp_gradients(rsot_mlp *m, int64_t rows, const float *x, const 
     if (!e) e = cudaMemcpyAsync(m->yin, y, (size_t)rows * 4, cudaMemcpyDefault, m->stream);
     if (!e) {
         mlp_backward(m, rows);
-        k_sum<<<1, 256, 0, m->stream>>>(m->lt, R, m->scal);
+        colsum<float>(m->stream, m->lt, nullptr, R, 1, m->red, m->scal);
         e = cudaGetLastError();
     }
     float l = 0.f;
     if (!e) e = cudaMemcpyAsync(&l, m->scal, 4, cudaMemcpyDeviceToHost, m->stream);
     if (!e && grad_out) e = cudaMemcpyAsync(grad_out, m->G, m->n_params * 4, cudaMemcpyDefault, m->stream);
+    int fl = 0;
+    if (!e) e = cudaMemcpyAsync(&fl, m->flags, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
     if (!e) e = cudaStreamSynchronize(m->stream);
     if (e) {
         cudaGetLastError();
         return RSOT_ERR_CUDA;
     }
+    const rsot_status fs = mlp_take_flags(m, fl);
+    if (fs) return fs;
     if (loss_out) *loss_out = l / (float)rows;
     return RSOT_OK;
 }

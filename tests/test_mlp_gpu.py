@@ -1,6 +1,7 @@
 """The warm-start network's own kernels (BF16 tensor-core GEMMs, FP32
-accumulation) against the FP64 MLP oracle that rounds to bfloat16 where the
-kernels do."""
+accumulation; both GEMM kernels: tcgen05 with the accumulator in tensor memory,
+and warp-level mma.sync) against the FP64 MLP oracle that rounds to bfloat16
+where the kernels do."""
 import numpy as np
 import pytest
 
@@ -14,17 +15,23 @@ def rs():
     return m
 
 
-def setup(in_dim, width, rows, seed):
+def setup(in_dim, width, rows, seed, kind=0):
     net = rs().MLP(in_dim, width, seed=seed)
+    net.set_gemm_kernel(kind)
     rng = np.random.default_rng(seed)
     x = rng.normal(0, 1, (rows, in_dim)).astype(np.float32)
     y = rng.normal(0, 1, rows).astype(np.float32)
     return net, x, y
 
 
-@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 1000), (18, 256, 4096), (5, 64, 300)])
-def test_forward_matches_oracle(in_dim, width, rows):
-    net, x, y = setup(in_dim, width, rows, 7)
+KINDS = [0, 1]   # GEMM_TCGEN05, GEMM_MMA_SYNC
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 1000), (18, 256, 4096), (5, 64, 300),
+                                               (7, 200, 777)])
+def test_forward_matches_oracle(in_dim, width, rows, kind):
+    net, x, y = setup(in_dim, width, rows, 7, kind)
     try:
         out = net.forward(x)
         ref, _ = omlp.forward(net.params(), x.astype(np.float64), in_dim, width)
@@ -33,9 +40,10 @@ def test_forward_matches_oracle(in_dim, width, rows):
         net.close()
 
 
-@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300)])
-def test_gradients_match_oracle(in_dim, width, rows):
-    net, x, y = setup(in_dim, width, rows, 11)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300), (7, 200, 777)])
+def test_gradients_match_oracle(in_dim, width, rows, kind):
+    net, x, y = setup(in_dim, width, rows, 11, kind)
     try:
         loss, g = net.gradients(x, y)
         lo, go = omlp.loss_and_grad(net.params(), x.astype(np.float64), y.astype(np.float64),
@@ -64,5 +72,33 @@ def test_training_reduces_the_loss():
             net.train_step(x[idx], y[idx], 3e-3)
         l1, _ = net.gradients(x, y)
         assert l1 < 0.05 * l0, (l0, l1)
+    finally:
+        net.close()
+
+
+def test_gemm_kernels_agree():
+    """The tcgen05 and mma.sync GEMM kernels on the same network and batch:
+    the same products summed in another order, so forward outputs and
+    gradients agree to FP32 accumulation (plus the rare BF16 activation that
+    rounds the other way)."""
+    net, x, y = setup(18, 256, 5000, 13, 0)
+    try:
+        o0 = net.forward(x)
+        l0, g0 = net.gradients(x, y)
+        net.set_gemm_kernel(1)
+        o1 = net.forward(x)
+        l1, g1 = net.gradients(x, y)
+        assert np.max(np.abs(o0 - o1)) <= 2e-3 * np.max(np.abs(o1)) + 1e-5
+        assert abs(l0 - l1) <= 1e-3 * abs(l1)
+        assert np.linalg.norm(g0 - g1) <= 1e-2 * np.linalg.norm(g1)
+    finally:
+        net.close()
+
+
+def test_gemm_kernel_kind_is_checked():
+    net = rs().MLP(4, 64, seed=1)
+    try:
+        with pytest.raises(rs().RsotError):
+            net.set_gemm_kernel(2)
     finally:
         net.close()
