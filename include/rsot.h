@@ -252,9 +252,13 @@ typedef struct {
     double eps_factor;   /* stage ratio in (0,1), e.g. 0.5; the last stage is eps  */
     double tail;         /* > 0: truncate the mixed (and FP64 / compensated stage)
                             evaluations with the psi-aware cutoffs of this tail
-                            (rsot_eval_dual_grad_tail); the refinement's reference
-                            evaluations stay dense, so a refined stop holds for the
-                            untruncated J.  0: dense                           */
+                            (rsot_eval_dual_grad_tail).  The refinement's
+                            compensated reference evaluations are truncated too
+                            when tail <= 1e-8 (else dense, as are FP64 ones), and
+                            the truncation bound tail sum(nu) (2 sum(m) + sum(nu))
+                            on ||grad J~ - grad J||_1 is subtracted from tol_l1
+                            with the compensated one, so a refined stop holds for
+                            the untruncated J.  0: dense                       */
     double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
     double stage_tol_l1; /* tolerance of the intermediate stages (<=0: 100 tol_l1:
                             they only warm-start the next stage)                 */

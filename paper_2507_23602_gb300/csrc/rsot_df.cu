@@ -60,6 +60,7 @@ struct __align__(16) DRec {
     float4 a, b, c, d;
 };
 
+
 typedef float2 f2;
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
@@ -172,10 +173,12 @@ __device__ __forceinline__ bool keep_pair(const float *xf, const float *yf, floa
 }
 
 // per-target records (rounded from FP64) and the block partials of sum psi nu
+// (perm non-null: record j is target perm[j], the cell list's order)
 __global__ void k_prep_df(const double *__restrict__ psi, const double *__restrict__ y64,
                           const double *__restrict__ lnu, const double *__restrict__ nu, int64_t n,
-                          int64_t n_alloc, int d, double eps, DRec *__restrict__ trec,
-                          double *__restrict__ psinu_part, int *__restrict__ flags) {
+                          int64_t n_alloc, int d, double eps, const int *__restrict__ perm,
+                          DRec *__restrict__ trec, double *__restrict__ psinu_part,
+                          int *__restrict__ flags) {
     __shared__ double sh[32];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double k = kLog2e / (2.0 * eps);
@@ -183,22 +186,88 @@ __global__ void k_prep_df(const double *__restrict__ psi, const double *__restri
     if (j < n_alloc) {
         float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kExcl, 0.f};
         if (j < n) {
-            const double ps = psi[j];
+            const int64_t o = perm ? (int64_t)perm[j] : j;
+            const double ps = psi[o];
             if (!isfinite(ps)) atomicOr(flags, kErrNonfinitePsi);
-            const double b = ((ps - psi[0]) / eps + lnu[j]) * kLog2e;
+            const double b = ((ps - psi[0]) / eps + lnu[o]) * kLog2e;
             double yy = 0.0;
             for (int t = 0; t < d; ++t) {
-                const double yt = y64[j * d + t];
+                const double yt = y64[o * d + t];
                 split_f(2.0 * k * yt, v[2 * t], v[2 * t + 1]);
                 yy += yt * yt;
             }
             split_f(fmax(b - k * yy, -1.0e29), v[6], v[7]);
-            contrib = ps * nu[j];
+            contrib = ps * nu[o];
         }
         trec[j] = make_drec(v);
     }
     const double s = block_sum_d(contrib, sh);
     if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
+}
+
+// ---- block data of the truncated passes (targets in the cell list's order)
+// ball (centre of the bounding box, radius to its corner, rounded up) of each
+// block of B consecutive rows of c64 [cnt][d]; radius -1: no member
+__global__ void k_df_balls(const double *__restrict__ c64, int64_t cnt, int d, int B, int64_t nblocks,
+                           float4 *__restrict__ ball) {
+    const int64_t bi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bi >= nblocks) return;
+    const int64_t a = bi * B, e = min((bi + 1) * B, cnt);
+    if (a >= e) {
+        ball[bi] = make_float4(0.f, 0.f, 0.f, -1.f);
+        return;
+    }
+    double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < d; ++k) lo[k] = hi[k] = c64[a * d + k];
+    for (int64_t q = a + 1; q < e; ++q)
+        for (int k = 0; k < d; ++k) {
+            lo[k] = fmin(lo[k], c64[q * d + k]);
+            hi[k] = fmax(hi[k], c64[q * d + k]);
+        }
+    double c[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        c[k] = 0.5 * (lo[k] + hi[k]);
+        r2 += 0.25 * (hi[k] - lo[k]) * (hi[k] - lo[k]);
+    }
+    ball[bi] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)(sqrt(r2) * (1.0 + 1e-6) + 1e-9));
+}
+
+// (min, max) of v over blocks of B consecutive entries (v[perm[s]] when perm is
+// given), rounded outwards to FP32; no member: (+inf, -inf)
+__global__ void k_df_ranges(const double *__restrict__ v, const int *__restrict__ perm, int64_t cnt, int B,
+                            int64_t nblocks, float2 *__restrict__ out) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t s = b * B; s < min((b + 1) * B, cnt); ++s) {
+        const double a = v[perm ? (int64_t)perm[s] : s];
+        lo = fmin(lo, a);
+        hi = fmax(hi, a);
+    }
+    float flo = (float)lo, fhi = (float)hi;
+    if ((double)flo > lo) flo = nextafterf(flo, -INFINITY);
+    if ((double)fhi < hi) fhi = nextafterf(fhi, INFINITY);
+    out[b] = make_float2(flo, fhi);
+}
+
+// out[s] = v[perm[s]] (v[s] without perm) for s < n, +inf beyond, in FP64
+// (out, nullable) and rounded to FP32 (outf, nullable: the value the FP32
+// pair tests use)
+__global__ void k_df_gather(const double *__restrict__ v, const int *__restrict__ perm, int64_t n,
+                            int64_t n_alloc, double *__restrict__ out, float *__restrict__ outf) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_alloc) return;
+    const double x = s < n ? v[perm ? (int64_t)perm[s] : s] : INFINITY;
+    if (out) out[s] = x;
+    if (outf) outf[s] = (float)x;
+}
+
+// FP32 coordinates [3][n_alloc] of the rows c64 [n][d] (1e30 beyond)
+__global__ void k_df_coords(const double *__restrict__ c64, int64_t n, int64_t n_alloc, int d,
+                            float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_alloc)
+        for (int t = 0; t < 3; ++t) out[t * n_alloc + i] = (i < n && t < d) ? (float)c64[i * d + t] : 1.0e30f;
 }
 
 // static point records (x' head/tail; the shift is written by pass 1) and
@@ -229,15 +298,21 @@ __global__ void __launch_bounds__(D_THREADS)
              int64_t n_alloc, const double *__restrict__ alpha, const double *__restrict__ beta,
              float span2, const double *__restrict__ lmass2, const double *__restrict__ mass,
              const double *__restrict__ psi, double eps, double *__restrict__ blockJ,
-             double *__restrict__ lse_buf, EvalResult *__restrict__ res) {
-    __shared__ DRec sm[D_TS];
-    __shared__ float sy[TRUNC ? 4 : 1][D_TS];
+             double *__restrict__ lse_buf, EvalResult *__restrict__ res,
+             const float4 *__restrict__ pball64, const float2 *__restrict__ pal64,
+             const float4 *__restrict__ tball8, const float2 *__restrict__ tbe8,
+             const float *__restrict__ betaf) {
+    __shared__ DRec sm[D_TS];   // the block's target tile
+    __shared__ float sy[TRUNC ? 4 : 1][D_TS];   // truncated: its FP32 coordinates and beta
+    __shared__ unsigned s_live[D_THREADS / 32];   // truncated: live sub-tiles of each warp
     __shared__ double sh[32];
     __shared__ unsigned long long s_cnt, s_empty;
     if (threadIdx.x == 0) s_cnt = s_empty = 0;
+    // truncated: a thread takes two consecutive points, a warp 64 (one ball)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t q[2];
-    q[0] = (int64_t)blockIdx.x * D_ROWS + threadIdx.x;   // < nq_pad
-    q[1] = q[0] + D_THREADS;
+    q[0] = (int64_t)blockIdx.x * D_ROWS + (TRUNC ? 2 * threadIdx.x : threadIdx.x);   // < nq_pad
+    q[1] = q[0] + (TRUNC ? 1 : D_THREADS);
     const DRec p0 = prec[q[0]], p1 = prec[q[1]];
     Op2 X[3];
     f2 unused_h, unused_t;
@@ -253,31 +328,106 @@ __global__ void __launch_bounds__(D_THREADS)
     float M[2] = {-INFINITY, -INFINITY};
     double S[2] = {0.0, 0.0};
     unsigned long long npair = 0;
-    for (int64_t t0 = 0; t0 < n_rec; t0 += D_TS) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
-            sm[i] = trec[t0 + i];
-            if (TRUNC) {
-                for (int t = 0; t < 3; ++t) sy[t][i] = ys[t * n_alloc + t0 + i];
-                sy[3][i] = (float)beta[t0 + i];
+    // truncated: the warp's 64 points against each sub-tile of 8 targets (ball
+    // classes, bit maps lv / bd): outside sub-tiles are skipped, inside ones
+    // need no pair test; a tile no warp needs is not loaded
+    const int64_t wblk = (int64_t)blockIdx.x * (D_ROWS / 64) + warp;
+    const float4 wb = TRUNC ? pball64[wblk] : make_float4(0.f, 0.f, 0.f, -1.f);
+    const float2 wa = TRUNC ? pal64[wblk] : make_float2(0.f, 0.f);
+    if constexpr (!TRUNC) {
+        for (int64_t t0 = 0; t0 < n_rec; t0 += D_TS) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < D_TS; i += D_THREADS) sm[i] = trec[t0 + i];
+            __syncthreads();
+            f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
+            for (int u0 = 0; u0 < D_TS; u0 += D_SUB) {
+                f2 rh[D_SUB], rt[D_SUB];
+                float mx0 = -INFINITY, mx1 = -INFINITY;
+    #pragma unroll
+                for (int i = 0; i < D_SUB; ++i) {
+                    const DRec &B = sm[u0 + i];
+                    df_exponent2<D>(X, B, lo2(B.d), hi2(B.d), rh[i], rt[i]);
+                    mx0 = fmaxf(mx0, rh[i].x);
+                    mx1 = fmaxf(mx1, rh[i].y);
+                }
+                if (mx0 > M[0] || mx1 > M[1]) {   // raise a shift to ceil(max): exact rescaling
+                    float f[2] = {1.f, 1.f};
+                    const float mx[2] = {mx0, mx1};
+                    for (int l = 0; l < 2; ++l) {
+                        if (mx[l] > M[l] && mx[l] > -1.0e29f) {
+                            const float mn = ceilf(mx[l]);
+                            if (M[l] != -INFINITY) {
+                                f[l] = pow2_int_f(M[l] - mn);
+                                S[l] *= pow2_int_d(M[l] - mn);
+                            }
+                            M[l] = mn;
+                        }
+                    }
+                    const f2 ff = make_float2(f[0], f[1]);
+                    s = mul2(s, ff);
+                    comp = mul2(comp, ff);
+                    cs = mul2(cs, ff);
+                }
+                // a lane with no kept pair yet subtracts a huge shift: its terms are 0
+                const f2 Me = make_float2(M[0] == -INFINITY ? 1.0e30f : M[0],
+                                          M[1] == -INFINITY ? 1.0e30f : M[1]);
+    #pragma unroll
+                for (int i = 0; i < D_SUB; ++i) {
+                    f2 ah, ae;
+                    two_diff2(rh[i], Me, ah, ae);
+                    const f2 e = make_float2(ex2_approx(ah.x), ex2_approx(ah.y));
+                    kahan2(s, comp, e);
+                    cs = fma2(e, add2(ae, rt[i]), cs);
+                }
             }
+            S[0] += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
+            S[1] += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
         }
-        __syncthreads();
-        f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
-        for (int u0 = 0; u0 < D_TS; u0 += D_SUB) {
-            f2 rh[D_SUB], rt[D_SUB];
-            float mx0 = -INFINITY, mx1 = -INFINITY;
+    } else {
+        // the warp's 64 points against every sub-tile of 8 targets of each tile
+        // (ball classes, bit maps lv / bd): outside sub-tiles are skipped, inside
+        // ones need no pair test; a tile that no warp of the block needs is not
+        // loaded
+        for (int64_t t0 = 0; t0 < n_rec; t0 += D_TS) {
+            int c = 0;
+            if (lane < D_TS / D_SUB) {
+                const int64_t sb = t0 / D_SUB + lane;
+                c = tp_class(wb, tball8[sb], wa, tbe8[sb]);
+            }
+            const unsigned lv = __ballot_sync(0xffffffffu, c != 0);
+            const unsigned bd = __ballot_sync(0xffffffffu, c == 2);
+            __syncthreads();   // the previous tile's readers are done
+            if (lane == 0) s_live[warp] = lv;
+            __syncthreads();
+            unsigned any = 0;
+            for (int w = 0; w < D_THREADS / 32; ++w) any |= s_live[w];
+            if (!any) continue;   // block-uniform
+            for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
+                sm[i] = trec[t0 + i];
+                for (int t = 0; t < 3; ++t) sy[t][i] = ys[t * n_alloc + t0 + i];
+                sy[3 % (TRUNC ? 4 : 1)][i] = betaf[t0 + i];
+            }
+            __syncthreads();
+            if (!lv) continue;   // warp-uniform: the next tile's first barrier waits for the others
+            f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
+            for (unsigned mm = lv; mm; mm &= mm - 1) {
+                const int sub = __ffs(mm) - 1;
+                const bool test = (bd >> sub) & 1u;
+                const int u0 = sub * D_SUB;
+                f2 rh[D_SUB], rt[D_SUB];
+                float mx0 = -INFINITY, mx1 = -INFINITY;
 #pragma unroll
-            for (int i = 0; i < D_SUB; ++i) {
-                const DRec &B = sm[u0 + i];
-                df_exponent2<D>(X, B, lo2(B.d), hi2(B.d), rh[i], rt[i]);
-                if (TRUNC) {
-                    const float yf[3] = {sy[0][u0 + i], sy[1][u0 + i], sy[2][u0 + i]};
+                for (int i = 0; i < D_SUB; ++i) {
                     const int64_t j = t0 + u0 + i;
+                    const DRec &B = sm[u0 + i];
+                    df_exponent2<D>(X, B, lo2(B.d), hi2(B.d), rh[i], rt[i]);
+                    const float yf[3] = {sy[0][u0 + i], sy[1 % (TRUNC ? 4 : 1)][u0 + i],
+                                         sy[2 % (TRUNC ? 4 : 1)][u0 + i]};
                     for (int l = 0; l < 2; ++l) {
                         const bool k = j < n && q[l] < nq &&
-                                       keep_pair<D>(xf[l], yf, (float)a64[l], sy[3][u0 + i], span2,
-                                                    x64 + q[l] * D, y64 + j * D, a64[l], beta + j);
+                                       (!test || keep_pair<D>(xf[l], yf, (float)a64[l],
+                                                              sy[3 % (TRUNC ? 4 : 1)][u0 + i], span2,
+                                                              x64 + q[l] * D, y64 + j * D, a64[l], beta + j));
                         if (k) {
                             ++npair;
                         } else if (l == 0) {
@@ -288,42 +438,41 @@ __global__ void __launch_bounds__(D_THREADS)
                             rt[i].y = 0.f;
                         }
                     }
+                    mx0 = fmaxf(mx0, rh[i].x);
+                    mx1 = fmaxf(mx1, rh[i].y);
                 }
-                mx0 = fmaxf(mx0, rh[i].x);
-                mx1 = fmaxf(mx1, rh[i].y);
-            }
-            if (mx0 > M[0] || mx1 > M[1]) {   // raise a shift to ceil(max): exact rescaling
-                float f[2] = {1.f, 1.f};
-                const float mx[2] = {mx0, mx1};
-                for (int l = 0; l < 2; ++l) {
-                    if (mx[l] > M[l] && mx[l] > -1.0e29f) {
-                        const float mn = ceilf(mx[l]);
-                        if (M[l] != -INFINITY) {
-                            f[l] = pow2_int_f(M[l] - mn);
-                            S[l] *= pow2_int_d(M[l] - mn);
+                if (mx0 > M[0] || mx1 > M[1]) {   // raise a shift to ceil(max): exact rescaling
+                    float f[2] = {1.f, 1.f};
+                    const float mx[2] = {mx0, mx1};
+                    for (int l = 0; l < 2; ++l) {
+                        if (mx[l] > M[l] && mx[l] > -1.0e29f) {
+                            const float mn = ceilf(mx[l]);
+                            if (M[l] != -INFINITY) {
+                                f[l] = pow2_int_f(M[l] - mn);
+                                S[l] *= pow2_int_d(M[l] - mn);
+                            }
+                            M[l] = mn;
                         }
-                        M[l] = mn;
                     }
+                    const f2 ff = make_float2(f[0], f[1]);
+                    s = mul2(s, ff);
+                    comp = mul2(comp, ff);
+                    cs = mul2(cs, ff);
                 }
-                const f2 ff = make_float2(f[0], f[1]);
-                s = mul2(s, ff);
-                comp = mul2(comp, ff);
-                cs = mul2(cs, ff);
-            }
-            // a lane with no kept pair yet subtracts a huge shift: its terms are 0
-            const f2 Me = make_float2(M[0] == -INFINITY ? 1.0e30f : M[0],
-                                      M[1] == -INFINITY ? 1.0e30f : M[1]);
+                const f2 Me = make_float2(M[0] == -INFINITY ? 1.0e30f : M[0],
+                                          M[1] == -INFINITY ? 1.0e30f : M[1]);
 #pragma unroll
-            for (int i = 0; i < D_SUB; ++i) {
-                f2 ah, ae;
-                two_diff2(rh[i], Me, ah, ae);
-                const f2 e = make_float2(ex2_approx(ah.x), ex2_approx(ah.y));
-                kahan2(s, comp, e);
-                cs = fma2(e, add2(ae, rt[i]), cs);
+                for (int i = 0; i < D_SUB; ++i) {
+                    f2 ah, ae;
+                    two_diff2(rh[i], Me, ah, ae);
+                    const f2 e = make_float2(ex2_approx(ah.x), ex2_approx(ah.y));
+                    kahan2(s, comp, e);
+                    cs = fma2(e, add2(ae, rt[i]), cs);
+                }
             }
+            S[0] += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
+            S[1] += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
         }
-        S[0] += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
-        S[1] += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
     }
     double contrib = 0.0;
     int empties = 0;
@@ -371,12 +520,18 @@ __global__ void __launch_bounds__(D_THREADS)
               const DRec *__restrict__ prec, const float *__restrict__ xs,
               const double *__restrict__ x64, int64_t nq, int64_t nq_pad, int64_t chunk,
               const double *__restrict__ alpha, const double *__restrict__ beta, float span2,
-              double *__restrict__ part2) {
-    __shared__ DRec sm[D_TS];
-    __shared__ float sx[TRUNC ? 4 : 1][D_TS];
+              double *__restrict__ part2, const int *__restrict__ perm,
+              const float4 *__restrict__ tball64, const float2 *__restrict__ tbe64,
+              const float4 *__restrict__ pball8, const float2 *__restrict__ pal8,
+              const float *__restrict__ alphaf) {
+    __shared__ DRec sm[D_TS];   // the block's point tile
+    __shared__ float sx[TRUNC ? 4 : 1][D_TS];   // truncated: its FP32 coordinates and alpha
+    __shared__ unsigned s_live[D_THREADS / 32];   // truncated: live sub-tiles of each warp
+    // truncated: a thread takes two consecutive (sorted) targets, a warp 64 (one ball)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t j[2];
-    j[0] = (int64_t)blockIdx.x * D_ROWS + threadIdx.x;   // < n_alloc
-    j[1] = j[0] + D_THREADS;
+    j[0] = (int64_t)blockIdx.x * D_ROWS + (TRUNC ? 2 * threadIdx.x : threadIdx.x);   // < n_alloc
+    j[1] = j[0] + (TRUNC ? 1 : D_THREADS);
     Op2 W[3];
     f2 Ch, Ct;
     load_ops(trec[j[0]], trec[j[1]], W, Ch, Ct);
@@ -390,45 +545,97 @@ __global__ void __launch_bounds__(D_THREADS)
     const int64_t p_begin = (int64_t)blockIdx.y * chunk;
     const int64_t p_end = min(nq_pad, p_begin + chunk);
     double acc0 = 0.0, acc1 = 0.0;
-    for (int64_t p0 = p_begin; p0 < p_end; p0 += D_TS) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
-            sm[i] = prec[p0 + i];
-            if (TRUNC) {
+    // truncated: the warp's 64 targets against each sub-tile of 8 points (ball
+    // classes, bit maps lv / bd): outside sub-tiles are skipped, inside ones need
+    // no pair test; a tile no warp needs is not loaded
+    const int64_t wblk = (int64_t)blockIdx.x * (D_ROWS / 64) + warp;
+    const float4 wb = TRUNC ? tball64[wblk] : make_float4(0.f, 0.f, 0.f, -1.f);
+    const float2 wr = TRUNC ? tbe64[wblk] : make_float2(0.f, 0.f);
+    if constexpr (!TRUNC) {
+        for (int64_t p0 = p_begin; p0 < p_end; p0 += D_TS) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < D_TS; i += D_THREADS) sm[i] = prec[p0 + i];
+            __syncthreads();
+            f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
+    #pragma unroll 2
+            for (int i = 0; i < D_TS; ++i) {
+                const DRec &B = sm[i];
+                f2 rh, rt;
+                df_exponent2<D>(W, B, Ch, Ct, rh, rt);
+                f2 th, te;
+                two_sum2(rh, lo2(B.d), th, te);
+                const f2 e = make_float2(ex2_approx(th.x), ex2_approx(th.y));
+                kahan2(s, comp, e);
+                cs = fma2(e, add2(add2(te, rt), hi2(B.d)), cs);
+            }
+            acc0 += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
+            acc1 += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
+        }
+    } else {
+        // the warp's 64 targets against every sub-tile of 8 points of each tile of
+        // the chunk (ball classes, bit maps lv / bd): outside sub-tiles are
+        // skipped, inside ones need no pair test; a tile that no warp of the
+        // block needs is not loaded
+        for (int64_t p0 = p_begin; p0 < p_end; p0 += D_TS) {
+            int c = 0;
+            if (lane < D_TS / D_SUB) {
+                const int64_t sb = p0 / D_SUB + lane;
+                c = tp_class(wb, pball8[sb], wr, pal8[sb]);
+            }
+            const unsigned lv = __ballot_sync(0xffffffffu, c != 0);
+            const unsigned bd = __ballot_sync(0xffffffffu, c == 2);
+            __syncthreads();   // the previous tile's readers are done
+            if (lane == 0) s_live[warp] = lv;
+            __syncthreads();
+            unsigned any = 0;
+            for (int w = 0; w < D_THREADS / 32; ++w) any |= s_live[w];
+            if (!any) continue;   // block-uniform
+            for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
+                sm[i] = prec[p0 + i];
                 for (int t = 0; t < 3; ++t) sx[t][i] = t < D ? xs[t * nq_pad + p0 + i] : 0.f;
-                sx[3][i] = (float)alpha[p0 + i];
+                sx[3 % (TRUNC ? 4 : 1)][i] = alphaf[p0 + i];
             }
-        }
-        __syncthreads();
-        f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
+            __syncthreads();
+            if (!lv) continue;   // warp-uniform: the next tile's first barrier waits for the others
+            f2 s = make_float2(0.f, 0.f), comp = s, cs = s;
+            for (unsigned mm = lv; mm; mm &= mm - 1) {
+                const int sub = __ffs(mm) - 1;
+                const bool test = (bd >> sub) & 1u;
+                const int u0 = sub * D_SUB;
 #pragma unroll 2
-        for (int i = 0; i < D_TS; ++i) {
-            const DRec &B = sm[i];
-            f2 rh, rt;
-            df_exponent2<D>(W, B, Ch, Ct, rh, rt);
-            f2 th, te;
-            two_sum2(rh, lo2(B.d), th, te);
-            f2 e = make_float2(ex2_approx(th.x), ex2_approx(th.y));
-            if (TRUNC) {
-                const float xf[3] = {sx[0][i], sx[1][i], sx[2][i]};
-                const int64_t qq = p0 + i;
-                if (!(qq < nq && j[0] < n &&
-                      keep_pair<D>(xf, yf[0], sx[3][i], bf[0], span2, x64 + qq * D, y64 + j[0] * D,
-                                   alpha[qq], beta + j[0])))
-                    e.x = 0.f;
-                if (!(qq < nq && j[1] < n &&
-                      keep_pair<D>(xf, yf[1], sx[3][i], bf[1], span2, x64 + qq * D, y64 + j[1] * D,
-                                   alpha[qq], beta + j[1])))
-                    e.y = 0.f;
+                for (int i = u0; i < u0 + D_SUB; ++i) {
+                    const int64_t qq = p0 + i;
+                    const DRec &B = sm[i];
+                    f2 rh, rt;
+                    df_exponent2<D>(W, B, Ch, Ct, rh, rt);
+                    f2 th, te;
+                    two_sum2(rh, lo2(B.d), th, te);
+                    f2 e = make_float2(ex2_approx(th.x), ex2_approx(th.y));
+                    if (test) {
+                        const float xf[3] = {sx[0][i], sx[1 % (TRUNC ? 4 : 1)][i], sx[2 % (TRUNC ? 4 : 1)][i]};
+                        const float af = sx[3 % (TRUNC ? 4 : 1)][i];
+                        if (!(qq < nq && j[0] < n &&
+                              keep_pair<D>(xf, yf[0], af, bf[0], span2, x64 + qq * D, y64 + j[0] * D,
+                                           alpha[qq], beta + j[0])))
+                            e.x = 0.f;
+                        if (!(qq < nq && j[1] < n &&
+                              keep_pair<D>(xf, yf[1], af, bf[1], span2, x64 + qq * D, y64 + j[1] * D,
+                                           alpha[qq], beta + j[1])))
+                            e.y = 0.f;
+                    }
+                    kahan2(s, comp, e);
+                    cs = fma2(e, add2(add2(te, rt), hi2(B.d)), cs);
+                }
             }
-            kahan2(s, comp, e);
-            cs = fma2(e, add2(add2(te, rt), hi2(B.d)), cs);
+            acc0 += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
+            acc1 += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
         }
-        acc0 += ((double)s.x - (double)comp.x) + kLn2 * (double)cs.x;
-        acc1 += ((double)s.y - (double)comp.y) + kLn2 * (double)cs.y;
     }
-    part2[(int64_t)blockIdx.y * n_alloc + j[0]] = acc0;
-    part2[(int64_t)blockIdx.y * n_alloc + j[1]] = acc1;
+    // truncated: j is a sorted index, the partial goes to the caller's target
+    const int64_t o0 = (TRUNC && j[0] < n) ? (int64_t)perm[j[0]] : j[0];
+    const int64_t o1 = (TRUNC && j[1] < n) ? (int64_t)perm[j[1]] : j[1];
+    part2[(int64_t)blockIdx.y * n_alloc + o0] = acc0;
+    part2[(int64_t)blockIdx.y * n_alloc + o1] = acc1;
 }
 
 int occupancy_df(const void *f) {
@@ -472,33 +679,74 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, bool t
     // squared extent of the translated coordinates: bounds their FP32 rounding
     const float span2 = (float)p->diam2;
     const double *alpha = trunc ? p->alpha : nullptr, *beta = trunc ? p->beta : nullptr;
+    // truncated: targets in the cell list's order, blocks classified by balls
+    SortedTargets T;
+    const float *ys = p->df_ys;
+    const double *y64 = p->y64;
+    if (trunc) {
+        if ((e = trunc_sorted_targets(p, &T))) return e;
+        const int d = p->d;
+        auto nb = [](int64_t m) { return (unsigned)((m + 255) / 256); };
+        if (!p->df_ys_s) {
+            if ((e = cudaMalloc(&p->df_ys_s, (size_t)3 * p->n_pad * sizeof(float)))) return e;
+            if ((e = cudaMalloc(&p->df_beta_s, (size_t)p->n_pad * sizeof(double)))) return e;
+            if ((e = cudaMalloc(&p->df_beta_sf, (size_t)p->n_pad * sizeof(float)))) return e;
+            if ((e = cudaMalloc(&p->df_alpha_f, (size_t)p->nq_pad * sizeof(float)))) return e;
+            if ((e = cudaMalloc(&p->df_pb64, (size_t)(p->nq_pad / 64) * sizeof(float4)))) return e;
+            if ((e = cudaMalloc(&p->df_pb8, (size_t)(p->nq_pad / 8) * sizeof(float4)))) return e;
+            if ((e = cudaMalloc(&p->df_pa64, (size_t)(p->nq_pad / 64) * sizeof(float2)))) return e;
+            if ((e = cudaMalloc(&p->df_pa8, (size_t)(p->nq_pad / 8) * sizeof(float2)))) return e;
+            if ((e = cudaMalloc(&p->df_tbe64, (size_t)(p->n_pad / 64) * sizeof(float2)))) return e;
+            if ((e = cudaMalloc(&p->df_tbe8, (size_t)(p->n_pad / 8) * sizeof(float2)))) return e;
+            k_df_coords<<<nb(p->n_pad), 256, 0, st>>>(T.y64, p->n, p->n_pad, d, p->df_ys_s);
+            k_df_balls<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->x64, p->nq, d, 64, p->nq_pad / 64, p->df_pb64);
+            k_df_balls<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->x64, p->nq, d, 8, p->nq_pad / 8, p->df_pb8);
+        }
+        k_df_gather<<<nb(p->n_pad), 256, 0, st>>>(p->beta, T.perm, p->n, p->n_pad, p->df_beta_s,
+                                                  p->df_beta_sf);
+        k_df_gather<<<nb(p->nq_pad), 256, 0, st>>>(p->alpha, nullptr, p->nq, p->nq_pad, nullptr,
+                                                   p->df_alpha_f);
+        k_df_ranges<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->alpha, nullptr, p->nq, 64, p->nq_pad / 64,
+                                                         p->df_pa64);
+        k_df_ranges<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->alpha, nullptr, p->nq, 8, p->nq_pad / 8, p->df_pa8);
+        k_df_ranges<<<nb(p->n_pad / 64), 256, 0, st>>>(p->beta, T.perm, p->n, 64, p->n_pad / 64, p->df_tbe64);
+        k_df_ranges<<<nb(p->n_pad / 8), 256, 0, st>>>(p->beta, T.perm, p->n, 8, p->n_pad / 8, p->df_tbe8);
+        ys = p->df_ys_s;
+        y64 = T.y64;
+        beta = p->df_beta_s;
+        if ((e = cudaGetLastError())) return e;
+    }
     trace_begin(p, "prep_df");
     k_prep_df<<<p->nblk_prep, 256, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad, p->d, eps,
-                                           trec, p->psinu, p->flags);
+                                           trunc ? T.perm : nullptr, trec, p->psinu, p->flags);
     trace_end(p);
     const unsigned nb1 = (unsigned)(p->nq_pad / D_ROWS);
     trace_begin(p, "lse_df");
     if (trunc)
-        k_lse_df<D, true><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec,
-                                                     p->df_ys, p->y64, p->n, p->n_pad, alpha, beta,
-                                                     span2, p->lmass2, p->mass, psi, eps,
-                                                     p->blockJ, p->lse_buf, p->res_dev);
+        k_lse_df<D, true><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec, ys, y64,
+                                                     p->n, p->n_pad, alpha, beta, span2, p->lmass2,
+                                                     p->mass, psi, eps, p->blockJ, p->lse_buf, p->res_dev,
+                                                     p->df_pb64, p->df_pa64, T.ball8, p->df_tbe8,
+                                                     p->df_beta_sf);
     else
-        k_lse_df<D, false><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec,
-                                                      p->df_ys, p->y64, p->n, p->n_pad, alpha, beta,
-                                                      span2, p->lmass2, p->mass, psi, eps,
-                                                      p->blockJ, p->lse_buf, p->res_dev);
+        k_lse_df<D, false><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec, ys,
+                                                      y64, p->n, p->n_pad, alpha, beta, span2,
+                                                      p->lmass2, p->mass, psi, eps, p->blockJ,
+                                                      p->lse_buf, p->res_dev, nullptr, nullptr,
+                                                      nullptr, nullptr, nullptr);
     trace_end(p);
     dim3 g2((unsigned)tblocks, (unsigned)s2);
     trace_begin(p, "grad_df");
     if (trunc)
-        k_grad_df<D, true><<<g2, D_THREADS, 0, st>>>(trec, p->df_ys, p->y64, p->n, p->n_pad, prec,
-                                                     p->xs, p->x64, p->nq, p->nq_pad, chunk, alpha,
-                                                     beta, span2, p->df_part2);
+        k_grad_df<D, true><<<g2, D_THREADS, 0, st>>>(trec, ys, y64, p->n, p->n_pad, prec, p->xs, p->x64,
+                                                     p->nq, p->nq_pad, chunk, alpha, beta, span2,
+                                                     p->df_part2, T.perm, T.ball64, p->df_tbe64,
+                                                     p->df_pb8, p->df_pa8, p->df_alpha_f);
     else
-        k_grad_df<D, false><<<g2, D_THREADS, 0, st>>>(trec, p->df_ys, p->y64, p->n, p->n_pad, prec,
-                                                      p->xs, p->x64, p->nq, p->nq_pad, chunk, alpha,
-                                                      beta, span2, p->df_part2);
+        k_grad_df<D, false><<<g2, D_THREADS, 0, st>>>(trec, ys, y64, p->n, p->n_pad, prec, p->xs,
+                                                      p->x64, p->nq, p->nq_pad, chunk, alpha, beta,
+                                                      span2, p->df_part2, nullptr, nullptr, nullptr,
+                                                      nullptr, nullptr, nullptr);
     trace_end(p);
     if ((e = cudaGetLastError())) return e;
     return launch_finalize_log2(p, psi, eps, p->df_part2, (int)s2, (int)nb1, grad);
@@ -523,6 +771,14 @@ void compensated_free(rsot_problem *p) {
     p->df_ys = nullptr;
     p->df_part2 = nullptr;
     p->df_s2 = 0;
+    void *blk[] = {p->df_ys_s, p->df_beta_s, p->df_pb64, p->df_pb8, p->df_pa64, p->df_pa8,
+                   p->df_tbe64, p->df_tbe8, p->df_beta_sf, p->df_alpha_f};
+    for (void *q : blk) cudaFree(q);
+    p->df_ys_s = nullptr;
+    p->df_beta_s = nullptr;
+    p->df_beta_sf = p->df_alpha_f = nullptr;
+    p->df_pb64 = p->df_pb8 = nullptr;
+    p->df_pa64 = p->df_pa8 = p->df_tbe64 = p->df_tbe8 = nullptr;
 }
 
 }  // namespace rsot

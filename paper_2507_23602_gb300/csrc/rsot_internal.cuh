@@ -117,6 +117,16 @@ struct rsot_problem {
     float *df_ys = nullptr;         // [3][n_pad] FP32 target coordinates
     double *df_part2 = nullptr;     // [df_s2][n_pad] pass-2 partials
     int df_s2 = 0;
+    // truncated compensated passes: targets in the Morton order of the cell list,
+    // blocks classified by balls (rsot_df.cu)
+    float *df_ys_s = nullptr;       // [3][n_pad] FP32 sorted target coordinates (once)
+    double *df_beta_s = nullptr;    // [n_pad] beta in sorted order (per evaluation)
+    float *df_beta_sf = nullptr;    // [n_pad] the same rounded to FP32
+    float *df_alpha_f = nullptr;    // [nq_pad] alpha rounded to FP32 (caller order)
+    float4 *df_pb64 = nullptr;      // [nq_pad / 64] balls of 64 caller-order points (once)
+    float4 *df_pb8 = nullptr;       // [nq_pad / 8] balls of 8 caller-order points (once)
+    float2 *df_pa64 = nullptr, *df_pa8 = nullptr;    // alpha ranges of those point blocks
+    float2 *df_tbe64 = nullptr, *df_tbe8 = nullptr;  // beta ranges of 64 / 8 sorted targets
 
     // truncation cutoffs per pair, c(x_q, y_j) < alpha_q + beta_j (rsot_cutoff.cu)
     int *nn = nullptr;              // [nq] nearest target of each point (once per problem)
@@ -218,6 +228,15 @@ cudaError_t trunc_eval(rsot_problem *p, const double *psi_dev, double eps, int m
                        double *grad_dev);
 void trunc_free(rsot_problem *p);
 cudaError_t trunc_point_L(rsot_problem *p, double *L_dev);
+// the cell list's target order for the compensated passes (grid built on first
+// use): perm (sorted -> caller index, -1 for padding), sorted FP64 coordinates
+// [n_pad][d], balls of 8 and of 64 sorted targets [n_pad / 8], [n_pad / 64]
+struct SortedTargets {
+    const int *perm = nullptr;
+    const double *y64 = nullptr;
+    const float4 *ball8 = nullptr, *ball64 = nullptr;
+};
+cudaError_t trunc_sorted_targets(rsot_problem *p, SortedTargets *out);
 
 // ---- device helpers ----------------------------------------------------------
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -285,6 +304,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
     for (long long i = 0; i < kWaitLimit; ++i)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
+}
+
+// Classification of a block pair for the truncated passes: balls a, b (centre,
+// radius; radius < 0: no member) of the two blocks and the (min, max) of their
+// members' cutoff terms ra, rb (alpha of points, beta of targets; the pair is
+// kept when |x - y|^2 / 2 < alpha_q + beta_j).  0: every pair outside, 1: every
+// pair inside, 2: boundary (each pair tested).  The radii are widened /
+// narrowed by 1e-4 relative, far more than the rounding of the pairwise tests.
+// square root on the SFU (sqrt.approx, relative error about 2^-23): far inside
+// the classification margins of 1e-4 relative
+__device__ __forceinline__ float sqrt_sfu(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ int tp_class(float4 a, float4 b, float2 ra, float2 rb) {
+    if (a.w < 0.f || b.w < 0.f) return 0;
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float dist = sqrt_sfu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float Rout = sqrt_sfu(fmaxf(0.f, 2.f * (ra.y + rb.y))) * (1.0f + 1e-4f) + 1e-6f;
+    if (dist - a.w - b.w >= Rout) return 0;
+    const float Rin = sqrt_sfu(fmaxf(0.f, 2.f * (ra.x + rb.x))) * (1.0f - 1e-4f) - 1e-6f;
+    if (dist + a.w + b.w < Rin) return 1;
+    return 2;
 }
 
 // Block-wide FP64 sum (blockDim.x a multiple of 32, <= 1024); result in thread 0.

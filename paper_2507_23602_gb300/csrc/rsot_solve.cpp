@@ -133,6 +133,9 @@ struct CorrectedEvaluator {
 // iterations without halving the corrected objective's gradient after which
 // a correction's mixed run stops at its rounding noise
 constexpr int kCorrStallWindow = 25;
+// largest tail tolerance at which the compensated reference evaluations are
+// truncated (its bound stays far below any useful tolerance)
+constexpr double kRefTailMax = 1e-8;
 
 double norm1(const std::vector<double> &a) {
     double s = 0.0;
@@ -209,8 +212,17 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     // intermediate eps stages only warm-start the next one: 100 tol_l1 unless given
     const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : rsot::kStageTolFactor * opt->tol_l1;
     // reference evaluations of the final stop: compensated with its certified
-    // bound subtracted from tol where the bound leaves room, else FP64
-    const double comp_bound = RSOT_COMPENSATED_GRAD_REL * rsot::mass_sum(p);
+    // bound subtracted from tol where the bound leaves room, else FP64.  With a
+    // tail tolerance (psi-aware cutoffs) the compensated references are
+    // truncated too and the truncation's own bound joins: per point at most
+    // tail * sum(nu) of the kept mass is lost, so ||grad J~ - grad J||_1 <=
+    // tail * sum(nu) * (2 sum(m) + sum(nu))
+    const double msum = rsot::mass_sum(p);
+    double nusum = 0.0;
+    for (int64_t j = 0; j < n; ++j) nusum += nu[j];
+    const double ref_tail = (opt->tail > 0.0 && opt->tail <= kRefTailMax && opt->tau_int <= 0.0) ? opt->tail : 0.0;
+    const double comp_bound =
+        RSOT_COMPENSATED_GRAD_REL * msum + ref_tail * nusum * (2.0 * msum + nusum);
     const bool comp_ref = opt->refine_precision == RSOT_COMPENSATED && comp_bound <= 0.8 * opt->tol_l1;
     const rsot_precision ref_prec = comp_ref ? RSOT_COMPENSATED : RSOT_FP64;
     const double ref_tol = comp_ref ? opt->tol_l1 - comp_bound : opt->tol_l1;
@@ -258,10 +270,11 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             // in kCorrStallWindow iterations); then L-BFGS on compensated
             // evaluations finishes from there (the D-scaled first step is
             // Newton-like near the optimum: a few iterations)
-            // reference evaluations are dense: the stop holds for the untruncated J
-            // (a truncated mixed phase differs by tail-level terms, which the
-            // correction absorbs)
-            Evaluator evc{p, n, eps, 0.0, RSOT_COMPENSATED, 0.0};
+            // reference evaluations: dense, or truncated at the solve's tail with
+            // its bound inside comp_bound (the stop then holds for the
+            // untruncated J); a truncated mixed phase differs by tail-level
+            // terms, which the correction absorbs
+            Evaluator evc{p, n, eps, ref_tail, RSOT_COMPENSATED, 0.0};
             Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
             const int kernel_before = rsot::pair_kernel_of(p);
             rsot_set_pair_kernel(p, RSOT_PAIRS_FP32);

@@ -665,24 +665,6 @@ __global__ void __launch_bounds__(L_THREADS, 3)
 // FP32 on the mma result, as the weight of tp_incl).  The classification margins (1e-4 R) exceed the
 // rounding of the pairwise test, so a classified pair gets the decision the
 // test would give and both passes sum over the same pairs.
-// square root on the SFU (sqrt.approx, relative error about 2^-23): far inside
-// the classification margins of 1e-4 relative
-__device__ __forceinline__ float sqrt_sfu(float x) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ int tp_class(float4 a, float4 b, float2 ra, float2 rb) {
-    if (a.w < 0.f || b.w < 0.f) return 0;
-    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    const float dist = sqrt_sfu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float Rout = sqrt_sfu(fmaxf(0.f, 2.f * (ra.y + rb.y))) * (1.0f + 1e-4f) + 1e-6f;
-    if (dist - a.w - b.w >= Rout) return 0;
-    const float Rin = sqrt_sfu(fmaxf(0.f, 2.f * (ra.x + rb.x))) * (1.0f - 1e-4f) - 1e-6f;
-    if (dist + a.w + b.w < Rin) return 1;
-    return 2;
-}
 
 // The per-pair test of a boundary block, on the FMA pipe.  A pair is kept when
 // its test value v = r_qj - (b_j - 2k beta_j) exceeds A_q = k|x'_q|^2 - 2k alpha_q;
@@ -1741,6 +1723,19 @@ cudaError_t trunc_eval(rsot_problem *p, const double *psi, double eps, int mixed
     // the target prep writes one psi.nu partial per 256 sorted targets
     if ((int64_t)p->nblk_prep * 256 < p->grid->nt) return cudaErrorInvalidValue;
     return p->d == 3 ? trunc_mixed<3>(p, psi, eps, grad) : trunc_mixed<2>(p, psi, eps, grad);
+}
+
+cudaError_t trunc_sorted_targets(rsot_problem *p, SortedTargets *out) {
+    if (!p->grid) {
+        cudaError_t e = grid_build(p);
+        if (e) return e;
+    }
+    if (p->grid->nt != p->n_pad) return cudaErrorInvalidValue;   // both pad to whole 1,024s
+    out->perm = p->grid->perm_t;
+    out->y64 = p->grid->y64;
+    out->ball8 = p->grid->tball8;
+    out->ball64 = p->grid->tball64;
+    return cudaSuccess;
 }
 
 cudaError_t trunc_point_L(rsot_problem *p, double *L) {

@@ -152,8 +152,9 @@ def test_solve_with_tail_meets_tolerance_against_dense():
         tail = 1e-10
         psi, st = P.solve(eps=p.eps, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, tail=tail)
         assert st.status == 0
-        # the refinement's reference evaluations are dense: the dense gradient meets
-        # tol (certified); the truncated one within the tail bound of it
+        # the refinement's compensated reference evaluations are truncated at the
+        # tail, its bound subtracted from tol: the dense gradient meets tol
+        # (certified); the truncated one within the tail bound of it
         _, gd, _, _ = oracle.dual_grad(p.x, p.mass, p.y, p.nu, psi, p.eps)
         assert np.abs(gd).sum() <= 1e-6
         a, b = truncation.separable_cutoffs(p.x, p.y, p.nu, psi, p.eps, tail)
