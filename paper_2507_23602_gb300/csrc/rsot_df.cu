@@ -148,37 +148,16 @@ __device__ __forceinline__ void load_ops(const DRec &r0, const DRec &r1, Op2 *R,
 // errors (|c_32 - c| <= 2^-19 |coords|^2 + 2^-23 c from the rounded translated
 // coordinates, their differences and squares; 2^-23 (|alpha| + |beta|) from the
 // rounded cutoff; taken 4x); the FP64 test of the FP64 path decides inside it
-template <int D>
-__device__ __forceinline__ bool keep_pair(const float *xf, const float *yf, float af, float bf,
-                                          float span2, const double *x64, const double *y64,
-                                          double a64, const double *b64) {
-    float c2 = 0.f;
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-        const float dd = xf[t] - yf[t];
-        c2 = fmaf(dd, dd, c2);
-    }
-    const float c32 = 0.5f * c2;
-    const float C = af + bf;
-    const float margin = fmaf(0x1p-17f, span2 + fabsf(C), 0x1p-21f * (fabsf(af) + fabsf(bf)));
-    if (fabsf(c32 - C) > margin) return c32 < C;
-    double c = 0.0;
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-        const double dd = x64[t] - y64[t];
-        c += dd * dd;
-    }
-    c *= 0.5;
-    return c < a64 + *b64;
-}
-
 // per-target records (rounded from FP64) and the block partials of sum psi nu
 // (perm non-null: record j is target perm[j], the cell list's order)
+// (nb non-null: nb[j] = b_j - 2k beta_j in FP32, the target's term of the
+// truncation test on the exponent; +inf for padding)
 __global__ void k_prep_df(const double *__restrict__ psi, const double *__restrict__ y64,
                           const double *__restrict__ lnu, const double *__restrict__ nu, int64_t n,
                           int64_t n_alloc, int d, double eps, const int *__restrict__ perm,
                           DRec *__restrict__ trec, double *__restrict__ psinu_part,
-                          int *__restrict__ flags) {
+                          int *__restrict__ flags, const double *__restrict__ beta,
+                          float *__restrict__ nb) {
     __shared__ double sh[32];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double k = kLog2e / (2.0 * eps);
@@ -198,6 +177,9 @@ __global__ void k_prep_df(const double *__restrict__ psi, const double *__restri
             }
             split_f(fmax(b - k * yy, -1.0e29), v[6], v[7]);
             contrib = ps * nu[o];
+            if (nb) nb[j] = (float)(b - 2.0 * k * beta[o]);
+        } else if (nb) {
+            nb[j] = INFINITY;
         }
         trec[j] = make_drec(v);
     }
@@ -262,19 +244,48 @@ __global__ void k_df_gather(const double *__restrict__ v, const int *__restrict_
     if (outf) outf[s] = (float)x;
 }
 
-// FP32 coordinates [3][n_alloc] of the rows c64 [n][d] (1e30 beyond)
-__global__ void k_df_coords(const double *__restrict__ c64, int64_t n, int64_t n_alloc, int d,
-                            float *__restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_alloc)
-        for (int t = 0; t < 3; ++t) out[t * n_alloc + i] = (i < n && t < d) ? (float)c64[i * d + t] : 1.0e30f;
+// A[q] = k |x'_q|^2 - 2k alpha_q in FP32, the point's term of the truncation
+// test on the exponent (+inf for padding)
+__global__ void k_df_A(const double *__restrict__ x64, const double *__restrict__ alpha, int64_t nq,
+                       int64_t nq_pad, int d, double k, float *__restrict__ A) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq_pad) return;
+    if (q >= nq) {
+        A[q] = INFINITY;
+        return;
+    }
+    double r2 = 0.0;
+    for (int t = 0; t < d; ++t) r2 += x64[q * d + t] * x64[q * d + t];
+    A[q] = (float)(k * r2 - 2.0 * k * alpha[q]);
 }
 
-// static point records (x' head/tail; the shift is written by pass 1) and
-// FP32 target coordinates [3][n_alloc] for the truncation test
-__global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
-                            const double *__restrict__ y64, int64_t n, int64_t n_alloc, int d,
-                            DRec *__restrict__ prec, float *__restrict__ ys) {
+// The truncation test of a pair from its exponent: the pair is kept when
+// c(x_q, y_j) < alpha_q + beta_j, i.e. r_qj > nb_j + A_q (r_qj = b_j - 2k c_qj
+// + k |x'_q|^2 in the log2 domain).  With the double-float head rh of r_qj and
+// nb_j, A_q rounded to FP32, the sign of rh - nb_j - A_q decides wherever it
+// exceeds 2^-20 of the magnitudes (the FP32 and double-float errors are below
+// 2^-22 of them); inside that band the FP64 cost decides (keep_fp64, the FP64
+// path's own expression), so the kept pairs are exactly the FP64 path's.
+// 1: kept, 0: excluded, -1: the FP64 test decides.
+__device__ __forceinline__ int exp_test(float rh, float nb, float A) {
+    const float v = (rh - nb) - A;
+    const float mg = 0x1p-20f * (fabsf(rh) + fabsf(nb) + fabsf(A)) + 0x1p-100f;
+    return v > mg ? 1 : (v < -mg ? 0 : -1);
+}
+template <int D>
+__device__ __forceinline__ bool keep_fp64(const double *x64, const double *y64, double a64, double b64) {
+    double c = 0.0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        const double dd = x64[t] - y64[t];
+        c += dd * dd;
+    }
+    return 0.5 * c < a64 + b64;
+}
+
+// static point records (x' head/tail; the shift is written by pass 1)
+__global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t nq_pad, int d,
+                            DRec *__restrict__ prec) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nq_pad) {
         float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, kExcl, 0.f};
@@ -282,9 +293,6 @@ __global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t 
             for (int t = 0; t < d; ++t) split_f(x64[i * d + t], v[2 * t], v[2 * t + 1]);
         prec[i] = make_drec(v);
     }
-    if (i < n_alloc)
-        for (int t = 0; t < 3; ++t)
-            ys[t * n_alloc + i] = (i < n && t < d) ? (float)y64[i * d + t] : 1.0e30f;
 }
 
 // Pass 1: R_q = log2 sum_{j in I_q} 2^{r_qj} with an integral running shift M,
@@ -292,18 +300,17 @@ __global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t 
 // of a thread is point blockIdx.x * D_ROWS + l * D_THREADS + threadIdx.x.
 template <int D, bool TRUNC>
 __global__ void __launch_bounds__(D_THREADS)
-    k_lse_df(DRec *__restrict__ prec, const float *__restrict__ xs, const double *__restrict__ x64,
-             int64_t nq, int64_t nq_pad, const DRec *__restrict__ trec,
-             const float *__restrict__ ys, const double *__restrict__ y64, int64_t n,
-             int64_t n_alloc, const double *__restrict__ alpha, const double *__restrict__ beta,
-             float span2, const double *__restrict__ lmass2, const double *__restrict__ mass,
+    k_lse_df(DRec *__restrict__ prec, const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
+             const DRec *__restrict__ trec, const double *__restrict__ y64, int64_t n,
+             const double *__restrict__ alpha, const double *__restrict__ beta,
+             const double *__restrict__ lmass2, const double *__restrict__ mass,
              const double *__restrict__ psi, double eps, double *__restrict__ blockJ,
              double *__restrict__ lse_buf, EvalResult *__restrict__ res,
              const float4 *__restrict__ pball64, const float2 *__restrict__ pal64,
              const float4 *__restrict__ tball8, const float2 *__restrict__ tbe8,
-             const float *__restrict__ betaf) {
+             const float *__restrict__ nbs, const float *__restrict__ Aq) {
     __shared__ DRec sm[D_TS];   // the block's target tile
-    __shared__ float sy[TRUNC ? 4 : 1][D_TS];   // truncated: its FP32 coordinates and beta
+    __shared__ float snb[D_TS];   // truncated: the tile's nb_j (exp_test)
     __shared__ unsigned s_live[D_THREADS / 32];   // truncated: live sub-tiles of each warp
     __shared__ double sh[32];
     __shared__ unsigned long long s_cnt, s_empty;
@@ -317,11 +324,11 @@ __global__ void __launch_bounds__(D_THREADS)
     Op2 X[3];
     f2 unused_h, unused_t;
     load_ops(p0, p1, X, unused_h, unused_t);
-    float xf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float Ap[2] = {0.f, 0.f};   // truncated: A_q of the two points (exp_test)
     double a64[2] = {0.0, 0.0};
     if (TRUNC)
         for (int l = 0; l < 2; ++l) {
-            for (int t = 0; t < D; ++t) xf[l][t] = xs[t * nq_pad + q[l]];
+            Ap[l] = Aq[q[l]];
             a64[l] = alpha[q[l]];
         }
     const int64_t n_rec = (n + D_TS - 1) / D_TS * D_TS;
@@ -404,8 +411,7 @@ __global__ void __launch_bounds__(D_THREADS)
             if (!any) continue;   // block-uniform
             for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
                 sm[i] = trec[t0 + i];
-                for (int t = 0; t < 3; ++t) sy[t][i] = ys[t * n_alloc + t0 + i];
-                sy[3 % (TRUNC ? 4 : 1)][i] = betaf[t0 + i];
+                snb[i] = nbs[t0 + i];
             }
             __syncthreads();
             if (!lv) continue;   // warp-uniform: the next tile's first barrier waits for the others
@@ -421,13 +427,12 @@ __global__ void __launch_bounds__(D_THREADS)
                     const int64_t j = t0 + u0 + i;
                     const DRec &B = sm[u0 + i];
                     df_exponent2<D>(X, B, lo2(B.d), hi2(B.d), rh[i], rt[i]);
-                    const float yf[3] = {sy[0][u0 + i], sy[1 % (TRUNC ? 4 : 1)][u0 + i],
-                                         sy[2 % (TRUNC ? 4 : 1)][u0 + i]};
                     for (int l = 0; l < 2; ++l) {
-                        const bool k = j < n && q[l] < nq &&
-                                       (!test || keep_pair<D>(xf[l], yf, (float)a64[l],
-                                                              sy[3 % (TRUNC ? 4 : 1)][u0 + i], span2,
-                                                              x64 + q[l] * D, y64 + j * D, a64[l], beta + j));
+                        bool k = j < n && q[l] < nq;
+                        if (k && test) {
+                            const int e = exp_test(l ? rh[i].y : rh[i].x, snb[u0 + i], Ap[l]);
+                            k = e > 0 || (e < 0 && keep_fp64<D>(x64 + q[l] * D, y64 + j * D, a64[l], beta[j]));
+                        }
                         if (k) {
                             ++npair;
                         } else if (l == 0) {
@@ -515,17 +520,15 @@ __global__ void __launch_bounds__(D_THREADS)
 // Lane l of a thread is target blockIdx.x * D_ROWS + l * D_THREADS + threadIdx.x.
 template <int D, bool TRUNC>
 __global__ void __launch_bounds__(D_THREADS)
-    k_grad_df(const DRec *__restrict__ trec, const float *__restrict__ ys,
-              const double *__restrict__ y64, int64_t n, int64_t n_alloc,
-              const DRec *__restrict__ prec, const float *__restrict__ xs,
-              const double *__restrict__ x64, int64_t nq, int64_t nq_pad, int64_t chunk,
-              const double *__restrict__ alpha, const double *__restrict__ beta, float span2,
-              double *__restrict__ part2, const int *__restrict__ perm,
+    k_grad_df(const DRec *__restrict__ trec, const double *__restrict__ y64, int64_t n,
+              int64_t n_alloc, const DRec *__restrict__ prec, const double *__restrict__ x64,
+              int64_t nq, int64_t nq_pad, int64_t chunk, const double *__restrict__ alpha,
+              const double *__restrict__ beta, double *__restrict__ part2, const int *__restrict__ perm,
               const float4 *__restrict__ tball64, const float2 *__restrict__ tbe64,
               const float4 *__restrict__ pball8, const float2 *__restrict__ pal8,
-              const float *__restrict__ alphaf) {
+              const float *__restrict__ Aq, const float *__restrict__ nbs) {
     __shared__ DRec sm[D_TS];   // the block's point tile
-    __shared__ float sx[TRUNC ? 4 : 1][D_TS];   // truncated: its FP32 coordinates and alpha
+    __shared__ float sA[D_TS];   // truncated: the tile's A_q (exp_test)
     __shared__ unsigned s_live[D_THREADS / 32];   // truncated: live sub-tiles of each warp
     // truncated: a thread takes two consecutive (sorted) targets, a warp 64 (one ball)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -535,13 +538,9 @@ __global__ void __launch_bounds__(D_THREADS)
     Op2 W[3];
     f2 Ch, Ct;
     load_ops(trec[j[0]], trec[j[1]], W, Ch, Ct);
-    float yf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float bf[2] = {0.f, 0.f};
+    float nbl[2] = {0.f, 0.f};   // truncated: nb_j of the two targets (exp_test)
     if (TRUNC)
-        for (int l = 0; l < 2; ++l) {
-            for (int t = 0; t < D; ++t) yf[l][t] = ys[t * n_alloc + j[l]];
-            bf[l] = (float)beta[j[l]];
-        }
+        for (int l = 0; l < 2; ++l) nbl[l] = nbs[j[l]];
     const int64_t p_begin = (int64_t)blockIdx.y * chunk;
     const int64_t p_end = min(nq_pad, p_begin + chunk);
     double acc0 = 0.0, acc1 = 0.0;
@@ -592,8 +591,7 @@ __global__ void __launch_bounds__(D_THREADS)
             if (!any) continue;   // block-uniform
             for (int i = threadIdx.x; i < D_TS; i += D_THREADS) {
                 sm[i] = prec[p0 + i];
-                for (int t = 0; t < 3; ++t) sx[t][i] = t < D ? xs[t * nq_pad + p0 + i] : 0.f;
-                sx[3 % (TRUNC ? 4 : 1)][i] = alphaf[p0 + i];
+                sA[i] = Aq[p0 + i];
             }
             __syncthreads();
             if (!lv) continue;   // warp-uniform: the next tile's first barrier waits for the others
@@ -612,16 +610,19 @@ __global__ void __launch_bounds__(D_THREADS)
                     two_sum2(rh, lo2(B.d), th, te);
                     f2 e = make_float2(ex2_approx(th.x), ex2_approx(th.y));
                     if (test) {
-                        const float xf[3] = {sx[0][i], sx[1 % (TRUNC ? 4 : 1)][i], sx[2 % (TRUNC ? 4 : 1)][i]};
-                        const float af = sx[3 % (TRUNC ? 4 : 1)][i];
-                        if (!(qq < nq && j[0] < n &&
-                              keep_pair<D>(xf, yf[0], af, bf[0], span2, x64 + qq * D, y64 + j[0] * D,
-                                           alpha[qq], beta + j[0])))
-                            e.x = 0.f;
-                        if (!(qq < nq && j[1] < n &&
-                              keep_pair<D>(xf, yf[1], af, bf[1], span2, x64 + qq * D, y64 + j[1] * D,
-                                           alpha[qq], beta + j[1])))
-                            e.y = 0.f;
+                        const float Ai = sA[i];
+                        for (int l = 0; l < 2; ++l) {
+                            bool k = qq < nq && j[l] < n;
+                            if (k) {
+                                const int c2 = exp_test(l ? rh.y : rh.x, nbl[l], Ai);
+                                k = c2 > 0 ||
+                                    (c2 < 0 && keep_fp64<D>(x64 + qq * D, y64 + j[l] * D, alpha[qq], beta[j[l]]));
+                            }
+                            if (!k) {
+                                if (l) e.y = 0.f;
+                                else e.x = 0.f;
+                            }
+                        }
                     }
                     kahan2(s, comp, e);
                     cs = fma2(e, add2(add2(te, rt), hi2(B.d)), cs);
@@ -660,11 +661,9 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, bool t
     if (!p->df_prec) {
         if ((e = cudaMalloc(&p->df_prec, (size_t)p->nq_pad * sizeof(DRec)))) return e;
         if ((e = cudaMalloc(&p->df_trec, (size_t)p->n_pad * sizeof(DRec)))) return e;
-        if ((e = cudaMalloc(&p->df_ys, (size_t)3 * p->n_pad * sizeof(float)))) return e;
         const int64_t m = std::max(p->nq_pad, p->n_pad);
-        k_static_df<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(
-            p->x64, p->nq, p->nq_pad, p->y64, p->n, p->n_pad, p->d,
-            reinterpret_cast<DRec *>(p->df_prec), p->df_ys);
+        k_static_df<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p->x64, p->nq, p->nq_pad, p->d,
+                                                                reinterpret_cast<DRec *>(p->df_prec));
         if ((e = cudaGetLastError())) return e;
     }
     if (p->df_s2 < s2) {
@@ -676,77 +675,68 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, bool t
     }
     DRec *prec = reinterpret_cast<DRec *>(p->df_prec);
     DRec *trec = reinterpret_cast<DRec *>(p->df_trec);
-    // squared extent of the translated coordinates: bounds their FP32 rounding
-    const float span2 = (float)p->diam2;
     const double *alpha = trunc ? p->alpha : nullptr, *beta = trunc ? p->beta : nullptr;
     // truncated: targets in the cell list's order, blocks classified by balls
     SortedTargets T;
-    const float *ys = p->df_ys;
     const double *y64 = p->y64;
     if (trunc) {
         if ((e = trunc_sorted_targets(p, &T))) return e;
         const int d = p->d;
         auto nb = [](int64_t m) { return (unsigned)((m + 255) / 256); };
-        if (!p->df_ys_s) {
-            if ((e = cudaMalloc(&p->df_ys_s, (size_t)3 * p->n_pad * sizeof(float)))) return e;
+        if (!p->df_beta_s) {
             if ((e = cudaMalloc(&p->df_beta_s, (size_t)p->n_pad * sizeof(double)))) return e;
-            if ((e = cudaMalloc(&p->df_beta_sf, (size_t)p->n_pad * sizeof(float)))) return e;
-            if ((e = cudaMalloc(&p->df_alpha_f, (size_t)p->nq_pad * sizeof(float)))) return e;
+            if ((e = cudaMalloc(&p->df_beta_sf, (size_t)p->n_pad * sizeof(float)))) return e;   // nb_j
+            if ((e = cudaMalloc(&p->df_alpha_f, (size_t)p->nq_pad * sizeof(float)))) return e;  // A_q
             if ((e = cudaMalloc(&p->df_pb64, (size_t)(p->nq_pad / 64) * sizeof(float4)))) return e;
             if ((e = cudaMalloc(&p->df_pb8, (size_t)(p->nq_pad / 8) * sizeof(float4)))) return e;
             if ((e = cudaMalloc(&p->df_pa64, (size_t)(p->nq_pad / 64) * sizeof(float2)))) return e;
             if ((e = cudaMalloc(&p->df_pa8, (size_t)(p->nq_pad / 8) * sizeof(float2)))) return e;
             if ((e = cudaMalloc(&p->df_tbe64, (size_t)(p->n_pad / 64) * sizeof(float2)))) return e;
             if ((e = cudaMalloc(&p->df_tbe8, (size_t)(p->n_pad / 8) * sizeof(float2)))) return e;
-            k_df_coords<<<nb(p->n_pad), 256, 0, st>>>(T.y64, p->n, p->n_pad, d, p->df_ys_s);
             k_df_balls<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->x64, p->nq, d, 64, p->nq_pad / 64, p->df_pb64);
             k_df_balls<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->x64, p->nq, d, 8, p->nq_pad / 8, p->df_pb8);
         }
-        k_df_gather<<<nb(p->n_pad), 256, 0, st>>>(p->beta, T.perm, p->n, p->n_pad, p->df_beta_s,
-                                                  p->df_beta_sf);
-        k_df_gather<<<nb(p->nq_pad), 256, 0, st>>>(p->alpha, nullptr, p->nq, p->nq_pad, nullptr,
-                                                   p->df_alpha_f);
+        k_df_gather<<<nb(p->n_pad), 256, 0, st>>>(p->beta, T.perm, p->n, p->n_pad, p->df_beta_s, nullptr);
+        k_df_A<<<nb(p->nq_pad), 256, 0, st>>>(p->x64, p->alpha, p->nq, p->nq_pad, d, kLog2e / (2.0 * eps),
+                                              p->df_alpha_f);
         k_df_ranges<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->alpha, nullptr, p->nq, 64, p->nq_pad / 64,
                                                          p->df_pa64);
         k_df_ranges<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->alpha, nullptr, p->nq, 8, p->nq_pad / 8, p->df_pa8);
         k_df_ranges<<<nb(p->n_pad / 64), 256, 0, st>>>(p->beta, T.perm, p->n, 64, p->n_pad / 64, p->df_tbe64);
         k_df_ranges<<<nb(p->n_pad / 8), 256, 0, st>>>(p->beta, T.perm, p->n, 8, p->n_pad / 8, p->df_tbe8);
-        ys = p->df_ys_s;
         y64 = T.y64;
         beta = p->df_beta_s;
         if ((e = cudaGetLastError())) return e;
     }
     trace_begin(p, "prep_df");
     k_prep_df<<<p->nblk_prep, 256, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad, p->d, eps,
-                                           trunc ? T.perm : nullptr, trec, p->psinu, p->flags);
+                                           trunc ? T.perm : nullptr, trec, p->psinu, p->flags,
+                                           p->beta, trunc ? p->df_beta_sf : nullptr);
     trace_end(p);
     const unsigned nb1 = (unsigned)(p->nq_pad / D_ROWS);
     trace_begin(p, "lse_df");
     if (trunc)
-        k_lse_df<D, true><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec, ys, y64,
-                                                     p->n, p->n_pad, alpha, beta, span2, p->lmass2,
-                                                     p->mass, psi, eps, p->blockJ, p->lse_buf, p->res_dev,
-                                                     p->df_pb64, p->df_pa64, T.ball8, p->df_tbe8,
-                                                     p->df_beta_sf);
+        k_lse_df<D, true><<<nb1, D_THREADS, 0, st>>>(prec, p->x64, p->nq, p->nq_pad, trec, y64, p->n, alpha,
+                                                     beta, p->lmass2, p->mass, psi, eps, p->blockJ,
+                                                     p->lse_buf, p->res_dev, p->df_pb64, p->df_pa64, T.ball8,
+                                                     p->df_tbe8, p->df_beta_sf, p->df_alpha_f);
     else
-        k_lse_df<D, false><<<nb1, D_THREADS, 0, st>>>(prec, p->xs, p->x64, p->nq, p->nq_pad, trec, ys,
-                                                      y64, p->n, p->n_pad, alpha, beta, span2,
-                                                      p->lmass2, p->mass, psi, eps, p->blockJ,
-                                                      p->lse_buf, p->res_dev, nullptr, nullptr,
-                                                      nullptr, nullptr, nullptr);
+        k_lse_df<D, false><<<nb1, D_THREADS, 0, st>>>(prec, p->x64, p->nq, p->nq_pad, trec, y64, p->n,
+                                                      alpha, beta, p->lmass2, p->mass, psi, eps,
+                                                      p->blockJ, p->lse_buf, p->res_dev, nullptr, nullptr,
+                                                      nullptr, nullptr, nullptr, nullptr);
     trace_end(p);
     dim3 g2((unsigned)tblocks, (unsigned)s2);
     trace_begin(p, "grad_df");
     if (trunc)
-        k_grad_df<D, true><<<g2, D_THREADS, 0, st>>>(trec, ys, y64, p->n, p->n_pad, prec, p->xs, p->x64,
-                                                     p->nq, p->nq_pad, chunk, alpha, beta, span2,
-                                                     p->df_part2, T.perm, T.ball64, p->df_tbe64,
-                                                     p->df_pb8, p->df_pa8, p->df_alpha_f);
+        k_grad_df<D, true><<<g2, D_THREADS, 0, st>>>(trec, y64, p->n, p->n_pad, prec, p->x64, p->nq,
+                                                     p->nq_pad, chunk, alpha, beta, p->df_part2, T.perm,
+                                                     T.ball64, p->df_tbe64, p->df_pb8, p->df_pa8,
+                                                     p->df_alpha_f, p->df_beta_sf);
     else
-        k_grad_df<D, false><<<g2, D_THREADS, 0, st>>>(trec, ys, y64, p->n, p->n_pad, prec, p->xs,
-                                                      p->x64, p->nq, p->nq_pad, chunk, alpha, beta,
-                                                      span2, p->df_part2, nullptr, nullptr, nullptr,
-                                                      nullptr, nullptr, nullptr);
+        k_grad_df<D, false><<<g2, D_THREADS, 0, st>>>(trec, y64, p->n, p->n_pad, prec, p->x64, p->nq,
+                                                      p->nq_pad, chunk, alpha, beta, p->df_part2, nullptr,
+                                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     trace_end(p);
     if ((e = cudaGetLastError())) return e;
     return launch_finalize_log2(p, psi, eps, p->df_part2, (int)s2, (int)nb1, grad);
@@ -765,16 +755,13 @@ cudaError_t launch_compensated(rsot_problem *p, const double *psi, double eps, b
 void compensated_free(rsot_problem *p) {
     cudaFree(p->df_prec);
     cudaFree(p->df_trec);
-    cudaFree(p->df_ys);
     cudaFree(p->df_part2);
     p->df_prec = p->df_trec = nullptr;
-    p->df_ys = nullptr;
     p->df_part2 = nullptr;
     p->df_s2 = 0;
-    void *blk[] = {p->df_ys_s, p->df_beta_s, p->df_pb64, p->df_pb8, p->df_pa64, p->df_pa8,
+    void *blk[] = {p->df_beta_s, p->df_pb64, p->df_pb8, p->df_pa64, p->df_pa8,
                    p->df_tbe64, p->df_tbe8, p->df_beta_sf, p->df_alpha_f};
     for (void *q : blk) cudaFree(q);
-    p->df_ys_s = nullptr;
     p->df_beta_s = nullptr;
     p->df_beta_sf = p->df_alpha_f = nullptr;
     p->df_pb64 = p->df_pb8 = nullptr;

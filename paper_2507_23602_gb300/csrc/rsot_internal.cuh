@@ -114,15 +114,13 @@ struct rsot_problem {
     // compensated path scratch (rsot_df.cu), allocated on first use
     void *df_prec = nullptr;        // [nq_pad] point head/tail records (64 B)
     void *df_trec = nullptr;        // [n_pad] target head/tail records (64 B)
-    float *df_ys = nullptr;         // [3][n_pad] FP32 target coordinates
     double *df_part2 = nullptr;     // [df_s2][n_pad] pass-2 partials
     int df_s2 = 0;
     // truncated compensated passes: targets in the Morton order of the cell list,
     // blocks classified by balls (rsot_df.cu)
-    float *df_ys_s = nullptr;       // [3][n_pad] FP32 sorted target coordinates (once)
     double *df_beta_s = nullptr;    // [n_pad] beta in sorted order (per evaluation)
-    float *df_beta_sf = nullptr;    // [n_pad] the same rounded to FP32
-    float *df_alpha_f = nullptr;    // [nq_pad] alpha rounded to FP32 (caller order)
+    float *df_beta_sf = nullptr;    // [n_pad] nb_j = b_j - 2k beta_j in FP32, sorted (per evaluation)
+    float *df_alpha_f = nullptr;    // [nq_pad] A_q = k|x'_q|^2 - 2k alpha_q in FP32 (per evaluation)
     float4 *df_pb64 = nullptr;      // [nq_pad / 64] balls of 64 caller-order points (once)
     float4 *df_pb8 = nullptr;       // [nq_pad / 8] balls of 8 caller-order points (once)
     float2 *df_pa64 = nullptr, *df_pa8 = nullptr;    // alpha ranges of those point blocks
