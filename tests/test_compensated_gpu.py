@@ -180,3 +180,39 @@ def test_compensated_solve_and_fp64_reference_option():
         assert np.sum(np.abs(go3)) <= 1e-6 * 1.01
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_truncated_pairs_at_the_cutoff_match_fp64(d):
+    """Points and targets on lattices with the cutoff radius a lattice distance:
+    many pairs sit at the cutoff, where the exponent test of the truncated
+    compensated passes is undecided and the FP64 expression decides, so the
+    kept pairs equal the FP64 path's exactly (the oracle tests in the caller's
+    frame, so it may differ by those boundary pairs only)."""
+    k = 24 if d == 2 else 10
+    g = np.arange(k) / k
+    x = np.stack(np.meshgrid(*([g] * d), indexing="ij"), -1).reshape(-1, d)
+    gy = np.arange(k // 2) / (k // 2) + 0.5 / k
+    y = np.stack(np.meshgrid(*([gy] * d), indexing="ij"), -1).reshape(-1, d)
+    rng = np.random.default_rng(90 + d)
+    m = rng.uniform(0.5, 1.5, x.shape[0])
+    m /= m.sum()
+    nu = rng.uniform(0.5, 1.5, y.shape[0])
+    nu /= nu.sum()
+    psi = np.zeros(y.shape[0])
+    eps = 0.01
+    radius = np.sqrt(d) * 1.5 / k           # the distance of many lattice pairs
+    C = 0.5 * radius * radius
+    Jo, go, po, eo = oracle.dual_grad(x, m, y, nu, psi, eps, cutoff=C)
+    d2 = ((x[:, None, :] - y[None, :, :]) ** 2).sum(-1) * 0.5
+    at_cut = int(np.sum(np.abs(d2 - C) <= 1e-12))
+    assert at_cut > 100                       # the case really tests the band
+    P = rs().Problem(x, m, y, nu)
+    try:
+        J64, g64, p64 = P.eval(psi, eps, radius, rs().FP64, allow_empty=True)
+        J, g, pairs = P.eval(psi, eps, radius, rs().COMPENSATED, allow_empty=True)
+        assert pairs == p64
+        assert abs(pairs - po) <= at_cut
+        assert np.abs(g - g64).sum() <= rs().COMPENSATED_GRAD_REL * m.sum()
+    finally:
+        P.close()
