@@ -299,7 +299,8 @@ __global__ void k_static_df(const double *__restrict__ x64, int64_t nq, int64_t 
 // u_q = log2 m_q - R_q into the point record, sum_q m_q R_q by block.  Lane l
 // of a thread is point blockIdx.x * D_ROWS + l * D_THREADS + threadIdx.x.
 template <int D, bool TRUNC>
-__global__ void __launch_bounds__(D_THREADS)
+// (truncated: at most 96 registers, five blocks per SM, measured faster than four)
+__global__ void __launch_bounds__(D_THREADS, TRUNC ? 5 : 1)
     k_lse_df(DRec *__restrict__ prec, const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
              const DRec *__restrict__ trec, const double *__restrict__ y64, int64_t n,
              const double *__restrict__ alpha, const double *__restrict__ beta,
