@@ -681,33 +681,9 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, bool t
     SortedTargets T;
     const double *y64 = p->y64;
     if (trunc) {
-        if ((e = trunc_sorted_targets(p, &T))) return e;
-        const int d = p->d;
-        auto nb = [](int64_t m) { return (unsigned)((m + 255) / 256); };
-        if (!p->df_beta_s) {
-            if ((e = cudaMalloc(&p->df_beta_s, (size_t)p->n_pad * sizeof(double)))) return e;
-            if ((e = cudaMalloc(&p->df_beta_sf, (size_t)p->n_pad * sizeof(float)))) return e;   // nb_j
-            if ((e = cudaMalloc(&p->df_alpha_f, (size_t)p->nq_pad * sizeof(float)))) return e;  // A_q
-            if ((e = cudaMalloc(&p->df_pb64, (size_t)(p->nq_pad / 64) * sizeof(float4)))) return e;
-            if ((e = cudaMalloc(&p->df_pb8, (size_t)(p->nq_pad / 8) * sizeof(float4)))) return e;
-            if ((e = cudaMalloc(&p->df_pa64, (size_t)(p->nq_pad / 64) * sizeof(float2)))) return e;
-            if ((e = cudaMalloc(&p->df_pa8, (size_t)(p->nq_pad / 8) * sizeof(float2)))) return e;
-            if ((e = cudaMalloc(&p->df_tbe64, (size_t)(p->n_pad / 64) * sizeof(float2)))) return e;
-            if ((e = cudaMalloc(&p->df_tbe8, (size_t)(p->n_pad / 8) * sizeof(float2)))) return e;
-            k_df_balls<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->x64, p->nq, d, 64, p->nq_pad / 64, p->df_pb64);
-            k_df_balls<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->x64, p->nq, d, 8, p->nq_pad / 8, p->df_pb8);
-        }
-        k_df_gather<<<nb(p->n_pad), 256, 0, st>>>(p->beta, T.perm, p->n, p->n_pad, p->df_beta_s, nullptr);
-        k_df_A<<<nb(p->nq_pad), 256, 0, st>>>(p->x64, p->alpha, p->nq, p->nq_pad, d, kLog2e / (2.0 * eps),
-                                              p->df_alpha_f);
-        k_df_ranges<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->alpha, nullptr, p->nq, 64, p->nq_pad / 64,
-                                                         p->df_pa64);
-        k_df_ranges<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->alpha, nullptr, p->nq, 8, p->nq_pad / 8, p->df_pa8);
-        k_df_ranges<<<nb(p->n_pad / 64), 256, 0, st>>>(p->beta, T.perm, p->n, 64, p->n_pad / 64, p->df_tbe64);
-        k_df_ranges<<<nb(p->n_pad / 8), 256, 0, st>>>(p->beta, T.perm, p->n, 8, p->n_pad / 8, p->df_tbe8);
+        if ((e = trunc_block_setup(p, eps, &T))) return e;
         y64 = T.y64;
         beta = p->df_beta_s;
-        if ((e = cudaGetLastError())) return e;
     }
     trace_begin(p, "prep_df");
     k_prep_df<<<p->nblk_prep, 256, 0, st>>>(psi, p->y64, p->lnu, p->nu, p->n, p->n_pad, p->d, eps,
@@ -744,6 +720,39 @@ cudaError_t compensated_d(rsot_problem *p, const double *psi, double eps, bool t
 }
 
 }  // namespace
+
+// Block data of the truncated block-skip passes (compensated and FP32): the
+// cell list's target order, balls of 64 / 8 caller-order points (once), beta in
+// sorted order, A_q, and the alpha / beta ranges of the blocks (per evaluation,
+// from p->alpha / p->beta).
+cudaError_t trunc_block_setup(rsot_problem *p, double eps, SortedTargets *T) {
+    cudaError_t e;
+    cudaStream_t st = p->stream;
+    if ((e = trunc_sorted_targets(p, T))) return e;
+    const int d = p->d;
+    auto nb = [](int64_t m) { return (unsigned)((m + 255) / 256); };
+    if (!p->df_beta_s) {
+        if ((e = cudaMalloc(&p->df_beta_s, (size_t)p->n_pad * sizeof(double)))) return e;
+        if ((e = cudaMalloc(&p->df_beta_sf, (size_t)p->n_pad * sizeof(float)))) return e;   // nb_j
+        if ((e = cudaMalloc(&p->df_alpha_f, (size_t)p->nq_pad * sizeof(float)))) return e;  // A_q
+        if ((e = cudaMalloc(&p->df_pb64, (size_t)(p->nq_pad / 64) * sizeof(float4)))) return e;
+        if ((e = cudaMalloc(&p->df_pb8, (size_t)(p->nq_pad / 8) * sizeof(float4)))) return e;
+        if ((e = cudaMalloc(&p->df_pa64, (size_t)(p->nq_pad / 64) * sizeof(float2)))) return e;
+        if ((e = cudaMalloc(&p->df_pa8, (size_t)(p->nq_pad / 8) * sizeof(float2)))) return e;
+        if ((e = cudaMalloc(&p->df_tbe64, (size_t)(p->n_pad / 64) * sizeof(float2)))) return e;
+        if ((e = cudaMalloc(&p->df_tbe8, (size_t)(p->n_pad / 8) * sizeof(float2)))) return e;
+        k_df_balls<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->x64, p->nq, d, 64, p->nq_pad / 64, p->df_pb64);
+        k_df_balls<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->x64, p->nq, d, 8, p->nq_pad / 8, p->df_pb8);
+    }
+    k_df_gather<<<nb(p->n_pad), 256, 0, st>>>(p->beta, T->perm, p->n, p->n_pad, p->df_beta_s, nullptr);
+    k_df_A<<<nb(p->nq_pad), 256, 0, st>>>(p->x64, p->alpha, p->nq, p->nq_pad, d, kLog2e / (2.0 * eps),
+                                          p->df_alpha_f);
+    k_df_ranges<<<nb(p->nq_pad / 64), 256, 0, st>>>(p->alpha, nullptr, p->nq, 64, p->nq_pad / 64, p->df_pa64);
+    k_df_ranges<<<nb(p->nq_pad / 8), 256, 0, st>>>(p->alpha, nullptr, p->nq, 8, p->nq_pad / 8, p->df_pa8);
+    k_df_ranges<<<nb(p->n_pad / 64), 256, 0, st>>>(p->beta, T->perm, p->n, 64, p->n_pad / 64, p->df_tbe64);
+    k_df_ranges<<<nb(p->n_pad / 8), 256, 0, st>>>(p->beta, T->perm, p->n, 8, p->n_pad / 8, p->df_tbe8);
+    return cudaGetLastError();
+}
 
 // dense (Eq. discretized_functional / discretized_gradient), or the truncated
 // sums over c(x_q, y_j) < alpha_q + beta_j (p->alpha, p->beta)

@@ -142,7 +142,8 @@ struct rsot_problem {
 
     // per-point log partition of the last evaluation (see rsot_point_log_partition)
     double *lse_buf = nullptr;      // [nq_pad]: R_q (mixed, log2) or L'_q (FP64, natural)
-    int last_kind = -1;             // -1 none, 0 FP64 dense, 1 mixed dense, 2/3 truncated
+    int last_kind = -1;             // -1 none, 0 FP64 dense, 1 mixed dense, 2/3 truncated (FP64 /
+                                    // mixed cell list), 4/5 compensated
                                     // FP64/mixed, 4/5 compensated dense/truncated
     double last_eps = 0.0;
 
@@ -235,6 +236,10 @@ struct SortedTargets {
     const float4 *ball8 = nullptr, *ball64 = nullptr;
 };
 cudaError_t trunc_sorted_targets(rsot_problem *p, SortedTargets *out);
+// block data of the truncated block-skip passes from p->alpha / p->beta
+// (rsot_df.cu): df_beta_s, df_alpha_f (A_q), balls and ranges of point and
+// target blocks; T receives the sorted-target view
+cudaError_t trunc_block_setup(rsot_problem *p, double eps, SortedTargets *T);
 
 // ---- device helpers ----------------------------------------------------------
 __device__ __forceinline__ float ex2_approx(float x) {
