@@ -555,6 +555,26 @@ def main():
                                            f"{sms_c} SMs x {sm_max_c:.0f} MHz; "
                                            f"{COMP_FP32_OPS_PER_PAIR[dom_c]} lane-ops per pair",
                              "traffic": None}}
+        # the same evaluation truncated at tail 1e-12 (psi-aware cutoffs, block-skip
+        # passes keeping exactly the FP64 path's pairs), at the bench potential
+        P.eval_tail(psi_d, p.eps, 1e-12, rs.COMPENSATED, grad_out=grad_d)
+        P.kernel_timing(True)
+        tms, tpairs = [], 0
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, _, tpairs = P.eval_tail(psi_d, p.eps, 1e-12, rs.COMPENSATED, grad_out=grad_d)
+            b_.record()
+            torch.cuda.synchronize()
+            tms.append(a.elapsed_time(b_))
+        tk = {k: v[0] / v[1] for k, v in P.kernel_times().items()}
+        P.kernel_timing(False)
+        comp["truncated_tail_1e-12"] = {"ms_per_step": sum(tms) / len(tms), "pairs_per_step": tpairs,
+                                        "kept_fraction": tpairs / pairs, "per_kernel_ms": tk,
+                                        "dense_equivalent": pairs / (sum(tms) / len(tms) * 1e-3) / 1e9,
+                                        "unit": "G pairs/s"}
 
     # truncated evaluations at tail 1e-12 (secondary line, same workload): the
     # psi-aware cutoffs per pair (rsot_eval_dual_grad_tail) and the global tail
