@@ -601,6 +601,23 @@ def main():
             P.kernel_timing(False)
             return sum(tms) / len(tms), tp, tk
 
+        sms_t = torch.cuda.get_device_properties(dev).multi_processor_count
+        sfu_peak = SFU_EX2_PER_CLK_PER_SM * sms_t * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+        hbm_peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+
+        def trunc_roofline(t_ms, tp):
+            # SFU: two ex2 per kept pair (one per pass); HBM: the algorithmic bytes of
+            # one evaluation (point stream x' + m + result, target records, the
+            # gradient) -- both fractions, the larger one naming the binding unit
+            ex2 = 2.0 * tp / (t_ms * 1e-3)
+            by = p.nq * (8 * p.x.shape[1] + 16) + p.n * (16 + 8 + 8)
+            gbs = by / (t_ms * 1e-3) / 1e9
+            r = {"sfu": {"achieved_ex2_per_s": ex2, "peak": sfu_peak, "frac": ex2 / sfu_peak},
+                 "hbm": {"achieved_gbs": gbs, "peak": hbm_peak, "frac": gbs / hbm_peak,
+                         "algorithmic_bytes": by}}
+            r["binds"] = "sfu" if r["sfu"]["frac"] >= r["hbm"]["frac"] else "hbm"
+            return r
+
         def trunc_at(psi_t):
             t_ms, tp, tk = timed(lambda: P.eval_tail(psi_t, p.eps, 1e-12, rs.MIXED, grad_out=grad_d))
             R = P.radius_for_tail(psi_t, p.eps, 1e-12)
@@ -608,6 +625,7 @@ def main():
             return {"value": tp / (t_ms * 1e-3) / 1e9, "unit": "G pairs/s",
                     "dense_equivalent": pairs / (t_ms * 1e-3) / 1e9, "pairs_per_step": tp,
                     "kept_fraction": tp / pairs, "ms_per_step": t_ms,
+                    "roofline": trunc_roofline(t_ms, tp),
                     "per_kernel_ms": {k: v[0] / v[1] for k, v in tk.items()},
                     "gpu_launches": int(sum(v[1] for v in tk.values())),
                     "global_radius": {"radius": R, "pairs_per_step": rp, "kept_fraction": rp / pairs,
