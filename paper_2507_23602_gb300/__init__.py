@@ -31,7 +31,7 @@ FP64, MIXED, COMPENSATED = 0, 1, 2
 COMPENSATED_GRAD_REL = 6.5e-7
 PAIRS_FP32, PAIRS_TENSOR, PAIRS_AUTO = 0, 1, 2
 # GEMM kernels of the warm-start network (rsot_mlp_set_gemm_kernel)
-GEMM_TCGEN05, GEMM_MMA_SYNC = 0, 1
+GEMM_TCGEN05, GEMM_MMA_SYNC, GEMM_TCGEN05_CPASYNC = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
           4: "empty neighbourhood", 5: "not converged", 6: "line search failed",
           7: "device wait timed out", 8: "out of device memory"}

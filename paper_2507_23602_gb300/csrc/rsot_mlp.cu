@@ -11,6 +11,8 @@
 // transposed on the way in) and read with ldmatrix.  Epilogues: plain FP32,
 // bias + SiLU (writes the FP32 pre-activation and the BF16 activation), and
 // multiplication by SiLU'(Z) for back-propagation (writes BF16).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
@@ -184,7 +186,17 @@ __global__ void __launch_bounds__(G_THREADS)
 // (LBO = 128 B), 8-row groups 1,040 B apart (SBO), so a stage tile of 128 rows
 // x 64 K takes 16,640 B and no descriptor offset can leave it.  K-contiguous sources
 // arrive by 16-byte cp.async (zero-filled outside the matrix); a transposed
-// source is transposed on the way in by the threads.  The accumulator (128
+// source is transposed on the way in by the threads.  A K-contiguous operand
+// whose rows start on 16-byte boundaries comes instead by one TMA tile copy
+// per stage (tensor map box of 64 K x 128 rows, zero-filled outside the
+// matrix, 128-byte swizzle): rows of 128 B in 8-row atoms of 1,024 B (SBO),
+// the 16-byte chunks of row r permuted by r % 8, which the MMA's descriptor
+// (swizzle mode 128 B) undoes; the K = 16 steps advance its start address by
+// 32 B inside the atom.  A transposed operand (MN contiguous) comes by two TMA
+// copies of 64 MN x 64 K (8 KB apart) and is read MN-major (transpose bit of
+// the instruction descriptor): 128-byte rows along MN, one per k, 8-row atoms
+// 1,024 B apart along K (SBO), the two 64-wide MN halves 8,192 B apart (LBO),
+// 2,048 B per K = 16 step.  The accumulator (128
 // lanes x 128 FP32 columns) is read back by tcgen05.ld: warp w takes lanes
 // 32 (w % 4) .. + 31 and columns 64 (w / 4) .. + 63, transposes each 32 x 32
 // block through shared memory and stores whole rows (coalesced), for the
@@ -194,9 +206,12 @@ constexpr int T5_M = 128, T5_N = 128, T5_K = 64, T5_THREADS = 256;
 // 8-row groups 1,040 B apart (1,024 + 16: successive groups start in other
 // shared-memory banks, for the transposing loads)
 constexpr uint32_t T5_LBO = 128, T5_SBO = 1040;
-constexpr int T5_TILE = 16 * T5_SBO;       // bytes of one operand tile of a stage (16 row groups)
-constexpr int T5_SMEM = 2 * 2 * T5_TILE;   // two stages of A and B: 65 KB
-static_assert(T5_THREADS / 32 * 32 * 33 * 4 <= T5_SMEM, "epilogue transpose fits in the stage buffers");
+constexpr int T5_TILE = 16 * T5_SBO;       // bytes of one cp.async operand tile (16 row groups)
+constexpr int T5_TILE_TMA = 128 * 128;     // bytes of one TMA operand tile (128 rows of 128 B)
+constexpr int T5_TS = 17 * 1024;           // operand slot: holds either tile, 1,024-aligned
+constexpr int T5_SMEM = 2 * 2 * T5_TS + 1024;   // two stages of A and B, alignment slack: 69 KB
+static_assert(T5_TILE <= T5_TS && T5_TILE_TMA <= T5_TS, "operand tiles fit their slots");
+static_assert(T5_THREADS / 32 * 32 * 33 * 4 <= 4 * T5_TS, "epilogue transpose fits in the stage buffers");
 // instruction descriptor of kind::f16: F32 accumulator (bits 4-5 = 1), BF16 A
 // and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
 // bits 17-22, M >> 4 at bits 24-28
@@ -209,6 +224,28 @@ constexpr uint32_t T5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T
 __device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(T5_LBO >> 4) << 16) |
            ((uint64_t)(T5_SBO >> 4) << 32) | (1ull << 46);
+}
+// the same for a TMA tile: SBO 1,024 B (8-row atoms), LBO unused within one
+// 128-byte row (encoded 1), swizzle mode 2 (128 B) at bits 61-63
+__device__ __forceinline__ uint64_t t5_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+// an MN-major TMA tile: LBO 8,192 B (the two 64-wide MN halves), SBO 1,024 B
+// (8 k-rows of 128 B), swizzle mode 2
+__device__ __forceinline__ uint64_t t5_desc_mn_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(8192 >> 4) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// one 2-D TMA tile copy global -> shared (x = K element, y = row), completion
+// counted in bytes on bar
+__device__ __forceinline__ void tma_load_2d(void *smem, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned bytes) {
@@ -280,10 +317,19 @@ __global__ void __launch_bounds__(T5_THREADS)
     k_gemm_t5(int M, int N, int K, int kslice, const bf16 *__restrict__ A, int lda,
               const bf16 *__restrict__ B, int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias,
               bf16 *__restrict__ H, int ldh, const float *__restrict__ Z, int ldz,
-              int *__restrict__ flags) {
-    extern __shared__ __align__(1024) unsigned char t5_smem[];
+              int *__restrict__ flags, const __grid_constant__ CUtensorMap tmA,
+              const __grid_constant__ CUtensorMap tmB, int tma) {
+    extern __shared__ __align__(1024) unsigned char t5_dyn[];
     __shared__ __align__(8) uint64_t done[2];   // commit of the MMAs that read stage buffer s
+    __shared__ __align__(8) uint64_t full[2];   // TMA bytes of stage buffer s have landed
     __shared__ uint32_t s_tmem;
+    // operand slots on 1,024-byte boundaries (the 128-byte swizzle atoms)
+    unsigned char *const t5_smem = t5_dyn + ((1024u - (smem_u32(t5_dyn) & 1023u)) & 1023u);
+    // tma bit 0: A by TMA, bit 1: B by TMA; a transposed operand copied by TMA
+    // is read MN-major (transpose bits 15 / 16 of the instruction descriptor)
+    const bool tA = (tma & 1) != 0, tB = (tma & 2) != 0;
+    const unsigned tx = (tA ? T5_TILE_TMA : 0) + (tB ? T5_TILE_TMA : 0);
+    const uint32_t idesc = T5_IDESC | ((tA && AT) ? 1u << 15 : 0u) | ((tB && BT) ? 1u << 16 : 0u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * T5_M, n0 = blockIdx.x * T5_N;
     if (warp == 0) {
@@ -296,6 +342,8 @@ __global__ void __launch_bounds__(T5_THREADS)
     if (tid == 32) {
         mbar_init(&done[0], 1);
         mbar_init(&done[1], 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
         fence_barrier_init();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -307,30 +355,66 @@ __global__ void __launch_bounds__(T5_THREADS)
     if (EPI == EPI_F32) C += (int64_t)blockIdx.z * M * ldc;
     const int nk = ke > kb ? (ke - kb + T5_K - 1) / T5_K : 0;
     bool ok = true;
-    if (nk > 0) {
-        t5_load<AT>(t5_smem, A, lda, m0, M, kb, ke);
-        t5_load<BT>(t5_smem + T5_TILE, B, ldb, n0, N, kb, ke);
+    // stage loader: TMA operands by thread 0 (the tensor map zero-fills rows and
+    // K beyond the matrix; the host takes TMA only when the K slice is all of K),
+    // the others by every thread's cp.async
+    auto load_stage = [&](int buf, int k0) {
+        unsigned char *As = t5_smem + buf * 2 * T5_TS, *Bs = As + T5_TS;
+        if (tx && tid == 0) {
+            mbar_expect_tx(&full[buf], tx);
+            if (tA) {
+                if (AT) {
+                    tma_load_2d(As, &tmA, m0, k0, &full[buf]);
+                    tma_load_2d(As + T5_TILE_TMA / 2, &tmA, m0 + 64, k0, &full[buf]);
+                } else {
+                    tma_load_2d(As, &tmA, k0, m0, &full[buf]);
+                }
+            }
+            if (tB) {
+                if (BT) {
+                    tma_load_2d(Bs, &tmB, n0, k0, &full[buf]);
+                    tma_load_2d(Bs + T5_TILE_TMA / 2, &tmB, n0 + 64, k0, &full[buf]);
+                } else {
+                    tma_load_2d(Bs, &tmB, k0, n0, &full[buf]);
+                }
+            }
+        }
+        if (!tA) t5_load<AT>(As, A, lda, m0, M, k0, ke);
+        if (!tB) t5_load<BT>(Bs, B, ldb, n0, N, k0, ke);
         cp_async_commit();
-    }
+    };
+    // thread 0: bit s of fbad = a TMA wait of buffer s gave up, bit s of fpar =
+    // parity of buffer s's next completion
+    unsigned fbad = 0u, fpar = 0u;
+    if (nk > 0) load_stage(0, kb);
     for (int kt = 0; kt < nk; ++kt) {
         const int s = kt & 1;
-        unsigned char *As = t5_smem + s * 2 * T5_TILE, *Bs = As + T5_TILE;
+        unsigned char *As = t5_smem + s * 2 * T5_TS, *Bs = As + T5_TS;
         // stage kt has landed (the thread's copies, then every thread's); its
         // stores become visible to the tensor core (async proxy)
         cp_async_wait_all();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
+            if (tx) {
+                const bool got = mbar_wait(&full[s], (fpar >> s) & 1u);
+                fbad = got ? fbad & ~(1u << s) : fbad | (1u << s);
+                ok = got && ok;
+                fpar ^= 1u << s;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll
             for (int kk = 0; kk < T5_K / 16; ++kk) {
-                const uint64_t ad = t5_desc(a0 + kk * 2 * T5_LBO), bd = t5_desc(b0 + kk * 2 * T5_LBO);
+                const uint64_t ad = !tA ? t5_desc(a0 + kk * 2 * T5_LBO)
+                                    : AT ? t5_desc_mn_sw128(a0 + kk * 2048) : t5_desc_sw128(a0 + kk * 32);
+                const uint64_t bd = !tB ? t5_desc(b0 + kk * 2 * T5_LBO)
+                                    : BT ? t5_desc_mn_sw128(b0 + kk * 2048) : t5_desc_sw128(b0 + kk * 32);
                 const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(T5_IDESC), "r"(accum)
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -340,13 +424,15 @@ __global__ void __launch_bounds__(T5_THREADS)
         if (kt + 1 < nk) {
             // the other buffer was last read by the MMAs of stage kt - 1
             if (kt >= 1) ok = mbar_wait(&done[s ^ 1], (unsigned)((kt - 1) >> 1) & 1u) && ok;
-            unsigned char *An = t5_smem + (s ^ 1) * 2 * T5_TILE;
-            t5_load<AT>(An, A, lda, m0, M, kb + (kt + 1) * T5_K, ke);
-            t5_load<BT>(An + T5_TILE, B, ldb, n0, N, kb + (kt + 1) * T5_K, ke);
-            cp_async_commit();
+            load_stage(s ^ 1, kb + (kt + 1) * T5_K);
         }
     }
     if (nk > 0) ok = mbar_wait(&done[(nk - 1) & 1], (unsigned)((nk - 1) >> 1) & 1u) && ok;
+    // a TMA wait that gave up may leave its copy in flight: wait for it once
+    // more (bounded) before the buffers are reused or the CTA exits
+    if (tid == 0 && tx)
+        for (int b = 0; b < 2; ++b)
+            if ((fbad >> b) & 1u) mbar_wait(&full[b], ((fpar >> b) & 1u) ^ 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // every MMA is done: the stage buffers hold the epilogue's transposes
     float *T = reinterpret_cast<float *>(t5_smem) + warp * 32 * 33;
@@ -518,7 +604,36 @@ __global__ void k_split_sum(const float *__restrict__ ws, int S, int M, int N, i
 
 constexpr int SPLIT_MAX = 128;   // split-K slices at most (workspace SPLIT_MAX x M x ldc floats)
 
-// kind 0: tcgen05 kernel, 1: warp-level mma.sync kernel (same operands, epilogues).
+// Tensor map of a BF16 operand for the tcgen05 kernel's TMA stage copies,
+// 128-byte swizzle, zero fill outside: K-contiguous src[r * ld + k] (rows x K,
+// box 64 K x 128 rows) or, transposed, src[k * ld + r] (box 64 rows x 64 K).
+// false (the kernel then copies the operand with cp.async) when the driver's
+// encoder is unavailable or the operand breaks a TMA rule: base and row
+// stride multiples of 16 bytes.
+bool t5_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int K, int ld, bool trans) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || !src || rows < 1 || K < 1 || ld < (trans ? rows : K) ||
+        (reinterpret_cast<uintptr_t>(src) & 15) || ((int64_t)ld * 2) % 16)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)(trans ? rows : K), (cuuint64_t)(trans ? K : rows)};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {64, trans ? 64u : 128u}, estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(src), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// kind 0: tcgen05 kernel with TMA operand copies where the operand allows them,
+// 2: the same kernel with cp.async copies only, 1: warp-level mma.sync kernel
+// (same operands, epilogues).
 // A plain-FP32 GEMM with a long K and few output tiles (the weight gradients,
 // K = rows) is split along K over about two CTAs per SM, its partials summed
 // by k_split_sum in a fixed order (ws: SPLIT_MAX x M x ldc floats).
@@ -532,16 +647,26 @@ void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int 
     const int kslice = S > 1 ? (K + S - 1) / S / 64 * 64 + 64 : K;
     if (S > 1) S = (K + kslice - 1) / kslice;
     float *Cw = S > 1 ? ws : C;
-    if (kind == 0) {
-        static bool attr = false;   // 64 KB of dynamic shared memory, set once per instance
+    if (kind == 0 || kind == 2) {
+        static bool attr = false;   // 69 KB of dynamic shared memory, set once per instance
         if (!attr) {
             cudaFuncSetAttribute((const void *)k_gemm_t5<AT, BT, EPI>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, T5_SMEM);
             attr = true;
         }
+        // TMA operand copies: a box (64 K) never crosses a K slice's end, since
+        // slices start and end on multiples of 64 or at K, where zero fill begins
+        CUtensorMap ma, mb;
+        memset(&ma, 0, sizeof(ma));
+        memset(&mb, 0, sizeof(mb));
+        int tma = 0;
+        if (kind == 0 && (S == 1 || kslice % T5_K == 0)) {
+            if (t5_tensor_map(&ma, A, M, K, lda, AT)) tma |= 1;
+            if (t5_tensor_map(&mb, B, N, K, ldb, BT)) tma |= 2;
+        }
         dim3 grid((N + T5_N - 1) / T5_N, (M + T5_M - 1) / T5_M, S);
         k_gemm_t5<AT, BT, EPI><<<grid, T5_THREADS, T5_SMEM, st>>>(M, N, K, kslice, A, lda, B, ldb, Cw, ldc,
-                                                                   bias, H, ldh, Z, ldz, flags);
+                                                                   bias, H, ldh, Z, ldz, flags, ma, mb, tma);
     } else {
         dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, S);
         k_gemm_bf16<AT, BT, EPI><<<grid, G_THREADS, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, Cw, ldc, bias,
@@ -576,7 +701,7 @@ struct rsot_mlp {
     bf16 *X0 = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZ = nullptr, *dZ2 = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dH = nullptr, *out = nullptr, *dout = nullptr,
           *lt = nullptr, *xin = nullptr, *yin = nullptr, *scal = nullptr;
-    int gemm_kind = 0;       // 0: tcgen05 GEMM kernel, 1: mma.sync GEMM kernel
+    int gemm_kind = 0;       // 0: tcgen05 GEMM (TMA), 1: mma.sync GEMM, 2: tcgen05 GEMM (cp.async)
     float *ws = nullptr;     // split-K partials of the weight-gradient GEMMs
     float *red = nullptr;    // partials of the column sums (RED_CHUNKS x width)
     int sms = 1;
@@ -751,7 +876,7 @@ rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out
 int64_t rsot_mlp_num_params(const rsot_mlp *m) { return m ? m->n_params : 0; }
 
 rsot_status rsot_mlp_set_gemm_kernel(rsot_mlp *m, int kind) {
-    if (!m || kind < 0 || kind > 1) return RSOT_ERR_ARG;
+    if (!m || kind < 0 || kind > 2) return RSOT_ERR_ARG;
     m->gemm_kind = kind;
     return RSOT_OK;
 }

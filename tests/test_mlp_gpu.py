@@ -1,7 +1,7 @@
 """The warm-start network's own kernels (BF16 tensor-core GEMMs, FP32
-accumulation; both GEMM kernels: tcgen05 with the accumulator in tensor memory,
-and warp-level mma.sync) against the FP64 MLP oracle that rounds to bfloat16
-where the kernels do."""
+accumulation; every GEMM kernel: tcgen05 with the accumulator in tensor memory
+and TMA or cp.async operand copies, and warp-level mma.sync) against the FP64
+MLP oracle that rounds to bfloat16 where the kernels do."""
 import numpy as np
 import pytest
 
@@ -24,12 +24,14 @@ def setup(in_dim, width, rows, seed, kind=0):
     return net, x, y
 
 
-KINDS = [0, 1]   # GEMM_TCGEN05, GEMM_MMA_SYNC
+KINDS = [0, 1, 2]   # GEMM_TCGEN05 (TMA), GEMM_MMA_SYNC, GEMM_TCGEN05_CPASYNC
 
 
 @pytest.mark.parametrize("kind", KINDS)
+# (3, 64, 37): fewer rows than one TMA box; (5, 104, 300): K = 104, so the
+# second K box is zero-filled past 40 of its 64 columns, and N = 104 < 128 rows
 @pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 1000), (18, 256, 4096), (5, 64, 300),
-                                               (7, 200, 777)])
+                                               (7, 200, 777), (3, 64, 37), (5, 104, 300)])
 def test_forward_matches_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 7, kind)
     try:
@@ -41,7 +43,8 @@ def test_forward_matches_oracle(in_dim, width, rows, kind):
 
 
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300), (7, 200, 777)])
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300), (7, 200, 777),
+                                               (5, 104, 300)])
 def test_gradients_match_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 11, kind)
     try:
@@ -95,10 +98,30 @@ def test_gemm_kernels_agree():
         net.close()
 
 
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 5000), (7, 200, 777), (3, 64, 37)])
+def test_tma_and_cp_async_copies_give_equal_results(in_dim, width, rows):
+    """The tcgen05 kernel with TMA operand copies (128-byte swizzled tiles)
+    and with cp.async copies (unswizzled tiles): the same MMAs over the same
+    K stages, so outputs, loss and gradients are bitwise equal."""
+    net, x, y = setup(in_dim, width, rows, 17, rs().GEMM_TCGEN05)
+    try:
+        o0 = net.forward(x)
+        l0, g0 = net.gradients(x, y)
+        net.set_gemm_kernel(rs().GEMM_TCGEN05_CPASYNC)
+        o2 = net.forward(x)
+        l2, g2 = net.gradients(x, y)
+        assert np.array_equal(o0, o2)
+        assert l0 == l2
+        assert np.array_equal(g0, g2)
+    finally:
+        net.close()
+
+
 def test_gemm_kernel_kind_is_checked():
     net = rs().MLP(4, 64, seed=1)
     try:
-        with pytest.raises(rs().RsotError):
-            net.set_gemm_kernel(2)
+        for bad in (3, -1):
+            with pytest.raises(rs().RsotError):
+                net.set_gemm_kernel(bad)
     finally:
         net.close()
