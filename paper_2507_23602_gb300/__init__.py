@@ -585,7 +585,8 @@ class MLP:
         _check(lib.rsot_mlp_set_stream(h, ctypes.c_void_p(s or 0)), "mlp_set_stream")
 
     def set_gemm_kernel(self, kind):
-        """GEMM_TCGEN05 (default) or GEMM_MMA_SYNC for the layers' GEMMs."""
+        """GEMM_TCGEN05 (default: TMA operand copies), GEMM_TCGEN05_CPASYNC or
+        GEMM_MMA_SYNC for the layers' GEMMs."""
         _check(self._lib.rsot_mlp_set_gemm_kernel(self._h, int(kind)), "mlp_set_gemm_kernel")
 
     def close(self):
