@@ -74,3 +74,28 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(rs, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         rs.load()
+
+
+def test_binding_constants_match_the_header(lib):
+    """Every enum value and numeric limit the binding restates equals the
+    header's (a GEMM kind or status added to one side only fails here)."""
+    import paper_2507_23602_gb300 as rs
+    src = open(os.path.join(ROOT, "include", "rsot.h")).read()
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(RSOT_[A-Z0-9_]+)\s*=\s*(\d+)", src)}
+    defs = {m.group(1): float(m.group(2))
+            for m in re.finditer(r"#define\s+(RSOT_[A-Z0-9_]+)\s+([0-9.eE+-]+)\s*$", src, re.M)}
+    prefixes = {"RSOT_MLP_GEMM_": "GEMM_", "RSOT_PAIRS_": "PAIRS_"}
+    checked = 0
+    for name, v in vals.items():
+        if name.startswith("RSOT_ERR_") or name == "RSOT_OK":
+            assert v in rs.STATUS, name
+            checked += 1
+            continue
+        py = next((p2 + name[len(p1):] for p1, p2 in prefixes.items() if name.startswith(p1)),
+                  name[len("RSOT_"):])
+        assert getattr(rs, py) == v, (name, py)
+        checked += 1
+    assert set(rs.STATUS) == {v for n, v in vals.items() if n.startswith("RSOT_ERR_") or n == "RSOT_OK"}
+    assert rs.COMPENSATED_GRAD_REL == defs["RSOT_COMPENSATED_GRAD_REL"]
+    assert rs.MAX_LEVELS == defs["RSOT_MAX_LEVELS"]
+    assert checked >= 18
