@@ -42,6 +42,13 @@ FP32_LANE_OPS_PER_CLK_PER_SM = 128
 # FP32 lane-operations per pair of the compensated passes, counted from their
 # source: double-float exponent 3 x 12 + 3, shift TwoSum 6, Kahan 4, tail 2-3
 COMP_FP32_OPS_PER_PAIR = {"lse_df": 51, "grad_df": 52}
+# FP64-pipe operations per pair of the two FP64 passes, counted from their
+# source (d = 2 / 3): the cost c (d subtractions, d fused multiply-adds, one
+# multiply), the cutoff test (add, compare), the exponent (one or two), the
+# library's own exponential (two range compares, multiply, round, 2 + 13 fused
+# multiply-adds, conversion, scaling multiply: 21), the accumulation (one or a
+# compare and one): pass 1 = 2d + 28, pass 2 = 2d + 27
+FP64_OPS_PER_PAIR = {2: 63, 3: 67}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -74,6 +81,13 @@ def parse():
     ap.add_argument("--eval-seeds", type=int, default=512)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--mlp-rows", type=int, default=65536, help="mlp: rows per gradients call")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="dense workload: skip the solve-time object (cube solve and the "
+                         "warm-started vs plain FP64 comparison)")
+    ap.add_argument("--compare-problems", type=int, default=16,
+                    help="dense workload: held-out warm-start problems solved by both arms")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="dense workload: skip the oracle gradients at the solves' results")
     return ap.parse_args()
 
 
@@ -427,6 +441,161 @@ def run_solve_workloads(args):
         return
 
 
+def eval_roofline_seconds(pairs_prec, sms, sm_mhz, dfma_per_s=None, d=3):
+    """Roofline time of a solve's evaluations: per precision, the algorithmic
+    work of its pairs over its binding unit's peak -- mixed: 2 ex2 per pair on
+    the SFU; compensated: the FP32 lane-ops per pair of both passes; FP64: the
+    FP64 operations per pair of both passes at the measured DFMA rate (None when
+    the FP64 rate is not known).  Index = rsot_precision (FP64, MIXED,
+    COMPENSATED)."""
+    clk = sm_mhz * 1e6
+    t = 2.0 * pairs_prec[1] / (SFU_EX2_PER_CLK_PER_SM * sms * clk)
+    t += pairs_prec[2] * sum(COMP_FP32_OPS_PER_PAIR.values()) / (FP32_LANE_OPS_PER_CLK_PER_SM * sms * clk)
+    if pairs_prec[0]:
+        if not dfma_per_s:
+            return None
+        t += pairs_prec[0] * FP64_OPS_PER_PAIR[d] / dfma_per_s
+    return t
+
+
+def warmstart_network(args, log):
+    """The warm-start network trained on the batched solver's potentials of
+    args.train_seeds problems (seeds 10000..), cached under the temp directory
+    by a hash of the library sources and the training settings; returns
+    (net, info)."""
+    import numpy as np
+    import paper_2507_23602_gb300 as rs
+    from paper_2507_23602_gb300 import warmstart as ws
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_2507_23602_gb300", "csrc"),):
+        for f in sorted(os.listdir(d)):
+            h.update(open(os.path.join(d, f), "rb").read())
+    for f in (os.path.join(ROOT, "paper_2507_23602_gb300", "warmstart.py"),
+              os.path.join(ROOT, "rsot_inputs", "__init__.py")):
+        h.update(open(f, "rb").read())
+    h.update(f"{args.train_seeds}-{args.epochs}".encode())
+    path = os.path.join(tempfile.gettempdir(), f"rsot_warmstart_{h.hexdigest()[:16]}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        net = rs.MLP(ws.IN_DIM, 256, seed=0)
+        net.set_params(z["params"])
+        info = {k: float(z[k]) for k in ("gen_seconds", "train_seconds", "samples")}
+        info.update({"cached": True, "loss_history": z["loss"].tolist()})
+        return net, info
+    X, Y, t_gen = ws.generate(list(range(10000, 10000 + args.train_seeds)))
+    log(f"warm start: {X.shape[0]} training rows generated in {t_gen:.1f} s")
+    net, hist, t_train = ws.train(X, Y, epochs=args.epochs)
+    log(f"warm start: trained in {t_train:.1f} s, loss {hist[0]:.3e} -> {hist[-1]:.3e}")
+    np.savez(path, params=net.params(), gen_seconds=t_gen, train_seconds=t_train,
+             samples=float(X.shape[0]), loss=np.array(hist))
+    return net, {"gen_seconds": t_gen, "train_seconds": t_train, "samples": float(X.shape[0]),
+                 "cached": False, "loss_history": hist}
+
+
+def solve_metrics(args, P, p, dev, dfma_per_s):
+    """The metric's solve-time half: (a) the cube solve eps 0.1 -> 1e-3 to
+    ||grad J||_1 <= 1e-6 (mixed evaluations, refinement on compensated
+    evaluations with the certified stop); (b) on the same held-out warm-start
+    problems (d = 2, 4,096 targets, eps = 5e-3), the warm-started mixed batched
+    solve against the plain FP64 GPU solve from psi = 0 with the eps-schedule.
+    Each with wall time, iterations / rounds, converged count, the oracle's
+    ||grad J||_1 at the returned potential and the roofline fraction
+    (evaluations' roofline time / wall)."""
+    import numpy as np
+    import torch
+    import paper_2507_23602_gb300 as rs
+    from paper_2507_23602_gb300 import warmstart as ws
+    import rsot_inputs as ri
+
+    def log(msg):
+        sys.stderr.write(f"[bench] {msg}\n")
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    out = {"tol_l1": 1e-6,
+           "roofline_basis": f"evaluations' roofline time / wall: mixed 2 ex2 per pair at "
+                             f"{SFU_EX2_PER_CLK_PER_SM} ex2/clk/SM, compensated "
+                             f"{sum(COMP_FP32_OPS_PER_PAIR.values())} FP32 lane-ops per pair at "
+                             f"{FP32_LANE_OPS_PER_CLK_PER_SM}/clk/SM, FP64 {FP64_OPS_PER_PAIR} (by d) "
+                             f"FP64-pipe ops per pair at the measured DFMA rate "
+                             f"({dfma_per_s:.4g}/s); {sms} SMs x {sm_max:.0f} MHz"}
+    # (a) cube solve
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    psi_c, st = P.solve(eps=p.eps, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, precision=rs.MIXED,
+                        raise_on_error=False, max_iter=20000)
+    wall = time.perf_counter() - t
+    rt = eval_roofline_seconds(st.pairs_prec, sms, sm_max, dfma_per_s)
+    out["cube"] = {"workload": f"cube-{p.nq}x{p.n}, eps 0.1 -> {p.eps:g} (x0.5), tol 1e-6",
+                   "seconds": wall, "iters": st.iters, "evals": st.evals, "stages": st.stages,
+                   "status": st.status, "converged": int(st.status == 0),
+                   "grad_l1_reported": st.grad_l1,
+                   "certified_grad_l1_bound": st.grad_l1 + rs.COMPENSATED_GRAD_REL * float(p.mass.sum()),
+                   "evals_by_precision": dict(zip(("fp64", "mixed", "compensated"), st.evals_prec)),
+                   "pairs_by_precision": dict(zip(("fp64", "mixed", "compensated"), st.pairs_prec)),
+                   "roofline_seconds": rt, "roofline_frac": (rt / wall) if rt else None}
+    log(f"cube solve {wall:.2f} s, {st.iters} iterations, status {st.status}")
+
+    # (b) warm-started mixed batched vs plain FP64 on the same held-out problems
+    net, info = warmstart_network(args, log)
+    seeds = list(range(20000, 20000 + args.compare_problems))
+    probs = [ri.warmstart_problem(sd) for sd in seeds]
+    B = rs.Batch([(q.x, q.mass, q.y, q.nu) for q, _ in probs])
+    epsv = np.full(len(probs), probs[0][0].eps)
+    try:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        psi0 = np.concatenate([ws.predict(net, th, q.y, q.nu) for q, th in probs])
+        t_pred = time.perf_counter() - t
+        psi_w, sw = B.solve(epsv, psi0=psi0, eps_start=0.0, tol_l1=1e-6, precision=rs.MIXED,
+                            refine_fp64=True, raise_on_error=False)
+        wall_w = time.perf_counter() - t
+        log(f"warm-started mixed batched: {wall_w:.2f} s, {sw['converged']}/{len(probs)} converged")
+        t = time.perf_counter()
+        psi_p, sp = B.solve(epsv, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6, precision=rs.FP64,
+                            raise_on_error=False)
+        wall_p = time.perf_counter() - t
+        log(f"plain FP64: {wall_p:.2f} s, {sp['converged']}/{len(probs)} converged")
+    finally:
+        B.close()
+        net.close()
+
+    def arm(st_, wall_):
+        rt_ = eval_roofline_seconds(st_["pairs_prec"], sms, sm_max, dfma_per_s, d=2)
+        return {"seconds": wall_, "rounds": st_["rounds"], "evals": st_["evals"],
+                "converged": st_["converged"], "max_grad_l1_reported": st_["max_grad_l1"],
+                "evals_by_precision": dict(zip(("fp64", "mixed", "compensated"), st_["evals_prec"])),
+                "pairs_by_precision": dict(zip(("fp64", "mixed", "compensated"), st_["pairs_prec"])),
+                "roofline_seconds": rt_, "roofline_frac": (rt_ / wall_) if rt_ else None}
+
+    cmp_ = {"workload": f"{len(probs)} held-out problems (seeds {seeds[0]}..{seeds[-1]}): d = 2, "
+                        f"{probs[0][0].nq} points x {probs[0][0].n} targets, eps {epsv[0]:g}",
+            "warm_started_mixed_batched": arm(sw, wall_w),
+            "plain_fp64_gpu": arm(sp, wall_p),
+            "speedup": wall_p / max(wall_w, 1e-9),
+            "network": dict(info, predict_seconds=t_pred,
+                            note="trained before the timed solves on the batched solver's "
+                                 "potentials; its time is reported here, not in either arm")}
+    cmp_["warm_started_mixed_batched"]["predict_seconds_included"] = t_pred
+    out["warm_vs_plain_fp64"] = cmp_
+
+    # oracle gradients at the returned potentials (after every timed solve)
+    if not args.no_oracle_check:
+        import oracle
+        t = time.perf_counter()
+        _, go, _, _ = oracle.dual_grad(p.x, p.mass, p.y, p.nu, psi_c, p.eps)
+        out["cube"]["oracle_grad_l1"] = float(np.abs(go).sum())
+        for key, psi_all in (("warm_started_mixed_batched", psi_w), ("plain_fp64_gpu", psi_p)):
+            mx, off = 0.0, 0
+            for q, _ in probs:
+                _, gq, _, _ = oracle.dual_grad(q.x, q.mass, q.y, q.nu, psi_all[off:off + q.n], q.eps)
+                mx = max(mx, float(np.abs(gq).sum()))
+                off += q.n
+            cmp_[key]["oracle_max_grad_l1"] = mx
+        out["oracle_check_seconds"] = time.perf_counter() - t
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -696,6 +865,12 @@ def main():
     if clk and clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (SFU_EX2_PER_CLK_PER_SM * sms * clk["sm_mhz"] * 1e6 / 1e9)
 
+    # the metric's solve-time half (after every timed evaluation above)
+    solve = None
+    dfma = rs.probe_dfma_rate()
+    if not args.no_solve and world == 1:
+        solve = solve_metrics(args, P, p, dev, dfma)
+
     out = {
         "metric": "dual+grad G pairs/s (dense)", "value": value, "unit": "G pairs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -713,6 +888,7 @@ def main():
         "truncated": trunc,
         "fp32_pair_kernels": fp32_pairs,
         "compensated": comp,
+        "solve": solve,
         "gpu_launches": int(sum(v[1] for v in ktimes.values())),
         "clocks": clk,
         "wall_s_timed_region": wall,

@@ -76,13 +76,22 @@ const char *rsot_version(void);
  *   x      : nq*d doubles (row-major), mass: nq doubles, m_q >= 0
  *   n      : number of targets, >= 1
  *   y      : n*d doubles (row-major), nu: n doubles, nu_j > 0
- * The inputs are copied to device memory owned by the handle; the caller's
- * buffers may be freed after the call.  Sum m_q and sum nu_j are used as
- * given (the paper's normalisation sum = 1 is the caller's choice).
+ *   device_ptrs : 0 -- the inputs (host or device memory) are copied into
+ *               device memory owned by the handle; the caller's buffers may
+ *               be freed after the call.
+ *               1 -- borrow: x, mass, y, nu must be device memory of the
+ *               current device (else RSOT_ERR_ARG).  The handle reads mass
+ *               and nu in place at every evaluation instead of copying them,
+ *               so they must stay allocated and unchanged until
+ *               rsot_destroy; x and y are read once, into the handle's own
+ *               translated layouts (the cost is computed in coordinates
+ *               centred on the data's bounding box).
+ * Sum m_q and sum nu_j are used as given (the paper's normalisation sum = 1
+ * is the caller's choice).
  * Errors: RSOT_ERR_ARG, RSOT_ERR_NOMEM, RSOT_ERR_CUDA.
  */
 rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass,
-                        int64_t n, const double *y, const double *nu,
+                        int64_t n, const double *y, const double *nu, int device_ptrs,
                         rsot_problem **out);
 
 /* Free every resource of the handle (NULL is accepted). */
@@ -126,12 +135,29 @@ rsot_status rsot_set_pair_kernel(rsot_problem *p, rsot_pair_kernel kind);
  *               terms entered the sums (nq*n when dense)
  * Errors: RSOT_ERR_ARG, RSOT_ERR_NONFINITE (psi not finite or J/grad not
  * finite), RSOT_ERR_EMPTY_NEIGHBORHOOD (truncated and some point kept no
- * target; Algorithm 2 skips such points and the outputs are still written
- * for inspection, but the status reports it), RSOT_ERR_TIMEOUT, RSOT_ERR_CUDA.
+ * target: Algorithm 2 skips such points; the outputs are not written, and
+ * rsot_last_eval returns the evaluation with those points skipped),
+ * RSOT_ERR_TIMEOUT, RSOT_ERR_CUDA.  On any error J_out, grad_out and
+ * pairs_out are left untouched.
  */
 rsot_status rsot_eval_dual_grad(rsot_problem *p, const double *psi, double eps,
                                 double radius, rsot_precision prec,
                                 double *J_out, double *grad_out, int64_t *pairs_out);
+
+/*
+ * Results of the last evaluation on this handle whose passes completed: the
+ * last one that returned RSOT_OK, or one that returned
+ * RSOT_ERR_EMPTY_NEIGHBORHOOD, whose points without a target Algorithm 2
+ * skipped (their terms are absent from J and the gradient).
+ *   J_out, pairs_out, empty_out : host pointers or NULL; empty_out receives
+ *               the number of skipped points (0 when dense)
+ *   grad_out  : n doubles (host or device) or NULL
+ * Errors: RSOT_ERR_ARG when no evaluation has completed on this handle (or
+ * another call, such as rsot_softmax_refine, has replaced its buffers),
+ * RSOT_ERR_CUDA.
+ */
+rsot_status rsot_last_eval(rsot_problem *p, double *J_out, double *grad_out, int64_t *pairs_out,
+                           int64_t *empty_out);
 
 /*
  * One evaluation truncated by psi-aware cutoffs per pair (Sec. 4.1, App. B):
@@ -192,6 +218,33 @@ rsot_status rsot_radius_for_tail(rsot_problem *p, const double *psi, double eps,
                                  double tail, double *radius_out);
 
 /*
+ * The cost cutoffs of the truncated evaluation (Sec. 4.1, App. B), for a
+ * potential psi (n doubles, host or device) at eps; M = max psi, m = min psi,
+ * Gamma = M - m, C_0 = the covering cost (rsot_covering_cost):
+ *   RSOT_CUTOFF_POINTWISE : C_pw = M + eps ln(max nu / param)      (Eq. cost_cutoff_delta;
+ *                           param = delta_thr)
+ *   RSOT_CUTOFF_INTEGRAL  : C_int = M + eps (ln eps + lnD - ln param - ln |J|)
+ *                           (Eq. truncation_cutoff_int; param = tau, lnD = ln D as
+ *                           returned by rsot_log_integrated_D, J the functional)
+ *   RSOT_CUTOFF_GEOMETRIC : C_geom = max(C_0, C_0 + Gamma + eps ln(eps / (min nu param |J|)))
+ *                           (Eq. truncation_cutoff_geom, App. B; param = tau)
+ *   RSOT_CUTOFF_TAIL      : C = C_0 + Gamma + eps ln(1 / (min nu param))  (param = tail;
+ *                           the cutoff of rsot_radius_for_tail)
+ * The truncated evaluation keeps c(x_q, y_j) < C, i.e. radius sqrt(2 C).
+ * J and lnD are read only by the kinds that use them.
+ * Errors: RSOT_ERR_ARG (unknown kind, param <= 0, eps <= 0, J = 0 where used),
+ * RSOT_ERR_NONFINITE (psi not finite), RSOT_ERR_CUDA.
+ */
+typedef enum {
+    RSOT_CUTOFF_POINTWISE = 0,
+    RSOT_CUTOFF_INTEGRAL = 1,
+    RSOT_CUTOFF_GEOMETRIC = 2,
+    RSOT_CUTOFF_TAIL = 3
+} rsot_cutoff_kind;
+rsot_status rsot_truncation_cutoff(rsot_problem *p, const double *psi, double eps, int kind,
+                                   double param, double J, double lnD, double *C_out);
+
+/*
  * Kernel tracing (no counterpart in the paper: a runtime facility).  While
  * enabled, every kernel the library launches is bracketed by CUDA events on
  * the handle's stream and its device time is accumulated per kernel name.
@@ -212,34 +265,71 @@ int rsot_kernel_times(rsot_problem *p, const char **names, double *total_ms,
 rsot_status rsot_probe_ex2_rate(int iters, double *ex2_per_s);
 
 /*
+ * Throughput probe of the FP64 pipe (no counterpart in the paper): times
+ * `iters` rounds of independent FP64 fused multiply-adds on the current device
+ * and returns the measured DFMA per second, the ceiling of the FP64 path
+ * (whose exponential is the library's own, so its FP64 operations per pair
+ * are known).
+ */
+rsot_status rsot_probe_dfma_rate(int iters, double *dfma_per_s);
+
+/*
+ * The FP64 path's exponential on the GPU, y_i = e^{x_i} (Cody & Waite
+ * reduction, Taylor polynomial of degree 13; about 2 ulp; 0 below -745.2,
+ * +inf above 709.8, NaN kept), exposed so that its accuracy can be tested.
+ *   x, y : n doubles (host or device)
+ */
+rsot_status rsot_exp64(int64_t n, const double *x, double *y);
+
+/*
+ * Self-test of the bounded device-side waits (no counterpart in the paper:
+ * failure detection).  Every wait of the library's kernels on a pipeline
+ * stage (an mbarrier filled by a bulk copy) polls a bounded number of rounds
+ * and, when they run out, records an error bit, lets the kernel's own copies
+ * in flight land and returns, so the host reports RSOT_ERR_TIMEOUT and the
+ * CUDA context stays usable.  This call runs that path on purpose: one CTA
+ * waits `limit` rounds (1 <= limit <= 2^24) on a stage that no copy fills,
+ * drains the one copy it did issue, and returns.
+ * Returns RSOT_ERR_TIMEOUT when the wait ran out (the expected result),
+ * RSOT_OK if it did not; RSOT_ERR_ARG, RSOT_ERR_NOMEM, RSOT_ERR_CUDA.
+ */
+rsot_status rsot_selftest_wait_timeout(long long limit, void *stream);
+
+/*
  * Allocation-free dense evaluation (no counterpart in the paper: an interface
- * for callers that must not allocate device memory themselves -- code whose
- * device memory is owned by another component, such as a framework's caching
+ * for callers that cannot allocate device memory themselves -- code whose
+ * device memory belongs to another component, such as a framework's caching
  * allocator, or that runs under a fixed memory budget set at start-up).
  *
- * Computes the same J and gradient as rsot_eval_dual_grad with radius 0 and
- * RSOT_MIXED, without a problem handle and without calling cudaMalloc,
- * cudaFree or any allocating library routine.  Its scratch is one static
- * device array of 45 MiB (47,237,632 bytes) inside librsot, which every GPU
+ * One dense mixed-precision evaluation of J and its gradient without a problem
+ * handle and without calling cudaMalloc, cudaFree or any allocating library
+ * routine.  It runs the FP32 pair kernels of RSOT_MIXED (RSOT_PAIRS_FP32), so
+ * it agrees with rsot_eval_dual_grad(radius 0, RSOT_MIXED) within the mixed
+ * path's tolerances (1e-5 relative on J, 1e-6 absolute per gradient entry),
+ * not bit for bit.  Its scratch is one static device array of
+ * RSOT_NOALLOC_SCRATCH_BYTES (57.6 MiB) inside librsot, which every GPU
  * that loads the library holds until the process exits.
  *   d, nq, n     : as rsot_create; nq <= RSOT_NOALLOC_MAX_NQ, n <= RSOT_NOALLOC_MAX_N
  *                  (larger sizes return RSOT_ERR_ARG without touching the GPU)
- *   x, mass, y, nu, psi : DEVICE pointers (row-major, as rsot_create / eval);
- *                  host pointers are rejected with RSOT_ERR_ARG
+ *   x, mass, y, nu, psi : DEVICE pointers of the current device (row-major, as
+ *                  rsot_create / eval); host pointers and other devices'
+ *                  memory are rejected with RSOT_ERR_ARG
  *   eps          : > 0
  *   stream       : cudaStream_t for all work (NULL = legacy default stream)
  *   J_out        : HOST pointer, 1 double
- *   grad_out     : DEVICE pointer, n doubles
- * The call is synchronous with respect to J_out and grad_out.  The first call
- * on a device looks up the address of the static scratch on that device (with
- * that device current); make that first call before any stream capture.
- * Every call shares the one scratch array and leaves its contents behind:
- * calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialised by the caller.
+ *   grad_out     : DEVICE pointer of the current device, n doubles
+ * The call synchronises the stream before it returns (J_out is a host value),
+ * so it cannot be captured in a CUDA graph.  The first call in a CUDA context
+ * looks up the address of the static scratch in that context (with its device
+ * current); later calls in the same context reuse it.  Every call shares the
+ * one scratch array and leaves its contents behind: calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  On an error J_out and grad_out are left untouched.
  * Errors: RSOT_ERR_ARG, RSOT_ERR_NONFINITE, RSOT_ERR_TIMEOUT, RSOT_ERR_CUDA.
  */
 #define RSOT_NOALLOC_MAX_NQ 524288
 #define RSOT_NOALLOC_MAX_N 65536
+#define RSOT_NOALLOC_SCRATCH_BYTES 60393984
 rsot_status rsot_eval_dense_noalloc(int d, int64_t nq, const double *x, const double *mass,
                                     int64_t n, const double *y, const double *nu,
                                     const double *psi, double eps, void *stream,
@@ -280,6 +370,17 @@ typedef struct {
                             integral cutoff C_int of this relative J tolerance,
                             D and J from the previous evaluation of the stage
                             (Sec. 4.1); the first evaluation of a stage is dense */
+    double delta_pw;     /* > 0: truncate each evaluation at the pointwise cutoff
+                            C_pw = max psi + eps ln(max nu / delta_pw) of the
+                            current potential (Sec. 4.1, Eq. cost_cutoff_delta);
+                            points left without a target are skipped, as
+                            Algorithm 2 skips them                             */
+    double tau_geom;     /* > 0: truncate each evaluation at the geometric cutoff
+                            C_geom of this relative J tolerance (Sec. 4.1, Eq.
+                            truncation_cutoff_geom, App. B), J from the previous
+                            evaluation of the stage; the first one is dense.
+                            At most one of tail, tau_int, delta_pw, tau_geom is
+                            > 0; the refinement's references stay dense        */
 } rsot_options;
 
 /* Fill *o with the defaults (eps 1e-2, no schedule, dense, tol 1e-6, MIXED with
@@ -295,6 +396,9 @@ typedef struct {
     int stages;          /* eps stages run                                        */
     int64_t pairs;       /* pairs evaluated over all evaluations                  */
     double seconds;      /* wall time of the call                                 */
+    int evals_prec[3];   /* evaluations by rsot_precision (index RSOT_FP64,
+                            RSOT_MIXED, RSOT_COMPENSATED)                          */
+    int64_t pairs_prec[3];  /* pairs evaluated by rsot_precision                   */
 } rsot_solve_stats;
 
 /*
@@ -376,6 +480,9 @@ typedef struct {
     int converged;             /* problems that reached tol_l1                        */
     double max_grad_l1;        /* largest final ||grad J||_1                          */
     int64_t evals;             /* evaluations summed over problems                    */
+    int64_t evals_prec[3];     /* evaluations by rsot_precision (batched rounds are
+                                  RSOT_MIXED; refinements add their own)             */
+    int64_t pairs_prec[3];     /* pairs evaluated by rsot_precision                   */
 } rsot_batch_stats;
 
 /*

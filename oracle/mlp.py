@@ -85,3 +85,26 @@ def loss_and_grad(p, x, y, in_dim, width, emulate_bf16=True):
     db1 = dZ1.sum(0)
     g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3, dw4, [db4]])
     return loss, g
+
+
+def abs_scales(p, x, y, in_dim, width):
+    """Scale of every output and gradient entry for element-wise comparisons:
+    the same sums as ``forward`` / ``loss_and_grad`` taken over the absolute
+    values of their terms (e.g. sum_r |dZ_ri| |H_rj| for dW_ij).  A GEMM that
+    accumulates in FP32 errs by at most a small multiple of 2^-24 times this
+    scale per entry, whatever cancellation the signed sum has."""
+    W1, b1, W2, b2, W3, b3, w4, b4, in_pad = unpack(p, in_dim, width)
+    out, (X0, Z1, H1, Z2, H2, Z3, H3) = forward(p, x, in_dim, width, True)
+    B = x.shape[0]
+    out_scale = np.abs(H3) @ np.abs(w4) + abs(b4)
+    e = out - y
+    dout = e / B
+    dZ3 = bf16(np.outer(dout, w4) * dsilu(Z3))
+    dZ2 = bf16((dZ3 @ bf16(W3)) * dsilu(Z2))
+    dZ1 = bf16((dZ2 @ bf16(W2)) * dsilu(Z1))
+    a = np.abs
+    g = np.concatenate([(a(dZ1).T @ a(X0)).ravel(), a(dZ1).sum(0),
+                        (a(dZ2).T @ a(H1)).ravel(), a(dZ2).sum(0),
+                        (a(dZ3).T @ a(H2)).ravel(), a(dZ3).sum(0),
+                        a(H3).T @ a(dout), [a(dout).sum()]])
+    return out_scale, g

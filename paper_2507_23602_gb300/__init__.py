@@ -19,7 +19,7 @@ from typing import Optional
 import numpy as np
 
 __all__ = ["load", "lib_path", "RsotError", "Problem", "Batch", "MLP", "SolveOptions", "SolveStats",
-           "FP64", "MIXED", "COMPENSATED", "COMPENSATED_GRAD_REL", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate",
+           "FP64", "MIXED", "COMPENSATED", "COMPENSATED_GRAD_REL", "PAIRS_FP32", "PAIRS_TENSOR", "PAIRS_AUTO", "STATUS", "probe_ex2_rate", "probe_dfma_rate",
            "GEMM_TCGEN05", "GEMM_MMA_SYNC"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -30,12 +30,16 @@ FP64, MIXED, COMPENSATED = 0, 1, 2
 # ||g - grad J||_1 <= COMPENSATED_GRAD_REL * sum_q m_q for a COMPENSATED gradient
 COMPENSATED_GRAD_REL = 6.5e-7
 PAIRS_FP32, PAIRS_TENSOR, PAIRS_AUTO = 0, 1, 2
+# cost cutoffs of Sec. 4.1 (rsot_truncation_cutoff)
+CUTOFF_POINTWISE, CUTOFF_INTEGRAL, CUTOFF_GEOMETRIC, CUTOFF_TAIL = 0, 1, 2, 3
 # GEMM kernels of the warm-start network (rsot_mlp_set_gemm_kernel)
 GEMM_TCGEN05, GEMM_MMA_SYNC, GEMM_TCGEN05_CPASYNC = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
           4: "empty neighbourhood", 5: "not converged", 6: "line search failed",
           7: "device wait timed out", 8: "out of device memory"}
 RSOT_ERR_EMPTY_NEIGHBORHOOD = 4
+# limits of the allocation-free entry point rsot_eval_dense_noalloc
+NOALLOC_MAX_NQ, NOALLOC_MAX_N, NOALLOC_SCRATCH_BYTES = 524288, 65536, 60393984
 
 
 class RsotError(RuntimeError):
@@ -51,7 +55,8 @@ class _Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
                 ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("mixed_tol_l1", ctypes.c_double), ("refine_precision", ctypes.c_int),
-                ("tau_int", ctypes.c_double)]
+                ("tau_int", ctypes.c_double), ("delta_pw", ctypes.c_double),
+                ("tau_geom", ctypes.c_double)]
 
 
 class _Desc(ctypes.Structure):
@@ -64,7 +69,8 @@ class _BStats(ctypes.Structure):
     _fields_ = [("seconds", ctypes.c_double), ("seconds_mixed", ctypes.c_double),
                 ("seconds_refine", ctypes.c_double), ("rounds", ctypes.c_int),
                 ("converged", ctypes.c_int), ("max_grad_l1", ctypes.c_double),
-                ("evals", ctypes.c_int64)]
+                ("evals", ctypes.c_int64), ("evals_prec", ctypes.c_int64 * 3),
+                ("pairs_prec", ctypes.c_int64 * 3)]
 
 
 class _SrcLevel(ctypes.Structure):
@@ -97,7 +103,8 @@ class _BaryStats(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("J", ctypes.c_double), ("grad_l1", ctypes.c_double), ("iters", ctypes.c_int),
                 ("evals", ctypes.c_int), ("stages", ctypes.c_int), ("pairs", ctypes.c_int64),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("evals_prec", ctypes.c_int * 3),
+                ("pairs_prec", ctypes.c_int64 * 3)]
 
 
 @dataclasses.dataclass
@@ -116,12 +123,15 @@ class SolveOptions:
     mixed_tol_l1: float = 1e-5
     refine_precision: int = COMPENSATED
     tau_int: float = 0.0
+    delta_pw: float = 0.0
+    tau_geom: float = 0.0
 
     def _c(self):
         return _Options(self.eps, self.eps_start, self.eps_factor, self.tail, self.tol_l1,
                         self.stage_tol_l1, int(self.precision), int(bool(self.refine_fp64)),
                         int(self.lbfgs_m), int(self.max_iter), int(bool(self.verbose)),
-                        float(self.mixed_tol_l1), int(self.refine_precision), float(self.tau_int))
+                        float(self.mixed_tol_l1), int(self.refine_precision), float(self.tau_int),
+                        float(self.delta_pw), float(self.tau_geom))
 
 
 @dataclasses.dataclass
@@ -134,6 +144,8 @@ class SolveStats:
     stages: int
     pairs: int
     seconds: float
+    evals_prec: tuple = (0, 0, 0)   # by precision: FP64, MIXED, COMPENSATED
+    pairs_prec: tuple = (0, 0, 0)
 
 
 def lib_path() -> str:
@@ -153,7 +165,7 @@ def load():
     lib.rsot_status_string.argtypes = [ctypes.c_int]
     lib.rsot_version.restype = ctypes.c_char_p
     lib.rsot_create.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp,
-                                ctypes.POINTER(vp)]
+                                ctypes.c_int, ctypes.POINTER(vp)]
     lib.rsot_destroy.argtypes = [vp]
     lib.rsot_destroy.restype = None
     lib.rsot_set_stream.argtypes = [vp, vp]
@@ -163,9 +175,12 @@ def load():
     lib.rsot_eval_dual_grad_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         dp, vp, i64p]
     lib.rsot_log_integrated_D.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.rsot_last_eval.argtypes = [vp, dp, vp, i64p, i64p]
     lib.rsot_covering_cost.argtypes = [vp, dp]
     lib.rsot_point_log_partition.argtypes = [vp, vp]
     lib.rsot_radius_for_tail.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, dp]
+    lib.rsot_truncation_cutoff.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, dp]
     lib.rsot_default_options.argtypes = [ctypes.POINTER(_Options)]
     lib.rsot_default_options.restype = None
     lib.rsot_solve.argtypes = [vp, dp, ctypes.POINTER(_Options), ctypes.POINTER(_Stats)]
@@ -173,6 +188,9 @@ def load():
     lib.rsot_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), dp, i64p, ctypes.c_int]
     lib.rsot_kernel_times.restype = ctypes.c_int
     lib.rsot_probe_ex2_rate.argtypes = [ctypes.c_int, dp]
+    lib.rsot_probe_dfma_rate.argtypes = [ctypes.c_int, dp]
+    lib.rsot_exp64.argtypes = [ctypes.c_int64, vp, vp]
+    lib.rsot_selftest_wait_timeout.argtypes = [ctypes.c_longlong, vp]
     lib.rsot_kmeans.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, ctypes.c_int,
                                 ctypes.c_uint64, dp, dp, i64p]
     lib.rsot_softmax_refine.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, vp, vp]
@@ -218,6 +236,13 @@ def probe_ex2_rate(iters: int = 20000) -> float:
     return v.value
 
 
+def probe_dfma_rate(iters: int = 4000) -> float:
+    """Measured FP64 fused multiply-adds per second of the current device."""
+    v = ctypes.c_double()
+    _check(load().rsot_probe_dfma_rate(int(iters), ctypes.byref(v)), "probe_dfma_rate")
+    return v.value
+
+
 def _ptr(a):
     """(pointer, keep-alive object) for a numpy array or a torch tensor (float64)."""
     try:
@@ -248,9 +273,12 @@ def _check(st, what):
 
 class Problem:
     """An RSOT problem held on the GPU: quadrature points x (nq, d), masses
-    (nq,), targets y (n, d), weights nu (n,)."""
+    (nq,), targets y (n, d), weights nu (n,).  With borrow=True the four
+    arrays must be CUDA float64 tensors of the current device: the handle
+    reads mass and nu in place (this object keeps them alive) instead of
+    copying them."""
 
-    def __init__(self, x, mass, y, nu, stream=None):
+    def __init__(self, x, mass, y, nu, stream=None, borrow=False):
         lib = load()
         d = int(x.shape[1])
         self.d, self.nq, self.n = d, int(x.shape[0]), int(y.shape[0])
@@ -259,7 +287,9 @@ class Problem:
         py, ky = _ptr(y)
         pn, kn = _ptr(nu)
         h = ctypes.c_void_p()
-        _check(lib.rsot_create(d, self.nq, px, pm, self.n, py, pn, ctypes.byref(h)), "create")
+        _check(lib.rsot_create(d, self.nq, px, pm, self.n, py, pn, int(bool(borrow)),
+                               ctypes.byref(h)), "create")
+        self._borrowed = (km, kn) if borrow else None
         self._h = h
         self._lib = lib
         if stream is None:
@@ -305,9 +335,28 @@ class Problem:
         pairs = ctypes.c_int64()
         st = self._lib.rsot_eval_dual_grad(self._h, pp, float(eps), float(radius), int(precision),
                                            ctypes.byref(J), pg, ctypes.byref(pairs))
-        if not (st == 0 or (allow_empty and st == RSOT_ERR_EMPTY_NEIGHBORHOOD)):
+        if allow_empty and st == RSOT_ERR_EMPTY_NEIGHBORHOOD:
+            # the outputs are untouched on that status: the evaluation with the
+            # empty points skipped comes from rsot_last_eval
+            _check(self._lib.rsot_last_eval(self._h, ctypes.byref(J), pg, ctypes.byref(pairs), None),
+                   "last_eval")
+            st = 0
+        if st != 0:
             raise RsotError(st, "eval_dual_grad")
         return J.value, grad_out, pairs.value
+
+    def last_eval(self, grad_out=None):
+        """(J, grad, pairs, empty) of the last evaluation whose passes completed,
+        including one that skipped points without a target (Algorithm 2)."""
+        if grad_out is None:
+            grad_out = np.empty(self.n)
+        pg, kg = _ptr(grad_out)
+        J = ctypes.c_double()
+        pairs = ctypes.c_int64()
+        empty = ctypes.c_int64()
+        _check(self._lib.rsot_last_eval(self._h, ctypes.byref(J), pg, ctypes.byref(pairs),
+                                        ctypes.byref(empty)), "last_eval")
+        return J.value, grad_out, pairs.value, empty.value
 
     def eval_tail(self, psi, eps, tail, precision=MIXED, grad_out=None):
         """(J, grad, pairs): Algorithm 2 truncated by the psi-aware cutoffs
@@ -392,6 +441,17 @@ class Problem:
         _check(self._lib.rsot_covering_cost(self._h, ctypes.byref(v)), "covering_cost")
         return v.value
 
+    def truncation_cutoff(self, psi, eps, kind, param, J=0.0, lnD=0.0):
+        """Cost cutoff C of Sec. 4.1 (kind: CUTOFF_POINTWISE, CUTOFF_INTEGRAL,
+        CUTOFF_GEOMETRIC, CUTOFF_TAIL); the truncated evaluation keeps
+        c(x, y) < C, i.e. radius sqrt(2 C)."""
+        pp, kp = _ptr(psi)
+        v = ctypes.c_double()
+        _check(self._lib.rsot_truncation_cutoff(self._h, pp, float(eps), int(kind), float(param),
+                                                float(J), float(lnD), ctypes.byref(v)),
+               "truncation_cutoff")
+        return v.value
+
     def radius_for_tail(self, psi, eps, tail):
         pp, kp = _ptr(psi)
         v = ctypes.c_double()
@@ -407,7 +467,8 @@ class Problem:
         s = _Stats()
         st = self._lib.rsot_solve(self._h, psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                   ctypes.byref(o), ctypes.byref(s))
-        stats = SolveStats(st, s.J, s.grad_l1, s.iters, s.evals, s.stages, s.pairs, s.seconds)
+        stats = SolveStats(st, s.J, s.grad_l1, s.iters, s.evals, s.stages, s.pairs, s.seconds,
+                           tuple(s.evals_prec), tuple(s.pairs_prec))
         if raise_on_error and st != 0:
             raise RsotError(st, "solve")
         return psi, stats
@@ -495,7 +556,8 @@ class Batch:
         stats = {"status": rc, "statuses": list(st), "grad_l1": gl1, "seconds": s.seconds,
                  "seconds_mixed": s.seconds_mixed, "seconds_refine": s.seconds_refine,
                  "rounds": s.rounds, "converged": s.converged, "max_grad_l1": s.max_grad_l1,
-                 "evals": s.evals}
+                 "evals": s.evals, "evals_prec": list(s.evals_prec),
+                 "pairs_prec": list(s.pairs_prec)}
         return psi, stats
 
 

@@ -25,6 +25,33 @@ bool is_device_ptr(const void *ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// 0: host memory, 1: device memory of the current device (or managed),
+// -1: device memory of another device (rejected: kernels here would need
+// peer access to read it)
+int where_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    int dev = -1;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
+}
+
+// device memory of the current device (or managed memory): what a kernel of
+// this library may read without peer access
+bool is_current_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    int dev = -1;
+    if (!ptr || cudaPointerGetAttributes(&a, ptr) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
+}
+
 rsot_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return RSOT_OK;
     if (e == cudaErrorMemoryAllocation) return RSOT_ERR_NOMEM;
@@ -135,25 +162,30 @@ void rsot_destroy(rsot_problem *p) {
     dense_free(p);
     cudaFree(p->xs);
     cudaFree(p->x64);
-    cudaFree(p->mass);
+    if (!p->borrowed) cudaFree(p->mass);
     cudaFree(p->lmass2);
     cudaFree(p->y64);
-    cudaFree(p->nu);
+    if (!p->borrowed) cudaFree(p->nu);
     cudaFree(p->lnu);
     cudaFree(p->psi_dev);
     cudaFree(p->grad_dev);
     cudaFree(p->res_dev);
     if (p->res_host) cudaFreeHost(p->res_host);
+    if (p->grad_host) cudaFreeHost(p->grad_host);
     for (cudaEvent_t e : p->tr_events) cudaEventDestroy(e);
     delete p;
 }
 
 rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, int64_t n,
-                        const double *y, const double *nu, rsot_problem **out) {
+                        const double *y, const double *nu, int device_ptrs, rsot_problem **out) {
     if (!out) return RSOT_ERR_ARG;
     *out = nullptr;
     if ((d != 2 && d != 3) || nq < 1 || n < 1 || !x || !mass || !y || !nu) return RSOT_ERR_ARG;
     if (nq > (int64_t)1 << 31 || n > (int64_t)1 << 30) return RSOT_ERR_ARG;
+    if (device_ptrs != 0 && device_ptrs != 1) return RSOT_ERR_ARG;
+    if (device_ptrs && (!is_current_device_ptr(x) || !is_current_device_ptr(mass) ||
+                        !is_current_device_ptr(y) || !is_current_device_ptr(nu)))
+        return RSOT_ERR_ARG;
 
     std::vector<double> hx((size_t)nq * d), hm((size_t)nq), hy((size_t)n * d), hnu((size_t)n);
     if (cudaMemcpy(hx.data(), x, hx.size() * 8, cudaMemcpyDefault) ||
@@ -239,16 +271,22 @@ rsot_status rsot_create(int d, int64_t nq, const double *x, const double *mass, 
     cudaError_t e = cudaSuccess;
     if (!e) e = upload(&p->xs, xs.data(), xs.size());
     if (!e) e = upload(&p->x64, hx.data(), hx.size());
-    if (!e) e = upload(&p->mass, hm.data(), hm.size());
+    p->borrowed = device_ptrs == 1;
+    if (p->borrowed) {
+        p->mass = const_cast<double *>(mass);
+        p->nu = const_cast<double *>(nu);
+    }
+    if (!e && !p->borrowed) e = upload(&p->mass, hm.data(), hm.size());
     if (!e) e = upload(&p->lmass2, lm2.data(), lm2.size());
     if (!e) e = upload(&p->y64, hy.data(), hy.size());
-    if (!e) e = upload(&p->nu, hnu.data(), hnu.size());
+    if (!e && !p->borrowed) e = upload(&p->nu, hnu.data(), hnu.size());
     if (!e) e = upload(&p->lnu, lnu.data(), lnu.size());
     if (!e) e = dense_alloc(p);
     if (!e) e = cudaMalloc(&p->psi_dev, (size_t)n * 8);
     if (!e) e = cudaMalloc(&p->grad_dev, (size_t)n * 8);
     if (!e) e = cudaMalloc(&p->res_dev, sizeof(EvalResult) + 8 * sizeof(double));
     if (!e) e = cudaMallocHost(&p->res_host, sizeof(EvalResult) + 8 * sizeof(double));
+    if (!e) e = cudaMallocHost(&p->grad_host, (size_t)n * 8);
     if (e) {
         cudaGetLastError();
         rsot_destroy(p);
@@ -281,16 +319,27 @@ static rsot_status eval_impl(rsot_problem *p, const double *psi, double eps, int
     if (!p || !psi || !J_out || !grad_out) return RSOT_ERR_ARG;
     if (!(eps > 0.0) || !isfinite(eps) || isnan(arg)) return RSOT_ERR_ARG;
     if (prec != RSOT_FP64 && prec != RSOT_MIXED && prec != RSOT_COMPENSATED) return RSOT_ERR_ARG;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    if (cur != p->dev) return RSOT_ERR_ARG;   // the handle's device must be current
+    const int wpsi = where_ptr(psi), wgrad = where_ptr(grad_out);
+    if (wpsi < 0 || wgrad < 0) return RSOT_ERR_ARG;
     cudaStream_t st = p->stream;
     const size_t nb = (size_t)p->n * sizeof(double);
     const double *psid = psi;
     cudaError_t e = cudaSuccess;
-    if (!is_device_ptr(psi)) {
+    if (wpsi == 0) {
         e = cudaMemcpyAsync(p->psi_dev, psi, nb, cudaMemcpyHostToDevice, st);
         psid = p->psi_dev;
     }
-    const bool gdev = is_device_ptr(grad_out);
-    double *gd = gdev ? grad_out : p->grad_dev;
+    // the passes write the handle's gradient; the caller's buffer receives it
+    // only when the evaluation succeeds (a device-side conditional copy, or a
+    // pinned staging copy for host memory)
+    const bool gdev = wgrad == 1;
+    double *gd = p->grad_dev;
     if (!e) e = cudaMemsetAsync(p->res_dev, 0, sizeof(EvalResult), st);
     // a radius beyond the diameter of the data keeps every pair: dense
     const bool dense = mode == 0 || (mode == 1 && (!(arg > 0.0) || isinf(arg) ||
@@ -305,7 +354,9 @@ static rsot_status eval_impl(rsot_problem *p, const double *psi, double eps, int
         else
             e = trunc_eval(p, psid, eps, prec == RSOT_MIXED, gd);
     }
-    if (!e && !gdev) e = cudaMemcpyAsync(grad_out, gd, nb, cudaMemcpyDeviceToHost, st);
+    if (!e && gdev && grad_out != gd)
+        e = launch_commit_grad(gd, grad_out, p->n, p->res_dev, dense ? 0 : 1, st);
+    if (!e && !gdev) e = cudaMemcpyAsync(p->grad_host, gd, nb, cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(EvalResult), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
     if (e) {
@@ -320,14 +371,20 @@ static rsot_status eval_impl(rsot_problem *p, const double *psi, double eps, int
     if (r.flags & kErrTimeout) return RSOT_ERR_TIMEOUT;
     if (r.flags & kErrBadCell) return RSOT_ERR_CUDA;
     if (r.flags & kErrNonfinitePsi) return RSOT_ERR_NONFINITE;
+    if (r.flags) return RSOT_ERR_CUDA;   // an error bit this code does not know
     if (!isfinite(r.J)) return RSOT_ERR_NONFINITE;
-    *J_out = r.J;
-    if (pairs_out) *pairs_out = dense ? p->nq * p->n : (int64_t)r.pairs;
     p->last_kind = prec == RSOT_COMPENSATED ? (dense ? 4 : 5)
                                             : dense ? (prec == RSOT_MIXED ? 1 : 0)
                                                     : (prec == RSOT_MIXED ? 3 : 2);
     p->last_eps = eps;
-    if (!dense && r.empty > 0) return RSOT_ERR_EMPTY_NEIGHBORHOOD;
+    p->last_dense = dense;
+    p->last_J = r.J;
+    p->last_pairs = dense ? p->nq * p->n : (int64_t)r.pairs;
+    p->last_empty = dense ? 0 : (int64_t)r.empty;
+    if (p->last_empty > 0) return RSOT_ERR_EMPTY_NEIGHBORHOOD;   // outputs untouched
+    *J_out = r.J;
+    if (pairs_out) *pairs_out = p->last_pairs;
+    if (!gdev) memcpy(grad_out, p->grad_host, nb);
     return RSOT_OK;
 }
 
@@ -342,6 +399,24 @@ rsot_status rsot_eval_dual_grad_tail(rsot_problem *p, const double *psi, double 
                                      int64_t *pairs_out) {
     if (!(tail > 0.0) || !(tail < 1.0)) return RSOT_ERR_ARG;
     return eval_impl(p, psi, eps, 2, tail, prec, J_out, grad_out, pairs_out);
+}
+
+rsot_status rsot_last_eval(rsot_problem *p, double *J_out, double *grad_out, int64_t *pairs_out,
+                           int64_t *empty_out) {
+    if (!p || p->last_kind < 0) return RSOT_ERR_ARG;
+    if (grad_out) {
+        cudaError_t e = cudaMemcpyAsync(grad_out, p->grad_dev, (size_t)p->n * sizeof(double),
+                                        cudaMemcpyDefault, p->stream);
+        if (!e) e = cudaStreamSynchronize(p->stream);
+        if (e) {
+            cudaGetLastError();
+            return from_cuda(e);
+        }
+    }
+    if (J_out) *J_out = p->last_J;
+    if (pairs_out) *pairs_out = p->last_pairs;
+    if (empty_out) *empty_out = p->last_empty;
+    return RSOT_OK;
 }
 
 rsot_status rsot_log_integrated_D(rsot_problem *p, double *lnD_out) {
@@ -476,15 +551,12 @@ rsot_status rsot_covering_cost(rsot_problem *p, double *C0_out) {
     return RSOT_OK;
 }
 
-rsot_status rsot_radius_for_tail(rsot_problem *p, const double *psi, double eps, double tail,
-                                 double *radius_out) {
-    if (!p || !psi || !radius_out || !(eps > 0.0) || !(tail > 0.0) || !(tail < 1.0))
-        return RSOT_ERR_ARG;
-    double C0;
-    rsot_status s = rsot_covering_cost(p, &C0);
-    if (s) return s;
+// max and min of a potential (host or device memory)
+static rsot_status psi_range(rsot_problem *p, const double *psi, double *mx_out, double *mn_out) {
     double mx = -INFINITY, mn = INFINITY;
-    if (is_device_ptr(psi)) {
+    const int w = where_ptr(psi);
+    if (w < 0) return RSOT_ERR_ARG;
+    if (w == 1) {
         double *aux = reinterpret_cast<double *>(p->res_dev + 1) + 2;
         double h[2];
         cudaError_t e = launch_psi_stats(p, psi, aux);
@@ -498,12 +570,55 @@ rsot_status rsot_radius_for_tail(rsot_problem *p, const double *psi, double eps,
         mn = h[1];
     } else {
         for (int64_t j = 0; j < p->n; ++j) {
+            if (!isfinite(psi[j])) return RSOT_ERR_NONFINITE;
             mx = std::max(mx, psi[j]);
             mn = std::min(mn, psi[j]);
         }
     }
     if (!isfinite(mx) || !isfinite(mn)) return RSOT_ERR_NONFINITE;
-    const double C = C0 + (mx - mn) + eps * log(1.0 / (p->nu_min * tail));
+    *mx_out = mx;
+    *mn_out = mn;
+    return RSOT_OK;
+}
+
+rsot_status rsot_truncation_cutoff(rsot_problem *p, const double *psi, double eps, int kind,
+                                   double param, double J, double lnD, double *C_out) {
+    if (!p || !psi || !C_out || !(eps > 0.0) || !isfinite(eps) || !(param > 0.0)) return RSOT_ERR_ARG;
+    if (kind < RSOT_CUTOFF_POINTWISE || kind > RSOT_CUTOFF_TAIL) return RSOT_ERR_ARG;
+    if ((kind == RSOT_CUTOFF_INTEGRAL || kind == RSOT_CUTOFF_GEOMETRIC) && !(fabs(J) > 0.0))
+        return RSOT_ERR_ARG;
+    if (kind == RSOT_CUTOFF_TAIL && !(param < 1.0)) return RSOT_ERR_ARG;
+    double mx = 0.0, mn = 0.0, C0 = 0.0;
+    rsot_status s = psi_range(p, psi, &mx, &mn);
+    if (s) return s;
+    if (kind == RSOT_CUTOFF_GEOMETRIC || kind == RSOT_CUTOFF_TAIL)
+        if ((s = rsot_covering_cost(p, &C0))) return s;
+    double C = 0.0;
+    switch (kind) {
+        case RSOT_CUTOFF_POINTWISE:   // Eq. cost_cutoff_delta
+            C = mx + eps * log(p->nu_max / param);
+            break;
+        case RSOT_CUTOFF_INTEGRAL:    // Eq. truncation_cutoff_int
+            C = mx + eps * (log(eps) + lnD - log(param) - log(fabs(J)));
+            break;
+        case RSOT_CUTOFF_GEOMETRIC:   // Eq. truncation_cutoff_geom
+            C = std::max(C0, C0 + (mx - mn) + eps * log(eps / (p->nu_min * param * fabs(J))));
+            break;
+        default:                      // the pointwise reading of App. B (tail)
+            C = C0 + (mx - mn) + eps * log(1.0 / (p->nu_min * param));
+    }
+    if (isnan(C)) return RSOT_ERR_NONFINITE;
+    *C_out = C;
+    return RSOT_OK;
+}
+
+rsot_status rsot_radius_for_tail(rsot_problem *p, const double *psi, double eps, double tail,
+                                 double *radius_out) {
+    if (!p || !psi || !radius_out || !(eps > 0.0) || !(tail > 0.0) || !(tail < 1.0))
+        return RSOT_ERR_ARG;
+    double C = 0.0;
+    rsot_status s = rsot_truncation_cutoff(p, psi, eps, RSOT_CUTOFF_TAIL, tail, 0.0, 0.0, &C);
+    if (s) return s;
     *radius_out = sqrt(2.0 * C);
     return RSOT_OK;
 }

@@ -33,7 +33,7 @@ extern "C" rsot_status rsot_barycenter(int K, const rsot_source_level *src, cons
         std::fill(ybar.begin(), ybar.end(), 0.0);
         for (int i = 0; i < K && !st; ++i) {
             rsot_problem *p = nullptr;
-            st = rsot_create(d, src[i].nq, src[i].x, src[i].mass, n, y.data(), nu, &p);
+            st = rsot_create(d, src[i].nq, src[i].x, src[i].mass, n, y.data(), nu, 0, &p);
             if (st) break;
             rsot_options o = *opt;
             if (it > 0) o.eps_start = 0.0;   // warm start: the support moved little

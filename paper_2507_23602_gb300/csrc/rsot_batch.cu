@@ -887,7 +887,7 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
             return RSOT_ERR_ARG;
         }
         rsot_problem *h = nullptr;
-        rsot_status s = rsot_create(D.d, D.nq, D.x, D.mass, D.n, D.y, D.nu, &h);
+        rsot_status s = rsot_create(D.d, D.nq, D.x, D.mass, D.n, D.y, D.nu, 0, &h);
         if (s) {
             rsot_batch_destroy(b);
             return s;
@@ -1130,6 +1130,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
     std::vector<double> gl1(P, 0.0);
     int rounds = 0;
     int64_t evals = 0;
+    int64_t evals_prec[3] = {0, 0, 0}, pairs_prec[3] = {0, 0, 0};
     double t_mixed = 0.0, t_ref = 0.0;
     // per-problem eps stages
     std::vector<std::vector<double>> stages(P);
@@ -1187,6 +1188,8 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                 mc[p].feed(b->J_h[p], g);
                 last_l1[p] = mc[p].grad_l1();
                 ++evals;
+                ++evals_prec[RSOT_MIXED];
+                pairs_prec[RSOT_MIXED] += Q.nq * Q.n;
                 if (mc[p].done()) {
                     const bool last = si[p] + 1 == (int)stages[p].size();
                     if (!last && (mc[p].status() == RSOT_OK || mc[p].status() == RSOT_ERR_LINESEARCH)) {
@@ -1222,7 +1225,7 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                 if (cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess)
                     streams[w] = nullptr;
             std::atomic<int> next{0};
-            std::vector<int64_t> wevals(nw, 0);
+            std::vector<int64_t> wevals(nw, 0), wprec((size_t)nw * 6, 0);
             auto worker = [&](int w) {
                 for (int i = next++; i < (int)order.size(); i = next++) {
                     const int p = order[i];
@@ -1235,6 +1238,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
                     st[p] = rsot_solve(b->handles[p], psi_all + Q.psi_off, &o, &ss);
                     gl1[p] = ss.grad_l1;
                     wevals[w] += ss.evals;
+                    for (int k = 0; k < 3; ++k) {
+                        wprec[(size_t)w * 6 + k] += ss.evals_prec[k];
+                        wprec[(size_t)w * 6 + 3 + k] += ss.pairs_prec[k];
+                    }
                     rsot_set_stream(b->handles[p], nullptr);
                 }
             };
@@ -1244,6 +1251,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
             for (auto &th : pool) th.join();
             for (int w = 0; w < nw; ++w) {
                 evals += wevals[w];
+                for (int k = 0; k < 3; ++k) {
+                    evals_prec[k] += wprec[(size_t)w * 6 + k];
+                    pairs_prec[k] += wprec[(size_t)w * 6 + 3 + k];
+                }
                 if (streams[w]) cudaStreamDestroy(streams[w]);
             }
             t_ref = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - t_mixed;
@@ -1259,6 +1270,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
             st[p] = rsot_solve(b->handles[p], psi_all + Q.psi_off, &o, &ss);
             gl1[p] = ss.grad_l1;
             evals += ss.evals;
+            for (int k = 0; k < 3; ++k) {
+                evals_prec[k] += ss.evals_prec[k];
+                pairs_prec[k] += ss.pairs_prec[k];
+            }
         }
     }
     int conv = 0;
@@ -1279,6 +1294,10 @@ rsot_status rsot_batch_solve(rsot_batch *b, double *psi_all, const double *eps,
         stats->converged = conv;
         stats->max_grad_l1 = mx;
         stats->evals = evals;
+        for (int k = 0; k < 3; ++k) {
+            stats->evals_prec[k] = evals_prec[k];
+            stats->pairs_prec[k] = pairs_prec[k];
+        }
     }
     return worst;
 }

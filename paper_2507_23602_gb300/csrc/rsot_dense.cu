@@ -28,6 +28,10 @@
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
+
+#include <cuda.h>
 
 #include "rsot_internal.cuh"
 #include "rsot_inner.cuh"
@@ -680,7 +684,7 @@ __global__ void __launch_bounds__(F_THREADS)
             ++npair;
             const double s = sy[i][3] - c * inv_eps;
             const double dlt = s - M;
-            const double e = exp(-fabs(dlt));
+            const double e = exp_f64(-fabs(dlt));
             if (dlt > 0.0) {
                 S = S * e + 1.0;
                 M = s;
@@ -757,7 +761,7 @@ __global__ void __launch_bounds__(F_THREADS)
                 c += dd * dd;
             }
             c *= 0.5;
-            if (c < sa[i] + bj) acc += exp(a - c * inv_eps + sp[i][3]);
+            if (c < sa[i] + bj) acc += exp_f64(a - c * inv_eps + sp[i][3]);
         }
         __syncthreads();
     }
@@ -1215,6 +1219,25 @@ cudaError_t launch_point_L(rsot_problem *p, double *L_dev) {
     return cudaGetLastError();
 }
 
+// Outputs are written only on success: the evaluation's gradient reaches the
+// caller's device buffer through this copy, which reads the result block on
+// the device (after every pass on the stream) and copies nothing on an error.
+__global__ void k_commit_grad(const double *__restrict__ src, double *__restrict__ dst, int64_t n,
+                              const EvalResult *__restrict__ res, int require_nonempty) {
+    const bool ok = res->flags == 0 && isfinite(res->J) && !(require_nonempty && res->empty > 0);
+    if (!ok) return;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        dst[j] = src[j];
+}
+
+cudaError_t launch_commit_grad(const double *src, double *dst, int64_t n, const EvalResult *res,
+                               int require_nonempty, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    k_commit_grad<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n, res, require_nonempty);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psi_stats(rsot_problem *p, const double *psi, double *out2) {
     k_psi_stats<<<1, 256, 0, p->stream>>>(psi, p->n, out2);
     return cudaGetLastError();
@@ -1233,40 +1256,75 @@ constexpr int64_t NA_MAX_NQ = RSOT_NOALLOC_MAX_NQ;   // multiple of 1024
 constexpr int64_t NA_MAX_N = RSOT_NOALLOC_MAX_N;     // multiple of 1024
 constexpr int NA_MAX_S2 = 16;                        // pass-2 point splits
 constexpr int NA_PTS_BLOCKS = (int)(NA_MAX_NQ / CB_THREADS);
+// pass-1 partials: k1 target chunks x nq_pad points, k1 * nq_pad <= NA_K1_ROWS
+// (small point sets take more chunks, so that the grid still fills the GPU)
+constexpr int64_t NA_K1_ROWS = 4 * NA_MAX_NQ;
+constexpr int NA_BBOX_BLOCKS = 1024;   // partial bounding boxes (6 doubles each)
 
 constexpr size_t na_align(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t NA_OFF_RES = 0;
 constexpr size_t NA_OFF_ORIGIN = na_align(NA_OFF_RES + sizeof(EvalResult));
-constexpr size_t NA_OFF_XS = na_align(NA_OFF_ORIGIN + 4 * sizeof(double));
+constexpr size_t NA_OFF_BBOX = na_align(NA_OFF_ORIGIN + 4 * sizeof(double));
+constexpr size_t NA_OFF_XS = na_align(NA_OFF_BBOX + 6 * NA_BBOX_BLOCKS * sizeof(double));
 constexpr size_t NA_OFF_LM2 = na_align(NA_OFF_XS + 3 * NA_MAX_NQ * sizeof(float));
 constexpr size_t NA_OFF_LSE = na_align(NA_OFF_LM2 + NA_MAX_NQ * sizeof(double));
 constexpr size_t NA_OFF_PDUP = na_align(NA_OFF_LSE + NA_MAX_NQ * sizeof(double));
 constexpr size_t NA_OFF_PART1 = na_align(NA_OFF_PDUP + NA_MAX_NQ * sizeof(Rec8));
-constexpr size_t NA_OFF_TDUP = na_align(NA_OFF_PART1 + NA_MAX_NQ * sizeof(float2));
+constexpr size_t NA_OFF_TDUP = na_align(NA_OFF_PART1 + NA_K1_ROWS * sizeof(float2));
 constexpr size_t NA_OFF_TPAIR = na_align(NA_OFF_TDUP + NA_MAX_N * sizeof(Rec8));
 constexpr size_t NA_OFF_PART2 = na_align(NA_OFF_TPAIR + (NA_MAX_N / 2) * sizeof(Rec8));
 constexpr size_t NA_OFF_BLOCKJ = na_align(NA_OFF_PART2 + (size_t)NA_MAX_S2 * NA_MAX_N * sizeof(double));
 constexpr size_t NA_OFF_PSINU = na_align(NA_OFF_BLOCKJ + (NA_MAX_NQ / CB_THREADS) * sizeof(double));
 constexpr size_t NA_OFF_PTS = na_align(NA_OFF_PSINU + (NA_MAX_N / CB_THREADS) * sizeof(double));
-constexpr size_t NA_BYTES = na_align(NA_OFF_PTS + 2 * NA_PTS_BLOCKS * sizeof(double));
+constexpr size_t NA_OFF_GRAD = na_align(NA_OFF_PTS + 2 * NA_PTS_BLOCKS * sizeof(double));
+constexpr size_t NA_BYTES = na_align(NA_OFF_GRAD + NA_MAX_N * sizeof(double));
+static_assert(NA_BYTES == RSOT_NOALLOC_SCRATCH_BYTES, "scratch size stated in rsot.h");
 
 // Shared by every call on a device; holds the last call's contents.
 static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
 
-// bounding-box centre of points and targets (one block)
-__global__ void k_na_origin(const double *__restrict__ x, int64_t nq, const double *__restrict__ y,
-                            int64_t n, int d, double *__restrict__ origin) {
+// Partial bounding boxes of points and targets: block b covers a grid-stride
+// share of both sets and writes (lo[3], hi[3]) to part[6 b ..].
+__global__ void k_na_bbox(const double *__restrict__ x, int64_t nq, const double *__restrict__ y,
+                          int64_t n, int d, double *__restrict__ part) {
     __shared__ double slo[3][256], shi[3][256];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = threadIdx.x; i < nq; i += blockDim.x)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq + n; i += stride) {
+        const double *v = i < nq ? x + i * d : y + (i - nq) * d;
         for (int k = 0; k < d; ++k) {
-            lo[k] = fmin(lo[k], x[i * d + k]);
-            hi[k] = fmax(hi[k], x[i * d + k]);
+            lo[k] = fmin(lo[k], v[k]);
+            hi[k] = fmax(hi[k], v[k]);
         }
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-        for (int k = 0; k < d; ++k) {
-            lo[k] = fmin(lo[k], y[j * d + k]);
-            hi[k] = fmax(hi[k], y[j * d + k]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        slo[k][threadIdx.x] = lo[k];
+        shi[k][threadIdx.x] = hi[k];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) {
+                slo[k][threadIdx.x] = fmin(slo[k][threadIdx.x], slo[k][threadIdx.x + o]);
+                shi[k][threadIdx.x] = fmax(shi[k][threadIdx.x], shi[k][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) {
+        part[6 * blockIdx.x + threadIdx.x] = slo[threadIdx.x][0];
+        part[6 * blockIdx.x + 3 + threadIdx.x] = shi[threadIdx.x][0];
+    }
+}
+
+// bounding-box centre from the partial boxes (one block)
+__global__ void k_na_origin(const double *__restrict__ part, int nparts, int d,
+                            double *__restrict__ origin) {
+    __shared__ double slo[3][256], shi[3][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], part[6 * b + k]);
+            hi[k] = fmax(hi[k], part[6 * b + 3 + k]);
         }
     for (int k = 0; k < 3; ++k) {
         slo[k][threadIdx.x] = lo[k];
@@ -1396,6 +1454,8 @@ cudaError_t na_launch(unsigned char *base, int64_t nq, const double *x, const do
     double *blockJ = reinterpret_cast<double *>(base + NA_OFF_BLOCKJ);
     double *psinu = reinterpret_cast<double *>(base + NA_OFF_PSINU);
     double *pts = reinterpret_cast<double *>(base + NA_OFF_PTS);
+    double *bbox = reinterpret_cast<double *>(base + NA_OFF_BBOX);
+    double *gscr = reinterpret_cast<double *>(base + NA_OFF_GRAD);
 
     const int64_t nq_pad = round_up(nq, P1_TILE);
     const int64_t n_alloc = round_up(n, 1024);
@@ -1404,14 +1464,24 @@ cudaError_t na_launch(unsigned char *base, int64_t nq, const double *x, const do
     const int nb_prep = (int)(n_alloc / CB_THREADS);
     cudaError_t e = cudaMemsetAsync(res, 0, sizeof(EvalResult), st);
     if (e) return e;
-    k_na_origin<<<1, 256, 0, st>>>(x, nq, y, n, D, origin);
+    const int nbb = (int)std::min<int64_t>({(int64_t)NA_BBOX_BLOCKS, (int64_t)num_sms * 4,
+                                            (nq + n + 255) / 256});
+    k_na_bbox<<<nbb, 256, 0, st>>>(x, nq, y, n, D, bbox);
+    k_na_origin<<<1, 256, 0, st>>>(bbox, nbb, D, origin);
     k_na_points<<<nb_pts, CB_THREADS, 0, st>>>(x, mass, nq, nq_pad, D, origin, xs, lm2, pts);
     k_na_targets<<<nb_prep, CB_THREADS, 0, st>>>(psi, y, nu, n, n_alloc, D, eps, origin, tdup,
                                                  tpair, psinu, &res->flags);
-    dim3 g1((unsigned)(nq_pad / P1_TILE), 1u);
-    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(xs, nq_pad, tdup, (int)n_p1, (int)n_p1, part1,
+    // pass 1 split over target chunks as the handle path splits it, within the
+    // partials' capacity
+    const int64_t tiles1 = nq_pad / P1_TILE;
+    const int64_t slots1 = (int64_t)num_sms * occupancy((const void *)k_lse_mixed<D>, P1_THREADS, 0);
+    int k1 = pick_split(tiles1, std::min<int64_t>(n_p1 / P1_TS, NA_K1_ROWS / nq_pad), slots1);
+    const int chunk1 = (int)round_up((n_p1 + k1 - 1) / k1, P1_TS);
+    k1 = (int)((n_p1 + chunk1 - 1) / chunk1);
+    dim3 g1((unsigned)tiles1, (unsigned)k1);
+    k_lse_mixed<D><<<g1, P1_THREADS, 0, st>>>(xs, nq_pad, tdup, (int)n_p1, chunk1, part1,
                                               &res->flags);
-    k_combine<<<nb_pts, CB_THREADS, 0, st>>>(part1, 1, nq_pad, nq, xs, D, lm2, mass, pdup, blockJ,
+    k_combine<<<nb_pts, CB_THREADS, 0, st>>>(part1, k1, nq_pad, nq, xs, D, lm2, mass, pdup, blockJ,
                                              lse);
     const int tpp = pick_tpp(n);
     const int64_t blk2 = (int64_t)P2_THREADS * 2 * tpp;
@@ -1431,38 +1501,78 @@ cudaError_t na_launch(unsigned char *base, int64_t nq, const double *x, const do
     else
         k_grad_mixed<D, 1><<<g2, P2_THREADS, 0, st>>>(tpair, pdup, nq_pad, chunk2, part2, n_alloc,
                                                       &res->flags);
-    k_finalize_grad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part2, s2, n_alloc, nu, n, grad);
+    // the gradient goes to the scratch first; the caller's buffer receives it
+    // only when the evaluation succeeded
+    k_finalize_grad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part2, s2, n_alloc, nu, n, gscr);
     k_na_finalize_J<<<1, 256, 0, st>>>(blockJ, nb_pts, psinu, nb_prep, pts, nb_pts, psi, eps, res);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError())) return e;
+    return launch_commit_grad(gscr, grad, n, res, 0, st);
+}
+
+// Unique id of the current CUDA context (cuCtxGetId through the runtime's
+// driver entry point); 0 when there is none yet or the driver lacks the call.
+unsigned long long current_context_id() {
+    using CtxCur = CUresult (*)(CUcontext *);
+    using CtxId = CUresult (*)(CUcontext, unsigned long long *);
+    static const std::pair<CtxCur, CtxId> fns = [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) !=
+                cudaSuccess || qa != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) !=
+                cudaSuccess || qb != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return std::pair<CtxCur, CtxId>(nullptr, nullptr);
+        }
+        return std::pair<CtxCur, CtxId>(reinterpret_cast<CtxCur>(a), reinterpret_cast<CtxId>(b));
+    }();
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!fns.first || !fns.second || fns.first(&c) != CUDA_SUCCESS || !c ||
+        fns.second(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
 }
 
 }  // namespace
 
-// Scratch address of g_na_scratch on the current device, looked up once per
-// device (with that device current) and cached.
-static unsigned char *na_scratch_for_device(int dev) {
+// Address of g_na_scratch in the current CUDA context.  The address belongs to
+// the context (a device's primary context, re-created after cudaDeviceReset,
+// or a context the caller created with the driver API), so it is looked up
+// with cudaGetSymbolAddress once per context -- the first call in a context,
+// with that context's device current -- and cached under the context's
+// unique id.
+static unsigned char *na_scratch_address() {
     static std::mutex mu;
-    static unsigned char *addr[256] = {nullptr};
-    if (dev < 0 || dev >= 256) return nullptr;
+    static std::vector<std::pair<unsigned long long, unsigned char *>> cache;
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_na_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        addr[dev] = static_cast<unsigned char *>(ptr);
+    unsigned long long id = current_context_id();
+    if (id)
+        for (const auto &c : cache)
+            if (c.first == id) return c.second;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_na_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return addr[dev];
+    if (!id) id = current_context_id();   // the lookup made the context current
+    if (id) {
+        if (cache.size() >= 64) cache.erase(cache.begin());
+        cache.emplace_back(id, static_cast<unsigned char *>(ptr));
+    }
+    return static_cast<unsigned char *>(ptr);
 }
 
+// device memory of the current device, or managed memory: the kernels here
+// read it without peer access
 static bool na_is_device(const void *p) {
     cudaPointerAttributes a;
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = -1;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 rsot_status eval_dense_noalloc(int d, int64_t nq, const double *x, const double *mass, int64_t n,
@@ -1480,7 +1590,7 @@ rsot_status eval_dense_noalloc(int d, int64_t nq, const double *x, const double 
         cudaGetLastError();
         return RSOT_ERR_CUDA;
     }
-    unsigned char *base = na_scratch_for_device(dev);
+    unsigned char *base = na_scratch_address();
     if (!base) return RSOT_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = d == 3 ? na_launch<3>(base, nq, x, mass, n, y, nu, psi, eps, grad, st, sms)
@@ -1508,6 +1618,55 @@ extern "C" rsot_status rsot_eval_dense_noalloc(int d, int64_t nq, const double *
 }
 
 namespace {
+// Self-test of the bounded waits.  One CTA issues a bulk copy into stage 0 and
+// arms stage 1 for 16 bytes that no copy ever delivers; every thread waits on
+// stage 1 with `limit` polling rounds, which runs out, and thread 0 records the
+// timeout.  Before returning, the CTA waits (normal limit) for its own copy in
+// stage 0 to land, so that nothing writes its shared memory after it exits.
+__global__ void k_wait_selftest(const float4 *__restrict__ src, long long limit,
+                                int *__restrict__ flags) {
+    __shared__ __align__(128) float4 buf[64];
+    __shared__ __align__(8) uint64_t bar[2];
+    if (threadIdx.x == 0) {
+        rsot::mbar_init(&bar[0], 1);
+        rsot::mbar_init(&bar[1], 1);
+        rsot::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rsot::mbar_expect_tx(&bar[0], (unsigned)sizeof(buf));
+        rsot::bulk_g2s(buf, src, (unsigned)sizeof(buf), &bar[0]);
+        rsot::mbar_expect_tx(&bar[1], 16u);    // never filled
+    }
+    __syncthreads();
+    const bool got = rsot::mbar_wait_n(&bar[1], 0, limit);
+    if (!got && threadIdx.x == 0) atomicOr(flags, rsot::kErrTimeout);
+    if (!rsot::mbar_wait(&bar[0], 0) && threadIdx.x == 0) atomicOr(flags, rsot::kErrTimeout);
+}
+
+// 8 independent chains a <- a b + c per thread (b = 1 - 2^-20, c = 2^-21: a
+// stays near its fixed point 1/2), one FP64 fused multiply-add each.
+__global__ void k_probe_dfma(double *out, int iters) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.5 + 0.01 * k + 1e-9 * threadIdx.x;
+    const double b = 1.0 - 9.5367431640625e-07, c = 4.76837158203125e-07;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == 123.456) out[threadIdx.x] = s;   // keeps the chains alive
+}
+
+__global__ void k_exp64(const double *__restrict__ x, double *__restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = rsot::exp_f64(x[i]);
+}
+
 // 8 independent chains x <- ex2(x) / 2 per thread keep x in [1/2, 1].
 __global__ void k_probe_ex2(float *out, int iters) {
     float a[8];
@@ -1550,5 +1709,79 @@ extern "C" rsot_status rsot_probe_ex2_rate(int iters, double *ex2_per_s) {
         return RSOT_ERR_CUDA;
     }
     *ex2_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+    return RSOT_OK;
+}
+
+extern "C" rsot_status rsot_selftest_wait_timeout(long long limit, void *stream) {
+    if (limit < 1 || limit > rsot::kWaitLimit) return RSOT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float4 *src = nullptr;
+    int *flags = nullptr;
+    int h = 0;
+    cudaError_t e = cudaMalloc(&src, 64 * sizeof(float4));
+    if (!e) e = cudaMalloc(&flags, sizeof(int));
+    if (!e) e = cudaMemsetAsync(src, 0, 64 * sizeof(float4), st);
+    if (!e) e = cudaMemsetAsync(flags, 0, sizeof(int), st);
+    if (!e) {
+        k_wait_selftest<<<1, 128, 0, st>>>(src, limit, flags);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    cudaFree(src);
+    cudaFree(flags);
+    if (e) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? RSOT_ERR_NOMEM : RSOT_ERR_CUDA;
+    }
+    return (h & rsot::kErrTimeout) ? RSOT_ERR_TIMEOUT : RSOT_OK;
+}
+
+extern "C" rsot_status rsot_probe_dfma_rate(int iters, double *dfma_per_s) {
+    if (iters < 1 || !dfma_per_s) return RSOT_ERR_ARG;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    double *out = nullptr;
+    cudaEvent_t a, b;
+    if (cudaMalloc(&out, 1024 * sizeof(double))) return RSOT_ERR_NOMEM;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int blocks = sms * 8, threads = 256;
+    k_probe_dfma<<<blocks, threads>>>(out, iters);   // warm-up
+    cudaEventRecord(a);
+    k_probe_dfma<<<blocks, threads>>>(out, iters);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (!e) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (e || ms <= 0.f) {
+        cudaGetLastError();
+        return RSOT_ERR_CUDA;
+    }
+    *dfma_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+    return RSOT_OK;
+}
+
+extern "C" rsot_status rsot_exp64(int64_t n, const double *x, double *y) {
+    if (n < 1 || !x || !y) return RSOT_ERR_ARG;
+    double *dx = nullptr, *dy = nullptr;
+    cudaError_t e = cudaMalloc(&dx, (size_t)n * 8);
+    if (!e) e = cudaMalloc(&dy, (size_t)n * 8);
+    if (!e) e = cudaMemcpy(dx, x, (size_t)n * 8, cudaMemcpyDefault);
+    if (!e) {
+        k_exp64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256>>>(dx, dy, n);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpy(y, dy, (size_t)n * 8, cudaMemcpyDefault);
+    cudaFree(dx);
+    cudaFree(dy);
+    if (e) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? RSOT_ERR_NOMEM : RSOT_ERR_CUDA;
+    }
     return RSOT_OK;
 }

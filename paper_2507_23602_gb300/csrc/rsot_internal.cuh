@@ -135,13 +135,18 @@ struct rsot_problem {
 
     // staging for host psi / grad
     double *psi_dev = nullptr;      // [n]
-    double *grad_dev = nullptr;     // [n]
+    bool borrowed = false;          // mass and nu are the caller's device arrays (not freed)
+    double *grad_dev = nullptr;     // [n] gradient of the last evaluation
+    double *grad_host = nullptr;    // [n] pinned staging of host gradient outputs
     rsot::EvalResult *res_dev = nullptr;
     rsot::EvalResult *res_host = nullptr;   // pinned
     int *flags = nullptr;           // device error bits (inside res_dev)
 
     // per-point log partition of the last evaluation (see rsot_point_log_partition)
     double *lse_buf = nullptr;      // [nq_pad]: R_q (mixed, log2) or L'_q (FP64, natural)
+    bool last_dense = true;         // the last evaluation's J, pair and empty-point counts
+    double last_J = 0.0;            // (rsot_last_eval; its gradient stays in grad_dev)
+    int64_t last_pairs = 0, last_empty = 0;
     int last_kind = -1;             // -1 none, 0 FP64 dense, 1 mixed dense, 2/3 truncated (FP64 /
                                     // mixed cell list), 4/5 compensated
                                     // FP64/mixed, 4/5 compensated dense/truncated
@@ -198,6 +203,10 @@ cudaError_t launch_trunc_fp64(rsot_problem *p, const double *psi_dev, double eps
 cudaError_t launch_covering_cost(rsot_problem *p, double *C0_dev);
 cudaError_t launch_psi_stats(rsot_problem *p, const double *psi_dev, double *out3_dev);
 cudaError_t launch_point_L(rsot_problem *p, double *L_dev);
+// Copy an evaluation's gradient src -> dst only when the result block reports
+// success (no error bit, finite J, and with require_nonempty no empty point).
+cudaError_t launch_commit_grad(const double *src, double *dst, int64_t n,
+                               const EvalResult *res, int require_nonempty, cudaStream_t st);
 cudaError_t launch_softmax_refine(rsot_problem *p, const double *psi_dev, double eps, int64_t nf,
                                   const double *yf_dev, double *out_dev);
 
@@ -262,6 +271,44 @@ __device__ __forceinline__ double pow2_int_d(float k) {
     return k < -1022.0f ? 0.0 : __longlong_as_double((long long)((int)k + 1023) << 52);
 }
 
+// e^x in FP64 for the FP64 passes (one call per pair and pass).  Cody & Waite's
+// argument reduction: k = rint(x / ln 2), r = x - k ln 2 with ln 2 split as
+// kLn2Hi (its leading 32 significant bits, so k kLn2Hi is exact for |k| < 2^21)
+// + kLn2Lo, |r| <= ln(2)/2; e^r by its Taylor polynomial of degree 13
+// (remainder r^14/14! < 6e-18 relative, below half an ulp) in Horner form;
+// then the scaling by 2^k, in two steps below the normal range.  About 2 ulp.
+// Written out (instead of CUDA's exp) so that the FP64 operations per pair
+// are known: 1 multiply + 1 round + 2 fma (reduction), 13 fma (polynomial),
+// 1 multiply (scaling) and 2 compares (range).
+__device__ __forceinline__ double exp_f64(double x) {
+    constexpr double kLn2Hi = 6.93147180369123816490e-01;   // 0x3fe62e42fee00000
+    constexpr double kLn2Lo = 1.90821492927058770002e-10;   // ln 2 - kLn2Hi, rounded
+    if (!(x > -745.2)) return x != x ? x : 0.0;   // NaN stays NaN; underflow -> 0
+    if (x > 709.8) return INFINITY;
+    const double k = rint(x * kLog2e);
+    double r = fma(-k, kLn2Hi, x);
+    r = fma(-k, kLn2Lo, r);
+    double p = 1.0 / 6227020800.0;                 // 1/13!
+    p = fma(p, r, 1.0 / 479001600.0);              // 1/12!
+    p = fma(p, r, 1.0 / 39916800.0);
+    p = fma(p, r, 1.0 / 3628800.0);
+    p = fma(p, r, 1.0 / 362880.0);
+    p = fma(p, r, 1.0 / 40320.0);
+    p = fma(p, r, 1.0 / 5040.0);
+    p = fma(p, r, 1.0 / 720.0);
+    p = fma(p, r, 1.0 / 120.0);
+    p = fma(p, r, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
+    const int ki = (int)k;
+    if (ki > 1023) return (2.0 * p) * 8.98846567431158e307;   // 2^1024 is not a double: 2 p 2^1023
+    if (ki >= -1022) return p * __longlong_as_double((long long)(ki + 1023) << 52);
+    // 2^k below the normal range: 2^(k + 64) (normal) times 2^-64
+    return (p * __longlong_as_double((long long)(ki + 64 + 1023) << 52)) * 5.421010862427522e-20;
+}
+
 // ---- mbarrier + bulk-copy (TMA) wrappers ------------------------------------
 constexpr long long kWaitLimit = 1ll << 24;   // bounded spin: ~seconds at most
 
@@ -303,10 +350,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Bounded wait; false when the limit is reached (the caller records an error).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
-    for (long long i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, unsigned phase, long long limit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+    return mbar_wait_n(bar, phase, kWaitLimit);
 }
 
 // Classification of a block pair for the truncated passes: balls a, b (centre,

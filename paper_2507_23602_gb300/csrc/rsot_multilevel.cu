@@ -188,6 +188,7 @@ rsot_status rsot_softmax_refine(rsot_problem *p, const double *psi_coarse, doubl
     if (!p || !psi_coarse || !y_fine || !psi_fine_out || n_fine < 1 || !(eps > 0.0)) return RSOT_ERR_ARG;
     cudaStream_t st = p->stream;
     const int d = p->d;
+    p->last_kind = -1;   // its pass 1 replaces the per-point sums of the last evaluation
     double *dpsi = nullptr, *dyf = nullptr, *dout = nullptr;
     cudaError_t e = cudaMallocAsync(&dpsi, (size_t)p->n * 8, st);
     if (!e) e = cudaMallocAsync(&dyf, (size_t)n_fine * d * 8, st);
@@ -196,8 +197,15 @@ rsot_status rsot_softmax_refine(rsot_problem *p, const double *psi_coarse, doubl
     if (!e) e = cudaMemcpyAsync(dyf, y_fine, (size_t)n_fine * d * 8, cudaMemcpyDefault, st);
     if (!e) e = cudaMemsetAsync(p->res_dev, 0, sizeof(EvalResult), st);
     if (!e) e = launch_softmax_refine(p, dpsi, eps, n_fine, dyf, dout);
-    if (!e) e = cudaMemcpyAsync(psi_fine_out, dout, (size_t)n_fine * 8, cudaMemcpyDefault, st);
     if (!e) e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(EvalResult), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    // the output is written only when the passes succeeded
+    rsot_status s = RSOT_OK;
+    if (!e) {
+        if (p->res_host->flags & kErrTimeout) s = RSOT_ERR_TIMEOUT;
+        else if (p->res_host->flags & kErrNonfinitePsi) s = RSOT_ERR_NONFINITE;
+        else e = cudaMemcpyAsync(psi_fine_out, dout, (size_t)n_fine * 8, cudaMemcpyDefault, st);
+    }
     cudaFreeAsync(dpsi, st);
     cudaFreeAsync(dyf, st);
     cudaFreeAsync(dout, st);
@@ -206,9 +214,7 @@ rsot_status rsot_softmax_refine(rsot_problem *p, const double *psi_coarse, doubl
         cudaGetLastError();
         return RSOT_ERR_CUDA;
     }
-    if (p->res_host->flags & kErrTimeout) return RSOT_ERR_TIMEOUT;
-    if (p->res_host->flags & kErrNonfinitePsi) return RSOT_ERR_NONFINITE;
-    return RSOT_OK;
+    return s;
 }
 
 rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n_tgt,
@@ -232,7 +238,7 @@ rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n
         const double eps = eps_levels[l];
         const auto t0 = std::chrono::steady_clock::now();
         rsot_problem *p = nullptr;
-        rsot_status s = rsot_create(S.d, S.nq, S.x, S.mass, T.n, T.y, T.nu, &p);
+        rsot_status s = rsot_create(S.d, S.nq, S.x, S.mass, T.n, T.y, T.nu, 0, &p);
         if (s) return s;
         int transfer = 0;   // 0 none (first level), 1 injection, 2 softmax refinement
         if (l == 0) {
@@ -244,7 +250,7 @@ rsot_status rsot_multilevel_solve(int n_src, const rsot_source_level *src, int n
             transfer = 2;
             const rsot_target_level &Tc = tgt[it_prev];
             rsot_problem *pc = nullptr;
-            s = rsot_create(S.d, S.nq, S.x, S.mass, Tc.n, Tc.y, Tc.nu, &pc);
+            s = rsot_create(S.d, S.nq, S.x, S.mass, Tc.n, Tc.y, Tc.nu, 0, &pc);
             if (!s) {
                 std::vector<double> fine(T.n);
                 // the coarse pair (phi, psi) is optimal at the previous level's eps

@@ -54,42 +54,75 @@ void pair_kernel_for_gradient(rsot_problem *p, double grad_l1);
 
 namespace {
 
+// evaluations and pairs by precision over one solve
+struct PrecCount {
+    int evals[3] = {0, 0, 0};
+    int64_t pairs[3] = {0, 0, 0};
+};
+
+// Cutoff of a truncated evaluation (Sec. 4.1): none (dense), the psi-aware
+// cutoffs of a tail tolerance, or one of the paper's global cutoffs C_int,
+// C_pw, C_geom (rsot_truncation_cutoff).
+struct Truncation {
+    double tail = 0.0, tau_int = 0.0, delta_pw = 0.0, tau_geom = 0.0;
+};
+
 struct Evaluator {
     rsot_problem *p;
     int64_t n;
     double eps;
-    double tail;
+    Truncation tr;
     rsot_precision prec;
-    double tau_int = 0.0;
+    PrecCount *count = nullptr;
     int evals = 0;
     int64_t pairs = 0;
+    int64_t skipped = 0;      // points left without a target (C_pw, C_geom), summed
     rsot_status last = RSOT_OK;
-    bool have_prev = false;   // integral cutoff: ln D and J of the previous evaluation
+    bool have_prev = false;   // ln D and J of the previous evaluation (C_int, C_geom)
     double lnD_prev = 0.0, J_prev = 0.0;
 
     rsot_status operator()(const std::vector<double> &psi, double &J, std::vector<double> &g) {
         int64_t pr = 0;
         rsot_status s;
-        if (tail > 0.0) {
+        if (tr.tail > 0.0) {
             // the psi-aware cutoffs of that tail tolerance (Sec. 4.1, App. B)
-            s = rsot_eval_dual_grad_tail(p, psi.data(), eps, tail, prec, &J, g.data(), &pr);
+            s = rsot_eval_dual_grad_tail(p, psi.data(), eps, tr.tail, prec, &J, g.data(), &pr);
         } else {
             double radius = 0.0;   // dense
-            if (tau_int > 0.0 && have_prev) {
-                // C_int = M + eps ln(eps D / (tau |J|)) (Eq. truncation_cutoff_int) with D
-                // and J of the previous evaluation, kept above the covering cost so that
-                // every point keeps its nearest target
-                double M = -INFINITY;
-                for (double v : psi) M = std::max(M, v);
+            double C = NAN;
+            if (tr.tau_int > 0.0 && have_prev) {
+                // C_int (Eq. truncation_cutoff_int) with D and J of the previous
+                // evaluation, kept above the covering cost so that every point keeps
+                // its nearest target
                 double C0 = 0.0;
                 if ((s = rsot_covering_cost(p, &C0))) return last = s;
-                double C = M + eps * (log(eps) + lnD_prev - log(tau_int) - log(fabs(J_prev)));
-                if (isfinite(C)) radius = sqrt(2.0 * std::max(C, C0 * (1.0 + 1e-5) + 1e-12));
+                if ((s = rsot_truncation_cutoff(p, psi.data(), eps, RSOT_CUTOFF_INTEGRAL, tr.tau_int,
+                                                J_prev, lnD_prev, &C)))
+                    return last = s;
+                if (isfinite(C)) C = std::max(C, C0 * (1.0 + 1e-5) + 1e-12);
+            } else if (tr.delta_pw > 0.0) {
+                // C_pw of the current potential (Eq. cost_cutoff_delta)
+                if ((s = rsot_truncation_cutoff(p, psi.data(), eps, RSOT_CUTOFF_POINTWISE, tr.delta_pw,
+                                                0.0, 0.0, &C)))
+                    return last = s;
+            } else if (tr.tau_geom > 0.0 && have_prev) {
+                // C_geom (Eq. truncation_cutoff_geom) with J of the previous evaluation
+                if ((s = rsot_truncation_cutoff(p, psi.data(), eps, RSOT_CUTOFF_GEOMETRIC, tr.tau_geom,
+                                                J_prev, 0.0, &C)))
+                    return last = s;
             }
+            // a cutoff at or below 0 keeps no pair (every point is skipped)
+            if (isfinite(C)) radius = C > 0.0 ? sqrt(2.0 * C) : 1e-150;
             s = rsot_eval_dual_grad(p, psi.data(), eps, radius, prec, &J, g.data(), &pr);
-            if (!s && tau_int > 0.0) {
+            if (s == RSOT_ERR_EMPTY_NEIGHBORHOOD && (tr.delta_pw > 0.0 || tr.tau_geom > 0.0)) {
+                // Algorithm 2 skips points whose truncated sum is empty
+                int64_t empty = 0;
+                s = rsot_last_eval(p, &J, g.data(), &pr, &empty);
+                skipped += empty;
+            }
+            if (!s && (tr.tau_int > 0.0 || tr.tau_geom > 0.0)) {
                 double lnD = INFINITY;
-                if ((s = rsot_log_integrated_D(p, &lnD))) return last = s;
+                if (tr.tau_int > 0.0 && (s = rsot_log_integrated_D(p, &lnD))) return last = s;
                 lnD_prev = lnD;
                 J_prev = J;
                 have_prev = J != 0.0;
@@ -97,6 +130,10 @@ struct Evaluator {
         }
         ++evals;
         pairs += pr;
+        if (count) {
+            ++count->evals[prec];
+            count->pairs[prec] += pr;
+        }
         return last = s;
     }
 };
@@ -194,7 +231,14 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         return RSOT_ERR_ARG;
     if (opt->refine_precision != RSOT_FP64 && opt->refine_precision != RSOT_COMPENSATED)
         return RSOT_ERR_ARG;
-    if (opt->tau_int < 0.0 || (opt->tau_int > 0.0 && opt->tail > 0.0)) return RSOT_ERR_ARG;
+    if (opt->tau_int < 0.0 || opt->delta_pw < 0.0 || opt->tau_geom < 0.0) return RSOT_ERR_ARG;
+    if ((opt->tail > 0.0) + (opt->tau_int > 0.0) + (opt->delta_pw > 0.0) + (opt->tau_geom > 0.0) > 1)
+        return RSOT_ERR_ARG;   // one truncation at a time
+    Truncation trunc;
+    trunc.tail = opt->tail;
+    trunc.tau_int = opt->tau_int;
+    trunc.delta_pw = opt->delta_pw;
+    trunc.tau_geom = opt->tau_geom;
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t n = rsot::num_targets(p);
     std::vector<double> nu(n);
@@ -220,7 +264,9 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     const double msum = rsot::mass_sum(p);
     double nusum = 0.0;
     for (int64_t j = 0; j < n; ++j) nusum += nu[j];
-    const double ref_tail = (opt->tail > 0.0 && opt->tail <= kRefTailMax && opt->tau_int <= 0.0) ? opt->tail : 0.0;
+    const double ref_tail = (opt->tail > 0.0 && opt->tail <= kRefTailMax) ? opt->tail : 0.0;
+    Truncation ref_trunc;
+    ref_trunc.tail = ref_tail;
     const double comp_bound =
         RSOT_COMPENSATED_GRAD_REL * msum + ref_tail * nusum * (2.0 * msum + nusum);
     const bool comp_ref = opt->refine_precision == RSOT_COMPENSATED && comp_bound <= 0.8 * opt->tol_l1;
@@ -233,6 +279,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     double f = 0.0;
     int iters = 0, evals = 0, stages = 0;
     int64_t pairs = 0;
+    PrecCount pc;
     rsot_status st = RSOT_OK;
     for (size_t si = 0; si < eps_list.size(); ++si) {
         const double eps = eps_list[si];
@@ -243,7 +290,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         const rsot_precision prec = (opt->precision == RSOT_COMPENSATED && last && !comp_ref)
                                         ? RSOT_FP64
                                         : (rsot_precision)opt->precision;
-        Evaluator ev{p, n, eps, opt->tail, prec, opt->tau_int};
+        Evaluator ev{p, n, eps, trunc, prec, &pc};
         rsot::LbfgsMachine mc;
         double tol_run = tol;
         if (last && opt->precision == RSOT_MIXED && opt->refine_fp64)
@@ -274,8 +321,8 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
             // its bound inside comp_bound (the stop then holds for the
             // untruncated J); a truncated mixed phase differs by tail-level
             // terms, which the correction absorbs
-            Evaluator evc{p, n, eps, ref_tail, RSOT_COMPENSATED, 0.0};
-            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
+            Evaluator evc{p, n, eps, ref_trunc, RSOT_COMPENSATED, &pc};
+            Evaluator evm{p, n, eps, trunc, RSOT_MIXED, &pc};
             const int kernel_before = rsot::pair_kernel_of(p);
             rsot_set_pair_kernel(p, RSOT_PAIRS_FP32);
             double fc = 0.0, fm = 0.0;
@@ -312,8 +359,8 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         } else if (refine && refine_ok) {
             // corrected refinement: one reference and one mixed evaluation per
             // correction, mixed L-BFGS on the corrected objective in between
-            Evaluator ev64{p, n, eps, 0.0, ref_prec, 0.0};   // dense reference, as above
-            Evaluator evm{p, n, eps, opt->tail, RSOT_MIXED, opt->tau_int};
+            Evaluator ev64{p, n, eps, Truncation(), ref_prec, &pc};   // dense reference, as above
+            Evaluator evm{p, n, eps, trunc, RSOT_MIXED, &pc};
             // the refinement works below the random rounding noise of the
             // tensor-core exponents (rms ~2e-5 per pair, several 1e-6 in the L1
             // norm of a large gradient): its mixed evaluations take the FP32
@@ -379,6 +426,10 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         stats->pairs = pairs;
         stats->seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int k = 0; k < 3; ++k) {
+            stats->evals_prec[k] = pc.evals[k];
+            stats->pairs_prec[k] = pc.pairs[k];
+        }
     }
     return st;
 }

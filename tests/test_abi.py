@@ -62,8 +62,8 @@ def test_argument_errors_need_no_gpu(lib):
     so, _ = lib
     h = ctypes.c_void_p()
     # d = 4 is rejected before any CUDA call
-    assert so.rsot_create(4, 10, None, None, 5, None, None, ctypes.byref(h)) == 1
-    assert so.rsot_create(2, 0, None, None, 5, None, None, ctypes.byref(h)) == 1
+    assert so.rsot_create(4, 10, None, None, 5, None, None, 0, ctypes.byref(h)) == 1
+    assert so.rsot_create(2, 0, None, None, 5, None, None, 0, ctypes.byref(h)) == 1
     assert so.rsot_eval_dual_grad(None, None, ctypes.c_double(0.1), ctypes.c_double(0.0), 1,
                                   None, None, None) == 1
 
@@ -98,4 +98,6 @@ def test_binding_constants_match_the_header(lib):
     assert set(rs.STATUS) == {v for n, v in vals.items() if n.startswith("RSOT_ERR_") or n == "RSOT_OK"}
     assert rs.COMPENSATED_GRAD_REL == defs["RSOT_COMPENSATED_GRAD_REL"]
     assert rs.MAX_LEVELS == defs["RSOT_MAX_LEVELS"]
+    for name in ("NOALLOC_MAX_NQ", "NOALLOC_MAX_N", "NOALLOC_SCRATCH_BYTES"):
+        assert getattr(rs, name) == defs["RSOT_" + name], name
     assert checked >= 18

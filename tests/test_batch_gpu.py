@@ -91,7 +91,7 @@ def test_batch_solve_mixed_with_refinement_reaches_tolerance():
         assert st["rounds"] > 0
         for i, p in enumerate(probs):
             _, go, _, _ = oracle.dual_grad(p.x, p.mass, p.y, p.nu, B.split(psi)[i], eps[i])
-            assert np.sum(np.abs(go)) <= 1.5e-6, i
+            assert np.sum(np.abs(go)) <= 1e-6 * (1 + 1e-9), i
         # the plain FP64 path reaches the same minimisers (up to the constant)
         psi64, st64 = B.solve(eps, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6,
                               precision=rs().FP64)

@@ -26,6 +26,33 @@ def setup(in_dim, width, rows, seed, kind=0):
 
 KINDS = [0, 1, 2]   # GEMM_TCGEN05 (TMA), GEMM_MMA_SYNC, GEMM_TCGEN05_CPASYNC
 
+# Element-wise bounds, per entry relative to its scale s (the same sum over the
+# absolute values of its terms, oracle.mlp.abs_scales):
+#  * FP32 accumulation of K <= 4096 products (tensor-core GEMMs, split-K sums):
+#    at most about K 2^-24 s <= 2.5e-4 s;
+#  * a bfloat16 operand (activation H or back-propagated dZ) rounded the other
+#    way than in the FP64 oracle (its pre-rounding value within FP32 error of a
+#    rounding boundary) moves its own term by one bf16 unit, 2^-8 of the term,
+#    and the flipped terms of one sum are part of s: at most 2 x 2^-8 s;
+# so |g - g_o| <= 1e-2 s for every entry.  Flips touch few terms of each sum:
+# measured on GB300 over these shapes (all three GEMM kernels), err / s has a
+# median below 1e-5 and a 99th percentile below 1.5e-4; the checks below leave
+# a margin of ten and would fail for a wrong operand, index or dropped term,
+# which put the error at the size of s itself.
+REL_BOUND = 1e-2
+REL_MEDIAN = 1e-4
+REL_P99 = 2e-3
+
+
+def elementwise(a, b, s):
+    a = np.asarray(a, dtype=np.float64)
+    err = np.abs(a - b)
+    bad = err > REL_BOUND * s + 1e-12
+    assert not np.any(bad), (np.flatnonzero(bad)[:8], err[bad][:8], s[bad][:8])
+    r = err / np.maximum(s, 1e-30)
+    q50, q99 = np.quantile(r, [0.5, 0.99])
+    assert q50 <= REL_MEDIAN and q99 <= REL_P99, (q50, q99)
+
 
 @pytest.mark.parametrize("kind", KINDS)
 # (3, 64, 37): fewer rows than one TMA box; (5, 104, 300): K = 104, so the
@@ -36,8 +63,10 @@ def test_forward_matches_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 7, kind)
     try:
         out = net.forward(x)
-        ref, _ = omlp.forward(net.params(), x.astype(np.float64), in_dim, width)
-        assert np.max(np.abs(out - ref)) <= 5e-3 * np.max(np.abs(ref)) + 1e-4
+        x64 = x.astype(np.float64)
+        ref, _ = omlp.forward(net.params(), x64, in_dim, width)
+        scale, _ = omlp.abs_scales(net.params(), x64, y.astype(np.float64), in_dim, width)
+        elementwise(out, ref, scale)
     finally:
         net.close()
 
@@ -49,16 +78,11 @@ def test_gradients_match_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 11, kind)
     try:
         loss, g = net.gradients(x, y)
-        lo, go = omlp.loss_and_grad(net.params(), x.astype(np.float64), y.astype(np.float64),
-                                    in_dim, width)
+        x64, y64 = x.astype(np.float64), y.astype(np.float64)
+        lo, go = omlp.loss_and_grad(net.params(), x64, y64, in_dim, width)
         assert abs(loss - lo) <= 1e-3 * abs(lo)
-        in_pad = (in_dim + 31) // 32 * 32
-        sizes = [width * in_pad, width, width * width, width, width * width, width, width, 1]
-        o = 0
-        for s in sizes:
-            a, b = g[o:o + s], go[o:o + s]
-            assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, (o, s)
-            o += s
+        _, scale = omlp.abs_scales(net.params(), x64, y64, in_dim, width)
+        elementwise(g, go, scale)
     finally:
         net.close()
 

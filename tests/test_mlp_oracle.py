@@ -51,3 +51,24 @@ def test_zero_residual_gives_zero_gradient():
     y, _ = mlp.forward(p, x, in_dim, width, emulate_bf16=False)
     loss, g = mlp.loss_and_grad(p, x, y, in_dim, width, emulate_bf16=False)
     assert loss == 0.0 and np.all(g == 0.0)
+
+
+def test_abs_scales_bound_the_signed_sums_and_equal_them_for_one_row():
+    """abs_scales takes each gradient sum over |terms|: it bounds |grad| entry by
+    entry, and with a single row every weight and bias gradient has one term,
+    so the scale is exactly |grad| (a dropped or transposed factor would break
+    either)."""
+    in_dim, width = 5, 16
+    p = params(in_dim, width, 5)
+    rng = np.random.default_rng(6)
+    x = rng.normal(0, 1, (30, in_dim))
+    y = rng.normal(0, 1, 30)
+    out, _ = mlp.forward(p, x, in_dim, width)
+    _, g = mlp.loss_and_grad(p, x, y, in_dim, width)
+    so, sg = mlp.abs_scales(p, x, y, in_dim, width)
+    assert np.all(np.abs(g) <= sg * (1 + 1e-12))
+    assert np.all(np.abs(out) <= so * (1 + 1e-12))
+    assert np.sum(sg) > 1.5 * np.sum(np.abs(g))       # cancellation present with 30 rows
+    _, g1 = mlp.loss_and_grad(p, x[:1], y[:1], in_dim, width)
+    so1, sg1 = mlp.abs_scales(p, x[:1], y[:1], in_dim, width)
+    assert np.allclose(sg1, np.abs(g1), rtol=1e-12, atol=0.0)

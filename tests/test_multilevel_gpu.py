@@ -85,7 +85,7 @@ def test_multilevel_solve_reaches_tolerance_and_matches_single_level():
     assert st["grad_l1"] <= 1e-6
     xf, mf = src[-1]
     _, go, _, _ = oracle.dual_grad(xf, mf, y, nu, psi, eps)
-    assert np.sum(np.abs(go)) <= 1.5e-6
+    assert np.sum(np.abs(go)) <= 1e-6 * (1 + 1e-9)
     P = rs().Problem(xf, mf, y, nu)
     try:
         psi1, st1 = P.solve(eps=eps, tol_l1=1e-6, precision=rs().MIXED)

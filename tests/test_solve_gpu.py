@@ -28,7 +28,7 @@ def test_small_2d_fp64_solve_matches_oracle_solve():
         assert st.status == 0 and st.grad_l1 <= 1e-8
         # the reported gradient norm is the oracle's too
         Jo, go, _, _ = oracle.dual_grad(p.x, p.mass, p.y, p.nu, psi, p.eps)
-        assert np.sum(np.abs(go)) <= 1.5e-8
+        assert np.sum(np.abs(go)) <= 1e-8 * (1 + 1e-9)
         assert abs(st.J - Jo) <= 1e-10 * abs(Jo)
     finally:
         P.close()
@@ -47,7 +47,7 @@ def test_mixed_solve_with_fp64_refinement_reaches_tolerance():
         assert st.status == 0 and st.grad_l1 <= 1e-6
         assert st.stages == 6
         _, go, _, _ = oracle.dual_grad(p.x, p.mass, p.y, p.nu, psi, p.eps)
-        assert np.sum(np.abs(go)) <= 1.5e-6
+        assert np.sum(np.abs(go)) <= 1e-6 * (1 + 1e-9)
     finally:
         P.close()
 
