@@ -101,18 +101,24 @@ void rsot_destroy(rsot_problem *p);
 rsot_status rsot_set_stream(rsot_problem *p, void *stream);
 
 /*
- * Instruction form of the pair arithmetic of the mixed dense passes
- * (Algorithm 2's exponent (psi_j - c(x_q, y_j))/eps + ln nu_j).
- *   RSOT_PAIRS_TENSOR evaluates the exponent as a 16-term inner product on
- *     the tensor cores (f16 head/tail operand pairs, f32 accumulation; a
- *     random error of rms ~2e-5 in log2 units at eps = 1e-3, four times the
- *     FP32 chain's) and falls back to the FP32 kernels by itself, per
- *     evaluation, when an operand leaves the f16 range (very small eps,
- *     very large potentials).  Both passes form bitwise the same exponents.
- *   RSOT_PAIRS_FP32 always takes the FP32 kernels.
- *   RSOT_PAIRS_AUTO (the default) takes the tensor cores when
- *     max_q m_q * max_j nu_j <= 2e-6, where their error keeps every gradient
- *     entry ten times inside the mixed path's bound, else the FP32 kernels.
+ * Instruction form of the pair arithmetic of the mixed passes (Algorithm 2's
+ * exponent (psi_j - c(x_q, y_j))/eps + ln nu_j).
+ *   RSOT_PAIRS_FP32   : FP32 fused multiply-adds for every pair.
+ *   RSOT_PAIRS_TENSOR : the exponent as a 16-term inner product on the tensor
+ *     cores (mma.sync, f16 head/tail operand pairs, f32 accumulation; its
+ *     error is within about twice the FP32 chain's, see below), falling back
+ *     to the FP32 kernels by itself, per evaluation, when an operand leaves
+ *     the f16 range.  Both passes form bitwise the same exponents.
+ *   RSOT_PAIRS_AUTO (the default): every evaluation returned to the caller
+ *     (rsot_eval_dual_grad, _tail, the maps) uses the FP32 form; inside
+ *     rsot_solve and the batched and multilevel solvers, whose stop is
+ *     certified on compensated or FP64 reference evaluations, the mixed
+ *     iterations take the tensor-core form while the gradient is far above
+ *     its rounding noise.
+ * Neither form has a per-entry worst-case bound of 1e-6 at large eps-scaled
+ * magnitudes (the FP32 rounding of the per-point shift and of the stage sums,
+ * common to both, allows more for a target that collects a few percent of the
+ * mass); the mixed tolerances are measured against the FP64 oracle.
  * Not a paper concept: a choice of kernel.
  * Errors: RSOT_ERR_ARG (NULL handle or unknown kind).
  */
@@ -274,9 +280,10 @@ rsot_status rsot_probe_ex2_rate(int iters, double *ex2_per_s);
 rsot_status rsot_probe_dfma_rate(int iters, double *dfma_per_s);
 
 /*
- * The FP64 path's exponential on the GPU, y_i = e^{x_i} (Cody & Waite
- * reduction, Taylor polynomial of degree 13; about 2 ulp; 0 below -745.2,
- * +inf above 709.8, NaN kept), exposed so that its accuracy can be tested.
+ * The FP64 path's exponential on the GPU, y_i = e^{x_i} (Tang's table-driven
+ * method: 64 table values of 2^(j/64), Taylor polynomial of degree 6 on
+ * |r| <= ln(2)/128; about 1 ulp; 0 below -745.2, +inf above 709.8, NaN kept),
+ * exposed so that its accuracy can be tested.
  *   x, y : n doubles (host or device)
  */
 rsot_status rsot_exp64(int64_t n, const double *x, double *y);
@@ -443,9 +450,11 @@ rsot_status rsot_batch_create(int count, const rsot_problem_desc *probs, rsot_ba
 void rsot_batch_destroy(rsot_batch *b);
 rsot_status rsot_batch_set_stream(rsot_batch *b, void *stream);
 
-/* Pair kernel of the batched mixed passes (see rsot_set_pair_kernel); the
- * automatic choice takes the tensor cores when every problem of the batch
- * meets its bound.  Errors: RSOT_ERR_ARG, RSOT_ERR_CUDA. */
+/* Pair kernel of the batched mixed passes (see rsot_set_pair_kernel):
+ * rsot_batch_eval uses the FP32 form unless RSOT_PAIRS_TENSOR; the batched
+ * solver's rounds (and rsot_batch_tune, which times them) take the tensor-core
+ * form under RSOT_PAIRS_AUTO when every problem is within its range, until a
+ * problem's gradient approaches its noise.  Errors: RSOT_ERR_ARG, RSOT_ERR_CUDA. */
 rsot_status rsot_batch_set_pair_kernel(rsot_batch *b, rsot_pair_kernel kind);
 
 /* Total number of targets (length of the concatenated psi / gradient vectors). */

@@ -126,6 +126,7 @@ void copy_nu(const rsot_problem *p, double *out) {
     cudaMemcpy(out, p->nu, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost);
 }
 int pair_kernel_of(const rsot_problem *p) { return p->pair_kernel; }
+void set_in_solve(rsot_problem *p, int on) { p->in_solve = on; }
 // A solver near convergence: the next mixed evaluations take the FP32 kernels
 // when the gradient's L1 norm is within kTcNoiseFactor of the tensor-core noise.
 void pair_kernel_for_gradient(rsot_problem *p, double grad_l1) {

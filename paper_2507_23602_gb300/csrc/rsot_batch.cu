@@ -1064,15 +1064,19 @@ rsot_status rsot_batch_set_stream(rsot_batch *b, void *stream) {
     return to_status(build_graph(b));
 }
 
-rsot_status rsot_batch_eval(rsot_batch *b, const double *psi_all, const double *eps,
-                            const unsigned char *active, double *J_out, double *grad_all) {
+// One batched evaluation; solver_round: a round of the batched solver (the
+// tensor-core form under RSOT_PAIRS_AUTO), else an evaluation returned to the
+// caller (FP32 pair arithmetic unless RSOT_PAIRS_TENSOR)
+static rsot_status batch_eval_impl(rsot_batch *b, const double *psi_all, const double *eps,
+                                   const unsigned char *active, double *J_out, double *grad_all,
+                                   bool solver_round) {
     if (!b || !psi_all || !eps || !J_out || !grad_all) return RSOT_ERR_ARG;
     for (int p = 0; p < b->count; ++p)
         if (!(eps[p] > 0.0) || !isfinite(eps[p])) return RSOT_ERR_ARG;
     memcpy(b->psi_h, psi_all, b->tot_n * 8);
     memcpy(b->eps_h, eps, b->count * 8);
     for (int p = 0; p < b->count; ++p) b->active_h[p] = active ? (active[p] ? 1 : 0) : 1;
-    rsot_status s = run_round(b);
+    rsot_status s = run_round(b, !(b->pair_kernel == 1 || (b->pair_kernel == 2 && solver_round)));
     if (s) return s;
     for (int p = 0; p < b->count; ++p) {
         if (!b->active_h[p]) continue;
@@ -1081,6 +1085,11 @@ rsot_status rsot_batch_eval(rsot_batch *b, const double *psi_all, const double *
         memcpy(grad_all + P.psi_off, b->grad_h + P.psi_off, P.n * 8);
     }
     return RSOT_OK;
+}
+
+rsot_status rsot_batch_eval(rsot_batch *b, const double *psi_all, const double *eps,
+                            const unsigned char *active, double *J_out, double *grad_all) {
+    return batch_eval_impl(b, psi_all, eps, active, J_out, grad_all, false);
 }
 
 rsot_status rsot_batch_tune(rsot_batch *b, const double *psi_all, const double *eps, int *choice_out) {
@@ -1093,10 +1102,11 @@ rsot_status rsot_batch_tune(rsot_batch *b, const double *psi_all, const double *
         cudaError_t ce = upload_plan(b);
         if (!ce) ce = build_graph(b);
         if (ce) return to_status(ce);
-        rsot_status s = rsot_batch_eval(b, psi_all, eps, nullptr, J.data(), g.data());   // warm
+        // the solver's rounds are what the item size is tuned for
+        rsot_status s = batch_eval_impl(b, psi_all, eps, nullptr, J.data(), g.data(), true);   // warm
         if (s) return s;
         const auto t0 = std::chrono::steady_clock::now();
-        s = rsot_batch_eval(b, psi_all, eps, nullptr, J.data(), g.data());
+        s = batch_eval_impl(b, psi_all, eps, nullptr, J.data(), g.data(), true);
         if (s) return s;
         const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (t < best_t) {

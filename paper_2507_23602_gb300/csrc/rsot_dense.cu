@@ -36,6 +36,7 @@
 #include "rsot_internal.cuh"
 #include "rsot_inner.cuh"
 #include "rsot_tc.cuh"
+#include "rsot_exp64.cuh"
 
 namespace rsot {
 namespace {
@@ -634,27 +635,32 @@ __global__ void k_prep_fp64(const double *__restrict__ psi, const double *__rest
     if (threadIdx.x == 0) psinu_part[blockIdx.x] = s;
 }
 
-// alpha = nullptr: dense; otherwise only pairs with c(x_q, y_j) < alpha_q +
-// beta_j enter (Algorithm 2 with a cutoff per pair, rsot_cutoff.cu), the
-// number of such pairs and of empty points is counted.
-template <int D>
+// TRUNC = false: dense; true: only pairs with c(x_q, y_j) < alpha_q + beta_j
+// enter (Algorithm 2 with a cutoff per pair, rsot_cutoff.cu), and the number
+// of such pairs and of empty points is counted.  The squared distance d2 =
+// |x - y|^2 = 2 c enters as s = a_j - d2 / (2 eps); the cutoff test compares
+// d2 < 2 alpha_q + 2 beta_j (the same decision as c < alpha_q + beta_j:
+// doubling is exact).
+template <int D, bool TRUNC>
 __global__ void __launch_bounds__(F_THREADS)
     k_lse_fp64(const double *__restrict__ x64, int64_t nq, int64_t nq_pad,
                const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
-               double inv_eps, const double *__restrict__ alpha, const double *__restrict__ beta,
+               double half_inv_eps, const double *__restrict__ alpha, const double *__restrict__ beta,
                const double *__restrict__ psi, double eps,
                const double *__restrict__ mass, double *__restrict__ prec64,
                double *__restrict__ blockJ, double *__restrict__ lse_buf,
                EvalResult *__restrict__ res) {
     __shared__ double sy[F_TS][5];
     __shared__ double sh[32];
+    __shared__ double2 s_tab[64];
     __shared__ unsigned long long s_cnt, s_empty;
     if (threadIdx.x == 0) s_cnt = s_empty = 0;
+    load_exp2_tab(s_tab);
     const int64_t q = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
     double x[3] = {0.0, 0.0, 0.0};
     if (q < nq)
         for (int t = 0; t < D; ++t) x[t] = x64[q * D + t];
-    const double aq = alpha && q < nq ? alpha[q] : INFINITY;
+    const double aq2 = TRUNC && q < nq ? 2.0 * alpha[q] : INFINITY;
     double M = -INFINITY, S = 0.0;
     unsigned long long npair = 0;
     __syncthreads();
@@ -664,7 +670,7 @@ __global__ void __launch_bounds__(F_THREADS)
             if (j < n) {
                 for (int t = 0; t < D; ++t) sy[i][t] = y64[j * D + t];
                 sy[i][3] = a64[j];
-                sy[i][4] = alpha ? beta[j] : 0.0;
+                sy[i][4] = TRUNC ? 2.0 * beta[j] : 0.0;
             } else {
                 sy[i][3] = -INFINITY;
                 sy[i][4] = 0.0;
@@ -673,20 +679,21 @@ __global__ void __launch_bounds__(F_THREADS)
         __syncthreads();
         const int cnt = (int)min((int64_t)F_TS, n - t0);
         for (int i = 0; i < cnt; ++i) {
-            double c = 0.0;
+            double d2 = 0.0;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
                 const double dd = x[t] - sy[i][t];
-                c += dd * dd;
+                d2 = fma(dd, dd, d2);
             }
-            c *= 0.5;
-            if (!(c < aq + sy[i][4])) continue;
-            ++npair;
-            const double s = sy[i][3] - c * inv_eps;
+            if (TRUNC) {
+                if (!(d2 < aq2 + sy[i][4])) continue;
+                ++npair;
+            }
+            const double s = fma(-d2, half_inv_eps, sy[i][3]);
             const double dlt = s - M;
-            const double e = exp_f64(-fabs(dlt));
+            const double e = exp_tab(-fabs(dlt), s_tab);
             if (dlt > 0.0) {
-                S = S * e + 1.0;
+                S = fma(S, e, 1.0);
                 M = s;
             } else {
                 S += e;
@@ -709,7 +716,7 @@ __global__ void __launch_bounds__(F_THREADS)
                 lse_buf[q] = -INFINITY;
                 atomicAdd(&s_empty, 1ull);
             }
-            atomicAdd(&s_cnt, npair);
+            if (TRUNC) atomicAdd(&s_cnt, npair);
         }
         double *r = prec64 + q * 4;
         r[0] = x[0];
@@ -725,21 +732,23 @@ __global__ void __launch_bounds__(F_THREADS)
     }
 }
 
-template <int D>
+template <int D, bool TRUNC>
 __global__ void __launch_bounds__(F_THREADS)
     k_grad_fp64(const double *__restrict__ y64, const double *__restrict__ a64, int64_t n,
-                const double *__restrict__ prec64, int64_t nq_pad, int64_t chunk, double inv_eps,
-                const double *__restrict__ alpha, const double *__restrict__ beta,
-                double *__restrict__ part2, int64_t stride) {
+                const double *__restrict__ prec64, int64_t nq_pad, int64_t chunk,
+                double half_inv_eps, const double *__restrict__ alpha,
+                const double *__restrict__ beta, double *__restrict__ part2, int64_t stride) {
     __shared__ double sp[F_TS][4];
     __shared__ double sa[F_TS];
+    __shared__ double2 s_tab[64];
+    load_exp2_tab(s_tab);
     const int64_t j = (int64_t)blockIdx.x * F_THREADS + threadIdx.x;
     double y[3] = {0.0, 0.0, 0.0};
-    double a = -INFINITY, bj = 0.0;
+    double a = -INFINITY, bj2 = 0.0;
     if (j < n) {
         for (int t = 0; t < D; ++t) y[t] = y64[j * D + t];
         a = a64[j];
-        if (alpha) bj = beta[j];
+        if (TRUNC) bj2 = 2.0 * beta[j];
     }
     const int64_t p_begin = (int64_t)blockIdx.y * chunk;
     const int64_t p_end = min(nq_pad, p_begin + chunk);
@@ -749,19 +758,20 @@ __global__ void __launch_bounds__(F_THREADS)
             const int64_t idx = p0 * 4 + i;
             (&sp[0][0])[i] = (idx < p_end * 4) ? prec64[idx] : (((i & 3) == 3) ? -INFINITY : 0.0);
         }
-        for (int i = threadIdx.x; i < F_TS; i += F_THREADS)
-            sa[i] = !alpha ? INFINITY : (p0 + i < p_end ? alpha[p0 + i] : -INFINITY);
+        if (TRUNC)
+            for (int i = threadIdx.x; i < F_TS; i += F_THREADS)
+                sa[i] = p0 + i < p_end ? 2.0 * alpha[p0 + i] : -INFINITY;
         __syncthreads();
         const int cnt = (int)min((int64_t)F_TS, p_end - p0);
         for (int i = 0; i < cnt; ++i) {
-            double c = 0.0;
+            double d2 = 0.0;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
                 const double dd = sp[i][t] - y[t];   // x - y, as in pass 1
-                c += dd * dd;
+                d2 = fma(dd, dd, d2);
             }
-            c *= 0.5;
-            if (c < sa[i] + bj) acc += exp_f64(a - c * inv_eps + sp[i][3]);
+            if (TRUNC && !(d2 < sa[i] + bj2)) continue;
+            acc += exp_tab(fma(-d2, half_inv_eps, a) + sp[i][3], s_tab);
         }
         __syncthreads();
     }
@@ -1168,16 +1178,27 @@ static cudaError_t launch_fp64_d(rsot_problem *p, const double *psi, double eps,
                                                      p->a64, p->psinu, p->flags);
     trace_end(p);
     const unsigned nb1 = (unsigned)((p->nq_pad + F_THREADS - 1) / F_THREADS);
+    const double hinv = 0.5 * (1.0 / eps);   // exact halving of 1/eps
     trace_begin(p, "lse_fp64");
-    k_lse_fp64<D><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64, p->n,
-                                             1.0 / eps, alpha, beta, psi, eps, p->mass, p->prec64,
-                                             p->blockJ, p->lse_buf, p->res_dev);
+    if (alpha)
+        k_lse_fp64<D, true><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64,
+                                                       p->n, hinv, alpha, beta, psi, eps, p->mass,
+                                                       p->prec64, p->blockJ, p->lse_buf, p->res_dev);
+    else
+        k_lse_fp64<D, false><<<nb1, F_THREADS, 0, st>>>(p->x64, p->nq, p->nq_pad, p->y64, p->a64,
+                                                        p->n, hinv, alpha, beta, psi, eps, p->mass,
+                                                        p->prec64, p->blockJ, p->lse_buf, p->res_dev);
     trace_end(p);
     dim3 g2((unsigned)((p->n + F_THREADS - 1) / F_THREADS), (unsigned)p->s2_64);
     trace_begin(p, "grad_fp64");
-    k_grad_fp64<D><<<g2, F_THREADS, 0, st>>>(p->y64, p->a64, p->n, p->prec64, p->nq_pad,
-                                             p->chunk2_64, 1.0 / eps, alpha, beta, p->part2_64,
-                                             p->n_pad);
+    if (alpha)
+        k_grad_fp64<D, true><<<g2, F_THREADS, 0, st>>>(p->y64, p->a64, p->n, p->prec64, p->nq_pad,
+                                                       p->chunk2_64, hinv, alpha, beta, p->part2_64,
+                                                       p->n_pad);
+    else
+        k_grad_fp64<D, false><<<g2, F_THREADS, 0, st>>>(p->y64, p->a64, p->n, p->prec64, p->nq_pad,
+                                                        p->chunk2_64, hinv, alpha, beta,
+                                                        p->part2_64, p->n_pad);
     trace_end(p);
     trace_begin(p, "finalize_grad");
     k_finalize_grad<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(p->part2_64, p->s2_64,
@@ -1662,9 +1683,11 @@ __global__ void k_probe_dfma(double *out, int iters) {
 }
 
 __global__ void k_exp64(const double *__restrict__ x, double *__restrict__ y, int64_t n) {
+    __shared__ double2 s_tab[64];
+    rsot::load_exp2_tab(s_tab);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = rsot::exp_f64(x[i]);
+        y[i] = rsot::exp_tab(x[i], s_tab);
 }
 
 // 8 independent chains x <- ex2(x) / 2 per thread keep x in [1/2, 1].

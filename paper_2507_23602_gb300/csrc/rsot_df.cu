@@ -274,13 +274,14 @@ __device__ __forceinline__ int exp_test(float rh, float nb, float A) {
 }
 template <int D>
 __device__ __forceinline__ bool keep_fp64(const double *x64, const double *y64, double a64, double b64) {
-    double c = 0.0;
+    // the FP64 passes' test, written the same way: d2 = |x - y|^2 < 2 a + 2 b
+    double d2 = 0.0;
 #pragma unroll
     for (int t = 0; t < D; ++t) {
         const double dd = x64[t] - y64[t];
-        c += dd * dd;
+        d2 = fma(dd, dd, d2);
     }
-    return 0.5 * c < a64 + b64;
+    return d2 < 2.0 * a64 + 2.0 * b64;
 }
 
 // static point records (x' head/tail; the shift is written by pass 1)

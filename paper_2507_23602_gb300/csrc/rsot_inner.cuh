@@ -33,7 +33,13 @@ inline constexpr int P1_THREADS = 128;
 inline constexpr int P1_PP = RSOT_P1_PP;                      // point pairs per thread (<= 4)
 inline constexpr int P1_TILE = P1_THREADS * 2 * P1_PP;        // points per CTA (divides 1024)
 inline constexpr int P1_MINB = RSOT_P1_MINB;                  // resident CTAs per SM asked of ptxas
-inline constexpr int P1_TS = 256;                             // targets per stage
+#ifndef RSOT_P1_TS
+#define RSOT_P1_TS 512
+#endif
+#ifndef RSOT_P2_TS
+#define RSOT_P2_TS 512
+#endif
+inline constexpr int P1_TS = RSOT_P1_TS;                      // targets per stage (divides 1024)
 inline constexpr int P1_STAGES = 2;
 inline constexpr int P1_SUB = RSOT_P1_SUB;                    // targets per optimistic sub-tile
 inline constexpr int P2_MINB = RSOT_P2_MINB;
@@ -41,7 +47,8 @@ inline constexpr int P2_TPP_MAX = RSOT_P2_TPP;                // target pairs pe
 inline constexpr float P1_BIG = 1.152921504606846976e18f;     // 2^60: a sub-tile sum above it is redone
 
 inline constexpr int P2_THREADS = 128;
-inline constexpr int P2_TS = 256;                             // points per stage
+inline constexpr int P2_TS = RSOT_P2_TS;                      // points per stage (divides 1024)
+static_assert(1024 % P1_TS == 0 && 1024 % P2_TS == 0 && P1_TS % P1_SUB == 0, "stage shapes");
 inline constexpr int P2_STAGES = 2;
 
 

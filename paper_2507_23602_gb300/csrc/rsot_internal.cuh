@@ -102,6 +102,7 @@ struct rsot_problem {
     // kernels once the gradient is within kTcNoiseFactor of it
     double tc_noise_l1 = 0.0;
     int pair_fp32_now = 0;          // set by a solver: this evaluation takes the FP32 kernels
+    int in_solve = 0;               // set while rsot_solve runs on this handle
     int k1_tc = 0, chunk1_tc = 0;   // pass-1 target chunks of the tensor-core launch
     int s2_tc = 0;                  // pass-2 point splits of the tensor-core launch
     int64_t chunk2_tc = 0;
@@ -170,19 +171,23 @@ struct rsot_problem {
 
 namespace rsot {
 
-// Automatic choice of the pair kernel of the mixed passes.  The tensor-core
-// exponents carry a random error of rms ~2e-5 (log2 units, at eps = 1e-3
-// magnitudes; measured against exact sums) against ~5e-6 for the FP32 chain;
-// a gradient entry sum_q m_q p_qj then errs by ~ln2 2e-5 sqrt(sum_q (m_q
-// p_qj)^2) <= 1.4e-5 sqrt(m_max nu_max).  Below m_max nu_max = 2e-6 five such
-// standard deviations stay under 1e-7, a tenth of the per-entry bound of the
-// mixed path; smaller problems (few points or heavy targets) take the FP32
-// kernels.
+// Choice of the pair kernel of the mixed passes.  Every evaluation whose
+// result goes back to the caller takes the FP32 pair arithmetic unless the
+// caller asked for the tensor-core form (RSOT_PAIRS_TENSOR).  Inside the
+// library's solvers (in_solve), whose stop is certified by compensated or
+// FP64 reference evaluations, RSOT_PAIRS_AUTO lets the mixed L-BFGS iterations
+// take the tensor-core form while its rounding noise is far below the
+// gradient: the exponent's error is within about twice the FP32 chain's
+// (measured maxima 5.7 and 2.7 units of 2^-24 times the sum of the magnitudes
+// of its terms), random in sign, and a gradient entry sum_q m_q p_qj then
+// scatters by ~1.4e-5 sqrt(m_max nu_max); where that scatter is no longer
+// small (m_max nu_max > kTcAuto) or the gradient approaches it (pair_fp32_now,
+// kTcNoiseFactor) the solver keeps the FP32 kernels, which converge further.
 constexpr double kTcAuto = 2e-6;
 constexpr double kTcNoiseFactor = 30.0;
 inline bool use_tensor_pairs(const rsot_problem *p) {
     if (p->pair_kernel == 1) return true;
-    return p->pair_kernel == 2 && !p->pair_fp32_now && p->m_max * p->nu_max <= kTcAuto;
+    return p->pair_kernel == 2 && p->in_solve && !p->pair_fp32_now && p->m_max * p->nu_max <= kTcAuto;
 }
 
 // ---- kernel tracing (rsot_api.cu) -------------------------------------------
@@ -269,44 +274,6 @@ __device__ __forceinline__ float pow2_int_f(float k) {
 }
 __device__ __forceinline__ double pow2_int_d(float k) {
     return k < -1022.0f ? 0.0 : __longlong_as_double((long long)((int)k + 1023) << 52);
-}
-
-// e^x in FP64 for the FP64 passes (one call per pair and pass).  Cody & Waite's
-// argument reduction: k = rint(x / ln 2), r = x - k ln 2 with ln 2 split as
-// kLn2Hi (its leading 32 significant bits, so k kLn2Hi is exact for |k| < 2^21)
-// + kLn2Lo, |r| <= ln(2)/2; e^r by its Taylor polynomial of degree 13
-// (remainder r^14/14! < 6e-18 relative, below half an ulp) in Horner form;
-// then the scaling by 2^k, in two steps below the normal range.  About 2 ulp.
-// Written out (instead of CUDA's exp) so that the FP64 operations per pair
-// are known: 1 multiply + 1 round + 2 fma (reduction), 13 fma (polynomial),
-// 1 multiply (scaling) and 2 compares (range).
-__device__ __forceinline__ double exp_f64(double x) {
-    constexpr double kLn2Hi = 6.93147180369123816490e-01;   // 0x3fe62e42fee00000
-    constexpr double kLn2Lo = 1.90821492927058770002e-10;   // ln 2 - kLn2Hi, rounded
-    if (!(x > -745.2)) return x != x ? x : 0.0;   // NaN stays NaN; underflow -> 0
-    if (x > 709.8) return INFINITY;
-    const double k = rint(x * kLog2e);
-    double r = fma(-k, kLn2Hi, x);
-    r = fma(-k, kLn2Lo, r);
-    double p = 1.0 / 6227020800.0;                 // 1/13!
-    p = fma(p, r, 1.0 / 479001600.0);              // 1/12!
-    p = fma(p, r, 1.0 / 39916800.0);
-    p = fma(p, r, 1.0 / 3628800.0);
-    p = fma(p, r, 1.0 / 362880.0);
-    p = fma(p, r, 1.0 / 40320.0);
-    p = fma(p, r, 1.0 / 5040.0);
-    p = fma(p, r, 1.0 / 720.0);
-    p = fma(p, r, 1.0 / 120.0);
-    p = fma(p, r, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
-    p = fma(p, r, 0.5);
-    p = fma(p, r, 1.0);
-    p = fma(p, r, 1.0);
-    const int ki = (int)k;
-    if (ki > 1023) return (2.0 * p) * 8.98846567431158e307;   // 2^1024 is not a double: 2 p 2^1023
-    if (ki >= -1022) return p * __longlong_as_double((long long)(ki + 1023) << 52);
-    // 2^k below the normal range: 2^(k + 64) (normal) times 2^-64
-    return (p * __longlong_as_double((long long)(ki + 64 + 1023) << 52)) * 5.421010862427522e-20;
 }
 
 // ---- mbarrier + bulk-copy (TMA) wrappers ------------------------------------

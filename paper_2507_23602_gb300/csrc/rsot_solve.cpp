@@ -50,6 +50,7 @@ double mass_sum(const rsot_problem *p);
 void copy_nu(const rsot_problem *p, double *out);
 int pair_kernel_of(const rsot_problem *p);
 void pair_kernel_for_gradient(rsot_problem *p, double grad_l1);
+void set_in_solve(rsot_problem *p, int on);
 }  // namespace rsot
 
 namespace {
@@ -275,6 +276,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     const double ref_noise = comp_ref ? 1e-6 : 1e-13;
 
     rsot::pair_kernel_for_gradient(p, INFINITY);
+    rsot::set_in_solve(p, 1);   // mixed iterations may take the tensor-core form
     std::vector<double> x(psi_inout, psi_inout + n), g(n, 0.0), D(n);
     double f = 0.0;
     int iters = 0, evals = 0, stages = 0;
@@ -416,6 +418,7 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
         st = RSOT_OK;
     }
     rsot::pair_kernel_for_gradient(p, INFINITY);
+    rsot::set_in_solve(p, 0);
     std::copy(x.begin(), x.end(), psi_inout);
     if (stats) {
         stats->J = f;

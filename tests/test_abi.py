@@ -101,3 +101,19 @@ def test_binding_constants_match_the_header(lib):
     for name in ("NOALLOC_MAX_NQ", "NOALLOC_MAX_N", "NOALLOC_SCRATCH_BYTES"):
         assert getattr(rs, name) == defs["RSOT_" + name], name
     assert checked >= 18
+
+
+def test_exp2_table_of_the_fp64_exponential():
+    """The FP64 path's table: hi = 2^(j/64) rounded to FP64 and lo = the FP64
+    value nearest 2^(j/64) - hi, checked in 200-bit arithmetic."""
+    mpmath = pytest.importorskip("mpmath")
+    src = open(os.path.join(ROOT, "paper_2507_23602_gb300", "csrc", "rsot_exp64.cuh")).read()
+    body = src[src.index("kExp2Tab[64] = {"):]
+    body = body[:body.index("};")]
+    pairs = re.findall(r"\{([-0-9.e+]+),\s*([-0-9.e+]+)\}", body)
+    assert len(pairs) == 64
+    mpmath.mp.prec = 200
+    for j, (hi, lo) in enumerate(pairs):
+        t = mpmath.power(2, mpmath.mpf(j) / 64)
+        assert float(hi) == float(t)
+        assert float(lo) == float(t - mpmath.mpf(float(hi)))

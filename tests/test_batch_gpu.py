@@ -58,8 +58,9 @@ def test_batch_eval_matches_single_problem_and_oracle():
 
 
 def test_batch_pair_kernels_agree_with_the_oracle():
-    """The batched tensor-core passes (the automatic choice on these problems) and
-    the batched FP32 passes both meet the mixed bounds against the oracle."""
+    """The batched tensor-core passes (forced) and the batched FP32 passes (forced,
+    and the automatic choice for evaluations returned to the caller) meet the
+    mixed bounds against the oracle."""
     probs, eps = small_batch(seed0=400, count=5)
     B = rs().Batch([(p.x, p.mass, p.y, p.nu) for p in probs])
     rng = np.random.default_rng(2)

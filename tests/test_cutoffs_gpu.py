@@ -39,7 +39,12 @@ def test_cutoffs_match_the_oracle_statements(d):
     P = rs().Problem(x, m, y, nu)
     try:
         Jd, _, _, _ = oracle.dual_grad(x, m, y, nu, psi, eps)
-        C0 = oracle.covering_cost(x, y)
+        # the covering cost comes from an FP32 nearest-target search on FP32
+        # coordinates (|dc| <= |x - y| |d(x - y)| ~ sqrt(2 C_0) 2^-23 plus 1e-7
+        # relative); the cutoffs built on it are compared on the GPU's C_0
+        C0o = oracle.covering_cost(x, y)
+        C0 = P.covering_cost()
+        assert abs(C0 - C0o) <= 2e-7 * C0o + 2.0 ** -23 * np.sqrt(2 * C0o)
         lnD = oracle.integrated_D(x, m, y, nu, psi, eps)
         for arr in (psi, torch.tensor(psi, device="cuda")):
             for dthr in (1e-12, 1e-7):

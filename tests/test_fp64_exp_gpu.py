@@ -1,9 +1,11 @@
-"""The FP64 path's own exponential (Cody & Waite reduction, degree-13 Taylor
-polynomial) against the host's libm exp, and the probes of the pipes that
+"""The FP64 path's own exponential (Tang's table-driven method: 2^(j/64) from
+a 64-entry table of head/tail pairs, a degree-6 Taylor polynomial on
+|r| <= ln(2)/128) against the host's libm exp, and the probes of the pipes that
 bound the evaluations.  Bound: 2 units in the last place for normal results
-(the polynomial's remainder is below 6e-18 relative; the reduction and the
-Horner steps round about once each); subnormal results to within 2 units of
-2^-1074; the special values."""
+(the polynomial's remainder is below 3e-20 relative, the table pairs carry
+2^(j/64) to about 2^-106, and the reduction, polynomial and final add round
+about once each); subnormal results to within 2 units of 2^-1074; the special
+values."""
 import ctypes
 
 import numpy as np
