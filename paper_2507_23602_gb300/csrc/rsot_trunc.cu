@@ -83,6 +83,7 @@ struct Grid {
     float *pa512 = nullptr, *tb512 = nullptr, *tb1024 = nullptr;
     float2 *part1b = nullptr;
     double *part2b = nullptr;
+    Rec8 *pdup_s = nullptr;   // FP32 block-skip pass 2: sorted point records (per evaluation)
     int *off1b = nullptr, *off2b = nullptr;
     int k1b = 0, k2b = 0;
 };
@@ -1229,6 +1230,496 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
     }
 }
 
+// ------------------------------------------------- FP32 block-skip passes (FB)
+// The block-skip pipeline of the tensor-core truncated passes with the FP32
+// exponents of the dense FP32 kernels: r_qj = fma(x0, w0, fma(x1, w1, fma(x2,
+// w2, c_j))) in packed FFMA2 over two rows of one lane, bitwise the same in
+// both passes (and in the FP32 queue kernels).  A warp owns 128 rows as two
+// halves of 64 (lane l: rows 2l, 2l + 1 of each half), each half classified
+// by its own ball against every n-block of 8 columns (outside: skipped,
+// inside: no test, boundary: the weight tp_incl of every pair), so that both
+// halves skip independently; stages of FB_TS records are bulk-copied into
+// shared memory and released per warp, as in the tensor-core passes.
+constexpr int FB_THREADS = 256;
+constexpr int FB_WARPS = FB_THREADS / 32;
+constexpr int FB_ROWS = FB_WARPS * 128;     // rows per CTA
+constexpr int FB_TS = TC_TS;                // records per stage (1,024 columns)
+constexpr int FB_NBS = FB_TS / 8;           // n-blocks per stage
+constexpr int FB_STAGES = 2;
+constexpr int FB_GROUP = 8;                 // n-blocks per optimistic group (pass 1)
+constexpr size_t FB_SMEM1 = (size_t)FB_STAGES * (FB_TS * sizeof(Rec12) + FB_NBS * (sizeof(float4) + sizeof(float2)));
+constexpr size_t FB_SMEM2 =
+    (size_t)FB_STAGES * (FB_TS * (sizeof(Rec8) + sizeof(float)) + FB_NBS * (sizeof(float4) + sizeof(float2)));
+static_assert(FB_ROWS == PT && FB_TS == 1024 && FB_ROWS % TT == 0, "FB layout: a CTA is a point tile / four target tiles");
+
+// pass-1 exponents of one target for the lane's row pair of half h: returns r
+template <int D>
+__device__ __forceinline__ float2 fb_r(const float2 (&X)[3], float2 w0, float2 w1, float2 w2, float2 c) {
+    float2 r = c;
+    if (D == 3) r = __ffma2_rn(X[2], w2, r);
+    r = __ffma2_rn(X[1], w1, r);
+    r = __ffma2_rn(X[0], w0, r);
+    return r;
+}
+
+template <int D>
+__global__ void __launch_bounds__(FB_THREADS, 2)
+    k_lse_fb(const float *__restrict__ xs, int64_t nqt, const float *__restrict__ Aq,
+             const float *__restrict__ M0, const float4 *__restrict__ pball64,
+             const float2 *__restrict__ pal64, const float *__restrict__ pbox1024,
+             const float *__restrict__ pa1024, const Rec12 *__restrict__ tdup, int64_t n,
+             const float4 *__restrict__ tball8, const float2 *__restrict__ tbe8,
+             const float *__restrict__ tbox1024, const float *__restrict__ tb1024, int nstages,
+             int k1, float2 *__restrict__ part1, unsigned long long *__restrict__ pairs,
+             int *__restrict__ flags) {
+    extern __shared__ __align__(128) unsigned char fb_smem[];
+    constexpr size_t oBall = (size_t)FB_STAGES * FB_TS * sizeof(Rec12);
+    constexpr size_t oBe = oBall + (size_t)FB_STAGES * FB_NBS * sizeof(float4);
+    Rec12 (*s_rec)[FB_TS] = reinterpret_cast<Rec12 (*)[FB_TS]>(fb_smem);
+    float4 (*s_ball)[FB_NBS] = reinterpret_cast<float4 (*)[FB_NBS]>(fb_smem + oBall);
+    float2 (*s_be)[FB_NBS] = reinterpret_cast<float2 (*)[FB_NBS]>(fb_smem + oBe);
+    __shared__ __align__(8) uint64_t full[FB_STAGES], empty[FB_STAGES];
+    __shared__ int s_list[BS_CHUNK], s_cnt, s_ab;
+    __shared__ unsigned long long s_pairs;
+    __shared__ double2 s_Sd[FB_WARPS][32][2];
+    constexpr unsigned kStage = FB_TS * sizeof(Rec12) + FB_NBS * (sizeof(float4) + sizeof(float2));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kc = blockIdx.y;
+    if (tid == 0) {
+        s_cnt = bs_list(pbox1024 + (size_t)blockIdx.x * 6, pa1024[blockIdx.x], tbox1024, tb1024,
+                        kc * BS_CHUNK, min(nstages, (kc + 1) * BS_CHUNK), s_list);
+        s_pairs = 0;
+        s_ab = 0;
+        for (int st = 0; st < FB_STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], FB_WARPS);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+#define FB_ISSUE1(it_)                                                                               \
+    do {                                                                                             \
+        const int sl_ = (it_) % FB_STAGES;                                                           \
+        const int64_t j_ = (int64_t)s_list[it_] * FB_TS;                                             \
+        mbar_expect_tx(&full[sl_], kStage);                                                          \
+        bulk_g2s(s_rec[sl_], tdup + j_, FB_TS * sizeof(Rec12), &full[sl_]);                          \
+        bulk_g2s(s_ball[sl_], tball8 + j_ / 8, FB_NBS * sizeof(float4), &full[sl_]);                 \
+        bulk_g2s(s_be[sl_], tbe8 + j_ / 8, FB_NBS * sizeof(float2), &full[sl_]);                     \
+    } while (0)
+    if (tid == 0)
+        for (int it = 0; it < FB_STAGES && it < cnt; ++it) FB_ISSUE1(it);
+    int issued = min(FB_STAGES, cnt);
+    const int64_t r0 = (int64_t)blockIdx.x * FB_ROWS + warp * 128;
+    float2 X[2][3], M[2], Sf[2], nAS[2];
+    unsigned rvs[2];
+    float4 wball[2];
+    float2 wal[2];
+    double2 (&Sd)[2] = s_Sd[warp][lane];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t q = r0 + 64 * h + 2 * lane;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            X[h][k] = k < D ? *reinterpret_cast<const float2 *>(xs + k * nqt + q) : make_float2(0.f, 0.f);
+        const float2 A = *reinterpret_cast<const float2 *>(Aq + q);
+        nAS[h] = make_float2(A.x * -TP_S, A.y * -TP_S);
+        rvs[h] = (unsigned)(A.x < INFINITY) + (unsigned)(A.y < INFINITY);
+        M[h] = *reinterpret_cast<const float2 *>(M0 + q);
+        Sf[h] = make_float2(0.f, 0.f);
+        Sd[h] = make_double2(0.0, 0.0);
+        wball[h] = pball64[(r0 + 64 * h) / 64];
+        wal[h] = pal64[(r0 + 64 * h) / 64];
+    }
+    unsigned long long icnt = 0;            // pairs of inside blocks
+    float2 cntf = make_float2(0.f, 0.f);    // weights of boundary-block pairs
+    bool aborted = false;
+    for (int it = 0; it < cnt; ++it) {
+        const int slot = it % FB_STAGES;
+        const unsigned ph = (unsigned)(it / FB_STAGES) & 1u;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+            atomicOr(flags, kErrTimeout);
+            aborted = true;
+            break;
+        }
+        const int64_t sj0 = (int64_t)s_list[it] * FB_TS;   // sorted index of the stage's first column
+        unsigned cls0 = 0, cls1 = 0;   // 2 bits at 2 i: n-block lane + 32 i against half 0 / 1
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 bb = s_ball[slot][lane + 32 * i];
+            const float2 be = s_be[slot][lane + 32 * i];
+            cls0 |= (unsigned)tp_class(wball[0], bb, wal[0], be) << (2 * i);
+            cls1 |= (unsigned)tp_class(wball[1], bb, wal[1], be) << (2 * i);
+        }
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {
+            const unsigned lv0 = __ballot_sync(0xffffffffu, ((cls0 >> (2 * i)) & 3u) != 0u);
+            const unsigned bd0 = __ballot_sync(0xffffffffu, ((cls0 >> (2 * i)) & 3u) == 2u);
+            const unsigned lv1 = __ballot_sync(0xffffffffu, ((cls1 >> (2 * i)) & 3u) != 0u);
+            const unsigned bd1 = __ballot_sync(0xffffffffu, ((cls1 >> (2 * i)) & 3u) == 2u);
+#pragma unroll 1
+            for (int gq = 0; gq < 32 / FB_GROUP; ++gq) {
+                const int grp = i * (32 / FB_GROUP) + gq;
+                const unsigned g0 = (lv0 >> (gq * FB_GROUP)) & 0xffu, g1 = (lv1 >> (gq * FB_GROUP)) & 0xffu;
+                if (!(g0 | g1)) continue;
+                const unsigned b0 = (bd0 >> (gq * FB_GROUP)) & 0xffu, b1 = (bd1 >> (gq * FB_GROUP)) & 0xffu;
+                float2 acc[2], ng[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    acc[h] = make_float2(0.f, 0.f);
+                    ng[h] = make_float2(-M[h].x, -M[h].y);
+                }
+                for (unsigned gm = g0 | g1; gm; gm &= gm - 1) {
+                    const int b = __ffs(gm) - 1, nb = grp * FB_GROUP + b;
+                    const bool l0 = (g0 >> b) & 1u, l1 = (g1 >> b) & 1u;
+                    const bool x0 = (b0 >> b) & 1u, x1 = (b1 >> b) & 1u;
+                    const unsigned jreal = (unsigned)max((int64_t)0, min((int64_t)8, n - (sj0 + 8 * nb)));
+                    if (l0 && !x0) icnt += rvs[0] * jreal;
+                    if (l1 && !x1) icnt += rvs[1] * jreal;
+                    const Rec12 *T = &s_rec[slot][8 * nb];
+#pragma unroll 2
+                    for (int tt = 0; tt < 8; ++tt) {
+                        const float4 a4 = T[tt].a, b4 = T[tt].b;
+                        const float2 w0 = make_float2(a4.x, a4.y), w1 = make_float2(a4.z, a4.w);
+                        const float2 w2 = make_float2(b4.x, b4.y), c = make_float2(b4.z, b4.w);
+                        const float2 nbv = (x0 || x1) ? make_float2(T[tt].c.x, T[tt].c.y) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (!(h ? l1 : l0)) continue;
+                            const float2 r = fb_r<D>(X[h], w0, w1, w2, c);
+                            const float2 e = __fadd2_rn(r, ng[h]);
+                            const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                            if (h ? x1 : x0) {
+                                const float2 v = __fadd2_rn(r, nbv);
+                                const float2 y = make_float2(tp_incl(v.x, nAS[h].x), tp_incl(v.y, nAS[h].y));
+                                acc[h] = __ffma2_rn(p, y, acc[h]);
+                                cntf = __fadd2_rn(cntf, y);
+                            } else {
+                                acc[h] = __fadd2_rn(acc[h], p);
+                            }
+                        }
+                    }
+                }
+                bool bad = false;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    bad = bad || !(acc[h].x <= TC_BIG) || !(acc[h].y <= TC_BIG) ||
+                          (M[h].x == -INFINITY && acc[h].x != 0.f) || (M[h].y == -INFINITY && acc[h].y != 0.f);
+                if (__any_sync(0xffffffffu, bad)) {
+                    // exact redo of the group: maximum over the kept pairs (weight > 0),
+                    // shifts raised, sums recomputed (pairs are not counted again)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const unsigned gh = h ? g1 : g0, bh = h ? b1 : b0;
+                        float mx = -INFINITY, my = -INFINITY;
+                        for (unsigned gm = gh; gm; gm &= gm - 1) {
+                            const int b = __ffs(gm) - 1, nb = grp * FB_GROUP + b;
+                            const bool bnd = (bh >> b) & 1u;
+                            const Rec12 *T = &s_rec[slot][8 * nb];
+                            for (int tt = 0; tt < 8; ++tt) {
+                                const float4 a4 = T[tt].a, b4 = T[tt].b;
+                                const float2 r = fb_r<D>(X[h], make_float2(a4.x, a4.y), make_float2(a4.z, a4.w),
+                                                         make_float2(b4.x, b4.y), make_float2(b4.z, b4.w));
+                                float2 y = make_float2(1.f, 1.f);
+                                if (bnd) {
+                                    const float2 v = __fadd2_rn(r, make_float2(T[tt].c.x, T[tt].c.y));
+                                    y = make_float2(tp_incl(v.x, nAS[h].x), tp_incl(v.y, nAS[h].y));
+                                }
+                                mx = fmaxf(mx, y.x > 0.f ? r.x : -INFINITY);
+                                my = fmaxf(my, y.y > 0.f ? r.y : -INFINITY);
+                            }
+                        }
+                        if (mx > -INFINITY) tc_raise(M[h].x, mx, Sf[h].x, Sd[h].x);
+                        if (my > -INFINITY) tc_raise(M[h].y, my, Sf[h].y, Sd[h].y);
+                        const float2 nm = make_float2(-M[h].x, -M[h].y);
+                        float2 a2 = make_float2(0.f, 0.f);
+                        for (unsigned gm = gh; gm; gm &= gm - 1) {
+                            const int b = __ffs(gm) - 1, nb = grp * FB_GROUP + b;
+                            const bool bnd = (bh >> b) & 1u;
+                            const Rec12 *T = &s_rec[slot][8 * nb];
+                            for (int tt = 0; tt < 8; ++tt) {
+                                const float4 a4 = T[tt].a, b4 = T[tt].b;
+                                const float2 r = fb_r<D>(X[h], make_float2(a4.x, a4.y), make_float2(a4.z, a4.w),
+                                                         make_float2(b4.x, b4.y), make_float2(b4.z, b4.w));
+                                float2 y = make_float2(1.f, 1.f);
+                                if (bnd) {
+                                    const float2 v = __fadd2_rn(r, make_float2(T[tt].c.x, T[tt].c.y));
+                                    y = make_float2(tp_incl(v.x, nAS[h].x), tp_incl(v.y, nAS[h].y));
+                                }
+                                const float2 e = __fadd2_rn(r, nm);
+                                a2.x += y.x > 0.f ? y.x * ex2_approx(e.x) : 0.f;
+                                a2.y += y.y > 0.f ? y.y * ex2_approx(e.y) : 0.f;
+                            }
+                        }
+                        acc[h] = a2;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) Sf[h] = __fadd2_rn(Sf[h], acc[h]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (warp == 0 && it + FB_STAGES < cnt) {
+            bool ok = true;
+            if (tid == 0) {
+                ok = mbar_wait(&empty[slot], ph);
+                if (ok) {
+                    FB_ISSUE1(it + FB_STAGES);
+                    ++issued;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                atomicOr(flags, kErrTimeout);
+                aborted = true;
+                break;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            Sd[h].x += (double)Sf[h].x;
+            Sd[h].y += (double)Sf[h].y;
+            Sf[h] = make_float2(0.f, 0.f);
+        }
+    }
+#undef FB_ISSUE1
+    if (aborted && lane == 0) s_ab = 1;
+    if (!aborted) {
+        float2 *o = part1 + ((int64_t)blockIdx.x * k1 + kc) * PT;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = warp * 128 + 64 * h + 2 * lane;
+            o[l] = M[h].x == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(M[h].x, (float)Sd[h].x);
+            o[l + 1] = M[h].y == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(M[h].y, (float)Sd[h].y);
+        }
+    }
+    atomicAdd(&s_pairs, icnt + (unsigned long long)__float2uint_rn(cntf.x + cntf.y));
+    __syncthreads();
+    if (tid == 0) {
+        if (s_pairs) atomicAdd(pairs, s_pairs);
+        if (s_ab)
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % FB_STAGES], (unsigned)(it / FB_STAGES) & 1u);
+    }
+}
+
+// sorted point records of the FP32 block-skip pass 2: (x0,x0,x1,x1) (x2,x2,u,u)
+__global__ void k_pdup_s(const float *__restrict__ xs, const float *__restrict__ u_s, int64_t nqt, int d,
+                         Rec8 *__restrict__ pdup) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nqt) return;
+    float x[3] = {0.f, 0.f, 0.f};
+    for (int t = 0; t < d; ++t) x[t] = xs[t * nqt + q];
+    const float u = u_s[q];
+    Rec8 r;
+    r.a = make_float4(x[0], x[0], x[1], x[1]);
+    r.b = make_float4(x[2], x[2], u, u);
+    pdup[q] = r;
+}
+
+// Pass 2: rows are targets (lane l: targets 2l, 2l + 1 of each half of the
+// warp's 128), columns the sorted points of the stage; per pair the exponent
+// of pass 1 (the same FFMA2 chain on the same operands), shifted by u_q, and
+// in boundary blocks weighted by the same tp_incl test.
+template <int D>
+__global__ void __launch_bounds__(FB_THREADS, 2)
+    k_grad_fb(const Rec12 *__restrict__ tdup, const float4 *__restrict__ tball64,
+              const float2 *__restrict__ tbe64, const float *__restrict__ tbox1024,
+              const float *__restrict__ tb1024, const Rec8 *__restrict__ pdup,
+              const float *__restrict__ Aq, const float4 *__restrict__ pball8,
+              const float2 *__restrict__ pal8, const float *__restrict__ pbox1024,
+              const float *__restrict__ pa1024, int nstages, int k2, double *__restrict__ part2,
+              int *__restrict__ flags) {
+    extern __shared__ __align__(128) unsigned char fb_smem[];
+    constexpr size_t oA = (size_t)FB_STAGES * FB_TS * sizeof(Rec8);
+    constexpr size_t oBall = oA + (size_t)FB_STAGES * FB_TS * sizeof(float);
+    constexpr size_t oAl = oBall + (size_t)FB_STAGES * FB_NBS * sizeof(float4);
+    Rec8 (*s_rec)[FB_TS] = reinterpret_cast<Rec8 (*)[FB_TS]>(fb_smem);
+    float (*s_A)[FB_TS] = reinterpret_cast<float (*)[FB_TS]>(fb_smem + oA);
+    float4 (*s_ball)[FB_NBS] = reinterpret_cast<float4 (*)[FB_NBS]>(fb_smem + oBall);
+    float2 (*s_al)[FB_NBS] = reinterpret_cast<float2 (*)[FB_NBS]>(fb_smem + oAl);
+    __shared__ __align__(8) uint64_t full[FB_STAGES], empty[FB_STAGES];
+    __shared__ int s_list[BS_CHUNK], s_cnt;
+    constexpr unsigned kStage = FB_TS * (sizeof(Rec8) + sizeof(float)) + FB_NBS * (sizeof(float4) + sizeof(float2));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kc = blockIdx.y;
+    if (tid == 0) {
+        s_cnt = bs_list(tbox1024 + (size_t)blockIdx.x * 6, tb1024[blockIdx.x], pbox1024, pa1024,
+                        kc * BS_CHUNK, min(nstages, (kc + 1) * BS_CHUNK), s_list);
+        for (int st = 0; st < FB_STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], FB_WARPS);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+#define FB_ISSUE2(it_)                                                                               \
+    do {                                                                                             \
+        const int sl_ = (it_) % FB_STAGES;                                                           \
+        const int64_t q_ = (int64_t)s_list[it_] * FB_TS;                                             \
+        mbar_expect_tx(&full[sl_], kStage);                                                          \
+        bulk_g2s(s_rec[sl_], pdup + q_, FB_TS * sizeof(Rec8), &full[sl_]);                           \
+        bulk_g2s(s_A[sl_], Aq + q_, FB_TS * sizeof(float), &full[sl_]);                              \
+        bulk_g2s(s_ball[sl_], pball8 + q_ / 8, FB_NBS * sizeof(float4), &full[sl_]);                 \
+        bulk_g2s(s_al[sl_], pal8 + q_ / 8, FB_NBS * sizeof(float2), &full[sl_]);                     \
+    } while (0)
+    if (tid == 0)
+        for (int it = 0; it < FB_STAGES && it < cnt; ++it) FB_ISSUE2(it);
+    int issued = min(FB_STAGES, cnt);
+    const int64_t j0 = (int64_t)blockIdx.x * FB_ROWS + warp * 128;
+    float2 W[2][3], C[2], NB[2];
+    float4 wball[2];
+    float2 wbe[2];
+    double2 acc64[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t ja = j0 + 64 * h + 2 * lane;
+        const Rec12 ra = tdup[ja], rb = tdup[ja + 1];
+        W[h][0] = make_float2(ra.a.x, rb.a.x);
+        W[h][1] = make_float2(ra.a.z, rb.a.z);
+        W[h][2] = make_float2(ra.b.x, rb.b.x);
+        C[h] = make_float2(ra.b.z, rb.b.z);
+        NB[h] = make_float2(ra.c.x, rb.c.x);
+        acc64[h] = make_double2(0.0, 0.0);
+        wball[h] = tball64[(j0 + 64 * h) / 64];
+        wbe[h] = tbe64[(j0 + 64 * h) / 64];
+    }
+    bool aborted = false;
+    for (int it = 0; it < cnt; ++it) {
+        const int slot = it % FB_STAGES;
+        const unsigned ph = (unsigned)(it / FB_STAGES) & 1u;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], ph))) {
+            atomicOr(flags, kErrTimeout);
+            aborted = true;
+            break;
+        }
+        unsigned cls0 = 0, cls1 = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 bb = s_ball[slot][lane + 32 * i];
+            const float2 al = s_al[slot][lane + 32 * i];
+            cls0 |= (unsigned)tp_class(wball[0], bb, wbe[0], al) << (2 * i);
+            cls1 |= (unsigned)tp_class(wball[1], bb, wbe[1], al) << (2 * i);
+        }
+        float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {
+            const unsigned lv0 = __ballot_sync(0xffffffffu, ((cls0 >> (2 * i)) & 3u) != 0u);
+            const unsigned bd0 = __ballot_sync(0xffffffffu, ((cls0 >> (2 * i)) & 3u) == 2u);
+            const unsigned lv1 = __ballot_sync(0xffffffffu, ((cls1 >> (2 * i)) & 3u) != 0u);
+            const unsigned bd1 = __ballot_sync(0xffffffffu, ((cls1 >> (2 * i)) & 3u) == 2u);
+            for (unsigned live = lv0 | lv1; live; live &= live - 1) {
+                const int b = __ffs(live) - 1, nb = 32 * i + b;
+                const bool l0 = (lv0 >> b) & 1u, l1 = (lv1 >> b) & 1u;
+                const bool x0 = (bd0 >> b) & 1u, x1 = (bd1 >> b) & 1u;
+                const Rec8 *T = &s_rec[slot][8 * nb];
+                const float *Ab = &s_A[slot][8 * nb];
+#pragma unroll 2
+                for (int tt = 0; tt < 8; ++tt) {
+                    const float4 a4 = T[tt].a, b4 = T[tt].b;
+                    const float2 x0v = make_float2(a4.x, a4.y), x1v = make_float2(a4.z, a4.w);
+                    const float2 x2v = make_float2(b4.x, b4.y), u = make_float2(b4.z, b4.w);
+                    const float nA = (x0 || x1) ? Ab[tt] * -TP_S : 0.f;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (!(h ? l1 : l0)) continue;
+                        float2 r = C[h];
+                        if (D == 3) r = __ffma2_rn(x2v, W[h][2], r);
+                        r = __ffma2_rn(x1v, W[h][1], r);
+                        r = __ffma2_rn(x0v, W[h][0], r);
+                        const float2 e = __fadd2_rn(r, u);
+                        const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+                        if (h ? x1 : x0) {
+                            const float2 v = __fadd2_rn(r, NB[h]);
+                            acc[h] = __ffma2_rn(p, make_float2(tp_incl(v.x, nA), tp_incl(v.y, nA)), acc[h]);
+                        } else {
+                            acc[h] = __fadd2_rn(acc[h], p);
+                        }
+                    }
+                }
+            }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) bad = bad || !(acc[h].x < INFINITY) || !(acc[h].y < INFINITY);
+        if (__any_sync(0xffffffffu, bad)) {
+            // an excluded pair whose exponential overflowed (inf * 0): the stage
+            // again, with the excluded pairs' exponentials dropped
+#pragma unroll
+            for (int h = 0; h < 2; ++h) acc[h] = make_float2(0.f, 0.f);
+            for (int i = 0; i < 4; ++i) {
+                const unsigned lv0 = __ballot_sync(0xffffffffu, ((cls0 >> (2 * i)) & 3u) != 0u);
+                const unsigned bd0 = __ballot_sync(0xffffffffu, ((cls0 >> (2 * i)) & 3u) == 2u);
+                const unsigned lv1 = __ballot_sync(0xffffffffu, ((cls1 >> (2 * i)) & 3u) != 0u);
+                const unsigned bd1 = __ballot_sync(0xffffffffu, ((cls1 >> (2 * i)) & 3u) == 2u);
+                for (unsigned live = lv0 | lv1; live; live &= live - 1) {
+                    const int b = __ffs(live) - 1, nb = 32 * i + b;
+                    const Rec8 *T = &s_rec[slot][8 * nb];
+                    const float *Ab = &s_A[slot][8 * nb];
+                    for (int tt = 0; tt < 8; ++tt) {
+                        const float4 a4 = T[tt].a, b4 = T[tt].b;
+                        const float nA = Ab[tt] * -TP_S;
+                        for (int h = 0; h < 2; ++h) {
+                            if (!(((h ? lv1 : lv0) >> b) & 1u)) continue;
+                            const bool bnd = ((h ? bd1 : bd0) >> b) & 1u;
+                            float2 r = C[h];
+                            if (D == 3) r = __ffma2_rn(make_float2(b4.x, b4.y), W[h][2], r);
+                            r = __ffma2_rn(make_float2(a4.z, a4.w), W[h][1], r);
+                            r = __ffma2_rn(make_float2(a4.x, a4.y), W[h][0], r);
+                            const float2 e = __fadd2_rn(r, make_float2(b4.z, b4.w));
+                            float2 y = make_float2(1.f, 1.f);
+                            if (bnd) {
+                                const float2 v = __fadd2_rn(r, NB[h]);
+                                y = make_float2(tp_incl(v.x, nA), tp_incl(v.y, nA));
+                            }
+                            acc[h].x += y.x > 0.f ? y.x * ex2_approx(e.x) : 0.f;
+                            acc[h].y += y.y > 0.f ? y.y * ex2_approx(e.y) : 0.f;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            acc64[h].x += (double)acc[h].x;
+            acc64[h].y += (double)acc[h].y;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (warp == 0 && it + FB_STAGES < cnt) {
+            bool ok = true;
+            if (tid == 0) {
+                ok = mbar_wait(&empty[slot], ph);
+                if (ok) {
+                    FB_ISSUE2(it + FB_STAGES);
+                    ++issued;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                atomicOr(flags, kErrTimeout);
+                aborted = true;
+                break;
+            }
+        }
+    }
+#undef FB_ISSUE2
+    if (aborted) {
+        if (tid == 0)
+            for (int it = 0; it < issued; ++it)
+                (void)mbar_wait(&full[it % FB_STAGES], (unsigned)(it / FB_STAGES) & 1u);
+        return;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int l = warp * 128 + 64 * h + 2 * lane;   // < FB_ROWS; both rows in one target tile
+        const int64_t tile = (int64_t)blockIdx.x * (FB_ROWS / TT) + l / TT;
+        double *o = part2 + (tile * k2 + kc) * TT + (l % TT);
+        o[0] = acc64[h].x;
+        o[1] = acc64[h].y;
+    }
+}
+
 // off[i] = i * k for i <= rows: the item offsets of the block-skip layout
 __global__ void k_offsets_uniform(int *__restrict__ off, int rows, int k) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1588,6 +2079,7 @@ static cudaError_t grid_build(rsot_problem *p) {
     ALLOC(g->part2b, (int64_t)g->ttiles * g->k2b * TT);
     ALLOC(g->off1b, g->ptiles + 1);
     ALLOC(g->off2b, g->ttiles + 1);
+    ALLOC(g->pdup_s, g->nqt);
 #undef ALLOC
     k_gather_points<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(
         kq, p->nq, g->nqt, d, p->x64, p->mass, p->lmass2, g->perm_q, g->xs, g->x64, g->mass, g->lm2);
@@ -1607,6 +2099,12 @@ static cudaError_t grid_build(rsot_problem *p) {
             return e;
         if ((e = cudaFuncSetAttribute((const void *)k_grad_tcb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)BS_SMEM2)))
+            return e;
+        const void *fb1 = d == 3 ? (const void *)k_lse_fb<3> : (const void *)k_lse_fb<2>;
+        const void *fb2 = d == 3 ? (const void *)k_grad_fb<3> : (const void *)k_grad_fb<2>;
+        if ((e = cudaFuncSetAttribute(fb1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM1)))
+            return e;
+        if ((e = cudaFuncSetAttribute(fb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM2)))
             return e;
     }
     k_block_balls<<<(unsigned)((g->nqt / 64 + 127) / 128), 128, 0, st>>>(g->x64, p->nq, d, 64, g->nqt / 64, g->pball64);
@@ -1668,6 +2166,33 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
     unsigned long long *pairs = reinterpret_cast<unsigned long long *>(&p->res_dev->pairs);
     // block pairs are classified against their members' cutoff radii widened /
     // narrowed by 1e-4 relative: the pairwise FP32 test's rounding is far below
+    if (!tc) {
+        // FP32 pair arithmetic on the block-skip pipeline
+        trace_begin(p, "lse_trunc_fb");
+        k_lse_fb<D><<<dim3((unsigned)(g->nqt / FB_ROWS), (unsigned)g->k1b), FB_THREADS, FB_SMEM1, st>>>(
+            g->xs, g->nqt, g->Aq, g->m0_s, g->pball64, g->pal64, g->pbox, g->ptmax, g->tdup, p->n,
+            g->tball8, g->tbe8, g->tbox1024, g->tb1024, (int)(g->nt / FB_TS), g->k1b, g->part1b, pairs,
+            p->flags);
+        trace_end(p);
+        trace_begin(p, "combine_trunc_mixed");
+        k_combine_trunc<<<g->nblk_comb, 256, 0, st>>>(g->part1b, g->off1b, p->nq, g->nqt, g->xs, g->x64,
+                                                      g->mass, g->lm2, g->Aq, psi, eps, D, g->ppair,
+                                                      g->lse_s, g->blockJ, p->res_dev, g->u_s, nullptr, 0);
+        k_pdup_s<<<nb_of(g->nqt), 256, 0, st>>>(g->xs, g->u_s, g->nqt, D, g->pdup_s);
+        trace_end(p);
+        trace_begin(p, "grad_trunc_fb");
+        k_grad_fb<D><<<dim3((unsigned)(g->nt / FB_ROWS), (unsigned)g->k2b), FB_THREADS, FB_SMEM2, st>>>(
+            g->tdup, g->tball64, g->tbe64, g->tbox1024, g->tb1024, g->pdup_s, g->Aq, g->pball8, g->pal8,
+            g->pbox, g->ptmax, (int)(g->nqt / FB_TS), g->k2b, g->part2b, p->flags);
+        trace_end(p);
+        trace_begin(p, "finalize_trunc");
+        k_finalize_grad_trunc<<<(unsigned)((p->n + 255) / 256), 256, 0, st>>>(g->part2b, g->off2b, p->n,
+                                                                              g->perm_t, g->nu, grad,
+                                                                              nullptr, 0);
+        k_finalize_J_trunc<<<1, 256, 0, st>>>(g->blockJ, g->nblk_comb, p->psinu, nbp, psi, p->res_dev);
+        trace_end(p);
+        return cudaGetLastError();
+    }
     if (tc) {
         trace_begin(p, "lse_trunc_tc");
         k_lse_tcb<<<dim3((unsigned)(g->nqt / TC_ROWS), (unsigned)g->k1b), TC_THREADS, BS_SMEM1, st>>>(
@@ -1755,7 +2280,7 @@ void trunc_free(rsot_problem *p) {
                     g->pball64, g->pball8, g->tball64, g->tball8, g->prec_s, g->trec_s, g->b_s,
                     g->u_s, g->pal8, g->pal64, g->ptmax, g->tbe8, g->tbe64, g->ttmax, g->m0_s,
                     g->pbox512, g->tbox512, g->tbox1024, g->pa512, g->tb512, g->tb1024, g->part1b,
-                    g->part2b, g->off1b, g->off2b};
+                    g->part2b, g->off1b, g->off2b, g->pdup_s};
     for (void *q : ptrs) cudaFree(q);
     delete g;
     p->grid = nullptr;
