@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--tail", type=float, default=0.0,
                     help="multilevel: truncation tail of every evaluation (0: dense)")
     ap.add_argument("--workload", choices=["dense", "solve", "batch", "multilevel", "warmstart",
-                                           "maps", "barycenter", "mlp"],
+                                           "maps", "barycenter", "mlp", "cutoffs"],
                     default="dense",
                     help="dense: dual+grad throughput (default); the others time solves")
     ap.add_argument("--problems", type=int, default=32, help="batch: problems (seeds 1000..)")
@@ -427,6 +427,67 @@ def run_solve_workloads(args):
                             "note": "whole call (activation writes, column sums, host copy of the "
                                     "gradient included), not the GEMM kernels alone"}}
         print(json.dumps(out))
+        return
+    if args.workload == "cutoffs":
+        # the paper's truncation strategies (Sec. 4.1, Sec. 6 truncation table) on the
+        # cube: mixed L-BFGS solves to ||g||_1 <= 1e-5 (the mixed floor; no
+        # refinement, so the solve runs on the truncated functional throughout),
+        # then E_rel = |J~(psi) - J_none| / |J_none| from FP64 evaluations of the
+        # truncated functional at each result (its cutoff recomputed there) against
+        # the dense FP64 functional at the untruncated solve's result
+        import math as _m
+        q = ri.cube_3d(mesh_n=args.mesh, n_targets=args.targets, eps=args.eps)
+        Q = rs.Problem(q.x, q.mass, q.y, q.nu)
+        modes = [("none", {}), ("psi-aware tail", {"tail": 1e-12}),
+                 ("pointwise", {"delta_pw": 1e-12}), ("pointwise", {"delta_pw": 1e-10}),
+                 ("pointwise", {"delta_pw": 1e-7}),
+                 ("integral", {"tau_int": 1e-6}), ("integral", {"tau_int": 1e-5}),
+                 ("integral", {"tau_int": 1e-4}),
+                 ("geometric", {"tau_geom": 1e-6}), ("geometric", {"tau_geom": 1e-5}),
+                 ("geometric", {"tau_geom": 1e-4})]
+        out = {}
+        for eps_f in (1e-2, 1e-3):
+            rows, J_none = [], None
+            for name, kw in modes:
+                t = time.perf_counter()
+                psi_m, st = Q.solve(eps=eps_f, eps_start=0.1, eps_factor=0.5, tol_l1=1e-5,
+                                    precision=rs.MIXED, refine_fp64=False, max_iter=5000,
+                                    raise_on_error=False, **kw)
+                wall = time.perf_counter() - t
+                Jd, _, _ = Q.eval(psi_m, eps_f, 0.0, rs.FP64)
+                if name == "none":
+                    Jt, J_none = Jd, Jd
+                elif name == "psi-aware tail":
+                    Jt, _, _ = Q.eval_tail(psi_m, eps_f, kw["tail"], rs.FP64)
+                else:
+                    if name == "pointwise":
+                        C = Q.truncation_cutoff(psi_m, eps_f, rs.CUTOFF_POINTWISE, kw["delta_pw"])
+                    elif name == "integral":
+                        lnD = Q.log_integrated_D()          # of the dense FP64 evaluation above
+                        C = Q.truncation_cutoff(psi_m, eps_f, rs.CUTOFF_INTEGRAL, kw["tau_int"], J=Jd, lnD=lnD)
+                    else:
+                        C = Q.truncation_cutoff(psi_m, eps_f, rs.CUTOFF_GEOMETRIC, kw["tau_geom"], J=Jd)
+                    Jt, _, _ = Q.eval(psi_m, eps_f, _m.sqrt(2.0 * C) if C > 0 else 1e-150, rs.FP64,
+                                      allow_empty=True)
+                param = next(iter(kw.values()), None)
+                rows.append({"strategy": name, "param": param, "seconds": wall, "iters": st.iters,
+                             "evals": st.evals, "converged": st.status == 0, "status": st.status,
+                             "grad_l1": st.grad_l1,
+                             "kept_fraction": st.pairs / max(1, st.evals * q.nq * q.n),
+                             "J_trunc_fp64": Jt, "J_dense_fp64": Jd,
+                             "E_rel": abs(Jt - J_none) / abs(J_none)})
+                sys.stderr.write(f"[bench] eps {eps_f:g} {name} {param}: {wall:.2f} s, "
+                                 f"{st.iters} it, kept {rows[-1]['kept_fraction']:.3f}, "
+                                 f"E_rel {rows[-1]['E_rel']:.2e}\n")
+            out[f"eps_{eps_f:g}"] = rows
+        Q.close()
+        solve_line("solve time by truncation strategy (cube, mixed to ||g||_1 <= 1e-5)",
+                   out["eps_0.001"][0]["seconds"], "s", f"cube-{q.nq}x{q.n}-cutoffs",
+                   {"results": out,
+                    "note": "eps 1e-2 from eps_start 0.1 (x0.5 stages), eps 1e-3 likewise; E_rel "
+                            "as the paper's truncation table: the truncated functional at the "
+                            "strategy's result against the untruncated one at its own result, "
+                            "both FP64"}, args)
         return
     if args.workload == "warmstart":
         from paper_2507_23602_gb300 import warmstart as ws

@@ -1377,25 +1377,44 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                     if (l0 && !x0) icnt += rvs[0] * jreal;
                     if (l1 && !x1) icnt += rvs[1] * jreal;
                     const Rec12 *T = &s_rec[slot][8 * nb];
-#pragma unroll 2
-                    for (int tt = 0; tt < 8; ++tt) {
-                        const float4 a4 = T[tt].a, b4 = T[tt].b;
-                        const float2 w0 = make_float2(a4.x, a4.y), w1 = make_float2(a4.z, a4.w);
-                        const float2 w2 = make_float2(b4.x, b4.y), c = make_float2(b4.z, b4.w);
-                        const float2 nbv = (x0 || x1) ? make_float2(T[tt].c.x, T[tt].c.y) : make_float2(0.f, 0.f);
+                    if (l0 && l1 && !x0 && !x1) {
+                        // both halves inside: no test, both chains interleaved
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            if (!(h ? l1 : l0)) continue;
-                            const float2 r = fb_r<D>(X[h], w0, w1, w2, c);
-                            const float2 e = __fadd2_rn(r, ng[h]);
-                            const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                            if (h ? x1 : x0) {
+                        for (int tt = 0; tt < 8; ++tt) {
+                            const float4 a4 = T[tt].a, b4 = T[tt].b;
+                            const float2 w0 = make_float2(a4.x, a4.y), w1 = make_float2(a4.z, a4.w);
+                            const float2 w2 = make_float2(b4.x, b4.y), c = make_float2(b4.z, b4.w);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const float2 r = fb_r<D>(X[h], w0, w1, w2, c);
+                                const float2 e = __fadd2_rn(r, ng[h]);
+                                acc[h] = __fadd2_rn(acc[h], make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                            }
+                        }
+                    } else {
+                        // per half a weight: the test (boundary), 1 (inside) or 0 (outside),
+                        // selected without branching so that both chains interleave
+                        const float yin0 = l0 ? 1.f : 0.f, yin1 = l1 ? 1.f : 0.f;
+                        const float cb0 = x0 ? 1.f : 0.f, cb1 = x1 ? 1.f : 0.f;
+#pragma unroll
+                        for (int tt = 0; tt < 8; ++tt) {
+                            const float4 a4 = T[tt].a, b4 = T[tt].b;
+                            const float2 w0 = make_float2(a4.x, a4.y), w1 = make_float2(a4.z, a4.w);
+                            const float2 w2 = make_float2(b4.x, b4.y), c = make_float2(b4.z, b4.w);
+                            const float2 nbv = make_float2(T[tt].c.x, T[tt].c.y);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const float2 r = fb_r<D>(X[h], w0, w1, w2, c);
+                                const float2 e = __fadd2_rn(r, ng[h]);
+                                const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
                                 const float2 v = __fadd2_rn(r, nbv);
-                                const float2 y = make_float2(tp_incl(v.x, nAS[h].x), tp_incl(v.y, nAS[h].y));
+                                const bool bnd = h ? x1 : x0;
+                                const float yi = h ? yin1 : yin0;
+                                const float2 y = make_float2(bnd ? tp_incl(v.x, nAS[h].x) : yi,
+                                                             bnd ? tp_incl(v.y, nAS[h].y) : yi);
                                 acc[h] = __ffma2_rn(p, y, acc[h]);
-                                cntf = __fadd2_rn(cntf, y);
-                            } else {
-                                acc[h] = __fadd2_rn(acc[h], p);
+                                const float cb = h ? cb1 : cb0;
+                                cntf = __ffma2_rn(y, make_float2(cb, cb), cntf);
                             }
                         }
                     }
@@ -1615,26 +1634,45 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                 const bool x0 = (bd0 >> b) & 1u, x1 = (bd1 >> b) & 1u;
                 const Rec8 *T = &s_rec[slot][8 * nb];
                 const float *Ab = &s_A[slot][8 * nb];
-#pragma unroll 2
-                for (int tt = 0; tt < 8; ++tt) {
-                    const float4 a4 = T[tt].a, b4 = T[tt].b;
-                    const float2 x0v = make_float2(a4.x, a4.y), x1v = make_float2(a4.z, a4.w);
-                    const float2 x2v = make_float2(b4.x, b4.y), u = make_float2(b4.z, b4.w);
-                    const float nA = (x0 || x1) ? Ab[tt] * -TP_S : 0.f;
+                if (l0 && l1 && !x0 && !x1) {
+                    // both halves inside: no test, both chains interleaved
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (!(h ? l1 : l0)) continue;
-                        float2 r = C[h];
-                        if (D == 3) r = __ffma2_rn(x2v, W[h][2], r);
-                        r = __ffma2_rn(x1v, W[h][1], r);
-                        r = __ffma2_rn(x0v, W[h][0], r);
-                        const float2 e = __fadd2_rn(r, u);
-                        const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                        if (h ? x1 : x0) {
+                    for (int tt = 0; tt < 8; ++tt) {
+                        const float4 a4 = T[tt].a, b4 = T[tt].b;
+                        const float2 x0v = make_float2(a4.x, a4.y), x1v = make_float2(a4.z, a4.w);
+                        const float2 x2v = make_float2(b4.x, b4.y), u = make_float2(b4.z, b4.w);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float2 r = C[h];
+                            if (D == 3) r = __ffma2_rn(x2v, W[h][2], r);
+                            r = __ffma2_rn(x1v, W[h][1], r);
+                            r = __ffma2_rn(x0v, W[h][0], r);
+                            const float2 e = __fadd2_rn(r, u);
+                            acc[h] = __fadd2_rn(acc[h], make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                        }
+                    }
+                } else {
+                    // per half a weight: the test (boundary), 1 (inside) or 0 (outside)
+                    const float yin0 = l0 ? 1.f : 0.f, yin1 = l1 ? 1.f : 0.f;
+#pragma unroll
+                    for (int tt = 0; tt < 8; ++tt) {
+                        const float4 a4 = T[tt].a, b4 = T[tt].b;
+                        const float2 x0v = make_float2(a4.x, a4.y), x1v = make_float2(a4.z, a4.w);
+                        const float2 x2v = make_float2(b4.x, b4.y), u = make_float2(b4.z, b4.w);
+                        const float nA = Ab[tt] * -TP_S;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float2 r = C[h];
+                            if (D == 3) r = __ffma2_rn(x2v, W[h][2], r);
+                            r = __ffma2_rn(x1v, W[h][1], r);
+                            r = __ffma2_rn(x0v, W[h][0], r);
+                            const float2 e = __fadd2_rn(r, u);
+                            const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
                             const float2 v = __fadd2_rn(r, NB[h]);
-                            acc[h] = __ffma2_rn(p, make_float2(tp_incl(v.x, nA), tp_incl(v.y, nA)), acc[h]);
-                        } else {
-                            acc[h] = __fadd2_rn(acc[h], p);
+                            const bool bnd = h ? x1 : x0;
+                            const float yi = h ? yin1 : yin0;
+                            const float2 y = make_float2(bnd ? tp_incl(v.x, nA) : yi, bnd ? tp_incl(v.y, nA) : yi);
+                            acc[h] = __ffma2_rn(p, y, acc[h]);
                         }
                     }
                 }
