@@ -5,7 +5,8 @@ by hand-written back-propagation: in_dim -> W (SiLU) -> W (SiLU) -> W (SiLU)
 -> 1, loss = mean (f(x) - y)^2 / 2.  With ``emulate_bf16`` the operands are
 rounded to bfloat16 (round to nearest even) at the places where the GPU
 kernels round them (inputs, the three weight matrices, the hidden
-activations and the back-propagated dZ), everything else in FP64; without it
+activations, the stored pre-activations whose SiLU' the back-propagation
+takes, and the back-propagated dZ), everything else in FP64; without it
 the network is plain FP64 (the form pinned by finite differences).
 
 The parameter block layout is the library's: W1 [W][in_pad], b1 [W],
@@ -74,13 +75,13 @@ def loss_and_grad(p, x, y, in_dim, width, emulate_bf16=True):
     dout = e / B
     dw4 = H3.T @ dout
     db4 = dout.sum()
-    dZ3 = r(np.outer(dout, w4) * dsilu(Z3))
+    dZ3 = r(np.outer(dout, w4) * dsilu(r(Z3)))
     dW3 = dZ3.T @ H2
     db3 = dZ3.sum(0)
-    dZ2 = r((dZ3 @ r(W3)) * dsilu(Z2))
+    dZ2 = r((dZ3 @ r(W3)) * dsilu(r(Z2)))
     dW2 = dZ2.T @ H1
     db2 = dZ2.sum(0)
-    dZ1 = r((dZ2 @ r(W2)) * dsilu(Z1))
+    dZ1 = r((dZ2 @ r(W2)) * dsilu(r(Z1)))
     dW1 = dZ1.T @ X0
     db1 = dZ1.sum(0)
     g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dW3.ravel(), db3, dw4, [db4]])
@@ -99,9 +100,9 @@ def abs_scales(p, x, y, in_dim, width):
     out_scale = np.abs(H3) @ np.abs(w4) + abs(b4)
     e = out - y
     dout = e / B
-    dZ3 = bf16(np.outer(dout, w4) * dsilu(Z3))
-    dZ2 = bf16((dZ3 @ bf16(W3)) * dsilu(Z2))
-    dZ1 = bf16((dZ2 @ bf16(W2)) * dsilu(Z1))
+    dZ3 = bf16(np.outer(dout, w4) * dsilu(bf16(Z3)))
+    dZ2 = bf16((dZ3 @ bf16(W3)) * dsilu(bf16(Z2)))
+    dZ1 = bf16((dZ2 @ bf16(W2)) * dsilu(bf16(Z1)))
     a = np.abs
     g = np.concatenate([(a(dZ1).T @ a(X0)).ravel(), a(dZ1).sum(0),
                         (a(dZ2).T @ a(H1)).ravel(), a(dZ2).sum(0),

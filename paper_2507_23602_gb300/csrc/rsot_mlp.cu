@@ -101,7 +101,7 @@ template <bool AT, bool BT, int EPI>
 __global__ void __launch_bounds__(G_THREADS)
     k_gemm_bf16(int M, int N, int K, int kslice, const bf16 *__restrict__ A, int lda,
                 const bf16 *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
-                const float *__restrict__ bias, bf16 *__restrict__ H, int ldh, const float *__restrict__ Z,
+                const float *__restrict__ bias, bf16 *__restrict__ H, int ldh, bf16 *__restrict__ Z,
                 int ldz) {
     __shared__ __align__(16) bf16 As[GM][GK + GPAD];
     __shared__ __align__(16) bf16 Bs[GN][GK + GPAD];
@@ -164,11 +164,11 @@ __global__ void __launch_bounds__(G_THREADS)
                         C[(int64_t)row * ldc + cc] = v;
                     } else if (EPI == EPI_BIAS_SILU) {
                         v += bias[cc];
-                        C[(int64_t)row * ldc + cc] = v;                        // pre-activation
+                        Z[(int64_t)row * ldz + cc] = __float2bfloat16(v);       // pre-activation
                         H[(int64_t)row * ldh + cc] = __float2bfloat16(silu(v));  // activation
                     } else {
                         H[(int64_t)row * ldh + cc] =
-                            __float2bfloat16(v * dsilu(Z[(int64_t)row * ldz + cc]));
+                            __float2bfloat16(v * dsilu(__bfloat162float(Z[(int64_t)row * ldz + cc])));
                     }
                 }
             }
@@ -316,7 +316,7 @@ template <bool AT, bool BT, int EPI>
 __global__ void __launch_bounds__(T5_THREADS)
     k_gemm_t5(int M, int N, int K, int kslice, const bf16 *__restrict__ A, int lda,
               const bf16 *__restrict__ B, int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias,
-              bf16 *__restrict__ H, int ldh, const float *__restrict__ Z, int ldz,
+              bf16 *__restrict__ H, int ldh, bf16 *__restrict__ Z, int ldz,
               int *__restrict__ flags, const __grid_constant__ CUtensorMap tmA,
               const __grid_constant__ CUtensorMap tmB, int tma) {
     extern __shared__ __align__(1024) unsigned char t5_dyn[];
@@ -350,6 +350,16 @@ __global__ void __launch_bounds__(T5_THREADS)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
+    if (EPI == EPI_DSILU && warp == 7 && (N - n0) % 8 == 0 && ldz % 8 == 0) {
+        // the epilogue's Z rows go to L2 while the MMAs run: one bulk prefetch per
+        // row of the tile (min(T5_N, N - n0) BF16 = a multiple of 16 bytes, and
+        // row starts on 16-byte boundaries since ldz and n0 are multiples of 8)
+        const unsigned bytes = (unsigned)min(T5_N, N - n0) * 2u;
+        for (int i = lane; i < T5_M && m0 + i < M; i += 32)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Z + (int64_t)(m0 + i) * ldz + n0),
+                         "r"(bytes)
+                         : "memory");
+    }
     // split K: slice z covers [z kslice, (z + 1) kslice) and writes its own partial C
     const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
     if (EPI == EPI_F32) C += (int64_t)blockIdx.z * M * ldc;
@@ -454,7 +464,7 @@ __global__ void __launch_bounds__(T5_THREADS)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int row = m0 + 32 * q + r8 + i;
-                    zr[i] = (EPI == EPI_DSILU && row < M) ? Z[(int64_t)row * ldz + col] : 0.f;
+                    zr[i] = (EPI == EPI_DSILU && row < M) ? __bfloat162float(Z[(int64_t)row * ldz + col]) : 0.f;
                 }
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -465,7 +475,7 @@ __global__ void __launch_bounds__(T5_THREADS)
                         C[(int64_t)row * ldc + col] = x;
                     } else if (EPI == EPI_BIAS_SILU) {
                         x += bc;
-                        C[(int64_t)row * ldc + col] = x;                        // pre-activation
+                        Z[(int64_t)row * ldz + col] = __float2bfloat16(x);      // pre-activation
                         H[(int64_t)row * ldh + col] = __float2bfloat16(silu(x));  // activation
                     } else {
                         H[(int64_t)row * ldh + col] = __float2bfloat16(x * dsilu(zr[i]));
@@ -498,7 +508,7 @@ __global__ void k_head(const bf16 *__restrict__ H, int width, int64_t rows, cons
 // dZ3 = d_out w4 * SiLU'(Z3) (BF16)
 __global__ void k_head_back(const float *__restrict__ out, const float *__restrict__ y, int64_t rows,
                             int64_t valid, float inv_b, const float *__restrict__ w4,
-                            const float *__restrict__ Z3, int width, float *__restrict__ dout,
+                            const bf16 *__restrict__ Z3, int width, float *__restrict__ dout,
                             bf16 *__restrict__ dZ3, float *__restrict__ loss_terms) {
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -510,7 +520,109 @@ __global__ void k_head_back(const float *__restrict__ out, const float *__restri
         loss_terms[r] = 0.5f * e * e;
     }
     for (int i = lane; i < width; i += 32)
-        dZ3[r * width + i] = __float2bfloat16(d * w4[i] * dsilu(Z3[r * width + i]));
+        dZ3[r * width + i] = __float2bfloat16(d * w4[i] * dsilu(__bfloat162float(Z3[r * width + i])));
+}
+
+// The head's back-propagation with its column sums, for widths of at most 256
+// (a multiple of 8): per row d_out = (out - y) / B and its loss term, dZ3 =
+// BF16(d_out w4 SiLU'(Z3)), and per block the partial sums over its rows of
+// dZ3 (db3), of d_out H3 (dw4), of d_out (db4) and of the loss terms.  Lane l
+// of each warp handles columns 8l .. 8l + 7 with 16-byte loads; the 8 warps
+// take rows w, w + 8, ... of the block's chunk, two rows per step so that four
+// loads are in flight; the warps' sums are added in warp order (deterministic).
+constexpr int HB_CHUNKS = 512;
+__device__ __forceinline__ void hb_row(const uint4 &zv, const uint4 &hv, float d, const float (&wv)[8],
+                                       float (&s3)[8], float (&s4)[8], uint4 &ov) {
+    const __nv_bfloat162 *z2 = reinterpret_cast<const __nv_bfloat162 *>(&zv);
+    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hv);
+    __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&ov);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 z = __bfloat1622float2(z2[k]), h = __bfloat1622float2(h2[k]);
+        const __nv_bfloat16 a = __float2bfloat16(d * wv[2 * k] * dsilu(z.x));
+        const __nv_bfloat16 b = __float2bfloat16(d * wv[2 * k + 1] * dsilu(z.y));
+        o2[k] = __halves2bfloat162(a, b);
+        s3[2 * k] += __bfloat162float(a);
+        s3[2 * k + 1] += __bfloat162float(b);
+        s4[2 * k] = fmaf(d, h.x, s4[2 * k]);
+        s4[2 * k + 1] = fmaf(d, h.y, s4[2 * k + 1]);
+    }
+}
+__global__ void __launch_bounds__(256)
+    k_head_back_v8(const float *__restrict__ out, const float *__restrict__ y, int64_t rows,
+                   int64_t valid, float inv_b, const float *__restrict__ w4, const bf16 *__restrict__ Z3,
+                   const bf16 *__restrict__ H3, int width, float *__restrict__ dout, bf16 *__restrict__ dZ3,
+                   float *__restrict__ part_db3, float *__restrict__ part_dw4,
+                   float *__restrict__ part_db4, float *__restrict__ part_loss) {
+    __shared__ float sh[2][8][257];
+    __shared__ float shs[2][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(rows, r0 + per);
+    const bool act = 8 * lane < width;
+    float wv[8], s3[8], s4[8], sd = 0.f, sl = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        wv[k] = act ? w4[8 * lane + k] : 0.f;
+        s3[k] = 0.f;
+        s4[k] = 0.f;
+    }
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t r = r0 + w; r < r1; r += 16) {
+        const int64_t rb = r + 8;
+        const bool hb = rb < r1;
+        const float ea = r < valid ? out[r] - y[r] : 0.f;
+        const float eb = hb && rb < valid ? out[rb] - y[rb] : 0.f;
+        uint4 za = zero, ha = zero, zb = zero, hbv = zero;
+        if (act) {
+            za = *reinterpret_cast<const uint4 *>(Z3 + r * width + 8 * lane);
+            ha = *reinterpret_cast<const uint4 *>(H3 + r * width + 8 * lane);
+            if (hb) {
+                zb = *reinterpret_cast<const uint4 *>(Z3 + rb * width + 8 * lane);
+                hbv = *reinterpret_cast<const uint4 *>(H3 + rb * width + 8 * lane);
+            }
+        }
+        const float da = ea * inv_b, db = eb * inv_b;
+        sd += da + db;
+        sl += 0.5f * ea * ea + 0.5f * eb * eb;
+        if (lane == 0) {
+            dout[r] = da;
+            if (hb) dout[rb] = db;
+        }
+        if (act) {
+            uint4 o;
+            hb_row(za, ha, da, wv, s3, s4, o);
+            *reinterpret_cast<uint4 *>(dZ3 + r * width + 8 * lane) = o;
+            if (hb) {
+                hb_row(zb, hbv, db, wv, s3, s4, o);
+                *reinterpret_cast<uint4 *>(dZ3 + rb * width + 8 * lane) = o;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        sh[0][w][8 * lane + k] = s3[k];
+        sh[1][w][8 * lane + k] = s4[k];
+    }
+    if (lane == 0) {
+        shs[0][w] = sd;
+        shs[1][w] = sl;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < width; c += blockDim.x) {
+        float a = sh[0][0][c], b = sh[1][0][c];
+        for (int k = 1; k < 8; ++k) {
+            a += sh[0][k][c];
+            b += sh[1][k][c];
+        }
+        part_db3[(int64_t)blockIdx.x * width + c] = a;
+        part_dw4[(int64_t)blockIdx.x * width + c] = b;
+    }
+    if (threadIdx.x < 2) {
+        float t = shs[threadIdx.x][0];
+        for (int k = 1; k < 8; ++k) t += shs[threadIdx.x][k];
+        (threadIdx.x ? part_loss : part_db4)[blockIdx.x] = t;
+    }
 }
 
 // column sums over rows of a BF16 (or FP32 when F) matrix: out[c] = sum_r X[r][c]
@@ -543,19 +655,95 @@ __global__ void k_colsum_part(const T *__restrict__ X, const float *__restrict__
         part[(int64_t)blockIdx.y * cols + c] = t;
     }
 }
-__global__ void k_colsum_fin(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+// out[c] = sum_k part[k][c]: 32 columns per block (lane: column), the 8 warps
+// take chunks w, w + 8, ... and their sums are added in warp order
+__global__ void __launch_bounds__(256)
+    k_colsum_fin(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out) {
+    __shared__ float sh[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
     float t = 0.f;
-    for (int k = 0; k < chunks; ++k) t += part[(int64_t)k * cols + c];
-    out[c] = t;
+    if (c < cols) {
+#pragma unroll 4
+        for (int k = w; k < chunks; k += 8) t += part[(int64_t)k * cols + c];
+    }
+    sh[w][lane] = t;
+    __syncthreads();
+    if (w == 0 && c < cols) {
+        float u = sh[0][lane];
+        for (int k = 1; k < 8; ++k) u += sh[k][lane];
+        out[c] = u;
+    }
 }
-// out[c] = sum_r wgt[r] X[r][c]; part: RED_CHUNKS x cols floats
+inline void colsum_fin(cudaStream_t st, const float *part, int chunks, int cols, float *out) {
+    k_colsum_fin<<<(unsigned)((cols + 31) / 32), 256, 0, st>>>(part, chunks, cols, out);
+}
+// BF16 rows of at most 256 columns (a multiple of 8): lane l of every warp
+// reads columns 8l .. 8l + 7 of a row in one 16-byte load, so a warp reads
+// whole rows; the 8 warps of a block take every 8th row of the block's chunk,
+// and their sums are added in warp order (fixed: deterministic).
+constexpr int RED_CHUNKS_V = 256;
+__global__ void __launch_bounds__(256)
+    k_colsum_v8(const bf16 *__restrict__ X, const float *__restrict__ wgt, int64_t rows, int cols,
+                float *__restrict__ part) {
+    __shared__ float sh[8][257];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(rows, r0 + per);
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (8 * lane < cols)
+        for (int64_t r = r0 + w; r < r1; r += 16) {
+            // rows r and r + 8 per step: two loads in flight per lane
+            const bool hb = r + 8 < r1;
+            const uint4 va = *reinterpret_cast<const uint4 *>(X + r * cols + 8 * lane);
+            const uint4 vb = hb ? *reinterpret_cast<const uint4 *>(X + (r + 8) * cols + 8 * lane)
+                                : make_uint4(0u, 0u, 0u, 0u);
+            const float ga = wgt ? wgt[r] : 1.f, gb = hb ? (wgt ? wgt[r + 8] : 1.f) : 0.f;
+            const __nv_bfloat162 *ha = reinterpret_cast<const __nv_bfloat162 *>(&va);
+            const __nv_bfloat162 *hbp = reinterpret_cast<const __nv_bfloat162 *>(&vb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(ha[k]);
+                s[2 * k] = fmaf(ga, f.x, s[2 * k]);
+                s[2 * k + 1] = fmaf(ga, f.y, s[2 * k + 1]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(hbp[k]);
+                s[2 * k] = fmaf(gb, f.x, s[2 * k]);
+                s[2 * k + 1] = fmaf(gb, f.y, s[2 * k + 1]);
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[w][8 * lane + k] = s[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+        float t = sh[0][c];
+        for (int k = 1; k < 8; ++k) t += sh[k][c];
+        part[(int64_t)blockIdx.x * cols + c] = t;
+    }
+}
+
+// partial sums buffer of a network of the given width: the column sums' chunks,
+// or the head's four partial vectors
+inline size_t red_floats(int w) {
+    return std::max({(size_t)RED_CHUNKS * w, (size_t)RED_CHUNKS_V * w, (size_t)HB_CHUNKS * (2 * w + 2)});
+}
+
+// out[c] = sum_r wgt[r] X[r][c]; part: red_floats(cols) floats
 template <typename T>
 void colsum(cudaStream_t st, const T *X, const float *wgt, int64_t rows, int cols, float *part, float *out) {
+    if constexpr (sizeof(T) == 2) {
+        if (cols % 8 == 0 && cols <= 256) {
+            const int ch = (int)std::min<int64_t>(RED_CHUNKS_V, std::max<int64_t>(1, rows / 64));
+            k_colsum_v8<<<(unsigned)ch, 256, 0, st>>>(X, wgt, rows, cols, part);
+            colsum_fin(st, part, ch, cols, out);
+            return;
+        }
+    }
     const int ch = (int)std::min<int64_t>(RED_CHUNKS, std::max<int64_t>(1, rows / 256));
     k_colsum_part<T><<<dim3((unsigned)((cols + 31) / 32), (unsigned)ch), 256, 0, st>>>(X, wgt, rows, cols, part);
-    k_colsum_fin<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(part, ch, cols, out);
+    colsum_fin(st, part, ch, cols, out);
 }
 
 // Adam on the FP32 master parameters (bias-corrected moments)
@@ -593,13 +781,29 @@ __global__ void k_input_bf16(const float *__restrict__ x, int64_t rows, int in_d
 }
 
 // C[r][c] = sum_z ws[z][r][c] (the split-K partials, in slice order)
-__global__ void k_split_sum(const float *__restrict__ ws, int S, int M, int N, int ldc, float *__restrict__ C) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)M * N) return;
-    const int64_t o = (i / N) * ldc + i % N, zs = (int64_t)M * ldc;
+// 256 threads: 32 consecutive outputs x 8 slice groups; warp g sums slices
+// g, g + 8, g + 16, ... of its 32 outputs (coalesced 128-byte rows), then the 8
+// group sums are added in group order: a fixed order, so the result is
+// deterministic, with 8 x the parallelism of one thread per output.
+constexpr int SPLIT_GROUPS = 8;
+__global__ void __launch_bounds__(32 * SPLIT_GROUPS)
+    k_split_sum(const float *__restrict__ ws, int S, int M, int N, int ldc, float *__restrict__ C) {
+    __shared__ float sh[SPLIT_GROUPS][33];
+    const int cx = threadIdx.x & 31, gz = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + cx;
+    const bool ok = i < (int64_t)M * N;
+    const int64_t o = ok ? (i / N) * ldc + i % N : 0, zs = (int64_t)M * ldc;
     float v = 0.f;
-    for (int z = 0; z < S; ++z) v += ws[z * zs + o];
-    C[o] = v;
+    if (ok)
+        for (int z = gz; z < S; z += SPLIT_GROUPS) v += ws[z * zs + o];
+    sh[gz][cx] = v;
+    __syncthreads();
+    if (gz == 0 && ok) {
+        float t = sh[0][cx];
+#pragma unroll
+        for (int k = 1; k < SPLIT_GROUPS; ++k) t += sh[k][cx];
+        C[o] = t;
+    }
 }
 
 constexpr int SPLIT_MAX = 128;   // split-K slices at most (workspace SPLIT_MAX x M x ldc floats)
@@ -640,7 +844,7 @@ bool t5_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int K, int ld, b
 template <bool AT, bool BT, int EPI>
 void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int N, int K, const bf16 *A,
           int lda, const bf16 *B, int ldb, float *C, int ldc, const float *bias, bf16 *H, int ldh,
-          const float *Z, int ldz) {
+          bf16 *Z, int ldz) {
     const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
     int S = 1;
     if (EPI == EPI_F32 && ws) S = std::max(1, std::min({K / 512, 2 * sms / std::max(1, tiles), SPLIT_MAX}));
@@ -673,7 +877,7 @@ void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int 
                                                              H, ldh, Z, ldz);
     }
     if (S > 1)
-        k_split_sum<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, st>>>(ws, S, M, N, ldc, C);
+        k_split_sum<<<(unsigned)(((int64_t)M * N + 31) / 32), 32 * SPLIT_GROUPS, 0, st>>>(ws, S, M, N, ldc, C);
 }
 
 uint64_t mix64(uint64_t &s) {
@@ -699,7 +903,8 @@ struct rsot_mlp {
     bf16 *W1b = nullptr, *W1bT = nullptr, *W2b = nullptr, *W2bT = nullptr, *W3b = nullptr, *W3bT = nullptr;
     // activations
     bf16 *X0 = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZ = nullptr, *dZ2 = nullptr;
-    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dH = nullptr, *out = nullptr, *dout = nullptr,
+    bf16 *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr;   // pre-activations, rounded to BF16
+    float *dH = nullptr, *out = nullptr, *dout = nullptr,
           *lt = nullptr, *xin = nullptr, *yin = nullptr, *scal = nullptr;
     int gemm_kind = 0;       // 0: tcgen05 GEMM (TMA), 1: mma.sync GEMM, 2: tcgen05 GEMM (cp.async)
     float *ws = nullptr;     // split-K partials of the weight-gradient GEMMs
@@ -768,28 +973,45 @@ void mlp_forward(rsot_mlp *m, int64_t rows) {
     cudaStream_t st = m->stream;
     k_input_bf16<<<(unsigned)((R * (int64_t)m->in_pad + 255) / 256), 256, 0, st>>>(m->xin, R, m->in_dim,
                                                                                  m->in_pad, m->X0);
-    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, m->in_pad, m->X0, m->in_pad, m->W1b, m->in_pad, m->Z1,
-                                      w, m->P + m->off[1], m->H1, w, nullptr, 0);
-    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H1, w, m->W2b, w, m->Z2, w, m->P + m->off[3],
-                                      m->H2, w, nullptr, 0);
-    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H2, w, m->W3b, w, m->Z3, w, m->P + m->off[5],
-                                      m->H3, w, nullptr, 0);
+    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, m->in_pad, m->X0, m->in_pad, m->W1b, m->in_pad, nullptr,
+                                      w, m->P + m->off[1], m->H1, w, m->Z1, w);
+    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H1, w, m->W2b, w, nullptr, w, m->P + m->off[3],
+                                      m->H2, w, m->Z2, w);
+    gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H2, w, m->W3b, w, nullptr, w, m->P + m->off[5],
+                                      m->H3, w, m->Z3, w);
     k_head<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->H3, w, R, m->P + m->off[6], m->P + m->off[7], m->out);
 }
 
-// forward + backward: gradients of loss = sum_valid (out - y)^2 / (2 rows) into m->G
-void mlp_backward(rsot_mlp *m, int64_t rows) {
+// forward + backward: gradients of loss = sum_valid (out - y)^2 / (2 rows) into m->G;
+// loss_sum (device, one float) receives the sum of the loss terms 0.5 (out - y)^2
+void mlp_backward(rsot_mlp *m, int64_t rows, float *loss_sum) {
     const int w = m->width, R = (int)((rows + 127) / 128 * 128);
     cudaStream_t st = m->stream;
     mlp_forward(m, rows);
     float *G = m->G;
-    k_head_back<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
-                                                         m->P + m->off[6], m->Z3, w, m->dout, m->dZ, m->lt);
-    colsum<bf16>(st, m->H3, m->dout, R, w, m->red, G + m->off[6]);   // dw4 = sum_r dout_r H3[r]
-    colsum<float>(st, m->dout, nullptr, R, 1, m->red, G + m->off[7]);
-    // layer 3: dW3 = dZ3^T H2, db3 = colsum dZ3, dZ2 = (dZ3 W3) * SiLU'(Z2)
+    if (w % 8 == 0 && w <= 256) {
+        // head back-propagation with its column sums: dw4 = sum_r dout_r H3[r],
+        // db3 = colsum dZ3, db4 = sum_r dout_r and the loss
+        const int ch = (int)std::min<int64_t>(HB_CHUNKS, std::max<int64_t>(1, R / 64));
+        float *p3 = m->red, *p4 = p3 + (size_t)HB_CHUNKS * w, *p5 = p4 + (size_t)HB_CHUNKS * w,
+              *p6 = p5 + HB_CHUNKS;
+        k_head_back_v8<<<(unsigned)ch, 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
+                                                     m->P + m->off[6], m->Z3, m->H3, w, m->dout, m->dZ,
+                                                     p3, p4, p5, p6);
+        colsum_fin(st, p4, ch, w, G + m->off[6]);
+        colsum_fin(st, p3, ch, w, G + m->off[5]);
+        colsum_fin(st, p5, ch, 1, G + m->off[7]);
+        if (loss_sum) colsum_fin(st, p6, ch, 1, loss_sum);
+    } else {
+        k_head_back<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
+                                                             m->P + m->off[6], m->Z3, w, m->dout, m->dZ, m->lt);
+        colsum<bf16>(st, m->H3, m->dout, R, w, m->red, G + m->off[6]);   // dw4 = sum_r dout_r H3[r]
+        colsum<float>(st, m->dout, nullptr, R, 1, m->red, G + m->off[7]);
+        colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[5]);   // db3 = colsum dZ3
+        if (loss_sum) colsum<float>(st, m->lt, nullptr, R, 1, m->red, loss_sum);
+    }
+    // layer 3: dW3 = dZ3^T H2, dZ2 = (dZ3 W3) * SiLU'(Z2)
     gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, w, R, m->dZ, w, m->H2, w, G + m->off[4], w, nullptr, nullptr, 0, nullptr, 0);
-    colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[5]);
     gemm<false, false, EPI_DSILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->dZ, w, m->W3bT, w, nullptr, 0, nullptr, m->dZ2, w, m->Z2, w);
     // layer 2
     gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, w, R, m->dZ2, w, m->H1, w, G + m->off[2], w, nullptr, nullptr, 0, nullptr, 0);
@@ -853,7 +1075,7 @@ rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out
     if (!e) e = cudaMalloc(&m->scal, 16);
     if (!e) e = cudaMalloc(&m->flags, sizeof(int));
     if (!e) e = cudaMalloc(&m->ws, (size_t)SPLIT_MAX * w * std::max(w, m->in_pad) * sizeof(float));
-    if (!e) e = cudaMalloc(&m->red, (size_t)RED_CHUNKS * w * sizeof(float));
+    if (!e) e = cudaMalloc(&m->red, red_floats(w) * sizeof(float));
     int dev = 0;
     if (!e) e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -923,13 +1145,13 @@ rsot_status rsot_mlp_gradients(rsot_mlp *m, int64_t rows, const float *x, const 
     if (!m || rows < 1 || !x || !y) return RSOT_ERR_ARG;
     cudaError_t e = mlp_reserve(m, rows);
     const int64_t R = (rows + 127) / 128 * 128;
-    if (!e) e = cudaMemsetAsync(m->xin, 0, (size_t)R * m->in_dim * 4, m->stream);
-    if (!e) e = cudaMemsetAsync(m->yin, 0, (size_t)R * 4, m->stream);
+    // the padding rows (rows .. R) are zeroed; the copies fill the others
+    if (!e && R > rows) e = cudaMemsetAsync(m->xin + rows * m->in_dim, 0, (size_t)(R - rows) * m->in_dim * 4, m->stream);
+    if (!e && R > rows) e = cudaMemsetAsync(m->yin + rows, 0, (size_t)(R - rows) * 4, m->stream);
     if (!e) e = cudaMemcpyAsync(m->xin, x, (size_t)rows * m->in_dim * 4, cudaMemcpyDefault, m->stream);
     if (!e) e = cudaMemcpyAsync(m->yin, y, (size_t)rows * 4, cudaMemcpyDefault, m->stream);
     if (!e) {
-        mlp_backward(m, rows);
-        colsum<float>(m->stream, m->lt, nullptr, R, 1, m->red, m->scal);
+        mlp_backward(m, rows, m->scal);
         e = cudaGetLastError();
     }
     float l = 0.f;
