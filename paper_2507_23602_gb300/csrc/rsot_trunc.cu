@@ -1238,8 +1238,11 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB)
 // halves of 64 (lane l: rows 2l, 2l + 1 of each half), each half classified
 // by its own ball against every n-block of 8 columns (outside: skipped,
 // inside: no test, boundary: the weight tp_incl of every pair), so that both
-// halves skip independently; stages of FB_TS records are bulk-copied into
-// shared memory and released per warp, as in the tensor-core passes.
+// halves skip independently.  Per n-block one of three forms: one half live
+// (that half's chain alone), both inside (no test), otherwise both halves with
+// the weight, each half's class folded into the test's operand.  Stages of
+// FB_TS records are bulk-copied into shared memory and released per warp, as
+// in the tensor-core passes.
 constexpr int FB_THREADS = 256;
 constexpr int FB_WARPS = FB_THREADS / 32;
 constexpr int FB_ROWS = FB_WARPS * 128;     // rows per CTA
@@ -1260,6 +1263,36 @@ __device__ __forceinline__ float2 fb_r(const float2 (&X)[3], float2 w0, float2 w
     r = __ffma2_rn(X[1], w1, r);
     r = __ffma2_rn(X[0], w0, r);
     return r;
+}
+
+// pass 1, one half of the warp live in an n-block: the eight targets of the
+// half's row pair, tested (boundary) or not (inside)
+template <int D>
+__device__ __forceinline__ void fb1_half(const Rec12 *T, const float2 (&X)[3], float2 ng, float2 a, bool bnd,
+                                         float2 &acc, float2 &cntf) {
+    if (bnd) {
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) {
+            const float4 a4 = T[tt].a, b4 = T[tt].b;
+            const float2 r = fb_r<D>(X, make_float2(a4.x, a4.y), make_float2(a4.z, a4.w),
+                                     make_float2(b4.x, b4.y), make_float2(b4.z, b4.w));
+            const float2 e = __fadd2_rn(r, ng);
+            const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+            const float2 v = __fadd2_rn(r, make_float2(T[tt].c.x, T[tt].c.y));
+            const float2 y = make_float2(tp_incl(v.x, a.x), tp_incl(v.y, a.y));
+            acc = __ffma2_rn(p, y, acc);
+            cntf = __fadd2_rn(cntf, y);
+        }
+    } else {
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) {
+            const float4 a4 = T[tt].a, b4 = T[tt].b;
+            const float2 r = fb_r<D>(X, make_float2(a4.x, a4.y), make_float2(a4.z, a4.w),
+                                     make_float2(b4.x, b4.y), make_float2(b4.z, b4.w));
+            const float2 e = __fadd2_rn(r, ng);
+            acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+        }
+    }
 }
 
 template <int D>
@@ -1377,6 +1410,12 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                     if (l0 && !x0) icnt += rvs[0] * jreal;
                     if (l1 && !x1) icnt += rvs[1] * jreal;
                     const Rec12 *T = &s_rec[slot][8 * nb];
+                    if (l0 != l1) {
+                        // one half live: its chain alone (eight targets in flight)
+                        if (l0) fb1_half<D>(T, X[0], ng[0], nAS[0], x0, acc[0], cntf);
+                        else fb1_half<D>(T, X[1], ng[1], nAS[1], x1, acc[1], cntf);
+                        continue;
+                    }
                     if (l0 && l1 && !x0 && !x1) {
                         // both halves inside: no test, both chains interleaved
 #pragma unroll
@@ -1392,10 +1431,19 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                             }
                         }
                     } else {
-                        // per half a weight: the test (boundary), 1 (inside) or 0 (outside),
-                        // selected without branching so that both chains interleave
-                        const float yin0 = l0 ? 1.f : 0.f, yin1 = l1 ? 1.f : 0.f;
+                        // both halves live, at least one on the boundary: per half the weight
+                        // tp_incl(v, a) with the half's class folded into a -- its -A 2^64
+                        // (boundary: the test), +inf (inside: 1) or -inf (outside: 0) -- so
+                        // that every pair takes one form and both chains interleave; the
+                        // boundary halves' weights are counted (cb)
                         const float cb0 = x0 ? 1.f : 0.f, cb1 = x1 ? 1.f : 0.f;
+                        float2 nAc[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const bool bnd = h ? x1 : x0;
+                            const float f = (h ? l1 : l0) ? INFINITY : -INFINITY;
+                            nAc[h] = bnd ? nAS[h] : make_float2(f, f);
+                        }
 #pragma unroll
                         for (int tt = 0; tt < 8; ++tt) {
                             const float4 a4 = T[tt].a, b4 = T[tt].b;
@@ -1408,10 +1456,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                                 const float2 e = __fadd2_rn(r, ng[h]);
                                 const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
                                 const float2 v = __fadd2_rn(r, nbv);
-                                const bool bnd = h ? x1 : x0;
-                                const float yi = h ? yin1 : yin0;
-                                const float2 y = make_float2(bnd ? tp_incl(v.x, nAS[h].x) : yi,
-                                                             bnd ? tp_incl(v.y, nAS[h].y) : yi);
+                                const float2 y = make_float2(tp_incl(v.x, nAc[h].x), tp_incl(v.y, nAc[h].y));
                                 acc[h] = __ffma2_rn(p, y, acc[h]);
                                 const float cb = h ? cb1 : cb0;
                                 cntf = __ffma2_rn(y, make_float2(cb, cb), cntf);
@@ -1540,6 +1585,39 @@ __global__ void k_pdup_s(const float *__restrict__ xs, const float *__restrict__
 // warp's 128), columns the sorted points of the stage; per pair the exponent
 // of pass 1 (the same FFMA2 chain on the same operands), shifted by u_q, and
 // in boundary blocks weighted by the same tp_incl test.
+// pass 2, one half of the warp live in an n-block: the eight points against
+// the half's target pair, tested (boundary) or not (inside)
+template <int D>
+__device__ __forceinline__ void fb2_half(const Rec8 *T, const float *Ab, const float2 (&W)[3], float2 C,
+                                         float2 NB, bool bnd, float2 &acc) {
+    if (bnd) {
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) {
+            const float4 a4 = T[tt].a, b4 = T[tt].b;
+            float2 r = C;
+            if (D == 3) r = __ffma2_rn(make_float2(b4.x, b4.y), W[2], r);
+            r = __ffma2_rn(make_float2(a4.z, a4.w), W[1], r);
+            r = __ffma2_rn(make_float2(a4.x, a4.y), W[0], r);
+            const float2 e = __fadd2_rn(r, make_float2(b4.z, b4.w));
+            const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+            const float2 v = __fadd2_rn(r, NB);
+            const float a = Ab[tt] * -TP_S;
+            acc = __ffma2_rn(p, make_float2(tp_incl(v.x, a), tp_incl(v.y, a)), acc);
+        }
+    } else {
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) {
+            const float4 a4 = T[tt].a, b4 = T[tt].b;
+            float2 r = C;
+            if (D == 3) r = __ffma2_rn(make_float2(b4.x, b4.y), W[2], r);
+            r = __ffma2_rn(make_float2(a4.z, a4.w), W[1], r);
+            r = __ffma2_rn(make_float2(a4.x, a4.y), W[0], r);
+            const float2 e = __fadd2_rn(r, make_float2(b4.z, b4.w));
+            acc = __fadd2_rn(acc, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+        }
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(FB_THREADS, 2)
     k_grad_fb(const Rec12 *__restrict__ tdup, const float4 *__restrict__ tball64,
@@ -1634,6 +1712,12 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                 const bool x0 = (bd0 >> b) & 1u, x1 = (bd1 >> b) & 1u;
                 const Rec8 *T = &s_rec[slot][8 * nb];
                 const float *Ab = &s_A[slot][8 * nb];
+                if (l0 != l1) {
+                    // one half live: its chain alone (eight points in flight)
+                    if (l0) fb2_half<D>(T, Ab, W[0], C[0], NB[0], x0, acc[0]);
+                    else fb2_half<D>(T, Ab, W[1], C[1], NB[1], x1, acc[1]);
+                    continue;
+                }
                 if (l0 && l1 && !x0 && !x1) {
                     // both halves inside: no test, both chains interleaved
 #pragma unroll
@@ -1652,8 +1736,17 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                         }
                     }
                 } else {
-                    // per half a weight: the test (boundary), 1 (inside) or 0 (outside)
-                    const float yin0 = l0 ? 1.f : 0.f, yin1 = l1 ? 1.f : 0.f;
+                    // both halves live, at least one on the boundary: per half the weight
+                    // tp_incl(r + b, -A 2^64) with the half's class folded into b -- its
+                    // b'_j (boundary: the test), +inf (inside: 1, or 0 for a padding point,
+                    // whose -A 2^64 is -inf) or -inf (outside: 0) -- one form per pair
+                    float2 NBc[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const bool bnd = h ? x1 : x0;
+                        const float f = (h ? l1 : l0) ? INFINITY : -INFINITY;
+                        NBc[h] = bnd ? NB[h] : make_float2(f, f);
+                    }
 #pragma unroll
                     for (int tt = 0; tt < 8; ++tt) {
                         const float4 a4 = T[tt].a, b4 = T[tt].b;
@@ -1668,10 +1761,8 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                             r = __ffma2_rn(x0v, W[h][0], r);
                             const float2 e = __fadd2_rn(r, u);
                             const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
-                            const float2 v = __fadd2_rn(r, NB[h]);
-                            const bool bnd = h ? x1 : x0;
-                            const float yi = h ? yin1 : yin0;
-                            const float2 y = make_float2(bnd ? tp_incl(v.x, nA) : yi, bnd ? tp_incl(v.y, nA) : yi);
+                            const float2 v = __fadd2_rn(r, NBc[h]);
+                            const float2 y = make_float2(tp_incl(v.x, nA), tp_incl(v.y, nA));
                             acc[h] = __ffma2_rn(p, y, acc[h]);
                         }
                     }
