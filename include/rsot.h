@@ -355,7 +355,11 @@ typedef struct {
                             the truncation bound tail sum(nu) (2 sum(m) + sum(nu))
                             on ||grad J~ - grad J||_1 is subtracted from tol_l1
                             with the compensated one, so a refined stop holds for
-                            the untruncated J.  0: dense                       */
+                            the untruncated J.  An eps-stage (or refinement
+                            phase) whose first truncated evaluation keeps more
+                            than 35 % of all pairs evaluates dense from that
+                            point on (within tail of the truncated functional,
+                            and cheaper there).  0: dense                      */
     double tol_l1;       /* stop when ||grad J||_1 <= tol_l1 (Remark 3.3)           */
     double stage_tol_l1; /* tolerance of the intermediate stages (<=0: 100 tol_l1:
                             they only warm-start the next stage)                 */

@@ -121,6 +121,7 @@ void trace_collect(rsot_problem *p) {
 }
 
 int64_t num_targets(const rsot_problem *p) { return p->n; }
+int64_t num_points(const rsot_problem *p) { return p->nq; }
 double mass_sum(const rsot_problem *p) { return p->msum; }
 void copy_nu(const rsot_problem *p, double *out) {
     cudaMemcpy(out, p->nu, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost);

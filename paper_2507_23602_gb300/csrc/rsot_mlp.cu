@@ -530,7 +530,7 @@ __global__ void k_head_back(const float *__restrict__ out, const float *__restri
 // of each warp handles columns 8l .. 8l + 7 with 16-byte loads; the 8 warps
 // take rows w, w + 8, ... of the block's chunk, two rows per step so that four
 // loads are in flight; the warps' sums are added in warp order (deterministic).
-constexpr int HB_CHUNKS = 512;
+constexpr int HB_CHUNKS = 1024;   // most row chunks (blocks) of the head kernel
 __device__ __forceinline__ void hb_row(const uint4 &zv, const uint4 &hv, float d, const float (&wv)[8],
                                        float (&s3)[8], float (&s4)[8], uint4 &ov) {
     const __nv_bfloat162 *z2 = reinterpret_cast<const __nv_bfloat162 *>(&zv);
@@ -655,34 +655,51 @@ __global__ void k_colsum_part(const T *__restrict__ X, const float *__restrict__
         part[(int64_t)blockIdx.y * cols + c] = t;
     }
 }
-// out[c] = sum_k part[k][c]: 32 columns per block (lane: column), the 8 warps
-// take chunks w, w + 8, ... and their sums are added in warp order
-__global__ void __launch_bounds__(256)
-    k_colsum_fin(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out) {
-    __shared__ float sh[8][33];
+// out[c] = sum_k part[k][c] for up to four (part, chunks, cols, out) segments
+// (blockIdx.y): 32 columns per block (lane: column), the 32 warps take chunks
+// w, w + 32, ... and their sums are added in warp order (deterministic)
+struct FinSeg {
+    const float *part;
+    float *out;
+    int chunks, cols;
+};
+struct FinSegs {
+    FinSeg s[4];
+};
+__global__ void __launch_bounds__(1024) k_colsum_fin(const __grid_constant__ FinSegs segs) {
+    __shared__ float sh[32][33];
+    const FinSeg &g = segs.s[blockIdx.y];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= g.cols) return;   // uniform over the block
     float t = 0.f;
-    if (c < cols) {
+    if (c < g.cols) {
 #pragma unroll 4
-        for (int k = w; k < chunks; k += 8) t += part[(int64_t)k * cols + c];
+        for (int k = w; k < g.chunks; k += 32) t += g.part[(int64_t)k * g.cols + c];
     }
     sh[w][lane] = t;
     __syncthreads();
-    if (w == 0 && c < cols) {
+    if (w == 0 && c < g.cols) {
         float u = sh[0][lane];
-        for (int k = 1; k < 8; ++k) u += sh[k][lane];
-        out[c] = u;
+        for (int k = 1; k < 32; ++k) u += sh[k][lane];
+        g.out[c] = u;
     }
 }
+inline void colsum_fin(cudaStream_t st, const FinSegs &segs, int nseg) {
+    int cmax = 1;
+    for (int i = 0; i < nseg; ++i) cmax = std::max(cmax, segs.s[i].cols);
+    k_colsum_fin<<<dim3((unsigned)((cmax + 31) / 32), (unsigned)nseg), 1024, 0, st>>>(segs);
+}
 inline void colsum_fin(cudaStream_t st, const float *part, int chunks, int cols, float *out) {
-    k_colsum_fin<<<(unsigned)((cols + 31) / 32), 256, 0, st>>>(part, chunks, cols, out);
+    FinSegs segs{};
+    segs.s[0] = FinSeg{part, out, chunks, cols};
+    colsum_fin(st, segs, 1);
 }
 // BF16 rows of at most 256 columns (a multiple of 8): lane l of every warp
 // reads columns 8l .. 8l + 7 of a row in one 16-byte load, so a warp reads
 // whole rows; the 8 warps of a block take every 8th row of the block's chunk,
 // and their sums are added in warp order (fixed: deterministic).
-constexpr int RED_CHUNKS_V = 256;
+constexpr int RED_CHUNKS_V = 1024;   // most row chunks (blocks) of k_colsum_v8
 __global__ void __launch_bounds__(256)
     k_colsum_v8(const bf16 *__restrict__ X, const float *__restrict__ wgt, int64_t rows, int cols,
                 float *__restrict__ part) {
@@ -731,11 +748,19 @@ inline size_t red_floats(int w) {
 }
 
 // out[c] = sum_r wgt[r] X[r][c]; part: red_floats(cols) floats
+// row chunks of the 256-thread streaming kernels: four blocks per SM (two
+// waves at two resident blocks), at least 64 rows each
+inline int stream_chunks(int64_t rows, int sms, int most) {
+    return (int)std::min<int64_t>(std::min<int64_t>(most, 4 * (int64_t)std::max(1, sms)),
+                                  std::max<int64_t>(1, rows / 64));
+}
+
 template <typename T>
-void colsum(cudaStream_t st, const T *X, const float *wgt, int64_t rows, int cols, float *part, float *out) {
+void colsum(cudaStream_t st, const T *X, const float *wgt, int64_t rows, int cols, float *part, float *out,
+            int sms) {
     if constexpr (sizeof(T) == 2) {
         if (cols % 8 == 0 && cols <= 256) {
-            const int ch = (int)std::min<int64_t>(RED_CHUNKS_V, std::max<int64_t>(1, rows / 64));
+            const int ch = stream_chunks(rows, sms, RED_CHUNKS_V);
             k_colsum_v8<<<(unsigned)ch, 256, 0, st>>>(X, wgt, rows, cols, part);
             colsum_fin(st, part, ch, cols, out);
             return;
@@ -992,35 +1017,37 @@ void mlp_backward(rsot_mlp *m, int64_t rows, float *loss_sum) {
     if (w % 8 == 0 && w <= 256) {
         // head back-propagation with its column sums: dw4 = sum_r dout_r H3[r],
         // db3 = colsum dZ3, db4 = sum_r dout_r and the loss
-        const int ch = (int)std::min<int64_t>(HB_CHUNKS, std::max<int64_t>(1, R / 64));
+        const int ch = stream_chunks(R, m->sms, HB_CHUNKS);
         float *p3 = m->red, *p4 = p3 + (size_t)HB_CHUNKS * w, *p5 = p4 + (size_t)HB_CHUNKS * w,
               *p6 = p5 + HB_CHUNKS;
         k_head_back_v8<<<(unsigned)ch, 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
                                                      m->P + m->off[6], m->Z3, m->H3, w, m->dout, m->dZ,
                                                      p3, p4, p5, p6);
-        colsum_fin(st, p4, ch, w, G + m->off[6]);
-        colsum_fin(st, p3, ch, w, G + m->off[5]);
-        colsum_fin(st, p5, ch, 1, G + m->off[7]);
-        if (loss_sum) colsum_fin(st, p6, ch, 1, loss_sum);
+        FinSegs segs{};
+        segs.s[0] = FinSeg{p4, G + m->off[6], ch, w};
+        segs.s[1] = FinSeg{p3, G + m->off[5], ch, w};
+        segs.s[2] = FinSeg{p5, G + m->off[7], ch, 1};
+        segs.s[3] = FinSeg{p6, loss_sum, ch, 1};
+        colsum_fin(st, segs, loss_sum ? 4 : 3);
     } else {
         k_head_back<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
                                                              m->P + m->off[6], m->Z3, w, m->dout, m->dZ, m->lt);
-        colsum<bf16>(st, m->H3, m->dout, R, w, m->red, G + m->off[6]);   // dw4 = sum_r dout_r H3[r]
-        colsum<float>(st, m->dout, nullptr, R, 1, m->red, G + m->off[7]);
-        colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[5]);   // db3 = colsum dZ3
-        if (loss_sum) colsum<float>(st, m->lt, nullptr, R, 1, m->red, loss_sum);
+        colsum<bf16>(st, m->H3, m->dout, R, w, m->red, G + m->off[6], m->sms);   // dw4 = sum_r dout_r H3[r]
+        colsum<float>(st, m->dout, nullptr, R, 1, m->red, G + m->off[7], m->sms);
+        colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[5], m->sms);   // db3 = colsum dZ3
+        if (loss_sum) colsum<float>(st, m->lt, nullptr, R, 1, m->red, loss_sum, m->sms);
     }
     // layer 3: dW3 = dZ3^T H2, dZ2 = (dZ3 W3) * SiLU'(Z2)
     gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, w, R, m->dZ, w, m->H2, w, G + m->off[4], w, nullptr, nullptr, 0, nullptr, 0);
     gemm<false, false, EPI_DSILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->dZ, w, m->W3bT, w, nullptr, 0, nullptr, m->dZ2, w, m->Z2, w);
     // layer 2
     gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, w, R, m->dZ2, w, m->H1, w, G + m->off[2], w, nullptr, nullptr, 0, nullptr, 0);
-    colsum<bf16>(st, m->dZ2, nullptr, R, w, m->red, G + m->off[3]);
+    colsum<bf16>(st, m->dZ2, nullptr, R, w, m->red, G + m->off[3], m->sms);
     gemm<false, false, EPI_DSILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->dZ2, w, m->W2bT, w, nullptr, 0, nullptr, m->dZ, w, m->Z1, w);
     // layer 1: dW1 = dZ1^T X0, db1 = colsum dZ1
     gemm<true, true, EPI_F32>(st, m->gemm_kind, m->flags, m->ws, m->sms, w, m->in_pad, R, m->dZ, w, m->X0, m->in_pad, G + m->off[0], m->in_pad,
                               nullptr, nullptr, 0, nullptr, 0);
-    colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[1]);
+    colsum<bf16>(st, m->dZ, nullptr, R, w, m->red, G + m->off[1], m->sms);
 }
 
 }  // namespace

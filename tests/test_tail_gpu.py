@@ -162,3 +162,33 @@ def test_solve_with_tail_meets_tolerance_against_dense():
         assert np.abs(gt).sum() <= 1e-6 + 3 * tail
     finally:
         P.close()
+
+
+def test_tail_solve_runs_dense_where_most_pairs_are_kept():
+    """A tail-mode evaluator whose first (truncated) evaluation keeps more than
+    35 % of all pairs runs dense from then on (the dense functional lies within
+    the tail tolerance of the truncated one); an FP64 evaluator evaluates that
+    first point again dense.  A single-stage FP64 solve has one evaluator: it
+    equals the dense solve bitwise, with one more evaluation, the truncated
+    probe at the start point."""
+    eps = 1e-2      # psi = 0 keeps 83 % of the pairs at tail 1e-12
+    p = ri.make_problem(3, 10, 2000, eps, src_seed=74, src_k=3, tgt_seed=75, tgt_k=2, nu_seed=76)
+    P = rs().Problem(p.x, p.mass, p.y, p.nu)
+    try:
+        allp = p.x.shape[0] * p.y.shape[0]
+        _, _, pr0 = P.eval_tail(np.zeros(p.y.shape[0]), eps, 1e-12, rs().FP64)
+        assert 0.35 * allp < pr0 < allp
+        sd, std = P.solve(eps=eps, tol_l1=1e-8, precision=rs().FP64)
+        st_, stt = P.solve(eps=eps, tol_l1=1e-8, precision=rs().FP64, tail=1e-12)
+        assert std.status == 0 and stt.status == 0
+        assert np.array_equal(sd, st_)
+        assert stt.evals == std.evals + 1
+        assert stt.pairs == std.pairs + pr0
+        # where the start point keeps fewer pairs the solve stays truncated
+        eps2 = 3e-3     # psi = 0 keeps 28 %
+        _, _, pr1 = P.eval_tail(np.zeros(p.y.shape[0]), eps2, 1e-12, rs().FP64)
+        assert pr1 < 0.35 * allp
+        _, st2 = P.solve(eps=eps2, tol_l1=1e-8, precision=rs().FP64, tail=1e-12)
+        assert st2.status == 0 and st2.pairs < 0.5 * st2.evals * allp
+    finally:
+        P.close()
