@@ -248,6 +248,23 @@ __device__ __forceinline__ void tma_load_2d(void *smem, const CUtensorMap *map, 
         : "memory");
 }
 
+// one 2-D TMA tile copy shared -> global (x = column, y = row) in the thread's
+// bulk group; the part of the box beyond the tensor's extent is not written
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *smem, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(smem)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the bulk group's reads of shared memory are done (its global writes complete
+// on their own; the kernel's end orders them before later work on the stream)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
                  "r"(bytes)
@@ -318,15 +335,18 @@ __global__ void __launch_bounds__(T5_THREADS)
               const bf16 *__restrict__ B, int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias,
               bf16 *__restrict__ H, int ldh, bf16 *__restrict__ Z, int ldz,
               int *__restrict__ flags, const __grid_constant__ CUtensorMap tmA,
-              const __grid_constant__ CUtensorMap tmB, int tma) {
+              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmH,
+              const __grid_constant__ CUtensorMap tmZ, int tma) {
     extern __shared__ __align__(1024) unsigned char t5_dyn[];
     __shared__ __align__(8) uint64_t done[2];   // commit of the MMAs that read stage buffer s
     __shared__ __align__(8) uint64_t full[2];   // TMA bytes of stage buffer s have landed
     __shared__ uint32_t s_tmem;
+    __shared__ float s_bias[T5_N];
     // operand slots on 1,024-byte boundaries (the 128-byte swizzle atoms)
     unsigned char *const t5_smem = t5_dyn + ((1024u - (smem_u32(t5_dyn) & 1023u)) & 1023u);
     // tma bit 0: A by TMA, bit 1: B by TMA; a transposed operand copied by TMA
-    // is read MN-major (transpose bits 15 / 16 of the instruction descriptor)
+    // is read MN-major (transpose bits 15 / 16 of the instruction descriptor);
+    // bit 2: H stored by TMA, bit 3: Z stored by TMA (BF16 epilogues)
     const bool tA = (tma & 1) != 0, tB = (tma & 2) != 0;
     const unsigned tx = (tA ? T5_TILE_TMA : 0) + (tB ? T5_TILE_TMA : 0);
     const uint32_t idesc = T5_IDESC | ((tA && AT) ? 1u << 15 : 0u) | ((tB && BT) ? 1u << 16 : 0u);
@@ -339,6 +359,8 @@ __global__ void __launch_bounds__(T5_THREADS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (EPI == EPI_BIAS_SILU)
+        for (int i = tid; i < T5_N; i += T5_THREADS) s_bias[i] = n0 + i < N ? bias[n0 + i] : 0.f;
     if (tid == 32) {
         mbar_init(&done[0], 1);
         mbar_init(&done[1], 1);
@@ -443,12 +465,81 @@ __global__ void __launch_bounds__(T5_THREADS)
     if (tid == 0 && tx)
         for (int b = 0; b < 2; ++b)
             if ((fbad >> b) & 1u) mbar_wait(&full[b], ((fpar >> b) & 1u) ^ 1u);
+    // one verdict for the CTA: a wait that gave up in any thread voids the tile
+    // (and raises the flag below); the shared-memory epilogue starts after
+    // thread 0's last wait for its copies
+    ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp & 3, cb = (warp >> 2) * 64;   // lanes 32 q .. + 31, columns cb .. + 63
+    const bool tstore = EPI != EPI_F32 && (tma & 4) && (EPI != EPI_BIAS_SILU || (tma & 8));
+    if (tstore) {
+        // BF16 epilogue through TMA stores: every MMA is done, so the stage buffers
+        // hold the output tiles, per 64 columns a box of 128 rows x 128 B in the
+        // 128-byte swizzle (16-byte chunk j of row r at chunk j ^ (r % 8)): H at 0
+        // and 16 KB, Z at 32 and 48 KB.  The thread owns TMEM lane (row) r and
+        // writes whole 16-byte chunks (eight lanes of a quarter-warp: eight
+        // different chunk positions, no bank conflict)
+        unsigned char *const sH = t5_smem, *const sZ = t5_smem + 32768;
+        const int r = 32 * q + lane;
+        const bool live = ok && nk > 0;
+#pragma unroll 1
+        for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+            uint32_t v[32];
+            t5_ld32(v, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0);
+            const int hb = (c0 >> 6) * 16384, ch0 = (c0 & 63) >> 3;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int cc = c0 + 8 * k;   // first column of the chunk within the tile
+                const unsigned off = (unsigned)(hb + r * 128 + (((ch0 + k) ^ (r & 7)) << 4));
+                uint4 hv;
+                if (EPI == EPI_BIAS_SILU) {
+                    uint4 zv;
+                    float x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = __uint_as_float(v[8 * k + i]) + s_bias[cc + i];
+                    zv.x = pack_bf16(x[0], x[1]);    // pre-activation
+                    zv.y = pack_bf16(x[2], x[3]);
+                    zv.z = pack_bf16(x[4], x[5]);
+                    zv.w = pack_bf16(x[6], x[7]);
+                    hv.x = pack_bf16(silu(x[0]), silu(x[1]));   // activation
+                    hv.y = pack_bf16(silu(x[2]), silu(x[3]));
+                    hv.z = pack_bf16(silu(x[4]), silu(x[5]));
+                    hv.w = pack_bf16(silu(x[6]), silu(x[7]));
+                    *reinterpret_cast<uint4 *>(sZ + off) = zv;
+                } else {
+                    // x SiLU'(Z) with the stored BF16 pre-activation of the row
+                    uint4 zin = make_uint4(0u, 0u, 0u, 0u);
+                    if (live && m0 + r < M && n0 + cc < N)
+                        zin = *reinterpret_cast<const uint4 *>(Z + (int64_t)(m0 + r) * ldz + n0 + cc);
+                    const __nv_bfloat162 *z2 = reinterpret_cast<const __nv_bfloat162 *>(&zin);
+                    uint32_t *hp = &hv.x;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 z = __bfloat1622float2(z2[i]);
+                        hp[i] = pack_bf16(__uint_as_float(v[8 * k + 2 * i]) * dsilu(z.x),
+                                          __uint_as_float(v[8 * k + 2 * i + 1]) * dsilu(z.y));
+                    }
+                }
+                *reinterpret_cast<uint4 *>(sH + off) = hv;
+            }
+        }
+        // the tiles' generic-proxy writes become visible to the TMA (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && live) {
+            for (int h = 0; h < 2; ++h)
+                if (n0 + 64 * h < N) {
+                    tma_store_2d(&tmH, sH + h * 16384, n0 + 64 * h, m0);
+                    if (EPI == EPI_BIAS_SILU) tma_store_2d(&tmZ, sZ + h * 16384, n0 + 64 * h, m0);
+                }
+            bulk_commit();
+            bulk_wait_read();   // the tiles have left shared memory before the CTA exits
+        }
+    }
     // every MMA is done: the stage buffers hold the epilogue's transposes
     float *T = reinterpret_cast<float *>(t5_smem) + warp * 32 * 33;
-    const int q = warp & 3, cb = (warp >> 2) * 64;   // lanes 32 q .. + 31, columns cb .. + 63
 #pragma unroll 1
-    for (int c0 = cb; c0 < cb + 64; c0 += 32) {
+    for (int c0 = cb; c0 < (tstore ? cb : cb + 64); c0 += 32) {
         uint32_t v[32];
         t5_ld32(v, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0);
 #pragma unroll
@@ -885,17 +976,26 @@ void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int 
         }
         // TMA operand copies: a box (64 K) never crosses a K slice's end, since
         // slices start and end on multiples of 64 or at K, where zero fill begins
-        CUtensorMap ma, mb;
+        CUtensorMap ma, mb, mh, mz;
         memset(&ma, 0, sizeof(ma));
         memset(&mb, 0, sizeof(mb));
+        memset(&mh, 0, sizeof(mh));
+        memset(&mz, 0, sizeof(mz));
         int tma = 0;
         if (kind == 0 && (S == 1 || kslice % T5_K == 0)) {
             if (t5_tensor_map(&ma, A, M, K, lda, AT)) tma |= 1;
             if (t5_tensor_map(&mb, B, N, K, ldb, BT)) tma |= 2;
         }
+        // BF16 outputs by TMA stores (boxes of 64 columns x 128 rows); the
+        // x SiLU'(Z) epilogue reads Z rows in 16-byte pieces: N and ldz multiples of 8
+        if (kind == 0 && EPI != EPI_F32 && N % 8 == 0 && (EPI != EPI_DSILU || ldz % 8 == 0)) {
+            if (t5_tensor_map(&mh, H, M, N, ldh, false)) tma |= 4;
+            if (EPI == EPI_BIAS_SILU && t5_tensor_map(&mz, Z, M, N, ldz, false)) tma |= 8;
+        }
         dim3 grid((N + T5_N - 1) / T5_N, (M + T5_M - 1) / T5_M, S);
         k_gemm_t5<AT, BT, EPI><<<grid, T5_THREADS, T5_SMEM, st>>>(M, N, K, kslice, A, lda, B, ldb, Cw, ldc,
-                                                                   bias, H, ldh, Z, ldz, flags, ma, mb, tma);
+                                                                   bias, H, ldh, Z, ldz, flags, ma, mb, mh, mz,
+                                                                   tma);
     } else {
         dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, S);
         k_gemm_bf16<AT, BT, EPI><<<grid, G_THREADS, 0, st>>>(M, N, K, kslice, A, lda, B, ldb, Cw, ldc, bias,

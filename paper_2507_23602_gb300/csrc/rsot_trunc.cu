@@ -1364,7 +1364,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
         wball[h] = pball64[(r0 + 64 * h) / 64];
         wal[h] = pal64[(r0 + 64 * h) / 64];
     }
-    unsigned long long icnt = 0;            // pairs of inside blocks
+    unsigned icnt = 0;                      // pairs of inside blocks (at most 4 rows x 8 stages x FB_TS)
     float2 cntf = make_float2(0.f, 0.f);    // weights of boundary-block pairs
     bool aborted = false;
     for (int it = 0; it < cnt; ++it) {
@@ -1375,7 +1375,8 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
             aborted = true;
             break;
         }
-        const int64_t sj0 = (int64_t)s_list[it] * FB_TS;   // sorted index of the stage's first column
+        // real columns of the stage (FB_TS but in the array's last stage)
+        const int sreal = (int)min((int64_t)FB_TS, n - (int64_t)s_list[it] * FB_TS);
         unsigned cls0 = 0, cls1 = 0;   // 2 bits at 2 i: n-block lane + 32 i against half 0 / 1
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -1406,7 +1407,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                     const int b = __ffs(gm) - 1, nb = grp * FB_GROUP + b;
                     const bool l0 = (g0 >> b) & 1u, l1 = (g1 >> b) & 1u;
                     const bool x0 = (b0 >> b) & 1u, x1 = (b1 >> b) & 1u;
-                    const unsigned jreal = (unsigned)max((int64_t)0, min((int64_t)8, n - (sj0 + 8 * nb)));
+                    const unsigned jreal = (unsigned)max(0, min(8, sreal - 8 * nb));
                     if (l0 && !x0) icnt += rvs[0] * jreal;
                     if (l1 && !x1) icnt += rvs[1] * jreal;
                     const Rec12 *T = &s_rec[slot][8 * nb];
@@ -1557,7 +1558,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
             o[l + 1] = M[h].y == -INFINITY ? make_float2(kPadC, 0.f) : make_float2(M[h].y, (float)Sd[h].y);
         }
     }
-    atomicAdd(&s_pairs, icnt + (unsigned long long)__float2uint_rn(cntf.x + cntf.y));
+    atomicAdd(&s_pairs, (unsigned long long)icnt + (unsigned long long)__float2uint_rn(cntf.x + cntf.y));
     __syncthreads();
     if (tid == 0) {
         if (s_pairs) atomicAdd(pairs, s_pairs);
