@@ -583,6 +583,250 @@ __global__ void __launch_bounds__(T5_THREADS)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T5_N) : "memory");
 }
 
+// ------------------------------------------------ persistent tcgen05 GEMM (t6)
+// The BF16-epilogue GEMMs of the network (forward: bias + SiLU; back-
+// propagation: x SiLU'(Z)) with K-contiguous A [M][K] and B [N][K], N <= 256
+// a multiple of 32: one CTA per SM loops over 128-row tiles, each covering all
+// N columns, with warp-specialised roles so that a tile's epilogue overlaps the
+// next tile's MMAs:
+//   warp 0 (one lane): TMA copies of A (64 K x 128 rows) and B (64 K x N rows),
+//     128-byte swizzle, into T6_STAGES stages (full / empty mbarriers);
+//   warp 1: allocates 2 N TMEM columns (two accumulators); one lane issues
+//     tcgen05.mma (M 128, N, K 16) and commits each stage back to its empty
+//     barrier and each finished tile to its accumulator's full barrier;
+//   warps 2-17: the epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
+//     rows) and the box of 64 columns 64 (w - 2) / 4;
+//     it releases the accumulator after its last tcgen05.ld and stores each
+//     box (32 rows x 64 columns) through its staging tile in the 128-byte
+//     swizzle (TMA stores by the warp's lane 0); for x SiLU'(Z) the warp's Z
+//     box comes by TMA into the same layout while the tile's MMAs run.  Four
+//     warps per lane quarter keep the conversions and SiLU evaluations up with
+//     the MMAs (with one or two per quarter the epilogue was the bottleneck).
+// Every mbarrier wait is bounded; a wait that gives up raises kErrTimeout and
+// its role stops (the others then give up on their own waits).
+constexpr int T6_STAGES = 2, T6_EPI = 16, T6_THREADS = 32 * (2 + T6_EPI);
+constexpr int T6_A = 128 * 128;                     // A stage: 128 rows x 128 B
+constexpr int T6_B = 256 * 128;                     // B stage: up to 256 rows x 128 B
+constexpr int T6_STAGE = T6_A + T6_B;
+constexpr int T6_BOX = 32 * 128;                    // staging box: 32 rows x 64 BF16 columns
+constexpr int T6_STG = T6_EPI * 2 * T6_BOX;         // per epilogue warp: H and Z boxes
+constexpr int T6_SMEM = T6_STAGES * T6_STAGE + T6_STG + 1024;   // + alignment slack: 225 KB
+static_assert(T6_SMEM + 2048 <= 232448, "the persistent GEMM's shared memory fits one CTA per SM");
+
+__device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(T6_THREADS, 1)
+    k_gemm_t6(int M, int N, int K, const float *__restrict__ bias, int *__restrict__ flags,
+              const __grid_constant__ CUtensorMap tmA,
+              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmH,
+              const __grid_constant__ CUtensorMap tmZ) {
+    extern __shared__ __align__(1024) unsigned char t6_dyn[];
+    __shared__ __align__(8) uint64_t full[T6_STAGES], empty[T6_STAGES], accf[2], acce[2], mdone, zbar[T6_EPI];
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_bias[256];
+    unsigned char *const sm = t6_dyn + ((1024u - (smem_u32(t6_dyn) & 1023u)) & 1023u);
+    unsigned char *const stg = sm + T6_STAGES * T6_STAGE;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles = (M + 127) / 128, nkb = (K + 63) / 64;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t tcols = N <= 16 ? 32u : N <= 32 ? 64u : N <= 64 ? 128u : N <= 128 ? 256u : 512u;
+    if (EPI == EPI_BIAS_SILU)
+        for (int i = tid; i < 256; i += T6_THREADS) s_bias[i] = i < N ? bias[i] : 0.f;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < T6_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], T6_EPI);
+        }
+        mbar_init(&mdone, 1);
+        for (int e = 0; e < T6_EPI; ++e) mbar_init(&zbar[e], 1);
+        fence_barrier_init();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    bool ok = true;
+    if (warp == 0) {
+        // producer: stage it % T6_STAGES, its n-th use waits for the (n - 1)-th release
+        if (lane == 0) {
+            const unsigned bytes = (unsigned)(T6_A + N * 128);
+            int it = 0;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % T6_STAGES, n = it / T6_STAGES;
+                    if (n > 0 && !mbar_wait(&empty[s], (unsigned)(n - 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *As = sm + s * T6_STAGE, *Bs = As + T6_A;
+                    mbar_expect_tx(&full[s], bytes);
+                    tma_load_2d(As, &tmA, kb * 64, t * 128, &full[s]);
+                    tma_load_2d(Bs, &tmB, kb * 64, 0, &full[s]);
+                }
+            }
+            // copies still in flight land before the CTA exits: the last copy into
+            // every stage is awaited (bounded)
+            for (int s = 0; s < T6_STAGES; ++s) {
+                const int uses = it / T6_STAGES + (s < it % T6_STAGES ? 1 : 0);
+                if (uses > 0) (void)mbar_wait(&full[s], (unsigned)(uses - 1) & 1u);
+            }
+            if (!ok) atomicOr(flags, kErrTimeout);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, tc = 0;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tc) {
+                const int a = tc & 1, na = tc >> 1;
+                if (na > 0 && !mbar_wait(&acce[a], (unsigned)(na - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % T6_STAGES, n = it / T6_STAGES;
+                    if (!mbar_wait(&full[s], (unsigned)n & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sm + s * T6_STAGE), b0 = a0 + T6_A;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = t5_desc_sw128(a0 + kk * 32), bd = t5_desc_sw128(b0 + kk * 32);
+                        const uint32_t accum = (kb > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                tmem + (uint32_t)(a * N)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                            : "memory");
+                    }
+                    tcgen05_commit(&empty[s]);   // the stage is free once these MMAs are done
+                }
+                if (!ok) break;
+                tcgen05_commit(&accf[a]);        // the tile's accumulator is complete
+            }
+            // every MMA issued is complete before the tensor memory is freed
+            tcgen05_commit(&mdone);
+            (void)mbar_wait(&mdone, 0u);
+            if (!ok) atomicOr(flags, kErrTimeout);
+        }
+    } else {
+        // epilogue warps: rows 32 q .. + 31 of each tile, boxes 64 (jb + T6_EPI / 4 i)
+        const int q = warp & 3, jb = (warp - 2) >> 2;
+        unsigned char *const bH = stg + (warp - 2) * (2 * T6_BOX), *const bZ = bH + T6_BOX;
+        // x SiLU'(Z): the warp's Z box (32 rows x 64 columns, at most one per tile
+        // since N <= 256) comes by TMA into its Z staging tile while the MMAs run
+        const int cz = 64 * jb, e = warp - 2;
+        int tc = 0, nz = 0;
+        bool zpend = false;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tc) {
+            const int a = tc & 1, na = tc >> 1;
+            if (EPI == EPI_DSILU && cz < N && lane == 0) {
+                mbar_expect_tx(&zbar[e], (unsigned)T6_BOX);
+                tma_load_2d(bZ, &tmZ, cz, t * 128 + 32 * q, &zbar[e]);
+                zpend = true;
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&accf[a], (unsigned)na & 1u))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (EPI == EPI_DSILU && cz < N) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&zbar[e], (unsigned)nz & 1u))) {
+                    ok = false;
+                    break;
+                }
+                ++nz;
+                zpend = false;
+            }
+            for (int cb = 64 * jb; cb < N; cb += 64 * (T6_EPI / 4)) {
+#pragma unroll 1
+                for (int hf = 0; hf < 2 && cb + 32 * hf < N; ++hf) {
+                    const int c0 = cb + 32 * hf;
+                    uint32_t v[32];
+                    t5_ld32(v, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * N + c0));
+                    uint4 hv[4], zv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int cc = c0 + 8 * k;
+                        if (EPI == EPI_BIAS_SILU) {
+                            float x[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) x[i] = __uint_as_float(v[8 * k + i]) + s_bias[cc + i];
+                            zv[k].x = pack_bf16(x[0], x[1]);
+                            zv[k].y = pack_bf16(x[2], x[3]);
+                            zv[k].z = pack_bf16(x[4], x[5]);
+                            zv[k].w = pack_bf16(x[6], x[7]);
+                            hv[k].x = pack_bf16(silu(x[0]), silu(x[1]));
+                            hv[k].y = pack_bf16(silu(x[2]), silu(x[3]));
+                            hv[k].z = pack_bf16(silu(x[4]), silu(x[5]));
+                            hv[k].w = pack_bf16(silu(x[6]), silu(x[7]));
+                        } else {
+                            // Z of the row from the swizzled staging tile (zero beyond M)
+                            const uint4 zin = *reinterpret_cast<const uint4 *>(
+                                bZ + lane * 128 + (((4 * hf + k) ^ (lane & 7)) << 4));
+                            const __nv_bfloat162 *z2 = reinterpret_cast<const __nv_bfloat162 *>(&zin);
+                            uint32_t *hp = &hv[k].x;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float2 z = __bfloat1622float2(z2[i]);
+                                hp[i] = pack_bf16(__uint_as_float(v[8 * k + 2 * i]) * dsilu(z.x),
+                                                  __uint_as_float(v[8 * k + 2 * i + 1]) * dsilu(z.y));
+                            }
+                        }
+                    }
+                    if (hf == 0) {
+                        // the previous box's store has read the staging tile
+                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const unsigned off = (unsigned)(lane * 128 + (((4 * hf + k) ^ (lane & 7)) << 4));
+                        *reinterpret_cast<uint4 *>(bH + off) = hv[k];
+                        if (EPI == EPI_BIAS_SILU) *reinterpret_cast<uint4 *>(bZ + off) = zv[k];
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_2d(&tmH, bH, cb, t * 128 + 32 * q);
+                    if (EPI == EPI_BIAS_SILU) tma_store_2d(&tmZ, bZ, cb, t * 128 + 32 * q);
+                    bulk_commit();
+                }
+            }
+            // every TMEM read of this accumulator by the warp is done: release it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[a]);
+        }
+        if (lane == 0) bulk_wait_read();
+        // a Z copy issued before a wait that gave up lands before the CTA exits
+        if (zpend && lane == 0) (void)mbar_wait(&zbar[e], (unsigned)nz & 1u);
+        if (!ok && lane == 0) atomicOr(flags, kErrTimeout);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
 // out[b] = sum_i H3[b][i] w4[i] + b4 (FP32), one warp per row
 __global__ void k_head(const bf16 *__restrict__ H, int width, int64_t rows, const float *__restrict__ w,
                        const float *__restrict__ b, float *__restrict__ out) {
@@ -951,6 +1195,31 @@ bool t5_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int K, int ld, b
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of a BF16 matrix src[r * ld + c] (rows x cols) with boxes of 64
+// columns x box_rows rows in the 128-byte swizzle (TMA loads and stores of the
+// persistent kernel); false when the encoder is unavailable or a TMA rule is
+// broken (base and row stride multiples of 16 bytes, box_rows <= 256).
+bool t6_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int cols, int ld, int box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || !src || rows < 1 || cols < 1 || ld < cols || box_rows < 1 || box_rows > 256 ||
+        (reinterpret_cast<uintptr_t>(src) & 15) || ((int64_t)ld * 2) % 16)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows}, estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(src), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // kind 0: tcgen05 kernel with TMA operand copies where the operand allows them,
 // 2: the same kernel with cp.async copies only, 1: warp-level mma.sync kernel
 // (same operands, epilogues).
@@ -967,6 +1236,27 @@ void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int 
     const int kslice = S > 1 ? (K + S - 1) / S / 64 * 64 + 64 : K;
     if (S > 1) S = (K + kslice - 1) / kslice;
     float *Cw = S > 1 ? ws : C;
+    if (kind == 0 && EPI != EPI_F32 && !AT && !BT && N % 32 == 0 && N <= 256 &&
+        (EPI != EPI_DSILU || ldz % 8 == 0)) {
+        // the persistent warp-specialised kernel, when every operand allows TMA
+        CUtensorMap ma, mb, mh, mz;
+        memset(&mz, 0, sizeof(mz));
+        bool t6 = t6_tensor_map(&ma, A, M, K, lda, 128) && t6_tensor_map(&mb, B, N, K, ldb, N) &&
+                  t6_tensor_map(&mh, H, M, N, ldh, 32);
+        if (t6) t6 = t6_tensor_map(&mz, Z, M, N, ldz, 32);   // stored (forward) or loaded (x SiLU'(Z))
+        if (t6) {
+            static bool attr6 = false;   // 209 KB of dynamic shared memory, set once per instance
+            if (!attr6) {
+                cudaFuncSetAttribute((const void *)k_gemm_t6<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     T6_SMEM);
+                attr6 = true;
+            }
+            const int tiles = (M + 127) / 128;
+            k_gemm_t6<EPI><<<std::max(1, std::min(tiles, sms)), T6_THREADS, T6_SMEM, st>>>(
+                M, N, K, bias, flags, ma, mb, mh, mz);
+            return;
+        }
+    }
     if (kind == 0 || kind == 2) {
         static bool attr = false;   // 69 KB of dynamic shared memory, set once per instance
         if (!attr) {
