@@ -619,10 +619,10 @@ __device__ __forceinline__ void tcgen05_commit(uint64_t *bar) {
                  : "memory");
 }
 
-template <int EPI>
+template <bool AT, bool BT, int EPI>
 __global__ void __launch_bounds__(T6_THREADS, 1)
-    k_gemm_t6(int M, int N, int K, const float *__restrict__ bias, int *__restrict__ flags,
-              const __grid_constant__ CUtensorMap tmA,
+    k_gemm_t6(int M, int N, int K, int kslice, int mblocks, float *__restrict__ C, int ldc,
+              const float *__restrict__ bias, int *__restrict__ flags, const __grid_constant__ CUtensorMap tmA,
               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmH,
               const __grid_constant__ CUtensorMap tmZ) {
     extern __shared__ __align__(1024) unsigned char t6_dyn[];
@@ -632,8 +632,13 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
     unsigned char *const sm = t6_dyn + ((1024u - (smem_u32(t6_dyn) & 1023u)) & 1023u);
     unsigned char *const stg = sm + T6_STAGES * T6_STAGE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles = (M + 127) / 128, nkb = (K + 63) / 64;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+    // tile t: rows 128 (t % mblocks) .., K slice t / mblocks (partials at C + slice M ldc)
+    const int tiles = mblocks * ((K + kslice - 1) / kslice);
+    auto tile_rows = [&](int t) { return (t % mblocks) * 128; };
+    auto tile_k0 = [&](int t) { return (t / mblocks) * kslice; };
+    auto tile_nkb = [&](int t) { return (min(K, tile_k0(t) + kslice) - tile_k0(t) + 63) / 64; };
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (AT ? 1u << 15 : 0u) | (BT ? 1u << 16 : 0u) |
+                           ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
     const uint32_t tcols = N <= 16 ? 32u : N <= 32 ? 64u : N <= 64 ? 128u : N <= 128 ? 256u : 512u;
     if (EPI == EPI_BIAS_SILU)
         for (int i = tid; i < 256; i += T6_THREADS) s_bias[i] = i < N ? bias[i] : 0.f;
@@ -664,9 +669,13 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
     if (warp == 0) {
         // producer: stage it % T6_STAGES, its n-th use waits for the (n - 1)-th release
         if (lane == 0) {
-            const unsigned bytes = (unsigned)(T6_A + N * 128);
+            // A: one box of 64 K x 128 rows, or transposed two of 64 rows x 64 K
+            // (8 KB apart, read MN-major); B: one box of 64 K x N rows, or
+            // transposed N / 64 boxes of 64 columns x 64 K
+            const unsigned bytes = (unsigned)(T6_A + (BT ? (N + 63) / 64 * 8192 : N * 128));
             int it = 0;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int m0 = tile_rows(t), kb0 = tile_k0(t), nkb = tile_nkb(t);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % T6_STAGES, n = it / T6_STAGES;
                     if (n > 0 && !mbar_wait(&empty[s], (unsigned)(n - 1) & 1u)) {
@@ -674,9 +683,18 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                         break;
                     }
                     unsigned char *As = sm + s * T6_STAGE, *Bs = As + T6_A;
+                    const int k0 = kb0 + 64 * kb;
                     mbar_expect_tx(&full[s], bytes);
-                    tma_load_2d(As, &tmA, kb * 64, t * 128, &full[s]);
-                    tma_load_2d(Bs, &tmB, kb * 64, 0, &full[s]);
+                    if (AT) {
+                        tma_load_2d(As, &tmA, m0, k0, &full[s]);
+                        tma_load_2d(As + 8192, &tmA, m0 + 64, k0, &full[s]);
+                    } else {
+                        tma_load_2d(As, &tmA, k0, m0, &full[s]);
+                    }
+                    if (BT)
+                        for (int i = 0; 64 * i < N; ++i) tma_load_2d(Bs + 8192 * i, &tmB, 64 * i, k0, &full[s]);
+                    else
+                        tma_load_2d(Bs, &tmB, k0, 0, &full[s]);
                 }
             }
             // copies still in flight land before the CTA exits: the last copy into
@@ -697,6 +715,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int nkb = tile_nkb(t);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % T6_STAGES, n = it / T6_STAGES;
                     if (!mbar_wait(&full[s], (unsigned)n & 1u)) {
@@ -707,7 +726,8 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                     const uint32_t a0 = smem_u32(sm + s * T6_STAGE), b0 = a0 + T6_A;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = t5_desc_sw128(a0 + kk * 32), bd = t5_desc_sw128(b0 + kk * 32);
+                        const uint64_t ad = AT ? t5_desc_mn_sw128(a0 + kk * 2048) : t5_desc_sw128(a0 + kk * 32);
+                        const uint64_t bd = BT ? t5_desc_mn_sw128(b0 + kk * 2048) : t5_desc_sw128(b0 + kk * 32);
                         const uint32_t accum = (kb > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -736,10 +756,10 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
         int tc = 0, nz = 0;
         bool zpend = false;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tc) {
-            const int a = tc & 1, na = tc >> 1;
+            const int a = tc & 1, na = tc >> 1, m0 = tile_rows(t);
             if (EPI == EPI_DSILU && cz < N && lane == 0) {
                 mbar_expect_tx(&zbar[e], (unsigned)T6_BOX);
-                tma_load_2d(bZ, &tmZ, cz, t * 128 + 32 * q, &zbar[e]);
+                tma_load_2d(bZ, &tmZ, cz, m0 + 32 * q, &zbar[e]);
                 zpend = true;
             }
             if (!__all_sync(0xffffffffu, mbar_wait(&accf[a], (unsigned)na & 1u))) {
@@ -756,6 +776,37 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                 zpend = false;
             }
             for (int cb = 64 * jb; cb < N; cb += 64 * (T6_EPI / 4)) {
+                if constexpr (EPI == EPI_F32) {
+                    // FP32 (split-K partials of the slice, rows slice M + row of the
+                    // partials' map): two boxes of 32 columns x the warp's 32 rows in
+                    // the staging tiles (16-byte chunk j of row r at j ^ (r % 8)),
+                    // stored by TMA; M is a multiple of 32, so a box never reaches
+                    // into the next slice's rows
+                    const int prow = (t / mblocks) * M + m0 + 32 * q;
+                    const bool rows_in = m0 + 32 * q < M;
+#pragma unroll 1
+                    for (int hf = 0; hf < 2 && cb + 32 * hf < N; ++hf) {
+                        const int c0 = cb + 32 * hf;
+                        uint32_t v[32];
+                        t5_ld32(v, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * N + c0));
+                        if (hf == 0) {
+                            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                            __syncwarp();
+                        }
+                        unsigned char *const bx = hf ? bZ : bH;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            *reinterpret_cast<uint4 *>(bx + lane * 128 + ((i ^ (lane & 7)) << 4)) =
+                                make_uint4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && rows_in) {
+                        tma_store_2d(&tmH, bH, cb, prow);
+                        if (cb + 32 < N) tma_store_2d(&tmH, bZ, cb + 32, prow);
+                        bulk_commit();
+                    }
+                } else {
 #pragma unroll 1
                 for (int hf = 0; hf < 2 && cb + 32 * hf < N; ++hf) {
                     const int c0 = cb + 32 * hf;
@@ -806,9 +857,10 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) {
-                    tma_store_2d(&tmH, bH, cb, t * 128 + 32 * q);
-                    if (EPI == EPI_BIAS_SILU) tma_store_2d(&tmZ, bZ, cb, t * 128 + 32 * q);
+                    tma_store_2d(&tmH, bH, cb, m0 + 32 * q);
+                    if (EPI == EPI_BIAS_SILU) tma_store_2d(&tmZ, bZ, cb, m0 + 32 * q);
                     bulk_commit();
+                }
                 }
             }
             // every TMEM read of this accumulator by the warp is done: release it
@@ -1195,11 +1247,13 @@ bool t5_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int K, int ld, b
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tensor map of a BF16 matrix src[r * ld + c] (rows x cols) with boxes of 64
-// columns x box_rows rows in the 128-byte swizzle (TMA loads and stores of the
-// persistent kernel); false when the encoder is unavailable or a TMA rule is
-// broken (base and row stride multiples of 16 bytes, box_rows <= 256).
-bool t6_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int cols, int ld, int box_rows) {
+// Tensor map of a BF16 (or FP32) matrix src[r * ld + c] (rows x cols) with
+// boxes of 128 bytes of columns (64 BF16, 32 FP32) x box_rows rows in the
+// 128-byte swizzle (TMA loads and stores of the persistent kernel); false when
+// the encoder is unavailable or a TMA rule is broken (base and row stride
+// multiples of 16 bytes, box_rows <= 256).
+bool t6_tensor_map(CUtensorMap *map, const void *src, int rows, int cols, int ld, int box_rows,
+                   bool f32 = false) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -1209,13 +1263,15 @@ bool t6_tensor_map(CUtensorMap *map, const bf16 *src, int rows, int cols, int ld
             fn = nullptr;
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }();
+    const int es = f32 ? 4 : 2;   // element bytes; a box row is 128 bytes either way
     if (!encode || !src || rows < 1 || cols < 1 || ld < cols || box_rows < 1 || box_rows > 256 ||
-        (reinterpret_cast<uintptr_t>(src) & 15) || ((int64_t)ld * 2) % 16)
+        (reinterpret_cast<uintptr_t>(src) & 15) || ((int64_t)ld * es) % 16)
         return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows}, estr[2] = {1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(src), dims, strides, box, estr,
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows}, estr[2] = {1, 1};
+    return encode(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void *>(src), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1236,24 +1292,36 @@ void gemm(cudaStream_t st, int kind, int *flags, float *ws, int sms, int M, int 
     const int kslice = S > 1 ? (K + S - 1) / S / 64 * 64 + 64 : K;
     if (S > 1) S = (K + kslice - 1) / kslice;
     float *Cw = S > 1 ? ws : C;
-    if (kind == 0 && EPI != EPI_F32 && !AT && !BT && N % 32 == 0 && N <= 256 &&
-        (EPI != EPI_DSILU || ldz % 8 == 0)) {
-        // the persistent warp-specialised kernel, when every operand allows TMA
+    // the persistent warp-specialised kernel: the BF16 epilogues with K-contiguous
+    // operands and the FP32 weight gradients with MN-contiguous ones, N <= 256 a
+    // multiple of 32, when every operand allows TMA; the same K slices as the
+    // kernels below, so every form sums the same partials in the same order
+    const bool t6_shape = EPI == EPI_F32 ? (AT && BT && M % 32 == 0 && (S == 1 || kslice % 64 == 0))
+                                         : (!AT && !BT && (EPI != EPI_DSILU || ldz % 8 == 0));
+    if (kind == 0 && t6_shape && N % 32 == 0 && N <= 256) {
         CUtensorMap ma, mb, mh, mz;
+        memset(&mh, 0, sizeof(mh));
         memset(&mz, 0, sizeof(mz));
-        bool t6 = t6_tensor_map(&ma, A, M, K, lda, 128) && t6_tensor_map(&mb, B, N, K, ldb, N) &&
-                  t6_tensor_map(&mh, H, M, N, ldh, 32);
-        if (t6) t6 = t6_tensor_map(&mz, Z, M, N, ldz, 32);   // stored (forward) or loaded (x SiLU'(Z))
+        // boxes: K-contiguous A 64 x 128 rows, B 64 x N rows; MN-contiguous 64 x 64
+        bool t6 = AT ? t6_tensor_map(&ma, A, K, M, lda, 64) : t6_tensor_map(&ma, A, M, K, lda, 128);
+        if (t6) t6 = BT ? t6_tensor_map(&mb, B, K, N, ldb, 64) : t6_tensor_map(&mb, B, N, K, ldb, N);
+        if (t6 && EPI != EPI_F32)
+            t6 = t6_tensor_map(&mh, H, M, N, ldh, 32) &&
+                 t6_tensor_map(&mz, Z, M, N, ldz, 32);   // Z stored (forward) or loaded (x SiLU'(Z))
+        if (t6 && EPI == EPI_F32)   // the FP32 results: S slices of M rows, boxes 32 x 32
+            t6 = t6_tensor_map(&mh, Cw, S * M, N, ldc, 32, true);
         if (t6) {
-            static bool attr6 = false;   // 209 KB of dynamic shared memory, set once per instance
+            static bool attr6 = false;   // 225 KB of dynamic shared memory, set once per instance
             if (!attr6) {
-                cudaFuncSetAttribute((const void *)k_gemm_t6<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     T6_SMEM);
+                cudaFuncSetAttribute((const void *)k_gemm_t6<AT, BT, EPI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, T6_SMEM);
                 attr6 = true;
             }
-            const int tiles = (M + 127) / 128;
-            k_gemm_t6<EPI><<<std::max(1, std::min(tiles, sms)), T6_THREADS, T6_SMEM, st>>>(
-                M, N, K, bias, flags, ma, mb, mh, mz);
+            const int mblocks = (M + 127) / 128, tiles6 = mblocks * S;
+            k_gemm_t6<AT, BT, EPI><<<std::max(1, std::min(tiles6, sms)), T6_THREADS, T6_SMEM, st>>>(
+                M, N, K, kslice, mblocks, Cw, ldc, bias, flags, ma, mb, mh, mz);
+            if (S > 1)
+                k_split_sum<<<(unsigned)(((int64_t)M * N + 31) / 32), 32 * SPLIT_GROUPS, 0, st>>>(ws, S, M, N, ldc, C);
             return;
         }
     }

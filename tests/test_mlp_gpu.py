@@ -56,9 +56,12 @@ def elementwise(a, b, s):
 
 @pytest.mark.parametrize("kind", KINDS)
 # (3, 64, 37): fewer rows than one TMA box; (5, 104, 300): K = 104, so the
-# second K box is zero-filled past 40 of its 64 columns, and N = 104 < 128 rows
+# second K box is zero-filled past 40 of its 64 columns, and N = 104 < 128 rows;
+# (6, 96, 500) and (4, 160, 333): the persistent kernel's last 64-column box
+# half filled (N = 96, 160 are multiples of 32, not of 64)
 @pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 1000), (18, 256, 4096), (5, 64, 300),
-                                               (7, 200, 777), (3, 64, 37), (5, 104, 300)])
+                                               (7, 200, 777), (3, 64, 37), (5, 104, 300),
+                                               (6, 96, 500), (4, 160, 333)])
 def test_forward_matches_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 7, kind)
     try:
@@ -73,7 +76,7 @@ def test_forward_matches_oracle(in_dim, width, rows, kind):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300), (7, 200, 777),
-                                               (5, 104, 300)])
+                                               (5, 104, 300), (6, 96, 500), (4, 160, 333)])
 def test_gradients_match_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 11, kind)
     try:
@@ -122,11 +125,14 @@ def test_gemm_kernels_agree():
         net.close()
 
 
-@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 5000), (7, 200, 777), (3, 64, 37)])
+@pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 5000), (7, 200, 777), (3, 64, 37),
+                                               (4, 160, 333)])
 def test_tma_and_cp_async_copies_give_equal_results(in_dim, width, rows):
-    """The tcgen05 kernel with TMA operand copies (128-byte swizzled tiles)
-    and with cp.async copies (unswizzled tiles): the same MMAs over the same
-    K stages, so outputs, loss and gradients are bitwise equal."""
+    """The default tcgen05 GEMMs (TMA operand copies into 128-byte swizzled
+    tiles; the persistent kernel for the BF16 epilogues where N <= 256 is a
+    multiple of 32) and the tcgen05 kernel with cp.async copies (unswizzled
+    tiles): the same MMAs over the same K stages, so outputs, loss and
+    gradients are bitwise equal."""
     net, x, y = setup(in_dim, width, rows, 17, rs().GEMM_TCGEN05)
     try:
         o0 = net.forward(x)
