@@ -84,6 +84,7 @@ struct Grid {
     float2 *part1b = nullptr;
     double *part2b = nullptr;
     Rec8 *pdup_s = nullptr;   // FP32 block-skip pass 2: sorted point records (per evaluation)
+    float *nAq_s = nullptr;   // FP32 block-skip pass 2: -A_q 2^64 of the sorted points (per evaluation)
     int *off1b = nullptr, *off2b = nullptr;
     int k1b = 0, k2b = 0;
 };
@@ -1568,9 +1569,11 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
     }
 }
 
-// sorted point records of the FP32 block-skip pass 2: (x0,x0,x1,x1) (x2,x2,u,u)
-__global__ void k_pdup_s(const float *__restrict__ xs, const float *__restrict__ u_s, int64_t nqt, int d,
-                         Rec8 *__restrict__ pdup) {
+// sorted point records of the FP32 block-skip pass 2: (x0,x0,x1,x1) (x2,x2,u,u),
+// and the points' -A_q 2^64 (the tests' operand, formed once per evaluation)
+__global__ void k_pdup_s(const float *__restrict__ xs, const float *__restrict__ u_s,
+                         const float *__restrict__ Aq, int64_t nqt, int d, Rec8 *__restrict__ pdup,
+                         float *__restrict__ nAq) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nqt) return;
     float x[3] = {0.f, 0.f, 0.f};
@@ -1580,6 +1583,7 @@ __global__ void k_pdup_s(const float *__restrict__ xs, const float *__restrict__
     r.a = make_float4(x[0], x[0], x[1], x[1]);
     r.b = make_float4(x[2], x[2], u, u);
     pdup[q] = r;
+    nAq[q] = Aq[q] * -TP_S;   // the operand of tp_incl, bitwise as pass 1 forms it
 }
 
 // Pass 2: rows are targets (lane l: targets 2l, 2l + 1 of each half of the
@@ -1587,7 +1591,8 @@ __global__ void k_pdup_s(const float *__restrict__ xs, const float *__restrict__
 // of pass 1 (the same FFMA2 chain on the same operands), shifted by u_q, and
 // in boundary blocks weighted by the same tp_incl test.
 // pass 2, one half of the warp live in an n-block: the eight points against
-// the half's target pair, tested (boundary) or not (inside)
+// the half's target pair, tested (boundary) or not (inside); Ab holds the
+// points' -A_q 2^64
 template <int D>
 __device__ __forceinline__ void fb2_half(const Rec8 *T, const float *Ab, const float2 (&W)[3], float2 C,
                                          float2 NB, bool bnd, float2 &acc) {
@@ -1602,7 +1607,7 @@ __device__ __forceinline__ void fb2_half(const Rec8 *T, const float *Ab, const f
             const float2 e = __fadd2_rn(r, make_float2(b4.z, b4.w));
             const float2 p = make_float2(ex2_approx(e.x), ex2_approx(e.y));
             const float2 v = __fadd2_rn(r, NB);
-            const float a = Ab[tt] * -TP_S;
+            const float a = Ab[tt];
             acc = __ffma2_rn(p, make_float2(tp_incl(v.x, a), tp_incl(v.y, a)), acc);
         }
     } else {
@@ -1624,7 +1629,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
     k_grad_fb(const Rec12 *__restrict__ tdup, const float4 *__restrict__ tball64,
               const float2 *__restrict__ tbe64, const float *__restrict__ tbox1024,
               const float *__restrict__ tb1024, const Rec8 *__restrict__ pdup,
-              const float *__restrict__ Aq, const float4 *__restrict__ pball8,
+              const float *__restrict__ nAq, const float4 *__restrict__ pball8,
               const float2 *__restrict__ pal8, const float *__restrict__ pbox1024,
               const float *__restrict__ pa1024, int nstages, int k2, double *__restrict__ part2,
               int *__restrict__ flags) {
@@ -1658,7 +1663,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
         const int64_t q_ = (int64_t)s_list[it_] * FB_TS;                                             \
         mbar_expect_tx(&full[sl_], kStage);                                                          \
         bulk_g2s(s_rec[sl_], pdup + q_, FB_TS * sizeof(Rec8), &full[sl_]);                           \
-        bulk_g2s(s_A[sl_], Aq + q_, FB_TS * sizeof(float), &full[sl_]);                              \
+        bulk_g2s(s_A[sl_], nAq + q_, FB_TS * sizeof(float), &full[sl_]);                              \
         bulk_g2s(s_ball[sl_], pball8 + q_ / 8, FB_NBS * sizeof(float4), &full[sl_]);                 \
         bulk_g2s(s_al[sl_], pal8 + q_ / 8, FB_NBS * sizeof(float2), &full[sl_]);                     \
     } while (0)
@@ -1753,7 +1758,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                         const float4 a4 = T[tt].a, b4 = T[tt].b;
                         const float2 x0v = make_float2(a4.x, a4.y), x1v = make_float2(a4.z, a4.w);
                         const float2 x2v = make_float2(b4.x, b4.y), u = make_float2(b4.z, b4.w);
-                        const float nA = Ab[tt] * -TP_S;
+                        const float nA = Ab[tt];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             float2 r = C[h];
@@ -1789,7 +1794,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2)
                     const float *Ab = &s_A[slot][8 * nb];
                     for (int tt = 0; tt < 8; ++tt) {
                         const float4 a4 = T[tt].a, b4 = T[tt].b;
-                        const float nA = Ab[tt] * -TP_S;
+                        const float nA = Ab[tt];
                         for (int h = 0; h < 2; ++h) {
                             if (!(((h ? lv1 : lv0) >> b) & 1u)) continue;
                             const bool bnd = ((h ? bd1 : bd0) >> b) & 1u;
@@ -2210,6 +2215,7 @@ static cudaError_t grid_build(rsot_problem *p) {
     ALLOC(g->off1b, g->ptiles + 1);
     ALLOC(g->off2b, g->ttiles + 1);
     ALLOC(g->pdup_s, g->nqt);
+    ALLOC(g->nAq_s, g->nqt);
 #undef ALLOC
     k_gather_points<<<(unsigned)((g->nqt + 255) / 256), 256, 0, st>>>(
         kq, p->nq, g->nqt, d, p->x64, p->mass, p->lmass2, g->perm_q, g->xs, g->x64, g->mass, g->lm2);
@@ -2308,11 +2314,11 @@ static cudaError_t trunc_mixed(rsot_problem *p, const double *psi, double eps, d
         k_combine_trunc<<<g->nblk_comb, 256, 0, st>>>(g->part1b, g->off1b, p->nq, g->nqt, g->xs, g->x64,
                                                       g->mass, g->lm2, g->Aq, psi, eps, D, g->ppair,
                                                       g->lse_s, g->blockJ, p->res_dev, g->u_s, nullptr, 0);
-        k_pdup_s<<<nb_of(g->nqt), 256, 0, st>>>(g->xs, g->u_s, g->nqt, D, g->pdup_s);
+        k_pdup_s<<<nb_of(g->nqt), 256, 0, st>>>(g->xs, g->u_s, g->Aq, g->nqt, D, g->pdup_s, g->nAq_s);
         trace_end(p);
         trace_begin(p, "grad_trunc_fb");
         k_grad_fb<D><<<dim3((unsigned)(g->nt / FB_ROWS), (unsigned)g->k2b), FB_THREADS, FB_SMEM2, st>>>(
-            g->tdup, g->tball64, g->tbe64, g->tbox1024, g->tb1024, g->pdup_s, g->Aq, g->pball8, g->pal8,
+            g->tdup, g->tball64, g->tbe64, g->tbox1024, g->tb1024, g->pdup_s, g->nAq_s, g->pball8, g->pal8,
             g->pbox, g->ptmax, (int)(g->nqt / FB_TS), g->k2b, g->part2b, p->flags);
         trace_end(p);
         trace_begin(p, "finalize_trunc");
@@ -2410,7 +2416,7 @@ void trunc_free(rsot_problem *p) {
                     g->pball64, g->pball8, g->tball64, g->tball8, g->prec_s, g->trec_s, g->b_s,
                     g->u_s, g->pal8, g->pal64, g->ptmax, g->tbe8, g->tbe64, g->ttmax, g->m0_s,
                     g->pbox512, g->tbox512, g->tbox1024, g->pa512, g->tb512, g->tb1024, g->part1b,
-                    g->part2b, g->off1b, g->off2b, g->pdup_s};
+                    g->part2b, g->off1b, g->off2b, g->pdup_s, g->nAq_s};
     for (void *q : ptrs) cudaFree(q);
     delete g;
     p->grid = nullptr;
