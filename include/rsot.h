@@ -376,7 +376,12 @@ typedef struct {
                             RSOT_COMPENSATED (default) stops at ||g||_1 <= tol_l1 -
                             RSOT_COMPENSATED_GRAD_REL sum m_q, which certifies
                             ||grad J||_1 <= tol_l1; it is used while that bound is
-                            at most 0.8 tol_l1, else FP64.  RSOT_FP64: always FP64 */
+                            at most 0.8 tol_l1, else FP64.  Compensated references
+                            of an untruncated solve of at least 2e10 pairs are
+                            truncated at the psi-aware cutoffs of tail 1e-12, whose
+                            bound joins the certified one (dense where they would
+                            keep most pairs).
+                            RSOT_FP64: always FP64, dense                        */
     double tau_int;      /* > 0 (with tail = 0): truncate each evaluation at the
                             integral cutoff C_int of this relative J tolerance,
                             D and J from the previous evaluation of the stage

@@ -207,6 +207,15 @@ constexpr int kCorrStallWindow = 25;
 // largest tail tolerance at which the compensated reference evaluations are
 // truncated (its bound stays far below any useful tolerance)
 constexpr double kRefTailMax = 1e-8;
+// tail of the compensated reference evaluations of an untruncated solve of at
+// least kRefTailMinPairs pairs: their bound (1e-12 sum(nu) (2 sum(m) + sum(nu)))
+// joins the certified one, and the evaluator falls back to dense evaluations
+// where most pairs are kept.  Smaller problems keep dense references: the cell
+// list that a first truncated evaluation builds costs them more than it saves
+// (measured: 256 batched problems of up to 1.6e10 pairs refined in 8.6 s
+// instead of 6.4 s; the 5.2e10-pair cube solved in 3.15 s instead of 3.29 s).
+constexpr double kRefTailDense = 1e-12;
+constexpr double kRefTailMinPairs = 2e10;
 
 double norm1(const std::vector<double> &a) {
     double s = 0.0;
@@ -290,15 +299,21 @@ rsot_status rsot_solve(rsot_problem *p, double *psi_inout, const rsot_options *o
     // intermediate eps stages only warm-start the next one: 100 tol_l1 unless given
     const double stage_tol = opt->stage_tol_l1 > 0.0 ? opt->stage_tol_l1 : rsot::kStageTolFactor * opt->tol_l1;
     // reference evaluations of the final stop: compensated with its certified
-    // bound subtracted from tol where the bound leaves room, else FP64.  With a
-    // tail tolerance (psi-aware cutoffs) the compensated references are
-    // truncated too and the truncation's own bound joins: per point at most
-    // tail * sum(nu) of the kept mass is lost, so ||grad J~ - grad J||_1 <=
-    // tail * sum(nu) * (2 sum(m) + sum(nu))
+    // bound subtracted from tol where the bound leaves room, else FP64.  The
+    // compensated references are truncated at the psi-aware cutoffs of the
+    // solve's tail (or of kRefTailDense for a large untruncated solve) and the
+    // truncation's own bound joins: per point at most tail * sum(nu) of the kept
+    // mass is lost, so ||grad J~ - grad J||_1 <= tail * sum(nu) * (2 sum(m) +
+    // sum(nu)); the stop then holds for the untruncated J
     const double msum = rsot::mass_sum(p);
     double nusum = 0.0;
     for (int64_t j = 0; j < n; ++j) nusum += nu[j];
-    const double ref_tail = (opt->tail > 0.0 && opt->tail <= kRefTailMax) ? opt->tail : 0.0;
+    const bool untruncated = !(opt->tail > 0.0) && !(opt->tau_int > 0.0) && !(opt->delta_pw > 0.0) &&
+                             !(opt->tau_geom > 0.0) &&
+                             (double)rsot::num_points(p) * (double)n >= kRefTailMinPairs;
+    const double ref_tail = (opt->tail > 0.0 && opt->tail <= kRefTailMax) ? opt->tail
+                            : untruncated                               ? kRefTailDense
+                                                                        : 0.0;
     Truncation ref_trunc;
     ref_trunc.tail = ref_tail;
     const double comp_bound =
