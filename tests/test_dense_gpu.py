@@ -212,7 +212,7 @@ def test_tensor_pairs_passes_are_consistent():
 
 def test_automatic_pair_kernel_fp32_for_results_tensor_inside_solves():
     """RSOT_PAIRS_AUTO: an evaluation returned to the caller runs the FP32 pair
-    kernels (the benchmark spec's pair arithmetic); a solve on the same handle
+    kernels (FP32 pair arithmetic, FP64 reductions); a solve on the same handle
     takes the tensor-core form for its mixed iterations (its stop is certified
     on compensated evaluations) and still meets the tolerance."""
     p = ri.cube_3d(mesh_n=8, eps=1e-3)
