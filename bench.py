@@ -54,6 +54,24 @@ FP64_OPS_PER_PAIR = {2: 47, 3: 51}
 L2_FLUSH_BYTES = 256 << 20
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The maximum of a per-rank time over the ranks of the run (an all-reduce
+    on the default process group; the value itself on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, seconds: float) -> float:
+    """Units per second of the whole job in billions: every rank processes
+    units_per_step in each of its steps (weak scaling), timed by the slowest."""
+    return units_per_step * steps * world / seconds / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -719,13 +737,8 @@ def main():
     ktimes = P.kernel_times()
     P.kernel_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = pairs * args.steps * world / total_s / 1e9
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = whole_job_rate(pairs, args.steps, world, total_s)
     ms_per_step = 1e3 * total_s / args.steps
 
     # the same evaluation with the other pair form (the tensor-core exponents,
@@ -894,12 +907,8 @@ def main():
             t = time.perf_counter()
             P.eval(psi_h, p.eps, 0.0, rs.MIXED, grad_out=grad_h)
             e2e_s += time.perf_counter() - t
-        if world > 1:
-            import torch.distributed as tdist
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": pairs * args.steps * world / e2e_s / 1e9, "unit": "G pairs/s",
+        e2e_s = max_over_ranks(e2e_s, world, dev)
+        e2e = {"value": whole_job_rate(pairs, args.steps, world, e2e_s), "unit": "G pairs/s",
                "h2d_bytes_per_step": p.n * 8, "d2h_bytes_per_step": p.n * 8 + 48}
 
     if rank != 0:
