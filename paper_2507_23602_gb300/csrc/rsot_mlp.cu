@@ -879,6 +879,31 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
+// out[b] = sum_i H3[b][i] w4[i] + b4 (FP32), one warp per row; for widths of
+// at most 256 (a multiple of 8) lane l takes columns 8l .. 8l + 7 in one
+// 16-byte load
+__global__ void k_head_v8(const bf16 *__restrict__ H, int width, int64_t rows, const float *__restrict__ w,
+                          const float *__restrict__ b, float *__restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.f;
+    if (8 * lane < width) {
+        const uint4 hv = *reinterpret_cast<const uint4 *>(H + r * width + 8 * lane);
+        const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hv);
+        const float4 wa = *reinterpret_cast<const float4 *>(w + 8 * lane);
+        const float4 wb = *reinterpret_cast<const float4 *>(w + 8 * lane + 4);
+        const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 hf = __bfloat1622float2(h2[k]);
+            s = fmaf(hf.x, wv[2 * k], s);
+            s = fmaf(hf.y, wv[2 * k + 1], s);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s + b[0];
+}
 // out[b] = sum_i H3[b][i] w4[i] + b4 (FP32), one warp per row
 __global__ void k_head(const bf16 *__restrict__ H, int width, int64_t rows, const float *__restrict__ w,
                        const float *__restrict__ b, float *__restrict__ out) {
@@ -935,7 +960,7 @@ __device__ __forceinline__ void hb_row(const uint4 &zv, const uint4 &hv, float d
         s4[2 * k + 1] = fmaf(d, h.y, s4[2 * k + 1]);
     }
 }
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     k_head_back_v8(const float *__restrict__ out, const float *__restrict__ y, int64_t rows,
                    int64_t valid, float inv_b, const float *__restrict__ w4, const bf16 *__restrict__ Z3,
                    const bf16 *__restrict__ H3, int width, float *__restrict__ dout, bf16 *__restrict__ dZ3,
@@ -1135,10 +1160,10 @@ inline size_t red_floats(int w) {
 }
 
 // out[c] = sum_r wgt[r] X[r][c]; part: red_floats(cols) floats
-// row chunks of the 256-thread streaming kernels: four blocks per SM (two
-// waves at two resident blocks), at least 64 rows each
-inline int stream_chunks(int64_t rows, int sms, int most) {
-    return (int)std::min<int64_t>(std::min<int64_t>(most, 4 * (int64_t)std::max(1, sms)),
+// row chunks of the 256-thread streaming kernels: per_sm blocks per SM, at
+// least 64 rows each
+inline int stream_chunks(int64_t rows, int sms, int most, int per_sm = 4) {
+    return (int)std::min<int64_t>(std::min<int64_t>(most, per_sm * (int64_t)std::max(1, sms)),
                                   std::max<int64_t>(1, rows / 64));
 }
 
@@ -1183,13 +1208,23 @@ __global__ void k_to_bf16(const float *__restrict__ W, int rows, int cols, bf16 
     if (WbT) WbT[(int64_t)c * rows + r] = v;
 }
 
+// X0 = BF16 rows of the input, zero-padded from in_dim to in_pad columns (a
+// multiple of 8): one thread per row, eight columns per 16-byte store
 __global__ void k_input_bf16(const float *__restrict__ x, int64_t rows, int in_dim, int in_pad,
                              bf16 *__restrict__ X0) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * in_pad) return;
-    const int64_t r = i / in_pad;
-    const int c = (int)(i % in_pad);
-    X0[i] = __float2bfloat16(c < in_dim ? x[r * in_dim + c] : 0.f);
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const float *xr = x + r * in_dim;
+    for (int c0 = 0; c0 < in_pad; c0 += 8) {
+        uint4 v;
+        uint32_t *vp = &v.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + 2 * k;
+            vp[k] = pack_bf16(c < in_dim ? xr[c] : 0.f, c + 1 < in_dim ? xr[c + 1] : 0.f);
+        }
+        *reinterpret_cast<uint4 *>(X0 + r * in_pad + c0) = v;
+    }
 }
 
 // C[r][c] = sum_z ws[z][r][c] (the split-K partials, in slice order)
@@ -1454,7 +1489,7 @@ rsot_status mlp_take_flags(rsot_mlp *m, int fl) {
 void mlp_forward(rsot_mlp *m, int64_t rows) {
     const int w = m->width, R = (int)((rows + 127) / 128 * 128);
     cudaStream_t st = m->stream;
-    k_input_bf16<<<(unsigned)((R * (int64_t)m->in_pad + 255) / 256), 256, 0, st>>>(m->xin, R, m->in_dim,
+    k_input_bf16<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(m->xin, R, m->in_dim,
                                                                                  m->in_pad, m->X0);
     gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, m->in_pad, m->X0, m->in_pad, m->W1b, m->in_pad, nullptr,
                                       w, m->P + m->off[1], m->H1, w, m->Z1, w);
@@ -1462,7 +1497,10 @@ void mlp_forward(rsot_mlp *m, int64_t rows) {
                                       m->H2, w, m->Z2, w);
     gemm<false, false, EPI_BIAS_SILU>(st, m->gemm_kind, m->flags, m->ws, m->sms, R, w, w, m->H2, w, m->W3b, w, nullptr, w, m->P + m->off[5],
                                       m->H3, w, m->Z3, w);
-    k_head<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->H3, w, R, m->P + m->off[6], m->P + m->off[7], m->out);
+    if (w % 8 == 0 && w <= 256)
+        k_head_v8<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->H3, w, R, m->P + m->off[6], m->P + m->off[7], m->out);
+    else
+        k_head<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(m->H3, w, R, m->P + m->off[6], m->P + m->off[7], m->out);
 }
 
 // forward + backward: gradients of loss = sum_valid (out - y)^2 / (2 rows) into m->G;
@@ -1475,7 +1513,7 @@ void mlp_backward(rsot_mlp *m, int64_t rows, float *loss_sum) {
     if (w % 8 == 0 && w <= 256) {
         // head back-propagation with its column sums: dw4 = sum_r dout_r H3[r],
         // db3 = colsum dZ3, db4 = sum_r dout_r and the loss
-        const int ch = stream_chunks(R, m->sms, HB_CHUNKS);
+        const int ch = stream_chunks(R, m->sms, HB_CHUNKS, 3);   // one wave of three blocks per SM
         float *p3 = m->red, *p4 = p3 + (size_t)HB_CHUNKS * w, *p5 = p4 + (size_t)HB_CHUNKS * w,
               *p6 = p5 + HB_CHUNKS;
         k_head_back_v8<<<(unsigned)ch, 256, 0, st>>>(m->out, m->yin, R, rows, 1.0f / (float)rows,
