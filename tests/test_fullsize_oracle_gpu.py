@@ -75,3 +75,24 @@ def test_full_size_psi_aware_truncated_mixed_elementwise_against_oracle(cube):
     assert abs(J - Jo) <= J_TOL * abs(Jo), (J, Jo)
     err = np.abs(g - go)
     assert np.max(err) <= G_TOL, (np.argmax(err), np.max(err))
+
+
+def test_full_size_solve_certified_with_truncated_references(cube):
+    """The cube solve of the bench (eps 0.1 -> 1e-3, x0.5, tol 1e-6, mixed with
+    the compensated refinement): at 5.2e10 pairs its compensated reference
+    evaluations are truncated at tail 1e-12 with their bound in the certified
+    stop, so the oracle's dense gradient at the returned potential meets the
+    tolerance."""
+    import paper_2507_23602_gb300 as rs
+    p, _ = cube
+    P = rs.Problem(p.x, p.mass, p.y, p.nu)
+    try:
+        psi, st = P.solve(eps=p.eps, eps_start=0.1, eps_factor=0.5, tol_l1=1e-6)
+        assert st.status == 0
+        assert st.evals_prec[2] > 0                     # compensated references ran
+        # at least one reference evaluation was truncated (fewer pairs than dense)
+        assert st.pairs_prec[2] < st.evals_prec[2] * p.nq * p.n
+    finally:
+        P.close()
+    _, go, _, _ = oracle.dual_grad(p.x, p.mass, p.y, p.nu, psi, p.eps)
+    assert np.abs(go).sum() <= 1e-6 * (1 + 1e-9)
