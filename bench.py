@@ -220,9 +220,16 @@ def cpu_baseline(p, psi, target_seconds=12.0):
     oracle.dual_grad(p.x[:s], p.mass[:s], p.y, p.nu, psi, p.eps)
     dt = time.perf_counter() - t
     pairs = s * p.n
+    # the same oracle on one thread, on a sample of about 5 s
+    s1 = max(16, min(p.nq, int(s * 5.0 / max(dt * cores, 1e-3))))
+    t = time.perf_counter()
+    oracle.dual_grad(p.x[:s1], p.mass[:s1], p.y, p.nu, psi, p.eps, threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": pairs / dt / 1e9, "unit": "G pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"dense FP64 evaluation of quadrature points 0..{s - 1} of {p.nq} against all "
-                      f"{p.n} targets ({pairs:.3e} pairs, {dt:.1f} s)"}
+                      f"{p.n} targets ({pairs:.3e} pairs, {dt:.1f} s)",
+            "single_thread": {"value": s1 * p.n / dt1 / 1e9, "unit": "G pairs/s", "cores": 1,
+                              "sample": f"points 0..{s1 - 1} ({s1 * p.n:.3e} pairs, {dt1:.1f} s)"}}
 
 
 def run_reference(args, p, psi, workload):
