@@ -655,14 +655,15 @@ rsot_status rsot_mlp_create(int in_dim, int width, uint64_t seed, rsot_mlp **out
 void rsot_mlp_destroy(rsot_mlp *m);
 rsot_status rsot_mlp_set_stream(rsot_mlp *m, void *stream);
 /* GEMM kernel of the network's layers (forward, back-propagation, weight
- * gradients): RSOT_MLP_GEMM_TCGEN05 (default: tcgen05.mma issued by one thread
- * per CTA, FP32 accumulator in tensor memory, 128 x 128 tiles; operands whose
- * K runs along rows of 16-byte-aligned BF16 arrive by TMA tensor copies, the
- * transposed operands of the weight gradients by cp.async),
- * RSOT_MLP_GEMM_TCGEN05_CPASYNC (the same kernel with cp.async copies only) or
- * RSOT_MLP_GEMM_MMA_SYNC (warp-level mma.sync m16n8k16).  Same operands and
- * epilogues; the sums differ only in the order of FP32 accumulation (the two
- * tcgen05 forms give equal results).
+ * gradients): RSOT_MLP_GEMM_TCGEN05 (default: tcgen05.mma issued by one thread,
+ * FP32 accumulators in tensor memory, operands by TMA tensor copies; where the
+ * output width is at most 256 and a multiple of 32, a persistent kernel with
+ * one CTA per SM, a copy warp, an MMA warp and 16 epilogue warps over two
+ * accumulators, its outputs stored by TMA; otherwise 128 x 128 tiles),
+ * RSOT_MLP_GEMM_TCGEN05_CPASYNC (the 128 x 128 tcgen05 kernel with cp.async
+ * copies only) or RSOT_MLP_GEMM_MMA_SYNC (warp-level mma.sync m16n8k16).  Same
+ * operands, K slices and epilogues; the sums differ only in the order of FP32
+ * accumulation (the two tcgen05 forms give equal results).
  * Errors: RSOT_ERR_ARG (NULL handle or unknown kind).  Calls that run the
  * tcgen05 kernel return RSOT_ERR_TIMEOUT when one of its bounded waits gave up. */
 enum { RSOT_MLP_GEMM_TCGEN05 = 0, RSOT_MLP_GEMM_MMA_SYNC = 1, RSOT_MLP_GEMM_TCGEN05_CPASYNC = 2 };
