@@ -58,10 +58,13 @@ def elementwise(a, b, s):
 # (3, 64, 37): fewer rows than one TMA box; (5, 104, 300): K = 104, so the
 # second K box is zero-filled past 40 of its 64 columns, and N = 104 < 128 rows;
 # (6, 96, 500) and (4, 160, 333): the persistent kernel's last 64-column box
-# half filled (N = 96, 160 are multiples of 32, not of 64)
+# half filled (N = 96, 160 are multiples of 32, not of 64); (40, 128, 700):
+# in_pad 64, a full K box in the first layer and N = 64 in its weight
+# gradient; (3, 32, 129): the narrowest persistent-kernel width, two row tiles
 @pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 1000), (18, 256, 4096), (5, 64, 300),
                                                (7, 200, 777), (3, 64, 37), (5, 104, 300),
-                                               (6, 96, 500), (4, 160, 333)])
+                                               (6, 96, 500), (4, 160, 333), (40, 128, 700),
+                                               (3, 32, 129)])
 def test_forward_matches_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 7, kind)
     try:
@@ -76,7 +79,8 @@ def test_forward_matches_oracle(in_dim, width, rows, kind):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 2048), (5, 64, 300), (7, 200, 777),
-                                               (5, 104, 300), (6, 96, 500), (4, 160, 333)])
+                                               (5, 104, 300), (6, 96, 500), (4, 160, 333),
+                                               (40, 128, 700), (3, 32, 129)])
 def test_gradients_match_oracle(in_dim, width, rows, kind):
     net, x, y = setup(in_dim, width, rows, 11, kind)
     try:
@@ -126,7 +130,7 @@ def test_gemm_kernels_agree():
 
 
 @pytest.mark.parametrize("in_dim,width,rows", [(18, 256, 5000), (7, 200, 777), (3, 64, 37),
-                                               (4, 160, 333)])
+                                               (4, 160, 333), (40, 128, 700), (3, 32, 129)])
 def test_tma_and_cp_async_copies_give_equal_results(in_dim, width, rows):
     """The default tcgen05 GEMMs (TMA operand copies into 128-byte swizzled
     tiles; the persistent kernel for the BF16 epilogues where N <= 256 is a
